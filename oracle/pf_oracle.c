@@ -1,0 +1,442 @@
+/*
+ * pf_oracle.c -- plain, slow FP64 CPU oracle of the Poisson-Fermi solver
+ * (Chen, Chen, Liu, "A GPU Poisson-Fermi Solver for Ion Channel Simulations").
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark; never by the product path.  Every function follows one
+ * passage of the paper, cited beside it, in the paper's order and notation, with no
+ * blocking, fusion or reordering.  Readings of passages the paper leaves open:
+ *   - charges are spread trilinearly onto the grid instead of the Green's-function
+ *     decomposition of Eqs. (5)-(10), so the SMIB interface rows of Eqs. (17)-(18)
+ *     carry no jump term and reduce to harmonic-mean face coefficients;
+ *   - Gamma in Eq. (1) is taken from its own definition (an implicit pointwise
+ *     equation) rather than lagged from the previous iterate;
+ *   - Psi = 0 (Eq. 14) at membrane nodes and on the Dirichlet planes; the x/y sides
+ *     keep the zero-flux mirror of Eq. (4);
+ *   - the fixed charges enter the PF2 right-hand side at whatever node type holds them;
+ *   - Jacobi preconditioning is the right-preconditioned form of BiCGSTAB.
+ */
+#include "pf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- Table 1 constants ---------------------------------------------------- */
+static const double KB = 1.38e-23;        /* J/K */
+static const double QE = 1.602e-19;       /* C */
+static const double EPS0 = 8.85e-12;      /* F/m  (8.85e-14 F/cm) */
+static const double NAVO = 6.02214076e23; /* 1/mol; not printed in the paper (CODATA) */
+
+double pfo_thermal_voltage(double T) { return KB * T / QE; }
+
+/* e^2/(eps0 k_B T) expressed in Angstrom: the factor that turns -div(eps eps0 grad phi)
+ * = sum q C into -div(eps grad phi_hat) = lambda * sum z C with C in A^-3. */
+double pfo_lambda(double T) { return QE * QE / (EPS0 * KB * T * 1e-10); }
+
+double pfo_molar_to_per_A3(void) { return NAVO * 1e-27; }
+
+/* ---- species: Eq. (1) definitions of v_i, v_0, Gamma^B ----------------------- */
+int pfo_species_setup(int ns, const double* z, const double* radius_A, const double* bulk_M,
+                      double* v, double* p, double* cB, double* gammaB) {
+  if (ns < 1) return PFO_E_INVAL;
+  double v0 = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    if (radius_A[i] <= 0.0 || bulk_M[i] < 0.0) return PFO_E_INVAL;
+    v[i] = 4.0 * M_PI * radius_A[i] * radius_A[i] * radius_A[i] / 3.0;
+    v0 += v[i];
+  }
+  v0 /= ns; /* average volume over the K ions and water */
+  double g = 1.0, charge = 0.0, scale = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    p[i] = v[i] / v0;
+    cB[i] = bulk_M[i] * pfo_molar_to_per_A3();
+    g -= v[i] * cB[i];
+    charge += z[i] * cB[i];
+    scale += fabs(z[i]) * cB[i];
+  }
+  *gammaB = g;
+  if (g <= 0.0) return PFO_E_INVAL;
+  if (fabs(charge) > 1e-12 * (scale > 0.0 ? scale : 1.0)) return PFO_E_INVAL; /* neutral bath */
+  return PFO_OK;
+}
+
+/* ---- Eq. (1): Fermi-like concentrations and steric potential ----------------
+ * With C_i = cB_i exp(-z_i phi + p_i S), S = ln(Gamma/GammaB) and Gamma = 1 - sum v_i C_i,
+ * Gamma is the root of  f(u) = e^u + sum_i exp(la_i + p_i u) - 1,  u = ln Gamma,
+ * la_i = ln(v_i cB_i) - z_i phi - p_i ln GammaB.  f is increasing, so the root is unique. */
+int pfo_fermi_point(int ns, const double* z, const double* v, const double* p, const double* cB,
+                    double gammaB, double phi_hat, double* C, double* S, double* Gamma, int* iters) {
+  double la[64];
+  int used[64];
+  if (ns > 64) return PFO_E_INVAL;
+  const double lgB = log(gammaB);
+  int nterm = 0;
+  for (int i = 0; i < ns; ++i) {
+    used[i] = (cB[i] > 0.0);
+    if (used[i]) {
+      la[i] = log(v[i] * cB[i]) - z[i] * phi_hat - p[i] * lgB;
+      ++nterm;
+    }
+  }
+  /* bracket: at u_hi some term (or e^u) reaches 1, so f > 0; at u_lo every one of the
+   * nterm+1 positive parts is at most 1/(nterm+1), so f <= 0. */
+  const double lnn = log((double)(nterm + 1));
+  double hi = 0.0, lo = -lnn;
+  for (int i = 0; i < ns; ++i) {
+    if (!used[i]) continue;
+    double a = -la[i] / p[i];
+    double b = (-la[i] - lnn) / p[i];
+    if (a < hi) hi = a;
+    if (b < lo) lo = b;
+  }
+  double u = lgB;
+  if (!(u < hi && u > lo)) u = 0.5 * (lo + hi);
+  int it = 0, ok = 0;
+  for (it = 1; it <= 400; ++it) {
+    double f = exp(u) - 1.0, df = exp(u);
+    for (int i = 0; i < ns; ++i) {
+      if (!used[i]) continue;
+      double term = exp(la[i] + p[i] * u);
+      f += term;
+      df += p[i] * term;
+    }
+    if (f == 0.0) { ok = 1; break; }
+    if (f > 0.0) hi = u; else lo = u;
+    double un = u - f / df;
+    if (!(un > lo && un < hi)) un = 0.5 * (lo + hi); /* safeguard: bisect */
+    double du = un - u;
+    u = un;
+    if (fabs(du) <= 1e-15 * (fabs(u) > 1.0 ? fabs(u) : 1.0)) { ok = 1; break; }
+  }
+  if (iters) *iters = it;
+  if (!ok || !isfinite(u)) return PFO_E_GAMMA;
+  const double s = u - lgB;
+  for (int i = 0; i < ns; ++i)
+    C[i] = used[i] ? exp(log(cB[i]) - z[i] * phi_hat + p[i] * s) : 0.0;
+  *S = s;
+  *Gamma = exp(u);
+  return PFO_OK;
+}
+
+/* ---- 7-point FD operators in the diagonal storage of Section 4 --------------- */
+static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+/* Eqs. (7), (13), (15)-(18): with a zero jump the SMIB rows at x_l, x_{l+1} are
+ * eps_m[-phi_{l-1} + (2-c1) phi_l - c2 phi_{l+1}] and eps_s[-d1 phi_l + (2-d2) phi_{l+1} - phi_{l+2}],
+ * i.e. the flux form with face coefficient eps_m c2 = eps_s d1 = 2 eps_m eps_s/(eps_m+eps_s). */
+int pfo_assemble_eps(int nx, int ny, int nz, double h, const double* eps, const double* sigma,
+                     double* A) {
+  if (nx < 2 || ny < 2 || nz < 3 || h <= 0.0) return PFO_E_INVAL;
+  const long N = (long)nx * ny * nz, sx = 1, sy = nx, sz = (long)nx * ny;
+  const double ih2 = 1.0 / (h * h);
+  memset(A, 0, sizeof(double) * 7 * N);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const long c = i + nx * ((long)j + (long)ny * k);
+        if (k == 0 || k == nz - 1) { A[c] = 1.0; continue; } /* Dirichlet row, Eq. (4) */
+        const double e = eps[c];
+        double diag = 0.0, w;
+        /* east / west; at a side the ghost node mirrors its inner neighbour (zero flux) */
+        if (i < nx - 1) { w = harmonic(e, eps[c + sx]) * ih2; A[1 * N + c] -= w; diag += w; }
+        else            { w = harmonic(e, eps[c - sx]) * ih2; A[2 * N + c] -= w; diag += w; }
+        if (i > 0)      { w = harmonic(e, eps[c - sx]) * ih2; A[2 * N + c] -= w; diag += w; }
+        else            { w = harmonic(e, eps[c + sx]) * ih2; A[1 * N + c] -= w; diag += w; }
+        /* north / south */
+        if (j < ny - 1) { w = harmonic(e, eps[c + sy]) * ih2; A[4 * N + c] -= w; diag += w; }
+        else            { w = harmonic(e, eps[c - sy]) * ih2; A[3 * N + c] -= w; diag += w; }
+        if (j > 0)      { w = harmonic(e, eps[c - sy]) * ih2; A[3 * N + c] -= w; diag += w; }
+        else            { w = harmonic(e, eps[c + sy]) * ih2; A[4 * N + c] -= w; diag += w; }
+        /* up / down: interior planes always have both neighbours */
+        w = harmonic(e, eps[c + sz]) * ih2; A[6 * N + c] -= w; diag += w;
+        w = harmonic(e, eps[c - sz]) * ih2; A[5 * N + c] -= w; diag += w;
+        A[c] = diag + (sigma ? sigma[c] : 0.0);
+      }
+  return PFO_OK;
+}
+
+/* Eqs. (12), (14): eps_s (lc^2 Lap - 1) Psi = rho, written as eps_s lc^2 (-Lap_h) Psi + eps_s Psi
+ * = -rho; Psi = 0 on the boundary of the solvent domain. */
+int pfo_assemble_pf1(int nx, int ny, int nz, double h, const unsigned char* solvent,
+                     double eps_s, double lc, double* A) {
+  if (nx < 2 || ny < 2 || nz < 3 || h <= 0.0) return PFO_E_INVAL;
+  const long N = (long)nx * ny * nz;
+  const double w = eps_s * lc * lc / (h * h);
+  memset(A, 0, sizeof(double) * 7 * N);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const long c = i + nx * ((long)j + (long)ny * k);
+        if (k == 0 || k == nz - 1 || !solvent[c]) { A[c] = 1.0; continue; }
+        if (i < nx - 1) A[1 * N + c] -= w; else A[2 * N + c] -= w;
+        if (i > 0) A[2 * N + c] -= w; else A[1 * N + c] -= w;
+        if (j < ny - 1) A[4 * N + c] -= w; else A[3 * N + c] -= w;
+        if (j > 0) A[3 * N + c] -= w; else A[4 * N + c] -= w;
+        A[6 * N + c] -= w;
+        A[5 * N + c] -= w;
+        A[c] = 6.0 * w + eps_s;
+      }
+  return PFO_OK;
+}
+
+void pfo_dia_apply(int nx, int ny, int nz, const double* A, const double* x, double* y) {
+  const long N = (long)nx * ny * nz, sy = nx, sz = (long)nx * ny;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const long c = i + nx * ((long)j + (long)ny * k);
+        double s = A[c] * x[c];
+        if (i < nx - 1) s += A[1 * N + c] * x[c + 1];
+        if (i > 0) s += A[2 * N + c] * x[c - 1];
+        if (j > 0) s += A[3 * N + c] * x[c - sy];
+        if (j < ny - 1) s += A[4 * N + c] * x[c + sy];
+        if (k > 0) s += A[5 * N + c] * x[c - sz];
+        if (k < nz - 1) s += A[6 * N + c] * x[c + sz];
+        y[c] = s;
+      }
+}
+
+static double dot(long n, const double* a, const double* b) {
+  double s = 0.0;
+  for (long i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+static double norm_inf(long n, const double* a) {
+  double m = 0.0;
+  for (long i = 0; i < n; ++i) if (fabs(a[i]) > m) m = fabs(a[i]);
+  return m;
+}
+
+static int is_identity_row(long N, const double* A, long c) {
+  if (A[c] != 1.0) return 0;
+  for (int d = 1; d < 7; ++d) if (A[d * N + c] != 0.0) return 0;
+  return 1;
+}
+
+/* Table 3 (GPU Algorithm 1) with the Jacobi preconditioner M = diag(A) applied from the
+ * right, as in the preconditioned BiCGSTAB of the Templates book that the paper cites. */
+int pfo_bicgstab(int nx, int ny, int nz, const double* A, const double* b, double* x,
+                 int max_it, double tol, int norm_mode, int* iters, double* res) {
+  const long N = (long)nx * ny * nz;
+  double* r = malloc(sizeof(double) * N);
+  double* rt = malloc(sizeof(double) * N);
+  double* p = malloc(sizeof(double) * N);
+  double* ph = malloc(sizeof(double) * N);
+  double* v = malloc(sizeof(double) * N);
+  double* s = malloc(sizeof(double) * N);
+  double* sh = malloc(sizeof(double) * N);
+  double* t = malloc(sizeof(double) * N);
+  int status = PFO_E_NOCONV, it = 0;
+  double measure = 0.0;
+  if (!r || !rt || !p || !ph || !v || !s || !sh || !t) { status = PFO_E_INVAL; goto done; }
+
+  for (long c = 0; c < N; ++c) if (is_identity_row(N, A, c)) x[c] = b[c];
+
+  double bnorm = sqrt(dot(N, b, b));
+  if (bnorm == 0.0) bnorm = 1.0;
+#define PFO_MEASURE(vec) (norm_mode == 0 ? sqrt(dot(N, vec, vec)) / bnorm : norm_inf(N, vec))
+#define PFO_CONVERGED(m) (norm_mode == 0 ? (m) <= tol : (m) < tol)
+
+  pfo_dia_apply(nx, ny, nz, A, x, r); /* step 2: r0 = b - A x0, rtilde = r0 */
+  for (long c = 0; c < N; ++c) { r[c] = b[c] - r[c]; rt[c] = r[c]; }
+  measure = PFO_MEASURE(r);
+  if (PFO_CONVERGED(measure)) { status = PFO_OK; goto done; }
+
+  double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+  for (it = 1; it <= max_it; ++it) {
+    const double rho = dot(N, rt, r); /* step 4 */
+    if (rho == 0.0) { status = PFO_E_BREAKDOWN; break; }
+    if (it == 1) {
+      for (long c = 0; c < N; ++c) p[c] = r[c]; /* step 6 */
+    } else {
+      const double beta = (rho / rho_prev) * (alpha / omega); /* step 8 */
+      for (long c = 0; c < N; ++c) p[c] = r[c] + beta * (p[c] - omega * v[c]); /* step 9 */
+    }
+    for (long c = 0; c < N; ++c) ph[c] = p[c] / A[c]; /* Jacobi: phat = M^-1 p */
+    pfo_dia_apply(nx, ny, nz, A, ph, v); /* step 11 */
+    const double rtv = dot(N, rt, v);
+    if (rtv == 0.0) { status = PFO_E_BREAKDOWN; break; }
+    alpha = rho / rtv; /* step 12 */
+    for (long c = 0; c < N; ++c) s[c] = r[c] - alpha * v[c]; /* step 13 */
+    measure = PFO_MEASURE(s);
+    if (PFO_CONVERGED(measure)) { /* early exit on s: x = x + alpha phat */
+      for (long c = 0; c < N; ++c) x[c] += alpha * ph[c];
+      status = PFO_OK;
+      break;
+    }
+    for (long c = 0; c < N; ++c) sh[c] = s[c] / A[c];
+    pfo_dia_apply(nx, ny, nz, A, sh, t); /* step 14 */
+    const double tt = dot(N, t, t);
+    if (tt == 0.0) { status = PFO_E_BREAKDOWN; break; }
+    omega = dot(N, t, s) / tt; /* step 15 */
+    for (long c = 0; c < N; ++c) x[c] += alpha * ph[c] + omega * sh[c]; /* step 16 */
+    for (long c = 0; c < N; ++c) r[c] = s[c] - omega * t[c];             /* step 17 */
+    measure = PFO_MEASURE(r); /* step 18 */
+    if (PFO_CONVERGED(measure)) { status = PFO_OK; break; }
+    if (omega == 0.0) { status = PFO_E_BREAKDOWN; break; }
+    rho_prev = rho;
+  }
+  if (it > max_it) it = max_it;
+#undef PFO_MEASURE
+#undef PFO_CONVERGED
+done:
+  if (iters) *iters = it;
+  if (res) *res = measure;
+  free(r); free(rt); free(p); free(ph); free(v); free(s); free(sh); free(t);
+  return status;
+}
+
+/* Eq. (3) with the point charges spread onto the grid by trilinear weights: the source
+ * lambda * q_j * delta(r - r_j) becomes lambda q_j w_c / h^3 at the 8 corners c. */
+int pfo_spread_charges(int nx, int ny, int nz, double h, const double* origin, int nq,
+                       const double* charges, double lambda, double* f) {
+  const int n[3] = {nx, ny, nz};
+  for (int q = 0; q < nq; ++q) {
+    int i0[3];
+    double t[3];
+    for (int a = 0; a < 3; ++a) {
+      const double g = (charges[4 * q + a] - origin[a]) / h;
+      int i = (int)floor(g);
+      if (i == n[a] - 1 && g == (double)(n[a] - 1)) i = n[a] - 2; /* on the last plane */
+      if (!(g >= 0.0) || i < 0 || i > n[a] - 2) return PFO_E_INVAL;
+      i0[a] = i;
+      t[a] = g - i;
+    }
+    const double amp = lambda * charges[4 * q + 3] / (h * h * h);
+    for (int c = 0; c < 8; ++c) {
+      const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+      const double w = (dx ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) * (dz ? t[2] : 1.0 - t[2]);
+      const long id = (i0[0] + dx) + (long)nx * ((i0[1] + dy) + (long)ny * (i0[2] + dz));
+      f[id] += amp * w;
+    }
+  }
+  return PFO_OK;
+}
+
+/* ---- Table 2: sequential PF nonlinear solver (steps 2-5; step 1 is not needed
+ * because the charges are spread onto the grid) ------------------------------- */
+int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
+                 const double* eps, const unsigned char* solvent,
+                 int nq, const double* charges, double phi_lo_V, double phi_hi_V,
+                 int ns, const double* z, const double* radius_A, const double* bulk_M,
+                 double eps_s, double lc, double T, const pfo_nl_opts* opts,
+                 double* phi_V, double* C_M, double* S, double* Gamma, double* Psi_out,
+                 double* phi_hat_out, pfo_nl_report* rep) {
+  const long N = (long)nx * ny * nz;
+  const double Tv = pfo_thermal_voltage(T), lam = pfo_lambda(T);
+  pfo_nl_report R = {PFO_OK, 0, 0, 0, 0.0};
+  double v[64], pr[64], cB[64], gB;
+  if (ns > 64 || nx < 2 || ny < 2 || nz < 3) return PFO_E_INVAL;
+  int st = pfo_species_setup(ns, z, radius_A, bulk_M, v, pr, cB, &gB);
+  if (st) return st;
+
+  double* A = malloc(sizeof(double) * 7 * N);
+  double* ffix = calloc(N, sizeof(double));
+  double* b = malloc(sizeof(double) * N);
+  double* phi0 = calloc(N, sizeof(double));
+  double* phi = malloc(sizeof(double) * N);
+  double* psi = calloc(N, sizeof(double));
+  double* rho = calloc(N, sizeof(double));
+  double* kap = calloc(N, sizeof(double));
+  double* sig = calloc(N, sizeof(double));
+  double* C = calloc((size_t)ns * N, sizeof(double));
+  double* Sv = calloc(N, sizeof(double));
+  double* Gv = calloc(N, sizeof(double));
+  if (!A || !ffix || !b || !phi0 || !phi || !psi || !rho || !kap || !sig || !C || !Sv || !Gv) {
+    st = PFO_E_INVAL;
+    goto out;
+  }
+  st = pfo_spread_charges(nx, ny, nz, h, origin, nq, charges, lam, ffix);
+  if (st) goto out;
+  const double lo_hat = phi_lo_V / Tv, hi_hat = phi_hi_V / Tv;
+  const long plane = (long)nx * ny;
+#define PFO_SET_DIRICHLET(vec)                                        \
+  for (long c = 0; c < plane; ++c) { vec[c] = lo_hat; vec[N - plane + c] = hi_hat; }
+
+  /* Step 2: PF2 with rho' = Psi = 0, i.e. -div(eps grad phi0) = lambda rho_fix. */
+  pfo_assemble_eps(nx, ny, nz, h, eps, NULL, A);
+  for (long c = 0; c < N; ++c) b[c] = ffix[c];
+  PFO_SET_DIRICHLET(b);
+  int its = 0;
+  double res = 0.0;
+  st = pfo_bicgstab(nx, ny, nz, A, b, phi0, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
+  R.lin_iters_first = its;
+  R.lin_iters_total += its;
+  if (st) goto out;
+
+  for (int outer = 1; outer <= opts->max_outer; ++outer) {
+    /* Eq. (1) at Phi0 -> rho(Phi0) and rho'(Phi0) of Eq. (11) (scaled: kappa = -lambda rho') */
+    for (long c = 0; c < N; ++c) {
+      rho[c] = 0.0;
+      kap[c] = 0.0;
+      if (!solvent[c]) continue;
+      double Ci[64], s, g;
+      st = pfo_fermi_point(ns, z, v, pr, cB, gB, phi0[c], Ci, &s, &g, NULL);
+      if (st) goto out;
+      for (int i = 0; i < ns; ++i) {
+        rho[c] += z[i] * Ci[i];
+        kap[c] += lam * z[i] * z[i] * Ci[i];
+      }
+    }
+    /* Step 3: PF1, Eq. (12) */
+    pfo_assemble_pf1(nx, ny, nz, h, solvent, eps_s, lc, A);
+    for (long c = 0; c < N; ++c) b[c] = solvent[c] ? -lam * rho[c] : 0.0;
+    for (long c = 0; c < plane; ++c) { b[c] = 0.0; b[N - plane + c] = 0.0; }
+    st = pfo_bicgstab(nx, ny, nz, A, b, psi, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
+    R.lin_iters_total += its;
+    if (st) goto out;
+    /* Step 4: PF2, Eq. (13): -eps_s Lap phi - rho' phi = -eps_s Psi - rho' phi0 in the solvent,
+     * -div(eps_m grad phi) = lambda rho_fix in the membrane */
+    for (long c = 0; c < N; ++c) sig[c] = solvent[c] ? kap[c] : 0.0;
+    pfo_assemble_eps(nx, ny, nz, h, eps, sig, A);
+    for (long c = 0; c < N; ++c)
+      b[c] = (solvent[c] ? (-eps_s * psi[c] + kap[c] * phi0[c]) : 0.0) + ffix[c];
+    PFO_SET_DIRICHLET(b);
+    for (long c = 0; c < N; ++c) phi[c] = phi0[c]; /* warm start */
+    st = pfo_bicgstab(nx, ny, nz, A, b, phi, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
+    R.lin_iters_total += its;
+    if (st) goto out;
+    /* Step 5: relax and test */
+    double delta = 0.0;
+    for (long c = 0; c < N; ++c) {
+      phi[c] = opts->omega * phi0[c] + (1.0 - opts->omega) * phi[c];
+      const double d = fabs(phi[c] - phi0[c]);
+      if (d > delta) delta = d;
+      phi0[c] = phi[c];
+    }
+    R.outer_iters = outer;
+    R.delta = delta;
+    if (delta <= opts->tol_outer) break;
+    if (outer == opts->max_outer) st = PFO_E_NOCONV;
+  }
+#undef PFO_SET_DIRICHLET
+  /* concentrations, steric potential and void fraction at the final potential */
+  for (long c = 0; c < N; ++c) {
+    if (!solvent[c]) { for (int i = 0; i < ns; ++i) C[(long)i * N + c] = 0.0; Sv[c] = 0.0; Gv[c] = 0.0; continue; }
+    double Ci[64], s, g;
+    int st2 = pfo_fermi_point(ns, z, v, pr, cB, gB, phi0[c], Ci, &s, &g, NULL);
+    if (st2) { st = st2; goto out; }
+    for (int i = 0; i < ns; ++i) C[(long)i * N + c] = Ci[i];
+    Sv[c] = s;
+    Gv[c] = g;
+  }
+  {
+    const double m = pfo_molar_to_per_A3();
+    for (long c = 0; c < N; ++c) {
+      if (phi_V) phi_V[c] = phi0[c] * Tv;
+      if (phi_hat_out) phi_hat_out[c] = phi0[c];
+      if (S) S[c] = Sv[c];
+      if (Gamma) Gamma[c] = Gv[c];
+      if (Psi_out) Psi_out[c] = psi[c];
+    }
+    if (C_M) for (long c = 0; c < (long)ns * N; ++c) C_M[c] = C[c] / m;
+  }
+out:
+  R.status = st;
+  if (rep) *rep = R;
+  free(A); free(ffix); free(b); free(phi0); free(phi); free(psi); free(rho); free(kap);
+  free(sig); free(C); free(Sv); free(Gv);
+  return st;
+}

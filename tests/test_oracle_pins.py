@@ -1,0 +1,448 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test ties one oracle function to something other than itself: values printed in the
+paper (Table 1), textbook values, closed-form solutions, invariants the paper states
+(saturation, the bath state, the reduction to Poisson-Boltzmann), a dense LU solve.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1711_04060_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- constants / units
+def test_table1_constants(orc):
+    t1 = _gold("table1_constants.json")
+    kT_e = t1["k_B_J_per_K"] * t1["T_K"] / t1["e_C"]
+    assert orc.thermal_voltage(t1["T_K"]) == pytest.approx(kT_e, rel=1e-14)
+    # 50 mV in units of k_B T / e
+    assert 0.05 / orc.thermal_voltage() == pytest.approx(1.94679, abs=2e-5)
+    eps0_F_per_m = t1["eps0_F_per_cm"] * 100.0
+    lam = t1["e_C"] ** 2 / (eps0_F_per_m * t1["k_B_J_per_K"] * t1["T_K"] * 1e-10)
+    assert orc.lam(t1["T_K"]) == pytest.approx(lam, rel=1e-14)
+
+
+def test_debye_length_textbook(orc):
+    """lambda and the mol/L -> A^-3 conversion give the textbook Debye length."""
+    tb = _gold("textbook_values.json")
+    assert orc.molar_to_per_A3() == pytest.approx(tb["molar_per_A3"], rel=1e-15)
+    c = 0.1 * orc.molar_to_per_A3()
+    kappa2 = orc.lam() * (1 * 1 * c + 1 * 1 * c) / 78.5
+    assert 1.0 / math.sqrt(kappa2) == pytest.approx(tb["debye_length_0p1M_A"], abs=tb["debye_length_tol_A"])
+
+
+def test_species_setup_definitions(orc):
+    tb = _gold("textbook_values.json")
+    sp = orc.species_setup([1, -1, 0], [1.0, 2.0, 1.5], [0.1, 0.1, 55.5])
+    assert sp["status"] == 0
+    assert sp["v"][0] == pytest.approx(tb["sphere_volume_r1_A3"], rel=1e-14)
+    assert sp["v"][1] == pytest.approx(8 * tb["sphere_volume_r1_A3"], rel=1e-14)
+    # v0 is the mean volume, so the p_i average to one
+    assert sp["p"].sum() == pytest.approx(3.0, rel=1e-14)
+    # water at 55.5 M with radius 1.4 A fills about 38 % of space
+    sp2 = orc.species_setup([1, -1, 0], [0.95, 1.81, 1.4], [0.1, 0.1, 55.5])
+    vol_water = 55.5 * tb["molar_per_A3"] * 4.0 / 3.0 * math.pi * 1.4 ** 3
+    assert 0.38 < vol_water < 0.39
+    assert 0.6 < sp2["gammaB"] < 1.0 - vol_water
+    # a charged bath is rejected
+    assert orc.species_setup([1, -1, 0], [0.95, 1.81, 1.4], [0.2, 0.1, 55.5])["status"] != 0
+
+
+# ---------------------------------------------------------------- Eq. (1) pointwise step
+SPEC = ([1, -1, 0], [0.95, 1.81, 1.4], [0.1, 0.1, 55.5])
+SPEC2 = ([1, 2, -1, 0], [0.95, 0.99, 1.81, 1.4], [0.1, 0.001, 0.102, 55.5])
+
+
+@pytest.mark.parametrize("spec", [SPEC, SPEC2])
+def test_fermi_bath_state(orc, spec):
+    """phi = 0 gives Gamma = Gamma^B, S = 0 and the bulk concentrations (Section 2)."""
+    sp = orc.species_setup(*spec)
+    r = orc.fermi_point(sp, spec[0], 0.0)
+    assert r["status"] == 0
+    assert r["Gamma"] == pytest.approx(sp["gammaB"], rel=1e-15)
+    assert abs(r["S"]) < 1e-15
+    np.testing.assert_allclose(r["C"], sp["cB"], rtol=1e-14)
+    assert abs(np.dot(spec[0], r["C"])) < 1e-18  # neutral bath
+
+
+@pytest.mark.parametrize("phi", [-50.0, -3.0, 0.7, 10.0, 200.0])
+def test_fermi_equal_radii_closed_form(orc, phi):
+    """With equal radii every p_i = 1 and the void fraction has the closed form
+    Gamma = 1 / (1 + sum_i v cB_i exp(-z_i phi) / Gamma^B)."""
+    z = [1, -1, 2, 0]
+    sp = orc.species_setup(z, [1.2] * 4, [0.3, 0.5, 0.1, 40.0])
+    r = orc.fermi_point(sp, z, phi)
+    assert r["status"] == 0
+    v = sp["v"][0]
+    # sum in log space to stay finite at large |phi|
+    logs = [math.log(v * c) - zi * phi - math.log(sp["gammaB"]) for zi, c in zip(z, sp["cB"])]
+    m = max(logs)
+    if m > 0:
+        g = math.exp(-m) / (math.exp(-m) + sum(math.exp(l - m) for l in logs))
+    else:
+        g = 1.0 / (1.0 + sum(math.exp(l) for l in logs))
+    assert r["Gamma"] == pytest.approx(g, rel=1e-12)
+
+
+@pytest.mark.parametrize("phi", [10.0, -10.0, 100.0, -100.0, 1e3, -1e3, 1e6, -1e6])
+@pytest.mark.parametrize("spec", [SPEC, SPEC2])
+def test_fermi_saturation(orc, phi, spec):
+    """C_i < 1/v_i for any potential, even a huge one (Section 2), and Gamma = 1 - sum v_i C_i."""
+    sp = orc.species_setup(*spec)
+    r = orc.fermi_point(sp, spec[0], phi)
+    assert r["status"] == 0
+    # Gamma > 0 is carried by the finite steric potential S = ln(Gamma/Gamma^B); Gamma itself
+    # underflows to 0 in FP64 once ln Gamma < -745 (phi = -1e3 puts it near -3.7e3)
+    assert math.isfinite(r["S"]) and r["S"] < 0.0
+    assert 0.0 <= r["Gamma"] < 1.0
+    vc = sp["v"] * r["C"]
+    # v_i C_i = 1 - Gamma - (others) < 1 exactly; at |phi| >> 1 the exponent of Eq. (1) is a
+    # difference of two large numbers, so v_i C_i carries a rounding error of ~|phi| * 1e-16
+    tol = 1e-13 * max(1.0, abs(phi))
+    assert np.all(vc <= 1.0 + tol)
+    assert r["Gamma"] + vc.sum() == pytest.approx(1.0, abs=tol)
+
+
+def test_fermi_counterion_packing(orc):
+    """Far from the bath the counter-ion fills nearly all space."""
+    sp = orc.species_setup(*SPEC)
+    r = orc.fermi_point(sp, SPEC[0], -1e3)  # strongly negative potential attracts Na+
+    assert sp["v"][0] * r["C"][0] > 0.99
+    r = orc.fermi_point(sp, SPEC[0], 1e3)
+    assert sp["v"][1] * r["C"][1] > 0.99
+
+
+def test_fermi_boltzmann_limit(orc):
+    """Vanishing ion and water volumes turn Eq. (1) into Boltzmann distributions."""
+    z = [1, -1, 0]
+    sp = orc.species_setup(z, [1e-3, 1e-3, 1e-3], [0.1, 0.1, 55.5])
+    for phi in (-4.0, -1.0, 0.5, 3.0):
+        r = orc.fermi_point(sp, z, phi)
+        np.testing.assert_allclose(r["C"], sp["cB"] * np.exp(-np.array(z) * phi), rtol=1e-7)
+
+
+def test_fermi_monotone(orc):
+    sp = orc.species_setup(*SPEC)
+    prev = None
+    for phi in np.linspace(-6, 6, 49):  # beyond this the counter-ion is packed to 1e-13
+        r = orc.fermi_point(sp, SPEC[0], phi)
+        if prev is not None:
+            assert r["C"][0] < prev[0]  # cation decreases with potential
+            assert r["C"][1] > prev[1]  # anion increases
+        prev = r["C"]
+
+
+# ---------------------------------------------------------------- operators (Eqs. 7, 12-18)
+def test_interface_1d_exact(orc):
+    """Two dielectrics (eps_m = 2 below, eps_s = 78.5 above an interface midway between two
+    node planes), phi = 0 and 1 on the Dirichlet planes: the SMIB/harmonic-face scheme
+    reproduces the exact piecewise-linear solution at every node."""
+    nx, ny, nz, h = 3, 4, 21, 0.5
+    k0 = 8  # interface between planes k0-1 and k0
+    eps = np.empty((nz, ny, nx))
+    eps[:k0] = 2.0
+    eps[k0:] = 78.5
+    A = orc.assemble_eps(nx, ny, nz, h, eps.ravel())
+    b = np.zeros((nz, ny, nx))
+    b[-1] = 1.0
+    r = orc.bicgstab(nx, ny, nz, A, b.ravel(), tol=1e-15, max_it=500)
+    assert r["status"] == 0
+    # continuum: interface at z_i = (k0 - 0.5) h, slopes J/eps on each side, total drop 1
+    zi = (k0 - 0.5) * h
+    L = (nz - 1) * h
+    J = 1.0 / (zi / 2.0 + (L - zi) / 78.5)
+    zz = h * np.arange(nz)
+    exact = np.where(zz < zi, J * zz / 2.0, J * zi / 2.0 + J * (zz - zi) / 78.5)
+    got = r["x"].reshape(nz, ny, nx)
+    np.testing.assert_allclose(got, np.broadcast_to(exact[:, None, None], got.shape), atol=1e-12)
+
+
+def test_mirror_eigenfunction_3d(orc):
+    """cos(pi a i/(nx-1)) cos(pi b j/(ny-1)) sin(pi c k/(nz-1)) is an exact eigenvector of the
+    7-point operator with mirror sides and Dirichlet planes: A phi = eps (lx + ly + lz) phi."""
+    nx, ny, nz, h, e = 5, 6, 7, 0.7, 3.5
+    a, b, c = 1, 2, 3
+    i = np.arange(nx)
+    j = np.arange(ny)
+    k = np.arange(nz)
+    ph = (np.cos(np.pi * a * i / (nx - 1))[None, None, :] * np.cos(np.pi * b * j / (ny - 1))[None, :, None]
+          * np.sin(np.pi * c * k / (nz - 1))[:, None, None])
+    lam = sum((2 - 2 * np.cos(np.pi * m / (n - 1))) / h ** 2 for m, n in ((a, nx), (b, ny), (c, nz)))
+    A = orc.assemble_eps(nx, ny, nz, h, np.full(nx * ny * nz, e))
+    y = orc.dia_apply(nx, ny, nz, A, ph.ravel()).reshape(nz, ny, nx)
+    np.testing.assert_allclose(y[1:-1], e * lam * ph[1:-1], atol=1e-11)
+    np.testing.assert_allclose(y[[0, -1]], ph[[0, -1]], atol=1e-15)
+
+
+def test_operator_row_sums_and_symmetry(orc):
+    """-div(eps grad) annihilates constants away from the Dirichlet planes, and its rows are
+    symmetric between interior nodes (the mirror sides make the full matrix nonsymmetric)."""
+    p = W.linear_problem(n=7, seed=5, n_spheres=3)
+    g = p.grid
+    sig = np.linspace(0.1, 0.9, g.n)
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, p.eps, sig)
+    ones = np.ones(g.n)
+    y = orc.dia_apply(g.nx, g.ny, g.nz, A, ones).reshape(g.shape_zyx)
+    np.testing.assert_allclose(y[2:-2], sig.reshape(g.shape_zyx)[2:-2], rtol=1e-12)
+    M = orc.dense_from_dia(g.nx, g.ny, g.nz, A)
+    idx = np.arange(g.n).reshape(g.shape_zyx)
+    inner = idx[1:-1, 1:-1, 1:-1].ravel()
+    sub = M[np.ix_(inner, inner)]
+    np.testing.assert_allclose(sub, sub.T, rtol=1e-14, atol=0)
+    # a side node couples twice as strongly to its inner neighbour as that node couples back
+    c = idx[3, 3, 0]
+    assert M[c, c + 1] == pytest.approx(2.0 * M[c + 1, c], rel=1e-14)
+    assert not np.allclose(M, M.T)
+
+
+def test_debye_huckel_slab(orc):
+    """-phi'' + kD^2 phi = 0 between two Dirichlet planes: the discrete solution is
+    A r^k + B r^-k with r + 1/r = 2 + kD^2 h^2 (linear PB / Debye-Hueckel)."""
+    nx, ny, nz, h, e, kd = 2, 3, 41, 0.8, 78.5, 0.3
+    A = orc.assemble_eps(nx, ny, nz, h, np.full(nx * ny * nz, e), np.full(nx * ny * nz, e * kd * kd))
+    b = np.zeros((nz, ny, nx))
+    b[0] = 1.0
+    b[-1] = 0.25
+    r = orc.bicgstab(nx, ny, nz, A, b.ravel(), tol=1e-15, max_it=2000)
+    assert r["status"] == 0
+    q = 2 + (kd * h) ** 2
+    rr = (q - math.sqrt(q * q - 4)) / 2
+    K = nz - 1
+    # phi_k = Ac rr^k + Bc rr^(K-k):  phi_0 = 1, phi_K = 0.25
+    M = np.array([[1.0, rr ** K], [rr ** K, 1.0]])
+    Ac, Bc = np.linalg.solve(M, [1.0, 0.25])
+    k = np.arange(nz)
+    exact = Ac * rr ** k + Bc * rr ** (K - k)
+    got = r["x"].reshape(nz, ny, nx)
+    np.testing.assert_allclose(got, np.broadcast_to(exact[:, None, None], got.shape), atol=1e-12)
+
+
+def test_pf1_structure(orc):
+    """PF1 rows: eps_s (6 lc^2/h^2 + 1) on the diagonal, identity rows in the membrane and on
+    the Dirichlet planes; with lc = 0 the system is diagonal and Jacobi-BiCGSTAB ends in one step."""
+    p = W.channel_problem(9, box_half=4.0, slab_half=2.0, pores=((0.0, 0.0, 2.0),), n_charges=0)
+    g = p.grid
+    A = orc.assemble_pf1(g.nx, g.ny, g.nz, g.h, p.solvent, 78.5, 1.2)
+    free = (p.solvent.reshape(g.shape_zyx).copy() == 1)
+    free[0] = free[-1] = False
+    free = free.ravel()
+    np.testing.assert_allclose(A[0][free], 78.5 * (6 * 1.44 / g.h ** 2 + 1))
+    assert np.all(A[0][~free] == 1.0) and np.all(A[1:, ~free] == 0.0)
+    A0 = orc.assemble_pf1(g.nx, g.ny, g.nz, g.h, p.solvent, 78.5, 0.0)
+    b = np.where(free, np.linspace(-1, 1, g.n), 0.0)
+    r = orc.bicgstab(g.nx, g.ny, g.nz, A0, b, tol=1e-14)
+    assert r["status"] == 0 and r["iters"] == 1
+    np.testing.assert_allclose(r["x"][free], b[free] / 78.5, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- Table 3 solver vs dense LU
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bicgstab_matches_dense_lu(orc, seed):
+    nx, ny, nz, h = 5, 4, 6, 0.9
+    rng_eps = W.to_f32_exact(2.0 + 76.5 * W.uniform(W.substream(seed, 1), nx * ny * nz))
+    sig = W.uniform(W.substream(seed, 2), nx * ny * nz, 0.0, 3.0)
+    b = W.uniform(W.substream(seed, 3), nx * ny * nz, -1.0, 1.0)
+    x0 = W.uniform(W.substream(seed, 4), nx * ny * nz, -0.5, 0.5)
+    A = orc.assemble_eps(nx, ny, nz, h, rng_eps, sig)
+    M = orc.dense_from_dia(nx, ny, nz, A)
+    xe = np.linalg.solve(M, b)
+    r = orc.bicgstab(nx, ny, nz, A, b, x0=x0, tol=1e-15, max_it=2000)
+    assert r["status"] == 0
+    np.testing.assert_allclose(r["x"], xe, rtol=0, atol=1e-11 * np.abs(xe).max())
+    # the paper's absolute infinity-norm stop also converges to the same solution
+    r2 = orc.bicgstab(nx, ny, nz, A, b, tol=1e-13, norm_mode=1, max_it=2000)
+    assert r2["status"] == 0 and r2["res"] < 1e-13
+    np.testing.assert_allclose(r2["x"], xe, atol=1e-10 * np.abs(xe).max())
+
+
+def test_bicgstab_pf1_matches_dense_lu(orc):
+    p = W.channel_problem(9, box_half=4.0, slab_half=2.0, pores=((0.5, 0.0, 2.0),), n_charges=0)
+    g = p.grid
+    A = orc.assemble_pf1(g.nx, g.ny, g.nz, g.h, p.solvent, 78.5, 1.2)
+    b = np.where(p.solvent == 1, W.uniform(11, g.n, -1, 1), 0.0)
+    xe = np.linalg.solve(orc.dense_from_dia(g.nx, g.ny, g.nz, A), b)
+    r = orc.bicgstab(g.nx, g.ny, g.nz, A, b, tol=1e-15, max_it=2000)
+    assert r["status"] == 0
+    np.testing.assert_allclose(r["x"], xe, atol=1e-12 * np.abs(xe).max())
+
+
+def test_bicgstab_reports_noconv(orc):
+    p = W.linear_problem(n=9, seed=3, n_spheres=4)
+    g = p.grid
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, p.eps)
+    r = orc.bicgstab(g.nx, g.ny, g.nz, A, p.b, tol=1e-14, max_it=3)
+    assert r["status"] == 3 and r["iters"] == 3
+
+
+# ---------------------------------------------------------------- charge spreading (Eq. 3)
+def test_spread_charges_moments(orc):
+    nx, ny, nz, h = 6, 5, 7, 0.8
+    org = (-2.0, -1.5, -2.4)
+    ch = np.array([[-1.1, 0.3, 0.77, 0.5], [1.0, -0.9, -1.3, -0.25], [0.4, 0.4, 2.4, 1.0]])
+    st, f = orc.spread_charges(nx, ny, nz, h, org, ch, 7.0)
+    assert st == 0
+    g = W.Grid(nx, ny, nz, h, org)
+    X, Y, Z = (a.ravel() for a in g.coords())
+    scale = 7.0 / h ** 3
+    assert f.sum() == pytest.approx(scale * ch[:, 3].sum(), rel=1e-14)
+    for coord, col in ((X, 0), (Y, 1), (Z, 2)):
+        assert (f * coord).sum() == pytest.approx(scale * (ch[:, 3] * ch[:, col]).sum(), rel=1e-13, abs=1e-10)
+    # a charge exactly on a node lands on that node only (binary-exact grid spacing)
+    hb, ob = 0.5, (-2.0, -1.5, -2.5)
+    st, f1 = orc.spread_charges(nx, ny, nz, hb, ob, np.array([[ob[0] + 2 * hb, ob[1] + 3 * hb, ob[2] + hb, 1.0]]), 1.0)
+    assert st == 0 and np.count_nonzero(f1) == 1
+    assert f1[2 + nx * (3 + ny * 1)] == 1.0 / hb ** 3
+    # and one on the last plane is kept inside the grid
+    st, f2 = orc.spread_charges(nx, ny, nz, hb, ob, np.array([[ob[0] + (nx - 1) * hb, ob[1], ob[2], 1.0]]), 1.0)
+    assert st == 0 and f2[nx - 1] == 1.0 / hb ** 3
+    st, _ = orc.spread_charges(nx, ny, nz, h, org, np.array([[100.0, 0.0, 0.0, 1.0]]), 1.0)
+    assert st != 0
+
+
+# ---------------------------------------------------------------- Table 2 nonlinear loop
+def _pb_newton(orc, prob, tiny):
+    """Separately written nonlinear Poisson-Boltzmann solve (Newton with dense LU):
+    -div(eps grad phi) = lambda [ s sum_i z_i cB_i exp(-z_i phi) ] + lambda rho_fix."""
+    g = prob.grid
+    lam = orc.lam(prob.T_K)
+    z = np.array([s.z for s in prob.species], float)
+    cB = np.array([s.bulk_M for s in prob.species]) * orc.molar_to_per_A3()
+    s = prob.solvent.astype(float)
+    _, ffix = orc.spread_charges(g.nx, g.ny, g.nz, g.h, g.origin, prob.charges, lam)
+    Tv = orc.thermal_voltage(prob.T_K)
+    phi = np.zeros(g.n).reshape(g.shape_zyx)
+    phi[0] = prob.phi_lo_V / Tv
+    phi[-1] = prob.phi_hi_V / Tv
+    phi = phi.ravel()
+    interior = np.ones(g.shape_zyx, bool)
+    interior[0] = interior[-1] = False
+    interior = interior.ravel()
+    for _ in range(60):
+        ez = np.exp(-np.outer(z, phi))
+        rho = (z[:, None] * cB[:, None] * ez).sum(0)
+        drho = (-(z * z)[:, None] * cB[:, None] * ez).sum(0)
+        A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, prob.eps, -lam * s * drho)
+        M = orc.dense_from_dia(g.nx, g.ny, g.nz, A)
+        A0 = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, prob.eps)
+        F = orc.dia_apply(g.nx, g.ny, g.nz, A0, phi) - lam * s * rho - ffix
+        F[~interior] = 0.0
+        d = np.linalg.solve(M, -F)
+        phi = phi + d
+        if np.abs(d).max() < 1e-13:
+            break
+    return phi
+
+
+def _small_channel(n=9, lc=1.2, tiny=False, charges=4, V=0.05, salt=0.1):
+    radii = (1e-3, 1e-3, 1e-3) if tiny else (0.95, 1.81, 1.4)
+    sp = [W.Species(1, radii[0], salt), W.Species(-1, radii[1], salt), W.Species(0, radii[2], 55.5)]
+    return W.channel_problem(n, box_half=8.0, slab_half=3.0, pores=((0.0, 0.0, 3.0),), n_charges=charges,
+                             charge_seed=9, phi_hi_V=V, species=sp, lc_A=lc)
+
+
+def test_pf_reduces_to_pb(orc):
+    """With lc = 0 and vanishing volumes the PF solution is the nonlinear PB solution."""
+    prob = _small_channel(9, lc=0.0, tiny=True)
+    out = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-14)
+    assert out["status"] == 0
+    pb = _pb_newton(orc, prob, True)
+    np.testing.assert_allclose(out["phi_hat"], pb, rtol=0, atol=1e-8 * np.abs(pb).max())
+
+
+def test_gouy_chapman(orc):
+    """1:1 salt next to a wall at potential phi0 (lc = 0, vanishing volumes): the discrete
+    solution converges at second order to 4 artanh(tanh(phi0/4) exp(-kD z))."""
+    errs = []
+    phi0 = 2.0
+    for nz in (101, 201):
+        L = 100.0
+        h = L / (nz - 1)
+        g = W.Grid(2, 2, nz, h, (0.0, 0.0, 0.0))
+        sp = [W.Species(1, 1e-3, 0.1), W.Species(-1, 1e-3, 0.1), W.Species(0, 1e-3, 55.5)]
+        Tv = orc.thermal_voltage()
+        z_ = [1, -1, 0]
+        out = orc.pf_solve(2, 2, nz, h, g.origin, np.full(g.n, 78.5), np.ones(g.n, np.uint8), np.zeros((0, 4)),
+                           phi0 * Tv, 0.0, z_, [s.radius_A for s in sp], [s.bulk_M for s in sp], 78.5, 0.0,
+                           tol_outer=1e-12, lin_tol=1e-14)
+        assert out["status"] == 0
+        kd = math.sqrt(orc.lam() * 2 * 0.1 * orc.molar_to_per_A3() / 78.5)
+        zz = h * np.arange(nz)
+        exact = 4 * np.arctanh(np.tanh(phi0 / 4) * np.exp(-kd * zz))
+        # far plane is held at 0 instead of the (tiny) exact value: compare away from it
+        mask = zz < 40.0
+        errs.append(np.abs(out["phi_hat"].reshape(nz, 2, 2)[:, 0, 0] - exact)[mask].max())
+    assert errs[0] < 2e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.5])
+def test_fixed_point_independent_of_omega(orc, omega):
+    prob = _small_channel(9)
+    ref = orc.pf_solve_problem(prob, omega=0.3, tol_outer=1e-12, lin_tol=1e-14)
+    out = orc.pf_solve_problem(prob, omega=omega, tol_outer=1e-12, lin_tol=1e-14)
+    assert ref["status"] == 0 and out["status"] == 0
+    np.testing.assert_allclose(out["phi_hat"], ref["phi_hat"], atol=1e-9 * np.abs(ref["phi_hat"]).max())
+
+
+def test_pf_fixed_point_satisfies_equations(orc):
+    """At convergence the PF1/PF2 pair of Eqs. (12)-(13) holds with phi0 = phi, i.e.
+    -div(eps grad phi) = -s eps_s Psi + lambda rho_fix and eps_s(lc^2 Lap - 1) Psi = lambda rho(phi)."""
+    prob = _small_channel(9)
+    g = prob.grid
+    out = orc.pf_solve_problem(prob, tol_outer=1e-13, lin_tol=1e-14)
+    assert out["status"] == 0
+    lam = orc.lam()
+    _, ffix = orc.spread_charges(g.nx, g.ny, g.nz, g.h, g.origin, prob.charges, lam)
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, prob.eps)
+    phi = out["phi_hat"]
+    s = prob.solvent.astype(float)
+    res = orc.dia_apply(g.nx, g.ny, g.nz, A, phi) + s * prob.eps_s * out["Psi"] - ffix
+    res = res.reshape(g.shape_zyx)[1:-1]
+    scale = np.abs(ffix).max()
+    assert np.abs(res).max() < 1e-8 * scale
+    # PF1 with rho from the returned concentrations
+    m = orc.molar_to_per_A3()
+    rho = sum(sp.z * out["C_M"][i] * m for i, sp in enumerate(prob.species))
+    A1 = orc.assemble_pf1(g.nx, g.ny, g.nz, g.h, prob.solvent, prob.eps_s, prob.lc_A)
+    r1 = orc.dia_apply(g.nx, g.ny, g.nz, A1, out["Psi"]) + lam * rho * s
+    free = (prob.solvent.reshape(g.shape_zyx).copy() == 1)
+    free[0] = free[-1] = False
+    assert np.abs(r1[free.ravel()]).max() < 1e-8 * np.abs(lam * rho).max()
+
+
+def test_pf_zero_field_is_bath(orc):
+    """No charges and no applied voltage: phi = 0 and the bath concentrations everywhere."""
+    prob = _small_channel(9, charges=0, V=0.0)
+    out = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-12)
+    assert out["status"] == 0
+    assert np.abs(out["phi_hat"]).max() == 0.0
+    sol = prob.solvent == 1
+    for i, sp in enumerate(prob.species):
+        np.testing.assert_allclose(out["C_M"][i][sol], sp.bulk_M, rtol=1e-14)
+        assert np.all(out["C_M"][i][~sol] == 0.0)
+
+
+def test_pf_antisymmetry(orc):
+    """Reversing the applied voltage and every fixed charge, with cation and anion of equal
+    size, reverses the potential and swaps the two ion profiles."""
+    sp = [W.Species(1, 1.2, 0.1), W.Species(-1, 1.2, 0.1), W.Species(0, 1.4, 55.5)]
+    a = W.channel_problem(9, box_half=8.0, slab_half=3.0, pores=((0.0, 0.0, 3.0),), n_charges=4, charge_seed=9,
+                          phi_hi_V=0.05, phi_lo_V=-0.05, species=sp)
+    b = W.channel_problem(9, box_half=8.0, slab_half=3.0, pores=((0.0, 0.0, 3.0),), n_charges=4, charge_seed=9,
+                          phi_hi_V=-0.05, phi_lo_V=0.05, species=sp)
+    b.charges[:, 3] *= -1
+    oa = orc.pf_solve_problem(a, tol_outer=1e-12, lin_tol=1e-14)
+    ob = orc.pf_solve_problem(b, tol_outer=1e-12, lin_tol=1e-14)
+    np.testing.assert_allclose(ob["phi_hat"], -oa["phi_hat"], atol=1e-9 * np.abs(oa["phi_hat"]).max())
+    np.testing.assert_allclose(ob["C_M"][0], oa["C_M"][1], rtol=1e-8, atol=1e-12)
