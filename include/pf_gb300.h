@@ -1,0 +1,246 @@
+/*
+ * pf_gb300.h -- C ABI of the GB300 (sm_103a) Poisson-Fermi solver.
+ *
+ * The library solves the Poisson-Fermi (PF) model of Chen, Chen and Liu, "A GPU
+ * Poisson-Fermi Solver for Ion Channel Simulations": the Fermi-like concentrations and
+ * steric potential of Eq. (1), the fourth-order PF equation (2) split into the two
+ * second-order equations PF1 (12) and PF2 (13) of the inexact-Newton linearisation (11),
+ * discretised by the 7-point finite-difference scheme of Section 3 with the simplified
+ * matched-interface (SMIB) rows of Eqs. (15)-(18), and solved by the nonlinear iteration of
+ * Table 4 around Jacobi-preconditioned BiCGSTAB (Table 3).  All arithmetic of the solve runs
+ * in CUDA kernels on one GPU; this header is the whole interface.
+ *
+ * Conventions shared by every call:
+ *  - Grid: nx*ny*nz nodes, uniform spacing h (Angstrom), node (i,j,k) at
+ *    origin + h*(i,j,k).  Arrays are node-major with x fastest: id = i + nx*(j + ny*k)
+ *    (the index order of the diagonal storage in Section 4).  N = nx*ny*nz counts the
+ *    boundary nodes, as the paper's N does.
+ *  - Boundary conditions (Eq. 4): Dirichlet values on the planes k = 0 and k = nz-1,
+ *    zero normal flux (mirror ghost nodes) on the four x/y sides.
+ *  - Scaled units: lengths in Angstrom, concentrations in Angstrom^-3 inside the solver,
+ *    potential phi_hat = e*phi/(k_B T); the constants are those of Table 1.  Inputs and
+ *    outputs of pf_nonlinear_solve are in volts and mol/L.
+ *  - Pointers: "host" arrays are read (or written) during the call only and stay owned by
+ *    the caller.  "device" arrays are device pointers of the current CUDA device, used in
+ *    stream order on the grid's stream; the call returns after its work on that stream has
+ *    finished.  The library owns and frees every device buffer it allocates.
+ *  - Errors: every call returns a pf_status and never aborts.  pf_last_error() gives a
+ *    message for the calling thread's last failing call.  Non-convergence and breakdown
+ *    still write the last iterate and the report.
+ *  - Threads: one grid must not be used by two threads at once; different grids may.
+ */
+#ifndef PF_GB300_H
+#define PF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PF_OK = 0,
+  PF_E_INVAL = 1,      /* bad argument (sizes, pointers, non-neutral bath, charge off grid) */
+  PF_E_OOM = 2,        /* device allocation failed, or a request can never fit the budget */
+  PF_E_NOCONV = 3,     /* iteration limit reached before the tolerance */
+  PF_E_BREAKDOWN = 4,  /* BiCGSTAB breakdown (rho, r~.v or omega became zero) */
+  PF_E_GAMMA = 5,      /* the pointwise void-fraction root of Eq. (1) was not found */
+  PF_E_CUDA = 6,       /* a CUDA runtime error (message in pf_last_error) */
+  PF_E_TIMEOUT = 7,    /* a bounded device wait ran out */
+  PF_PENDING = 8       /* serving: the ticket has not finished yet */
+} pf_status;
+
+typedef enum { PF_FP64 = 0, PF_MIXED = 1 } pf_precision;
+
+/* Linear operators that pf_linear_solve can invert (all 7-point, Section 3):
+ *  PF_OP_POISSON: (A x)_c = (1/h^2) sum_nb eps_f (x_c - x_nb), eps_f = 2 eps_a eps_b/(eps_a+eps_b)
+ *                 (Eqs. 7 and 15-18 with zero jump), identity rows on k = 0, nz-1;
+ *  PF_OP_PF2:     the same plus s_c kappa_c x_c (Eq. 13 with kappa = -lambda rho'(phi_0)),
+ *                 kappa from pf_set_kappa (zero until set), s_c = 1 at solvent nodes;
+ *  PF_OP_PF1:     eps_s (lc^2/h^2 sum_nb (x_c - x_nb) + x_c) at solvent nodes off the Dirichlet
+ *                 planes (Eq. 12), identity rows at membrane nodes and on k = 0, nz-1 (Eq. 14). */
+typedef enum { PF_OP_POISSON = 0, PF_OP_PF1 = 1, PF_OP_PF2 = 2 } pf_operator;
+
+typedef enum { PF_MEM_HOST = 0, PF_MEM_DEVICE = 1 } pf_mem;
+
+/* Stop tests: PF_NORM_REL2 stops when ||b - A x||_2 <= tol * ||b||_2; PF_NORM_ABSINF stops
+ * when ||b - A x||_inf < tol (the test of Table 3, step 19). */
+typedef enum { PF_NORM_REL2 = 0, PF_NORM_ABSINF = 1 } pf_norm;
+
+#define PF_MAX_SPECIES 8
+
+typedef struct pf_grid pf_grid;
+
+typedef struct {
+  int z;            /* charge number (q_i = z e); water has z = 0 and comes last */
+  double radius_A;  /* hard-sphere radius a_i (Angstrom), v_i = 4 pi a_i^3 / 3 */
+  double bulk_M;    /* bulk concentration C_i^B (mol/L) */
+} pf_species;
+
+/* Problem data of Eqs. (1)-(4) on one grid.  All arrays are host arrays of N entries unless
+ * noted; they are copied to the device by pf_set_coeffs. */
+typedef struct {
+  const double* eps;       /* relative dielectric at each node (eps_m in the membrane/protein,
+                              eps_s in the solvent); must be > 0 */
+  const uint8_t* solvent;  /* 1 = node of the solvent domain Omega_s, 0 = biomolecular domain */
+  int n_charges;           /* number of fixed point charges (Eq. 3), may be 0 */
+  const double* charges;   /* n_charges x 4: x, y, z (Angstrom), q (units of e); spread onto
+                              the 8 corners of their cell by trilinear weights; each must lie
+                              inside the grid */
+  double phi_zlo_V;        /* Dirichlet potential on the plane k = 0 (volts) */
+  double phi_zhi_V;        /* Dirichlet potential on the plane k = nz-1 (volts) */
+  int n_species;           /* K ions + water, 1 <= n_species <= PF_MAX_SPECIES */
+  const pf_species* species;
+  double eps_s;            /* solvent dielectric constant of Eqs. (12)-(13) */
+  double lc_A;             /* correlation length l_c (Angstrom), >= 0 */
+  double T_K;              /* temperature (K); 298.15 in Table 1 */
+} pf_coeffs;
+
+typedef struct {
+  int max_iter;       /* BiCGSTAB iterations (FP64) or total inner iterations (mixed) */
+  double tol;         /* tolerance of the stop test named by `norm` */
+  int norm;           /* pf_norm */
+  int precision;      /* pf_precision: PF_FP64, or PF_MIXED = FP32 BiCGSTAB inside FP64
+                         iterative refinement (true residual b - A x in FP64) */
+  double inner_tol;   /* PF_MIXED: relative residual reduction of each FP32 inner solve */
+  int max_refine;     /* PF_MIXED: limit on FP64 refinement steps */
+} pf_solve_opts;
+
+typedef struct {
+  int status;         /* pf_status of the solve */
+  int iterations;     /* BiCGSTAB iterations performed (summed over inner solves) */
+  int refinements;    /* PF_MIXED: FP64 residual recomputations; 0 for PF_FP64 */
+  double residual;    /* final true residual: ||b-Ax||_2/||b||_2 (REL2) or ||b-Ax||_inf */
+  double time_ms;     /* device time of the solve (CUDA events on the grid's stream) */
+} pf_report;
+
+typedef struct {
+  double omega;       /* relaxation omega_PF of Table 2/4 step 5/7 (0.3 in the paper) */
+  double tol_outer;   /* stop when ||Phi - Phi_0||_inf <= tol_outer (phi_hat units) */
+  int max_outer;      /* outer (Newton) iteration limit */
+  pf_solve_opts lin;  /* options of every linear solve inside the loop */
+} pf_nl_opts;
+
+/* Output and report of pf_nonlinear_solve.  Output pointers may be NULL; `mem` says whether
+ * the non-NULL ones are host or device arrays. */
+typedef struct {
+  double* phi_V;      /* [N] electric potential (volts) */
+  double* C_M;        /* [n_species * N] concentrations (mol/L), species-major; zero outside
+                         the solvent */
+  double* S;          /* [N] steric potential S^trc = ln(Gamma/Gamma^B); zero outside the solvent */
+  double* Gamma;      /* [N] void fraction; zero outside the solvent */
+  double* Psi;        /* [N] the PF1 variable Psi of Eq. (12) (Angstrom^-2, phi_hat units) from the last
+                         outer iteration */
+  int mem;            /* pf_mem of the five arrays above */
+  /* report */
+  int status;
+  int outer_iters;
+  int lin_iters_total;
+  int lin_iters_first;  /* iterations of the initial PF2 solve (Table 4, step 4) */
+  double delta;         /* last ||Phi - Phi_0||_inf */
+  double time_ms;       /* device time of the whole solve */
+} pf_result;
+
+/* Fills the options with defaults: FP64, relative 2-norm 1e-10, 20000 iterations; mixed
+ * inner tolerance 1e-3, 64 refinements; omega 0.3, tol_outer 1e-9, 500 outer iterations. */
+void pf_default_solve_opts(pf_solve_opts* o);
+void pf_default_nl_opts(pf_nl_opts* o);
+
+/* Creates a grid: nx, ny >= 2, nz >= 3, h_A > 0; origin_A[3] is the coordinate of node (0,0,0).
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream) that every later call on
+ * this grid uses.  Allocates the device state of the grid (about 370 bytes per node: operators,
+ * FP64 and FP32 Krylov vectors, nonlinear state and outputs); returns PF_E_OOM when that fails.
+ * *out receives the handle. */
+pf_status pf_create_grid(int nx, int ny, int nz, double h_A, const double origin_A[3],
+                         void* cuda_stream, pf_grid** out);
+
+/* Copies the problem data (host arrays) to the device and builds the operators: harmonic
+ * face coefficients (Eqs. 15-18 with zero jump), diagonals and Jacobi scalings, the
+ * trilinear fixed-charge source (Eq. 3) and the species constants of Eq. (1).  Validates
+ * the bath (neutral, Gamma^B > 0) and the charges (inside the grid).  Resets kappa to 0. */
+pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c);
+
+/* Sets kappa_c (Angstrom^-2) of PF_OP_PF2 from N values in host or device memory. */
+pf_status pf_set_kappa(pf_grid* g, const double* kappa, int mem);
+
+/* Solves A x = b for the operator `op` (Table 3, Jacobi-preconditioned BiCGSTAB, preconditioner
+ * applied from the right).  b and x have N entries in host or device memory (`mem`); x holds the
+ * initial guess on entry and the solution on return; on identity rows x is first set to b.
+ * opts may be NULL (defaults); report may be NULL. */
+pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int mem,
+                          const pf_solve_opts* opts, pf_report* report);
+
+/* Runs the PF nonlinear iteration of Table 4 with the data of pf_set_coeffs: the initial PF2
+ * solve with rho' = Psi = 0, then {Fermi/steric update (Eq. 1) -> PF1 solve (Eq. 12) -> PF2
+ * solve (Eq. 13) -> Phi = omega Phi_0 + (1-omega) Phi, delta = ||Phi - Phi_0||_inf} until
+ * delta <= tol_outer, and finally the concentrations, S and Gamma at the converged potential.
+ * opts may be NULL (defaults).  The result structure receives the outputs and the report. */
+pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res);
+
+/* ---- profiling: device time per kernel kind on one grid ----------------------------------- */
+enum {
+  PF_PROF_INIT = 0,        /* BiCGSTAB start: r0 = b - A x0 (Table 3, step 2) */
+  PF_PROF_B_FP64 = 1,      /* phase B in FP64: s, t = A M^-1 s and its inner products (steps 13-15) */
+  PF_PROF_CA_FP64 = 2,     /* phase C+A in FP64: x, r updates, next p and v = A M^-1 p (steps 16-17, 9-12) */
+  PF_PROF_B_FP32 = 3,      /* the same two phases in FP32 (mixed precision inner solves) */
+  PF_PROF_CA_FP32 = 4,
+  PF_PROF_RESIDUAL = 5,    /* FP64 true residual b - A x of iterative refinement */
+  PF_PROF_FERMI = 6,       /* pointwise Fermi/steric step of Eq. (1) */
+  PF_PROF_OTHER = 7,       /* setup, right-hand sides, relaxation, output conversion */
+  PF_PROF_KINDS = 8
+};
+
+typedef struct {
+  long long launches;                 /* kernels launched on this grid since the last reset */
+  long long count[PF_PROF_KINDS];     /* launches per kind while profiling was on */
+  double ms[PF_PROF_KINDS];           /* summed device time per kind (CUDA events around each launch) */
+} pf_profile;
+
+/* on != 0 resets the counters and starts timing every kernel launch with CUDA events (a small
+ * overhead per launch); on = 0 stops timing.  Launch counting is always on. */
+pf_status pf_profile_enable(pf_grid* g, int on);
+pf_status pf_profile_get(pf_grid* g, pf_profile* out);
+
+/* Frees the grid and all its device memory.  NULL is accepted. */
+pf_status pf_destroy_grid(pf_grid* g);
+
+/* Message of the calling thread's last failing call ("" if none). */
+const char* pf_last_error(void);
+
+/* ---- serving: continuous batching of PF solves -------------------------------------
+ * A server admits submitted problems while their device state fits the HBM budget and a
+ * slot is free, runs every admitted problem concurrently (each on its own stream, interleaved
+ * outer iteration by outer iteration by a host scheduler thread), and frees the state of a
+ * finished problem as soon as it is polled.  Results equal those of pf_nonlinear_solve on
+ * the same problem. */
+typedef struct pf_server pf_server;
+
+typedef struct {
+  int nx, ny, nz;
+  double h_A;
+  double origin_A[3];
+  pf_coeffs coeffs;   /* host arrays; copied by pf_submit, the caller may free them afterwards */
+  pf_nl_opts opts;
+} pf_request;
+
+/* hbm_budget_bytes: device memory the server may hold for problem state; max_slots: problems
+ * in flight at once (>= 1). */
+pf_status pf_server_create(size_t hbm_budget_bytes, int max_slots, pf_server** out);
+
+/* Queues a request and returns at once with a ticket.  PF_E_OOM if the request alone needs
+ * more than the whole budget (it could never be admitted); PF_E_INVAL for bad data. */
+pf_status pf_submit(pf_server* s, const pf_request* req, uint64_t* ticket);
+
+/* *done = 1 when the ticket has finished: the outputs (host arrays in `res`, `res->mem` must be
+ * PF_MEM_HOST) and the report are written and the ticket is released; returns the solve's
+ * status.  *done = 0 and PF_PENDING while it is queued or running. */
+pf_status pf_poll(pf_server* s, uint64_t ticket, pf_result* res, int* done);
+
+/* Stops the scheduler, cancels queued requests and frees everything. */
+pf_status pf_server_destroy(pf_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

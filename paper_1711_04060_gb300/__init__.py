@@ -1,1 +1,20 @@
-"""GB300-native Poisson-Fermi solver (placeholder; the binding is added with the library)."""
+"""GB300-native Poisson-Fermi solver.
+
+The solver of Chen, Chen and Liu ("A GPU Poisson-Fermi Solver for Ion Channel Simulations"):
+Jacobi-preconditioned BiCGSTAB (Table 3) on the 7-point variable-dielectric operator with
+SMIB/harmonic interface faces, inside the relaxed inexact-Newton PF iteration (Table 4) whose
+pointwise step evaluates the Fermi-like concentrations and steric potential of Eq. (1), as
+hand-written sm_103a CUDA kernels behind the C ABI of include/pf_gb300.h.
+
+Importing the package loads nothing; the binding loads libpf_gb300.so on first use and fails
+loudly when it has not been built.  `workloads` generates the seeded synthetic inputs.
+"""
+from . import workloads  # noqa: F401
+
+
+def __getattr__(name):
+    # the binding is imported lazily so that `workloads` can be used without the CUDA library
+    if name == "api":
+        from . import api
+        return api
+    raise AttributeError(name)

@@ -1,0 +1,279 @@
+"""Python binding of the C ABI (include/pf_gb300.h): argument marshalling only.
+
+The functions keep the C names (pf_create_grid, pf_set_coeffs, pf_linear_solve,
+pf_nonlinear_solve, pf_submit, pf_poll, ...) and take numpy arrays (host memory) or CUDA torch
+tensors (device memory; the pointer and the current torch stream are passed through).  Every
+step of a solve runs in the CUDA library; nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import (PF_FP64, PF_MIXED, PF_OP_POISSON, PF_OP_PF1, PF_OP_PF2, PF_MEM_HOST, PF_MEM_DEVICE,  # noqa
+                       PF_NORM_REL2, PF_NORM_ABSINF, PF_OK, PF_PENDING, STATUS_NAMES)
+
+
+class PFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def _check(status, allow=()):
+    if status != PF_OK and status not in allow:
+        raise PFError(status, B.last_error())
+    return status
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, mem) of a numpy array (host) or a torch tensor (device when on CUDA)."""
+    if _is_torch(a):
+        import torch
+        want = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        return ctypes.c_void_p(a.data_ptr()), (PF_MEM_DEVICE if a.is_cuda else PF_MEM_HOST)
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"array must be a C-contiguous numpy {np.dtype(dtype).name} array")
+    return ctypes.c_void_p(a.ctypes.data), PF_MEM_HOST
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # torch missing: use the default stream
+        pass
+    return ctypes.c_void_p(0)
+
+
+def solve_opts(max_iter=20000, tol=1e-10, norm=PF_NORM_REL2, precision=PF_FP64, inner_tol=1e-3, max_refine=64):
+    o = B.pf_solve_opts()
+    B.load().pf_default_solve_opts(ctypes.byref(o))
+    o.max_iter, o.tol, o.norm, o.precision, o.inner_tol, o.max_refine = max_iter, tol, norm, precision, inner_tol, \
+        max_refine
+    return o
+
+
+def nl_opts(omega=0.3, tol_outer=1e-9, max_outer=500, **lin):
+    o = B.pf_nl_opts()
+    B.load().pf_default_nl_opts(ctypes.byref(o))
+    o.omega, o.tol_outer, o.max_outer = omega, tol_outer, max_outer
+    o.lin = solve_opts(**lin)
+    return o
+
+
+class _Coeffs:
+    """Keeps the host arrays referenced by a pf_coeffs alive."""
+
+    def __init__(self, eps, solvent, charges, phi_lo_V, phi_hi_V, species, eps_s, lc_A, T_K):
+        self.eps = np.ascontiguousarray(eps, dtype=np.float64)
+        self.solvent = np.ascontiguousarray(solvent, dtype=np.uint8)
+        self.charges = np.ascontiguousarray(np.asarray(charges, dtype=np.float64).reshape(-1, 4))
+        self.sp = (B.pf_species * max(1, len(species)))()
+        for i, s in enumerate(species):
+            self.sp[i].z, self.sp[i].radius_A, self.sp[i].bulk_M = int(s.z), float(s.radius_A), float(s.bulk_M)
+        c = B.pf_coeffs()
+        c.eps = self.eps.ctypes.data
+        c.solvent = self.solvent.ctypes.data
+        c.n_charges = self.charges.shape[0]
+        c.charges = self.charges.ctypes.data if self.charges.size else None
+        c.phi_zlo_V, c.phi_zhi_V = float(phi_lo_V), float(phi_hi_V)
+        c.n_species = len(species)
+        c.species = self.sp
+        c.eps_s, c.lc_A, c.T_K = float(eps_s), float(lc_A), float(T_K)
+        self.c = c
+
+
+def coeffs_of(prob) -> _Coeffs:
+    return _Coeffs(prob.eps, prob.solvent, prob.charges, prob.phi_lo_V, prob.phi_hi_V, prob.species, prob.eps_s,
+                   prob.lc_A, prob.T_K)
+
+
+# ---------------------------------------------------------------- C names
+def pf_create_grid(nx, ny, nz, h_A, origin_A, cuda_stream=None):
+    org = (ctypes.c_double * 3)(*origin_A)
+    h = ctypes.c_void_p()
+    stream = _torch_stream() if cuda_stream is None else ctypes.c_void_p(cuda_stream)
+    _check(B.load().pf_create_grid(nx, ny, nz, h_A, org, stream, ctypes.byref(h)))
+    return h
+
+
+def pf_set_coeffs(grid, coeffs: _Coeffs):
+    _check(B.load().pf_set_coeffs(grid, ctypes.byref(coeffs.c)))
+
+
+def pf_set_kappa(grid, kappa):
+    p, mem = _ptr(kappa, np.float64)
+    _check(B.load().pf_set_kappa(grid, p, mem))
+
+
+def pf_linear_solve(grid, op, b, x, opts=None, allow=()):
+    """Solves A x = b in place of x; returns the report as a dict.  Statuses in `allow` do not raise."""
+    pb, mb = _ptr(b, np.float64)
+    px, mx = _ptr(x, np.float64)
+    if mb != mx:
+        raise TypeError("b and x must both be host or both be device arrays")
+    rep = B.pf_report()
+    st = B.load().pf_linear_solve(grid, op, pb, px, mb, ctypes.byref(opts) if opts is not None else None,
+                                  ctypes.byref(rep))
+    _check(st, allow)
+    return {"status": rep.status, "iterations": rep.iterations, "refinements": rep.refinements,
+            "residual": rep.residual, "time_ms": rep.time_ms}
+
+
+def pf_nonlinear_solve(grid, n_nodes, n_species, opts=None, out=None, allow=()):
+    """Runs the PF iteration; `out` maps phi_V/C_M/S/Gamma/Psi to preallocated arrays (numpy or CUDA
+    tensors, all of one kind); by default fresh numpy arrays are returned."""
+    if out is None:
+        out = {"phi_V": np.zeros(n_nodes), "C_M": np.zeros(n_species * n_nodes), "S": np.zeros(n_nodes),
+               "Gamma": np.zeros(n_nodes), "Psi": np.zeros(n_nodes)}
+    res = B.pf_result()
+    mems = set()
+    for k in ("phi_V", "C_M", "S", "Gamma", "Psi"):
+        if out.get(k) is not None:
+            p, m = _ptr(out[k], np.float64)
+            setattr(res, k, p.value)
+            mems.add(m)
+    if len(mems) > 1:
+        raise TypeError("outputs must all be host or all be device arrays")
+    res.mem = mems.pop() if mems else PF_MEM_HOST
+    st = B.load().pf_nonlinear_solve(grid, ctypes.byref(opts) if opts is not None else None, ctypes.byref(res))
+    _check(st, allow)
+    rep = {"status": res.status, "outer_iters": res.outer_iters, "lin_iters_total": res.lin_iters_total,
+           "lin_iters_first": res.lin_iters_first, "delta": res.delta, "time_ms": res.time_ms}
+    return out, rep
+
+
+def pf_destroy_grid(grid):
+    if grid is not None and grid.value:
+        _check(B.load().pf_destroy_grid(grid))
+
+
+def pf_profile_enable(grid, on=True):
+    _check(B.load().pf_profile_enable(grid, 1 if on else 0))
+
+
+def pf_profile_get(grid):
+    """{'launches': n, '<kind>': (count, ms), ...} for the grid's kernel launches."""
+    p = B.pf_profile()
+    _check(B.load().pf_profile_get(grid, ctypes.byref(p)))
+    out = {"launches": p.launches}
+    for k, name in enumerate(B.PROF_NAMES):
+        out[name] = (p.count[k], p.ms[k])
+    return out
+
+
+def pf_last_error():
+    return B.last_error()
+
+
+def pf_server_create(hbm_budget_bytes, max_slots):
+    h = ctypes.c_void_p()
+    _check(B.load().pf_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+    return h
+
+
+def make_request(prob, opts=None):
+    """A pf_request for a problem of the workloads module (keeps its arrays alive on the object)."""
+    q = B.pf_request()
+    g = prob.grid
+    q.nx, q.ny, q.nz, q.h_A = g.nx, g.ny, g.nz, g.h
+    for a in range(3):
+        q.origin_A[a] = g.origin[a]
+    co = coeffs_of(prob)
+    q.coeffs = co.c
+    q.opts = opts if opts is not None else nl_opts()
+    q._keep = co
+    return q
+
+
+def pf_submit(server, request):
+    t = ctypes.c_uint64()
+    _check(B.load().pf_submit(server, ctypes.byref(request), ctypes.byref(t)))
+    return t.value
+
+
+def pf_poll(server, ticket, n_nodes, n_species, allow=()):
+    """(done, outputs-or-None, report-or-None) for a ticket; outputs are numpy arrays."""
+    out = {"phi_V": np.zeros(n_nodes), "C_M": np.zeros(n_species * n_nodes), "S": np.zeros(n_nodes),
+           "Gamma": np.zeros(n_nodes)}
+    res = B.pf_result()
+    for k in out:
+        setattr(res, k, out[k].ctypes.data)
+    res.mem = PF_MEM_HOST
+    done = ctypes.c_int(0)
+    st = B.load().pf_poll(server, ticket, ctypes.byref(res), ctypes.byref(done))
+    if not done.value:
+        _check(st, allow=(PF_PENDING,))
+        return False, None, None
+    _check(st, allow)
+    return True, out, {"status": res.status, "outer_iters": res.outer_iters, "lin_iters_total": res.lin_iters_total,
+                       "delta": res.delta, "time_ms": res.time_ms}
+
+
+def pf_server_destroy(server):
+    if server is not None and server.value:
+        _check(B.load().pf_server_destroy(server))
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class Grid:
+    """Owns one pf_grid handle."""
+
+    def __init__(self, nx, ny, nz, h_A, origin_A, cuda_stream=None):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n = nx * ny * nz
+        self.n_species = 0
+        self.handle = pf_create_grid(nx, ny, nz, h_A, origin_A, cuda_stream)
+
+    @classmethod
+    def for_problem(cls, prob, cuda_stream=None):
+        g = prob.grid
+        grid = cls(g.nx, g.ny, g.nz, g.h, g.origin, cuda_stream)
+        grid.set_problem(prob)
+        return grid
+
+    def set_problem(self, prob):
+        self._coeffs = coeffs_of(prob)
+        self.n_species = len(prob.species)
+        pf_set_coeffs(self.handle, self._coeffs)
+
+    def set_coeffs(self, eps, solvent, charges, phi_lo_V, phi_hi_V, species, eps_s, lc_A, T_K=298.15):
+        self._coeffs = _Coeffs(eps, solvent, charges, phi_lo_V, phi_hi_V, species, eps_s, lc_A, T_K)
+        self.n_species = len(species)
+        pf_set_coeffs(self.handle, self._coeffs)
+
+    def set_kappa(self, kappa):
+        pf_set_kappa(self.handle, kappa)
+
+    def linear_solve(self, op, b, x, opts=None, allow=()):
+        return pf_linear_solve(self.handle, op, b, x, opts, allow)
+
+    def nonlinear_solve(self, opts=None, out=None, allow=()):
+        return pf_nonlinear_solve(self.handle, self.n, self.n_species, opts, out, allow)
+
+    def profile(self, on=True):
+        pf_profile_enable(self.handle, on)
+
+    def profile_get(self):
+        return pf_profile_get(self.handle)
+
+    def close(self):
+        pf_destroy_grid(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None:
+                self.close()
+        except Exception:
+            pass

@@ -1,0 +1,197 @@
+"""GPU-vs-oracle parity through the C ABI (run on a GB300: pytest -m gpu).
+
+Every case builds its input from the seeded generators, solves it with the CUDA library and with
+the FP64 CPU oracle, and compares element by element.  Sizes span several 32x8xZ tiles with
+ragged tails (n = 9, 33, 37, 65, non-cubic grids) so that every tile-edge, mirror-side and
+Dirichlet-plane path of the kernels is exercised.
+"""
+import numpy as np
+import pytest
+
+from paper_1711_04060_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-8     # relative potential error, FP64 path
+TOL_MIXED = 1e-6    # relative potential error, FP32 inner + FP64 refinement
+TOL_CONC = 1e-6     # relative concentration error
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_04060_gb300 import build
+    build.build()
+    from paper_1711_04060_gb300 import api as A
+    return A
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _linear_case(n, seed, shape=None):
+    p = W.linear_problem(n=n, seed=seed, n_spheres=6)
+    if shape is not None:
+        nx, ny, nz = shape
+        g = W.Grid(nx, ny, nz, 1.0, (-(nx - 1) / 2, -(ny - 1) / 2, -(nz - 1) / 2))
+        eps = W.to_f32_exact(40.0 * np.exp(0.5 * W.normal(W.substream(seed, 1), g.n)))
+        b = W.uniform(W.substream(seed, 4), g.n, -1.0, 1.0).reshape(g.shape_zyx)
+        b[0] = b[-1] = 0.0
+        p = W.LinearProblem(g, eps, b.ravel().copy())
+    return p
+
+
+def _grid_for_linear(api, p, solvent=None, lc=1.2):
+    g = p.grid
+    grid = api.Grid(g.nx, g.ny, g.nz, g.h, g.origin)
+    sol = np.ones(g.n, np.uint8) if solvent is None else solvent
+    grid.set_coeffs(p.eps, sol, np.zeros((0, 4)), 0.0, 0.0, [W.NA, W.CL, W.WATER], 78.5, lc)
+    return grid
+
+
+@pytest.mark.parametrize("n,shape", [(9, None), (33, None), (37, None), (0, (45, 11, 20)), (0, (33, 40, 5))])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_poisson_solve_matches_oracle(api, orc, n, shape, precision):
+    p = _linear_case(n, seed=11 + n, shape=shape)
+    g = p.grid
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, p.eps)
+    ref = orc.bicgstab(g.nx, g.ny, g.nz, A, p.b, tol=1e-13, max_it=20000)
+    assert ref["status"] == 0
+    grid = _grid_for_linear(api, p)
+    x = np.zeros(g.n)
+    prec = api.PF_FP64 if precision == "fp64" else api.PF_MIXED
+    rep = grid.linear_solve(api.PF_OP_POISSON, p.b, x, api.solve_opts(tol=1e-13, precision=prec))
+    grid.close()
+    assert rep["status"] == 0 and rep["residual"] <= 1e-13
+    assert _rel(x, ref["x"]) < (1e-10 if precision == "fp64" else 1e-9)
+    if precision == "fp64":
+        # the same algorithm: iteration counts agree up to rounding-driven +-2
+        assert abs(rep["iterations"] - ref["iters"]) <= 2, (rep["iterations"], ref["iters"])
+
+
+def test_dense_lu_tiny(api, orc):
+    nx, ny, nz, h = 5, 4, 6, 0.9
+    eps = W.to_f32_exact(2.0 + 76.5 * W.uniform(W.substream(3, 1), nx * ny * nz))
+    b = W.uniform(W.substream(3, 3), nx * ny * nz, -1.0, 1.0)
+    p = W.LinearProblem(W.Grid(nx, ny, nz, h, (0.0, 0.0, 0.0)), eps, b)
+    M = orc.dense_from_dia(nx, ny, nz, orc.assemble_eps(nx, ny, nz, h, eps))
+    xe = np.linalg.solve(M, b)
+    grid = _grid_for_linear(api, p)
+    x = np.zeros(nx * ny * nz)
+    grid.linear_solve(api.PF_OP_POISSON, b, x, api.solve_opts(tol=1e-14))
+    grid.close()
+    assert _rel(x, xe) < 1e-11
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 12])
+def test_fixed_iteration_count_matches_oracle(api, orc, k):
+    """After k iterations (limit reached, PF_E_NOCONV) the iterate equals the oracle's k-th iterate."""
+    p = _linear_case(33, seed=5)
+    g = p.grid
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, p.eps)
+    x0 = W.uniform(77, g.n, -0.1, 0.1)
+    ref = orc.bicgstab(g.nx, g.ny, g.nz, A, p.b, x0=x0, tol=1e-30, max_it=k)
+    grid = _grid_for_linear(api, p)
+    x = x0.copy()
+    rep = grid.linear_solve(api.PF_OP_POISSON, p.b, x, api.solve_opts(tol=1e-30, max_iter=k),
+                            allow=(3,))
+    grid.close()
+    assert rep["status"] == 3 and rep["iterations"] == k
+    assert _rel(x, ref["x"]) < 1e-11
+
+
+def test_pf1_and_pf2_operators(api, orc):
+    prob = W.channel_problem(37, box_half=9.0, slab_half=3.0, pores=((0.5, 0.0, 3.0),), n_charges=0)
+    g = prob.grid
+    grid = api.Grid.for_problem(prob)
+    # PF1 (Eq. 12): uniform faces, identity rows in the membrane
+    A1 = orc.assemble_pf1(g.nx, g.ny, g.nz, g.h, prob.solvent, prob.eps_s, prob.lc_A)
+    b1 = np.where(prob.solvent == 1, W.uniform(21, g.n, -1, 1), 0.0).reshape(g.shape_zyx)
+    b1[0] = b1[-1] = 0.0
+    b1 = b1.ravel().copy()
+    ref = orc.bicgstab(g.nx, g.ny, g.nz, A1, b1, tol=1e-13)
+    x = np.zeros(g.n)
+    grid.linear_solve(api.PF_OP_PF1, b1, x, api.solve_opts(tol=1e-13))
+    assert _rel(x, ref["x"]) < 1e-10
+    # PF2 (Eq. 13): variable faces plus kappa on solvent nodes
+    kappa = W.uniform(22, g.n, 0.0, 2.0)
+    grid.set_kappa(kappa)
+    A2 = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, prob.eps, kappa * prob.solvent)
+    b2 = W.uniform(23, g.n, -1, 1)
+    ref = orc.bicgstab(g.nx, g.ny, g.nz, A2, b2, tol=1e-13)
+    x = np.zeros(g.n)
+    grid.linear_solve(api.PF_OP_PF2, b2, x, api.solve_opts(tol=1e-13))
+    assert _rel(x, ref["x"]) < 1e-10
+    x = np.zeros(g.n)
+    grid.linear_solve(api.PF_OP_PF2, b2, x, api.solve_opts(tol=1e-12, precision=api.PF_MIXED))
+    assert _rel(x, ref["x"]) < 1e-9
+    grid.close()
+
+
+def test_absinf_stop_and_device_memory(api, orc):
+    import torch
+    p = _linear_case(33, seed=8)
+    g = p.grid
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, p.eps)
+    ref = orc.bicgstab(g.nx, g.ny, g.nz, A, p.b, tol=1e-10, norm_mode=1, max_it=20000)
+    grid = _grid_for_linear(api, p)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    rep = grid.linear_solve(api.PF_OP_POISSON, b, x, api.solve_opts(tol=1e-10, norm=api.PF_NORM_ABSINF))
+    torch.cuda.synchronize()
+    grid.close()
+    assert rep["status"] == 0 and rep["residual"] < 1e-10
+    assert abs(rep["iterations"] - ref["iters"]) <= 2
+    np.testing.assert_allclose(x.cpu().numpy(), ref["x"], atol=1e-8 * np.abs(ref["x"]).max())
+
+
+def _nl_compare(api, orc, prob, precision, tol_phi):
+    g = prob.grid
+    ref = orc.pf_solve_problem(prob, tol_outer=1e-11, lin_tol=1e-12)
+    assert ref["status"] == 0
+    grid = api.Grid.for_problem(prob)
+    prec = api.PF_FP64 if precision == "fp64" else api.PF_MIXED
+    out, rep = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=prec))
+    grid.close()
+    assert rep["status"] == 0
+    assert _rel(out["phi_V"], ref["phi_V"]) < tol_phi
+    ns = len(prob.species)
+    C = out["C_M"].reshape(ns, g.n)
+    for i in range(ns):
+        assert _rel(C[i], ref["C_M"][i]) < TOL_CONC, (i, _rel(C[i], ref["C_M"][i]))
+    sol = prob.solvent == 1
+    assert _rel(out["S"][sol], ref["S"][sol]) < TOL_CONC
+    assert _rel(out["Gamma"][sol], ref["Gamma"][sol]) < TOL_CONC
+    return rep, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nonlinear_33_single_pore(api, orc, precision):
+    """The 33^3 channel (membrane slab, pore of radius 5 A, 8 wall charges, 0.1 M NaCl, 50 mV)."""
+    rep, ref = _nl_compare(api, orc, W.config0(), precision, TOL_FP64 if precision == "fp64" else TOL_MIXED)
+    if precision == "fp64":
+        assert abs(rep["outer_iters"] - ref["report"]["outer_iters"]) <= 1
+
+
+@pytest.mark.parametrize("case", ["no_field", "lc0", "ragged", "calcium"])
+def test_nonlinear_edge_cases(api, orc, case):
+    if case == "no_field":  # bath everywhere, phi = 0
+        prob = W.channel_problem(17, box_half=8.0, slab_half=3.0, pores=((0, 0, 3.0),), n_charges=0, phi_hi_V=0.0)
+    elif case == "lc0":  # PF1 degenerates to a diagonal system
+        prob = W.channel_problem(17, box_half=8.0, slab_half=3.0, pores=((0, 0, 3.0),), n_charges=4, lc_A=0.0)
+    elif case == "ragged":  # non-cubic grid with ragged tiles in x and y
+        prob = W.channel_problem(17, box_half=8.0, slab_half=3.0, pores=((1.0, 0, 3.0),), n_charges=4)
+        g = W.Grid(35, 13, 21, 0.5, (-8.5, -3.0, -5.0))
+        X, Y, Z = g.coords()
+        memb = (np.abs(Z) < 2.0) & ((X - 1.0) ** 2 + Y ** 2 >= 4.0)
+        prob.grid = g
+        prob.solvent = (~memb).astype(np.uint8).ravel()
+        prob.eps = np.where(memb, 2.0, 78.5).ravel()
+        prob.charges = np.array([[1.0, 2.0, 0.3, 0.5], [-1.0, 1.8, -1.1, -0.5]])
+    else:  # four species with a divalent cation
+        sp = [W.Species(1, 0.95, 0.1), W.Species(2, 0.99, 0.001), W.Species(-1, 1.81, 0.102), W.WATER]
+        prob = W.channel_problem(17, box_half=8.0, slab_half=3.0, pores=((0, 0, 3.0),), n_charges=6, species=sp)
+    _nl_compare(api, orc, prob, "fp64", TOL_FP64)
