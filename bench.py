@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark: nonlinear Poisson-Fermi solves per second on one GB300.
+
+Workload: the 257^3 four-pore channel (h = 0.25 A on [-32, 32]^3: membrane slab |z| < 8 A with
+four water pores, 48 wall charges of +-0.5 e, 0.1 M NaCl + 1 mM CaCl2, 0 / +50 mV on the bath
+planes), synthetic and seeded.  One step = one full PF solve through the C ABI: operator setup,
+the initial PF2 solve and the outer iteration {Fermi/steric update -> PF1 -> PF2 -> relaxation}
+to the outer tolerance, with FP32 BiCGSTAB inside FP64 iterative refinement (mixed) by default.
+
+Printed JSON line: value = solves/s with the inputs resident in HBM and the outputs written to
+device memory; e2e = the same through pf_set_coeffs + pf_nonlinear_solve with host buffers
+(host<->device copies inside the timed region); fp64 = the plain FP64 path on the same
+workload; roofline = the dominant kernel's algorithmic bytes over its CUDA-event time against
+the measured HBM copy bandwidth; cpu_baseline = the FP64 CPU oracle timed on a bounded sample
+of the same workload on the host.  With torchrun (N > 1) every rank solves its own replica.
+
+--impl reference times the CPU oracle (the reference arm) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PF solves/s"
+UNIT = "solves/s"
+# algorithmic DRAM bytes per interior node per launch of each stencil kernel (operator data read
+# once, each vector read or written once): phase B reads r, v, M^-1, r~ and three faces and
+# writes t; phase C+A reads r, v, t, p, M^-1, x, r~ and three faces and writes x, r, p, v; the
+# PF1 operator has uniform faces (no face arrays); the FP64 residual of refinement reads x, b,
+# M^-1, the diagonal and three faces and writes the FP32 residual.
+WORDS = {"b": 8, "ca": 14, "b_pf1": 5, "ca_pf1": 11}
+KERNEL_BYTES = {
+    "b_fp32": WORDS["b"] * 4, "ca_fp32": WORDS["ca"] * 4, "b_fp64": WORDS["b"] * 8, "ca_fp64": WORDS["ca"] * 8,
+    "b_fp32_pf1": WORDS["b_pf1"] * 4, "ca_fp32_pf1": WORDS["ca_pf1"] * 4, "b_fp64_pf1": WORDS["b_pf1"] * 8,
+    "ca_fp64_pf1": WORDS["ca_pf1"] * 8, "residual_fp64": 7 * 8 + 4,
+}
+KERNEL_NAMES = {
+    "b_fp32": "k_phase_b<float, false>", "ca_fp32": "k_phase_ca<float, false>", "b_fp64": "k_phase_b<double, false>",
+    "ca_fp64": "k_phase_ca<double, false>", "b_fp32_pf1": "k_phase_b<float, true>",
+    "ca_fp32_pf1": "k_phase_ca<float, true>", "b_fp64_pf1": "k_phase_b<double, true>",
+    "ca_fp64_pf1": "k_phase_ca<double, true>", "residual_fp64": "k_residual<false>",
+}
+# Work of one FP64 solve of this workload (outer iterations, BiCGSTAB iterations), used by the
+# reference arm to turn the oracle's per-iteration cost into solves/s; the oracle runs the same
+# algorithm, whose BiCGSTAB counts agree with these up to the rounding sensitivity of BiCGSTAB.
+# The ours-arm cpu_baseline uses the counts of its own FP64 solve instead.
+REF_WORK = {"outer": 226, "lin_iters": 30000}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=257)
+    ap.add_argument("--tol-outer", type=float, default=1e-3, help="||Phi - Phi_0||_inf stop (phi_hat units)")
+    ap.add_argument("--lin-tol", type=float, default=1e-6, help="relative 2-norm tolerance of each linear solve")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=6)
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_1711_04060_gb300 import workloads as W
+    return W.config2(n=n)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while a region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(kind):
+    """DRAM bytes per interior node of one launch from the committed ncu summary, if it was
+    captured from the current kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1711_04060_gb300", "csrc", "pf_kernels.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get(kind)
+    if not e or e.get("kernel_source_sha256_16") != h:
+        return None
+    return float(e["dram_bytes_per_node"])
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(prob, phi_hat_sample, iters):
+    """Times the FP64 CPU oracle on a bounded sample of the workload: BiCGSTAB iterations on the
+    full-size PF2 operator and the pointwise Fermi step on sampled solvent nodes."""
+    import oracle
+    oracle.build()
+    g = prob.grid
+    z = [s.z for s in prob.species]
+    sp = oracle.species_setup(z, [s.radius_A for s in prob.species], [s.bulk_M for s in prob.species])
+    t0 = time.perf_counter()
+    A = oracle.assemble_eps(g.nx, g.ny, g.nz, g.h, prob.eps)
+    t_asm = time.perf_counter() - t0
+    b = np.zeros(g.n)
+    b[g.nx * g.ny: -g.nx * g.ny] = 1.0
+    t0 = time.perf_counter()
+    oracle.bicgstab(g.nx, g.ny, g.nz, A, b, tol=1e-300, max_it=1)
+    t1 = time.perf_counter()
+    oracle.bicgstab(g.nx, g.ny, g.nz, A, b, tol=1e-300, max_it=1 + iters)
+    t2 = time.perf_counter()
+    t_iter = max((t2 - t1) - (t1 - t0), 1e-9) / iters
+    del A
+    t0 = time.perf_counter()
+    for ph in phi_hat_sample:
+        oracle.fermi_point(sp, z, float(ph))
+    t_node = (time.perf_counter() - t0) / len(phi_hat_sample)
+    return {"t_iter": t_iter, "t_node": t_node, "t_asm": t_asm, "iters": iters, "nodes": len(phi_hat_sample),
+            "n_solvent": int(prob.solvent.sum())}
+
+
+def oracle_solve_time(samp, outer, lin_iters):
+    # per outer iteration: one Fermi step over the solvent nodes and two operator assemblies
+    return outer * (samp["n_solvent"] * samp["t_node"] + 2 * samp["t_asm"]) + lin_iters * samp["t_iter"]
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return
+    prob = workload(args.n)
+    rng_phi = np.linspace(-8.0, 8.0, 4000)
+    t_steps = []
+    samp = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        samp = oracle_sample(prob, rng_phi, args.cpu_iters)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            t_steps.append(oracle_solve_time(samp, REF_WORK["outer"], REF_WORK["lin_iters"]))
+    T = float(np.mean(t_steps))
+    value = 1.0 / T
+    sample = (f"{args.cpu_iters} FP64 BiCGSTAB iterations of the oracle on the full {args.n}^3 operator plus the "
+              f"pointwise Fermi step on {len(rng_phi)} nodes per step, scaled to one solve of "
+              f"{REF_WORK['outer']} outer and {REF_WORK['lin_iters']} BiCGSTAB iterations")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": T * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args),
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1, "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args):
+    return {"workload": f"pf_{args.n}_four_pores_NaCaCl", "grid": f"{args.n}^3", "h_A": 64.0 / (args.n - 1),
+            "species": "Na+ 0.1 M, Ca2+ 1 mM, Cl- 0.102 M, water 55.5 M", "charges": 48,
+            "precision": args.precision, "tol_outer": args.tol_outer, "lin_tol": args.lin_tol,
+            "omega": 0.3, "l2": "inputs larger than L2 (working set > 1 GB)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1711_04060_gb300 import api, build
+    build.build()
+    prob = workload(args.n)
+    g = prob.grid
+    N, ns = g.n, len(prob.species)
+    stream = torch.cuda.Stream(device=dev)
+    grid = api.Grid.for_problem(prob, cuda_stream=stream.cuda_stream)
+    out = {k: torch.zeros(m, dtype=torch.float64, device=dev)
+           for k, m in (("phi_V", N), ("C_M", ns * N), ("S", N), ("Gamma", N))}
+    prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
+    opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def solve(o, outs):
+        _, rep = grid.nonlinear_solve(o, out=outs, allow=(3,))
+        return rep
+
+    for _ in range(args.warmup):
+        rep = solve(opts, out)
+    barrier()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = str(local)
+    grid.profile(True)
+    reps = []
+    with Clocks(uuid) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            reps.append(solve(opts, out))
+        e1.record(stream)
+        e1.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = grid.profile_get()
+    grid.profile(False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+    clocks = clk.summary()
+    phi_mixed = out["phi_V"].cpu().numpy()
+    C_mixed = out["C_M"].cpu().numpy()
+
+    # roofline of the dominant stencil kernel (by device time in the timed region)
+    n_int = g.nx * g.ny * (g.nz - 2)
+    kinds = [k for k in KERNEL_BYTES if prof.get(k, (0, 0.0))[0] > 0]
+    dom = max(kinds, key=lambda k: prof[k][1])
+    cnt, kms = prof[dom]
+    avg_s = kms / cnt / 1e3
+    peak, peak_src = measured_peaks()
+    achieved = KERNEL_BYTES[dom] * n_int / avg_s / 1e9
+    traffic = kernel_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": (traffic * n_int) if traffic is not None else None,
+                "algorithmic_bytes_per_launch": KERNEL_BYTES[dom] * n_int, "avg_launch_ms": avg_s * 1e3,
+                "launches": cnt}
+    kernels = {k: {"launches": prof[k][0], "ms": round(prof[k][1], 3),
+                   "avg_us": round(prof[k][1] / prof[k][0] * 1e3, 2) if prof[k][0] else None,
+                   "GB/s": round(KERNEL_BYTES[k] * n_int / (prof[k][1] / prof[k][0] / 1e3) / 1e9, 1)
+                   if k in KERNEL_BYTES and prof[k][0] else None}
+               for k in prof if k != "launches" and prof[k][0] > 0}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic (seeded channel geometry, wall charges and bath; no dataset)",
+            "config": config_of(args), "clocks": clocks, "gpu_launches": int(prof["launches"]),
+            "roofline": roofline,
+            "solve": {"outer_iters": reps[-1]["outer_iters"], "lin_iters": reps[-1]["lin_iters_total"],
+                      "status": reps[-1]["status"], "delta": reps[-1]["delta"]},
+            "kernels": kernels}
+
+    # FP64 path on the same workload (solves/s and the mixed path's deviation from it)
+    fp64_rep = None
+    if not args.no_fp64 and args.precision == "mixed":
+        o64 = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_FP64)
+        out64 = {k: torch.zeros_like(v) for k, v in out.items()}
+        xw = np.zeros(N)
+        grid.linear_solve(api.PF_OP_POISSON, np.zeros(N), xw, api.solve_opts(max_iter=2), allow=(3,))
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fp64_rep = solve(o64, out64)
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        phi64 = out64["phi_V"].cpu().numpy()
+        C64 = out64["C_M"].cpu().numpy().reshape(ns, N)
+        Cm = C_mixed.reshape(ns, N)
+        line["fp64"] = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "outer_iters": fp64_rep["outer_iters"],
+                        "lin_iters": fp64_rep["lin_iters_total"], "status": fp64_rep["status"]}
+        line["accuracy_vs_fp64"] = {
+            "phi_rel": float(np.abs(phi_mixed - phi64).max() / np.abs(phi64).max()),
+            "conc_rel": float(max(np.abs(Cm[i] - C64[i]).max() / C64[i].max() for i in range(ns)))}
+        line["mixed_speedup_vs_fp64"] = value / world / (1e3 / ms64)
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        hout = {k: np.zeros(m) for k, m in (("phi_V", N), ("C_M", ns * N), ("S", N), ("Gamma", N))}
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            grid.set_problem(prob)
+            solve(opts, hout)
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        h2d = prob.eps.nbytes + prob.solvent.nbytes + prob.charges.nbytes
+        d2h = sum(v.nbytes for v in hout.values())
+        line["e2e"] = {"value": world * max(1, args.steps) / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h)}
+    grid.close()
+
+    # CPU oracle on a bounded sample (rank 0, one GPU only)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        phat = phi_mixed / 0.025683333333333336
+        sol = np.flatnonzero(prob.solvent)
+        pick = sol[np.linspace(0, len(sol) - 1, 4000).astype(np.int64)]
+        samp = oracle_sample(prob, phat[pick], args.cpu_iters)
+        if fp64_rep is not None:
+            work_outer, work_lin = fp64_rep["outer_iters"], fp64_rep["lin_iters_total"]
+        else:
+            work_outer, work_lin = reps[-1]["outer_iters"], reps[-1]["lin_iters_total"]
+        T = oracle_solve_time(samp, work_outer, work_lin)
+        line["cpu_baseline"] = {
+            "value": 1.0 / T, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{samp['iters']} FP64 BiCGSTAB iterations on the full {args.n}^3 operator "
+                       f"({samp['t_iter']:.3f} s each), the Fermi step on {samp['nodes']} solvent nodes of this "
+                       f"solution ({samp['t_node'] * 1e6:.2f} us each), one operator assembly ({samp['t_asm']:.2f} s); "
+                       f"scaled to this workload's FP64 solve of {work_outer} outer and {work_lin} BiCGSTAB "
+                       f"iterations")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -143,7 +143,8 @@ typedef struct {
 } pf_result;
 
 /* Fills the options with defaults: FP64, relative 2-norm 1e-10, 20000 iterations; mixed
- * inner tolerance 1e-3, 64 refinements; omega 0.3, tol_outer 1e-9, 500 outer iterations. */
+ * inner tolerance 0.1 (at most 1000 FP32 iterations per refinement step), 64 refinements;
+ * omega 0.3, tol_outer 1e-9, 500 outer iterations. */
 void pf_default_solve_opts(pf_solve_opts* o);
 void pf_default_nl_opts(pf_nl_opts* o);
 
@@ -181,14 +182,20 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
 /* ---- profiling: device time per kernel kind on one grid ----------------------------------- */
 enum {
   PF_PROF_INIT = 0,        /* BiCGSTAB start: r0 = b - A x0 (Table 3, step 2) */
-  PF_PROF_B_FP64 = 1,      /* phase B in FP64: s, t = A M^-1 s and its inner products (steps 13-15) */
-  PF_PROF_CA_FP64 = 2,     /* phase C+A in FP64: x, r updates, next p and v = A M^-1 p (steps 16-17, 9-12) */
+  PF_PROF_B_FP64 = 1,      /* phase B in FP64: s, t = A M^-1 s and its inner products (steps 13-15),
+                              variable-dielectric operators (PF_OP_POISSON, PF_OP_PF2) */
+  PF_PROF_CA_FP64 = 2,     /* phase C+A in FP64: x, r updates, next p and v = A M^-1 p (steps 16-17,
+                              9-12), variable-dielectric operators */
   PF_PROF_B_FP32 = 3,      /* the same two phases in FP32 (mixed precision inner solves) */
   PF_PROF_CA_FP32 = 4,
-  PF_PROF_RESIDUAL = 5,    /* FP64 true residual b - A x of iterative refinement */
-  PF_PROF_FERMI = 6,       /* pointwise Fermi/steric step of Eq. (1) */
-  PF_PROF_OTHER = 7,       /* setup, right-hand sides, relaxation, output conversion */
-  PF_PROF_KINDS = 8
+  PF_PROF_B_FP64_PF1 = 5,  /* the four phase kernels on the uniform-face PF1 operator */
+  PF_PROF_CA_FP64_PF1 = 6,
+  PF_PROF_B_FP32_PF1 = 7,
+  PF_PROF_CA_FP32_PF1 = 8,
+  PF_PROF_RESIDUAL = 9,    /* FP64 true residual b - A x of iterative refinement */
+  PF_PROF_FERMI = 10,      /* pointwise Fermi/steric step of Eq. (1) */
+  PF_PROF_OTHER = 11,      /* setup, right-hand sides, relaxation, output conversion */
+  PF_PROF_KINDS = 12
 };
 
 typedef struct {

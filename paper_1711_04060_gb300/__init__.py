@@ -6,15 +6,6 @@ SMIB/harmonic interface faces, inside the relaxed inexact-Newton PF iteration (T
 pointwise step evaluates the Fermi-like concentrations and steric potential of Eq. (1), as
 hand-written sm_103a CUDA kernels behind the C ABI of include/pf_gb300.h.
 
-Importing the package loads nothing; the binding loads libpf_gb300.so on first use and fails
-loudly when it has not been built.  `workloads` generates the seeded synthetic inputs.
+Importing the package loads nothing: `paper_1711_04060_gb300.api` loads libpf_gb300.so on first
+use and fails loudly when it has not been built; `workloads` generates the seeded inputs.
 """
-from . import workloads  # noqa: F401
-
-
-def __getattr__(name):
-    # the binding is imported lazily so that `workloads` can be used without the CUDA library
-    if name == "api":
-        from . import api
-        return api
-    raise AttributeError(name)

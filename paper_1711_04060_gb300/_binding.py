@@ -52,8 +52,9 @@ class pf_result(ctypes.Structure):
                 ("time_ms", _D)]
 
 
-PF_PROF_KINDS = 8
-PROF_NAMES = ["init", "b_fp64", "ca_fp64", "b_fp32", "ca_fp32", "residual_fp64", "fermi", "other"]
+PF_PROF_KINDS = 12
+PROF_NAMES = ["init", "b_fp64", "ca_fp64", "b_fp32", "ca_fp32", "b_fp64_pf1", "ca_fp64_pf1", "b_fp32_pf1",
+              "ca_fp32_pf1", "residual_fp64", "fermi", "other"]
 
 
 class pf_profile(ctypes.Structure):

@@ -55,7 +55,7 @@ def _torch_stream():
     return ctypes.c_void_p(0)
 
 
-def solve_opts(max_iter=20000, tol=1e-10, norm=PF_NORM_REL2, precision=PF_FP64, inner_tol=1e-3, max_refine=64):
+def solve_opts(max_iter=20000, tol=1e-10, norm=PF_NORM_REL2, precision=PF_FP64, inner_tol=0.1, max_refine=64):
     o = B.pf_solve_opts()
     B.load().pf_default_solve_opts(ctypes.byref(o))
     o.max_iter, o.tol, o.norm, o.precision, o.inner_tol, o.max_refine = max_iter, tol, norm, precision, inner_tol, \

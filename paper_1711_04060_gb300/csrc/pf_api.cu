@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -49,6 +50,7 @@ pf_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr int CHUNK = 8;  // BiCGSTAB iterations launched between two host checks of the done flag
+constexpr int INNER_CAP = 1000;  // FP32 iterations per refinement step at most
 constexpr int PROF_SLOTS = 64;  // timed launches between two resolutions of the profiling events
 
 }  // namespace
@@ -78,6 +80,8 @@ struct pf_grid {
   double *phi0 = nullptr, *phi = nullptr, *psi = nullptr, *b1 = nullptr, *c2 = nullptr, *b2 = nullptr;
   double *Cbuf = nullptr, *Sbuf = nullptr, *Gbuf = nullptr;
   double* part = nullptr;
+  double* dch = nullptr;     // fixed charges (x, y, z, q) on the device
+  int nq = 0;
   BicgState* st = nullptr;   // FP64 solve / refinement state
   BicgState* st2 = nullptr;  // FP32 inner solve state
   BicgState* host_st = nullptr;  // pinned mirror
@@ -114,6 +118,8 @@ pf_status dalloc(pf_grid* g, T** p, size_t count) {
 }
 
 void free_all(pf_grid* g) {
+  if (g->dch) cudaFree(g->dch);
+  g->dch = nullptr;
   for (cudaEvent_t e : g->pool) cudaEventDestroy(e);
   g->pool.clear();
   for (void* q : g->allocs) cudaFree(q);
@@ -164,6 +170,17 @@ pf_status allocate(pf_grid* g) {
   g->pkind.resize(PROF_SLOTS, 0);
   for (auto& e : g->pool) PF_CK(cudaEventCreate(&e));
   return PF_OK;
+}
+
+// PF_TRACE=1 prints one line per linear solve and outer iteration to stderr, PF_TRACE=2 also one
+// line per chunk of BiCGSTAB iterations.
+int trace_level() {
+  static int lvl = -1;
+  if (lvl < 0) {
+    const char* e = getenv("PF_TRACE");
+    lvl = e ? atoi(e) : 0;
+  }
+  return lvl;
 }
 
 // ---- profiling ---------------------------------------------------------------------------
@@ -264,7 +281,8 @@ pf_status run_bicgstab(pf_grid* g, const OpView<T>& op, T* x, bool x_zero, const
                        T* const v[2], T* rt, T* t, BicgState* st, BicgState* out) {
   const pf::Launch& L = g->L;
   const bool f64 = sizeof(T) == 8;
-  const int kb = f64 ? PF_PROF_B_FP64 : PF_PROF_B_FP32, kca = f64 ? PF_PROF_CA_FP64 : PF_PROF_CA_FP32;
+  const int kb = UNI ? (f64 ? PF_PROF_B_FP64_PF1 : PF_PROF_B_FP32_PF1) : (f64 ? PF_PROF_B_FP64 : PF_PROF_B_FP32);
+  const int kca = UNI ? (f64 ? PF_PROF_CA_FP64_PF1 : PF_PROF_CA_FP32_PF1) : (f64 ? PF_PROF_CA_FP64 : PF_PROF_CA_FP32);
   PF_LAUNCH(g, PF_PROF_INIT, (pf::launch_init<T, UNI>(op, x, x_zero, b, r[0], rt, p[0], v[0], t, g->part, st, L)));
   PF_LAUNCH(g, kca, (pf::launch_phase_ca<T, UNI>(op, r[0], v[0], p[0], t, rt, x, r[1], p[1], v[1], g->part, st, 1, L)));
   int cur = 1;
@@ -277,6 +295,10 @@ pf_status run_bicgstab(pf_grid* g, const OpView<T>& op, T* x, bool x_zero, const
     }
     BicgState s;
     PF_TRY(read_state(g, st, &s));
+    if (trace_level() > 1)
+      fprintf(stderr, "[pf] %s it %d rel %.3e rho %.3e alpha %.3e omega %.3e done %d status %d\n",
+              sizeof(T) == 8 ? "fp64" : "fp32", s.iter, sqrt(s.rnorm2 / (s.bnorm2 > 0 ? s.bnorm2 : 1.0)), s.rho,
+              s.alpha, s.omega, s.done, s.status);
     if (s.done) {
       *out = s;
       return PF_OK;
@@ -316,6 +338,9 @@ pf_status solve_fp64(pf_grid* g, int op, const double* b, double* x, const pf_so
   rep->iterations = s.iter;
   rep->refinements = 0;
   rep->residual = measure_of(tr, o.norm);
+  if (trace_level() > 0)
+    fprintf(stderr, "[pf] fp64 solve op %d: status %d iters %d residual %.3e\n", op, rep->status, rep->iterations,
+            rep->residual);
   return PF_OK;
 }
 
@@ -337,16 +362,25 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
       status = PF_E_NOCONV;
       break;
     }
-    // FP32 inner solve A d = r (r = b - A x in b32), d0 = 0, to relative tolerance inner_tol
+    // FP32 inner solve A d = r (r = b - A x in b32), d0 = 0, to relative tolerance inner_tol; an inner
+    // solve that stagnates is cut off after INNER_CAP iterations and its correction is kept
     PF_CK(cudaMemsetAsync(g->d32, 0, g->N * sizeof(float), g->stream));
-    PF_TRY(set_state(g, g->st2, o.inner_tol, PF_NORM_REL2, o.max_iter - iters));
+    const int cap = o.max_iter - iters < INNER_CAP ? o.max_iter - iters : INNER_CAP;
+    PF_TRY(set_state(g, g->st2, o.inner_tol, PF_NORM_REL2, cap));
     BicgState s;
     PF_TRY((run_bicgstab<float, UNI>(g, W, g->d32, true, g->b32, g->r32, g->p32, g->v32, g->rt32, g->t32, g->st2,
                                      &s)));
     iters += s.iter;
     have_d = true;
     ++ref;
+    if (trace_level() > 0)
+      fprintf(stderr, "[pf] mixed op %d refinement %d: true residual %.3e, inner status %d iters %d\n", op, ref,
+              measure_of(tr, o.norm), s.status, s.iter);
     if (s.status == PF_E_BREAKDOWN && s.iter == 0) {
+      status = PF_E_BREAKDOWN;
+      break;
+    }
+    if (!isfinite(tr.rnorm2)) {
       status = PF_E_BREAKDOWN;
       break;
     }
@@ -379,6 +413,32 @@ pf_status update_pf2(pf_grid* g) {
   return PF_OK;
 }
 
+// Step a1 on the device from the stored eps, solvent mask and charges: harmonic faces (Eqs. 15-18
+// with zero jump) in FP64 and FP32, diagonals and Jacobi scalings of the three operators, the
+// trilinear fixed-charge source (Eq. 3).  kappa (PF2) is reset to zero.  Sets g->err when a charge
+// lies outside the grid.
+pf_status build_operators(pf_grid* g) {
+  const long N = g->N;
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_faces(g->eps, g->nx, g->ny, g->nz, g->h, g->wE, g->wN, g->wU, g->dsum,
+                                               g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wE, g->wE32, N, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wN, g->wN32, N, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wU, g->wU32, N, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_eps_diag(g->dsum, nullptr, nullptr, g->nx, g->ny, g->nz, g->diagP, g->dinvP,
+                                                  g->dinvP32, g->stream));
+  PF_CK(cudaMemsetAsync(g->sig, 0, N * sizeof(double), g->stream));
+  PF_TRY(update_pf2(g));
+  const double wc = g->eps_s * g->lc * g->lc / (g->h * g->h);
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf1_dinv(g->solvent, g->nx, g->ny, g->nz, 1.0 / (6.0 * wc + g->eps_s),
+                                                  g->dinv1, g->dinv1_32, g->stream));
+  PF_CK(cudaMemsetAsync(g->ffix, 0, N * sizeof(double), g->stream));
+  PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), g->stream));
+  if (g->nq > 0)
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_spread(g->dch, g->nq, g->origin[0], g->origin[1], g->origin[2], g->h,
+                                                  g->lam, g->nx, g->ny, g->nz, g->ffix, g->err, g->stream));
+  return PF_OK;
+}
+
 }  // namespace
 
 // Device bytes that pf_create_grid allocates for n_nodes nodes (used for the serving budget).
@@ -395,7 +455,7 @@ void pf_default_solve_opts(pf_solve_opts* o) {
   o->tol = 1e-10;
   o->norm = PF_NORM_REL2;
   o->precision = PF_FP64;
-  o->inner_tol = 1e-3;
+  o->inner_tol = 0.1;
   o->max_refine = 64;
 }
 
@@ -524,38 +584,19 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
   const long N = g->N;
   PF_CK(cudaMemcpyAsync(g->eps, c->eps, N * sizeof(double), cudaMemcpyHostToDevice, g->stream));
   PF_CK(cudaMemcpyAsync(g->solvent, c->solvent, N, cudaMemcpyHostToDevice, g->stream));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_faces(g->eps, g->nx, g->ny, g->nz, g->h, g->wE, g->wN, g->wU, g->dsum,
-                                               g->stream));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wE, g->wE32, N, g->stream));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wN, g->wN32, N, g->stream));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wU, g->wU32, N, g->stream));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_eps_diag(g->dsum, nullptr, nullptr, g->nx, g->ny, g->nz, g->diagP, g->dinvP,
-                                                  g->dinvP32, g->stream));
-  PF_CK(cudaMemsetAsync(g->sig, 0, N * sizeof(double), g->stream));
-  PF_TRY(update_pf2(g));
-  const double wc = g->eps_s * g->lc * g->lc / (g->h * g->h);
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf1_dinv(g->solvent, g->nx, g->ny, g->nz, 1.0 / (6.0 * wc + g->eps_s),
-                                                  g->dinv1, g->dinv1_32, g->stream));
-  // fixed-charge source lambda q w / h^3 (Eq. 3, trilinear)
-  PF_CK(cudaMemsetAsync(g->ffix, 0, N * sizeof(double), g->stream));
-  PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), g->stream));
-  if (c->n_charges > 0) {
-    double* dch = nullptr;
-    PF_CK(cudaMalloc(&dch, sizeof(double) * 4 * c->n_charges));
-    cudaError_t e = cudaMemcpyAsync(dch, c->charges, sizeof(double) * 4 * c->n_charges, cudaMemcpyHostToDevice,
-                                    g->stream);
-    if (e == cudaSuccess) {
-      g->launches += 1;
-      e = pf::launch_spread(dch, c->n_charges, g->origin[0], g->origin[1], g->origin[2], g->h, g->lam, g->nx, g->ny,
-                            g->nz, g->ffix, g->err, g->stream);
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    cudaFree(dch);
-    if (e != cudaSuccess) return cuda_fail(e, "charge spreading");
-    if (*g->host_err) return fail(PF_E_INVAL, "a fixed charge lies outside the grid");
+  if (g->dch) {
+    cudaFree(g->dch);
+    g->dch = nullptr;
   }
+  g->nq = c->n_charges;
+  if (g->nq > 0) {
+    PF_CK(cudaMalloc(&g->dch, sizeof(double) * 4 * g->nq));
+    PF_CK(cudaMemcpyAsync(g->dch, c->charges, sizeof(double) * 4 * g->nq, cudaMemcpyHostToDevice, g->stream));
+  }
+  PF_TRY(build_operators(g));
+  PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
   PF_CK(cudaStreamSynchronize(g->stream));
+  if (*g->host_err) return fail(PF_E_INVAL, "a fixed charge lies outside the grid");
   g->have_coeffs = true;
   return PF_OK;
 }
@@ -624,6 +665,8 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   res->delta = 0.0;
   pf_status st = PF_OK;
   pf_report rep{};
+  // step a1: operators and fixed-charge source from the device-resident coefficients
+  PF_TRY(build_operators(g));
   // Table 4 step 4: PF2 with rho' = Psi = 0 -> Phi_0
   PF_CK(cudaMemsetAsync(g->phi0, 0, N * sizeof(double), s));
   PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, nx, ny, nz, s));
@@ -657,6 +700,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
     if (*g->host_err) { st = PF_E_GAMMA; break; }
     res->outer_iters = outer;
     res->delta = *g->host_delta;
+    if (trace_level() > 0) fprintf(stderr, "[pf] outer %d delta %.6e lin_total %d\n", outer, res->delta, res->lin_iters_total);
     if (res->delta <= o.tol_outer) break;
     if (outer == o.max_outer) st = PF_E_NOCONV;
   }

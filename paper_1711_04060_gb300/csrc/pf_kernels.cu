@@ -401,8 +401,8 @@ __global__ void __launch_bounds__(NTHREADS) k_phase_b(OpView<T> op, const T* __r
         st->sexit = 1;
         st->omega = 0.0;
         st->beta = 0.0;
-      } else if (tt == 0.0) {
-        st->status = 4;  // PF_E_BREAKDOWN
+      } else if (tt == 0.0 || !isfinite(tt) || !isfinite(ts) || !isfinite(ss)) {
+        st->status = 4;  // PF_E_BREAKDOWN (a zero or non-finite t.t stops before x is touched)
         st->done = 1;
       } else {
         const double om = ts / tt;  // step 15
@@ -410,7 +410,8 @@ __global__ void __launch_bounds__(NTHREADS) k_phase_b(OpView<T> op, const T* __r
         // r~.r_new with r_new = s - omega t (steps 17 and 4 of the next iteration), needed now
         // because the next p is formed in the same kernel as r_new
         const double rho_new = rs - om * rtt;
-        st->beta = (om != 0.0) ? (rho_new / st->rho) * (st->alpha / om) : 0.0;  // step 8
+        const double be = (om != 0.0) ? (rho_new / st->rho) * (st->alpha / om) : 0.0;  // step 8
+        st->beta = isfinite(be) ? be : 0.0;
       }
       st->ticket = 0;
     }
@@ -540,7 +541,7 @@ __global__ void __launch_bounds__(NTHREADS) k_phase_ca(OpView<T> op, const T* __
           return;
         }
       }
-      if (rr == 0.0 || rv == 0.0) {
+      if (rr == 0.0 || rv == 0.0 || !isfinite(rr) || !isfinite(rv) || !isfinite(rr / rv)) {
         st->done = 1;
         st->status = 4;
         return;
