@@ -1,21 +1,24 @@
 // pf_api.cu -- the C ABI of include/pf_gb300.h: grid state, coefficient setup, and the host
 // control of the device solvers (Table 3 linear solver, Table 4 nonlinear solver, FP64 iterative
 // refinement around FP32 BiCGSTAB).  Every arithmetic step runs in the kernels of pf_kernels.cu;
-// this file only allocates, launches, and reads back the few scalars that steer the iteration.
+// this file allocates, encodes the TMA descriptors, launches, and reads back the few scalars that
+// steer the iteration.  Device arrays use the padded layout of pf::Geom; caller arrays are compact
+// and are packed / unpacked at this boundary.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/pf_gb300.h"
 #include "pf_internal.cuh"
 
 using pf::BicgState;
-using pf::OpView;
 
 namespace {
 
@@ -49,15 +52,17 @@ pf_status cuda_fail(cudaError_t e, const char* what) {
     if (s_ != PF_OK) return s_;         \
   } while (0)
 
-constexpr int CHUNK = 8;  // BiCGSTAB iterations launched between two host checks of the done flag
+constexpr int CHUNK = 8;         // BiCGSTAB iterations launched between two host checks of the done flag
 constexpr int INNER_CAP = 1000;  // FP32 iterations per refinement step at most
-constexpr int PROF_SLOTS = 64;  // timed launches between two resolutions of the profiling events
+constexpr int PROF_SLOTS = 64;   // timed launches between two resolutions of the profiling events
+constexpr unsigned long long WAIT_LIMIT = 4000000000ull;  // clock cycles (about 2 s) per TMA stage wait
 
 }  // namespace
 
 struct pf_grid {
   int nx = 0, ny = 0, nz = 0;
-  long N = 0;
+  long N = 0;   // nodes
+  pf::Geom geom{};
   double h = 1.0, origin[3] = {0, 0, 0};
   cudaStream_t stream = nullptr;
   pf::Launch L{};
@@ -65,7 +70,7 @@ struct pf_grid {
   // problem constants
   double eps_s = 78.5, lc = 0.0, T = 298.15, Tv = 0.0, lam = 0.0, lo_hat = 0.0, hi_hat = 0.0, molar = 0.0;
   pf::SpeciesParams sp{};
-  // device arrays
+  // device arrays (padded layout)
   std::vector<void*> allocs;
   double *eps = nullptr, *wE = nullptr, *wN = nullptr, *wU = nullptr, *dsum = nullptr, *ffix = nullptr;
   uint8_t* solvent = nullptr;
@@ -76,7 +81,7 @@ struct pf_grid {
   double *rt64 = nullptr, *t64 = nullptr;
   float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr}, *v32[2] = {nullptr, nullptr};
   float *rt32 = nullptr, *t32 = nullptr, *d32 = nullptr, *b32 = nullptr;
-  double *xb = nullptr, *bb = nullptr;
+  double *xb = nullptr, *bb = nullptr, *stage = nullptr;
   double *phi0 = nullptr, *phi = nullptr, *psi = nullptr, *b1 = nullptr, *c2 = nullptr, *b2 = nullptr;
   double *Cbuf = nullptr, *Sbuf = nullptr, *Gbuf = nullptr;
   double* part = nullptr;
@@ -91,6 +96,8 @@ struct pf_grid {
   unsigned int* ticket = nullptr;
   double* host_delta = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // TMA descriptors, keyed by (array, halo box?)
+  std::map<std::pair<const void*, int>, CUtensorMap> maps;
   // profiling: event pairs around launches, resolved at the next host synchronisation
   int prof_on = 0;
   long long launches = 0;
@@ -135,17 +142,17 @@ void free_all(pf_grid* g) {
 }
 
 pf_status allocate(pf_grid* g) {
-  const long N = g->N;
+  const long NP = g->geom.np;
   double** d64[] = {&g->eps, &g->wE, &g->wN, &g->wU, &g->dsum, &g->ffix, &g->diagP, &g->dinvP, &g->diag2,
                     &g->dinv2, &g->sig, &g->dinv1, &g->r64[0], &g->r64[1], &g->p64[0], &g->p64[1], &g->v64[0],
-                    &g->v64[1], &g->rt64, &g->t64, &g->xb, &g->bb, &g->phi0, &g->phi, &g->psi, &g->b1,
+                    &g->v64[1], &g->rt64, &g->t64, &g->xb, &g->bb, &g->stage, &g->phi0, &g->phi, &g->psi, &g->b1,
                     &g->c2, &g->b2, &g->Sbuf, &g->Gbuf};
-  for (double** p : d64) PF_TRY(dalloc(g, p, N));
-  PF_TRY(dalloc(g, &g->Cbuf, (size_t)N * pf::MAXSP));
+  for (double** p : d64) PF_TRY(dalloc(g, p, NP));
+  PF_TRY(dalloc(g, &g->Cbuf, (size_t)NP * pf::MAXSP));
   float** d32[] = {&g->wE32, &g->wN32, &g->wU32, &g->dinvP32, &g->dinv2_32, &g->dinv1_32, &g->r32[0], &g->r32[1],
                    &g->p32[0], &g->p32[1], &g->v32[0], &g->v32[1], &g->rt32, &g->t32, &g->d32, &g->b32};
-  for (float** p : d32) PF_TRY(dalloc(g, p, N));
-  PF_TRY(dalloc(g, &g->solvent, N));
+  for (float** p : d32) PF_TRY(dalloc(g, p, NP));
+  PF_TRY(dalloc(g, &g->solvent, NP));
   PF_TRY(dalloc(g, &g->part, (size_t)pf::max_partial_blocks() * pf::NPART));
   PF_TRY(dalloc(g, &g->st, 1));
   PF_TRY(dalloc(g, &g->st2, 1));
@@ -155,15 +162,15 @@ pf_status allocate(pf_grid* g) {
   PF_CK(cudaMallocHost(&g->host_st, sizeof(BicgState)));
   PF_CK(cudaMallocHost(&g->host_err, sizeof(int)));
   PF_CK(cudaMallocHost(&g->host_delta, sizeof(double)));
-  // Krylov vectors stay zero on the Dirichlet planes, which no stencil kernel writes
-  for (double* p : {g->r64[0], g->r64[1], g->p64[0], g->p64[1], g->v64[0], g->v64[1], g->rt64, g->t64})
-    PF_CK(cudaMemsetAsync(p, 0, N * sizeof(double), g->stream));
-  for (float* p : {g->r32[0], g->r32[1], g->p32[0], g->p32[1], g->v32[0], g->v32[1], g->rt32, g->t32, g->d32, g->b32})
-    PF_CK(cudaMemsetAsync(p, 0, N * sizeof(float), g->stream));
+  // every array starts at zero: the pad columns and the Krylov vectors on the Dirichlet planes, which no
+  // kernel writes, stay zero
+  for (double** p : d64) PF_CK(cudaMemsetAsync(*p, 0, NP * sizeof(double), g->stream));
+  PF_CK(cudaMemsetAsync(g->Cbuf, 0, (size_t)NP * pf::MAXSP * sizeof(double), g->stream));
+  for (float** p : d32) PF_CK(cudaMemsetAsync(*p, 0, NP * sizeof(float), g->stream));
+  PF_CK(cudaMemsetAsync(g->solvent, 0, NP, g->stream));
   PF_CK(cudaMemsetAsync(g->st, 0, sizeof(BicgState), g->stream));
   PF_CK(cudaMemsetAsync(g->st2, 0, sizeof(BicgState), g->stream));
   PF_CK(cudaMemsetAsync(g->ticket, 0, sizeof(unsigned int), g->stream));
-  PF_CK(cudaMemsetAsync(g->sig, 0, N * sizeof(double), g->stream));
   PF_CK(cudaEventCreate(&g->ev0));
   PF_CK(cudaEventCreate(&g->ev1));
   g->pool.resize(2 * PROF_SLOTS, nullptr);
@@ -184,7 +191,6 @@ int trace_level() {
 }
 
 // ---- profiling ---------------------------------------------------------------------------
-
 void prof_resolve(pf_grid* g) {
   if (g->np == 0) return;
   if (cudaEventSynchronize(g->pool[2 * (g->np - 1) + 1]) == cudaSuccess) {
@@ -222,43 +228,59 @@ void prof_end(pf_grid* g, int slot, int kind) {
     prof_end((g), slot_, (kind));                 \
   } while (0)
 
-// ---- operator views -----------------------------------------------------------------------
-OpView<double> view64(const pf_grid* g, int op) {
-  OpView<double> v{};
-  v.nx = g->nx;
-  v.ny = g->ny;
-  v.nz = g->nz;
-  if (op == PF_OP_PF1) {
-    v.dinv = g->dinv1;
-    v.wc = g->eps_s * g->lc * g->lc / (g->h * g->h);
-    v.diagc = 6.0 * v.wc + g->eps_s;
-  } else {
-    v.wE = g->wE;
-    v.wN = g->wN;
-    v.wU = g->wU;
-    v.dinv = op == PF_OP_PF2 ? g->dinv2 : g->dinvP;
-    v.diag = op == PF_OP_PF2 ? g->diag2 : g->diagP;
-  }
-  return v;
+// ---- TMA descriptors ---------------------------------------------------------------------
+template <typename T>
+const CUtensorMap* tmap(pf_grid* g, const T* base, bool halo) {
+  const auto key = std::make_pair(static_cast<const void*>(base), (int)sizeof(T) * 2 + (halo ? 1 : 0));
+  auto it = g->maps.find(key);
+  if (it != g->maps.end()) return &it->second;
+  CUtensorMap m;
+  if (!pf::encode_map(&m, base, g->geom, (int)sizeof(T), halo)) return nullptr;
+  return &(g->maps[key] = m);
 }
 
-OpView<float> view32(const pf_grid* g, int op) {
-  OpView<float> v{};
-  v.nx = g->nx;
-  v.ny = g->ny;
-  v.nz = g->nz;
-  if (op == PF_OP_PF1) {
-    v.dinv = g->dinv1_32;
-    const double wc = g->eps_s * g->lc * g->lc / (g->h * g->h);
-    v.wc = (float)wc;
-    v.diagc = 6.0 * wc + g->eps_s;
-  } else {
-    v.wE = g->wE32;
-    v.wN = g->wN32;
-    v.wU = g->wU32;
-    v.dinv = op == PF_OP_PF2 ? g->dinv2_32 : g->dinvP32;
+template <int NH, int NC, typename T>
+pf_status fill_maps(pf_grid* g, pf::Maps<NH, NC>* m, const T* const (&h)[NH], const T* const (&c)[NC]) {
+  for (int i = 0; i < NH; ++i) {
+    const CUtensorMap* p = tmap(g, h[i], true);
+    if (!p) return fail(PF_E_CUDA, "cuTensorMapEncodeTiled failed");
+    m->h[i] = *p;
   }
-  return v;
+  for (int i = 0; i < NC; ++i) {
+    const CUtensorMap* p = tmap(g, c[i], false);
+    if (!p) return fail(PF_E_CUDA, "cuTensorMapEncodeTiled failed");
+    m->c[i] = *p;
+  }
+  return PF_OK;
+}
+
+// ---- operators -------------------------------------------------------------------------
+// The arrays of one operator in one precision: Jacobi scaling (0 on identity rows), FP64 diagonal,
+// face arrays (null for the uniform PF1 operator), uniform face and diagonal.
+template <typename T>
+struct OpArrays {
+  const T* dinv;
+  const double* diag;
+  const T *wE, *wN, *wU;
+  double wc, diagc;
+};
+
+double pf1_face(const pf_grid* g) { return g->eps_s * g->lc * g->lc / (g->h * g->h); }
+
+OpArrays<double> ops64(const pf_grid* g, int op) {
+  if (op == PF_OP_PF1) {
+    const double wc = pf1_face(g);
+    return {g->dinv1, nullptr, nullptr, nullptr, nullptr, wc, 6.0 * wc + g->eps_s};
+  }
+  return {op == PF_OP_PF2 ? g->dinv2 : g->dinvP, op == PF_OP_PF2 ? g->diag2 : g->diagP, g->wE, g->wN, g->wU, 0.0, 0.0};
+}
+
+OpArrays<float> ops32(const pf_grid* g, int op) {
+  if (op == PF_OP_PF1) {
+    const double wc = pf1_face(g);
+    return {g->dinv1_32, nullptr, nullptr, nullptr, nullptr, wc, 6.0 * wc + g->eps_s};
+  }
+  return {op == PF_OP_PF2 ? g->dinv2_32 : g->dinvP32, nullptr, g->wE32, g->wN32, g->wU32, 0.0, 0.0};
 }
 
 pf_status set_state(pf_grid* g, BicgState* dst, double tol, int norm, int max_iter) {
@@ -274,50 +296,100 @@ pf_status read_state(pf_grid* g, const BicgState* src, BicgState* out) {
   return PF_OK;
 }
 
-// Runs BiCGSTAB iterations (init, prime, then [B, CA] pairs in chunks) on operator `op` in precision T,
-// with the initial residual from x (or x = 0).  Returns the final device state in *out.
+// Krylov vectors of one precision
+template <typename T>
+struct Krylov {
+  T* r[2];
+  T* p[2];
+  T* v[2];
+  T* rt;
+  T* t;
+};
+
+Krylov<double> kry64(pf_grid* g) { return {{g->r64[0], g->r64[1]}, {g->p64[0], g->p64[1]}, {g->v64[0], g->v64[1]}, g->rt64, g->t64}; }
+Krylov<float> kry32(pf_grid* g) { return {{g->r32[0], g->r32[1]}, {g->p32[0], g->p32[1]}, {g->v32[0], g->v32[1]}, g->rt32, g->t32}; }
+
+// FP64 residual r = b - A x over the operator: init = 1 starts BiCGSTAB (r, r~, p = v = t = 0 in K),
+// init = 0 writes (float) r to b32 for iterative refinement.  The state must have been reset.
+template <bool UNI>
+pf_status residual(pf_grid* g, const OpArrays<double>& A, const double* x, const double* b, int init,
+                   const Krylov<double>* K, BicgState* st) {
+  using S = pf::SlotsRes<UNI>;
+  pf::Maps<S::NH, S::NC> m;
+  if constexpr (UNI) {
+    const double* h[S::NH] = {x, A.dinv};
+    const double* c[S::NC] = {b};
+    PF_TRY((fill_maps<S::NH, S::NC, double>(g, &m, h,
+                                            c)));
+  } else {
+    const double* h[S::NH] = {x, A.dinv, A.wE, A.wN};
+    const double* c[S::NC] = {b, A.diag, A.wU};
+    PF_TRY((fill_maps<S::NH, S::NC, double>(g, &m, h,
+                                            c)));
+  }
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b, g->geom, st, g->stream));
+  const int slot = prof_begin(g, 1);
+  PF_CK((pf::launch_residual<UNI>(m, g->geom, A.wc, A.diagc, init, K ? K->r[0] : nullptr, K ? K->rt : nullptr,
+                                  K ? K->p[0] : nullptr, K ? K->v[0] : nullptr, K ? K->t : nullptr, g->b32, g->part,
+                                  st, g->L)));
+  prof_end(g, slot, init ? PF_PROF_INIT : PF_PROF_RESIDUAL);
+  return PF_OK;
+}
+
+// BiCGSTAB iterations (prime, then [B, C+A] pairs in chunks) after the start kernel has written r0 = r[0],
+// r~, p[0] = v[0] = t = 0 and started the state.  Returns the final device state in *out.
 template <typename T, bool UNI>
-pf_status run_bicgstab(pf_grid* g, const OpView<T>& op, T* x, bool x_zero, const T* b, T* const r[2], T* const p[2],
-                       T* const v[2], T* rt, T* t, BicgState* st, BicgState* out) {
-  const pf::Launch& L = g->L;
+pf_status iterate(pf_grid* g, const OpArrays<T>& A, T* x, const Krylov<T>& K, BicgState* st, BicgState* out) {
+  using SB = pf::SlotsB<UNI>;
+  using SC = pf::SlotsCA<UNI>;
   const bool f64 = sizeof(T) == 8;
   const int kb = UNI ? (f64 ? PF_PROF_B_FP64_PF1 : PF_PROF_B_FP32_PF1) : (f64 ? PF_PROF_B_FP64 : PF_PROF_B_FP32);
   const int kca = UNI ? (f64 ? PF_PROF_CA_FP64_PF1 : PF_PROF_CA_FP32_PF1) : (f64 ? PF_PROF_CA_FP64 : PF_PROF_CA_FP32);
-  PF_LAUNCH(g, PF_PROF_INIT, (pf::launch_init<T, UNI>(op, x, x_zero, b, r[0], rt, p[0], v[0], t, g->part, st, L)));
-  PF_LAUNCH(g, kca, (pf::launch_phase_ca<T, UNI>(op, r[0], v[0], p[0], t, rt, x, r[1], p[1], v[1], g->part, st, 1, L)));
+  // descriptors for the two parities of the ping-pong vectors (r, p, v of iteration parity `cur`)
+  pf::Maps<SB::NH, SB::NC> mb[2];
+  pf::Maps<SC::NH, SC::NC> mca[2];
+  for (int cur = 0; cur < 2; ++cur) {
+    if constexpr (UNI) {
+      const T* hb[SB::NH] = {K.r[cur], K.v[cur], A.dinv};
+      const T* cb[SB::NC] = {K.rt};
+      PF_TRY((fill_maps<SB::NH, SB::NC, T>(g, &mb[cur], hb,
+                                           cb)));
+      const T* hc[SC::NH] = {K.r[cur], K.v[cur], K.t, K.p[cur], A.dinv};
+      const T* cc[SC::NC] = {x, K.rt};
+      PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &mca[cur], hc,
+                                           cc)));
+    } else {
+      const T* hb[SB::NH] = {K.r[cur], K.v[cur], A.dinv, A.wE, A.wN};
+      const T* cb[SB::NC] = {K.rt, A.wU};
+      PF_TRY((fill_maps<SB::NH, SB::NC, T>(g, &mb[cur], hb,
+                                           cb)));
+      const T* hc[SC::NH] = {K.r[cur], K.v[cur], K.t, K.p[cur], A.dinv, A.wE, A.wN};
+      const T* cc[SC::NC] = {x, K.rt, A.wU};
+      PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &mca[cur], hc,
+                                           cc)));
+    }
+  }
+  const T wc = (T)A.wc;
+  PF_LAUNCH(g, kca, (pf::launch_phase_ca<T, UNI>(mca[0], g->geom, wc, x, K.r[1], K.p[1], K.v[1], g->part, st, 1, g->L)));
   int cur = 1;
   for (;;) {
     for (int i = 0; i < CHUNK; ++i) {
-      PF_LAUNCH(g, kb, (pf::launch_phase_b<T, UNI>(op, r[cur], v[cur], rt, t, g->part, st, L)));
-      PF_LAUNCH(g, kca, (pf::launch_phase_ca<T, UNI>(op, r[cur], v[cur], p[cur], t, rt, x, r[1 - cur], p[1 - cur],
-                                                    v[1 - cur], g->part, st, 0, L)));
+      PF_LAUNCH(g, kb, (pf::launch_phase_b<T, UNI>(mb[cur], g->geom, wc, K.t, g->part, st, g->L)));
+      PF_LAUNCH(g, kca, (pf::launch_phase_ca<T, UNI>(mca[cur], g->geom, wc, x, K.r[1 - cur], K.p[1 - cur],
+                                                     K.v[1 - cur], g->part, st, 0, g->L)));
       cur = 1 - cur;
     }
     BicgState s;
     PF_TRY(read_state(g, st, &s));
     if (trace_level() > 1)
       fprintf(stderr, "[pf] %s it %d rel %.3e rho %.3e alpha %.3e omega %.3e done %d status %d\n",
-              sizeof(T) == 8 ? "fp64" : "fp32", s.iter, sqrt(s.rnorm2 / (s.bnorm2 > 0 ? s.bnorm2 : 1.0)), s.rho,
-              s.alpha, s.omega, s.done, s.status);
+              f64 ? "fp64" : "fp32", s.iter, sqrt(s.rnorm2 / (s.bnorm2 > 0 ? s.bnorm2 : 1.0)), s.rho, s.alpha,
+              s.omega, s.done, s.status);
     if (s.done) {
       *out = s;
       return PF_OK;
     }
   }
-}
-
-// True FP64 residual of x: fills st (rnorm2, rinf, bnorm2, done) and writes (float)(b - A x) to b32.
-template <bool UNI>
-pf_status true_residual(pf_grid* g, const OpView<double>& op, double* x, const float* d, const double* b,
-                        double tol, int norm, BicgState* out) {
-  PF_TRY(set_state(g, g->st, tol, norm, 0));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b, g->nx, g->ny, g->nz, g->st, g->stream));
-  {
-    const int slot = prof_begin(g, d ? 2 : 1);
-    PF_CK((pf::launch_refine<UNI>(op, x, d, b, g->b32, g->part, g->st, g->L)));
-    prof_end(g, slot, PF_PROF_RESIDUAL);
-  }
-  return read_state(g, g->st, out);
 }
 
 double measure_of(const BicgState& s, int norm) {
@@ -326,14 +398,18 @@ double measure_of(const BicgState& s, int norm) {
 
 template <bool UNI>
 pf_status solve_fp64(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, pf_report* rep) {
-  const OpView<double> V = view64(g, op);
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_impose(x, b, V.dinv, g->N, g->stream));
+  const OpArrays<double> A = ops64(g, op);
+  const Krylov<double> K = kry64(g);
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_impose(x, b, A.dinv, g->geom.np, g->stream));
   PF_TRY(set_state(g, g->st, o.tol, o.norm, o.max_iter));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b, g->nx, g->ny, g->nz, g->st, g->stream));
+  PF_TRY(residual<UNI>(g, A, x, b, 1, &K, g->st));  // Table 3 step 2
   BicgState s;
-  PF_TRY((run_bicgstab<double, UNI>(g, V, x, false, b, g->r64, g->p64, g->v64, g->rt64, g->t64, g->st, &s)));
+  PF_TRY((iterate<double, UNI>(g, A, x, K, g->st, &s)));
+  // true residual of the final iterate
   BicgState tr;
-  PF_TRY(true_residual<UNI>(g, V, x, nullptr, b, o.tol, o.norm, &tr));
+  PF_TRY(set_state(g, g->st, o.tol, o.norm, 0));
+  PF_TRY(residual<UNI>(g, A, x, b, 0, nullptr, g->st));
+  PF_TRY(read_state(g, g->st, &tr));
   rep->status = s.status;
   rep->iterations = s.iter;
   rep->refinements = 0;
@@ -346,44 +422,47 @@ pf_status solve_fp64(pf_grid* g, int op, const double* b, double* x, const pf_so
 
 template <bool UNI>
 pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, pf_report* rep) {
-  const OpView<double> V = view64(g, op);
-  const OpView<float> W = view32(g, op);
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_impose(x, b, V.dinv, g->N, g->stream));
+  const OpArrays<double> A = ops64(g, op);
+  const OpArrays<float> W = ops32(g, op);
+  const Krylov<float> K = kry32(g);
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_impose(x, b, A.dinv, g->geom.np, g->stream));
   int iters = 0, ref = 0, status = PF_E_NOCONV;
   BicgState tr{};
-  bool have_d = false;
   for (;;) {
-    PF_TRY(true_residual<UNI>(g, V, x, have_d ? g->d32 : nullptr, b, o.tol, o.norm, &tr));
+    // FP64 true residual b - A x -> b32 (and its norms)
+    PF_TRY(set_state(g, g->st, o.tol, o.norm, 0));
+    PF_TRY(residual<UNI>(g, A, x, b, 0, nullptr, g->st));
+    PF_TRY(read_state(g, g->st, &tr));
+    if (trace_level() > 0)
+      fprintf(stderr, "[pf] mixed op %d refinement %d: true residual %.3e\n", op, ref, measure_of(tr, o.norm));
     if (tr.done) {
       status = PF_OK;
-      break;
-    }
-    if (ref >= o.max_refine || iters >= o.max_iter) {
-      status = PF_E_NOCONV;
-      break;
-    }
-    // FP32 inner solve A d = r (r = b - A x in b32), d0 = 0, to relative tolerance inner_tol; an inner
-    // solve that stagnates is cut off after INNER_CAP iterations and its correction is kept
-    PF_CK(cudaMemsetAsync(g->d32, 0, g->N * sizeof(float), g->stream));
-    const int cap = o.max_iter - iters < INNER_CAP ? o.max_iter - iters : INNER_CAP;
-    PF_TRY(set_state(g, g->st2, o.inner_tol, PF_NORM_REL2, cap));
-    BicgState s;
-    PF_TRY((run_bicgstab<float, UNI>(g, W, g->d32, true, g->b32, g->r32, g->p32, g->v32, g->rt32, g->t32, g->st2,
-                                     &s)));
-    iters += s.iter;
-    have_d = true;
-    ++ref;
-    if (trace_level() > 0)
-      fprintf(stderr, "[pf] mixed op %d refinement %d: true residual %.3e, inner status %d iters %d\n", op, ref,
-              measure_of(tr, o.norm), s.status, s.iter);
-    if (s.status == PF_E_BREAKDOWN && s.iter == 0) {
-      status = PF_E_BREAKDOWN;
       break;
     }
     if (!isfinite(tr.rnorm2)) {
       status = PF_E_BREAKDOWN;
       break;
     }
+    if (ref >= o.max_refine || iters >= o.max_iter) {
+      status = PF_E_NOCONV;
+      break;
+    }
+    // FP32 inner solve A d = r from d = 0 to relative tolerance inner_tol; an inner solve that stagnates is cut
+    // off after INNER_CAP iterations and its correction kept
+    PF_CK(cudaMemsetAsync(g->d32, 0, g->geom.np * sizeof(float), g->stream));
+    const int cap = o.max_iter - iters < INNER_CAP ? o.max_iter - iters : INNER_CAP;
+    PF_TRY(set_state(g, g->st2, o.inner_tol, PF_NORM_REL2, cap));
+    PF_LAUNCH(g, PF_PROF_INIT, pf::launch_init_zero<float>(g->b32, g->geom, K.r[0], K.rt, K.p[0], K.v[0], K.t,
+                                                            g->part, g->st2, g->stream));
+    BicgState s;
+    PF_TRY((iterate<float, UNI>(g, W, g->d32, K, g->st2, &s)));
+    iters += s.iter;
+    ++ref;
+    if (s.status == PF_E_BREAKDOWN && s.iter == 0) {
+      status = PF_E_BREAKDOWN;
+      break;
+    }
+    PF_LAUNCH(g, PF_PROF_RESIDUAL, pf::launch_add_f32(x, g->d32, g->geom.np, g->stream));  // x += d
   }
   rep->status = status;
   rep->iterations = iters;
@@ -408,8 +487,8 @@ pf_status check_opts(const pf_solve_opts& o) {
 }
 
 pf_status update_pf2(pf_grid* g) {
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_eps_diag(g->dsum, g->sig, g->solvent, g->nx, g->ny, g->nz, g->diag2,
-                                                  g->dinv2, g->dinv2_32, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER,
+            pf::launch_eps_diag(g->dsum, g->sig, g->solvent, g->geom, g->diag2, g->dinv2, g->dinv2_32, g->stream));
   return PF_OK;
 }
 
@@ -418,33 +497,56 @@ pf_status update_pf2(pf_grid* g) {
 // trilinear fixed-charge source (Eq. 3).  kappa (PF2) is reset to zero.  Sets g->err when a charge
 // lies outside the grid.
 pf_status build_operators(pf_grid* g) {
-  const long N = g->N;
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_faces(g->eps, g->nx, g->ny, g->nz, g->h, g->wE, g->wN, g->wU, g->dsum,
-                                               g->stream));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wE, g->wE32, N, g->stream));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wN, g->wN32, N, g->stream));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wU, g->wU32, N, g->stream));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_eps_diag(g->dsum, nullptr, nullptr, g->nx, g->ny, g->nz, g->diagP, g->dinvP,
-                                                  g->dinvP32, g->stream));
-  PF_CK(cudaMemsetAsync(g->sig, 0, N * sizeof(double), g->stream));
+  const long NP = g->geom.np;
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_faces(g->eps, g->geom, g->h, g->wE, g->wN, g->wU, g->dsum, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wE, g->wE32, NP, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wN, g->wN32, NP, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wU, g->wU32, NP, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER,
+            pf::launch_eps_diag(g->dsum, nullptr, nullptr, g->geom, g->diagP, g->dinvP, g->dinvP32, g->stream));
+  PF_CK(cudaMemsetAsync(g->sig, 0, NP * sizeof(double), g->stream));
   PF_TRY(update_pf2(g));
-  const double wc = g->eps_s * g->lc * g->lc / (g->h * g->h);
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf1_dinv(g->solvent, g->nx, g->ny, g->nz, 1.0 / (6.0 * wc + g->eps_s),
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf1_dinv(g->solvent, g->geom, 1.0 / (6.0 * pf1_face(g) + g->eps_s),
                                                   g->dinv1, g->dinv1_32, g->stream));
-  PF_CK(cudaMemsetAsync(g->ffix, 0, N * sizeof(double), g->stream));
+  PF_CK(cudaMemsetAsync(g->ffix, 0, NP * sizeof(double), g->stream));
   PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), g->stream));
   if (g->nq > 0)
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_spread(g->dch, g->nq, g->origin[0], g->origin[1], g->origin[2], g->h,
-                                                  g->lam, g->nx, g->ny, g->nz, g->ffix, g->err, g->stream));
+                                                  g->lam, g->geom, g->ffix, g->err, g->stream));
+  return PF_OK;
+}
+
+// compact caller array (host or device) -> padded device array
+pf_status pack_in(pf_grid* g, const void* src, int mem, void* dst, int type) {
+  const size_t bytes = g->N * (type == 0 ? sizeof(double) : 1);
+  const void* from = src;
+  if (mem != PF_MEM_DEVICE) {
+    PF_CK(cudaMemcpyAsync(g->stage, src, bytes, cudaMemcpyHostToDevice, g->stream));
+    from = g->stage;
+  }
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pack(from, dst, g->geom, type, g->stream));
+  return PF_OK;
+}
+
+// padded device field(s) -> compact caller array (host or device), `count` consecutive fields
+pf_status unpack_out(pf_grid* g, const double* src, int count, double* dst, int mem) {
+  for (int f = 0; f < count; ++f) {
+    double* to = mem == PF_MEM_DEVICE ? dst + (size_t)f * g->N : g->stage;
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_unpack(src + (size_t)f * g->geom.np, to, g->geom, 1, g->stream));
+    if (mem != PF_MEM_DEVICE)
+      PF_CK(cudaMemcpyAsync(dst + (size_t)f * g->N, g->stage, g->N * sizeof(double), cudaMemcpyDeviceToHost,
+                            g->stream));
+  }
   return PF_OK;
 }
 
 }  // namespace
 
-// Device bytes that pf_create_grid allocates for n_nodes nodes (used for the serving budget).
-size_t pf_internal_grid_bytes(long n_nodes) {
-  const size_t per_node = 30 * sizeof(double) + pf::MAXSP * sizeof(double) + 16 * sizeof(float) + 1;
-  return (size_t)n_nodes * per_node + (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double) + 4096;
+// Device bytes that pf_create_grid allocates for a grid (used for the serving budget).
+size_t pf_internal_grid_bytes(int nx, int ny, int nz) {
+  const pf::Geom g = pf::make_geom(nx, ny, nz);
+  const size_t per_node = 31 * sizeof(double) + pf::MAXSP * sizeof(double) + 16 * sizeof(float) + 1;
+  return (size_t)g.np * per_node + (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double) + 4096;
 }
 
 extern "C" {
@@ -481,6 +583,7 @@ pf_status pf_create_grid(int nx, int ny, int nz, double h_A, const double origin
   g->ny = ny;
   g->nz = nz;
   g->N = (long)nx * ny * nz;
+  g->geom = pf::make_geom(nx, ny, nz);
   g->h = h_A;
   for (int a = 0; a < 3; ++a) g->origin[a] = origin_A[a];
   g->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -490,7 +593,9 @@ pf_status pf_create_grid(int nx, int ny, int nz, double h_A, const double origin
     delete g;
     return s;
   }
-  g->L = pf::make_launch(nx, ny, nz, g->stream);
+  g->L.ntiles = pf::tiles_for(nx, ny, nz);
+  g->L.stream = g->stream;
+  g->L.wait_limit = WAIT_LIMIT;
   cudaError_t e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) {
     free_all(g);
@@ -581,9 +686,8 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
   g->lo_hat = c->phi_zlo_V / g->Tv;
   g->hi_hat = c->phi_zhi_V / g->Tv;
 
-  const long N = g->N;
-  PF_CK(cudaMemcpyAsync(g->eps, c->eps, N * sizeof(double), cudaMemcpyHostToDevice, g->stream));
-  PF_CK(cudaMemcpyAsync(g->solvent, c->solvent, N, cudaMemcpyHostToDevice, g->stream));
+  PF_TRY(pack_in(g, c->eps, PF_MEM_HOST, g->eps, 0));
+  PF_TRY(pack_in(g, c->solvent, PF_MEM_HOST, g->solvent, 1));
   if (g->dch) {
     cudaFree(g->dch);
     g->dch = nullptr;
@@ -604,8 +708,7 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
 pf_status pf_set_kappa(pf_grid* g, const double* kappa, int mem) {
   if (!g || !kappa) return fail(PF_E_INVAL, "grid and kappa are required");
   if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first");
-  PF_CK(cudaMemcpyAsync(g->sig, kappa, g->N * sizeof(double),
-                        mem == PF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+  PF_TRY(pack_in(g, kappa, mem, g->sig, 0));
   PF_TRY(update_pf2(g));
   PF_CK(cudaStreamSynchronize(g->stream));
   return PF_OK;
@@ -621,18 +724,11 @@ pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int me
   if (opts) o = *opts; else pf_default_solve_opts(&o);
   PF_TRY(check_opts(o));
   pf_report rep{};
-  const size_t bytes = g->N * sizeof(double);
   PF_CK(cudaEventRecord(g->ev0, g->stream));
-  const double* bd = b;
-  double* xd = x;
-  if (mem == PF_MEM_HOST) {
-    PF_CK(cudaMemcpyAsync(g->bb, b, bytes, cudaMemcpyHostToDevice, g->stream));
-    PF_CK(cudaMemcpyAsync(g->xb, x, bytes, cudaMemcpyHostToDevice, g->stream));
-    bd = g->bb;
-    xd = g->xb;
-  }
-  PF_TRY(solve_dev(g, op, bd, xd, o, &rep));
-  if (mem == PF_MEM_HOST) PF_CK(cudaMemcpyAsync(x, g->xb, bytes, cudaMemcpyDeviceToHost, g->stream));
+  PF_TRY(pack_in(g, b, mem, g->bb, 0));
+  PF_TRY(pack_in(g, x, mem, g->xb, 0));
+  PF_TRY(solve_dev(g, op, g->bb, g->xb, o, &rep));
+  PF_TRY(unpack_out(g, g->xb, 1, x, mem));
   PF_CK(cudaEventRecord(g->ev1, g->stream));
   PF_CK(cudaEventSynchronize(g->ev1));
   float ms = 0.f;
@@ -642,7 +738,8 @@ pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int me
   if (report) *report = rep;
   if (rep.status != PF_OK)
     return fail((pf_status)rep.status, rep.status == PF_E_NOCONV ? "linear solve did not converge"
-                                                                  : "BiCGSTAB breakdown");
+                                       : rep.status == PF_E_TIMEOUT ? "a device wait timed out"
+                                                                    : "BiCGSTAB breakdown");
   return PF_OK;
 }
 
@@ -654,8 +751,9 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   PF_TRY(check_opts(o.lin));
   if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1)
     return fail(PF_E_INVAL, "invalid pf_nl_opts");
-  const int nx = g->nx, ny = g->ny, nz = g->nz;
-  const long N = g->N;
+  if (res->mem != PF_MEM_HOST && res->mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "bad result mem");
+  const pf::Geom& G = g->geom;
+  const long NP = G.np;
   cudaStream_t s = g->stream;
   PF_CK(cudaEventRecord(g->ev0, s));
   res->status = PF_OK;
@@ -668,11 +766,10 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   // step a1: operators and fixed-charge source from the device-resident coefficients
   PF_TRY(build_operators(g));
   // Table 4 step 4: PF2 with rho' = Psi = 0 -> Phi_0
-  PF_CK(cudaMemsetAsync(g->phi0, 0, N * sizeof(double), s));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, nx, ny, nz, s));
-  PF_CK(cudaMemsetAsync(g->psi, 0, N * sizeof(double), s));
-  PF_LAUNCH(g, PF_PROF_OTHER,
-            pf::launch_pf2_rhs(g->psi, g->solvent, g->ffix, g->eps_s, g->lo_hat, g->hi_hat, nx, ny, nz, g->b2, s));
+  PF_CK(cudaMemsetAsync(g->phi0, 0, NP * sizeof(double), s));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, G, s));
+  PF_CK(cudaMemsetAsync(g->psi, 0, NP * sizeof(double), s));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf2_rhs(g->psi, g->solvent, g->ffix, g->eps_s, g->lo_hat, g->hi_hat, G, g->b2, s));
   PF_TRY(solve_dev(g, PF_OP_POISSON, g->b2, g->phi0, o.lin, &rep));
   res->lin_iters_first = rep.iterations;
   res->lin_iters_total += rep.iterations;
@@ -680,47 +777,47 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   for (int outer = 1; st == PF_OK && outer <= o.max_outer; ++outer) {
     // Eq. (1) at Phi_0 -> b_PF1 = -lambda rho, kappa, PF2 right-hand-side part (Table 4 steps 5-6)
     PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
-    PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, nx, ny, nz, g->b1, g->sig,
-                                                 g->c2, nullptr, nullptr, nullptr, g->err, s));
+    PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, g->b1, g->sig, g->c2,
+                                                 nullptr, nullptr, nullptr, g->err, s));
     PF_TRY(update_pf2(g));
     PF_TRY(solve_dev(g, PF_OP_PF1, g->b1, g->psi, o.lin, &rep));  // Eq. (12)
     res->lin_iters_total += rep.iterations;
     if (rep.status != PF_OK) { st = (pf_status)rep.status; break; }
     PF_LAUNCH(g, PF_PROF_OTHER,
-              pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat, nx, ny, nz, g->b2, s));
-    PF_CK(cudaMemcpyAsync(g->phi, g->phi0, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+              pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat, G, g->b2, s));
+    PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
     PF_TRY(solve_dev(g, PF_OP_PF2, g->b2, g->phi, o.lin, &rep));  // Eq. (13)
     res->lin_iters_total += rep.iterations;
     if (rep.status != PF_OK) { st = (pf_status)rep.status; break; }
     // Table 4 step 7: relax and test
-    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_relax(g->phi0, g->phi, o.omega, N, g->part, g->ticket, g->delta, s));
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_relax(g->phi0, g->phi, o.omega, NP, g->part, g->ticket, g->delta, s));
     PF_CK(cudaMemcpyAsync(g->host_delta, g->delta, sizeof(double), cudaMemcpyDeviceToHost, s));
     PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     PF_CK(cudaStreamSynchronize(s));
     if (*g->host_err) { st = PF_E_GAMMA; break; }
     res->outer_iters = outer;
     res->delta = *g->host_delta;
-    if (trace_level() > 0) fprintf(stderr, "[pf] outer %d delta %.6e lin_total %d\n", outer, res->delta, res->lin_iters_total);
+    if (trace_level() > 0)
+      fprintf(stderr, "[pf] outer %d delta %.6e lin_total %d\n", outer, res->delta, res->lin_iters_total);
     if (res->delta <= o.tol_outer) break;
     if (outer == o.max_outer) st = PF_E_NOCONV;
   }
   // outputs at the final potential
   PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
-  PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, nx, ny, nz, nullptr, nullptr,
-                                               nullptr, g->Cbuf, g->Sbuf, g->Gbuf, g->err, s));
-  const cudaMemcpyKind kind = res->mem == PF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, nullptr, nullptr, nullptr,
+                                               g->Cbuf, g->Sbuf, g->Gbuf, g->err, s));
   if (res->phi_V) {
-    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, N, s));
-    PF_CK(cudaMemcpyAsync(res->phi_V, g->phi, N * sizeof(double), kind, s));
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, NP, s));
+    PF_TRY(unpack_out(g, g->phi, 1, res->phi_V, res->mem));
   }
   if (res->C_M) {
-    const long nc = N * g->sp.ns;
+    const long nc = NP * g->sp.ns;
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->Cbuf, 1.0 / g->molar, g->Cbuf, nc, s));
-    PF_CK(cudaMemcpyAsync(res->C_M, g->Cbuf, nc * sizeof(double), kind, s));
+    PF_TRY(unpack_out(g, g->Cbuf, g->sp.ns, res->C_M, res->mem));
   }
-  if (res->S) PF_CK(cudaMemcpyAsync(res->S, g->Sbuf, N * sizeof(double), kind, s));
-  if (res->Gamma) PF_CK(cudaMemcpyAsync(res->Gamma, g->Gbuf, N * sizeof(double), kind, s));
-  if (res->Psi) PF_CK(cudaMemcpyAsync(res->Psi, g->psi, N * sizeof(double), kind, s));
+  if (res->S) PF_TRY(unpack_out(g, g->Sbuf, 1, res->S, res->mem));
+  if (res->Gamma) PF_TRY(unpack_out(g, g->Gbuf, 1, res->Gamma, res->mem));
+  if (res->Psi) PF_TRY(unpack_out(g, g->psi, 1, res->Psi, res->mem));
   PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   PF_CK(cudaEventRecord(g->ev1, s));
   PF_CK(cudaEventSynchronize(g->ev1));

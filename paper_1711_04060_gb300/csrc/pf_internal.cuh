@@ -1,5 +1,6 @@
 // pf_internal.cuh -- types and kernel launchers shared by the library's translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -11,6 +12,29 @@ constexpr int NTHREADS = TX * TY;
 constexpr int ZC = 16;           // interior planes per z-chunk of a tile
 constexpr int MAXSP = 8;
 constexpr int NPART = 8;         // per-block partial values reduced by the last block
+constexpr int HBX = TX + 8;      // TMA halo box: x from x0-4 (16-byte aligned start) to x0+TX+3
+constexpr int HBY = TY + 2;      // halo box rows y0-1 .. y0+TY
+
+// Device arrays use a padded layout: node (i,j,k) at i + px*j + px*ny*k with px a multiple of 8,
+// so every row starts on a 32-byte boundary and rows are valid TMA strides.
+struct Geom {
+  int nx, ny, nz, px;
+  long plane;  // px * ny
+  long np;     // plane * nz (allocated elements)
+  long n;      // nx * ny * nz (nodes)
+};
+
+inline Geom make_geom(int nx, int ny, int nz) {
+  Geom g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.px = (nx + 7) / 8 * 8;
+  g.plane = (long)g.px * ny;
+  g.np = g.plane * nz;
+  g.n = (long)nx * ny * nz;
+  return g;
+}
 
 // Device-resident BiCGSTAB scalars (Table 3); written only by the last block of a kernel.
 struct BicgState {
@@ -28,25 +52,26 @@ struct BicgState {
   int pad;
 };
 
-// View of one 7-point operator in right-preconditioned form.  Rows with dinv == 0 are
-// identity rows (Dirichlet or membrane rows of PF1).
-template <typename T>
-struct OpView {
-  const T* wE;    // face coefficient between (i,j,k) and (i+1,j,k), already / h^2; at i = nx-1 it
-                  // holds the mirror face of (nx-2, nx-1)
-  const T* wN;    // same in y
-  const T* wU;    // same in z
-  const T* dinv;  // 1/diag on free rows, 0 on identity rows
-  const double* diag;  // FP64 diagonal (only for FP64 full-operator applies); may be null for UNI
-  T wc;           // uniform face coefficient (UNI operators)
-  double diagc;   // uniform diagonal (UNI operators)
-  int nx, ny, nz;
+// Tensor maps of one stencil kernel: NH arrays loaded as halo boxes (HBX x HBY at (x0-4, y0-1, k)),
+// NC arrays loaded as centre boxes (TX x TY at (x0, y0, k)).
+template <int NH, int NC>
+struct Maps {
+  CUtensorMap h[NH];
+  CUtensorMap c[NC > 0 ? NC : 1];
 };
 
+// Slots of the stencil kernels (the API fills the maps in this order):
+//   phase B:   halo {r, v, dinv, wE, wN} (PF1: {r, v, dinv}),      centre {r~, wU} (PF1: {r~})
+//   phase C+A: halo {r, v, t, p, dinv, wE, wN} (PF1: first five), centre {x, r~, wU} (PF1: {x, r~})
+//   residual:  halo {x, dinv, wE, wN} (PF1: {x, dinv}),             centre {b, diag, wU} (PF1: {b})
+template <bool UNI> struct SlotsB { static constexpr int NH = UNI ? 3 : 5, NC = UNI ? 1 : 2; };
+template <bool UNI> struct SlotsCA { static constexpr int NH = UNI ? 5 : 7, NC = UNI ? 2 : 3; };
+template <bool UNI> struct SlotsRes { static constexpr int NH = UNI ? 2 : 4, NC = UNI ? 1 : 3; };
+
 struct Launch {
-  int blocks;       // persistent grid size for stencil kernels
   int ntiles;
   cudaStream_t stream;
+  unsigned long long wait_limit;  // clock cycles a block may wait on one TMA stage
 };
 
 // species constants of Eq. (1) in scaled units
@@ -61,57 +86,57 @@ struct SpeciesParams {
 };
 
 int tiles_for(int nx, int ny, int nz);
-
-// ---- setup (a1) ----
-cudaError_t launch_faces(const double* eps, int nx, int ny, int nz, double h, double* wE, double* wN,
-                         double* wU, double* dsum, cudaStream_t s);
-cudaError_t launch_spread(const double* charges, int nq, double ox, double oy, double oz, double h, double lam,
-                          int nx, int ny, int nz, double* f, int* err, cudaStream_t s);
-// diag = dsum + sig (sig may be null, masked by solvent when smask non-null); dinv = 1/diag off the
-// Dirichlet planes, 0 on them; optional FP32 copies.
-cudaError_t launch_eps_diag(const double* dsum, const double* sig, const uint8_t* smask, int nx, int ny, int nz,
-                            double* diag, double* dinv, float* dinv32, cudaStream_t s);
-cudaError_t launch_pf1_dinv(const uint8_t* solvent, int nx, int ny, int nz, double dinvc, double* dinv,
-                            float* dinv32, cudaStream_t s);
-cudaError_t launch_to_f32(const double* a, float* b, long n, cudaStream_t s);
-cudaError_t launch_impose(double* x, const double* b, const double* dinv, long n, cudaStream_t s);
-
-// ---- BiCGSTAB (Table 3) ----
-template <typename T, bool UNI>
-cudaError_t launch_init(const OpView<T>& op, const T* x, bool x_zero, const T* b, T* r, T* rt, T* p, T* v, T* t,
-                        double* part, BicgState* st, const Launch& L);
-template <typename T, bool UNI>
-cudaError_t launch_phase_b(const OpView<T>& op, const T* r, const T* v, const T* rt, T* t, double* part,
-                           BicgState* st, const Launch& L);
-template <typename T, bool UNI>
-cudaError_t launch_phase_ca(const OpView<T>& op, const T* r, const T* v, const T* p, const T* t, const T* rt, T* x,
-                            T* r_out, T* p_out, T* v_out, double* part, BicgState* st, int prime, const Launch& L);
-
-// FP64 residual for iterative refinement: x += d (if d), r = b - A x; writes r32 = (float) r; fills st
-// (bnorm2, rnorm2, rinf) and sets st->done when the FP64 tolerance is met.
-template <bool UNI>
-cudaError_t launch_refine(const OpView<double>& op, double* x, const float* d, const double* b, float* r32,
-                          double* part, BicgState* st, const Launch& L);
-// resets a solver state with the given stop test (all scalars zero, not done)
-cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, cudaStream_t s);
-// sum of b^2 over the Dirichlet planes into st->bnorm2 (launch before init / refine)
-cudaError_t launch_plane_bb(const double* b, int nx, int ny, int nz, BicgState* st, cudaStream_t s);
-Launch make_launch(int nx, int ny, int nz, cudaStream_t s);
 int max_partial_blocks();
 
+// host: encode a 3D tensor map over a padded device array (halo box when halo, else centre box)
+bool encode_map(CUtensorMap* m, const void* base, const Geom& g, int elem_bytes, bool halo);
+
+// ---- setup (a1) ----
+cudaError_t launch_faces(const double* eps, const Geom& g, double h, double* wE, double* wN, double* wU,
+                         double* dsum, cudaStream_t s);
+cudaError_t launch_spread(const double* charges, int nq, double ox, double oy, double oz, double h, double lam,
+                          const Geom& g, double* f, int* err, cudaStream_t s);
+cudaError_t launch_eps_diag(const double* dsum, const double* sig, const uint8_t* smask, const Geom& g, double* diag,
+                            double* dinv, float* dinv32, cudaStream_t s);
+cudaError_t launch_pf1_dinv(const uint8_t* solvent, const Geom& g, double dinvc, double* dinv, float* dinv32,
+                            cudaStream_t s);
+cudaError_t launch_to_f32(const double* a, float* b, long n, cudaStream_t s);
+cudaError_t launch_impose(double* x, const double* b, const double* dinv, long n, cudaStream_t s);
+// compact (x fastest, pitch nx) <-> padded (pitch px) copies of `count` consecutive fields;
+// type 0 double, 1 uint8
+cudaError_t launch_pack(const void* src, void* dst, const Geom& g, int type, cudaStream_t s);
+cudaError_t launch_unpack(const double* src, double* dst, const Geom& g, int count, cudaStream_t s);
+
+// ---- BiCGSTAB (Table 3) ----
+cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, cudaStream_t s);
+cudaError_t launch_plane_bb(const double* b, const Geom& g, BicgState* st, cudaStream_t s);
+// r = r~ = b, p = v = t = 0 on interior nodes (x0 = 0); partials b.b, r.r, max|r|
+template <typename T>
+cudaError_t launch_init_zero(const T* b, const Geom& g, T* r, T* rt, T* p, T* v, T* t, double* part, BicgState* st,
+                             cudaStream_t s);
+// r = b - A x (x holds b on identity rows) in FP64; init = 1 also writes r~ = r, p = v = t = 0 and starts
+// the BiCGSTAB state; init = 0 writes r32 = (float) r and the refinement state
+template <bool UNI>
+cudaError_t launch_residual(const Maps<SlotsRes<UNI>::NH, SlotsRes<UNI>::NC>& m, const Geom& g, double wc,
+                            double diagc, int init, double* r, double* rt, double* p, double* v, double* t, float* r32,
+                            double* part, BicgState* st, const Launch& L);
+template <typename T, bool UNI>
+cudaError_t launch_phase_b(const Maps<SlotsB<UNI>::NH, SlotsB<UNI>::NC>& m, const Geom& g, T wc, T* t, double* part,
+                           BicgState* st, const Launch& L);
+template <typename T, bool UNI>
+cudaError_t launch_phase_ca(const Maps<SlotsCA<UNI>::NH, SlotsCA<UNI>::NC>& m, const Geom& g, T wc, T* x, T* r_out,
+                            T* p_out, T* v_out, double* part, BicgState* st, int prime, const Launch& L);
+cudaError_t launch_add_f32(double* x, const float* d, long n, cudaStream_t s);
+
 // ---- nonlinear step (Eq. 1, Eq. 11-13, Table 4) ----
-// Pointwise Fermi/steric step at phi0 (solvent nodes).  Writes b1 = -lambda rho (free PF1 rows, else 0),
-// sig = kappa (solvent nodes, else 0), c2 = sig*phi0 + ffix; when C/S/G are non-null also the outputs.
 cudaError_t launch_fermi(const double* phi0, const uint8_t* solvent, const double* ffix, const SpeciesParams& sp,
-                         int nx, int ny, int nz, double* b1, double* sig, double* c2, double* C, double* S,
-                         double* G, int* err, cudaStream_t s);
-// b2 = -s eps_s Psi + c2 off the Dirichlet planes, Dirichlet values on them
+                         const Geom& g, double* b1, double* sig, double* c2, double* C, double* S, double* G, int* err,
+                         cudaStream_t s);
 cudaError_t launch_pf2_rhs(const double* psi, const uint8_t* solvent, const double* c2, double eps_s, double lo,
-                           double hi, int nx, int ny, int nz, double* b2, cudaStream_t s);
-// phi0 <- omega phi0 + (1-omega) phi, delta = max |change| (block maxima in part, last block -> *delta)
+                           double hi, const Geom& g, double* b2, cudaStream_t s);
 cudaError_t launch_relax(double* phi0, const double* phi, double omega, long n, double* part, unsigned int* ticket,
                          double* delta, cudaStream_t s);
 cudaError_t launch_scale(const double* a, double s, double* out, long n, cudaStream_t st);
-cudaError_t launch_set_dirichlet(double* x, double lo, double hi, int nx, int ny, int nz, cudaStream_t s);
+cudaError_t launch_set_dirichlet(double* x, double lo, double hi, const Geom& g, cudaStream_t s);
 
 }  // namespace pf

@@ -1,19 +1,66 @@
 // pf_kernels.cu -- sm_103a kernels of the Poisson-Fermi hot path.
 //
-// Stencil kernels walk 2D tiles (TX x TY nodes in x-y, one warp per x row, so every global
-// access of a warp is one coalesced row segment) up through a chunk of ZC interior z-planes.
-// The stencil input of a plane is computed once per node (with its one-node x-y halo) into a
-// shared-memory plane; the planes below and above come from registers of the same thread, so a
-// node's input vectors are read from DRAM once per kernel (halo rows of neighbouring tiles come
-// from L2).  The axpy updates of BiCGSTAB (Table 3 steps 9, 13, 16, 17), the Jacobi scaling
-// and the inner products (steps 4, 12, 15) are fused into the two stencil kernels of an
-// iteration; each kernel's inner products are reduced by warp shuffles, a block tree and a
-// last-arriving-block pass over the per-block partials in fixed order (deterministic).
+// Stencil kernels (BiCGSTAB phases and the FP64 residual) walk 2D tiles of TX x TY nodes (one warp
+// per x row) up through a chunk of ZC interior z-planes.  Every input plane of a tile arrives by
+// TMA (cp.async.bulk.tensor.3d) into a ring of D shared-memory stages, each guarded by an mbarrier
+// that the copies complete; one thread keeps D planes in flight ahead of the consumers, and the
+// stream of planes continues across the tiles a block owns, so the copy engine hides DRAM latency
+// without registers.  Arrays read at neighbours arrive as halo boxes (x0-4 .. x0+TX+3, y0-1 ..
+// y0+TY: the x start stays 16-byte aligned), the others as centre boxes.  Each plane's stencil input
+// (the BiCGSTAB direction p or s after the axpy and the Jacobi scaling) is computed once per node
+// into a ring of three shared planes; the planes below and above come from registers.  The axpy
+// updates (Table 3 steps 9, 13, 16, 17), the Jacobi scaling and the inner products (steps 4, 12, 15)
+// are fused into the two stencil kernels of an iteration.  Inner products are reduced by warp
+// shuffles, a block tree and the last-arriving block over the per-block partials in fixed order.
 #include <math.h>
+#include <stdio.h>
 
 #include "pf_internal.cuh"
 
 namespace pf {
+
+// ------------------------------------------------------------------ PTX helpers (TMA + mbarrier)
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` clock cycles (the caller then reports PF_E_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 
 // ------------------------------------------------------------------ accumulation helpers
 template <typename T>
@@ -27,8 +74,7 @@ struct Acc<double> {
 };
 
 // FP32 products summed with an error-free transformation (TwoProduct by FMA, TwoSum), so a
-// thread's partial sum carries about twice the FP32 precision before it is handed to the
-// FP64 block reduction.
+// thread's partial sum carries about twice the FP32 precision before the FP64 block reduction.
 template <>
 struct Acc<float> {
   float hi = 0.f, lo = 0.f;
@@ -47,11 +93,10 @@ struct Acc<float> {
 template <typename T>
 __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
 
-// Reduce NV per-thread values over the block (value j is a max when bit j of maxmask is set,
-// else a sum) and store the block's result in part[blockIdx.x * NPART + j].
+// Block reduction of NV values (bit j of maxmask: value j is a maximum, else a sum) into
+// part[blockIdx.x * NPART + j]; scratch holds at least NTHREADS / 32 * NV doubles.
 template <int NV>
-__device__ __forceinline__ void block_partials(double (&v)[NV], unsigned maxmask, double* part) {
-  __shared__ double red[NTHREADS / 32][NV];
+__device__ __forceinline__ void block_partials(double (&v)[NV], unsigned maxmask, double* part, double* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
@@ -61,18 +106,19 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], unsigned maxmask
       const double b = __shfl_down_sync(0xffffffffu, a, o);
       a = ((maxmask >> j) & 1u) ? fmax(a, b) : a + b;
     }
-    if (lane == 0) red[warp][j] = a;
+    if (lane == 0) scratch[warp * NV + j] = a;
   }
   __syncthreads();
   if (threadIdx.x < NV) {
     const int j = threadIdx.x;
-    double a = red[0][j];
-    for (int w = 1; w < NTHREADS / 32; ++w) a = ((maxmask >> j) & 1u) ? fmax(a, red[w][j]) : a + red[w][j];
+    double a = scratch[j];
+    for (int w = 1; w < NTHREADS / 32; ++w)
+      a = ((maxmask >> j) & 1u) ? fmax(a, scratch[w * NV + j]) : a + scratch[w * NV + j];
     part[blockIdx.x * NPART + j] = a;
   }
 }
 
-// Returns true in the block that arrives last; that block then sees every partial.
+// True in the block that arrives last; that block then sees every block's partials.
 __device__ __forceinline__ bool arrive_last(unsigned int* ticket) {
   __shared__ int last;
   __threadfence();
@@ -83,10 +129,10 @@ __device__ __forceinline__ bool arrive_last(unsigned int* ticket) {
   return last;
 }
 
-// In the last block: totals over all blocks' partials, in fixed order.
+// In the last block: totals over all blocks' partials in fixed order; scratch holds NTHREADS * NV doubles.
 template <int NV>
-__device__ __forceinline__ void total_partials(const double* part, unsigned maxmask, double (&tot)[NV]) {
-  __shared__ double red[NTHREADS][NV];
+__device__ __forceinline__ void total_partials(const double* part, unsigned maxmask, double (&tot)[NV],
+                                               double* scratch) {
   double a[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) a[j] = 0.0;  // sums start at 0; maxima are of absolute values
@@ -98,19 +144,20 @@ __device__ __forceinline__ void total_partials(const double* part, unsigned maxm
     }
   }
 #pragma unroll
-  for (int j = 0; j < NV; ++j) red[threadIdx.x][j] = a[j];
+  for (int j = 0; j < NV; ++j) scratch[threadIdx.x * NV + j] = a[j];
   __syncthreads();
   for (int s = NTHREADS / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
 #pragma unroll
-      for (int j = 0; j < NV; ++j)
-        red[threadIdx.x][j] = ((maxmask >> j) & 1u) ? fmax(red[threadIdx.x][j], red[threadIdx.x + s][j])
-                                                     : red[threadIdx.x][j] + red[threadIdx.x + s][j];
+      for (int j = 0; j < NV; ++j) {
+        const double u = scratch[threadIdx.x * NV + j], w = scratch[(threadIdx.x + s) * NV + j];
+        scratch[threadIdx.x * NV + j] = ((maxmask >> j) & 1u) ? fmax(u, w) : u + w;
+      }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int j = 0; j < NV; ++j) tot[j] = red[0][j];
+  for (int j = 0; j < NV; ++j) tot[j] = scratch[j];
 }
 
 // ------------------------------------------------------------------ tile geometry
@@ -123,7 +170,7 @@ struct Tile {
   int x0, y0, kb, ke;
 };
 
-__device__ __forceinline__ Tile tile_of(int t, int nx, int ny, int nz) {
+__device__ __forceinline__ Tile tile_of(int t, int nx, int nz) {
   const int nzc = (nz - 2 + ZC - 1) / ZC, ntx = (nx + TX - 1) / TX;
   const int zc = t % nzc, xy = t / nzc;
   Tile r;
@@ -134,9 +181,8 @@ __device__ __forceinline__ Tile tile_of(int t, int nx, int ny, int nz) {
   return r;
 }
 
-// Position g in [-1, n] of a tile (with halo) -> node index whose value it holds: the node
-// itself, the mirror image for the two ghost positions (zero-flux sides, Eq. 4), or -1 when
-// no output of the tile uses it.
+// Position g in [-1, n] -> the node whose value it holds: itself, the mirror image for the two ghost
+// positions of the zero-flux sides (Eq. 4), or -1 when no output of the tile uses it.
 __device__ __forceinline__ int mirror(int g, int n) {
   if (g < 0) return 1;
   if (g < n) return g;
@@ -144,11 +190,12 @@ __device__ __forceinline__ int mirror(int g, int n) {
   return -1;
 }
 
-constexpr int PW = TX + 2;                 // smem plane row pitch
-constexpr int PLANE = (TY + 2) * PW;       // smem plane size
+constexpr int PW = TX + 2;             // shared stencil-plane row pitch
+constexpr int PLANE = (TY + 2) * PW;   // shared stencil-plane size
 constexpr int NHALO = 2 * (TX + 2) + 2 * TY;
 
-// halo slot h (0..NHALO-1) -> tile-local (lx, ly) in [-1, TX] x [-1, TY]
+__device__ __forceinline__ int cs(int lx, int ly) { return (ly + 1) * PW + (lx + 1); }
+
 __device__ __forceinline__ void halo_pos(int h, int& lx, int& ly) {
   if (h < TX + 2) { lx = h - 1; ly = -1; return; }
   h -= TX + 2;
@@ -160,14 +207,21 @@ __device__ __forceinline__ void halo_pos(int h, int& lx, int& ly) {
   ly = h;
 }
 
-// Per-thread geometry of one tile: the (mirrored) x-y offsets of the thread's centre and halo slot.
+// Per-thread geometry of a tile: halo-box offsets of the thread's centre and of its halo slot (with
+// the mirror applied), the shared-plane index of the halo slot, and whether the centre is a node.
 struct TileGeo {
-  long cxy;       // x-y offset of the centre position (or -1)
-  long hxy;       // x-y offset of the halo slot (or -1 / no slot)
-  int hs;         // smem index of the halo slot
-  int gi, gj;     // centre node
-  bool valid;     // centre is a real node (produces output)
+  int cbo;    // halo-box offset of the centre position, -1 if unused
+  int hbo;    // halo-box offset of the halo slot's position, -1 if unused
+  int hs;     // shared-plane index of the halo slot, -1 if the thread has none
+  int gi, gj;
+  bool valid;
 };
+
+__device__ __forceinline__ int box_off(int gi, int gj, const Tile& tl, int nx, int ny) {
+  const int mi = mirror(gi, nx), mj = mirror(gj, ny);
+  if (mi < 0 || mj < 0) return -1;
+  return (mj - tl.y0 + 1) * HBX + (mi - tl.x0 + 4);
+}
 
 __device__ __forceinline__ TileGeo tile_geo(const Tile& tl, int nx, int ny) {
   TileGeo g;
@@ -175,491 +229,595 @@ __device__ __forceinline__ TileGeo tile_geo(const Tile& tl, int nx, int ny) {
   g.gi = tl.x0 + lx;
   g.gj = tl.y0 + ly;
   g.valid = g.gi < nx && g.gj < ny;
-  const int mi = mirror(g.gi, nx), mj = mirror(g.gj, ny);
-  g.cxy = (mi >= 0 && mj >= 0) ? (mi + (long)nx * mj) : -1;
-  g.hxy = -1;
+  g.cbo = box_off(g.gi, g.gj, tl, nx, ny);
+  g.hbo = -1;
   g.hs = -1;
   if (threadIdx.x < NHALO) {
     int hx, hy;
     halo_pos(threadIdx.x, hx, hy);
-    const int hi = mirror(tl.x0 + hx, nx), hj = mirror(tl.y0 + hy, ny);
-    g.hs = (hy + 1) * PW + (hx + 1);
-    g.hxy = (hi >= 0 && hj >= 0) ? (hi + (long)nx * hj) : -1;
+    g.hs = cs(hx, hy);
+    g.hbo = box_off(tl.x0 + hx, tl.y0 + hy, tl, nx, ny);
   }
   return g;
 }
 
-__device__ __forceinline__ int cs(int lx, int ly) { return (ly + 1) * PW + (lx + 1); }
-
-// Weighted neighbour sum of the 7-point operator at an output node: sum_nb w_nb q_nb with the
-// west/south faces taken from the neighbour's east/north face (or the node's own at a mirror
-// side) and the down face carried from the plane below.
-template <typename T, bool UNI>
-__device__ __forceinline__ T nb_sum(const OpView<T>& op, const T* cur, int lx, int ly, long c, int gi, int gj,
-                                    T q_up, T q_dn, T wU_c, T wD) {
-  const T qE = cur[cs(lx + 1, ly)], qW = cur[cs(lx - 1, ly)];
-  const T qN = cur[cs(lx, ly + 1)], qS = cur[cs(lx, ly - 1)];
-  if (UNI) {
-    return op.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
-  } else {
-    const T wE = __ldg(op.wE + c), wW = __ldg(op.wE + c - (gi > 0 ? 1 : 0));
-    const T wN = __ldg(op.wN + c), wS = __ldg(op.wN + c - (gj > 0 ? op.nx : 0));
-    T a = wE * qE;
-    a = fma(wW, qW, a);
-    a = fma(wN, qN, a);
-    a = fma(wS, qS, a);
-    a = fma(wU_c, q_up, a);
-    a = fma(wD, q_dn, a);
-    return a;
-  }
+template <typename T>
+__host__ __device__ constexpr int halo_slot_bytes() {
+  return (HBX * HBY * (int)sizeof(T) + 127) / 128 * 128;
+}
+template <typename T>
+__host__ __device__ constexpr int centre_slot_bytes() {
+  return TX * TY * (int)sizeof(T);
 }
 
-template <typename T, bool UNI>
-__device__ __forceinline__ T face_up(const OpView<T>& op, long c) {
-  if (UNI) return op.wc;
-  return __ldg(op.wU + c);
+template <class Op>
+__host__ __device__ constexpr int stage_bytes() {
+  return Op::NH * halo_slot_bytes<typename Op::T>() + Op::NC * centre_slot_bytes<typename Op::T>();
 }
 
-// ------------------------------------------------------------------ BiCGSTAB init
-// r = b - A x (x already holds b on identity rows), r~ = r, p = v = t = 0; partials: b.b, r.r, max|r|.
-template <typename T, bool UNI>
-__global__ void __launch_bounds__(NTHREADS) k_init(OpView<T> op, const T* __restrict__ x, int x_zero,
-                                                   const T* __restrict__ b, T* __restrict__ r, T* __restrict__ rt,
-                                                   T* __restrict__ p, T* __restrict__ v, T* __restrict__ t,
-                                                   double* part, BicgState* st, int ntiles) {
-  __shared__ T Qa[PLANE], Qb[PLANE];
-  const int nx = op.nx, ny = op.ny, nz = op.nz;
-  const long sxy = (long)nx * ny;
-  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-  Acc<T> abb, arr;
-  T rmax = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const Tile tl = tile_of(tile, nx, ny, nz);
-    const TileGeo g = tile_geo(tl, nx, ny);
-    T* cur = Qa;
-    T* nxt = Qb;
-    auto xq = [&](long id) -> T { return x_zero ? T(0) : x[id]; };
-    T q_dn = (g.cxy >= 0) ? xq(g.cxy + (tl.kb - 1) * sxy) : T(0);
-    T q_c = (g.cxy >= 0) ? xq(g.cxy + tl.kb * sxy) : T(0);
-    cur[cs(lx, ly)] = q_c;
-    if (g.hs >= 0) cur[g.hs] = (g.hxy >= 0) ? xq(g.hxy + tl.kb * sxy) : T(0);
-    T wD = (g.cxy >= 0 && !x_zero) ? face_up<T, UNI>(op, g.cxy + (tl.kb - 1) * sxy) : T(0);
-    __syncthreads();
-    for (int k = tl.kb; k < tl.ke; ++k) {
-      const T q_up = (g.cxy >= 0) ? xq(g.cxy + (k + 1) * sxy) : T(0);
-      nxt[cs(lx, ly)] = q_up;
-      if (g.hs >= 0) nxt[g.hs] = (g.hxy >= 0) ? xq(g.hxy + (k + 1) * sxy) : T(0);
-      __syncthreads();
-      if (g.valid) {
-        const long c = g.gi + (long)nx * g.gj + k * sxy;
-        const T bc = b[c];
-        T rc;
-        T wU_c = T(0);
-        if (x_zero) {
-          rc = bc;
-        } else {
-          wU_c = face_up<T, UNI>(op, c);
-          const T dv = op.dinv[c];
-          if (dv == T(0)) {
-            rc = bc - q_c;
-          } else {
-            const T diag = UNI ? T(op.diagc) : (op.diag ? T(op.diag[c]) : T(1) / dv);
-            const T a = nb_sum<T, UNI>(op, cur, lx, ly, c, g.gi, g.gj, q_up, q_dn, wU_c, wD);
-            rc = bc - (diag * q_c - a);
-          }
-        }
-        r[c] = rc;
-        rt[c] = rc;
-        p[c] = T(0);
-        v[c] = T(0);
-        t[c] = T(0);
-        abb.prod(bc, bc);
-        arr.prod(rc, rc);
-        rmax = fmax(rmax, tabs(rc));
-        wD = wU_c;
-      }
-      __syncthreads();
-      T* tmp = cur;
-      cur = nxt;
-      nxt = tmp;
-      q_dn = q_c;
-      q_c = q_up;
-    }
-    __syncthreads();
-  }
-  double vals[3] = {abb.value(), arr.value(), (double)rmax};
-  block_partials<3>(vals, 4u, part);
-  if (arrive_last(&st->ticket)) {
-    double tot[3];
-    total_partials<3>(part, 4u, tot);
-    if (threadIdx.x == 0) {
-      // Dirichlet planes: r = b - x = 0 there, b may be nonzero; the norms above skip them, so add b.b of
-      // the planes through the host (st->bnorm2 is preset to that value).
-      double bb = tot[0] + st->bnorm2;
-      if (bb == 0.0) bb = 1.0;
-      st->bnorm2 = bb;
-      st->rho = tot[1];
-      st->rnorm2 = tot[1];
-      st->rinf = tot[2];
-      st->tol2 = st->tol * st->tol * bb;
-      st->alpha = st->omega = st->beta = 0.0;
-      st->sexit = 0;
-      st->iter = 0;
-      const bool conv = st->norm == 0 ? (tot[1] <= st->tol2) : (tot[2] < st->tol);
-      st->done = conv ? 1 : 0;
-      st->status = 0;
-      st->ticket = 0;
-    }
-  }
+template <class Op>
+__host__ __device__ constexpr int smem_bytes() {
+  // stages | three stencil planes | D mbarriers | 128 bytes of alignment slack
+  return Op::D * stage_bytes<Op>() + 3 * PLANE * (int)sizeof(typename Op::T) + Op::D * 8 + 128;
 }
 
-// ------------------------------------------------------------------ BiCGSTAB phase B
-// s = r - alpha v (step 13), t = A M^-1 s (step 14); partials r~.s, r~.t, t.s, t.t, s.s, max|s|.
-template <typename T, bool UNI>
-__global__ void __launch_bounds__(NTHREADS) k_phase_b(OpView<T> op, const T* __restrict__ r,
-                                                      const T* __restrict__ v, const T* __restrict__ rt,
-                                                      T* __restrict__ t, double* part, BicgState* st, int ntiles) {
-  if (*(volatile int*)&st->done) return;
-  __shared__ T Qa[PLANE], Qb[PLANE];
-  const int nx = op.nx, ny = op.ny, nz = op.nz;
-  const long sxy = (long)nx * ny;
-  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-  const T al = (T)st->alpha;
-  Acc<T> a_rs, a_rt, a_ts, a_tt, a_ss;
-  T smax = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const Tile tl = tile_of(tile, nx, ny, nz);
-    const TileGeo g = tile_geo(tl, nx, ny);
-    T* cur = Qa;
-    T* nxt = Qb;
-    auto sq = [&](long id, T& s_) -> T {
-      s_ = fma(-al, v[id], r[id]);
-      return op.dinv[id] * s_;
-    };
-    T s_dn, s_c, s_up;
-    T q_dn = (g.cxy >= 0) ? sq(g.cxy + (tl.kb - 1) * sxy, s_dn) : T(0);
-    T q_c = T(0);
-    s_c = T(0);
-    if (g.cxy >= 0) q_c = sq(g.cxy + tl.kb * sxy, s_c);
-    cur[cs(lx, ly)] = q_c;
-    if (g.hs >= 0) {
-      T dummy;
-      cur[g.hs] = (g.hxy >= 0) ? sq(g.hxy + tl.kb * sxy, dummy) : T(0);
-    }
-    T wD = (g.cxy >= 0) ? face_up<T, UNI>(op, g.cxy + (tl.kb - 1) * sxy) : T(0);
-    __syncthreads();
-    for (int k = tl.kb; k < tl.ke; ++k) {
-      T q_up = T(0);
-      s_up = T(0);
-      if (g.cxy >= 0) q_up = sq(g.cxy + (k + 1) * sxy, s_up);
-      nxt[cs(lx, ly)] = q_up;
-      if (g.hs >= 0) {
-        T dummy;
-        nxt[g.hs] = (g.hxy >= 0) ? sq(g.hxy + (k + 1) * sxy, dummy) : T(0);
-      }
-      __syncthreads();
-      if (g.valid) {
-        const long c = g.gi + (long)nx * g.gj + k * sxy;
-        const T wU_c = face_up<T, UNI>(op, c);
-        T tc;
-        if (op.dinv[c] == T(0)) {
-          tc = s_c;
-        } else {
-          tc = s_c - nb_sum<T, UNI>(op, cur, lx, ly, c, g.gi, g.gj, q_up, q_dn, wU_c, wD);
-        }
-        t[c] = tc;
-        const T rtc = rt[c];
-        a_rs.prod(rtc, s_c);
-        a_rt.prod(rtc, tc);
-        a_ts.prod(tc, s_c);
-        a_tt.prod(tc, tc);
-        a_ss.prod(s_c, s_c);
-        smax = fmax(smax, tabs(s_c));
-        wD = wU_c;
-      }
-      __syncthreads();
-      T* tmp = cur;
-      cur = nxt;
-      nxt = tmp;
-      q_dn = q_c;
-      q_c = q_up;
-      s_c = s_up;
-    }
-    __syncthreads();
-  }
-  double vals[6] = {a_rs.value(), a_rt.value(), a_ts.value(), a_tt.value(), a_ss.value(), (double)smax};
-  block_partials<6>(vals, 32u, part);
-  if (arrive_last(&st->ticket)) {
-    double tot[6];
-    total_partials<6>(part, 32u, tot);
-    if (threadIdx.x == 0) {
-      const double rs = tot[0], rtt = tot[1], ts = tot[2], tt = tot[3], ss = tot[4], smx = tot[5];
-      st->snorm2 = ss;
-      st->sinf = smx;
-      const bool sconv = st->norm == 0 ? (ss <= st->tol2) : (smx < st->tol);
-      if (sconv) {  // early exit of the Templates algorithm: x += alpha M^-1 p, r = s
-        st->sexit = 1;
-        st->omega = 0.0;
-        st->beta = 0.0;
-      } else if (tt == 0.0 || !isfinite(tt) || !isfinite(ts) || !isfinite(ss)) {
-        st->status = 4;  // PF_E_BREAKDOWN (a zero or non-finite t.t stops before x is touched)
-        st->done = 1;
-      } else {
-        const double om = ts / tt;  // step 15
-        st->omega = om;
-        // r~.r_new with r_new = s - omega t (steps 17 and 4 of the next iteration), needed now
-        // because the next p is formed in the same kernel as r_new
-        const double rho_new = rs - om * rtt;
-        const double be = (om != 0.0) ? (rho_new / st->rho) * (st->alpha / om) : 0.0;  // step 8
-        st->beta = isfinite(be) ? be : 0.0;
-      }
-      st->ticket = 0;
-    }
-  }
+// The reduction scratch at the end of a kernel reuses the stage ring (all copies consumed by then).
+template <class Op>
+constexpr bool scratch_fits() {
+  return Op::D * stage_bytes<Op>() >= NTHREADS * 8 * (int)sizeof(double);
 }
 
-// ------------------------------------------------------------------ BiCGSTAB phase C+A
-// s = r - alpha v, x += alpha M^-1 p + omega M^-1 s (step 16), r' = s - omega t (step 17),
-// p' = r' + beta (p - omega v) (step 9 of the next iteration), v' = A M^-1 p' (step 11);
-// partials r~.v', r~.r', r'.r', max|r'|.  With prime = 1 (alpha = omega = beta = 0) it forms the
-// first p = r0 and v = A M^-1 r0.
-template <typename T, bool UNI>
-__global__ void __launch_bounds__(NTHREADS) k_phase_ca(OpView<T> op, const T* __restrict__ r,
-                                                       const T* __restrict__ v, const T* __restrict__ p,
-                                                       const T* __restrict__ t, const T* __restrict__ rt,
-                                                       T* __restrict__ x, T* __restrict__ r_out,
-                                                       T* __restrict__ p_out, T* __restrict__ v_out, double* part,
-                                                       BicgState* st, int prime, int ntiles) {
-  if (*(volatile int*)&st->done) return;
-  __shared__ T Qa[PLANE], Qb[PLANE];
-  const int nx = op.nx, ny = op.ny, nz = op.nz;
-  const long sxy = (long)nx * ny;
-  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-  const T al = (T)st->alpha, om = (T)st->omega, be = (T)st->beta;
-  Acc<T> a_rv, a_rr, a_r2;
-  T rmax = 0;
-  struct Ctr {
-    T s, rn, pn, pold, di;
+// ------------------------------------------------------------------ the pipelined stencil kernel
+// Op supplies: T, NH, NC, D, CHECK_DONE, Args, Sc, Ctr, Accs and scalars(), q_of(), centre(),
+// up_face(), output(), finish().
+template <class Op>
+__global__ void __launch_bounds__(NTHREADS) k_stencil(const __grid_constant__ Maps<Op::NH, Op::NC> maps,
+                                                      typename Op::Args a, Geom g, int ntiles,
+                                                      unsigned long long wait_limit) {
+  using T = typename Op::T;
+  constexpr int D = Op::D, NH = Op::NH, NC = Op::NC;
+  constexpr int HB = halo_slot_bytes<T>(), CB = centre_slot_bytes<T>(), STAGE = stage_bytes<Op>();
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  T* qring = reinterpret_cast<T*>(smem + D * STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + D * STAGE + 3 * PLANE * sizeof(T));
+
+  if (Op::CHECK_DONE && *(volatile int*)&a.st->done) return;
+  const typename Op::Sc sc = Op::scalars(a);
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // producer (thread 0): the next (tile, plane) of this block's stream of planes
+  int pt = blockIdx.x, pj = 0;
+  unsigned pseq = 0;
+  auto issue = [&]() {
+    const Tile tl = tile_of(pt, g.nx, g.nz);
+    const int stage = pseq % D;
+    unsigned char* sb = smem + stage * STAGE;
+    uint64_t* bar = &bars[stage];
+    mbar_expect_tx(bar, NH * HBX * HBY * sizeof(T) + NC * TX * TY * sizeof(T));
+    const int k = tl.kb - 1 + pj;
+#pragma unroll
+    for (int h = 0; h < NH; ++h) tma_load_3d(sb + h * HB, &maps.h[h], tl.x0 - 4, tl.y0 - 1, k, bar);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) tma_load_3d(sb + NH * HB + c * CB, &maps.c[c], tl.x0, tl.y0, k, bar);
+    ++pseq;
+    if (++pj == tl.ke - tl.kb + 2) {
+      pj = 0;
+      pt += gridDim.x;
+    }
   };
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const Tile tl = tile_of(tile, nx, ny, nz);
-    const TileGeo g = tile_geo(tl, nx, ny);
-    T* cur = Qa;
-    T* nxt = Qb;
-    auto pq = [&](long id, Ctr& o) -> T {
-      const T vv = v[id], pp = p[id];
-      o.s = fma(-al, vv, r[id]);
-      o.rn = fma(-om, t[id], o.s);
-      o.pn = fma(be, fma(-om, vv, pp), o.rn);
-      o.pold = pp;
-      o.di = op.dinv[id];
-      return o.di * o.pn;
-    };
-    Ctr cd, cc, cu;
-    T q_dn = (g.cxy >= 0) ? pq(g.cxy + (tl.kb - 1) * sxy, cd) : T(0);
-    T q_c = T(0);
-    cc.s = cc.rn = cc.pn = cc.pold = cc.di = T(0);
-    if (g.cxy >= 0) q_c = pq(g.cxy + tl.kb * sxy, cc);
-    cur[cs(lx, ly)] = q_c;
-    if (g.hs >= 0) {
-      Ctr dummy;
-      cur[g.hs] = (g.hxy >= 0) ? pq(g.hxy + tl.kb * sxy, dummy) : T(0);
-    }
-    T wD = (g.cxy >= 0) ? face_up<T, UNI>(op, g.cxy + (tl.kb - 1) * sxy) : T(0);
-    __syncthreads();
-    for (int k = tl.kb; k < tl.ke; ++k) {
-      T q_up = T(0);
-      cu.s = cu.rn = cu.pn = cu.pold = cu.di = T(0);
-      if (g.cxy >= 0) q_up = pq(g.cxy + (k + 1) * sxy, cu);
-      nxt[cs(lx, ly)] = q_up;
-      if (g.hs >= 0) {
-        Ctr dummy;
-        nxt[g.hs] = (g.hxy >= 0) ? pq(g.hxy + (k + 1) * sxy, dummy) : T(0);
+  if (threadIdx.x == 0)
+    for (int d = 0; d < D && pt < ntiles; ++d) issue();
+
+  typename Op::Accs acc;
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  unsigned seq = 0;
+  bool failed = false;
+  for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+    const Tile tl = tile_of(t, g.nx, g.nz);
+    const TileGeo geo = tile_geo(tl, g.nx, g.ny);
+    const int planes = tl.ke - tl.kb + 2;
+    typename Op::Ctr cprev{}, cnow{};
+    T q_dn = T(0), q_prev = T(0), wD = T(0);
+    for (int j = 0; j < planes; ++j, ++seq) {
+      const int stage = seq % D;
+      const bool ok = mbar_wait(&bars[stage], (seq / D) & 1u, wait_limit);
+      T qc = T(0);
+      T* Q = qring + (j % 3) * PLANE;
+      if (ok) {
+        const unsigned char* sb = smem + stage * STAGE;
+        const T* H[NH];
+        const T* C[NC];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) H[h] = reinterpret_cast<const T*>(sb + h * HB);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) C[c] = reinterpret_cast<const T*>(sb + NH * HB + c * CB);
+        if (geo.cbo >= 0) qc = Op::q_of(sc, H, geo.cbo, &cnow);
+        if (geo.valid) Op::centre(a, H, C, geo.cbo, ly * TX + lx, geo.gi > 0, geo.gj > 0, cnow);
+        Q[cs(lx, ly)] = qc;
+        if (geo.hs >= 0) Q[geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
       }
-      __syncthreads();
-      if (g.valid) {
-        const long c = g.gi + (long)nx * g.gj + k * sxy;
-        const T wU_c = face_up<T, UNI>(op, c);
-        T vn;
-        if (cc.di == T(0)) {
-          vn = cc.pn;
-        } else {
-          vn = cc.pn - nb_sum<T, UNI>(op, cur, lx, ly, c, g.gi, g.gj, q_up, q_dn, wU_c, wD);
-          if (!prime) {
-            T xc = x[c];
-            xc = fma(al, cc.di * cc.pold, xc);
-            xc = fma(om, cc.di * cc.s, xc);
-            x[c] = xc;
-          }
-        }
-        r_out[c] = cc.rn;
-        p_out[c] = cc.pn;
-        v_out[c] = vn;
-        const T rtc = rt[c];
-        a_rv.prod(rtc, vn);
-        a_rr.prod(rtc, cc.rn);
-        a_r2.prod(cc.rn, cc.rn);
-        rmax = fmax(rmax, tabs(cc.rn));
-        wD = wU_c;
+      // one barrier per plane; the vote makes a timed-out wait a decision of the whole block
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
       }
-      __syncthreads();
-      T* tmp = cur;
-      cur = nxt;
-      nxt = tmp;
-      q_dn = q_c;
-      q_c = q_up;
-      cc = cu;
+      if (threadIdx.x == 0 && pt < ntiles) {
+        fence_proxy_async();
+        issue();
+      }
+      if (j >= 2 && geo.valid) {
+        const int k = tl.kb + j - 2;
+        const long cidx = geo.gi + (long)g.px * geo.gj + g.plane * k;
+        Op::output(sc, a, qring + ((j - 1) % 3) * PLANE, lx, ly, cidx, cprev, q_dn, qc, wD, acc);
+      }
+      if (j >= 1) {
+        q_dn = q_prev;
+        wD = Op::up_face(a, cprev);
+      }
+      q_prev = qc;
+      cprev = cnow;
     }
-    __syncthreads();
+    if (!failed) __syncthreads();
   }
-  double vals[4] = {a_rv.value(), a_rr.value(), a_r2.value(), (double)rmax};
-  block_partials<4>(vals, 8u, part);
-  if (arrive_last(&st->ticket)) {
-    double tot[4];
-    total_partials<4>(part, 8u, tot);
+  if (failed) {
+    // give up: let this block's copies in flight land (bounded), report the timeout, skip the reduction
     if (threadIdx.x == 0) {
-      const double rv = tot[0], rr = tot[1], r2 = tot[2], rmx = tot[3];
-      st->ticket = 0;
-      if (!prime) {
-        st->iter += 1;
-        st->rnorm2 = r2;
-        st->rinf = rmx;
-        const bool conv = st->norm == 0 ? (r2 <= st->tol2) : (rmx < st->tol);
-        if (st->sexit || conv) {
-          st->done = 1;
-          st->status = 0;
-          return;
-        }
-        if (st->omega == 0.0) {
-          st->done = 1;
-          st->status = 4;
-          return;
-        }
-        if (st->iter >= st->max_iter) {
-          st->done = 1;
-          st->status = 3;  // PF_E_NOCONV
-          return;
-        }
+      for (unsigned s = seq; s < pseq; ++s) mbar_wait(&bars[s % D], (s / D) & 1u, wait_limit);
+      a.st->status = 7;  // PF_E_TIMEOUT
+      atomicExch(&a.st->done, 1);
+    }
+    return;
+  }
+  __syncthreads();
+  Op::finish(a, acc, reinterpret_cast<double*>(smem));
+}
+
+// ------------------------------------------------------------------ phase B: s = r - alpha v, t = A M^-1 s
+template <typename T_, bool UNI>
+struct OpB {
+  using T = T_;
+  static constexpr int NH = SlotsB<UNI>::NH, NC = SlotsB<UNI>::NC, D = sizeof(T_) == 4 ? 3 : 2;
+  static constexpr bool CHECK_DONE = true;
+  enum { R = 0, V = 1, DI = 2, WE = 3, WN = 4 };
+  enum { RT = 0, WU = 1 };
+  struct Args {
+    double* part;
+    BicgState* st;
+    T* t;
+    T wc;
+  };
+  struct Sc {
+    T al;
+  };
+  struct Ctr {
+    T s, di, rt, wU, wEc, wEw, wNc, wNs;
+  };
+  struct Accs {
+    Acc<T> rs, rtt, ts, tt, ss;
+    T smax = T(0);
+  };
+  __device__ static Sc scalars(const Args& a) { return Sc{(T)a.st->alpha}; }
+  __device__ static T q_of(const Sc& sc, const T* const* H, int o, Ctr* c) {
+    const T s = fma(-sc.al, H[V][o], H[R][o]);
+    const T di = H[DI][o];
+    if (c) {
+      c->s = s;
+      c->di = di;
+    }
+    return di * s;
+  }
+  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, int co, bool west,
+                                bool south, Ctr& c) {
+    c.rt = C[RT][co];
+    if (UNI) {
+      c.wU = c.wEc = c.wEw = c.wNc = c.wNs = a.wc;
+    } else {
+      c.wU = C[WU][co];
+      c.wEc = H[WE][o];
+      c.wEw = west ? H[WE][o - 1] : c.wEc;
+      c.wNc = H[WN][o];
+      c.wNs = south ? H[WN][o - HBX] : c.wNc;
+    }
+  }
+  __device__ static T up_face(const Args& a, const Ctr& c) { return UNI ? a.wc : c.wU; }
+  __device__ static void output(const Sc&, const Args& a, const T* Q, int lx, int ly, long cidx, const Ctr& c, T q_dn,
+                                T q_up, T wD, Accs& acc) {
+    T tc;
+    if (c.di == T(0)) {
+      tc = c.s;
+    } else {
+      const T qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
+      T nb;
+      if (UNI) {
+        nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
+      } else {
+        nb = c.wEc * qE;
+        nb = fma(c.wEw, qW, nb);
+        nb = fma(c.wNc, qN, nb);
+        nb = fma(c.wNs, qS, nb);
+        nb = fma(c.wU, q_up, nb);
+        nb = fma(wD, q_dn, nb);
       }
-      if (rr == 0.0 || rv == 0.0 || !isfinite(rr) || !isfinite(rv) || !isfinite(rr / rv)) {
+      tc = c.s - nb;
+    }
+    a.t[cidx] = tc;
+    acc.rs.prod(c.rt, c.s);
+    acc.rtt.prod(c.rt, tc);
+    acc.ts.prod(tc, c.s);
+    acc.tt.prod(tc, tc);
+    acc.ss.prod(c.s, c.s);
+    acc.smax = fmax(acc.smax, tabs(c.s));
+  }
+  __device__ static void finish(const Args& a, const Accs& acc, double* scratch) {
+    double vals[6] = {acc.rs.value(), acc.rtt.value(), acc.ts.value(), acc.tt.value(), acc.ss.value(),
+                      (double)acc.smax};
+    block_partials<6>(vals, 32u, a.part, scratch);
+    if (!arrive_last(&a.st->ticket)) return;
+    double tot[6];
+    total_partials<6>(a.part, 32u, tot, scratch);
+    if (threadIdx.x != 0) return;
+    BicgState* st = a.st;
+    const double rs = tot[0], rtt = tot[1], ts = tot[2], tt = tot[3], ss = tot[4], smx = tot[5];
+    st->snorm2 = ss;
+    st->sinf = smx;
+    const bool sconv = st->norm == 0 ? (ss <= st->tol2) : (smx < st->tol);
+    if (sconv) {  // early exit of the Templates algorithm: x += alpha M^-1 p, r = s
+      st->sexit = 1;
+      st->omega = 0.0;
+      st->beta = 0.0;
+    } else if (tt == 0.0 || !isfinite(tt) || !isfinite(ts) || !isfinite(ss)) {
+      st->status = 4;  // PF_E_BREAKDOWN, before x is touched
+      st->done = 1;
+    } else {
+      const double om = ts / tt;  // step 15
+      st->omega = om;
+      // r~.r_new with r_new = s - omega t (steps 17 and 4 of the next iteration): the next p is
+      // formed in the same kernel as r_new, so its beta is taken from the exact identity
+      const double rho_new = rs - om * rtt;
+      const double be = (om != 0.0) ? (rho_new / st->rho) * (st->alpha / om) : 0.0;  // step 8
+      st->beta = isfinite(be) ? be : 0.0;
+    }
+    st->ticket = 0;
+  }
+};
+
+// ------------------------------------------------------------------ phase C+A
+// s = r - alpha v, x += alpha M^-1 p + omega M^-1 s (step 16), r' = s - omega t (step 17),
+// p' = r' + beta (p - omega v) (step 9 of the next iteration), v' = A M^-1 p' (step 11).
+template <typename T_, bool UNI>
+struct OpCA {
+  using T = T_;
+  static constexpr int NH = SlotsCA<UNI>::NH, NC = SlotsCA<UNI>::NC, D = sizeof(T_) == 4 ? 3 : 2;
+  static constexpr bool CHECK_DONE = true;
+  enum { R = 0, V = 1, TT = 2, P = 3, DI = 4, WE = 5, WN = 6 };
+  enum { X = 0, RT = 1, WU = 2 };
+  struct Args {
+    double* part;
+    BicgState* st;
+    T* x;
+    T* r_out;
+    T* p_out;
+    T* v_out;
+    T wc;
+    int prime;
+  };
+  struct Sc {
+    T al, om, be;
+  };
+  struct Ctr {
+    T s, rn, pn, pold, di, x, rt, wU, wEc, wEw, wNc, wNs;
+  };
+  struct Accs {
+    Acc<T> rv, rr, r2;
+    T rmax = T(0);
+  };
+  __device__ static Sc scalars(const Args& a) { return Sc{(T)a.st->alpha, (T)a.st->omega, (T)a.st->beta}; }
+  __device__ static T q_of(const Sc& sc, const T* const* H, int o, Ctr* c) {
+    const T vv = H[V][o], pp = H[P][o];
+    const T s = fma(-sc.al, vv, H[R][o]);
+    const T rn = fma(-sc.om, H[TT][o], s);
+    const T pn = fma(sc.be, fma(-sc.om, vv, pp), rn);
+    const T di = H[DI][o];
+    if (c) {
+      c->s = s;
+      c->rn = rn;
+      c->pn = pn;
+      c->pold = pp;
+      c->di = di;
+    }
+    return di * pn;
+  }
+  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, int co, bool west,
+                                bool south, Ctr& c) {
+    c.x = C[X][co];
+    c.rt = C[RT][co];
+    if (UNI) {
+      c.wU = c.wEc = c.wEw = c.wNc = c.wNs = a.wc;
+    } else {
+      c.wU = C[WU][co];
+      c.wEc = H[WE][o];
+      c.wEw = west ? H[WE][o - 1] : c.wEc;
+      c.wNc = H[WN][o];
+      c.wNs = south ? H[WN][o - HBX] : c.wNc;
+    }
+  }
+  __device__ static T up_face(const Args& a, const Ctr& c) { return UNI ? a.wc : c.wU; }
+  __device__ static void output(const Sc& sc, const Args& a, const T* Q, int lx, int ly, long cidx, const Ctr& c,
+                                T q_dn, T q_up, T wD, Accs& acc) {
+    T vn;
+    if (c.di == T(0)) {
+      vn = c.pn;
+    } else {
+      const T qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
+      T nb;
+      if (UNI) {
+        nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
+      } else {
+        nb = c.wEc * qE;
+        nb = fma(c.wEw, qW, nb);
+        nb = fma(c.wNc, qN, nb);
+        nb = fma(c.wNs, qS, nb);
+        nb = fma(c.wU, q_up, nb);
+        nb = fma(wD, q_dn, nb);
+      }
+      vn = c.pn - nb;
+      if (!a.prime) {
+        T xc = fma(sc.al, c.di * c.pold, c.x);
+        xc = fma(sc.om, c.di * c.s, xc);
+        a.x[cidx] = xc;
+      }
+    }
+    a.r_out[cidx] = c.rn;
+    a.p_out[cidx] = c.pn;
+    a.v_out[cidx] = vn;
+    acc.rv.prod(c.rt, vn);
+    acc.rr.prod(c.rt, c.rn);
+    acc.r2.prod(c.rn, c.rn);
+    acc.rmax = fmax(acc.rmax, tabs(c.rn));
+  }
+  __device__ static void finish(const Args& a, const Accs& acc, double* scratch) {
+    double vals[4] = {acc.rv.value(), acc.rr.value(), acc.r2.value(), (double)acc.rmax};
+    block_partials<4>(vals, 8u, a.part, scratch);
+    if (!arrive_last(&a.st->ticket)) return;
+    double tot[4];
+    total_partials<4>(a.part, 8u, tot, scratch);
+    if (threadIdx.x != 0) return;
+    BicgState* st = a.st;
+    const double rv = tot[0], rr = tot[1], r2 = tot[2], rmx = tot[3];
+    st->ticket = 0;
+    if (!a.prime) {
+      st->iter += 1;
+      st->rnorm2 = r2;
+      st->rinf = rmx;
+      const bool conv = st->norm == 0 ? (r2 <= st->tol2) : (rmx < st->tol);
+      if (st->sexit || conv) {
+        st->done = 1;
+        st->status = 0;
+        return;
+      }
+      if (st->omega == 0.0) {
         st->done = 1;
         st->status = 4;
         return;
       }
-      st->rho = rr;        // step 4 of the next iteration
-      st->alpha = rr / rv; // step 12 of the next iteration
-    }
-  }
-}
-
-// ------------------------------------------------------------------ FP64 residual (refinement)
-// r = b - A x in FP64; writes r32 = rt32 = (float) r; partials r.r, max|r|, b.b.
-template <bool UNI>
-__global__ void __launch_bounds__(NTHREADS) k_residual(OpView<double> op, const double* __restrict__ x,
-                                                       const double* __restrict__ b, float* __restrict__ r32,
-                                                       double* part, BicgState* st, int ntiles) {
-  __shared__ double Qa[PLANE], Qb[PLANE];
-  const int nx = op.nx, ny = op.ny, nz = op.nz;
-  const long sxy = (long)nx * ny;
-  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-  double arr = 0.0, abb = 0.0, rmax = 0.0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const Tile tl = tile_of(tile, nx, ny, nz);
-    const TileGeo g = tile_geo(tl, nx, ny);
-    double* cur = Qa;
-    double* nxt = Qb;
-    double q_dn = (g.cxy >= 0) ? x[g.cxy + (tl.kb - 1) * sxy] : 0.0;
-    double q_c = (g.cxy >= 0) ? x[g.cxy + tl.kb * sxy] : 0.0;
-    cur[cs(lx, ly)] = q_c;
-    if (g.hs >= 0) cur[g.hs] = (g.hxy >= 0) ? x[g.hxy + tl.kb * sxy] : 0.0;
-    double wD = (g.cxy >= 0) ? face_up<double, UNI>(op, g.cxy + (tl.kb - 1) * sxy) : 0.0;
-    __syncthreads();
-    for (int k = tl.kb; k < tl.ke; ++k) {
-      const double q_up = (g.cxy >= 0) ? x[g.cxy + (k + 1) * sxy] : 0.0;
-      nxt[cs(lx, ly)] = q_up;
-      if (g.hs >= 0) nxt[g.hs] = (g.hxy >= 0) ? x[g.hxy + (k + 1) * sxy] : 0.0;
-      __syncthreads();
-      if (g.valid) {
-        const long c = g.gi + (long)nx * g.gj + k * sxy;
-        const double wU_c = face_up<double, UNI>(op, c);
-        const double bc = b[c];
-        double rc;
-        if (op.dinv[c] == 0.0) {
-          rc = bc - q_c;
-        } else {
-          const double diag = UNI ? op.diagc : op.diag[c];
-          rc = bc - (diag * q_c - nb_sum<double, UNI>(op, cur, lx, ly, c, g.gi, g.gj, q_up, q_dn, wU_c, wD));
-        }
-        r32[c] = (float)rc;
-        arr = fma(rc, rc, arr);
-        abb = fma(bc, bc, abb);
-        rmax = fmax(rmax, fabs(rc));
-        wD = wU_c;
+      if (st->iter >= st->max_iter) {
+        st->done = 1;
+        st->status = 3;  // PF_E_NOCONV
+        return;
       }
-      __syncthreads();
-      double* tmp = cur;
-      cur = nxt;
-      nxt = tmp;
-      q_dn = q_c;
-      q_c = q_up;
     }
-    __syncthreads();
+    if (rr == 0.0 || rv == 0.0 || !isfinite(rr) || !isfinite(rv) || !isfinite(rr / rv)) {
+      st->done = 1;
+      st->status = 4;
+      return;
+    }
+    st->rho = rr;         // step 4 of the next iteration
+    st->alpha = rr / rv;  // step 12 of the next iteration
   }
-  double vals[3] = {arr, abb, rmax};
-  block_partials<3>(vals, 4u, part);
-  if (arrive_last(&st->ticket)) {
+};
+
+// ------------------------------------------------------------------ FP64 residual b - A x
+template <bool UNI>
+struct OpRes {
+  using T = double;
+  static constexpr int NH = SlotsRes<UNI>::NH, NC = SlotsRes<UNI>::NC, D = 2;
+  static constexpr bool CHECK_DONE = false;
+  enum { X = 0, DI = 1, WE = 2, WN = 3 };
+  enum { B = 0, DG = 1, WU = 2 };
+  struct Args {
+    double* part;
+    BicgState* st;
+    double wc, diagc;
+    int init;
+    double *r, *rt, *p, *v, *t;
+    float* r32;
+  };
+  struct Sc {
+    int unused;
+  };
+  struct Ctr {
+    double xc, di, b, diag, wU, wEc, wEw, wNc, wNs;
+  };
+  struct Accs {
+    double rr = 0.0, bb = 0.0, rmax = 0.0;
+  };
+  __device__ static Sc scalars(const Args&) { return Sc{0}; }
+  __device__ static double q_of(const Sc&, const double* const* H, int o, Ctr* c) {
+    const double xv = H[X][o];
+    if (c) {
+      c->xc = xv;
+      c->di = H[DI][o];
+    }
+    return xv;
+  }
+  __device__ static void centre(const Args& a, const double* const* H, const double* const* C, int o, int co,
+                                bool west, bool south, Ctr& c) {
+    c.b = C[B][co];
+    if (UNI) {
+      c.diag = a.diagc;
+      c.wU = c.wEc = c.wEw = c.wNc = c.wNs = a.wc;
+    } else {
+      c.diag = C[DG][co];
+      c.wU = C[WU][co];
+      c.wEc = H[WE][o];
+      c.wEw = west ? H[WE][o - 1] : c.wEc;
+      c.wNc = H[WN][o];
+      c.wNs = south ? H[WN][o - HBX] : c.wNc;
+    }
+  }
+  __device__ static double up_face(const Args& a, const Ctr& c) { return UNI ? a.wc : c.wU; }
+  __device__ static void output(const Sc&, const Args& a, const double* Q, int lx, int ly, long cidx, const Ctr& c,
+                                double q_dn, double q_up, double wD, Accs& acc) {
+    double rc;
+    if (c.di == 0.0) {
+      rc = c.b - c.xc;
+    } else {
+      const double qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
+      double nb;
+      if (UNI) {
+        nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
+      } else {
+        nb = c.wEc * qE;
+        nb = fma(c.wEw, qW, nb);
+        nb = fma(c.wNc, qN, nb);
+        nb = fma(c.wNs, qS, nb);
+        nb = fma(c.wU, q_up, nb);
+        nb = fma(wD, q_dn, nb);
+      }
+      rc = c.b - (c.diag * c.xc - nb);
+    }
+    if (a.init) {
+      a.r[cidx] = rc;
+      a.rt[cidx] = rc;
+      a.p[cidx] = 0.0;
+      a.v[cidx] = 0.0;
+      a.t[cidx] = 0.0;
+    } else {
+      a.r32[cidx] = (float)rc;
+    }
+    acc.rr = fma(rc, rc, acc.rr);
+    acc.bb = fma(c.b, c.b, acc.bb);
+    acc.rmax = fmax(acc.rmax, fabs(rc));
+  }
+  __device__ static void finish(const Args& a, const Accs& acc, double* scratch) {
+    double vals[3] = {acc.rr, acc.bb, acc.rmax};
+    block_partials<3>(vals, 4u, a.part, scratch);
+    if (!arrive_last(&a.st->ticket)) return;
     double tot[3];
-    total_partials<3>(part, 4u, tot);
-    if (threadIdx.x == 0) {
-      st->rnorm2 = tot[0];
-      st->rinf = tot[2];
-      double bb = tot[1] + st->bnorm2;  // bnorm2 preset to b.b over the Dirichlet planes
-      if (bb == 0.0) bb = 1.0;
-      st->bnorm2 = bb;
-      st->tol2 = st->tol * st->tol * bb;
-      st->done = (st->norm == 0 ? (tot[0] <= st->tol2) : (tot[2] < st->tol)) ? 1 : 0;
-      st->ticket = 0;
+    total_partials<3>(a.part, 4u, tot, scratch);
+    if (threadIdx.x != 0) return;
+    BicgState* st = a.st;
+    double bb = tot[1] + st->bnorm2;  // bnorm2 was preset to b.b over the Dirichlet planes
+    if (bb == 0.0) bb = 1.0;
+    st->bnorm2 = bb;
+    st->rnorm2 = tot[0];
+    st->rinf = tot[2];
+    st->tol2 = st->tol * st->tol * bb;
+    const bool conv = st->norm == 0 ? (tot[0] <= st->tol2) : (tot[2] < st->tol);
+    if (a.init) {
+      st->rho = tot[0];  // r~ = r0
+      st->alpha = st->omega = st->beta = 0.0;
+      st->sexit = 0;
+      st->iter = 0;
+      st->status = 0;
+    }
+    st->done = conv ? 1 : 0;
+    st->ticket = 0;
+  }
+};
+
+// ------------------------------------------------------------------ elementwise kernels
+// Nodes are visited row by row: row r = j + ny*k holds i = 0..nx-1 at padded index i + px*r.
+#define PF_ROWS(g)                                                           \
+  for (long row = blockIdx.x; row < (long)(g).ny * (g).nz; row += gridDim.x) \
+    for (int i = threadIdx.x; i < (g).nx; i += blockDim.x)
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_init_zero(const T* __restrict__ b, Geom g, T* __restrict__ r,
+                                                        T* __restrict__ rt, T* __restrict__ p, T* __restrict__ v,
+                                                        T* __restrict__ t, double* part, BicgState* st) {
+  __shared__ double scratch[NTHREADS * 2];
+  Acc<T> abb;
+  T bmax = T(0);
+  for (long row = blockIdx.x; row < (long)g.ny * g.nz; row += gridDim.x) {
+    const long k = row / g.ny;
+    if (k == 0 || k == g.nz - 1) continue;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const long c = i + (long)g.px * row;
+      const T bc = b[c];
+      r[c] = bc;
+      rt[c] = bc;
+      p[c] = T(0);
+      v[c] = T(0);
+      t[c] = T(0);
+      abb.prod(bc, bc);
+      bmax = fmax(bmax, tabs(bc));
     }
   }
+  double vals[2] = {abb.value(), (double)bmax};
+  block_partials<2>(vals, 2u, part, scratch);
+  if (!arrive_last(&st->ticket)) return;
+  double tot[2];
+  total_partials<2>(part, 2u, tot, scratch);
+  if (threadIdx.x != 0) return;
+  double bb = tot[0] + st->bnorm2;
+  if (bb == 0.0) bb = 1.0;
+  st->bnorm2 = bb;
+  st->rho = tot[0];
+  st->rnorm2 = tot[0];
+  st->rinf = tot[1];
+  st->tol2 = st->tol * st->tol * bb;
+  st->alpha = st->omega = st->beta = 0.0;
+  st->sexit = 0;
+  st->iter = 0;
+  st->status = 0;
+  st->done = (st->norm == 0 ? (tot[0] <= st->tol2) : (tot[1] < st->tol)) ? 1 : 0;
+  st->ticket = 0;
 }
 
-// ------------------------------------------------------------------ setup kernels (a1)
 __device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
 
-// Harmonic face coefficients (Eqs. 15-18 with zero jump) divided by h^2, stored per node for the
-// east, north and up faces; at i = nx-1 (j = ny-1) the east (north) face is the mirror face to the
-// ghost node.  dsum = sum of the six faces (the diagonal of -div(eps grad)), 1 on Dirichlet planes.
-__global__ void k_faces(const double* __restrict__ eps, int nx, int ny, int nz, double ih2, double* wE,
-                        double* wN, double* wU, double* dsum) {
-  const long N = (long)nx * ny * nz, sxy = (long)nx * ny;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / sxy);
+// Harmonic face coefficients (Eqs. 15-18 with zero jump) over h^2 for the east, north and up faces of
+// every node; at i = nx-1 (j = ny-1) the east (north) face is the mirror face to the ghost node.
+// dsum = sum of the six faces (the diagonal of -div(eps grad)), 1 on the Dirichlet planes.
+__global__ void k_faces(const double* __restrict__ eps, Geom g, double ih2, double* wE, double* wN, double* wU,
+                        double* dsum) {
+  const long sy = g.px, sz = g.plane;
+  PF_ROWS(g) {
+    const long c = i + g.px * row;
+    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
     const double e = eps[c];
-    const double fe = __dmul_rn(harm(e, eps[i < nx - 1 ? c + 1 : c - 1]), ih2);
+    const double fe = __dmul_rn(harm(e, eps[i < g.nx - 1 ? c + 1 : c - 1]), ih2);
     const double fw = __dmul_rn(harm(e, eps[i > 0 ? c - 1 : c + 1]), ih2);
-    const double fn = __dmul_rn(harm(e, eps[j < ny - 1 ? c + nx : c - nx]), ih2);
-    const double fs = __dmul_rn(harm(e, eps[j > 0 ? c - nx : c + nx]), ih2);
-    const double fu = k < nz - 1 ? __dmul_rn(harm(e, eps[c + sxy]), ih2) : 0.0;
-    const double fd = k > 0 ? __dmul_rn(harm(e, eps[c - sxy]), ih2) : 0.0;
+    const double fn = __dmul_rn(harm(e, eps[j < g.ny - 1 ? c + sy : c - sy]), ih2);
+    const double fs = __dmul_rn(harm(e, eps[j > 0 ? c - sy : c + sy]), ih2);
+    const double fu = k < g.nz - 1 ? __dmul_rn(harm(e, eps[c + sz]), ih2) : 0.0;
+    const double fd = k > 0 ? __dmul_rn(harm(e, eps[c - sz]), ih2) : 0.0;
     wE[c] = fe;
     wN[c] = fn;
     wU[c] = fu;
-    // same summation order as the assembled diagonal: east, west, north, south, up, down
+    // summation order of the assembled diagonal: east, west, north, south, up, down
     double d = __dadd_rn(fe, fw);
     d = __dadd_rn(d, fn);
     d = __dadd_rn(d, fs);
     d = __dadd_rn(d, fu);
     d = __dadd_rn(d, fd);
-    dsum[c] = (k == 0 || k == nz - 1) ? 1.0 : d;
+    dsum[c] = (k == 0 || k == g.nz - 1) ? 1.0 : d;
   }
 }
 
 // Trilinear spreading of the fixed charges (Eq. 3 on the grid): one thread, charges in order.
 __global__ void k_spread(const double* __restrict__ ch, int nq, double ox, double oy, double oz, double h, double lam,
-                         int nx, int ny, int nz, double* f, int* err) {
+                         Geom g, double* f, int* err) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double org[3] = {ox, oy, oz};
-  const int n[3] = {nx, ny, nz};
+  const int n[3] = {g.nx, g.ny, g.nz};
   for (int q = 0; q < nq; ++q) {
     int i0[3];
     double tt[3];
@@ -681,20 +839,19 @@ __global__ void k_spread(const double* __restrict__ ch, int nq, double ox, doubl
       const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
       const double w = __dmul_rn(__dmul_rn(dx ? tt[0] : __dsub_rn(1.0, tt[0]), dy ? tt[1] : __dsub_rn(1.0, tt[1])),
                                  dz ? tt[2] : __dsub_rn(1.0, tt[2]));
-      const long id = (i0[0] + dx) + (long)nx * ((i0[1] + dy) + (long)ny * (i0[2] + dz));
+      const long id = (i0[0] + dx) + (long)g.px * ((i0[1] + dy) + (long)g.ny * (i0[2] + dz));
       f[id] = __dadd_rn(f[id], __dmul_rn(amp, w));
     }
   }
 }
 
 __global__ void k_eps_diag(const double* __restrict__ dsum, const double* __restrict__ sig,
-                           const uint8_t* __restrict__ smask, int nx, int ny, int nz, double* diag, double* dinv,
-                           float* dinv32) {
-  const long N = (long)nx * ny * nz, sxy = (long)nx * ny;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
-    const long k = c / sxy;
+                           const uint8_t* __restrict__ smask, Geom g, double* diag, double* dinv, float* dinv32) {
+  PF_ROWS(g) {
+    const long c = i + g.px * row;
+    const long k = row / g.ny;
     double d = 1.0, di = 0.0;
-    if (k > 0 && k < nz - 1) {
+    if (k > 0 && k < g.nz - 1) {
       d = dsum[c];
       if (sig && (!smask || smask[c])) d = __dadd_rn(d, sig[c]);
       di = 1.0 / d;
@@ -705,12 +862,11 @@ __global__ void k_eps_diag(const double* __restrict__ dsum, const double* __rest
   }
 }
 
-__global__ void k_pf1_dinv(const uint8_t* __restrict__ solvent, int nx, int ny, int nz, double dinvc, double* dinv,
-                           float* dinv32) {
-  const long N = (long)nx * ny * nz, sxy = (long)nx * ny;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
-    const long k = c / sxy;
-    const double di = (k > 0 && k < nz - 1 && solvent[c]) ? dinvc : 0.0;
+__global__ void k_pf1_dinv(const uint8_t* __restrict__ solvent, Geom g, double dinvc, double* dinv, float* dinv32) {
+  PF_ROWS(g) {
+    const long c = i + g.px * row;
+    const long k = row / g.ny;
+    const double di = (k > 0 && k < g.nz - 1 && solvent[c]) ? dinvc : 0.0;
     dinv[c] = di;
     if (dinv32) dinv32[c] = (float)di;
   }
@@ -727,10 +883,60 @@ __global__ void k_impose(double* __restrict__ x, const double* __restrict__ b, c
     if (dinv[c] == 0.0) x[c] = b[c];
 }
 
+__global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, long n) {
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x)
+    x[c] += (double)d[c];
+}
+
+__global__ void k_pack_d(const double* __restrict__ src, double* __restrict__ dst, Geom g) {
+  PF_ROWS(g) dst[i + g.px * row] = src[i + (long)g.nx * row];
+}
+
+__global__ void k_pack_u8(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, Geom g) {
+  PF_ROWS(g) dst[i + g.px * row] = src[i + (long)g.nx * row];
+}
+
+__global__ void k_unpack(const double* __restrict__ src, double* __restrict__ dst, Geom g, int count) {
+  for (int f = 0; f < count; ++f) {
+    const double* s = src + f * g.np;
+    double* d = dst + f * g.n;
+    PF_ROWS(g) d[i + (long)g.nx * row] = s[i + g.px * row];
+  }
+}
+
+// b.b over the two Dirichlet planes (which the stencil kernels do not visit) -> st->bnorm2
+__global__ void k_plane_bb(const double* __restrict__ b, Geom g, BicgState* st) {
+  double a = 0.0;
+  const long last = g.plane * (g.nz - 1);
+  for (long r = 0; r < g.ny; ++r)
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const double u = b[i + g.px * r], w = b[last + i + g.px * r];
+      a = fma(u, u, a);
+      a = fma(w, w, a);
+    }
+  __shared__ double red[NTHREADS];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = NTHREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st->bnorm2 = red[0];
+}
+
+__global__ void k_set_state(BicgState* st, double tol, int norm, int max_iter) {
+  BicgState s = {};
+  s.tol = tol;
+  s.norm = norm;
+  s.max_iter = max_iter;
+  *st = s;
+}
+
 // ------------------------------------------------------------------ Eq. (1) pointwise step
-// Void fraction Gamma = e^u from f(u) = e^u + sum_i exp(la_i + p_i u) - 1 = 0 (bracketed Newton in u),
-// S = u - ln Gamma^B, C_i = cB_i exp(-z_i phi + p_i S), rho = sum z_i C_i, kappa = lambda sum z_i^2 C_i.
-__device__ __forceinline__ bool fermi_root(const SpeciesParams& sp, double phi, double& u_out, double (&la)[MAXSP]) {
+// Void fraction Gamma = e^u from f(u) = e^u + sum_i exp(la_i + p_i u) - 1 = 0 (Newton in u inside a
+// bracket), S = u - ln Gamma^B, C_i = cB_i exp(-z_i phi + p_i S), rho = sum z_i C_i, kappa = lambda sum z_i^2 C_i.
+__device__ __forceinline__ bool fermi_root(const SpeciesParams& sp, double phi, double& u_out) {
+  double la[MAXSP];
   int nterm = 0;
   for (int i = 0; i < sp.ns; ++i) {
     la[i] = sp.lvc[i] - sp.z[i] * phi - sp.p[i] * sp.lgB;
@@ -740,9 +946,8 @@ __device__ __forceinline__ bool fermi_root(const SpeciesParams& sp, double phi, 
   double hi = 0.0, lo = -lnn;
   for (int i = 0; i < sp.ns; ++i) {
     if (!(sp.lvc[i] > -INFINITY)) continue;
-    const double a = -la[i] / sp.p[i], b = (-la[i] - lnn) / sp.p[i];
-    hi = fmin(hi, a);
-    lo = fmin(lo, b);
+    hi = fmin(hi, -la[i] / sp.p[i]);
+    lo = fmin(lo, (-la[i] - lnn) / sp.p[i]);
   }
   double u = sp.lgB;
   if (!(u < hi && u > lo)) u = 0.5 * (lo + hi);
@@ -773,54 +978,55 @@ __device__ __forceinline__ bool fermi_root(const SpeciesParams& sp, double phi, 
 }
 
 __global__ void k_fermi(const double* __restrict__ phi0, const uint8_t* __restrict__ solvent,
-                        const double* __restrict__ ffix, SpeciesParams sp, int nx, int ny, int nz, double* b1,
-                        double* sig, double* c2, double* C, double* S, double* G, int* err) {
-  const long N = (long)nx * ny * nz, sxy = (long)nx * ny;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
-    const long k = c / sxy;
+                        const double* __restrict__ ffix, SpeciesParams sp, Geom g, double* b1, double* sig, double* c2,
+                        double* C, double* S, double* G, int* err) {
+  PF_ROWS(g) {
+    const long c = i + g.px * row;
+    const long k = row / g.ny;
     const double ph = phi0[c];
     double rho = 0.0, kap = 0.0, Sv = 0.0, Gv = 0.0;
-    double Ci[MAXSP];
-    for (int i = 0; i < MAXSP; ++i) Ci[i] = 0.0;
-    if (solvent[c]) {
-      double la[MAXSP], u = 0.0;
-      if (!fermi_root(sp, ph, u, la)) {
-        atomicExch(err, 5);
-      } else {
-        Sv = u - sp.lgB;
-        Gv = exp(u);
-        for (int i = 0; i < sp.ns; ++i) {
-          Ci[i] = (sp.lvc[i] > -INFINITY) ? exp(sp.lcB[i] - sp.z[i] * ph + sp.p[i] * Sv) : 0.0;
-          rho += sp.z[i] * Ci[i];
-          kap += sp.lam * sp.z[i] * sp.z[i] * Ci[i];
-        }
-      }
+    const bool sol = solvent[c] != 0;
+    double u = 0.0;
+    bool ok = true;
+    if (sol) {
+      ok = fermi_root(sp, ph, u);
+      if (!ok) atomicExch(err, 5);
     }
-    if (b1) b1[c] = (solvent[c] && k > 0 && k < nz - 1) ? -sp.lam * rho : 0.0;
+    if (sol && ok) {
+      Sv = u - sp.lgB;
+      Gv = exp(u);
+    }
+    for (int s = 0; s < sp.ns; ++s) {
+      const double Ci = (sol && ok && sp.lvc[s] > -INFINITY) ? exp(sp.lcB[s] - sp.z[s] * ph + sp.p[s] * Sv) : 0.0;
+      rho += sp.z[s] * Ci;
+      kap += sp.lam * sp.z[s] * sp.z[s] * Ci;
+      if (C) C[s * g.np + c] = Ci;
+    }
+    if (b1) b1[c] = (sol && k > 0 && k < g.nz - 1) ? -sp.lam * rho : 0.0;
     if (sig) sig[c] = kap;
     if (c2) c2[c] = fma(kap, ph, ffix[c]);
-    if (C) for (int i = 0; i < sp.ns; ++i) C[i * N + c] = Ci[i];
     if (S) S[c] = Sv;
     if (G) G[c] = Gv;
   }
 }
 
 __global__ void k_pf2_rhs(const double* __restrict__ psi, const uint8_t* __restrict__ solvent,
-                          const double* __restrict__ c2, double eps_s, double lo, double hi, int nx, int ny, int nz,
-                          double* b2) {
-  const long N = (long)nx * ny * nz, sxy = (long)nx * ny;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
-    const long k = c / sxy;
+                          const double* __restrict__ c2, double eps_s, double lo, double hi, Geom g, double* b2) {
+  PF_ROWS(g) {
+    const long c = i + g.px * row;
+    const long k = row / g.ny;
     double v;
     if (k == 0) v = lo;
-    else if (k == nz - 1) v = hi;
+    else if (k == g.nz - 1) v = hi;
     else v = (solvent[c] ? -eps_s * psi[c] : 0.0) + c2[c];
     b2[c] = v;
   }
 }
 
-__global__ void k_relax(double* __restrict__ phi0, const double* __restrict__ phi, double omega, long n,
-                        double* part, unsigned int* ticket, double* delta) {
+__global__ void __launch_bounds__(NTHREADS) k_relax(double* __restrict__ phi0, const double* __restrict__ phi,
+                                                    double omega, long n, double* part, unsigned int* ticket,
+                                                    double* delta) {
+  __shared__ double scratch[NTHREADS];
   double m = 0.0;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
     const double o = phi0[c];
@@ -829,38 +1035,14 @@ __global__ void k_relax(double* __restrict__ phi0, const double* __restrict__ ph
     phi0[c] = nw;
   }
   double vals[1] = {m};
-  block_partials<1>(vals, 1u, part);
-  if (arrive_last(ticket)) {
-    double tot[1];
-    total_partials<1>(part, 1u, tot);
-    if (threadIdx.x == 0) {
-      *delta = tot[0];
-      *ticket = 0;
-    }
+  block_partials<1>(vals, 1u, part, scratch);
+  if (!arrive_last(ticket)) return;
+  double tot[1];
+  total_partials<1>(part, 1u, tot, scratch);
+  if (threadIdx.x == 0) {
+    *delta = tot[0];
+    *ticket = 0;
   }
-}
-
-__global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, long n) {
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x)
-    x[c] += (double)d[c];
-}
-
-// b.b over the two Dirichlet planes (which the stencil kernels do not visit) -> st->bnorm2
-__global__ void k_plane_bb(const double* __restrict__ b, int nx, int ny, int nz, BicgState* st) {
-  const long plane = (long)nx * ny, N = plane * nz;
-  double a = 0.0;
-  for (long c = threadIdx.x; c < plane; c += blockDim.x) {
-    a = fma(b[c], b[c], a);
-    a = fma(b[N - plane + c], b[N - plane + c], a);
-  }
-  __shared__ double red[NTHREADS];
-  red[threadIdx.x] = a;
-  __syncthreads();
-  for (int s = NTHREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) st->bnorm2 = red[0];
 }
 
 __global__ void k_scale(const double* __restrict__ a, double s, double* __restrict__ out, long n) {
@@ -868,12 +1050,13 @@ __global__ void k_scale(const double* __restrict__ a, double s, double* __restri
     out[c] = a[c] * s;
 }
 
-__global__ void k_set_dirichlet(double* x, double lo, double hi, int nx, int ny, int nz) {
-  const long plane = (long)nx * ny, N = plane * nz;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < plane; c += (long)gridDim.x * blockDim.x) {
-    x[c] = lo;
-    x[N - plane + c] = hi;
-  }
+__global__ void k_set_dirichlet(double* x, double lo, double hi, Geom g) {
+  const long last = g.plane * (g.nz - 1);
+  for (long r = blockIdx.x; r < g.ny; r += gridDim.x)
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      x[i + g.px * r] = lo;
+      x[last + i + g.px * r] = hi;
+    }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -888,6 +1071,8 @@ static int nsm() {
   return g_nsm;
 }
 
+int max_partial_blocks() { return nsm() * 16 > 2048 ? nsm() * 16 : 2048; }
+
 static int ew_blocks(long n) {
   long b = (n + 255) / 256;
   const long cap = (long)nsm() * 8;
@@ -896,31 +1081,127 @@ static int ew_blocks(long n) {
   return (int)b;
 }
 
-cudaError_t launch_faces(const double* eps, int nx, int ny, int nz, double h, double* wE, double* wN, double* wU,
-                         double* dsum, cudaStream_t s) {
-  const long N = (long)nx * ny * nz;
-  k_faces<<<ew_blocks(N), 256, 0, s>>>(eps, nx, ny, nz, 1.0 / (h * h), wE, wN, wU, dsum);
+static int row_blocks(const Geom& g) {
+  long b = (long)g.ny * g.nz;
+  const long cap = (long)nsm() * 16;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+bool encode_map(CUtensorMap* m, const void* base, const Geom& g, int elem_bytes, bool halo) {
+  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return false;
+    fn = reinterpret_cast<EncodeFn>(p);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.px * elem_bytes, (cuuint64_t)g.plane * elem_bytes};
+  const cuuint32_t box[3] = {(cuuint32_t)(halo ? HBX : TX), (cuuint32_t)(halo ? HBY : TY), 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// Grid size of a stencil kernel: every SM, as many blocks as fit (shared memory, registers), never
+// more blocks than tiles.  Raises the kernel's dynamic shared-memory limit on first use.
+template <class Op>
+static int stencil_blocks(int ntiles) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    const int bytes = smem_bytes<Op>();
+    cudaFuncSetAttribute(k_stencil<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_stencil<Op>, NTHREADS, bytes);
+    per_sm = o > 0 ? o : 1;
+  }
+  const int b = nsm() * per_sm;
+  return b < ntiles ? b : ntiles;
+}
+
+template <class Op>
+static cudaError_t launch_stencil(const Maps<Op::NH, Op::NC>& m, const typename Op::Args& a, const Geom& g,
+                                  const Launch& L) {
+  static_assert(scratch_fits<Op>(), "reduction scratch must fit in the stage ring");
+  const int blocks = stencil_blocks<Op>(L.ntiles);
+  k_stencil<Op><<<blocks, NTHREADS, smem_bytes<Op>(), L.stream>>>(m, a, g, L.ntiles, L.wait_limit);
+  return cudaGetLastError();
+}
+
+template <typename T, bool UNI>
+cudaError_t launch_phase_b(const Maps<SlotsB<UNI>::NH, SlotsB<UNI>::NC>& m, const Geom& g, T wc, T* t, double* part,
+                           BicgState* st, const Launch& L) {
+  typename OpB<T, UNI>::Args a{part, st, t, wc};
+  return launch_stencil<OpB<T, UNI>>(m, a, g, L);
+}
+
+template <typename T, bool UNI>
+cudaError_t launch_phase_ca(const Maps<SlotsCA<UNI>::NH, SlotsCA<UNI>::NC>& m, const Geom& g, T wc, T* x, T* r_out,
+                            T* p_out, T* v_out, double* part, BicgState* st, int prime, const Launch& L) {
+  typename OpCA<T, UNI>::Args a{part, st, x, r_out, p_out, v_out, wc, prime};
+  return launch_stencil<OpCA<T, UNI>>(m, a, g, L);
+}
+
+template <bool UNI>
+cudaError_t launch_residual(const Maps<SlotsRes<UNI>::NH, SlotsRes<UNI>::NC>& m, const Geom& g, double wc,
+                            double diagc, int init, double* r, double* rt, double* p, double* v, double* t, float* r32,
+                            double* part, BicgState* st, const Launch& L) {
+  typename OpRes<UNI>::Args a{part, st, wc, diagc, init, r, rt, p, v, t, r32};
+  return launch_stencil<OpRes<UNI>>(m, a, g, L);
+}
+
+template <typename T>
+cudaError_t launch_init_zero(const T* b, const Geom& g, T* r, T* rt, T* p, T* v, T* t, double* part, BicgState* st,
+                             cudaStream_t s) {
+  k_init_zero<T><<<row_blocks(g), NTHREADS, 0, s>>>(b, g, r, rt, p, v, t, part, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_f32(double* x, const float* d, long n, cudaStream_t s) {
+  k_add_f32<<<ew_blocks(n), 256, 0, s>>>(x, d, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, cudaStream_t s) {
+  k_set_state<<<1, 1, 0, s>>>(st, tol, norm, max_iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_bb(const double* b, const Geom& g, BicgState* st, cudaStream_t s) {
+  k_plane_bb<<<1, NTHREADS, 0, s>>>(b, g, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_faces(const double* eps, const Geom& g, double h, double* wE, double* wN, double* wU, double* dsum,
+                         cudaStream_t s) {
+  k_faces<<<row_blocks(g), 128, 0, s>>>(eps, g, 1.0 / (h * h), wE, wN, wU, dsum);
   return cudaGetLastError();
 }
 
 cudaError_t launch_spread(const double* charges, int nq, double ox, double oy, double oz, double h, double lam,
-                          int nx, int ny, int nz, double* f, int* err, cudaStream_t s) {
+                          const Geom& g, double* f, int* err, cudaStream_t s) {
   if (nq <= 0) return cudaSuccess;
-  k_spread<<<1, 32, 0, s>>>(charges, nq, ox, oy, oz, h, lam, nx, ny, nz, f, err);
+  k_spread<<<1, 32, 0, s>>>(charges, nq, ox, oy, oz, h, lam, g, f, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_eps_diag(const double* dsum, const double* sig, const uint8_t* smask, int nx, int ny, int nz,
-                            double* diag, double* dinv, float* dinv32, cudaStream_t s) {
-  const long N = (long)nx * ny * nz;
-  k_eps_diag<<<ew_blocks(N), 256, 0, s>>>(dsum, sig, smask, nx, ny, nz, diag, dinv, dinv32);
+cudaError_t launch_eps_diag(const double* dsum, const double* sig, const uint8_t* smask, const Geom& g, double* diag,
+                            double* dinv, float* dinv32, cudaStream_t s) {
+  k_eps_diag<<<row_blocks(g), 128, 0, s>>>(dsum, sig, smask, g, diag, dinv, dinv32);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pf1_dinv(const uint8_t* solvent, int nx, int ny, int nz, double dinvc, double* dinv, float* dinv32,
+cudaError_t launch_pf1_dinv(const uint8_t* solvent, const Geom& g, double dinvc, double* dinv, float* dinv32,
                             cudaStream_t s) {
-  const long N = (long)nx * ny * nz;
-  k_pf1_dinv<<<ew_blocks(N), 256, 0, s>>>(solvent, nx, ny, nz, dinvc, dinv, dinv32);
+  k_pf1_dinv<<<row_blocks(g), 128, 0, s>>>(solvent, g, dinvc, dinv, dinv32);
   return cudaGetLastError();
 }
 
@@ -934,53 +1215,29 @@ cudaError_t launch_impose(double* x, const double* b, const double* dinv, long n
   return cudaGetLastError();
 }
 
-template <typename T, bool UNI>
-cudaError_t launch_init(const OpView<T>& op, const T* x, bool x_zero, const T* b, T* r, T* rt, T* p, T* v, T* t,
-                        double* part, BicgState* st, const Launch& L) {
-  k_init<T, UNI><<<L.blocks, NTHREADS, 0, L.stream>>>(op, x, x_zero ? 1 : 0, b, r, rt, p, v, t, part, st, L.ntiles);
+cudaError_t launch_pack(const void* src, void* dst, const Geom& g, int type, cudaStream_t s) {
+  if (type == 0)
+    k_pack_d<<<row_blocks(g), 128, 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst), g);
+  else
+    k_pack_u8<<<row_blocks(g), 128, 0, s>>>(static_cast<const uint8_t*>(src), static_cast<uint8_t*>(dst), g);
   return cudaGetLastError();
 }
 
-template <typename T, bool UNI>
-cudaError_t launch_phase_b(const OpView<T>& op, const T* r, const T* v, const T* rt, T* t, double* part,
-                           BicgState* st, const Launch& L) {
-  k_phase_b<T, UNI><<<L.blocks, NTHREADS, 0, L.stream>>>(op, r, v, rt, t, part, st, L.ntiles);
-  return cudaGetLastError();
-}
-
-template <typename T, bool UNI>
-cudaError_t launch_phase_ca(const OpView<T>& op, const T* r, const T* v, const T* p, const T* t, const T* rt, T* x,
-                            T* r_out, T* p_out, T* v_out, double* part, BicgState* st, int prime, const Launch& L) {
-  k_phase_ca<T, UNI><<<L.blocks, NTHREADS, 0, L.stream>>>(op, r, v, p, t, rt, x, r_out, p_out, v_out, part, st, prime,
-                                                          L.ntiles);
-  return cudaGetLastError();
-}
-
-template <bool UNI>
-cudaError_t launch_refine(const OpView<double>& op, double* x, const float* d, const double* b, float* r32,
-                          double* part, BicgState* st, const Launch& L) {
-  if (d) {
-    // x += d is an elementwise pass before the stencil: updating x inside the stencil kernel would race
-    // with neighbouring tiles that read x as their halo
-    const long N = (long)op.nx * op.ny * op.nz;
-    k_add_f32<<<ew_blocks(N), 256, 0, L.stream>>>(x, d, N);
-  }
-  k_residual<UNI><<<L.blocks, NTHREADS, 0, L.stream>>>(op, x, b, r32, part, st, L.ntiles);
+cudaError_t launch_unpack(const double* src, double* dst, const Geom& g, int count, cudaStream_t s) {
+  k_unpack<<<row_blocks(g), 128, 0, s>>>(src, dst, g, count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fermi(const double* phi0, const uint8_t* solvent, const double* ffix, const SpeciesParams& sp,
-                         int nx, int ny, int nz, double* b1, double* sig, double* c2, double* C, double* S, double* G,
-                         int* err, cudaStream_t s) {
-  const long N = (long)nx * ny * nz;
-  k_fermi<<<ew_blocks(N), 256, 0, s>>>(phi0, solvent, ffix, sp, nx, ny, nz, b1, sig, c2, C, S, G, err);
+                         const Geom& g, double* b1, double* sig, double* c2, double* C, double* S, double* G, int* err,
+                         cudaStream_t s) {
+  k_fermi<<<row_blocks(g), 128, 0, s>>>(phi0, solvent, ffix, sp, g, b1, sig, c2, C, S, G, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pf2_rhs(const double* psi, const uint8_t* solvent, const double* c2, double eps_s, double lo,
-                           double hi, int nx, int ny, int nz, double* b2, cudaStream_t s) {
-  const long N = (long)nx * ny * nz;
-  k_pf2_rhs<<<ew_blocks(N), 256, 0, s>>>(psi, solvent, c2, eps_s, lo, hi, nx, ny, nz, b2);
+                           double hi, const Geom& g, double* b2, cudaStream_t s) {
+  k_pf2_rhs<<<row_blocks(g), 128, 0, s>>>(psi, solvent, c2, eps_s, lo, hi, g, b2);
   return cudaGetLastError();
 }
 
@@ -995,68 +1252,30 @@ cudaError_t launch_scale(const double* a, double sc, double* out, long n, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_dirichlet(double* x, double lo, double hi, int nx, int ny, int nz, cudaStream_t s) {
-  k_set_dirichlet<<<ew_blocks((long)nx * ny), 256, 0, s>>>(x, lo, hi, nx, ny, nz);
+cudaError_t launch_set_dirichlet(double* x, double lo, double hi, const Geom& g, cudaStream_t s) {
+  k_set_dirichlet<<<row_blocks(g), 128, 0, s>>>(x, lo, hi, g);
   return cudaGetLastError();
 }
 
 // explicit instantiations
-#define PF_INST(T, U)                                                                                              \
-  template cudaError_t launch_init<T, U>(const OpView<T>&, const T*, bool, const T*, T*, T*, T*, T*, T*, double*, \
-                                         BicgState*, const Launch&);                                               \
-  template cudaError_t launch_phase_b<T, U>(const OpView<T>&, const T*, const T*, const T*, T*, double*,          \
+#define PF_INST(T, U)                                                                                               \
+  template cudaError_t launch_phase_b<T, U>(const Maps<SlotsB<U>::NH, SlotsB<U>::NC>&, const Geom&, T, T*, double*, \
                                             BicgState*, const Launch&);                                            \
-  template cudaError_t launch_phase_ca<T, U>(const OpView<T>&, const T*, const T*, const T*, const T*, const T*,  \
-                                             T*, T*, T*, T*, double*, BicgState*, int, const Launch&);
+  template cudaError_t launch_phase_ca<T, U>(const Maps<SlotsCA<U>::NH, SlotsCA<U>::NC>&, const Geom&, T, T*, T*,   \
+                                             T*, T*, double*, BicgState*, int, const Launch&);
 PF_INST(double, false)
 PF_INST(double, true)
 PF_INST(float, false)
 PF_INST(float, true)
-template cudaError_t launch_refine<false>(const OpView<double>&, double*, const float*, const double*, float*,
-                                          double*, BicgState*, const Launch&);
-template cudaError_t launch_refine<true>(const OpView<double>&, double*, const float*, const double*, float*,
-                                         double*, BicgState*, const Launch&);
-
-__global__ void k_set_state(BicgState* st, double tol, int norm, int max_iter) {
-  BicgState s = {};
-  s.tol = tol;
-  s.norm = norm;
-  s.max_iter = max_iter;
-  *st = s;
-}
-
-cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, cudaStream_t s) {
-  k_set_state<<<1, 1, 0, s>>>(st, tol, norm, max_iter);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_plane_bb(const double* b, int nx, int ny, int nz, BicgState* st, cudaStream_t s) {
-  k_plane_bb<<<1, NTHREADS, 0, s>>>(b, nx, ny, nz, st);
-  return cudaGetLastError();
-}
-
-// Persistent grid size of the stencil kernels: all SMs, as many blocks per SM as every stencil kernel
-// can keep resident, never more blocks than tiles.
-Launch make_launch(int nx, int ny, int nz, cudaStream_t s) {
-  static int per_sm = 0;
-  if (!per_sm) {
-    int occ = 64, o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_phase_ca<double, false>, NTHREADS, 0); occ = o < occ ? o : occ;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_phase_b<double, false>, NTHREADS, 0); occ = o < occ ? o : occ;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_phase_ca<float, false>, NTHREADS, 0); occ = o < occ ? o : occ;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_phase_b<float, false>, NTHREADS, 0); occ = o < occ ? o : occ;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_init<double, false>, NTHREADS, 0); occ = o < occ ? o : occ;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_residual<false>, NTHREADS, 0); occ = o < occ ? o : occ;
-    per_sm = occ > 0 ? occ : 1;
-  }
-  Launch L;
-  L.ntiles = tiles_for(nx, ny, nz);
-  L.blocks = nsm() * per_sm;
-  if (L.blocks > L.ntiles) L.blocks = L.ntiles;
-  L.stream = s;
-  return L;
-}
-
-int max_partial_blocks() { return nsm() * 16 > 2048 ? nsm() * 16 : 2048; }
+template cudaError_t launch_residual<false>(const Maps<SlotsRes<false>::NH, SlotsRes<false>::NC>&, const Geom&, double,
+                                            double, int, double*, double*, double*, double*, double*, float*, double*,
+                                            BicgState*, const Launch&);
+template cudaError_t launch_residual<true>(const Maps<SlotsRes<true>::NH, SlotsRes<true>::NC>&, const Geom&, double,
+                                           double, int, double*, double*, double*, double*, double*, float*, double*,
+                                           BicgState*, const Launch&);
+template cudaError_t launch_init_zero<float>(const float*, const Geom&, float*, float*, float*, float*, float*, double*,
+                                             BicgState*, cudaStream_t);
+template cudaError_t launch_init_zero<double>(const double*, const Geom&, double*, double*, double*, double*, double*,
+                                              double*, BicgState*, cudaStream_t);
 
 }  // namespace pf
