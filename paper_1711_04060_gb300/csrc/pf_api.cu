@@ -83,7 +83,7 @@ struct pf_grid {
   float *rt32 = nullptr, *t32 = nullptr, *d32 = nullptr, *b32 = nullptr;
   double *xb = nullptr, *bb = nullptr, *stage = nullptr;
   double *phi0 = nullptr, *phi = nullptr, *psi = nullptr, *b1 = nullptr, *c2 = nullptr, *b2 = nullptr;
-  double *Cbuf = nullptr, *Sbuf = nullptr, *Gbuf = nullptr;
+  double *Cbuf = nullptr, *Sbuf = nullptr, *Gbuf = nullptr, *ulast = nullptr;
   double* part = nullptr;
   double* dch = nullptr;     // fixed charges (x, y, z, q) on the device
   int nq = 0;
@@ -146,7 +146,7 @@ pf_status allocate(pf_grid* g) {
   double** d64[] = {&g->eps, &g->wE, &g->wN, &g->wU, &g->dsum, &g->ffix, &g->diagP, &g->dinvP, &g->diag2,
                     &g->dinv2, &g->sig, &g->dinv1, &g->r64[0], &g->r64[1], &g->p64[0], &g->p64[1], &g->v64[0],
                     &g->v64[1], &g->rt64, &g->t64, &g->xb, &g->bb, &g->stage, &g->phi0, &g->phi, &g->psi, &g->b1,
-                    &g->c2, &g->b2, &g->Sbuf, &g->Gbuf};
+                    &g->c2, &g->b2, &g->Sbuf, &g->Gbuf, &g->ulast};
   for (double** p : d64) PF_TRY(dalloc(g, p, NP));
   PF_TRY(dalloc(g, &g->Cbuf, (size_t)NP * pf::MAXSP));
   float** d32[] = {&g->wE32, &g->wN32, &g->wU32, &g->dinvP32, &g->dinv2_32, &g->dinv1_32, &g->r32[0], &g->r32[1],
@@ -545,7 +545,7 @@ pf_status unpack_out(pf_grid* g, const double* src, int count, double* dst, int 
 // Device bytes that pf_create_grid allocates for a grid (used for the serving budget).
 size_t pf_internal_grid_bytes(int nx, int ny, int nz) {
   const pf::Geom g = pf::make_geom(nx, ny, nz);
-  const size_t per_node = 31 * sizeof(double) + pf::MAXSP * sizeof(double) + 16 * sizeof(float) + 1;
+  const size_t per_node = 32 * sizeof(double) + pf::MAXSP * sizeof(double) + 16 * sizeof(float) + 1;
   return (size_t)g.np * per_node + (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double) + 4096;
 }
 
@@ -668,6 +668,9 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
     sp.p[i] = v[i] / v0;
     sp.lvc[i] = cB > 0 ? log(v[i] * cB) : -INFINITY;
     sp.lcB[i] = cB > 0 ? log(cB) : -INFINITY;
+    sp.inv_v[i] = 1.0 / v[i];
+    sp.inv_p[i] = 1.0 / sp.p[i];
+    if (cB > 0) sp.lnn += 1.0;
     gB -= v[i] * cB;
     q += s.z * cB;
     qs += fabs((double)s.z) * cB;
@@ -675,6 +678,7 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
   if (!(gB > 0)) return fail(PF_E_INVAL, "bulk void fraction Gamma^B <= 0");
   if (fabs(q) > 1e-12 * (qs > 0 ? qs : 1.0)) return fail(PF_E_INVAL, "bath is not electroneutral");
   sp.lgB = log(gB);
+  sp.lnn = log(1.0 + sp.lnn);  // ln(n + 1) over the species present
   g->T = c->T_K;
   g->Tv = KB * g->T / QE;
   g->lam = QE * QE / (EPS0 * KB * g->T * 1e-10);
@@ -778,7 +782,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
     // Eq. (1) at Phi_0 -> b_PF1 = -lambda rho, kappa, PF2 right-hand-side part (Table 4 steps 5-6)
     PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
     PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, g->b1, g->sig, g->c2,
-                                                 nullptr, nullptr, nullptr, g->err, s));
+                                                 nullptr, nullptr, nullptr, g->ulast, outer > 1, g->err, s));
     PF_TRY(update_pf2(g));
     PF_TRY(solve_dev(g, PF_OP_PF1, g->b1, g->psi, o.lin, &rep));  // Eq. (12)
     res->lin_iters_total += rep.iterations;
@@ -805,7 +809,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   // outputs at the final potential
   PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
   PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, nullptr, nullptr, nullptr,
-                                               g->Cbuf, g->Sbuf, g->Gbuf, g->err, s));
+                                               g->Cbuf, g->Sbuf, g->Gbuf, g->ulast, res->outer_iters > 0, g->err, s));
   if (res->phi_V) {
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, NP, s));
     PF_TRY(unpack_out(g, g->phi, 1, res->phi_V, res->mem));

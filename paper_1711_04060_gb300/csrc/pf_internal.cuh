@@ -81,7 +81,10 @@ struct SpeciesParams {
   double lvc[MAXSP];    // ln(v_i cB_i) (or -inf when cB_i = 0)
   double p[MAXSP];      // v_i / v0
   double lcB[MAXSP];    // ln cB_i
+  double inv_v[MAXSP];  // 1 / v_i, v_i = 4 pi a_i^3 / 3
+  double inv_p[MAXSP];  // 1 / p_i
   double lgB;           // ln Gamma^B
+  double lnn;           // ln(1 + number of species with cB_i > 0)
   double lam;           // lambda
 };
 
@@ -129,9 +132,10 @@ cudaError_t launch_phase_ca(const Maps<SlotsCA<UNI>::NH, SlotsCA<UNI>::NC>& m, c
 cudaError_t launch_add_f32(double* x, const float* d, long n, cudaStream_t s);
 
 // ---- nonlinear step (Eq. 1, Eq. 11-13, Table 4) ----
+// ulast: per-node ln Gamma of the previous call, read when warm != 0 (Newton start) and rewritten
 cudaError_t launch_fermi(const double* phi0, const uint8_t* solvent, const double* ffix, const SpeciesParams& sp,
-                         const Geom& g, double* b1, double* sig, double* c2, double* C, double* S, double* G, int* err,
-                         cudaStream_t s);
+                         const Geom& g, double* b1, double* sig, double* c2, double* C, double* S, double* G,
+                         double* ulast, int warm, int* err, cudaStream_t s);
 cudaError_t launch_pf2_rhs(const double* psi, const uint8_t* solvent, const double* c2, double eps_s, double lo,
                            double hi, const Geom& g, double* b2, cudaStream_t s);
 cudaError_t launch_relax(double* phi0, const double* phi, double omega, long n, double* part, unsigned int* ticket,

@@ -93,6 +93,29 @@ struct Acc<float> {
 template <typename T>
 __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
 
+// Inner-product partials of a thread: the products of one tile column (at most ZC + 1 terms) are
+// summed in the working precision, then added to an FP64 total once per tile, so the global inner
+// products are FP64 sums of short working-precision partial sums.
+template <typename T, int NV>
+struct Partials {
+  T t[NV];
+  double d[NV];
+  __device__ __forceinline__ Partials() {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      t[j] = T(0);
+      d[j] = 0.0;
+    }
+  }
+  __device__ __forceinline__ void flush() {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      d[j] += (double)t[j];
+      t[j] = T(0);
+    }
+  }
+};
+
 // Block reduction of NV values (bit j of maxmask: value j is a maximum, else a sum) into
 // part[blockIdx.x * NPART + j]; scratch holds at least NTHREADS / 32 * NV doubles.
 template <int NV>
@@ -232,9 +255,11 @@ __device__ __forceinline__ TileGeo tile_geo(const Tile& tl, int nx, int ny) {
   g.cbo = box_off(g.gi, g.gj, tl, nx, ny);
   g.hbo = -1;
   g.hs = -1;
-  if (threadIdx.x < NHALO) {
+  // the halo slots go to the last NHALO threads, away from the producer thread in warp 0
+  const int hslot = (int)threadIdx.x - (NTHREADS - NHALO);
+  if (hslot >= 0) {
     int hx, hy;
-    halo_pos(threadIdx.x, hx, hy);
+    halo_pos(hslot, hx, hy);
     g.hs = cs(hx, hy);
     g.hbo = box_off(tl.x0 + hx, tl.y0 + hy, tl, nx, ny);
   }
@@ -271,7 +296,7 @@ constexpr bool scratch_fits() {
 // Op supplies: T, NH, NC, D, CHECK_DONE, Args, Sc, Ctr, Accs and scalars(), q_of(), centre(),
 // up_face(), output(), finish().
 template <class Op>
-__global__ void __launch_bounds__(NTHREADS) k_stencil(const __grid_constant__ Maps<Op::NH, Op::NC> maps,
+__global__ void __launch_bounds__(NTHREADS, Op::MINB) k_stencil(const __grid_constant__ Maps<Op::NH, Op::NC> maps,
                                                       typename Op::Args a, Geom g, int ntiles,
                                                       unsigned long long wait_limit) {
   using T = typename Op::T;
@@ -292,23 +317,25 @@ __global__ void __launch_bounds__(NTHREADS) k_stencil(const __grid_constant__ Ma
   __syncthreads();
 
   // producer (thread 0): the next (tile, plane) of this block's stream of planes
+  static_assert((D & (D - 1)) == 0, "the stage ring has a power-of-two size");
   int pt = blockIdx.x, pj = 0;
   unsigned pseq = 0;
+  Tile ptl = tile_of(pt, g.nx, g.nz);
   auto issue = [&]() {
-    const Tile tl = tile_of(pt, g.nx, g.nz);
-    const int stage = pseq % D;
+    const int stage = pseq & (D - 1);
     unsigned char* sb = smem + stage * STAGE;
     uint64_t* bar = &bars[stage];
     mbar_expect_tx(bar, NH * HBX * HBY * sizeof(T) + NC * TX * TY * sizeof(T));
-    const int k = tl.kb - 1 + pj;
+    const int k = ptl.kb - 1 + pj;
 #pragma unroll
-    for (int h = 0; h < NH; ++h) tma_load_3d(sb + h * HB, &maps.h[h], tl.x0 - 4, tl.y0 - 1, k, bar);
+    for (int h = 0; h < NH; ++h) tma_load_3d(sb + h * HB, &maps.h[h], ptl.x0 - 4, ptl.y0 - 1, k, bar);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) tma_load_3d(sb + NH * HB + c * CB, &maps.c[c], tl.x0, tl.y0, k, bar);
+    for (int c = 0; c < NC; ++c) tma_load_3d(sb + NH * HB + c * CB, &maps.c[c], ptl.x0, ptl.y0, k, bar);
     ++pseq;
-    if (++pj == tl.ke - tl.kb + 2) {
+    if (++pj == ptl.ke - ptl.kb + 2) {
       pj = 0;
       pt += gridDim.x;
+      if (pt < ntiles) ptl = tile_of(pt, g.nx, g.nz);
     }
   };
   if (threadIdx.x == 0)
@@ -324,11 +351,14 @@ __global__ void __launch_bounds__(NTHREADS) k_stencil(const __grid_constant__ Ma
     const int planes = tl.ke - tl.kb + 2;
     typename Op::Ctr cprev{}, cnow{};
     T q_dn = T(0), q_prev = T(0), wD = T(0);
+    T* Qnow = qring;                 // plane j
+    T* Qprev = qring + 2 * PLANE;    // plane j-1
+    T* Qold = qring + PLANE;         // plane j-2 (free for plane j+1)
+    long cidx = geo.gi + (long)g.px * geo.gj + g.plane * (tl.kb - 1);
     for (int j = 0; j < planes; ++j, ++seq) {
-      const int stage = seq % D;
+      const int stage = seq & (D - 1);
       const bool ok = mbar_wait(&bars[stage], (seq / D) & 1u, wait_limit);
       T qc = T(0);
-      T* Q = qring + (j % 3) * PLANE;
       if (ok) {
         const unsigned char* sb = smem + stage * STAGE;
         const T* H[NH];
@@ -339,8 +369,8 @@ __global__ void __launch_bounds__(NTHREADS) k_stencil(const __grid_constant__ Ma
         for (int c = 0; c < NC; ++c) C[c] = reinterpret_cast<const T*>(sb + NH * HB + c * CB);
         if (geo.cbo >= 0) qc = Op::q_of(sc, H, geo.cbo, &cnow);
         if (geo.valid) Op::centre(a, H, C, geo.cbo, ly * TX + lx, geo.gi > 0, geo.gj > 0, cnow);
-        Q[cs(lx, ly)] = qc;
-        if (geo.hs >= 0) Q[geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
+        Qnow[cs(lx, ly)] = qc;
+        if (geo.hs >= 0) Qnow[geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
       }
       // one barrier per plane; the vote makes a timed-out wait a decision of the whole block
       if (__syncthreads_or(!ok)) {
@@ -351,24 +381,27 @@ __global__ void __launch_bounds__(NTHREADS) k_stencil(const __grid_constant__ Ma
         fence_proxy_async();
         issue();
       }
-      if (j >= 2 && geo.valid) {
-        const int k = tl.kb + j - 2;
-        const long cidx = geo.gi + (long)g.px * geo.gj + g.plane * k;
-        Op::output(sc, a, qring + ((j - 1) % 3) * PLANE, lx, ly, cidx, cprev, q_dn, qc, wD, acc);
-      }
+      if (j >= 2 && geo.valid) Op::output(sc, a, Qprev, lx, ly, cidx, cprev, q_dn, qc, wD, acc);
       if (j >= 1) {
         q_dn = q_prev;
         wD = Op::up_face(a, cprev);
+        cidx += g.plane;
       }
       q_prev = qc;
       cprev = cnow;
+      // rotate the three stencil planes
+      T* const freed = Qold;
+      Qold = Qprev;
+      Qprev = Qnow;
+      Qnow = freed;
     }
+    acc.flush();
     if (!failed) __syncthreads();
   }
   if (failed) {
     // give up: let this block's copies in flight land (bounded), report the timeout, skip the reduction
     if (threadIdx.x == 0) {
-      for (unsigned s = seq; s < pseq; ++s) mbar_wait(&bars[s % D], (s / D) & 1u, wait_limit);
+      for (unsigned s = seq; s < pseq; ++s) mbar_wait(&bars[s & (D - 1)], (s / D) & 1u, wait_limit);
       a.st->status = 7;  // PF_E_TIMEOUT
       atomicExch(&a.st->done, 1);
     }
@@ -382,7 +415,8 @@ __global__ void __launch_bounds__(NTHREADS) k_stencil(const __grid_constant__ Ma
 template <typename T_, bool UNI>
 struct OpB {
   using T = T_;
-  static constexpr int NH = SlotsB<UNI>::NH, NC = SlotsB<UNI>::NC, D = sizeof(T_) == 4 ? 3 : 2;
+  static constexpr int NH = SlotsB<UNI>::NH, NC = SlotsB<UNI>::NC, D = sizeof(T_) == 4 ? 4 : 2;
+  static constexpr int MINB = sizeof(T_) == 4 ? 4 : 2;
   static constexpr bool CHECK_DONE = true;
   enum { R = 0, V = 1, DI = 2, WE = 3, WN = 4 };
   enum { RT = 0, WU = 1 };
@@ -399,8 +433,9 @@ struct OpB {
     T s, di, rt, wU, wEc, wEw, wNc, wNs;
   };
   struct Accs {
-    Acc<T> rs, rtt, ts, tt, ss;
+    Partials<T, 5> p;  // r~.s, r~.t, t.s, t.t, s.s
     T smax = T(0);
+    __device__ void flush() { p.flush(); }
   };
   __device__ static Sc scalars(const Args& a) { return Sc{(T)a.st->alpha}; }
   __device__ static T q_of(const Sc& sc, const T* const* H, int o, Ctr* c) {
@@ -447,16 +482,15 @@ struct OpB {
       tc = c.s - nb;
     }
     a.t[cidx] = tc;
-    acc.rs.prod(c.rt, c.s);
-    acc.rtt.prod(c.rt, tc);
-    acc.ts.prod(tc, c.s);
-    acc.tt.prod(tc, tc);
-    acc.ss.prod(c.s, c.s);
+    acc.p.t[0] = fma(c.rt, c.s, acc.p.t[0]);
+    acc.p.t[1] = fma(c.rt, tc, acc.p.t[1]);
+    acc.p.t[2] = fma(tc, c.s, acc.p.t[2]);
+    acc.p.t[3] = fma(tc, tc, acc.p.t[3]);
+    acc.p.t[4] = fma(c.s, c.s, acc.p.t[4]);
     acc.smax = fmax(acc.smax, tabs(c.s));
   }
   __device__ static void finish(const Args& a, const Accs& acc, double* scratch) {
-    double vals[6] = {acc.rs.value(), acc.rtt.value(), acc.ts.value(), acc.tt.value(), acc.ss.value(),
-                      (double)acc.smax};
+    double vals[6] = {acc.p.d[0], acc.p.d[1], acc.p.d[2], acc.p.d[3], acc.p.d[4], (double)acc.smax};
     block_partials<6>(vals, 32u, a.part, scratch);
     if (!arrive_last(&a.st->ticket)) return;
     double tot[6];
@@ -493,7 +527,8 @@ struct OpB {
 template <typename T_, bool UNI>
 struct OpCA {
   using T = T_;
-  static constexpr int NH = SlotsCA<UNI>::NH, NC = SlotsCA<UNI>::NC, D = sizeof(T_) == 4 ? 3 : 2;
+  static constexpr int NH = SlotsCA<UNI>::NH, NC = SlotsCA<UNI>::NC, D = 2;
+  static constexpr int MINB = sizeof(T_) == 4 ? 4 : 2;
   static constexpr bool CHECK_DONE = true;
   enum { R = 0, V = 1, TT = 2, P = 3, DI = 4, WE = 5, WN = 6 };
   enum { X = 0, RT = 1, WU = 2 };
@@ -514,8 +549,9 @@ struct OpCA {
     T s, rn, pn, pold, di, x, rt, wU, wEc, wEw, wNc, wNs;
   };
   struct Accs {
-    Acc<T> rv, rr, r2;
+    Partials<T, 3> p;  // r~.v', r~.r', r'.r'
     T rmax = T(0);
+    __device__ void flush() { p.flush(); }
   };
   __device__ static Sc scalars(const Args& a) { return Sc{(T)a.st->alpha, (T)a.st->omega, (T)a.st->beta}; }
   __device__ static T q_of(const Sc& sc, const T* const* H, int o, Ctr* c) {
@@ -576,13 +612,13 @@ struct OpCA {
     a.r_out[cidx] = c.rn;
     a.p_out[cidx] = c.pn;
     a.v_out[cidx] = vn;
-    acc.rv.prod(c.rt, vn);
-    acc.rr.prod(c.rt, c.rn);
-    acc.r2.prod(c.rn, c.rn);
+    acc.p.t[0] = fma(c.rt, vn, acc.p.t[0]);
+    acc.p.t[1] = fma(c.rt, c.rn, acc.p.t[1]);
+    acc.p.t[2] = fma(c.rn, c.rn, acc.p.t[2]);
     acc.rmax = fmax(acc.rmax, tabs(c.rn));
   }
   __device__ static void finish(const Args& a, const Accs& acc, double* scratch) {
-    double vals[4] = {acc.rv.value(), acc.rr.value(), acc.r2.value(), (double)acc.rmax};
+    double vals[4] = {acc.p.d[0], acc.p.d[1], acc.p.d[2], (double)acc.rmax};
     block_partials<4>(vals, 8u, a.part, scratch);
     if (!arrive_last(&a.st->ticket)) return;
     double tot[4];
@@ -627,6 +663,7 @@ template <bool UNI>
 struct OpRes {
   using T = double;
   static constexpr int NH = SlotsRes<UNI>::NH, NC = SlotsRes<UNI>::NC, D = 2;
+  static constexpr int MINB = 2;
   static constexpr bool CHECK_DONE = false;
   enum { X = 0, DI = 1, WE = 2, WN = 3 };
   enum { B = 0, DG = 1, WU = 2 };
@@ -646,6 +683,7 @@ struct OpRes {
   };
   struct Accs {
     double rr = 0.0, bb = 0.0, rmax = 0.0;
+    __device__ void flush() {}
   };
   __device__ static Sc scalars(const Args&) { return Sc{0}; }
   __device__ static double q_of(const Sc&, const double* const* H, int o, Ctr* c) {
@@ -933,71 +971,106 @@ __global__ void k_set_state(BicgState* st, double tol, int norm, int max_iter) {
 }
 
 // ------------------------------------------------------------------ Eq. (1) pointwise step
-// Void fraction Gamma = e^u from f(u) = e^u + sum_i exp(la_i + p_i u) - 1 = 0 (Newton in u inside a
-// bracket), S = u - ln Gamma^B, C_i = cB_i exp(-z_i phi + p_i S), rho = sum z_i C_i, kappa = lambda sum z_i^2 C_i.
-__device__ __forceinline__ bool fermi_root(const SpeciesParams& sp, double phi, double& u_out) {
+// With la_i = ln(v_i cB_i) - z_i phi - p_i ln Gamma^B, the void fraction Gamma = e^u solves
+//   f(u) = e^u + sum_i exp(la_i + p_i u) - 1 = 0,
+// f increasing; every term is at most 1 on the bracket [lo, hi] below, so nothing overflows there.
+// Newton runs first in FP32 on du = u - u0 (u0: the previous outer iterate's root, or ln Gamma^B), then in
+// FP64 until the step is below 1e-8 |u|; as Newton converges quadratically the last FP64 step leaves u
+// exact to rounding, and the concentrations come from the last FP64 terms, term_i = v_i C_i, moved to the
+// final u by exp(p_i du) = 1 + p_i du + (p_i du)^2/2.
+struct FermiOut {
+  double u, S, G;
+  double C[MAXSP];
+};
+
+__device__ __forceinline__ bool fermi_point(const SpeciesParams& sp, double phi, double u0, FermiOut& o) {
   double la[MAXSP];
-  int nterm = 0;
+  double hi = 0.0, lo = -sp.lnn;
   for (int i = 0; i < sp.ns; ++i) {
     la[i] = sp.lvc[i] - sp.z[i] * phi - sp.p[i] * sp.lgB;
-    if (sp.lvc[i] > -INFINITY) ++nterm;
-  }
-  const double lnn = log((double)(nterm + 1));
-  double hi = 0.0, lo = -lnn;
-  for (int i = 0; i < sp.ns; ++i) {
     if (!(sp.lvc[i] > -INFINITY)) continue;
-    hi = fmin(hi, -la[i] / sp.p[i]);
-    lo = fmin(lo, (-la[i] - lnn) / sp.p[i]);
+    hi = fmin(hi, -la[i] * sp.inv_p[i]);
+    lo = fmin(lo, (-la[i] - sp.lnn) * sp.inv_p[i]);
   }
-  double u = sp.lgB;
+  double u = u0;
   if (!(u < hi && u > lo)) u = 0.5 * (lo + hi);
-  for (int it = 0; it < 400; ++it) {
+  // FP32 phase on du = u - u0c (u0c: the clamped start)
+  {
+    const double uc = u;
+    float A[MAXSP];
+    for (int i = 0; i < sp.ns; ++i) A[i] = (sp.lvc[i] > -INFINITY) ? (float)(la[i] + sp.p[i] * uc) : -INFINITY;
+    const float Ae = (float)uc;
+    float du = 0.f, dlo = (float)(lo - uc), dhi = (float)(hi - uc);
+    for (int it = 0; it < 60; ++it) {
+      const float eu = __expf(Ae + du);
+      float f = eu - 1.f, df = eu;
+      for (int i = 0; i < sp.ns; ++i) {
+        const float pi = (float)sp.p[i];
+        const float term = __expf(A[i] + pi * du);
+        f += term;
+        df = fmaf(pi, term, df);
+      }
+      if (f > 0.f) dhi = du; else dlo = du;
+      float dn = du - f / df;
+      if (!(dn > dlo && dn < dhi)) dn = 0.5f * (dlo + dhi);
+      const float step = dn - du;
+      du = dn;
+      if (fabsf(step) <= 2e-6f * fmaxf(1.f, fabsf((float)uc + du))) break;
+    }
+    u = uc + (double)du;
+    if (!(u < hi && u > lo)) u = 0.5 * (lo + hi);
+  }
+  // FP64 phase
+  double term[MAXSP];
+  for (int it = 0; it < 200; ++it) {
     const double eu = exp(u);
     double f = eu - 1.0, df = eu;
     for (int i = 0; i < sp.ns; ++i) {
-      if (!(sp.lvc[i] > -INFINITY)) continue;
-      const double term = exp(la[i] + sp.p[i] * u);
-      f += term;
-      df += sp.p[i] * term;
+      term[i] = (sp.lvc[i] > -INFINITY) ? exp(la[i] + sp.p[i] * u) : 0.0;
+      f += term[i];
+      df += sp.p[i] * term[i];
     }
-    if (f == 0.0) {
-      u_out = u;
-      return true;
+    const double du = (f == 0.0) ? 0.0 : -f / df;
+    if (fabs(du) <= 1e-8 * fmax(1.0, fabs(u))) {  // converged: take the last Newton step and finish
+      const double un = u + du;
+      o.u = un;
+      o.S = un - sp.lgB;
+      o.G = eu * (1.0 + du + 0.5 * du * du);
+      for (int i = 0; i < sp.ns; ++i) {
+        const double x = sp.p[i] * du;
+        o.C[i] = term[i] * sp.inv_v[i] * (1.0 + x + 0.5 * x * x);
+      }
+      return isfinite(un);
     }
     if (f > 0.0) hi = u; else lo = u;
-    double un = u - f / df;
-    if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
-    const double du = un - u;
+    double un = u + du;
+    if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);  // safeguard: bisect
     u = un;
-    if (fabs(du) <= 1e-15 * fmax(1.0, fabs(u))) {
-      u_out = u;
-      return isfinite(u);
-    }
   }
   return false;
 }
 
+// ulast holds each node's ln Gamma from the previous call (warm != 0) and receives the new one.
 __global__ void k_fermi(const double* __restrict__ phi0, const uint8_t* __restrict__ solvent,
                         const double* __restrict__ ffix, SpeciesParams sp, Geom g, double* b1, double* sig, double* c2,
-                        double* C, double* S, double* G, int* err) {
-  PF_ROWS(g) {
-    const long c = i + g.px * row;
+                        double* C, double* S, double* G, double* ulast, int warm, int* err) {
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < g.np; c += (long)gridDim.x * blockDim.x) {
+    const long row = c / g.px;
+    const int i = (int)(c - row * g.px);
+    if (i >= g.nx) continue;  // pad column
     const long k = row / g.ny;
     const double ph = phi0[c];
-    double rho = 0.0, kap = 0.0, Sv = 0.0, Gv = 0.0;
     const bool sol = solvent[c] != 0;
-    double u = 0.0;
-    bool ok = true;
+    FermiOut fo;
+    bool ok = false;
     if (sol) {
-      ok = fermi_root(sp, ph, u);
+      ok = fermi_point(sp, ph, warm ? ulast[c] : sp.lgB, fo);
       if (!ok) atomicExch(err, 5);
+      else ulast[c] = fo.u;
     }
-    if (sol && ok) {
-      Sv = u - sp.lgB;
-      Gv = exp(u);
-    }
+    double rho = 0.0, kap = 0.0;
     for (int s = 0; s < sp.ns; ++s) {
-      const double Ci = (sol && ok && sp.lvc[s] > -INFINITY) ? exp(sp.lcB[s] - sp.z[s] * ph + sp.p[s] * Sv) : 0.0;
+      const double Ci = (sol && ok) ? fo.C[s] : 0.0;
       rho += sp.z[s] * Ci;
       kap += sp.lam * sp.z[s] * sp.z[s] * Ci;
       if (C) C[s * g.np + c] = Ci;
@@ -1005,8 +1078,8 @@ __global__ void k_fermi(const double* __restrict__ phi0, const uint8_t* __restri
     if (b1) b1[c] = (sol && k > 0 && k < g.nz - 1) ? -sp.lam * rho : 0.0;
     if (sig) sig[c] = kap;
     if (c2) c2[c] = fma(kap, ph, ffix[c]);
-    if (S) S[c] = Sv;
-    if (G) G[c] = Gv;
+    if (S) S[c] = (sol && ok) ? fo.S : 0.0;
+    if (G) G[c] = (sol && ok) ? fo.G : 0.0;
   }
 }
 
@@ -1229,9 +1302,9 @@ cudaError_t launch_unpack(const double* src, double* dst, const Geom& g, int cou
 }
 
 cudaError_t launch_fermi(const double* phi0, const uint8_t* solvent, const double* ffix, const SpeciesParams& sp,
-                         const Geom& g, double* b1, double* sig, double* c2, double* C, double* S, double* G, int* err,
-                         cudaStream_t s) {
-  k_fermi<<<row_blocks(g), 128, 0, s>>>(phi0, solvent, ffix, sp, g, b1, sig, c2, C, S, G, err);
+                         const Geom& g, double* b1, double* sig, double* c2, double* C, double* S, double* G,
+                         double* ulast, int warm, int* err, cudaStream_t s) {
+  k_fermi<<<ew_blocks(g.np), 256, 0, s>>>(phi0, solvent, ffix, sp, g, b1, sig, c2, C, S, G, ulast, warm, err);
   return cudaGetLastError();
 }
 
