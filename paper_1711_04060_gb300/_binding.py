@@ -21,6 +21,7 @@ PF_OP_POISSON, PF_OP_PF1, PF_OP_PF2 = 0, 1, 2
 PF_MEM_HOST, PF_MEM_DEVICE = 0, 1
 PF_NORM_REL2, PF_NORM_ABSINF = 0, 1
 PF_MAX_SPECIES = 8
+PF_FERMI_NOALLOC_MAX_NODES = 1 << 20
 
 
 class pf_species(ctypes.Structure):
@@ -80,6 +81,7 @@ SIGNATURES = {
     "pf_profile_enable": (_I, [_VP, _I]),
     "pf_profile_get": (_I, [_VP, ctypes.POINTER(pf_profile)]),
     "pf_last_error": (ctypes.c_char_p, []),
+    "pf_fermi_noalloc": (_I, [ctypes.c_long, _VP, _VP, _I, ctypes.POINTER(pf_species), _D, _VP, _VP, _VP, _VP]),
     "pf_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_VP)]),
     "pf_submit": (_I, [_VP, ctypes.POINTER(pf_request), ctypes.POINTER(ctypes.c_uint64)]),
     "pf_poll": (_I, [_VP, ctypes.c_uint64, ctypes.POINTER(pf_result), ctypes.POINTER(_I)]),

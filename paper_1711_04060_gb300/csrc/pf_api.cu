@@ -542,6 +542,9 @@ pf_status unpack_out(pf_grid* g, const double* src, int count, double* dst, int 
 
 }  // namespace
 
+// Sets the message that pf_last_error returns on this thread (used by entry points in other files).
+void pf_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
 // Device bytes that pf_create_grid allocates for a grid (used for the serving budget).
 size_t pf_internal_grid_bytes(int nx, int ny, int nz) {
   const pf::Geom g = pf::make_geom(nx, ny, nz);
