@@ -65,7 +65,7 @@ typedef enum { PF_OP_POISSON = 0, PF_OP_PF1 = 1, PF_OP_PF2 = 2 } pf_operator;
 typedef enum { PF_MEM_HOST = 0, PF_MEM_DEVICE = 1 } pf_mem;
 
 /* Stop tests: PF_NORM_REL2 stops when ||b - A x||_2 <= tol * ||b||_2; PF_NORM_ABSINF stops
- * when ||b - A x||_inf < tol (the test of Table 3, step 19). */
+ * when ||b - A x||_inf < tol (the stop test of Table 3). */
 typedef enum { PF_NORM_REL2 = 0, PF_NORM_ABSINF = 1 } pf_norm;
 
 #define PF_MAX_SPECIES 8
@@ -116,10 +116,19 @@ typedef struct {
 } pf_report;
 
 typedef struct {
-  double omega;       /* relaxation omega_PF of Table 2/4 step 5/7 (0.3 in the paper) */
-  double tol_outer;   /* stop when ||Phi - Phi_0||_inf <= tol_outer (phi_hat units) */
+  double omega;       /* relaxation weight omega_PF of Tables 2 and 4 (0.3 in the paper) */
+  double tol_outer;   /* stop when ||Phi - Phi_0||_inf <= tol_outer (phi_hat units), where Phi is the relaxed
+                         update omega Phi_0 + (1-omega) Phi_solve of Table 4 */
   int max_outer;      /* outer (Newton) iteration limit */
   pf_solve_opts lin;  /* options of every linear solve inside the loop */
+  int accel_depth;    /* 0: the paper's relaxation.  m in 1..8: Anderson acceleration of the same fixed-point
+                         map with the last m differences (mixing 1 - omega); same fixed point, same stop test,
+                         not in the paper.  Needs 2m + 3 more FP64 vectors on the grid. */
+  double lin_forcing; /* 0: every linear solve uses lin.tol (the paper).  c > 0: the linear solves of outer
+                         iteration k also stop once ||r||_2 <= eta_k ||r0||_2, r0 the residual of their warm
+                         start and eta_k = min(1e-2, c * delta_{k-1}) (an inexact-Newton forcing term, not in the
+                         paper; 2-norm stop only).  The outer update is then exact to a fraction eta_k of itself,
+                         so the stop test on delta keeps its meaning. */
 } pf_nl_opts;
 
 /* Output and report of pf_nonlinear_solve.  Output pointers may be NULL; `mem` says whether
@@ -137,14 +146,14 @@ typedef struct {
   int status;
   int outer_iters;
   int lin_iters_total;
-  int lin_iters_first;  /* iterations of the initial PF2 solve (Table 4, step 4) */
+  int lin_iters_first;  /* iterations of the initial PF2 solve (Table 4) */
   double delta;         /* last ||Phi - Phi_0||_inf */
   double time_ms;       /* device time of the whole solve */
 } pf_result;
 
 /* Fills the options with defaults: FP64, relative 2-norm 1e-10, 20000 iterations; mixed
  * inner tolerance 0.1 (at most 1000 FP32 iterations per refinement step), 64 refinements;
- * omega 0.3, tol_outer 1e-9, 500 outer iterations. */
+ * omega 0.3, tol_outer 1e-9, 500 outer iterations, no acceleration, fixed linear tolerance. */
 void pf_default_solve_opts(pf_solve_opts* o);
 void pf_default_nl_opts(pf_nl_opts* o);
 
@@ -181,11 +190,11 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
 
 /* ---- profiling: device time per kernel kind on one grid ----------------------------------- */
 enum {
-  PF_PROF_INIT = 0,        /* BiCGSTAB start: r0 = b - A x0 (Table 3, step 2) */
-  PF_PROF_B_FP64 = 1,      /* phase B in FP64: s, t = A M^-1 s and its inner products (steps 13-15),
+  PF_PROF_INIT = 0,        /* BiCGSTAB start: r0 = b - A x0 (Table 3) */
+  PF_PROF_B_FP64 = 1,      /* phase B in FP64: s, t = A M^-1 s and its inner products (omega),
                               variable-dielectric operators (PF_OP_POISSON, PF_OP_PF2) */
-  PF_PROF_CA_FP64 = 2,     /* phase C+A in FP64: x, r updates, next p and v = A M^-1 p (steps 16-17,
-                              9-12), variable-dielectric operators */
+  PF_PROF_CA_FP64 = 2,     /* phase C+A in FP64: x, r updates, next p and v = A M^-1 p and
+                              the inner products of rho and alpha, variable-dielectric operators */
   PF_PROF_B_FP32 = 3,      /* the same two phases in FP32 (mixed precision inner solves) */
   PF_PROF_CA_FP32 = 4,
   PF_PROF_B_FP64_PF1 = 5,  /* the four phase kernels on the uniform-face PF1 operator */

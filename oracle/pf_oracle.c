@@ -239,27 +239,27 @@ int pfo_bicgstab(int nx, int ny, int nz, const double* A, const double* b, doubl
 #define PFO_MEASURE(vec) (norm_mode == 0 ? sqrt(dot(N, vec, vec)) / bnorm : norm_inf(N, vec))
 #define PFO_CONVERGED(m) (norm_mode == 0 ? (m) <= tol : (m) < tol)
 
-  pfo_dia_apply(nx, ny, nz, A, x, r); /* step 2: r0 = b - A x0, rtilde = r0 */
+  pfo_dia_apply(nx, ny, nz, A, x, r); /* r0 = b - A x0; the shadow residual rtilde = r0 */
   for (long c = 0; c < N; ++c) { r[c] = b[c] - r[c]; rt[c] = r[c]; }
   measure = PFO_MEASURE(r);
   if (PFO_CONVERGED(measure)) { status = PFO_OK; goto done; }
 
   double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
   for (it = 1; it <= max_it; ++it) {
-    const double rho = dot(N, rt, r); /* step 4 */
+    const double rho = dot(N, rt, r); /* rho = rtilde . r */
     if (rho == 0.0) { status = PFO_E_BREAKDOWN; break; }
     if (it == 1) {
-      for (long c = 0; c < N; ++c) p[c] = r[c]; /* step 6 */
+      for (long c = 0; c < N; ++c) p[c] = r[c]; /* first direction p = r */
     } else {
-      const double beta = (rho / rho_prev) * (alpha / omega); /* step 8 */
-      for (long c = 0; c < N; ++c) p[c] = r[c] + beta * (p[c] - omega * v[c]); /* step 9 */
+      const double beta = (rho / rho_prev) * (alpha / omega);
+      for (long c = 0; c < N; ++c) p[c] = r[c] + beta * (p[c] - omega * v[c]);
     }
     for (long c = 0; c < N; ++c) ph[c] = p[c] / A[c]; /* Jacobi: phat = M^-1 p */
-    pfo_dia_apply(nx, ny, nz, A, ph, v); /* step 11 */
+    pfo_dia_apply(nx, ny, nz, A, ph, v); /* v = A phat */
     const double rtv = dot(N, rt, v);
     if (rtv == 0.0) { status = PFO_E_BREAKDOWN; break; }
-    alpha = rho / rtv; /* step 12 */
-    for (long c = 0; c < N; ++c) s[c] = r[c] - alpha * v[c]; /* step 13 */
+    alpha = rho / rtv;
+    for (long c = 0; c < N; ++c) s[c] = r[c] - alpha * v[c];
     measure = PFO_MEASURE(s);
     if (PFO_CONVERGED(measure)) { /* early exit on s: x = x + alpha phat */
       for (long c = 0; c < N; ++c) x[c] += alpha * ph[c];
@@ -267,13 +267,13 @@ int pfo_bicgstab(int nx, int ny, int nz, const double* A, const double* b, doubl
       break;
     }
     for (long c = 0; c < N; ++c) sh[c] = s[c] / A[c];
-    pfo_dia_apply(nx, ny, nz, A, sh, t); /* step 14 */
+    pfo_dia_apply(nx, ny, nz, A, sh, t); /* t = A shat */
     const double tt = dot(N, t, t);
     if (tt == 0.0) { status = PFO_E_BREAKDOWN; break; }
-    omega = dot(N, t, s) / tt; /* step 15 */
-    for (long c = 0; c < N; ++c) x[c] += alpha * ph[c] + omega * sh[c]; /* step 16 */
-    for (long c = 0; c < N; ++c) r[c] = s[c] - omega * t[c];             /* step 17 */
-    measure = PFO_MEASURE(r); /* step 18 */
+    omega = dot(N, t, s) / tt; /* minimises ||s - omega t||_2 */
+    for (long c = 0; c < N; ++c) x[c] += alpha * ph[c] + omega * sh[c];
+    for (long c = 0; c < N; ++c) r[c] = s[c] - omega * t[c];
+    measure = PFO_MEASURE(r);
     if (PFO_CONVERGED(measure)) { status = PFO_OK; break; }
     if (omega == 0.0) { status = PFO_E_BREAKDOWN; break; }
     rho_prev = rho;
@@ -315,8 +315,9 @@ int pfo_spread_charges(int nx, int ny, int nz, double h, const double* origin, i
   return PFO_OK;
 }
 
-/* ---- Table 2: sequential PF nonlinear solver (steps 2-5; step 1 is not needed
- * because the charges are spread onto the grid) ------------------------------- */
+/* ---- Table 2: the sequential PF nonlinear solver (initial PF2 solve, then PF1, PF2 and the
+ * relaxation until the update is small; the charges are spread onto the grid, so no singular part
+ * is split off) ----------------------------------------------------------------- */
 int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
                  const double* eps, const unsigned char* solvent,
                  int nq, const double* charges, double phi_lo_V, double phi_hi_V,
@@ -355,7 +356,7 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
 #define PFO_SET_DIRICHLET(vec)                                        \
   for (long c = 0; c < plane; ++c) { vec[c] = lo_hat; vec[N - plane + c] = hi_hat; }
 
-  /* Step 2: PF2 with rho' = Psi = 0, i.e. -div(eps grad phi0) = lambda rho_fix. */
+  /* initial potential: PF2 with rho' = Psi = 0, i.e. -div(eps grad phi0) = lambda rho_fix. */
   pfo_assemble_eps(nx, ny, nz, h, eps, NULL, A);
   for (long c = 0; c < N; ++c) b[c] = ffix[c];
   PFO_SET_DIRICHLET(b);
@@ -380,14 +381,14 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
         kap[c] += lam * z[i] * z[i] * Ci[i];
       }
     }
-    /* Step 3: PF1, Eq. (12) */
+    /* PF1, Eq. (12) */
     pfo_assemble_pf1(nx, ny, nz, h, solvent, eps_s, lc, A);
     for (long c = 0; c < N; ++c) b[c] = solvent[c] ? -lam * rho[c] : 0.0;
     for (long c = 0; c < plane; ++c) { b[c] = 0.0; b[N - plane + c] = 0.0; }
     st = pfo_bicgstab(nx, ny, nz, A, b, psi, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
     R.lin_iters_total += its;
     if (st) goto out;
-    /* Step 4: PF2, Eq. (13): -eps_s Lap phi - rho' phi = -eps_s Psi - rho' phi0 in the solvent,
+    /* PF2, Eq. (13): -eps_s Lap phi - rho' phi = -eps_s Psi - rho' phi0 in the solvent,
      * -div(eps_m grad phi) = lambda rho_fix in the membrane */
     for (long c = 0; c < N; ++c) sig[c] = solvent[c] ? kap[c] : 0.0;
     pfo_assemble_eps(nx, ny, nz, h, eps, sig, A);
@@ -398,7 +399,7 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
     st = pfo_bicgstab(nx, ny, nz, A, b, phi, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
     R.lin_iters_total += its;
     if (st) goto out;
-    /* Step 5: relax and test */
+    /* relaxation and stop test */
     double delta = 0.0;
     for (long c = 0; c < N; ++c) {
       phi[c] = opts->omega * phi0[c] + (1.0 - opts->omega) * phi[c];

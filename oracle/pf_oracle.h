@@ -83,7 +83,7 @@ int pfo_spread_charges(int nx, int ny, int nz, double h, const double* origin, i
 
 /* ---- nonlinear PF solve (Table 2; the GPU variant of Table 4 computes the same) ---- */
 typedef struct {
-  double omega;      /* relaxation omega_PF of Table 2, step 5 */
+  double omega;      /* relaxation weight omega_PF of Table 2 */
   double tol_outer;  /* stop when ||Phi - Phi0||_inf <= tol_outer (phi_hat units) */
   double lin_tol;    /* linear-solver tolerance */
   int lin_norm;      /* 0: relative 2-norm, 1: absolute inf-norm */
@@ -95,7 +95,7 @@ typedef struct {
   int status;
   int outer_iters;
   int lin_iters_total;
-  int lin_iters_first;   /* iterations of the initial PF2 solve (Table 2, step 2) */
+  int lin_iters_first;   /* iterations of the initial PF2 solve (Table 2) */
   double delta;          /* last ||Phi - Phi0||_inf */
 } pfo_nl_report;
 

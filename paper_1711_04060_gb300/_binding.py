@@ -44,7 +44,8 @@ class pf_report(ctypes.Structure):
 
 
 class pf_nl_opts(ctypes.Structure):
-    _fields_ = [("omega", _D), ("tol_outer", _D), ("max_outer", _I), ("lin", pf_solve_opts)]
+    _fields_ = [("omega", _D), ("tol_outer", _D), ("max_outer", _I), ("lin", pf_solve_opts), ("accel_depth", _I),
+                ("lin_forcing", _D)]
 
 
 class pf_result(ctypes.Structure):

@@ -85,6 +85,10 @@ struct pf_grid {
   double *phi0 = nullptr, *phi = nullptr, *psi = nullptr, *b1 = nullptr, *c2 = nullptr, *b2 = nullptr;
   double *Cbuf = nullptr, *Sbuf = nullptr, *Gbuf = nullptr, *ulast = nullptr;
   double* part = nullptr;
+  // Anderson acceleration of the outer loop (allocated on first use)
+  int aa_alloc = 0;
+  double *aa_f = nullptr, *aa_fprev = nullptr, *aa_xprev = nullptr, *aa_out = nullptr, *aa_host = nullptr;
+  double *aa_dF[pf::AA_MAX] = {}, *aa_dX[pf::AA_MAX] = {};
   double* dch = nullptr;     // fixed charges (x, y, z, q) on the device
   int nq = 0;
   BicgState* st = nullptr;   // FP64 solve / refinement state
@@ -134,6 +138,8 @@ void free_all(pf_grid* g) {
   if (g->host_st) cudaFreeHost(g->host_st);
   if (g->host_err) cudaFreeHost(g->host_err);
   if (g->host_delta) cudaFreeHost(g->host_delta);
+  if (g->aa_host) cudaFreeHost(g->aa_host);
+  g->aa_host = nullptr;
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
   g->host_st = nullptr;
@@ -283,8 +289,9 @@ OpArrays<float> ops32(const pf_grid* g, int op) {
   return {op == PF_OP_PF2 ? g->dinv2_32 : g->dinvP32, nullptr, g->wE32, g->wN32, g->wU32, 0.0, 0.0};
 }
 
-pf_status set_state(pf_grid* g, BicgState* dst, double tol, int norm, int max_iter) {
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_state(dst, tol, norm, max_iter, g->stream));
+pf_status set_state(pf_grid* g, BicgState* dst, double tol, int norm, int max_iter, double tol_r0 = 0.0,
+                    int keep_r0 = 0) {
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_state(dst, tol, norm, max_iter, tol_r0, keep_r0, g->stream));
   return PF_OK;
 }
 
@@ -397,17 +404,18 @@ double measure_of(const BicgState& s, int norm) {
 }
 
 template <bool UNI>
-pf_status solve_fp64(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, pf_report* rep) {
+pf_status solve_fp64(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, double tol_r0,
+                     pf_report* rep) {
   const OpArrays<double> A = ops64(g, op);
   const Krylov<double> K = kry64(g);
   PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_impose(x, b, A.dinv, g->geom.np, g->stream));
-  PF_TRY(set_state(g, g->st, o.tol, o.norm, o.max_iter));
-  PF_TRY(residual<UNI>(g, A, x, b, 1, &K, g->st));  // Table 3 step 2
+  PF_TRY(set_state(g, g->st, o.tol, o.norm, o.max_iter, tol_r0));
+  PF_TRY(residual<UNI>(g, A, x, b, 1, &K, g->st));  // r0 = b - A x0 (Table 3)
   BicgState s;
   PF_TRY((iterate<double, UNI>(g, A, x, K, g->st, &s)));
   // true residual of the final iterate
   BicgState tr;
-  PF_TRY(set_state(g, g->st, o.tol, o.norm, 0));
+  PF_TRY(set_state(g, g->st, o.tol, o.norm, 0, tol_r0, 1));
   PF_TRY(residual<UNI>(g, A, x, b, 0, nullptr, g->st));
   PF_TRY(read_state(g, g->st, &tr));
   rep->status = s.status;
@@ -421,7 +429,8 @@ pf_status solve_fp64(pf_grid* g, int op, const double* b, double* x, const pf_so
 }
 
 template <bool UNI>
-pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, pf_report* rep) {
+pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, double tol_r0,
+                      pf_report* rep) {
   const OpArrays<double> A = ops64(g, op);
   const OpArrays<float> W = ops32(g, op);
   const Krylov<float> K = kry32(g);
@@ -430,7 +439,7 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
   BicgState tr{};
   for (;;) {
     // FP64 true residual b - A x -> b32 (and its norms)
-    PF_TRY(set_state(g, g->st, o.tol, o.norm, 0));
+    PF_TRY(set_state(g, g->st, o.tol, o.norm, 0, tol_r0, ref > 0));
     PF_TRY(residual<UNI>(g, A, x, b, 0, nullptr, g->st));
     PF_TRY(read_state(g, g->st, &tr));
     if (trace_level() > 0)
@@ -471,11 +480,14 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
   return PF_OK;
 }
 
-pf_status solve_dev(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, pf_report* rep) {
+// tol_r0 > 0 also accepts ||r||_2 <= tol_r0 ||r0||_2 (r0: the residual of the starting x), the forcing
+// term of an inexact outer iteration
+pf_status solve_dev(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, pf_report* rep,
+                    double tol_r0 = 0.0) {
   const bool uni = op == PF_OP_PF1;
   if (o.precision == PF_MIXED)
-    return uni ? solve_mixed<true>(g, op, b, x, o, rep) : solve_mixed<false>(g, op, b, x, o, rep);
-  return uni ? solve_fp64<true>(g, op, b, x, o, rep) : solve_fp64<false>(g, op, b, x, o, rep);
+    return uni ? solve_mixed<true>(g, op, b, x, o, tol_r0, rep) : solve_mixed<false>(g, op, b, x, o, tol_r0, rep);
+  return uni ? solve_fp64<true>(g, op, b, x, o, tol_r0, rep) : solve_fp64<false>(g, op, b, x, o, tol_r0, rep);
 }
 
 pf_status check_opts(const pf_solve_opts& o) {
@@ -540,16 +552,70 @@ pf_status unpack_out(pf_grid* g, const double* src, int count, double* dst, int 
   return PF_OK;
 }
 
+// Buffers of Anderson acceleration with depth m (kept for later solves on the grid).
+pf_status ensure_aa(pf_grid* g, int m) {
+  const long NP = g->geom.np;
+  if (!g->aa_f) {
+    PF_TRY(dalloc(g, &g->aa_f, NP));
+    PF_TRY(dalloc(g, &g->aa_fprev, NP));
+    PF_TRY(dalloc(g, &g->aa_xprev, NP));
+    PF_TRY(dalloc(g, &g->aa_out, 2 * pf::AA_MAX));
+    PF_CK(cudaMallocHost(&g->aa_host, 2 * pf::AA_MAX * sizeof(double)));
+  }
+  for (; g->aa_alloc < m; ++g->aa_alloc) {
+    PF_TRY(dalloc(g, &g->aa_dF[g->aa_alloc], NP));
+    PF_TRY(dalloc(g, &g->aa_dX[g->aa_alloc], NP));
+  }
+  return PF_OK;
+}
+
+// Solves (A + reg I) x = b for a small symmetric positive semi-definite A (k <= AA_MAX) by Cholesky;
+// false when a pivot is not positive.
+bool small_spd_solve(int k, const double (&A)[pf::AA_MAX][pf::AA_MAX], const double* b, double* x) {
+  double L[pf::AA_MAX][pf::AA_MAX] = {};
+  double tr = 0.0;
+  for (int i = 0; i < k; ++i) tr = fmax(tr, A[i][i]);
+  const double reg = 1e-10 * (tr > 0 ? tr : 1.0);
+  for (int i = 0; i < k; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double sum = A[i][j] + (i == j ? reg : 0.0);
+      for (int q = 0; q < j; ++q) sum -= L[i][q] * L[j][q];
+      if (i == j) {
+        if (!(sum > 0.0)) return false;
+        L[i][i] = sqrt(sum);
+      } else {
+        L[i][j] = sum / L[j][j];
+      }
+    }
+  }
+  double y[pf::AA_MAX];
+  for (int i = 0; i < k; ++i) {
+    double sum = b[i];
+    for (int q = 0; q < i; ++q) sum -= L[i][q] * y[q];
+    y[i] = sum / L[i][i];
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double sum = y[i];
+    for (int q = i + 1; q < k; ++q) sum -= L[q][i] * x[q];
+    x[i] = sum / L[i][i];
+  }
+  for (int i = 0; i < k; ++i)
+    if (!isfinite(x[i])) return false;
+  return true;
+}
+
 }  // namespace
 
 // Sets the message that pf_last_error returns on this thread (used by entry points in other files).
 void pf_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
 
 // Device bytes that pf_create_grid allocates for a grid (used for the serving budget).
-size_t pf_internal_grid_bytes(int nx, int ny, int nz) {
+size_t pf_internal_grid_bytes(int nx, int ny, int nz, int accel_depth) {
   const pf::Geom g = pf::make_geom(nx, ny, nz);
-  const size_t per_node = 32 * sizeof(double) + pf::MAXSP * sizeof(double) + 16 * sizeof(float) + 1;
-  return (size_t)g.np * per_node + (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double) + 4096;
+  // Anderson acceleration adds f, f_prev, x_prev and two history columns per depth
+  const int aa = accel_depth > 0 ? 3 + 2 * accel_depth : 0;
+  const size_t per_node = (32 + aa) * sizeof(double) + pf::MAXSP * sizeof(double) + 16 * sizeof(float) + 1;
+  return (size_t)g.np * per_node + (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double) + 8192;
 }
 
 extern "C" {
@@ -570,6 +636,8 @@ void pf_default_nl_opts(pf_nl_opts* o) {
   o->tol_outer = 1e-9;
   o->max_outer = 500;
   pf_default_solve_opts(&o->lin);
+  o->accel_depth = 0;
+  o->lin_forcing = 0.0;
 }
 
 const char* pf_last_error(void) { return g_err.c_str(); }
@@ -756,8 +824,11 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   pf_nl_opts o;
   if (opts) o = *opts; else pf_default_nl_opts(&o);
   PF_TRY(check_opts(o.lin));
-  if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1)
+  if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1 || o.accel_depth < 0 ||
+      o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0))
     return fail(PF_E_INVAL, "invalid pf_nl_opts");
+  const int m = o.accel_depth;
+  if (m > 0) PF_TRY(ensure_aa(g, m));
   if (res->mem != PF_MEM_HOST && res->mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "bad result mem");
   const pf::Geom& G = g->geom;
   const long NP = G.np;
@@ -772,7 +843,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   pf_report rep{};
   // step a1: operators and fixed-charge source from the device-resident coefficients
   PF_TRY(build_operators(g));
-  // Table 4 step 4: PF2 with rho' = Psi = 0 -> Phi_0
+  // initial potential (Table 4): PF2 with rho' = Psi = 0 -> Phi_0
   PF_CK(cudaMemsetAsync(g->phi0, 0, NP * sizeof(double), s));
   PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, G, s));
   PF_CK(cudaMemsetAsync(g->psi, 0, NP * sizeof(double), s));
@@ -781,31 +852,91 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   res->lin_iters_first = rep.iterations;
   res->lin_iters_total += rep.iterations;
   if (rep.status != PF_OK) st = (pf_status)rep.status;
+  const double beta = 1.0 - o.omega;
+  double Gm[pf::AA_MAX][pf::AA_MAX] = {};  // Gram matrix of the history columns, indexed by ring slot
+  int nact = 0, head = 0, kaa = 0;         // active columns, next slot, accelerated iterations done
+  double delta_prev = 1.0;
   for (int outer = 1; st == PF_OK && outer <= o.max_outer; ++outer) {
-    // Eq. (1) at Phi_0 -> b_PF1 = -lambda rho, kappa, PF2 right-hand-side part (Table 4 steps 5-6)
+    // forcing term: the linear solves of this outer iteration stop at eta ||r0|| (r0: the residual of the warm
+    // start, which shrinks with the outer update) or at lin.tol ||b||, whichever is reached first
+    double eta = 0.0;
+    if (o.lin_forcing > 0) eta = outer == 1 ? 1e-2 : fmin(1e-2, o.lin_forcing * delta_prev);
+    const pf_solve_opts& lo = o.lin;
+    // Eq. (1) at Phi_0 -> b_PF1 = -lambda rho, kappa, PF2 right-hand-side part (Table 4)
     PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
     PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, g->b1, g->sig, g->c2,
                                                  nullptr, nullptr, nullptr, g->ulast, outer > 1, g->err, s));
     PF_TRY(update_pf2(g));
-    PF_TRY(solve_dev(g, PF_OP_PF1, g->b1, g->psi, o.lin, &rep));  // Eq. (12)
+    PF_TRY(solve_dev(g, PF_OP_PF1, g->b1, g->psi, lo, &rep, eta));  // Eq. (12)
     res->lin_iters_total += rep.iterations;
     if (rep.status != PF_OK) { st = (pf_status)rep.status; break; }
     PF_LAUNCH(g, PF_PROF_OTHER,
               pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat, G, g->b2, s));
     PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    PF_TRY(solve_dev(g, PF_OP_PF2, g->b2, g->phi, o.lin, &rep));  // Eq. (13)
+    PF_TRY(solve_dev(g, PF_OP_PF2, g->b2, g->phi, lo, &rep, eta));  // Eq. (13)
     res->lin_iters_total += rep.iterations;
     if (rep.status != PF_OK) { st = (pf_status)rep.status; break; }
-    // Table 4 step 7: relax and test
-    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_relax(g->phi0, g->phi, o.omega, NP, g->part, g->ticket, g->delta, s));
-    PF_CK(cudaMemcpyAsync(g->host_delta, g->delta, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PF_CK(cudaStreamSynchronize(s));
+    double delta = 0.0;
+    if (m == 0) {
+      // relaxation and stop test of Table 4
+      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_relax(g->phi0, g->phi, o.omega, NP, g->part, g->ticket, g->delta, s));
+      PF_CK(cudaMemcpyAsync(g->host_delta, g->delta, sizeof(double), cudaMemcpyDeviceToHost, s));
+      PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      PF_CK(cudaStreamSynchronize(s));
+      delta = *g->host_delta;
+    } else {
+      // Anderson acceleration of the same map: f = Phi_solve - Phi_0, delta = (1-omega) ||f||_inf is the
+      // relaxed update of Table 4; the accelerated update mixes the last m differences of f and Phi_0
+      const int slot = head;
+      PF_LAUNCH(g, PF_PROF_OTHER,
+                pf::launch_aa_residual(g->phi, g->phi0, g->aa_f, g->aa_fprev, g->aa_xprev, g->aa_dF[slot],
+                                       g->aa_dX[slot], kaa >= 1, NP, g->part, g->ticket, g->delta, s));
+      PF_CK(cudaMemcpyAsync(g->host_delta, g->delta, sizeof(double), cudaMemcpyDeviceToHost, s));
+      PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      PF_CK(cudaStreamSynchronize(s));
+      delta = beta * *g->host_delta;
+      pf::AAPtrs cols{};
+      pf::AACoef gam{};
+      int k = 0;
+      if (delta > o.tol_outer && kaa >= 1) {
+        head = (head + 1) % m;
+        nact = nact < m ? nact + 1 : m;
+        int act[pf::AA_MAX];  // active slots, oldest first
+        for (int j = 0; j < nact; ++j) act[j] = ((head - nact + j) % m + m) % m;
+        for (int j = 0; j < nact; ++j) {
+          cols.dF[j] = g->aa_dF[act[j]];
+          cols.dX[j] = g->aa_dX[act[j]];
+        }
+        PF_LAUNCH(g, PF_PROF_OTHER,
+                  pf::launch_aa_dots(cols, nact, g->aa_dF[slot], g->aa_f, NP, g->part, g->ticket, g->aa_out, s));
+        PF_CK(cudaMemcpyAsync(g->aa_host, g->aa_out, 2 * pf::AA_MAX * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PF_CK(cudaStreamSynchronize(s));
+        double A[pf::AA_MAX][pf::AA_MAX] = {}, bvec[pf::AA_MAX], x[pf::AA_MAX];
+        for (int j = 0; j < nact; ++j) Gm[slot][act[j]] = Gm[act[j]][slot] = g->aa_host[j];
+        for (int i = 0; i < nact; ++i) {
+          for (int j = 0; j < nact; ++j) A[i][j] = Gm[act[i]][act[j]];
+          bvec[i] = g->aa_host[pf::AA_MAX + i];
+        }
+        bool ok = small_spd_solve(nact, A, bvec, x);
+        for (int j = 0; ok && j < nact; ++j) ok = fabs(x[j]) < 1e4;
+        if (ok) {
+          k = nact;
+          for (int j = 0; j < nact; ++j) gam.g[j] = x[j];
+        } else {
+          nact = 0;  // ill-conditioned history: restart with a plain relaxed step
+        }
+      }
+      // at the stop k = 0: the plain relaxed update, so the final iterate is the relaxed one of Table 4
+      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_aa_update(cols, gam, k, beta, g->phi0, g->aa_f, NP, s));
+      ++kaa;
+    }
     if (*g->host_err) { st = PF_E_GAMMA; break; }
     res->outer_iters = outer;
-    res->delta = *g->host_delta;
+    res->delta = delta;
+    delta_prev = delta;
     if (trace_level() > 0)
-      fprintf(stderr, "[pf] outer %d delta %.6e lin_total %d\n", outer, res->delta, res->lin_iters_total);
+      fprintf(stderr, "[pf] outer %d delta %.6e lin_total %d eta %.1e\n", outer, res->delta, res->lin_iters_total,
+              eta);
     if (res->delta <= o.tol_outer) break;
     if (outer == o.max_outer) st = PF_E_NOCONV;
   }

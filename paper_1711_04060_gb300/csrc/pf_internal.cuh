@@ -11,7 +11,7 @@ constexpr int TY = 8;            // tile height in y
 constexpr int NTHREADS = TX * TY;
 constexpr int ZC = 16;           // interior planes per z-chunk of a tile
 constexpr int MAXSP = 8;
-constexpr int NPART = 8;         // per-block partial values reduced by the last block
+constexpr int NPART = 16;        // per-block partial values reduced by the last block
 constexpr int HBX = TX + 8;      // TMA halo box: x from x0-4 (16-byte aligned start) to x0+TX+3
 constexpr int HBY = TY + 2;      // halo box rows y0-1 .. y0+TY
 
@@ -44,7 +44,9 @@ struct BicgState {
   double rnorm2, rinf;   // ||r||_2^2, ||r||_inf of the latest residual
   double snorm2, sinf;
   double tol;      // tolerance as given
-  double tol2;     // REL2: tol^2 * ||b||^2
+  double tol2;     // REL2: max(tol^2 ||b||^2, tol_r0^2 ||r0||^2)
+  double tol_r0;   // additional tolerance relative to the first residual of the solve (0: none)
+  double r0norm2;  // ||r0||_2^2 of the first residual computed since the state was reset (< 0: none yet)
   int norm;        // 0 REL2, 1 ABSINF
   int iter, max_iter;
   int done, status, sexit;
@@ -111,7 +113,9 @@ cudaError_t launch_pack(const void* src, void* dst, const Geom& g, int type, cud
 cudaError_t launch_unpack(const double* src, double* dst, const Geom& g, int count, cudaStream_t s);
 
 // ---- BiCGSTAB (Table 3) ----
-cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, cudaStream_t s);
+// keep_r0 != 0 keeps r0norm2 of the previous state (later refinement steps of one solve)
+cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, double tol_r0, int keep_r0,
+                             cudaStream_t s);
 cudaError_t launch_plane_bb(const double* b, const Geom& g, BicgState* st, cudaStream_t s);
 // r = r~ = b, p = v = t = 0 on interior nodes (x0 = 0); partials b.b, r.r, max|r|
 template <typename T>
@@ -141,6 +145,24 @@ cudaError_t launch_pf2_rhs(const double* psi, const uint8_t* solvent, const doub
 cudaError_t launch_relax(double* phi0, const double* phi, double omega, long n, double* part, unsigned int* ticket,
                          double* delta, cudaStream_t s);
 cudaError_t launch_scale(const double* a, double s, double* out, long n, cudaStream_t st);
+
+// ---- Anderson acceleration of the outer iteration (history of at most AA_MAX columns) ----
+constexpr int AA_MAX = 8;
+struct AAPtrs {
+  const double* dF[AA_MAX];
+  const double* dX[AA_MAX];
+};
+struct AACoef {
+  double g[AA_MAX];
+};
+cudaError_t launch_aa_residual(const double* gval, const double* x, double* f, double* fprev, double* xprev,
+                               double* dF, double* dX, int have_prev, long n, double* part, unsigned int* ticket,
+                               double* fmax, cudaStream_t s);
+// out[j] = dF_new . dF_j, out[AA_MAX + j] = dF_j . f for j < k
+cudaError_t launch_aa_dots(const AAPtrs& cols, int k, const double* dFnew, const double* f, long n, double* part,
+                           unsigned int* ticket, double* out, cudaStream_t s);
+cudaError_t launch_aa_update(const AAPtrs& cols, const AACoef& gam, int k, double beta, double* x, const double* f,
+                             long n, cudaStream_t s);
 cudaError_t launch_set_dirichlet(double* x, double lo, double hi, const Geom& g, cudaStream_t s);
 
 }  // namespace pf

@@ -9,8 +9,8 @@
 // y0+TY: the x start stays 16-byte aligned), the others as centre boxes.  Each plane's stencil input
 // (the BiCGSTAB direction p or s after the axpy and the Jacobi scaling) is computed once per node
 // into a ring of three shared planes; the planes below and above come from registers.  The axpy
-// updates (Table 3 steps 9, 13, 16, 17), the Jacobi scaling and the inner products (steps 4, 12, 15)
-// are fused into the two stencil kernels of an iteration.  Inner products are reduced by warp
+// updates of p, s, x and r (Table 3), the Jacobi scaling and the inner products that give rho, alpha
+// and omega are fused into the two stencil kernels of an iteration.  Inner products are reduced by warp
 // shuffles, a block tree and the last-arriving block over the per-block partials in fixed order.
 #include <math.h>
 #include <stdio.h>
@@ -509,12 +509,12 @@ struct OpB {
       st->status = 4;  // PF_E_BREAKDOWN, before x is touched
       st->done = 1;
     } else {
-      const double om = ts / tt;  // step 15
+      const double om = ts / tt;  // omega = t.s / t.t
       st->omega = om;
-      // r~.r_new with r_new = s - omega t (steps 17 and 4 of the next iteration): the next p is
+      // r~.r_new with r_new = s - omega t (the next rho): the next p is
       // formed in the same kernel as r_new, so its beta is taken from the exact identity
       const double rho_new = rs - om * rtt;
-      const double be = (om != 0.0) ? (rho_new / st->rho) * (st->alpha / om) : 0.0;  // step 8
+      const double be = (om != 0.0) ? (rho_new / st->rho) * (st->alpha / om) : 0.0;  // beta
       st->beta = isfinite(be) ? be : 0.0;
     }
     st->ticket = 0;
@@ -522,8 +522,8 @@ struct OpB {
 };
 
 // ------------------------------------------------------------------ phase C+A
-// s = r - alpha v, x += alpha M^-1 p + omega M^-1 s (step 16), r' = s - omega t (step 17),
-// p' = r' + beta (p - omega v) (step 9 of the next iteration), v' = A M^-1 p' (step 11).
+// s = r - alpha v, x += alpha M^-1 p + omega M^-1 s, r' = s - omega t, and for the next iteration
+// p' = r' + beta (p - omega v) and v' = A M^-1 p'.
 template <typename T_, bool UNI>
 struct OpCA {
   using T = T_;
@@ -653,10 +653,17 @@ struct OpCA {
       st->status = 4;
       return;
     }
-    st->rho = rr;         // step 4 of the next iteration
-    st->alpha = rr / rv;  // step 12 of the next iteration
+    st->rho = rr;         // rho of the next iteration
+    st->alpha = rr / rv;  // alpha of the next iteration
   }
 };
+
+// Squared 2-norm stop of a state whose residual has squared norm rr and right-hand side bb: the first
+// residual of a solve fixes r0norm2; the threshold is the larger of the b-relative and r0-relative ones.
+__device__ __forceinline__ void set_tol2(BicgState* st, double rr, double bb) {
+  if (!(st->r0norm2 >= 0.0)) st->r0norm2 = rr;
+  st->tol2 = fmax(st->tol * st->tol * bb, st->tol_r0 * st->tol_r0 * st->r0norm2);
+}
 
 // ------------------------------------------------------------------ FP64 residual b - A x
 template <bool UNI>
@@ -756,7 +763,7 @@ struct OpRes {
     st->bnorm2 = bb;
     st->rnorm2 = tot[0];
     st->rinf = tot[2];
-    st->tol2 = st->tol * st->tol * bb;
+    set_tol2(st, tot[0], bb);
     const bool conv = st->norm == 0 ? (tot[0] <= st->tol2) : (tot[2] < st->tol);
     if (a.init) {
       st->rho = tot[0];  // r~ = r0
@@ -810,7 +817,7 @@ __global__ void __launch_bounds__(NTHREADS) k_init_zero(const T* __restrict__ b,
   st->rho = tot[0];
   st->rnorm2 = tot[0];
   st->rinf = tot[1];
-  st->tol2 = st->tol * st->tol * bb;
+  set_tol2(st, tot[0], bb);
   st->alpha = st->omega = st->beta = 0.0;
   st->sexit = 0;
   st->iter = 0;
@@ -962,13 +969,17 @@ __global__ void k_plane_bb(const double* __restrict__ b, Geom g, BicgState* st) 
   if (threadIdx.x == 0) st->bnorm2 = red[0];
 }
 
-__global__ void k_set_state(BicgState* st, double tol, int norm, int max_iter) {
+__global__ void k_set_state(BicgState* st, double tol, int norm, int max_iter, double tol_r0, int keep_r0) {
+  const double r0 = keep_r0 ? st->r0norm2 : -1.0;
   BicgState s = {};
   s.tol = tol;
   s.norm = norm;
   s.max_iter = max_iter;
+  s.tol_r0 = tol_r0;
+  s.r0norm2 = r0;
   *st = s;
 }
+
 
 // ------------------------------------------------------------------ Eq. (1) pointwise step
 // With la_i = ln(v_i cB_i) - z_i phi - p_i ln Gamma^B, the void fraction Gamma = e^u solves
@@ -1243,8 +1254,9 @@ cudaError_t launch_add_f32(double* x, const float* d, long n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, cudaStream_t s) {
-  k_set_state<<<1, 1, 0, s>>>(st, tol, norm, max_iter);
+cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, double tol_r0, int keep_r0,
+                             cudaStream_t s) {
+  k_set_state<<<1, 1, 0, s>>>(st, tol, norm, max_iter, tol_r0, keep_r0);
   return cudaGetLastError();
 }
 
@@ -1486,3 +1498,103 @@ pf_status pf_fermi_noalloc(long n, const double* phi_V, const uint8_t* solvent, 
 }
 
 }  // extern "C"
+
+namespace pf {
+
+// ------------------------------------------------------------------ Anderson acceleration of the outer loop
+// f = g - x at the new outer iterate (g: the PF2 solution from x), the newest history columns
+// dF = f - f_prev and dX = x - x_prev (when have_prev), then f_prev <- f, x_prev <- x; the block maxima of
+// |f| go to part, the last block writes max |f| to *fmax.
+__global__ void __launch_bounds__(NTHREADS) k_aa_residual(const double* __restrict__ gval, const double* __restrict__ x,
+                                                          double* __restrict__ f, double* __restrict__ fprev,
+                                                          double* __restrict__ xprev, double* __restrict__ dF,
+                                                          double* __restrict__ dX, int have_prev, long n,
+                                                          double* part, unsigned int* ticket, double* fmax_out) {
+  __shared__ double scratch[NTHREADS];
+  double m = 0.0;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const double xc = x[c], fc = gval[c] - xc;
+    if (have_prev) {
+      dF[c] = fc - fprev[c];
+      dX[c] = xc - xprev[c];
+    }
+    f[c] = fc;
+    fprev[c] = fc;
+    xprev[c] = xc;
+    m = fmax(m, fabs(fc));
+  }
+  double vals[1] = {m};
+  block_partials<1>(vals, 1u, part, scratch);
+  if (!arrive_last(ticket)) return;
+  double tot[1];
+  total_partials<1>(part, 1u, tot, scratch);
+  if (threadIdx.x == 0) {
+    *fmax_out = tot[0];
+    *ticket = 0;
+  }
+}
+
+// Inner products of the Anderson least-squares problem: out[j] = dF_new . dF_j and out[AA_MAX + j] = dF_j . f
+// for the k active columns.
+__global__ void __launch_bounds__(NTHREADS) k_aa_dots(AAPtrs cols, int k, const double* __restrict__ dFnew,
+                                                      const double* __restrict__ f, long n, double* part,
+                                                      unsigned int* ticket, double* out) {
+  __shared__ double scratch[NTHREADS * 2 * AA_MAX];
+  double a[2 * AA_MAX];
+#pragma unroll
+  for (int j = 0; j < 2 * AA_MAX; ++j) a[j] = 0.0;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    const double dn = dFnew[c], fc = f[c];
+#pragma unroll
+    for (int j = 0; j < AA_MAX; ++j) {
+      if (j < k) {
+        const double d = cols.dF[j][c];
+        a[j] = fma(dn, d, a[j]);
+        a[AA_MAX + j] = fma(d, fc, a[AA_MAX + j]);
+      }
+    }
+  }
+  // the block partial vectors are reduced with the same fixed-order machinery as the solver's dots
+  block_partials<2 * AA_MAX>(a, 0u, part, scratch);
+  if (!arrive_last(ticket)) return;
+  double tot[2 * AA_MAX];
+  total_partials<2 * AA_MAX>(part, 0u, tot, scratch);
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < 2 * AA_MAX; ++j) out[j] = tot[j];
+    *ticket = 0;
+  }
+}
+
+// x <- x + beta f - sum_j gamma_j (dX_j + beta dF_j) over the k active columns.
+__global__ void k_aa_update(AAPtrs cols, AACoef gam, int k, double beta, double* __restrict__ x,
+                            const double* __restrict__ f, long n) {
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
+    double v = fma(beta, f[c], x[c]);
+#pragma unroll
+    for (int j = 0; j < AA_MAX; ++j)
+      if (j < k) v -= gam.g[j] * fma(beta, cols.dF[j][c], cols.dX[j][c]);
+    x[c] = v;
+  }
+}
+
+cudaError_t launch_aa_residual(const double* gval, const double* x, double* f, double* fprev, double* xprev,
+                               double* dF, double* dX, int have_prev, long n, double* part, unsigned int* ticket,
+                               double* fmax_out, cudaStream_t s) {
+  k_aa_residual<<<ew_blocks(n), NTHREADS, 0, s>>>(gval, x, f, fprev, xprev, dF, dX, have_prev, n, part, ticket,
+                                                  fmax_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aa_dots(const AAPtrs& cols, int k, const double* dFnew, const double* f, long n, double* part,
+                           unsigned int* ticket, double* out, cudaStream_t s) {
+  k_aa_dots<<<ew_blocks(n), NTHREADS, 0, s>>>(cols, k, dFnew, f, n, part, ticket, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aa_update(const AAPtrs& cols, const AACoef& gam, int k, double beta, double* x, const double* f,
+                             long n, cudaStream_t s) {
+  k_aa_update<<<ew_blocks(n), 256, 0, s>>>(cols, gam, k, beta, x, f, n);
+  return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -22,7 +22,7 @@
 
 #include "../../include/pf_gb300.h"
 
-size_t pf_internal_grid_bytes(int nx, int ny, int nz);  // pf_api.cu
+size_t pf_internal_grid_bytes(int nx, int ny, int nz, int accel_depth);  // pf_api.cu
 
 namespace {
 
@@ -146,7 +146,7 @@ pf_status pf_submit(pf_server* sv, const pf_request* q, uint64_t* ticket) {
   r->h = q->h_A;
   for (int a = 0; a < 3; ++a) r->origin[a] = q->origin_A[a];
   r->N = (long)q->nx * q->ny * q->nz;
-  r->bytes = pf_internal_grid_bytes(r->nx, r->ny, r->nz);
+  r->bytes = pf_internal_grid_bytes(r->nx, r->ny, r->nz, q->opts.accel_depth);
   if (r->bytes > sv->budget) {
     delete r;
     return PF_E_OOM;

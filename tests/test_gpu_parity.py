@@ -171,13 +171,13 @@ def test_absinf_stop_and_device_memory(api, orc):
     np.testing.assert_allclose(x.cpu().numpy(), ref["x"], atol=1e-8 * np.abs(ref["x"]).max())
 
 
-def _nl_compare(api, orc, prob, precision, tol_phi):
+def _nl_compare(api, orc, prob, precision, tol_phi, **accel):
     g = prob.grid
     ref = orc.pf_solve_problem(prob, tol_outer=1e-11, lin_tol=1e-12)
     assert ref["status"] == 0
     grid = api.Grid.for_problem(prob)
     prec = api.PF_FP64 if precision == "fp64" else api.PF_MIXED
-    out, rep = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=prec))
+    out, rep = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=prec, **accel))
     grid.close()
     assert rep["status"] == 0
     # potentials relative to their maximum, floored at the thermal voltage (a field-free bath has phi = 0)
@@ -198,6 +198,29 @@ def test_nonlinear_33_single_pore(api, orc, precision):
     rep, ref = _nl_compare(api, orc, W.config0(), precision, TOL_FP64 if precision == "fp64" else TOL_MIXED)
     if precision == "fp64":
         assert abs(rep["outer_iters"] - ref["report"]["outer_iters"]) <= 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("depth,forcing", [(5, 0.0), (5, 0.1), (1, 0.0), (0, 0.1)])
+def test_nonlinear_accelerated_same_fixed_point(api, orc, precision, depth, forcing):
+    """Anderson acceleration and the adaptive linear tolerance change the path, not the fixed point of
+    Table 4: the potential and concentrations agree with the oracle's relaxed iteration."""
+    rep, ref = _nl_compare(api, orc, W.config0(), precision, TOL_FP64 if precision == "fp64" else TOL_MIXED,
+                           accel_depth=depth, lin_forcing=forcing)
+    if depth >= 5:
+        assert rep["outer_iters"] < 0.6 * ref["report"]["outer_iters"]
+
+
+def test_nonlinear_options_rejected(api):
+    prob = W.channel_problem(9, box_half=4.0, slab_half=1.0, pores=((0, 0, 2.0),), n_charges=0)
+    grid = api.Grid.for_problem(prob)
+    try:
+        for bad in (dict(accel_depth=9), dict(accel_depth=-1), dict(lin_forcing=-1.0)):
+            with pytest.raises(api.PFError) as e:
+                grid.nonlinear_solve(api.nl_opts(**bad))
+            assert e.value.status == 1  # PF_E_INVAL
+    finally:
+        grid.close()
 
 
 @pytest.mark.parametrize("case", ["no_field", "lc0", "ragged", "calcium"])
