@@ -71,7 +71,13 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-accel", action="store_true", help="skip the Anderson-accelerated comparison solve")
     ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--accel-depth", type=int, default=0, help="Anderson depth of the timed solves (0: relaxation)")
+    ap.add_argument("--serve-requests", type=int, default=16, help="requests of the serving sample (0: skip)")
+    ap.add_argument("--serve-gap", type=float, default=0.25, help="mean inter-arrival time of the serving sample (s)")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     return ap.parse_args()
 
 
@@ -149,6 +155,17 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def iteration_gbps(prof, prec, n_int):
+    """Algorithmic bytes over device time of the two BiCGSTAB phase kernels of one precision, summed over the
+    variable-dielectric and PF1 operators."""
+    by, ms = 0.0, 0.0
+    for k in (f"b_{prec}", f"ca_{prec}", f"b_{prec}_pf1", f"ca_{prec}_pf1"):
+        cnt, kms = prof.get(k, (0, 0.0))
+        by += cnt * KERNEL_BYTES[k] * n_int
+        ms += kms
+    return round(by / (ms / 1e3) / 1e9, 1) if ms > 0 else None
 
 
 def kernel_traffic(kind):
@@ -234,8 +251,50 @@ def config_of(args):
     return {"workload": f"pf_{args.n}_four_pores_NaCaCl", "grid": f"{args.n}^3", "h_A": 64.0 / (args.n - 1),
             "species": "Na+ 0.1 M, Ca2+ 1 mM, Cl- 0.102 M, water 55.5 M", "charges": 48,
             "precision": args.precision, "tol_outer": args.tol_outer, "lin_tol": args.lin_tol,
-            "omega": 0.3, "l2": "inputs larger than L2 (working set > 1 GB)",
+            "omega": 0.3, "accel_depth": args.accel_depth, "l2": "inputs larger than L2 (working set > 1 GB)",
             "parallelism": f"replicas x{args.gpus}"}
+
+
+# ------------------------------------------------------------------ serving sample
+def serve_sample(api, args, precision):
+    """Replays the first requests of the Poisson request stream (edges 49..193, voltage and salt drawn per
+    request) against pf_submit / pf_poll at their arrival times; latency = completion - arrival."""
+    from paper_1711_04060_gb300 import workloads as W
+    reqs = W.request_stream(count=args.serve_requests, seed=4, mean_gap_s=args.serve_gap)
+    probs = [(t, make()) for t, _, make in reqs]
+    opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=precision,
+                       accel_depth=args.accel_depth)
+    qs = [api.make_request(p, opts) for _, p in probs]
+    srv = api.pf_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
+    lat, status, nodes = [], [], 0
+    try:
+        t0 = time.perf_counter()
+        pending = {}
+        nxt = 0
+        while nxt < len(qs) or pending:
+            now = time.perf_counter() - t0
+            while nxt < len(qs) and probs[nxt][0] <= now:
+                pending[api.pf_submit(srv, qs[nxt])] = nxt
+                nxt += 1
+            for tk in list(pending):
+                if api.pf_done(srv, tk):
+                    i = pending.pop(tk)
+                    done_t = time.perf_counter() - t0
+                    g = probs[i][1].grid
+                    _, _, rep = api.pf_poll(srv, tk, g.n, len(probs[i][1].species), allow=(3,))
+                    lat.append(done_t - probs[i][0])
+                    status.append(rep["status"])
+                    nodes += g.n
+            time.sleep(0.001)
+        span = time.perf_counter() - t0 - probs[0][0]
+    finally:
+        api.pf_server_destroy(srv)
+    lat = np.array(lat)
+    return {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
+            "solves_per_s": len(lat) / span, "mean_nodes": nodes / max(1, len(lat)),
+            "all_ok": bool(all(st == 0 for st in status)), "offered_per_s": 1.0 / args.serve_gap,
+            "slots": args.serve_slots, "budget_GB": args.serve_budget_gb}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -257,7 +316,7 @@ def run_ours(args):
     out = {k: torch.zeros(m, dtype=torch.float64, device=dev)
            for k, m in (("phi_V", N), ("C_M", ns * N), ("S", N), ("Gamma", N))}
     prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
-    opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec)
+    opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, accel_depth=args.accel_depth)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -344,11 +403,14 @@ def run_ours(args):
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        grid.profile(True)
         e0.record(stream)
         fp64_rep = solve(o64, out64)
         e1.record(stream)
         e1.synchronize()
         ms64 = e0.elapsed_time(e1)
+        prof64 = grid.profile_get()
+        grid.profile(False)
         phi64 = out64["phi_V"].cpu().numpy()
         C64 = out64["C_M"].cpu().numpy().reshape(ns, N)
         Cm = C_mixed.reshape(ns, N)
@@ -358,6 +420,30 @@ def run_ours(args):
             "phi_rel": float(np.abs(phi_mixed - phi64).max() / np.abs(phi64).max()),
             "conc_rel": float(max(np.abs(Cm[i] - C64[i]).max() / C64[i].max() for i in range(ns)))}
         line["mixed_speedup_vs_fp64"] = value / world / (1e3 / ms64)
+        line["bicgstab_iteration_GBps"] = {"fp32_inner": iteration_gbps(prof, "fp32", n_int),
+                                           "fp64": iteration_gbps(prof64, "fp64", n_int),
+                                           "peak": peak, "unit": "GB/s"}
+
+    # Anderson-accelerated solve of the same workload (same fixed point and stop test)
+    if args.accel_depth == 0 and not args.no_accel:
+        oa = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, accel_depth=5)
+        outa = {k: torch.zeros_like(v) for k, v in out.items()}
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        arep = solve(oa, outa)
+        e1.record(stream)
+        e1.synchronize()
+        msa = e0.elapsed_time(e1)
+        phia = outa["phi_V"].cpu().numpy()
+        Ca = outa["C_M"].cpu().numpy().reshape(ns, N)
+        Cm = C_mixed.reshape(ns, N)
+        line["anderson5"] = {"value": 1e3 / msa, "unit": UNIT, "ms_per_step": msa, "outer_iters": arep["outer_iters"],
+                             "lin_iters": arep["lin_iters_total"], "status": arep["status"],
+                             "phi_rel_vs_relaxation": float(np.abs(phia - phi_mixed).max() / np.abs(phi_mixed).max()),
+                             "conc_rel_vs_relaxation": float(max(np.abs(Ca[i] - Cm[i]).max() / Cm[i].max()
+                                                                 for i in range(ns)))}
 
     # end to end through the public API with host buffers
     if not args.no_e2e:
@@ -379,6 +465,12 @@ def run_ours(args):
         line["e2e"] = {"value": world * max(1, args.steps) / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)}
     grid.close()
+
+    # serving: Poisson arrivals of mixed-size requests through pf_submit / pf_poll
+    if args.serve_requests > 0 and world == 1:
+        line["serving"] = {"mixed": serve_sample(api, args, api.PF_MIXED)}
+        if not args.no_fp64:
+            line["serving"]["fp64"] = serve_sample(api, args, api.PF_FP64)
 
     # CPU oracle on a bounded sample (rank 0, one GPU only)
     if rank == 0 and world == 1 and not args.no_cpu:

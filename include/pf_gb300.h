@@ -277,7 +277,8 @@ pf_status pf_submit(pf_server* s, const pf_request* req, uint64_t* ticket);
 
 /* *done = 1 when the ticket has finished: the outputs (host arrays in `res`, `res->mem` must be
  * PF_MEM_HOST) and the report are written and the ticket is released; returns the solve's
- * status.  *done = 0 and PF_PENDING while it is queued or running. */
+ * status.  *done = 0 and PF_PENDING while it is queued or running.  With res == NULL the call
+ * only reports *done (PF_OK when finished) and keeps the result for a later poll. */
 pf_status pf_poll(pf_server* s, uint64_t ticket, pf_result* res, int* done);
 
 /* Stops the scheduler, cancels queued requests and frees everything. */

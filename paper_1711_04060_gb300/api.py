@@ -217,10 +217,19 @@ def pf_submit(server, request):
     return t.value
 
 
-def pf_poll(server, ticket, n_nodes, n_species, allow=()):
-    """(done, outputs-or-None, report-or-None) for a ticket; outputs are numpy arrays."""
-    out = {"phi_V": np.zeros(n_nodes), "C_M": np.zeros(n_species * n_nodes), "S": np.zeros(n_nodes),
-           "Gamma": np.zeros(n_nodes)}
+def pf_done(server, ticket):
+    """True when the ticket has finished (its result stays for pf_poll)."""
+    done = ctypes.c_int(0)
+    _check(B.load().pf_poll(server, ticket, None, ctypes.byref(done)), allow=(PF_PENDING,))
+    return bool(done.value)
+
+
+def pf_poll(server, ticket, n_nodes, n_species, allow=(), out=None):
+    """(done, outputs-or-None, report-or-None) for a ticket; outputs are numpy arrays (those of `out`, a dict
+    with phi_V, C_M, S and Gamma, when given)."""
+    if out is None:
+        out = {"phi_V": np.zeros(n_nodes), "C_M": np.zeros(n_species * n_nodes), "S": np.zeros(n_nodes),
+               "Gamma": np.zeros(n_nodes)}
     res = B.pf_result()
     for k in out:
         setattr(res, k, out[k].ctypes.data)

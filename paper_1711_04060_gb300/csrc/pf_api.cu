@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -99,6 +100,7 @@ struct pf_grid {
   double* delta = nullptr;
   unsigned int* ticket = nullptr;
   double* host_delta = nullptr;
+  void* hostblk = nullptr;   // pinned block holding host_st, host_err, host_delta and aa_host
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // TMA descriptors, keyed by (array, halo box?)
   std::map<std::pair<const void*, int>, CUtensorMap> maps;
@@ -114,13 +116,16 @@ struct pf_grid {
 
 namespace {
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the grid's stream), so creating and
+// destroying grids does not synchronise the device while other grids run on other streams.
 template <typename T>
 pf_status dalloc(pf_grid* g, T** p, size_t count) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
+  const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 1;
+  cudaError_t e = cudaMallocAsync(&q, bytes, g->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(PF_E_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes failed: " +
+    return fail(PF_E_OOM, std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
                               cudaGetErrorString(e));
   }
   g->allocs.push_back(q);
@@ -128,55 +133,91 @@ pf_status dalloc(pf_grid* g, T** p, size_t count) {
   return PF_OK;
 }
 
+// Small pinned host blocks (for the scalars the host reads back) come from a process-wide free list and are
+// never returned to the driver, so no grid's teardown waits on the device.
+constexpr size_t PINNED_BLOCK = 4096;
+std::mutex g_pinned_mu;
+std::vector<void*> g_pinned_free;
+
+void* pinned_get() {
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  if (g_pinned_free.empty()) {
+    unsigned char* slab = nullptr;
+    if (cudaMallocHost(&slab, 64 * PINNED_BLOCK) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = 63; i >= 0; --i) g_pinned_free.push_back(slab + i * PINNED_BLOCK);
+  }
+  void* b = g_pinned_free.back();
+  g_pinned_free.pop_back();
+  memset(b, 0, PINNED_BLOCK);
+  return b;
+}
+
+void pinned_put(void* b) {
+  if (!b) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.push_back(b);
+}
+
 void free_all(pf_grid* g) {
-  if (g->dch) cudaFree(g->dch);
+  if (g->dch) cudaFreeAsync(g->dch, g->stream);
   g->dch = nullptr;
   for (cudaEvent_t e : g->pool) cudaEventDestroy(e);
   g->pool.clear();
-  for (void* q : g->allocs) cudaFree(q);
+  for (void* q : g->allocs) cudaFreeAsync(q, g->stream);
   g->allocs.clear();
-  if (g->host_st) cudaFreeHost(g->host_st);
-  if (g->host_err) cudaFreeHost(g->host_err);
-  if (g->host_delta) cudaFreeHost(g->host_delta);
-  if (g->aa_host) cudaFreeHost(g->aa_host);
-  g->aa_host = nullptr;
+  pinned_put(g->hostblk);
+  g->hostblk = nullptr;
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
   g->host_st = nullptr;
   g->host_err = nullptr;
   g->host_delta = nullptr;
+  g->aa_host = nullptr;
 }
 
+// All arrays of a grid are carved from one allocation (each start 256-byte aligned, as TMA needs 16).
 pf_status allocate(pf_grid* g) {
   const long NP = g->geom.np;
   double** d64[] = {&g->eps, &g->wE, &g->wN, &g->wU, &g->dsum, &g->ffix, &g->diagP, &g->dinvP, &g->diag2,
                     &g->dinv2, &g->sig, &g->dinv1, &g->r64[0], &g->r64[1], &g->p64[0], &g->p64[1], &g->v64[0],
                     &g->v64[1], &g->rt64, &g->t64, &g->xb, &g->bb, &g->stage, &g->phi0, &g->phi, &g->psi, &g->b1,
                     &g->c2, &g->b2, &g->Sbuf, &g->Gbuf, &g->ulast};
-  for (double** p : d64) PF_TRY(dalloc(g, p, NP));
-  PF_TRY(dalloc(g, &g->Cbuf, (size_t)NP * pf::MAXSP));
   float** d32[] = {&g->wE32, &g->wN32, &g->wU32, &g->dinvP32, &g->dinv2_32, &g->dinv1_32, &g->r32[0], &g->r32[1],
                    &g->p32[0], &g->p32[1], &g->v32[0], &g->v32[1], &g->rt32, &g->t32, &g->d32, &g->b32};
-  for (float** p : d32) PF_TRY(dalloc(g, p, NP));
-  PF_TRY(dalloc(g, &g->solvent, NP));
-  PF_TRY(dalloc(g, &g->part, (size_t)pf::max_partial_blocks() * pf::NPART));
-  PF_TRY(dalloc(g, &g->st, 1));
-  PF_TRY(dalloc(g, &g->st2, 1));
-  PF_TRY(dalloc(g, &g->err, 1));
-  PF_TRY(dalloc(g, &g->delta, 1));
-  PF_TRY(dalloc(g, &g->ticket, 1));
-  PF_CK(cudaMallocHost(&g->host_st, sizeof(BicgState)));
-  PF_CK(cudaMallocHost(&g->host_err, sizeof(int)));
-  PF_CK(cudaMallocHost(&g->host_delta, sizeof(double)));
+  std::vector<std::pair<void**, size_t>> parts;
+  for (double** p : d64) parts.push_back({reinterpret_cast<void**>(p), NP * sizeof(double)});
+  parts.push_back({reinterpret_cast<void**>(&g->Cbuf), (size_t)NP * pf::MAXSP * sizeof(double)});
+  for (float** p : d32) parts.push_back({reinterpret_cast<void**>(p), NP * sizeof(float)});
+  parts.push_back({reinterpret_cast<void**>(&g->solvent), (size_t)NP});
+  parts.push_back({reinterpret_cast<void**>(&g->part), (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double)});
+  parts.push_back({reinterpret_cast<void**>(&g->st), sizeof(BicgState)});
+  parts.push_back({reinterpret_cast<void**>(&g->st2), sizeof(BicgState)});
+  parts.push_back({reinterpret_cast<void**>(&g->err), sizeof(int)});
+  parts.push_back({reinterpret_cast<void**>(&g->delta), sizeof(double)});
+  parts.push_back({reinterpret_cast<void**>(&g->ticket), sizeof(unsigned int)});
+  size_t total = 0;
+  for (auto& q : parts) total += (q.second + 255) / 256 * 256;
+  unsigned char* base = nullptr;
+  PF_TRY(dalloc(g, &base, total));
+  size_t off = 0;
+  for (auto& q : parts) {
+    *q.first = base + off;
+    off += (q.second + 255) / 256 * 256;
+  }
+  g->hostblk = pinned_get();
+  if (!g->hostblk) return fail(PF_E_OOM, "pinned host allocation failed");
+  static_assert(sizeof(BicgState) <= 512, "the pinned block layout holds the state in 512 bytes");
+  unsigned char* hb = static_cast<unsigned char*>(g->hostblk);
+  g->host_st = reinterpret_cast<BicgState*>(hb);
+  g->host_err = reinterpret_cast<int*>(hb + 512);
+  g->host_delta = reinterpret_cast<double*>(hb + 1024);
+  g->aa_host = reinterpret_cast<double*>(hb + 1536);
   // every array starts at zero: the pad columns and the Krylov vectors on the Dirichlet planes, which no
   // kernel writes, stay zero
-  for (double** p : d64) PF_CK(cudaMemsetAsync(*p, 0, NP * sizeof(double), g->stream));
-  PF_CK(cudaMemsetAsync(g->Cbuf, 0, (size_t)NP * pf::MAXSP * sizeof(double), g->stream));
-  for (float** p : d32) PF_CK(cudaMemsetAsync(*p, 0, NP * sizeof(float), g->stream));
-  PF_CK(cudaMemsetAsync(g->solvent, 0, NP, g->stream));
-  PF_CK(cudaMemsetAsync(g->st, 0, sizeof(BicgState), g->stream));
-  PF_CK(cudaMemsetAsync(g->st2, 0, sizeof(BicgState), g->stream));
-  PF_CK(cudaMemsetAsync(g->ticket, 0, sizeof(unsigned int), g->stream));
+  PF_CK(cudaMemsetAsync(base, 0, total, g->stream));
   PF_CK(cudaEventCreate(&g->ev0));
   PF_CK(cudaEventCreate(&g->ev1));
   g->pool.resize(2 * PROF_SLOTS, nullptr);
@@ -560,7 +601,6 @@ pf_status ensure_aa(pf_grid* g, int m) {
     PF_TRY(dalloc(g, &g->aa_fprev, NP));
     PF_TRY(dalloc(g, &g->aa_xprev, NP));
     PF_TRY(dalloc(g, &g->aa_out, 2 * pf::AA_MAX));
-    PF_CK(cudaMallocHost(&g->aa_host, 2 * pf::AA_MAX * sizeof(double)));
   }
   for (; g->aa_alloc < m; ++g->aa_alloc) {
     PF_TRY(dalloc(g, &g->aa_dF[g->aa_alloc], NP));
@@ -764,12 +804,12 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
   PF_TRY(pack_in(g, c->eps, PF_MEM_HOST, g->eps, 0));
   PF_TRY(pack_in(g, c->solvent, PF_MEM_HOST, g->solvent, 1));
   if (g->dch) {
-    cudaFree(g->dch);
+    cudaFreeAsync(g->dch, g->stream);
     g->dch = nullptr;
   }
   g->nq = c->n_charges;
   if (g->nq > 0) {
-    PF_CK(cudaMalloc(&g->dch, sizeof(double) * 4 * g->nq));
+    PF_CK(cudaMallocAsync(&g->dch, sizeof(double) * 4 * g->nq, g->stream));
     PF_CK(cudaMemcpyAsync(g->dch, c->charges, sizeof(double) * 4 * g->nq, cudaMemcpyHostToDevice, g->stream));
   }
   PF_TRY(build_operators(g));

@@ -171,7 +171,7 @@ pf_status pf_submit(pf_server* sv, const pf_request* q, uint64_t* ticket) {
 }
 
 pf_status pf_poll(pf_server* sv, uint64_t ticket, pf_result* res, int* done) {
-  if (!sv || !res || !done) return PF_E_INVAL;
+  if (!sv || !done) return PF_E_INVAL;
   std::lock_guard<std::mutex> lk(sv->mu);
   auto it = sv->all.find(ticket);
   if (it == sv->all.end()) return PF_E_INVAL;
@@ -179,6 +179,10 @@ pf_status pf_poll(pf_server* sv, uint64_t ticket, pf_result* res, int* done) {
   if (!r->done) {
     *done = 0;
     return PF_PENDING;
+  }
+  if (!res) {
+    *done = 1;
+    return PF_OK;
   }
   if (res->mem != PF_MEM_HOST) return PF_E_INVAL;
   *done = 1;
