@@ -251,12 +251,60 @@ pf_status pf_destroy_grid(pf_grid* g);
 /* Message of the calling thread's last failing call ("" if none). */
 const char* pf_last_error(void);
 
+/* ---- batched solves: many independent problems in shared launches -------------------
+ * A batch solves the problems already set on `count` grids (pf_create_grid + pf_set_coeffs,
+ * any sizes) together: the nonlinear iteration of Table 4 runs for every grid in lockstep
+ * (each grid stops on its own test), and each BiCGSTAB phase (Table 3) and each FP64 residual
+ * of all grids still iterating is ONE launch of a batched stencil kernel in which every grid
+ * owns nblk = ceil(tiles / tiles_per_block) blocks; the chunks of BiCGSTAB iterations between
+ * host checks are replayed as a captured CUDA graph.  A grid's arithmetic and reduction order
+ * depend only on its own size and tiles_per_block, so a problem's result is bitwise the same
+ * in any batch with the same tiles_per_block; against pf_nonlinear_solve (another block count)
+ * it agrees to the solver tolerance.  Not in the paper.
+ *
+ * The batch borrows the grids (they must outlive it and must not be used by another call while
+ * a batch call runs); its work is queued on cuda_stream, ordered after the work queued on each
+ * grid's stream before the call, and the grids' streams wait for it afterwards. */
+typedef struct pf_batch pf_batch;
+
+#define PF_BATCH_TUNE_MAX 8
+/* Autotuner record: candidate tiles-per-block values and the device time (ms) of one timed
+ * prime + 4 BiCGSTAB iterations of the batch's FP32 Poisson operators for each; chosen = the value in use. */
+typedef struct {
+  int n;
+  int tiles_per_block[PF_BATCH_TUNE_MAX];
+  float ms[PF_BATCH_TUNE_MAX];
+  int chosen;
+} pf_batch_tune;
+
+/* PF_E_INVAL for count < 1, a NULL or repeated grid; PF_E_OOM if the launch tables cannot be allocated. */
+pf_status pf_batch_create(pf_grid* const* grids, int count, void* cuda_stream, pf_batch** out);
+
+/* tiles_per_block >= 1 pins the block split (reproducible results across runs); 0 makes the next
+ * solve run the autotuner first (the default). */
+pf_status pf_batch_set_tiles_per_block(pf_batch* b, int tiles_per_block);
+
+/* Runs the autotuner now (needs the coefficients on every grid); *out (may be NULL) gets its record.
+ * It uses the grids' FP32 scratch vectors, which every solve re-initialises. */
+pf_status pf_batch_autotune(pf_batch* b, pf_batch_tune* out);
+pf_status pf_batch_get_tune(pf_batch* b, pf_batch_tune* out);
+
+/* pf_nonlinear_solve for every grid of the batch with the same options; results[i] (count entries)
+ * receives grid i's outputs and report, results[i].time_ms the whole batch's device time.  Returns
+ * PF_OK when every problem converged, else the first failing status (each results[i].status holds
+ * its own).  accel_depth and lin_forcing work per grid as in pf_nonlinear_solve. */
+pf_status pf_batch_nonlinear_solve(pf_batch* b, const pf_nl_opts* opts, pf_result* results);
+
+/* Frees the batch (not its grids). */
+pf_status pf_batch_destroy(pf_batch* b);
+
 /* ---- serving: continuous batching of PF solves -------------------------------------
  * A server admits submitted problems while their device state fits the HBM budget and a
- * slot is free, runs every admitted problem concurrently (each on its own stream, interleaved
- * outer iteration by outer iteration by a host scheduler thread), and frees the state of a
- * finished problem as soon as it is polled.  Results equal those of pf_nonlinear_solve on
- * the same problem. */
+ * slot is free; each slot is a worker thread with its own CUDA stream, so admitted problems
+ * run concurrently on the device.  A worker creates the grid (stream-ordered allocation),
+ * solves it exactly as pf_nonlinear_solve does, copies the outputs to host memory and frees
+ * the device state at once, returning its bytes to the budget.  Results equal those of
+ * pf_nonlinear_solve on the same problem. */
 typedef struct pf_server pf_server;
 
 typedef struct {

@@ -69,6 +69,14 @@ class pf_request(ctypes.Structure):
                 ("opts", pf_nl_opts)]
 
 
+PF_BATCH_TUNE_MAX = 8
+
+
+class pf_batch_tune(ctypes.Structure):
+    _fields_ = [("n", _I), ("tiles_per_block", _I * PF_BATCH_TUNE_MAX), ("ms", ctypes.c_float * PF_BATCH_TUNE_MAX),
+                ("chosen", _I)]
+
+
 # names declared in include/pf_gb300.h, with their ctypes signatures
 SIGNATURES = {
     "pf_default_solve_opts": (None, [ctypes.POINTER(pf_solve_opts)]),
@@ -83,6 +91,12 @@ SIGNATURES = {
     "pf_profile_get": (_I, [_VP, ctypes.POINTER(pf_profile)]),
     "pf_last_error": (ctypes.c_char_p, []),
     "pf_fermi_noalloc": (_I, [ctypes.c_long, _VP, _VP, _I, ctypes.POINTER(pf_species), _D, _VP, _VP, _VP, _VP]),
+    "pf_batch_create": (_I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
+    "pf_batch_set_tiles_per_block": (_I, [_VP, _I]),
+    "pf_batch_autotune": (_I, [_VP, ctypes.POINTER(pf_batch_tune)]),
+    "pf_batch_get_tune": (_I, [_VP, ctypes.POINTER(pf_batch_tune)]),
+    "pf_batch_nonlinear_solve": (_I, [_VP, ctypes.POINTER(pf_nl_opts), ctypes.POINTER(pf_result)]),
+    "pf_batch_destroy": (_I, [_VP]),
     "pf_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_VP)]),
     "pf_submit": (_I, [_VP, ctypes.POINTER(pf_request), ctypes.POINTER(ctypes.c_uint64)]),
     "pf_poll": (_I, [_VP, ctypes.c_uint64, ctypes.POINTER(pf_result), ctypes.POINTER(_I)]),

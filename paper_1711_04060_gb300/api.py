@@ -131,13 +131,11 @@ def pf_linear_solve(grid, op, b, x, opts=None, allow=()):
             "residual": rep.residual, "time_ms": rep.time_ms}
 
 
-def pf_nonlinear_solve(grid, n_nodes, n_species, opts=None, out=None, allow=()):
-    """Runs the PF iteration; `out` maps phi_V/C_M/S/Gamma/Psi to preallocated arrays (numpy or CUDA
-    tensors, all of one kind); by default fresh numpy arrays are returned."""
+def _result_for(res, n_nodes, n_species, out):
+    """Fills a pf_result's output pointers from `out` (fresh numpy arrays when None); returns `out`."""
     if out is None:
         out = {"phi_V": np.zeros(n_nodes), "C_M": np.zeros(n_species * n_nodes), "S": np.zeros(n_nodes),
                "Gamma": np.zeros(n_nodes), "Psi": np.zeros(n_nodes)}
-    res = B.pf_result()
     mems = set()
     for k in ("phi_V", "C_M", "S", "Gamma", "Psi"):
         if out.get(k) is not None:
@@ -147,11 +145,67 @@ def pf_nonlinear_solve(grid, n_nodes, n_species, opts=None, out=None, allow=()):
     if len(mems) > 1:
         raise TypeError("outputs must all be host or all be device arrays")
     res.mem = mems.pop() if mems else PF_MEM_HOST
+    return out
+
+
+def _report(res):
+    return {"status": res.status, "outer_iters": res.outer_iters, "lin_iters_total": res.lin_iters_total,
+            "lin_iters_first": res.lin_iters_first, "delta": res.delta, "time_ms": res.time_ms}
+
+
+def pf_nonlinear_solve(grid, n_nodes, n_species, opts=None, out=None, allow=()):
+    """Runs the PF iteration; `out` maps phi_V/C_M/S/Gamma/Psi to preallocated arrays (numpy or CUDA
+    tensors, all of one kind); by default fresh numpy arrays are returned."""
+    res = B.pf_result()
+    out = _result_for(res, n_nodes, n_species, out)
     st = B.load().pf_nonlinear_solve(grid, ctypes.byref(opts) if opts is not None else None, ctypes.byref(res))
     _check(st, allow)
-    rep = {"status": res.status, "outer_iters": res.outer_iters, "lin_iters_total": res.lin_iters_total,
-           "lin_iters_first": res.lin_iters_first, "delta": res.delta, "time_ms": res.time_ms}
-    return out, rep
+    return out, _report(res)
+
+
+def pf_batch_create(grid_handles, cuda_stream=None):
+    arr = (ctypes.c_void_p * len(grid_handles))(*[g.value for g in grid_handles])
+    h = ctypes.c_void_p()
+    stream = _torch_stream() if cuda_stream is None else ctypes.c_void_p(cuda_stream)
+    _check(B.load().pf_batch_create(arr, len(grid_handles), stream, ctypes.byref(h)))
+    return h
+
+
+def pf_batch_set_tiles_per_block(batch, tiles_per_block):
+    _check(B.load().pf_batch_set_tiles_per_block(batch, int(tiles_per_block)))
+
+
+def _tune_dict(t):
+    return {"tiles_per_block": [t.tiles_per_block[i] for i in range(t.n)], "ms": [t.ms[i] for i in range(t.n)],
+            "chosen": t.chosen}
+
+
+def pf_batch_autotune(batch):
+    t = B.pf_batch_tune()
+    _check(B.load().pf_batch_autotune(batch, ctypes.byref(t)))
+    return _tune_dict(t)
+
+
+def pf_batch_get_tune(batch):
+    t = B.pf_batch_tune()
+    _check(B.load().pf_batch_get_tune(batch, ctypes.byref(t)))
+    return _tune_dict(t)
+
+
+def pf_batch_nonlinear_solve(batch, sizes, opts=None, outs=None, allow=()):
+    """sizes: [(n_nodes, n_species)] per grid; outs: per-grid output dicts as for pf_nonlinear_solve (or None).
+    Returns [(out, report)] in batch order."""
+    res = (B.pf_result * len(sizes))()
+    outs = outs if outs is not None else [None] * len(sizes)
+    outs = [_result_for(res[i], n, ns, outs[i]) for i, (n, ns) in enumerate(sizes)]
+    st = B.load().pf_batch_nonlinear_solve(batch, ctypes.byref(opts) if opts is not None else None, res)
+    _check(st, allow)
+    return [(outs[i], _report(res[i])) for i in range(len(sizes))]
+
+
+def pf_batch_destroy(batch):
+    if batch is not None and batch.value:
+        _check(B.load().pf_batch_destroy(batch))
 
 
 def pf_destroy_grid(grid):
@@ -249,7 +303,40 @@ def pf_server_destroy(server):
         _check(B.load().pf_server_destroy(server))
 
 
-# ---------------------------------------------------------------- convenience wrapper
+# ---------------------------------------------------------------- convenience wrappers
+class Batch:
+    """Owns one pf_batch over a list of Grid objects (which it keeps alive)."""
+
+    def __init__(self, grids, cuda_stream=None, tiles_per_block=0):
+        self.grids = list(grids)
+        self.handle = pf_batch_create([g.handle for g in self.grids], cuda_stream)
+        if tiles_per_block:
+            pf_batch_set_tiles_per_block(self.handle, tiles_per_block)
+
+    def autotune(self):
+        return pf_batch_autotune(self.handle)
+
+    def tune(self):
+        return pf_batch_get_tune(self.handle)
+
+    def set_tiles_per_block(self, tiles_per_block):
+        pf_batch_set_tiles_per_block(self.handle, tiles_per_block)
+
+    def nonlinear_solve(self, opts=None, outs=None, allow=()):
+        return pf_batch_nonlinear_solve(self.handle, [(g.n, g.n_species) for g in self.grids], opts, outs, allow)
+
+    def close(self):
+        pf_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None:
+                self.close()
+        except Exception:
+            pass
+
+
 class Grid:
     """Owns one pf_grid handle."""
 

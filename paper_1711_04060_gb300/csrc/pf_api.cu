@@ -17,19 +17,15 @@
 #include <vector>
 
 #include "../../include/pf_gb300.h"
-#include "pf_internal.cuh"
+#include "pf_grid.cuh"
 
 using pf::BicgState;
 
-namespace {
+using namespace pfi;
+
+namespace pfi {
 
 thread_local std::string g_err;
-
-// Table 1 constants
-constexpr double KB = 1.38e-23;        // J/K
-constexpr double QE = 1.602e-19;       // C
-constexpr double EPS0 = 8.85e-12;      // F/m (8.85e-14 F/cm)
-constexpr double NAVO = 6.02214076e23; // 1/mol (SI value; the paper does not print it)
 
 pf_status fail(pf_status s, const std::string& msg) {
   g_err = msg;
@@ -41,97 +37,19 @@ pf_status cuda_fail(cudaError_t e, const char* what) {
   return PF_E_CUDA;
 }
 
-#define PF_CK(call)                                        \
-  do {                                                     \
-    cudaError_t e_ = (call);                               \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
-  } while (0)
-
-#define PF_TRY(call)                    \
-  do {                                  \
-    pf_status s_ = (call);              \
-    if (s_ != PF_OK) return s_;         \
-  } while (0)
-
-constexpr int CHUNK = 8;         // BiCGSTAB iterations launched between two host checks of the done flag
-constexpr int INNER_CAP = 1000;  // FP32 iterations per refinement step at most
-constexpr int PROF_SLOTS = 64;   // timed launches between two resolutions of the profiling events
-constexpr unsigned long long WAIT_LIMIT = 4000000000ull;  // clock cycles (about 2 s) per TMA stage wait
-
-}  // namespace
-
-struct pf_grid {
-  int nx = 0, ny = 0, nz = 0;
-  long N = 0;   // nodes
-  pf::Geom geom{};
-  double h = 1.0, origin[3] = {0, 0, 0};
-  cudaStream_t stream = nullptr;
-  pf::Launch L{};
-  bool have_coeffs = false;
-  // problem constants
-  double eps_s = 78.5, lc = 0.0, T = 298.15, Tv = 0.0, lam = 0.0, lo_hat = 0.0, hi_hat = 0.0, molar = 0.0;
-  pf::SpeciesParams sp{};
-  // device arrays (padded layout)
-  std::vector<void*> allocs;
-  double *eps = nullptr, *wE = nullptr, *wN = nullptr, *wU = nullptr, *dsum = nullptr, *ffix = nullptr;
-  uint8_t* solvent = nullptr;
-  double *diagP = nullptr, *dinvP = nullptr, *diag2 = nullptr, *dinv2 = nullptr, *sig = nullptr, *dinv1 = nullptr;
-  float *wE32 = nullptr, *wN32 = nullptr, *wU32 = nullptr, *dinvP32 = nullptr, *dinv2_32 = nullptr,
-        *dinv1_32 = nullptr;
-  double *r64[2] = {nullptr, nullptr}, *p64[2] = {nullptr, nullptr}, *v64[2] = {nullptr, nullptr};
-  double *rt64 = nullptr, *t64 = nullptr;
-  float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr}, *v32[2] = {nullptr, nullptr};
-  float *rt32 = nullptr, *t32 = nullptr, *d32 = nullptr, *b32 = nullptr;
-  double *xb = nullptr, *bb = nullptr, *stage = nullptr;
-  double *phi0 = nullptr, *phi = nullptr, *psi = nullptr, *b1 = nullptr, *c2 = nullptr, *b2 = nullptr;
-  double *Cbuf = nullptr, *Sbuf = nullptr, *Gbuf = nullptr, *ulast = nullptr;
-  double* part = nullptr;
-  // Anderson acceleration of the outer loop (allocated on first use)
-  int aa_alloc = 0;
-  double *aa_f = nullptr, *aa_fprev = nullptr, *aa_xprev = nullptr, *aa_out = nullptr, *aa_host = nullptr;
-  double *aa_dF[pf::AA_MAX] = {}, *aa_dX[pf::AA_MAX] = {};
-  double* dch = nullptr;     // fixed charges (x, y, z, q) on the device
-  int nq = 0;
-  BicgState* st = nullptr;   // FP64 solve / refinement state
-  BicgState* st2 = nullptr;  // FP32 inner solve state
-  BicgState* host_st = nullptr;  // pinned mirror
-  int* err = nullptr;        // device error flag
-  int* host_err = nullptr;   // pinned
-  double* delta = nullptr;
-  unsigned int* ticket = nullptr;
-  double* host_delta = nullptr;
-  void* hostblk = nullptr;   // pinned block holding host_st, host_err, host_delta and aa_host
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  // TMA descriptors, keyed by (array, halo box?)
-  std::map<std::pair<const void*, int>, CUtensorMap> maps;
-  // profiling: event pairs around launches, resolved at the next host synchronisation
-  int prof_on = 0;
-  long long launches = 0;
-  long long pcount[PF_PROF_KINDS] = {};
-  double pms[PF_PROF_KINDS] = {};
-  std::vector<cudaEvent_t> pool;
-  std::vector<int> pkind;
-  int np = 0;
-};
+}  // namespace pfi
 
 namespace {
 
-// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the grid's stream), so creating and
-// destroying grids does not synchronise the device while other grids run on other streams.
-template <typename T>
-pf_status dalloc(pf_grid* g, T** p, size_t count) {
-  void* q = nullptr;
-  const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 1;
-  cudaError_t e = cudaMallocAsync(&q, bytes, g->stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(PF_E_OOM, std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
-                              cudaGetErrorString(e));
-  }
-  g->allocs.push_back(q);
-  *p = static_cast<T*>(q);
-  return PF_OK;
-}
+// Table 1 constants
+constexpr double KB = 1.38e-23;        // J/K
+constexpr double QE = 1.602e-19;       // C
+constexpr double EPS0 = 8.85e-12;      // F/m (8.85e-14 F/cm)
+constexpr double NAVO = 6.02214076e23; // 1/mol (SI value; the paper does not print it)
+
+}  // namespace
+
+namespace pfi {
 
 // Small pinned host blocks (for the scalars the host reads back) come from a process-wide free list and are
 // never returned to the driver, so no grid's teardown waits on the device.
@@ -268,49 +186,9 @@ void prof_end(pf_grid* g, int slot, int kind) {
   g->np = slot + 1;
 }
 
-#define PF_LAUNCH(g, kind, call)                  \
-  do {                                            \
-    const int slot_ = prof_begin((g), 1);         \
-    PF_CK(call);                                  \
-    prof_end((g), slot_, (kind));                 \
-  } while (0)
 
-// ---- TMA descriptors ---------------------------------------------------------------------
-template <typename T>
-const CUtensorMap* tmap(pf_grid* g, const T* base, bool halo) {
-  const auto key = std::make_pair(static_cast<const void*>(base), (int)sizeof(T) * 2 + (halo ? 1 : 0));
-  auto it = g->maps.find(key);
-  if (it != g->maps.end()) return &it->second;
-  CUtensorMap m;
-  if (!pf::encode_map(&m, base, g->geom, (int)sizeof(T), halo)) return nullptr;
-  return &(g->maps[key] = m);
-}
-
-template <int NH, int NC, typename T>
-pf_status fill_maps(pf_grid* g, pf::Maps<NH, NC>* m, const T* const (&h)[NH], const T* const (&c)[NC]) {
-  for (int i = 0; i < NH; ++i) {
-    const CUtensorMap* p = tmap(g, h[i], true);
-    if (!p) return fail(PF_E_CUDA, "cuTensorMapEncodeTiled failed");
-    m->h[i] = *p;
-  }
-  for (int i = 0; i < NC; ++i) {
-    const CUtensorMap* p = tmap(g, c[i], false);
-    if (!p) return fail(PF_E_CUDA, "cuTensorMapEncodeTiled failed");
-    m->c[i] = *p;
-  }
-  return PF_OK;
-}
 
 // ---- operators -------------------------------------------------------------------------
-// The arrays of one operator in one precision: Jacobi scaling (0 on identity rows), FP64 diagonal,
-// face arrays (null for the uniform PF1 operator), uniform face and diagonal.
-template <typename T>
-struct OpArrays {
-  const T* dinv;
-  const double* diag;
-  const T *wE, *wN, *wU;
-  double wc, diagc;
-};
 
 double pf1_face(const pf_grid* g) { return g->eps_s * g->lc * g->lc / (g->h * g->h); }
 
@@ -330,8 +208,8 @@ OpArrays<float> ops32(const pf_grid* g, int op) {
   return {op == PF_OP_PF2 ? g->dinv2_32 : g->dinvP32, nullptr, g->wE32, g->wN32, g->wU32, 0.0, 0.0};
 }
 
-pf_status set_state(pf_grid* g, BicgState* dst, double tol, int norm, int max_iter, double tol_r0 = 0.0,
-                    int keep_r0 = 0) {
+pf_status set_state(pf_grid* g, BicgState* dst, double tol, int norm, int max_iter, double tol_r0,
+                    int keep_r0) {
   PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_state(dst, tol, norm, max_iter, tol_r0, keep_r0, g->stream));
   return PF_OK;
 }
@@ -344,15 +222,6 @@ pf_status read_state(pf_grid* g, const BicgState* src, BicgState* out) {
   return PF_OK;
 }
 
-// Krylov vectors of one precision
-template <typename T>
-struct Krylov {
-  T* r[2];
-  T* p[2];
-  T* v[2];
-  T* rt;
-  T* t;
-};
 
 Krylov<double> kry64(pf_grid* g) { return {{g->r64[0], g->r64[1]}, {g->p64[0], g->p64[1]}, {g->v64[0], g->v64[1]}, g->rt64, g->t64}; }
 Krylov<float> kry32(pf_grid* g) { return {{g->r32[0], g->r32[1]}, {g->p32[0], g->p32[1]}, {g->v32[0], g->v32[1]}, g->rt32, g->t32}; }
@@ -644,7 +513,76 @@ bool small_spd_solve(int k, const double (&A)[pf::AA_MAX][pf::AA_MAX], const dou
   return true;
 }
 
-}  // namespace
+pf_status outer_stage1(pf_grid* g, OuterUpdate& u, int m, double omega) {
+  const long NP = g->geom.np;
+  cudaStream_t s = g->stream;
+  if (m == 0) {
+    // relaxation and stop test of Table 4
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_relax(g->phi0, g->phi, omega, NP, g->part, g->ticket, g->delta, s));
+  } else {
+    // Anderson acceleration of the same map: f = Phi_solve - Phi_0, delta = (1-omega) ||f||_inf is the
+    // relaxed update of Table 4; the accelerated update mixes the last m differences of f and Phi_0
+    u.slot = u.head;
+    PF_LAUNCH(g, PF_PROF_OTHER,
+              pf::launch_aa_residual(g->phi, g->phi0, g->aa_f, g->aa_fprev, g->aa_xprev, g->aa_dF[u.slot],
+                                     g->aa_dX[u.slot], u.kaa >= 1, NP, g->part, g->ticket, g->delta, s));
+  }
+  PF_CK(cudaMemcpyAsync(g->host_delta, g->delta, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return PF_OK;
+}
+
+double outer_delta(const pf_grid* g, int m, double omega) {
+  return m == 0 ? *g->host_delta : (1.0 - omega) * *g->host_delta;
+}
+
+pf_status outer_stage2(pf_grid* g, OuterUpdate& u, int m, bool stop) {
+  u.dots = false;
+  u.cols = pf::AAPtrs{};
+  if (m == 0 || stop || u.kaa < 1) return PF_OK;
+  u.head = (u.head + 1) % m;
+  u.nact = u.nact < m ? u.nact + 1 : m;
+  for (int j = 0; j < u.nact; ++j) {  // active slots, oldest first
+    u.act[j] = ((u.head - u.nact + j) % m + m) % m;
+    u.cols.dF[j] = g->aa_dF[u.act[j]];
+    u.cols.dX[j] = g->aa_dX[u.act[j]];
+  }
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_aa_dots(u.cols, u.nact, g->aa_dF[u.slot], g->aa_f, g->geom.np, g->part,
+                                                 g->ticket, g->aa_out, g->stream));
+  PF_CK(cudaMemcpyAsync(g->aa_host, g->aa_out, 2 * pf::AA_MAX * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  u.dots = true;
+  return PF_OK;
+}
+
+pf_status outer_stage3(pf_grid* g, OuterUpdate& u, int m, double omega, bool stop) {
+  if (m == 0) return PF_OK;
+  pf::AACoef gam{};
+  int k = 0;
+  if (u.dots && !stop) {
+    const int slot = u.slot, n = u.nact;
+    double A[pf::AA_MAX][pf::AA_MAX] = {}, bvec[pf::AA_MAX], x[pf::AA_MAX];
+    for (int j = 0; j < n; ++j) u.Gm[slot][u.act[j]] = u.Gm[u.act[j]][slot] = g->aa_host[j];
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < n; ++j) A[i][j] = u.Gm[u.act[i]][u.act[j]];
+      bvec[i] = g->aa_host[pf::AA_MAX + i];
+    }
+    bool ok = small_spd_solve(n, A, bvec, x);
+    for (int j = 0; ok && j < n; ++j) ok = fabs(x[j]) < 1e4;
+    if (ok) {
+      k = n;
+      for (int j = 0; j < n; ++j) gam.g[j] = x[j];
+    } else {
+      u.nact = 0;  // ill-conditioned history: restart with a plain relaxed step
+    }
+  }
+  // at the stop k = 0: the plain relaxed update, so the final iterate is the relaxed one of Table 4
+  PF_LAUNCH(g, PF_PROF_OTHER,
+            pf::launch_aa_update(u.cols, gam, k, 1.0 - omega, g->phi0, g->aa_f, g->geom.np, g->stream));
+  ++u.kaa;
+  return PF_OK;
+}
+
+}  // namespace pfi
 
 // Sets the message that pf_last_error returns on this thread (used by entry points in other files).
 void pf_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
@@ -892,9 +830,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   res->lin_iters_first = rep.iterations;
   res->lin_iters_total += rep.iterations;
   if (rep.status != PF_OK) st = (pf_status)rep.status;
-  const double beta = 1.0 - o.omega;
-  double Gm[pf::AA_MAX][pf::AA_MAX] = {};  // Gram matrix of the history columns, indexed by ring slot
-  int nact = 0, head = 0, kaa = 0;         // active columns, next slot, accelerated iterations done
+  OuterUpdate U;
   double delta_prev = 1.0;
   for (int outer = 1; st == PF_OK && outer <= o.max_outer; ++outer) {
     // forcing term: the linear solves of this outer iteration stop at eta ||r0|| (r0: the residual of the warm
@@ -916,60 +852,13 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
     PF_TRY(solve_dev(g, PF_OP_PF2, g->b2, g->phi, lo, &rep, eta));  // Eq. (13)
     res->lin_iters_total += rep.iterations;
     if (rep.status != PF_OK) { st = (pf_status)rep.status; break; }
-    double delta = 0.0;
-    if (m == 0) {
-      // relaxation and stop test of Table 4
-      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_relax(g->phi0, g->phi, o.omega, NP, g->part, g->ticket, g->delta, s));
-      PF_CK(cudaMemcpyAsync(g->host_delta, g->delta, sizeof(double), cudaMemcpyDeviceToHost, s));
-      PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-      PF_CK(cudaStreamSynchronize(s));
-      delta = *g->host_delta;
-    } else {
-      // Anderson acceleration of the same map: f = Phi_solve - Phi_0, delta = (1-omega) ||f||_inf is the
-      // relaxed update of Table 4; the accelerated update mixes the last m differences of f and Phi_0
-      const int slot = head;
-      PF_LAUNCH(g, PF_PROF_OTHER,
-                pf::launch_aa_residual(g->phi, g->phi0, g->aa_f, g->aa_fprev, g->aa_xprev, g->aa_dF[slot],
-                                       g->aa_dX[slot], kaa >= 1, NP, g->part, g->ticket, g->delta, s));
-      PF_CK(cudaMemcpyAsync(g->host_delta, g->delta, sizeof(double), cudaMemcpyDeviceToHost, s));
-      PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-      PF_CK(cudaStreamSynchronize(s));
-      delta = beta * *g->host_delta;
-      pf::AAPtrs cols{};
-      pf::AACoef gam{};
-      int k = 0;
-      if (delta > o.tol_outer && kaa >= 1) {
-        head = (head + 1) % m;
-        nact = nact < m ? nact + 1 : m;
-        int act[pf::AA_MAX];  // active slots, oldest first
-        for (int j = 0; j < nact; ++j) act[j] = ((head - nact + j) % m + m) % m;
-        for (int j = 0; j < nact; ++j) {
-          cols.dF[j] = g->aa_dF[act[j]];
-          cols.dX[j] = g->aa_dX[act[j]];
-        }
-        PF_LAUNCH(g, PF_PROF_OTHER,
-                  pf::launch_aa_dots(cols, nact, g->aa_dF[slot], g->aa_f, NP, g->part, g->ticket, g->aa_out, s));
-        PF_CK(cudaMemcpyAsync(g->aa_host, g->aa_out, 2 * pf::AA_MAX * sizeof(double), cudaMemcpyDeviceToHost, s));
-        PF_CK(cudaStreamSynchronize(s));
-        double A[pf::AA_MAX][pf::AA_MAX] = {}, bvec[pf::AA_MAX], x[pf::AA_MAX];
-        for (int j = 0; j < nact; ++j) Gm[slot][act[j]] = Gm[act[j]][slot] = g->aa_host[j];
-        for (int i = 0; i < nact; ++i) {
-          for (int j = 0; j < nact; ++j) A[i][j] = Gm[act[i]][act[j]];
-          bvec[i] = g->aa_host[pf::AA_MAX + i];
-        }
-        bool ok = small_spd_solve(nact, A, bvec, x);
-        for (int j = 0; ok && j < nact; ++j) ok = fabs(x[j]) < 1e4;
-        if (ok) {
-          k = nact;
-          for (int j = 0; j < nact; ++j) gam.g[j] = x[j];
-        } else {
-          nact = 0;  // ill-conditioned history: restart with a plain relaxed step
-        }
-      }
-      // at the stop k = 0: the plain relaxed update, so the final iterate is the relaxed one of Table 4
-      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_aa_update(cols, gam, k, beta, g->phi0, g->aa_f, NP, s));
-      ++kaa;
-    }
+    PF_TRY(outer_stage1(g, U, m, o.omega));
+    PF_CK(cudaStreamSynchronize(s));
+    const double delta = outer_delta(g, m, o.omega);
+    const bool stop = delta <= o.tol_outer;
+    PF_TRY(outer_stage2(g, U, m, stop));
+    if (U.dots) PF_CK(cudaStreamSynchronize(s));
+    PF_TRY(outer_stage3(g, U, m, o.omega, stop));
     if (*g->host_err) { st = PF_E_GAMMA; break; }
     res->outer_iters = outer;
     res->delta = delta;

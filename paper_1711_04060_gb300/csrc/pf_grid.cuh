@@ -1,0 +1,212 @@
+// pf_grid.cuh -- the library's per-grid state (struct pf_grid) and the host helpers that the single-grid
+// solver (pf_api.cu) and the batched solver (pf_batch.cu) share: error reporting, stream-ordered device
+// allocation, launch profiling, TMA descriptor cache, operator and Krylov array views.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/pf_gb300.h"
+#include "pf_internal.cuh"
+
+namespace pfi {
+
+using pf::BicgState;
+
+pf_status fail(pf_status s, const std::string& msg);
+pf_status cuda_fail(cudaError_t e, const char* what);
+
+#define PF_CK(call)                                        \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+#define PF_TRY(call)                    \
+  do {                                  \
+    pf_status s_ = (call);              \
+    if (s_ != PF_OK) return s_;         \
+  } while (0)
+
+constexpr int CHUNK = 8;         // BiCGSTAB iterations launched between two host checks of the done flag
+constexpr int INNER_CAP = 1000;  // FP32 iterations per refinement step at most
+constexpr int PROF_SLOTS = 64;   // timed launches between two resolutions of the profiling events
+constexpr unsigned long long WAIT_LIMIT = 4000000000ull;  // clock cycles (about 2 s) per TMA stage wait
+
+}  // namespace pfi
+
+struct pf_grid {
+  int nx = 0, ny = 0, nz = 0;
+  long N = 0;   // nodes
+  pf::Geom geom{};
+  double h = 1.0, origin[3] = {0, 0, 0};
+  cudaStream_t stream = nullptr;
+  pf::Launch L{};
+  bool have_coeffs = false;
+  // problem constants
+  double eps_s = 78.5, lc = 0.0, T = 298.15, Tv = 0.0, lam = 0.0, lo_hat = 0.0, hi_hat = 0.0, molar = 0.0;
+  pf::SpeciesParams sp{};
+  // device arrays (padded layout)
+  std::vector<void*> allocs;
+  double *eps = nullptr, *wE = nullptr, *wN = nullptr, *wU = nullptr, *dsum = nullptr, *ffix = nullptr;
+  uint8_t* solvent = nullptr;
+  double *diagP = nullptr, *dinvP = nullptr, *diag2 = nullptr, *dinv2 = nullptr, *sig = nullptr, *dinv1 = nullptr;
+  float *wE32 = nullptr, *wN32 = nullptr, *wU32 = nullptr, *dinvP32 = nullptr, *dinv2_32 = nullptr,
+        *dinv1_32 = nullptr;
+  double *r64[2] = {nullptr, nullptr}, *p64[2] = {nullptr, nullptr}, *v64[2] = {nullptr, nullptr};
+  double *rt64 = nullptr, *t64 = nullptr;
+  float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr}, *v32[2] = {nullptr, nullptr};
+  float *rt32 = nullptr, *t32 = nullptr, *d32 = nullptr, *b32 = nullptr;
+  double *xb = nullptr, *bb = nullptr, *stage = nullptr;
+  double *phi0 = nullptr, *phi = nullptr, *psi = nullptr, *b1 = nullptr, *c2 = nullptr, *b2 = nullptr;
+  double *Cbuf = nullptr, *Sbuf = nullptr, *Gbuf = nullptr, *ulast = nullptr;
+  double* part = nullptr;
+  // Anderson acceleration of the outer loop (allocated on first use)
+  int aa_alloc = 0;
+  double *aa_f = nullptr, *aa_fprev = nullptr, *aa_xprev = nullptr, *aa_out = nullptr, *aa_host = nullptr;
+  double *aa_dF[pf::AA_MAX] = {}, *aa_dX[pf::AA_MAX] = {};
+  double* dch = nullptr;     // fixed charges (x, y, z, q) on the device
+  int nq = 0;
+  pf::BicgState* st = nullptr;   // FP64 solve / refinement state
+  pf::BicgState* st2 = nullptr;  // FP32 inner solve state
+  pf::BicgState* host_st = nullptr;  // pinned mirror
+  int* err = nullptr;        // device error flag
+  int* host_err = nullptr;   // pinned
+  double* delta = nullptr;
+  unsigned int* ticket = nullptr;
+  double* host_delta = nullptr;
+  void* hostblk = nullptr;   // pinned block holding host_st, host_err, host_delta and aa_host
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // TMA descriptors, keyed by (array, halo box?)
+  std::map<std::pair<const void*, int>, CUtensorMap> maps;
+  // profiling: event pairs around launches, resolved at the next host synchronisation
+  int prof_on = 0;
+  long long launches = 0;
+  long long pcount[PF_PROF_KINDS] = {};
+  double pms[PF_PROF_KINDS] = {};
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> pkind;
+  int np = 0;
+};
+
+namespace pfi {
+
+int trace_level();
+void prof_resolve(pf_grid* g);
+int prof_begin(pf_grid* g, int n_launches);
+void prof_end(pf_grid* g, int slot, int kind);
+
+#define PF_LAUNCH(g, kind, call)                  \
+  do {                                            \
+    const int slot_ = prof_begin((g), 1);         \
+    PF_CK(call);                                  \
+    prof_end((g), slot_, (kind));                 \
+  } while (0)
+
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the grid's stream), so creating and
+// destroying grids does not synchronise the device while other grids run on other streams.
+template <typename T>
+pf_status dalloc(pf_grid* g, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 1;
+  cudaError_t e = cudaMallocAsync(&q, bytes, g->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PF_E_OOM, std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
+                              cudaGetErrorString(e));
+  }
+  g->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return PF_OK;
+}
+
+// ---- TMA descriptors ---------------------------------------------------------------------
+template <typename T>
+const CUtensorMap* tmap(pf_grid* g, const T* base, bool halo) {
+  const auto key = std::make_pair(static_cast<const void*>(base), (int)sizeof(T) * 2 + (halo ? 1 : 0));
+  auto it = g->maps.find(key);
+  if (it != g->maps.end()) return &it->second;
+  CUtensorMap m;
+  if (!pf::encode_map(&m, base, g->geom, (int)sizeof(T), halo)) return nullptr;
+  return &(g->maps[key] = m);
+}
+
+template <int NH, int NC, typename T>
+pf_status fill_maps(pf_grid* g, pf::Maps<NH, NC>* m, const T* const (&h)[NH], const T* const (&c)[NC]) {
+  for (int i = 0; i < NH; ++i) {
+    const CUtensorMap* p = tmap(g, h[i], true);
+    if (!p) return fail(PF_E_CUDA, "cuTensorMapEncodeTiled failed");
+    m->h[i] = *p;
+  }
+  for (int i = 0; i < NC; ++i) {
+    const CUtensorMap* p = tmap(g, c[i], false);
+    if (!p) return fail(PF_E_CUDA, "cuTensorMapEncodeTiled failed");
+    m->c[i] = *p;
+  }
+  return PF_OK;
+}
+
+// The arrays of one operator in one precision: Jacobi scaling (0 on identity rows), FP64 diagonal,
+// face arrays (null for the uniform PF1 operator), uniform face and diagonal.
+template <typename T>
+struct OpArrays {
+  const T* dinv;
+  const double* diag;
+  const T *wE, *wN, *wU;
+  double wc, diagc;
+};
+
+// Krylov vectors of one precision
+template <typename T>
+struct Krylov {
+  T* r[2];
+  T* p[2];
+  T* v[2];
+  T* rt;
+  T* t;
+};
+
+double pf1_face(const pf_grid* g);
+OpArrays<double> ops64(const pf_grid* g, int op);
+OpArrays<float> ops32(const pf_grid* g, int op);
+Krylov<double> kry64(pf_grid* g);
+Krylov<float> kry32(pf_grid* g);
+pf_status set_state(pf_grid* g, BicgState* dst, double tol, int norm, int max_iter, double tol_r0 = 0.0,
+                    int keep_r0 = 0);
+pf_status read_state(pf_grid* g, const BicgState* src, BicgState* out);
+double measure_of(const BicgState& s, int norm);
+pf_status check_opts(const pf_solve_opts& o);
+pf_status update_pf2(pf_grid* g);
+pf_status build_operators(pf_grid* g);
+pf_status pack_in(pf_grid* g, const void* src, int mem, void* dst, int type);
+pf_status unpack_out(pf_grid* g, const double* src, int count, double* dst, int mem);
+pf_status ensure_aa(pf_grid* g, int m);
+bool small_spd_solve(int k, const double (&A)[pf::AA_MAX][pf::AA_MAX], const double* b, double* x);
+
+// The update at the end of an outer iteration (Table 4's relaxation, or Anderson acceleration of the same
+// map when m > 0), split at its host read-backs so that a batch runs each stage over all of its grids
+// between two synchronisations: stage 1 queues the update (relaxation) or f = Phi - Phi_0 with the history
+// (Anderson) and the read-back of max |.| and the error flag; outer_delta gives delta once that landed;
+// stage 2 queues the least-squares inner products (Anderson, when the iteration goes on and history
+// exists; sets dots); stage 3 solves the small least-squares problem and updates Phi_0.
+struct OuterUpdate {
+  double Gm[pf::AA_MAX][pf::AA_MAX] = {};  // Gram matrix of the history columns, by ring slot
+  int nact = 0, head = 0, kaa = 0, slot = 0;  // active columns, next slot, accelerated iterations, newest slot
+  int act[pf::AA_MAX] = {};                // active slots, oldest first
+  pf::AAPtrs cols{};
+  bool dots = false;
+};
+pf_status outer_stage1(pf_grid* g, OuterUpdate& u, int m, double omega);
+double outer_delta(const pf_grid* g, int m, double omega);
+pf_status outer_stage2(pf_grid* g, OuterUpdate& u, int m, bool stop);
+pf_status outer_stage3(pf_grid* g, OuterUpdate& u, int m, double omega, bool stop);
+
+}  // namespace pfi

@@ -1,781 +1,27 @@
-// pf_kernels.cu -- sm_103a kernels of the Poisson-Fermi hot path.
-//
-// Stencil kernels (BiCGSTAB phases and the FP64 residual) walk 2D tiles of TX x TY nodes (one warp
-// per x row) up through a chunk of ZC interior z-planes.  Every input plane of a tile arrives by
-// TMA (cp.async.bulk.tensor.3d) into a ring of D shared-memory stages, each guarded by an mbarrier
-// that the copies complete; one thread keeps D planes in flight ahead of the consumers, and the
-// stream of planes continues across the tiles a block owns, so the copy engine hides DRAM latency
-// without registers.  Arrays read at neighbours arrive as halo boxes (x0-4 .. x0+TX+3, y0-1 ..
-// y0+TY: the x start stays 16-byte aligned), the others as centre boxes.  Each plane's stencil input
-// (the BiCGSTAB direction p or s after the axpy and the Jacobi scaling) is computed once per node
-// into a ring of three shared planes; the planes below and above come from registers.  The axpy
-// updates of p, s, x and r (Table 3), the Jacobi scaling and the inner products that give rho, alpha
-// and omega are fused into the two stencil kernels of an iteration.  Inner products are reduced by warp
-// shuffles, a block tree and the last-arriving block over the per-block partials in fixed order.
+// pf_kernels.cu -- sm_103a kernels of the Poisson-Fermi hot path on one grid: the single-grid stencil
+// launches (BiCGSTAB phases and the FP64 residual, whose body is in pf_stencil.cuh), operator setup, the
+// pointwise Fermi/steric step of Eq. (1), the right-hand-side builds, relaxation and the elementwise
+// helpers of the solver, with their host launchers.
 #include <math.h>
 #include <stdio.h>
 
-#include "pf_internal.cuh"
+#include "pf_stencil.cuh"
 
 namespace pf {
 
-// ------------------------------------------------------------------ PTX helpers (TMA + mbarrier)
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: gives up after `limit` clock cycles (the caller then reports PF_E_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > limit) return false;
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// ------------------------------------------------------------------ accumulation helpers
-template <typename T>
-struct Acc;
-
-template <>
-struct Acc<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void prod(double a, double b) { s = fma(a, b, s); }
-  __device__ __forceinline__ double value() const { return s; }
-};
-
-// FP32 products summed with an error-free transformation (TwoProduct by FMA, TwoSum), so a
-// thread's partial sum carries about twice the FP32 precision before the FP64 block reduction.
-template <>
-struct Acc<float> {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void prod(float a, float b) {
-    const float p = __fmul_rn(a, b);
-    const float pe = fmaf(a, b, -p);
-    const float t = __fadd_rn(hi, p);
-    const float z = __fsub_rn(t, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p, z));
-    hi = t;
-    lo = __fadd_rn(lo, __fadd_rn(e, pe));
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
-template <typename T>
-__device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
-
-// Inner-product partials of a thread: the products of one tile column (at most ZC + 1 terms) are
-// summed in the working precision, then added to an FP64 total once per tile, so the global inner
-// products are FP64 sums of short working-precision partial sums.
-template <typename T, int NV>
-struct Partials {
-  T t[NV];
-  double d[NV];
-  __device__ __forceinline__ Partials() {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      t[j] = T(0);
-      d[j] = 0.0;
-    }
-  }
-  __device__ __forceinline__ void flush() {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      d[j] += (double)t[j];
-      t[j] = T(0);
-    }
-  }
-};
-
-// Block reduction of NV values (bit j of maxmask: value j is a maximum, else a sum) into
-// part[blockIdx.x * NPART + j]; scratch holds at least NTHREADS / 32 * NV doubles.
-template <int NV>
-__device__ __forceinline__ void block_partials(double (&v)[NV], unsigned maxmask, double* part, double* scratch) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    double a = v[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double b = __shfl_down_sync(0xffffffffu, a, o);
-      a = ((maxmask >> j) & 1u) ? fmax(a, b) : a + b;
-    }
-    if (lane == 0) scratch[warp * NV + j] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    const int j = threadIdx.x;
-    double a = scratch[j];
-    for (int w = 1; w < NTHREADS / 32; ++w)
-      a = ((maxmask >> j) & 1u) ? fmax(a, scratch[w * NV + j]) : a + scratch[w * NV + j];
-    part[blockIdx.x * NPART + j] = a;
-  }
-}
-
-// True in the block that arrives last; that block then sees every block's partials.
-__device__ __forceinline__ bool arrive_last(unsigned int* ticket) {
-  __shared__ int last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (last) __threadfence();
-  return last;
-}
-
-// In the last block: totals over all blocks' partials in fixed order; scratch holds NTHREADS * NV doubles.
-template <int NV>
-__device__ __forceinline__ void total_partials(const double* part, unsigned maxmask, double (&tot)[NV],
-                                               double* scratch) {
-  double a[NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) a[j] = 0.0;  // sums start at 0; maxima are of absolute values
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += NTHREADS) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      const double x = __ldcg(part + (long)b * NPART + j);
-      a[j] = ((maxmask >> j) & 1u) ? fmax(a[j], x) : a[j] + x;
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < NV; ++j) scratch[threadIdx.x * NV + j] = a[j];
-  __syncthreads();
-  for (int s = NTHREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-#pragma unroll
-      for (int j = 0; j < NV; ++j) {
-        const double u = scratch[threadIdx.x * NV + j], w = scratch[(threadIdx.x + s) * NV + j];
-        scratch[threadIdx.x * NV + j] = ((maxmask >> j) & 1u) ? fmax(u, w) : u + w;
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int j = 0; j < NV; ++j) tot[j] = scratch[j];
-}
-
-// ------------------------------------------------------------------ tile geometry
 int tiles_for(int nx, int ny, int nz) {
   const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, nzc = (nz - 2 + ZC - 1) / ZC;
   return ntx * nty * nzc;
 }
 
-struct Tile {
-  int x0, y0, kb, ke;
-};
-
-__device__ __forceinline__ Tile tile_of(int t, int nx, int nz) {
-  const int nzc = (nz - 2 + ZC - 1) / ZC, ntx = (nx + TX - 1) / TX;
-  const int zc = t % nzc, xy = t / nzc;
-  Tile r;
-  r.x0 = (xy % ntx) * TX;
-  r.y0 = (xy / ntx) * TY;
-  r.kb = 1 + zc * ZC;
-  r.ke = min(r.kb + ZC, nz - 1);
-  return r;
-}
-
-// Position g in [-1, n] -> the node whose value it holds: itself, the mirror image for the two ghost
-// positions of the zero-flux sides (Eq. 4), or -1 when no output of the tile uses it.
-__device__ __forceinline__ int mirror(int g, int n) {
-  if (g < 0) return 1;
-  if (g < n) return g;
-  if (g == n) return n - 2;
-  return -1;
-}
-
-constexpr int PW = TX + 2;             // shared stencil-plane row pitch
-constexpr int PLANE = (TY + 2) * PW;   // shared stencil-plane size
-constexpr int NHALO = 2 * (TX + 2) + 2 * TY;
-
-__device__ __forceinline__ int cs(int lx, int ly) { return (ly + 1) * PW + (lx + 1); }
-
-__device__ __forceinline__ void halo_pos(int h, int& lx, int& ly) {
-  if (h < TX + 2) { lx = h - 1; ly = -1; return; }
-  h -= TX + 2;
-  if (h < TX + 2) { lx = h - 1; ly = TY; return; }
-  h -= TX + 2;
-  if (h < TY) { lx = -1; ly = h; return; }
-  h -= TY;
-  lx = TX;
-  ly = h;
-}
-
-// Per-thread geometry of a tile: halo-box offsets of the thread's centre and of its halo slot (with
-// the mirror applied), the shared-plane index of the halo slot, and whether the centre is a node.
-struct TileGeo {
-  int cbo;    // halo-box offset of the centre position, -1 if unused
-  int hbo;    // halo-box offset of the halo slot's position, -1 if unused
-  int hs;     // shared-plane index of the halo slot, -1 if the thread has none
-  int gi, gj;
-  bool valid;
-};
-
-__device__ __forceinline__ int box_off(int gi, int gj, const Tile& tl, int nx, int ny) {
-  const int mi = mirror(gi, nx), mj = mirror(gj, ny);
-  if (mi < 0 || mj < 0) return -1;
-  return (mj - tl.y0 + 1) * HBX + (mi - tl.x0 + 4);
-}
-
-__device__ __forceinline__ TileGeo tile_geo(const Tile& tl, int nx, int ny) {
-  TileGeo g;
-  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-  g.gi = tl.x0 + lx;
-  g.gj = tl.y0 + ly;
-  g.valid = g.gi < nx && g.gj < ny;
-  g.cbo = box_off(g.gi, g.gj, tl, nx, ny);
-  g.hbo = -1;
-  g.hs = -1;
-  // the halo slots go to the last NHALO threads, away from the producer thread in warp 0
-  const int hslot = (int)threadIdx.x - (NTHREADS - NHALO);
-  if (hslot >= 0) {
-    int hx, hy;
-    halo_pos(hslot, hx, hy);
-    g.hs = cs(hx, hy);
-    g.hbo = box_off(tl.x0 + hx, tl.y0 + hy, tl, nx, ny);
-  }
-  return g;
-}
-
-template <typename T>
-__host__ __device__ constexpr int halo_slot_bytes() {
-  return (HBX * HBY * (int)sizeof(T) + 127) / 128 * 128;
-}
-template <typename T>
-__host__ __device__ constexpr int centre_slot_bytes() {
-  return TX * TY * (int)sizeof(T);
-}
-
-template <class Op>
-__host__ __device__ constexpr int stage_bytes() {
-  return Op::NH * halo_slot_bytes<typename Op::T>() + Op::NC * centre_slot_bytes<typename Op::T>();
-}
-
-template <class Op>
-__host__ __device__ constexpr int smem_bytes() {
-  // stages | three stencil planes | D mbarriers | 128 bytes of alignment slack
-  return Op::D * stage_bytes<Op>() + 3 * PLANE * (int)sizeof(typename Op::T) + Op::D * 8 + 128;
-}
-
-// The reduction scratch at the end of a kernel reuses the stage ring (all copies consumed by then).
-template <class Op>
-constexpr bool scratch_fits() {
-  return Op::D * stage_bytes<Op>() >= NTHREADS * 8 * (int)sizeof(double);
-}
-
-// ------------------------------------------------------------------ the pipelined stencil kernel
-// Op supplies: T, NH, NC, D, CHECK_DONE, Args, Sc, Ctr, Accs and scalars(), q_of(), centre(),
-// up_face(), output(), finish().
+// ------------------------------------------------------------------ single-grid stencil kernel
+// One grid: a persistent launch whose blocks stride over the grid's tiles.
 template <class Op>
 __global__ void __launch_bounds__(NTHREADS, Op::MINB) k_stencil(const __grid_constant__ Maps<Op::NH, Op::NC> maps,
                                                       typename Op::Args a, Geom g, int ntiles,
                                                       unsigned long long wait_limit) {
-  using T = typename Op::T;
-  constexpr int D = Op::D, NH = Op::NH, NC = Op::NC;
-  constexpr int HB = halo_slot_bytes<T>(), CB = centre_slot_bytes<T>(), STAGE = stage_bytes<Op>();
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  T* qring = reinterpret_cast<T*>(smem + D * STAGE);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + D * STAGE + 3 * PLANE * sizeof(T));
-
-  if (Op::CHECK_DONE && *(volatile int*)&a.st->done) return;
-  const typename Op::Sc sc = Op::scalars(a);
-  if (threadIdx.x == 0) {
-    for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-
-  // producer (thread 0): the next (tile, plane) of this block's stream of planes
-  static_assert((D & (D - 1)) == 0, "the stage ring has a power-of-two size");
-  int pt = blockIdx.x, pj = 0;
-  unsigned pseq = 0;
-  Tile ptl = tile_of(pt, g.nx, g.nz);
-  auto issue = [&]() {
-    const int stage = pseq & (D - 1);
-    unsigned char* sb = smem + stage * STAGE;
-    uint64_t* bar = &bars[stage];
-    mbar_expect_tx(bar, NH * HBX * HBY * sizeof(T) + NC * TX * TY * sizeof(T));
-    const int k = ptl.kb - 1 + pj;
-#pragma unroll
-    for (int h = 0; h < NH; ++h) tma_load_3d(sb + h * HB, &maps.h[h], ptl.x0 - 4, ptl.y0 - 1, k, bar);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) tma_load_3d(sb + NH * HB + c * CB, &maps.c[c], ptl.x0, ptl.y0, k, bar);
-    ++pseq;
-    if (++pj == ptl.ke - ptl.kb + 2) {
-      pj = 0;
-      pt += gridDim.x;
-      if (pt < ntiles) ptl = tile_of(pt, g.nx, g.nz);
-    }
-  };
-  if (threadIdx.x == 0)
-    for (int d = 0; d < D && pt < ntiles; ++d) issue();
-
-  typename Op::Accs acc;
-  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-  unsigned seq = 0;
-  bool failed = false;
-  for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
-    const Tile tl = tile_of(t, g.nx, g.nz);
-    const TileGeo geo = tile_geo(tl, g.nx, g.ny);
-    const int planes = tl.ke - tl.kb + 2;
-    typename Op::Ctr cprev{}, cnow{};
-    T q_dn = T(0), q_prev = T(0), wD = T(0);
-    T* Qnow = qring;                 // plane j
-    T* Qprev = qring + 2 * PLANE;    // plane j-1
-    T* Qold = qring + PLANE;         // plane j-2 (free for plane j+1)
-    long cidx = geo.gi + (long)g.px * geo.gj + g.plane * (tl.kb - 1);
-    for (int j = 0; j < planes; ++j, ++seq) {
-      const int stage = seq & (D - 1);
-      const bool ok = mbar_wait(&bars[stage], (seq / D) & 1u, wait_limit);
-      T qc = T(0);
-      if (ok) {
-        const unsigned char* sb = smem + stage * STAGE;
-        const T* H[NH];
-        const T* C[NC];
-#pragma unroll
-        for (int h = 0; h < NH; ++h) H[h] = reinterpret_cast<const T*>(sb + h * HB);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) C[c] = reinterpret_cast<const T*>(sb + NH * HB + c * CB);
-        if (geo.cbo >= 0) qc = Op::q_of(sc, H, geo.cbo, &cnow);
-        if (geo.valid) Op::centre(a, H, C, geo.cbo, ly * TX + lx, geo.gi > 0, geo.gj > 0, cnow);
-        Qnow[cs(lx, ly)] = qc;
-        if (geo.hs >= 0) Qnow[geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
-      }
-      // one barrier per plane; the vote makes a timed-out wait a decision of the whole block
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
-      if (threadIdx.x == 0 && pt < ntiles) {
-        fence_proxy_async();
-        issue();
-      }
-      if (j >= 2 && geo.valid) Op::output(sc, a, Qprev, lx, ly, cidx, cprev, q_dn, qc, wD, acc);
-      if (j >= 1) {
-        q_dn = q_prev;
-        wD = Op::up_face(a, cprev);
-        cidx += g.plane;
-      }
-      q_prev = qc;
-      cprev = cnow;
-      // rotate the three stencil planes
-      T* const freed = Qold;
-      Qold = Qprev;
-      Qprev = Qnow;
-      Qnow = freed;
-    }
-    acc.flush();
-    if (!failed) __syncthreads();
-  }
-  if (failed) {
-    // give up: let this block's copies in flight land (bounded), report the timeout, skip the reduction
-    if (threadIdx.x == 0) {
-      for (unsigned s = seq; s < pseq; ++s) mbar_wait(&bars[s & (D - 1)], (s / D) & 1u, wait_limit);
-      a.st->status = 7;  // PF_E_TIMEOUT
-      atomicExch(&a.st->done, 1);
-    }
-    return;
-  }
-  __syncthreads();
-  Op::finish(a, acc, reinterpret_cast<double*>(smem));
+  stencil_run<Op>(&maps, a, g, ntiles, blockIdx.x, gridDim.x, wait_limit);
 }
-
-// ------------------------------------------------------------------ phase B: s = r - alpha v, t = A M^-1 s
-template <typename T_, bool UNI>
-struct OpB {
-  using T = T_;
-  static constexpr int NH = SlotsB<UNI>::NH, NC = SlotsB<UNI>::NC, D = sizeof(T_) == 4 ? 4 : 2;
-  static constexpr int MINB = sizeof(T_) == 4 ? 4 : 2;
-  static constexpr bool CHECK_DONE = true;
-  enum { R = 0, V = 1, DI = 2, WE = 3, WN = 4 };
-  enum { RT = 0, WU = 1 };
-  struct Args {
-    double* part;
-    BicgState* st;
-    T* t;
-    T wc;
-  };
-  struct Sc {
-    T al;
-  };
-  struct Ctr {
-    T s, di, rt, wU, wEc, wEw, wNc, wNs;
-  };
-  struct Accs {
-    Partials<T, 5> p;  // r~.s, r~.t, t.s, t.t, s.s
-    T smax = T(0);
-    __device__ void flush() { p.flush(); }
-  };
-  __device__ static Sc scalars(const Args& a) { return Sc{(T)a.st->alpha}; }
-  __device__ static T q_of(const Sc& sc, const T* const* H, int o, Ctr* c) {
-    const T s = fma(-sc.al, H[V][o], H[R][o]);
-    const T di = H[DI][o];
-    if (c) {
-      c->s = s;
-      c->di = di;
-    }
-    return di * s;
-  }
-  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, int co, bool west,
-                                bool south, Ctr& c) {
-    c.rt = C[RT][co];
-    if (UNI) {
-      c.wU = c.wEc = c.wEw = c.wNc = c.wNs = a.wc;
-    } else {
-      c.wU = C[WU][co];
-      c.wEc = H[WE][o];
-      c.wEw = west ? H[WE][o - 1] : c.wEc;
-      c.wNc = H[WN][o];
-      c.wNs = south ? H[WN][o - HBX] : c.wNc;
-    }
-  }
-  __device__ static T up_face(const Args& a, const Ctr& c) { return UNI ? a.wc : c.wU; }
-  __device__ static void output(const Sc&, const Args& a, const T* Q, int lx, int ly, long cidx, const Ctr& c, T q_dn,
-                                T q_up, T wD, Accs& acc) {
-    T tc;
-    if (c.di == T(0)) {
-      tc = c.s;
-    } else {
-      const T qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
-      T nb;
-      if (UNI) {
-        nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
-      } else {
-        nb = c.wEc * qE;
-        nb = fma(c.wEw, qW, nb);
-        nb = fma(c.wNc, qN, nb);
-        nb = fma(c.wNs, qS, nb);
-        nb = fma(c.wU, q_up, nb);
-        nb = fma(wD, q_dn, nb);
-      }
-      tc = c.s - nb;
-    }
-    a.t[cidx] = tc;
-    acc.p.t[0] = fma(c.rt, c.s, acc.p.t[0]);
-    acc.p.t[1] = fma(c.rt, tc, acc.p.t[1]);
-    acc.p.t[2] = fma(tc, c.s, acc.p.t[2]);
-    acc.p.t[3] = fma(tc, tc, acc.p.t[3]);
-    acc.p.t[4] = fma(c.s, c.s, acc.p.t[4]);
-    acc.smax = fmax(acc.smax, tabs(c.s));
-  }
-  __device__ static void finish(const Args& a, const Accs& acc, double* scratch) {
-    double vals[6] = {acc.p.d[0], acc.p.d[1], acc.p.d[2], acc.p.d[3], acc.p.d[4], (double)acc.smax};
-    block_partials<6>(vals, 32u, a.part, scratch);
-    if (!arrive_last(&a.st->ticket)) return;
-    double tot[6];
-    total_partials<6>(a.part, 32u, tot, scratch);
-    if (threadIdx.x != 0) return;
-    BicgState* st = a.st;
-    const double rs = tot[0], rtt = tot[1], ts = tot[2], tt = tot[3], ss = tot[4], smx = tot[5];
-    st->snorm2 = ss;
-    st->sinf = smx;
-    const bool sconv = st->norm == 0 ? (ss <= st->tol2) : (smx < st->tol);
-    if (sconv) {  // early exit of the Templates algorithm: x += alpha M^-1 p, r = s
-      st->sexit = 1;
-      st->omega = 0.0;
-      st->beta = 0.0;
-    } else if (tt == 0.0 || !isfinite(tt) || !isfinite(ts) || !isfinite(ss)) {
-      st->status = 4;  // PF_E_BREAKDOWN, before x is touched
-      st->done = 1;
-    } else {
-      const double om = ts / tt;  // omega = t.s / t.t
-      st->omega = om;
-      // r~.r_new with r_new = s - omega t (the next rho): the next p is
-      // formed in the same kernel as r_new, so its beta is taken from the exact identity
-      const double rho_new = rs - om * rtt;
-      const double be = (om != 0.0) ? (rho_new / st->rho) * (st->alpha / om) : 0.0;  // beta
-      st->beta = isfinite(be) ? be : 0.0;
-    }
-    st->ticket = 0;
-  }
-};
-
-// ------------------------------------------------------------------ phase C+A
-// s = r - alpha v, x += alpha M^-1 p + omega M^-1 s, r' = s - omega t, and for the next iteration
-// p' = r' + beta (p - omega v) and v' = A M^-1 p'.
-template <typename T_, bool UNI>
-struct OpCA {
-  using T = T_;
-  static constexpr int NH = SlotsCA<UNI>::NH, NC = SlotsCA<UNI>::NC, D = 2;
-  static constexpr int MINB = sizeof(T_) == 4 ? 4 : 2;
-  static constexpr bool CHECK_DONE = true;
-  enum { R = 0, V = 1, TT = 2, P = 3, DI = 4, WE = 5, WN = 6 };
-  enum { X = 0, RT = 1, WU = 2 };
-  struct Args {
-    double* part;
-    BicgState* st;
-    T* x;
-    T* r_out;
-    T* p_out;
-    T* v_out;
-    T wc;
-    int prime;
-  };
-  struct Sc {
-    T al, om, be;
-  };
-  struct Ctr {
-    T s, rn, pn, pold, di, x, rt, wU, wEc, wEw, wNc, wNs;
-  };
-  struct Accs {
-    Partials<T, 3> p;  // r~.v', r~.r', r'.r'
-    T rmax = T(0);
-    __device__ void flush() { p.flush(); }
-  };
-  __device__ static Sc scalars(const Args& a) { return Sc{(T)a.st->alpha, (T)a.st->omega, (T)a.st->beta}; }
-  __device__ static T q_of(const Sc& sc, const T* const* H, int o, Ctr* c) {
-    const T vv = H[V][o], pp = H[P][o];
-    const T s = fma(-sc.al, vv, H[R][o]);
-    const T rn = fma(-sc.om, H[TT][o], s);
-    const T pn = fma(sc.be, fma(-sc.om, vv, pp), rn);
-    const T di = H[DI][o];
-    if (c) {
-      c->s = s;
-      c->rn = rn;
-      c->pn = pn;
-      c->pold = pp;
-      c->di = di;
-    }
-    return di * pn;
-  }
-  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, int co, bool west,
-                                bool south, Ctr& c) {
-    c.x = C[X][co];
-    c.rt = C[RT][co];
-    if (UNI) {
-      c.wU = c.wEc = c.wEw = c.wNc = c.wNs = a.wc;
-    } else {
-      c.wU = C[WU][co];
-      c.wEc = H[WE][o];
-      c.wEw = west ? H[WE][o - 1] : c.wEc;
-      c.wNc = H[WN][o];
-      c.wNs = south ? H[WN][o - HBX] : c.wNc;
-    }
-  }
-  __device__ static T up_face(const Args& a, const Ctr& c) { return UNI ? a.wc : c.wU; }
-  __device__ static void output(const Sc& sc, const Args& a, const T* Q, int lx, int ly, long cidx, const Ctr& c,
-                                T q_dn, T q_up, T wD, Accs& acc) {
-    T vn;
-    if (c.di == T(0)) {
-      vn = c.pn;
-    } else {
-      const T qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
-      T nb;
-      if (UNI) {
-        nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
-      } else {
-        nb = c.wEc * qE;
-        nb = fma(c.wEw, qW, nb);
-        nb = fma(c.wNc, qN, nb);
-        nb = fma(c.wNs, qS, nb);
-        nb = fma(c.wU, q_up, nb);
-        nb = fma(wD, q_dn, nb);
-      }
-      vn = c.pn - nb;
-      if (!a.prime) {
-        T xc = fma(sc.al, c.di * c.pold, c.x);
-        xc = fma(sc.om, c.di * c.s, xc);
-        a.x[cidx] = xc;
-      }
-    }
-    a.r_out[cidx] = c.rn;
-    a.p_out[cidx] = c.pn;
-    a.v_out[cidx] = vn;
-    acc.p.t[0] = fma(c.rt, vn, acc.p.t[0]);
-    acc.p.t[1] = fma(c.rt, c.rn, acc.p.t[1]);
-    acc.p.t[2] = fma(c.rn, c.rn, acc.p.t[2]);
-    acc.rmax = fmax(acc.rmax, tabs(c.rn));
-  }
-  __device__ static void finish(const Args& a, const Accs& acc, double* scratch) {
-    double vals[4] = {acc.p.d[0], acc.p.d[1], acc.p.d[2], (double)acc.rmax};
-    block_partials<4>(vals, 8u, a.part, scratch);
-    if (!arrive_last(&a.st->ticket)) return;
-    double tot[4];
-    total_partials<4>(a.part, 8u, tot, scratch);
-    if (threadIdx.x != 0) return;
-    BicgState* st = a.st;
-    const double rv = tot[0], rr = tot[1], r2 = tot[2], rmx = tot[3];
-    st->ticket = 0;
-    if (!a.prime) {
-      st->iter += 1;
-      st->rnorm2 = r2;
-      st->rinf = rmx;
-      const bool conv = st->norm == 0 ? (r2 <= st->tol2) : (rmx < st->tol);
-      if (st->sexit || conv) {
-        st->done = 1;
-        st->status = 0;
-        return;
-      }
-      if (st->omega == 0.0) {
-        st->done = 1;
-        st->status = 4;
-        return;
-      }
-      if (st->iter >= st->max_iter) {
-        st->done = 1;
-        st->status = 3;  // PF_E_NOCONV
-        return;
-      }
-    }
-    if (rr == 0.0 || rv == 0.0 || !isfinite(rr) || !isfinite(rv) || !isfinite(rr / rv)) {
-      st->done = 1;
-      st->status = 4;
-      return;
-    }
-    st->rho = rr;         // rho of the next iteration
-    st->alpha = rr / rv;  // alpha of the next iteration
-  }
-};
-
-// Squared 2-norm stop of a state whose residual has squared norm rr and right-hand side bb: the first
-// residual of a solve fixes r0norm2; the threshold is the larger of the b-relative and r0-relative ones.
-__device__ __forceinline__ void set_tol2(BicgState* st, double rr, double bb) {
-  if (!(st->r0norm2 >= 0.0)) st->r0norm2 = rr;
-  st->tol2 = fmax(st->tol * st->tol * bb, st->tol_r0 * st->tol_r0 * st->r0norm2);
-}
-
-// ------------------------------------------------------------------ FP64 residual b - A x
-template <bool UNI>
-struct OpRes {
-  using T = double;
-  static constexpr int NH = SlotsRes<UNI>::NH, NC = SlotsRes<UNI>::NC, D = 2;
-  static constexpr int MINB = 2;
-  static constexpr bool CHECK_DONE = false;
-  enum { X = 0, DI = 1, WE = 2, WN = 3 };
-  enum { B = 0, DG = 1, WU = 2 };
-  struct Args {
-    double* part;
-    BicgState* st;
-    double wc, diagc;
-    int init;
-    double *r, *rt, *p, *v, *t;
-    float* r32;
-  };
-  struct Sc {
-    int unused;
-  };
-  struct Ctr {
-    double xc, di, b, diag, wU, wEc, wEw, wNc, wNs;
-  };
-  struct Accs {
-    double rr = 0.0, bb = 0.0, rmax = 0.0;
-    __device__ void flush() {}
-  };
-  __device__ static Sc scalars(const Args&) { return Sc{0}; }
-  __device__ static double q_of(const Sc&, const double* const* H, int o, Ctr* c) {
-    const double xv = H[X][o];
-    if (c) {
-      c->xc = xv;
-      c->di = H[DI][o];
-    }
-    return xv;
-  }
-  __device__ static void centre(const Args& a, const double* const* H, const double* const* C, int o, int co,
-                                bool west, bool south, Ctr& c) {
-    c.b = C[B][co];
-    if (UNI) {
-      c.diag = a.diagc;
-      c.wU = c.wEc = c.wEw = c.wNc = c.wNs = a.wc;
-    } else {
-      c.diag = C[DG][co];
-      c.wU = C[WU][co];
-      c.wEc = H[WE][o];
-      c.wEw = west ? H[WE][o - 1] : c.wEc;
-      c.wNc = H[WN][o];
-      c.wNs = south ? H[WN][o - HBX] : c.wNc;
-    }
-  }
-  __device__ static double up_face(const Args& a, const Ctr& c) { return UNI ? a.wc : c.wU; }
-  __device__ static void output(const Sc&, const Args& a, const double* Q, int lx, int ly, long cidx, const Ctr& c,
-                                double q_dn, double q_up, double wD, Accs& acc) {
-    double rc;
-    if (c.di == 0.0) {
-      rc = c.b - c.xc;
-    } else {
-      const double qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
-      double nb;
-      if (UNI) {
-        nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
-      } else {
-        nb = c.wEc * qE;
-        nb = fma(c.wEw, qW, nb);
-        nb = fma(c.wNc, qN, nb);
-        nb = fma(c.wNs, qS, nb);
-        nb = fma(c.wU, q_up, nb);
-        nb = fma(wD, q_dn, nb);
-      }
-      rc = c.b - (c.diag * c.xc - nb);
-    }
-    if (a.init) {
-      a.r[cidx] = rc;
-      a.rt[cidx] = rc;
-      a.p[cidx] = 0.0;
-      a.v[cidx] = 0.0;
-      a.t[cidx] = 0.0;
-    } else {
-      a.r32[cidx] = (float)rc;
-    }
-    acc.rr = fma(rc, rc, acc.rr);
-    acc.bb = fma(c.b, c.b, acc.bb);
-    acc.rmax = fmax(acc.rmax, fabs(rc));
-  }
-  __device__ static void finish(const Args& a, const Accs& acc, double* scratch) {
-    double vals[3] = {acc.rr, acc.bb, acc.rmax};
-    block_partials<3>(vals, 4u, a.part, scratch);
-    if (!arrive_last(&a.st->ticket)) return;
-    double tot[3];
-    total_partials<3>(a.part, 4u, tot, scratch);
-    if (threadIdx.x != 0) return;
-    BicgState* st = a.st;
-    double bb = tot[1] + st->bnorm2;  // bnorm2 was preset to b.b over the Dirichlet planes
-    if (bb == 0.0) bb = 1.0;
-    st->bnorm2 = bb;
-    st->rnorm2 = tot[0];
-    st->rinf = tot[2];
-    set_tol2(st, tot[0], bb);
-    const bool conv = st->norm == 0 ? (tot[0] <= st->tol2) : (tot[2] < st->tol);
-    if (a.init) {
-      st->rho = tot[0];  // r~ = r0
-      st->alpha = st->omega = st->beta = 0.0;
-      st->sexit = 0;
-      st->iter = 0;
-      st->status = 0;
-    }
-    st->done = conv ? 1 : 0;
-    st->ticket = 0;
-  }
-};
 
 // ------------------------------------------------------------------ elementwise kernels
 // Nodes are visited row by row: row r = j + ny*k holds i = 0..nx-1 at padded index i + px*r.
@@ -1257,6 +503,13 @@ cudaError_t launch_add_f32(double* x, const float* d, long n, cudaStream_t s) {
 cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, double tol_r0, int keep_r0,
                              cudaStream_t s) {
   k_set_state<<<1, 1, 0, s>>>(st, tol, norm, max_iter, tol_r0, keep_r0);
+  return cudaGetLastError();
+}
+
+__global__ void k_mark_done(BicgState* st) { st->done = 1; }
+
+cudaError_t launch_mark_done(BicgState* st, cudaStream_t s) {
+  k_mark_done<<<1, 1, 0, s>>>(st);
   return cudaGetLastError();
 }
 

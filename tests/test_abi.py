@@ -43,7 +43,7 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_1711_04060_gb300 import _binding as B
     structs = {"pf_species": B.pf_species, "pf_coeffs": B.pf_coeffs, "pf_solve_opts": B.pf_solve_opts,
                "pf_report": B.pf_report, "pf_nl_opts": B.pf_nl_opts, "pf_result": B.pf_result,
-               "pf_request": B.pf_request, "pf_profile": B.pf_profile}
+               "pf_request": B.pf_request, "pf_profile": B.pf_profile, "pf_batch_tune": B.pf_batch_tune}
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
@@ -68,6 +68,10 @@ def test_errors_without_device_are_reported(lib):
     assert lib.pf_create_grid(1, 4, 4, 1.0, org, None, ctypes.byref(h)) == 1  # PF_E_INVAL
     assert b"nz" in lib.pf_last_error() or b"nx" in lib.pf_last_error()
     assert lib.pf_destroy_grid(None) == 0
+    b = ctypes.c_void_p()
+    assert lib.pf_batch_create(None, 0, None, ctypes.byref(b)) == 1
+    assert b"grid" in lib.pf_last_error()
+    assert lib.pf_batch_destroy(None) == 0
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
