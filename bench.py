@@ -76,7 +76,8 @@ def parse():
     ap.add_argument("--accel-depth", type=int, default=0, help="Anderson depth of the timed solves (0: relaxation)")
     ap.add_argument("--serve-requests", type=int, default=16, help="requests of the serving sample (0: skip)")
     ap.add_argument("--serve-gap", type=float, default=0.25, help="mean inter-arrival time of the serving sample (s)")
-    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=64, help="instances of the batched leg (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     return ap.parse_args()
 
@@ -297,6 +298,48 @@ def serve_sample(api, args, precision):
             "slots": args.serve_slots, "budget_GB": args.serve_budget_gb}
 
 
+# ------------------------------------------------------------------ batched leg
+def batch_sample(api, args, torch, dev):
+    """The batched workload: independent channel problems on [-16, 16]^3 with n in {33, 49, 65, 97}, voltage
+    U[-100, 100] mV and NaCl U[0.01, 0.5] M per instance, solved in one pf_batch (mixed precision, tiles per
+    block from the autotuner) against the same problems solved one after another by the FP64 single-grid
+    path."""
+    from paper_1711_04060_gb300 import workloads as W
+    probs = W.batch_instances(args.batch)
+    grids = [api.Grid.for_problem(p) for p in probs]
+    batch = api.Batch(grids)
+    om = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_MIXED)
+    o64 = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_FP64)
+    try:
+        batch.nonlinear_solve(om, allow=(3,))  # warm-up (runs the autotuner)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        res = batch.nonlinear_solve(om, allow=(3,))
+        torch.cuda.synchronize(dev)
+        t_batch = time.perf_counter() - t0
+        tune = batch.tune()
+        t0 = time.perf_counter()
+        worst_phi, seq_ok = 0.0, True
+        for g, (out, _) in zip(grids, res):
+            ref, rep = g.nonlinear_solve(o64, allow=(3,))
+            seq_ok = seq_ok and rep["status"] == 0
+            worst_phi = max(worst_phi, float(np.abs(out["phi_V"] - ref["phi_V"]).max() /
+                                             max(np.abs(ref["phi_V"]).max(), 0.0257)))
+        torch.cuda.synchronize(dev)
+        t_seq = time.perf_counter() - t0
+    finally:
+        batch.close()
+        for g in grids:
+            g.close()
+    sizes = sorted({p.grid.nx for p in probs})
+    return {"workload": f"{args.batch} channel problems, n in {sizes}, mixed precision, one pf_batch",
+            "value": args.batch / t_batch, "unit": UNIT, "s": t_batch,
+            "all_ok": bool(all(r["status"] == 0 for _, r in res)), "outer_iters_sum": int(sum(r["outer_iters"] for _, r in res)),
+            "tiles_per_block": tune["chosen"],
+            "fp64_single_solves": {"value": args.batch / t_seq, "unit": UNIT, "s": t_seq, "all_ok": seq_ok},
+            "speedup_vs_fp64_single": t_seq / t_batch, "phi_rel_vs_fp64_single": worst_phi}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -465,6 +508,10 @@ def run_ours(args):
         line["e2e"] = {"value": world * max(1, args.steps) / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)}
     grid.close()
+
+    # batched: many uneven problems in shared launches, against the FP64 single-grid path
+    if args.batch > 0 and world == 1:
+        line["batched"] = batch_sample(api, args, torch, dev)
 
     # serving: Poisson arrivals of mixed-size requests through pf_submit / pf_poll
     if args.serve_requests > 0 and world == 1:

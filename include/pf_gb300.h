@@ -299,12 +299,15 @@ pf_status pf_batch_nonlinear_solve(pf_batch* b, const pf_nl_opts* opts, pf_resul
 pf_status pf_batch_destroy(pf_batch* b);
 
 /* ---- serving: continuous batching of PF solves -------------------------------------
- * A server admits submitted problems while their device state fits the HBM budget and a
- * slot is free; each slot is a worker thread with its own CUDA stream, so admitted problems
- * run concurrently on the device.  A worker creates the grid (stream-ordered allocation),
- * solves it exactly as pf_nonlinear_solve does, copies the outputs to host memory and frees
- * the device state at once, returning its bytes to the budget.  Results equal those of
- * pf_nonlinear_solve on the same problem. */
+ * A server runs one scheduler thread over a batched engine (the machinery of pf_batch with 4
+ * tiles per block).  Between two engine steps it admits queued requests, first fit in arrival
+ * order, while fewer than max_slots are in flight and the request's device state fits the
+ * remaining HBM budget; every step runs one outer iteration of all requests in flight in shared
+ * batched launches, so a request that arrives while others run joins their launches at the next
+ * step.  Each request's state stays on the device until it finishes; then its outputs go to host
+ * memory and its device memory returns to the budget at once.  A request's result is bitwise that
+ * of pf_batch_nonlinear_solve on a batch of this problem alone with tiles_per_block 4, and agrees
+ * with pf_nonlinear_solve to the solver tolerance. */
 typedef struct pf_server pf_server;
 
 typedef struct {

@@ -1,15 +1,22 @@
-// pf_batch.cu -- many independent PF problems solved together (pf_batch_*): every BiCGSTAB phase and
-// every FP64 residual of all grids of the batch runs as ONE launch of a batched stencil kernel, and the
-// chunks of BiCGSTAB iterations between two host checks are replayed as a captured CUDA graph.
+// pf_batch.cu -- many independent PF problems solved together: the batched engine behind pf_batch_* and
+// the server.  Every BiCGSTAB phase (Table 3) and every FP64 residual of all problems that need one at the
+// same time runs as ONE launch of a batched stencil kernel, and each problem's chunk of BiCGSTAB iterations
+// between host checks is part of a captured CUDA graph that all iterating problems share.
 //
-// The batched kernel gives each grid a contiguous range of blocks (a block map, block -> grid): nblk
-// blocks for a grid of ntiles tiles, nblk = ceil(ntiles / tiles_per_block), so a block works for one grid
-// only and reduces into that grid's partials and state exactly as the single-grid kernel does.  A grid's
-// reduction order therefore depends only on its own size and tiles_per_block: a problem gives bitwise the
-// same result alone in a batch or in any mix.  tiles_per_block is picked by timing the FP32 phase kernels
-// of the batch's own operators for each candidate (pf_batch_autotune), or set by the caller.  The tensor
-// maps and arguments of all grids live in a device table that the blocks read at start.  Grids whose
-// solve has finished have their state marked done and their blocks return at once.
+// Scheduling is per problem (iteration-level): every problem is a state machine (operators, initial
+// potential, Fermi step, PF1 solve, PF2 solve, outer update, outputs; inside a linear solve: FP64 residual,
+// FP32 inner start, inner chunks, or the FP64 chunks), and every engine tick advances each problem by one
+// step.  The launches of a tick are shared by the problems whose step needs them, so a problem never waits
+// for another problem's linear solve to finish, and problems can join or leave between ticks.
+//
+// The batched kernel gives each problem a contiguous range of blocks: nblk = ceil(ntiles / tiles_per_block)
+// blocks, so a block works for one problem only and reduces into that problem's partials and state exactly
+// as the single-grid kernel does.  A problem's arithmetic and reduction order therefore depend only on its
+// own size and tiles_per_block: its result is bitwise the same alone or in any mix.  A per-launch block map
+// (rewritten every tick) sends the blocks of problems that do not take part in that launch home at once.
+// tiles_per_block is chosen by timing the FP32 phase kernels of the batch's own operators for each
+// candidate (pf_batch_autotune), or set by the caller.  The tensor maps and arguments of all problems live
+// in device tables that each block reads at start.
 #include "pf_grid.cuh"
 #include "pf_stencil.cuh"
 
@@ -60,9 +67,14 @@ __global__ void __launch_bounds__(NTHREADS, Op::MINB)
   stencil_run<Op>(&it->maps, sa, sg, sn[0], sn[1], sn[2], wait_limit);
 }
 
-__global__ void k_gather_states(BicgState* const* __restrict__ src, int n, BicgState* __restrict__ dst) {
+// dst[i] = *st64[i] (FP64 / refinement state) and dst[n + i] = *st32[i] (FP32 inner state) of every member
+__global__ void k_gather_states(BicgState* const* __restrict__ st64, BicgState* const* __restrict__ st32, int n,
+                                BicgState* __restrict__ dst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = *src[i];
+  if (i < n) {
+    dst[i] = *st64[i];
+    dst[n + i] = *st32[i];
+  }
 }
 
 }  // namespace pf
@@ -70,27 +82,46 @@ __global__ void k_gather_states(BicgState* const* __restrict__ src, int n, BicgS
 using namespace pfi;
 using pf::BicgState;
 
+using namespace pfi;
+using pf::BicgState;
+
+namespace {
+
+// the launch kinds of a tick, per operator (x3): map slots in the device map pool
+enum { K_RES0 = 0, K_RES1, K_PRIME32, K_PRIME64, K_CHUNK32, K_CHUNK64, K_PER_OP };
+constexpr int N_OPS = 3;
+constexpr int SLOT_FULL = N_OPS * K_PER_OP;  // every member active (autotuner)
+constexpr int N_SLOTS = SLOT_FULL + 1;
+
+}  // namespace
+
 struct pf_batch {
-  std::vector<pf_grid*> grids;
+  std::vector<pf_grid*> grids;    // grids[i] belongs to members[i]
+  std::vector<pfi::BatchMember> members;
   cudaStream_t user = nullptr;    // the caller's stream
-  cudaStream_t stream = nullptr;  // the batch's own stream (graphs are captured on it)
-  int tpb = 0;  // tiles per block; 0: tune at the next solve
+  cudaStream_t stream = nullptr;  // the batch's own stream: per-problem work, tables, state read-back
+  cudaStream_t ops[N_OPS] = {};   // the batched launches of each operator run concurrently on these
+  cudaStream_t cstream = nullptr; // chunk graphs are captured here
+  cudaEvent_t fork = nullptr, join[N_OPS] = {};
+  int tpb = 0;                    // tiles per block; 0: tune at the next solve
   pf_batch_tune tune{};
-  // launch descriptors: a device arena filled from a pinned staging copy
+  // device arena for launch tables, filled from a pinned staging copy
   unsigned char* darena = nullptr;
   unsigned char* harena = nullptr;
   size_t cap = 0, top = 0;
-  std::map<std::string, const void*> items;  // launch kind -> device item table
+  // tables built for the current membership (invalidated when it changes)
+  bool built = false;
+  int nblocks = 0;                      // blocks of a batched launch (all members)
+  std::vector<int> block0, nblk;        // block range of each member
+  int* dmaps = nullptr;                 // N_SLOTS block maps of nblocks entries
+  std::vector<int> hmaps;
+  BicgState** dst64 = nullptr;          // members' state pointers (device)
+  BicgState** dst32 = nullptr;
+  std::map<std::string, const void*> items;
   std::map<std::string, cudaGraphExec_t> graphs;
-  // the grids of the current launch set, in batch order, with their block map
-  std::vector<int> set;
-  int set_tpb = -1;
-  const int* dmap = nullptr;
-  int nblocks = 0;
-  BicgState** dst_fp64 = nullptr;  // device arrays of the set's state pointers
-  BicgState** dst_fp32 = nullptr;
-  BicgState* dgather = nullptr;    // gathered states (device) and their pinned host copy
+  BicgState* dgather = nullptr;         // gathered states (device) and their pinned copy
   BicgState* hgather = nullptr;
+  int gather_cap = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
 
@@ -112,30 +143,6 @@ Krylov<double> kryT<double>(pf_grid* g) { return kry64(g); }
 template <>
 Krylov<float> kryT<float>(pf_grid* g) { return kry32(g); }
 
-void drop_launches(pf_batch* B) {
-  cudaStreamSynchronize(B->stream);
-  for (auto& kv : B->graphs) cudaGraphExecDestroy(kv.second);
-  B->graphs.clear();
-  B->items.clear();
-  B->top = 0;
-  B->set.clear();
-  B->set_tpb = -1;
-  B->dmap = nullptr;
-}
-
-// Copies host bytes into the arena (after the stream has drained, so no queued copy still reads the
-// staging area); nullptr when the arena is full.
-const void* upload(pf_batch* B, const void* src, size_t bytes) {
-  const size_t at = (B->top + 255) / 256 * 256;
-  if (at + bytes > B->cap) return nullptr;
-  cudaStreamSynchronize(B->stream);
-  memcpy(B->harena + at, src, bytes);
-  if (cudaMemcpyAsync(B->darena + at, B->harena + at, bytes, cudaMemcpyHostToDevice, B->stream) != cudaSuccess)
-    return nullptr;
-  B->top = at + bytes;
-  return B->darena + at;
-}
-
 int blocks_for(int ntiles, int tpb) {
   int b = (ntiles + tpb - 1) / tpb;
   const int cap = pf::max_partial_blocks();
@@ -144,32 +151,79 @@ int blocks_for(int ntiles, int tpb) {
   return b < 1 ? 1 : b;
 }
 
-// Makes `set` (indices into the batch, in order) the current launch set: block map and state pointers.
-pf_status use_set(pf_batch* B, const std::vector<int>& set) {
-  if (set == B->set && B->set_tpb == B->tpb && B->dmap) return PF_OK;
-  drop_launches(B);
-  std::vector<int> map;
-  for (size_t j = 0; j < set.size(); ++j) {
-    const pf_grid* g = B->grids[set[j]];
-    const int nb = blocks_for(g->L.ntiles, B->tpb);
-    for (int b = 0; b < nb; ++b) map.push_back((int)j);
+void drain(pf_batch* B) {
+  cudaStreamSynchronize(B->stream);
+  for (int o = 0; o < N_OPS; ++o)
+    if (B->ops[o]) cudaStreamSynchronize(B->ops[o]);
+}
+
+// Forgets every table and graph (after every stream drained).
+void invalidate(pf_batch* B) {
+  drain(B);
+  for (auto& kv : B->graphs) cudaGraphExecDestroy(kv.second);
+  B->graphs.clear();
+  B->items.clear();
+  B->top = 0;
+  B->built = false;
+}
+
+// Copies host bytes into the arena and waits for the copy, so that launches on any stream may read them;
+// nullptr when the arena is full.
+const void* upload(pf_batch* B, const void* src, size_t bytes) {
+  const size_t at = (B->top + 255) / 256 * 256;
+  if (at + bytes > B->cap) return nullptr;
+  cudaStreamSynchronize(B->stream);
+  memcpy(B->harena + at, src, bytes);
+  if (cudaMemcpyAsync(B->darena + at, B->harena + at, bytes, cudaMemcpyHostToDevice, B->stream) != cudaSuccess ||
+      cudaStreamSynchronize(B->stream) != cudaSuccess)
+    return nullptr;
+  B->top = at + bytes;
+  return B->darena + at;
+}
+
+// Block ranges, map pool and state pointers for the current members (tables are built on first use).
+pf_status build(pf_batch* B) {
+  if (B->built) return PF_OK;
+  invalidate(B);
+  const int n = (int)B->grids.size();
+  B->block0.assign(n, 0);
+  B->nblk.assign(n, 0);
+  int nb = 0;
+  for (int i = 0; i < n; ++i) {
+    B->block0[i] = nb;
+    B->nblk[i] = blocks_for(B->grids[i]->L.ntiles, B->tpb);
+    nb += B->nblk[i];
   }
-  B->dmap = static_cast<const int*>(upload(B, map.data(), map.size() * sizeof(int)));
+  B->nblocks = nb;
+  B->hmaps.assign((size_t)N_SLOTS * nb, -1);
+  for (int i = 0; i < n; ++i)
+    for (int b = 0; b < B->nblk[i]; ++b) B->hmaps[(size_t)SLOT_FULL * nb + B->block0[i] + b] = i;
+  B->dmaps = (int*)upload(B, B->hmaps.data(), B->hmaps.size() * sizeof(int));
   std::vector<BicgState*> s64, s32;
-  for (int i : set) {
-    s64.push_back(B->grids[i]->st);
-    s32.push_back(B->grids[i]->st2);
+  for (pf_grid* g : B->grids) {
+    s64.push_back(g->st);
+    s32.push_back(g->st2);
   }
-  B->dst_fp64 = (BicgState**)upload(B, s64.data(), s64.size() * sizeof(BicgState*));
-  B->dst_fp32 = (BicgState**)upload(B, s32.data(), s32.size() * sizeof(BicgState*));
-  if (!B->dmap || !B->dst_fp64 || !B->dst_fp32) return fail(PF_E_OOM, "batch launch table does not fit");
-  B->nblocks = (int)map.size();
-  B->set = set;
-  B->set_tpb = B->tpb;
+  B->dst64 = (BicgState**)upload(B, s64.data(), s64.size() * sizeof(BicgState*));
+  B->dst32 = (BicgState**)upload(B, s32.data(), s32.size() * sizeof(BicgState*));
+  if (!B->dmaps || !B->dst64 || !B->dst32) return fail(PF_E_OOM, "batch launch tables do not fit");
+  if (n > B->gather_cap) {
+    if (B->dgather) cudaFree(B->dgather);
+    if (B->hgather) cudaFreeHost(B->hgather);
+    B->dgather = nullptr;
+    B->hgather = nullptr;
+    B->gather_cap = 0;
+    PF_CK(cudaMalloc(&B->dgather, 2 * n * sizeof(BicgState)));
+    PF_CK(cudaMallocHost(&B->hgather, 2 * n * sizeof(BicgState)));
+    B->gather_cap = n;
+  }
+  B->built = true;
   return PF_OK;
 }
 
-// The item table of one launch kind over the current set, built on first use.
+const int* map_of(pf_batch* B, int slot) { return B->dmaps + (size_t)slot * B->nblocks; }
+
+// The item table of one launch kind over all members, built on first use.
 template <class Op, class Fill>
 pf_status items_for(pf_batch* B, const std::string& key, Fill fill, const void** out) {
   auto it = B->items.find(key);
@@ -177,29 +231,27 @@ pf_status items_for(pf_batch* B, const std::string& key, Fill fill, const void**
     *out = it->second;
     return PF_OK;
   }
-  std::vector<pf::BatchItem<Op>> v(B->set.size());
-  int block0 = 0;
-  for (size_t j = 0; j < B->set.size(); ++j) {
-    pf_grid* g = B->grids[B->set[j]];
-    PF_TRY(fill(g, v[j]));
+  std::vector<pf::BatchItem<Op>> v(B->grids.size());
+  for (size_t j = 0; j < B->grids.size(); ++j) {
+    pf_grid* g = B->grids[j];
+    PF_TRY(fill((int)j, g, v[j]));
     v[j].g = g->geom;
     v[j].ntiles = g->L.ntiles;
-    v[j].nblk = blocks_for(g->L.ntiles, B->tpb);
-    v[j].block0 = block0;
-    block0 += v[j].nblk;
+    v[j].nblk = B->nblk[j];
+    v[j].block0 = B->block0[j];
   }
   const void* d = upload(B, v.data(), v.size() * sizeof(v[0]));
-  if (!d) return fail(PF_E_OOM, "batch launch table does not fit");
+  if (!d) return fail(PF_E_OOM, "batch launch tables do not fit");
   B->items[key] = d;
   *out = d;
   return PF_OK;
 }
 
 template <class Op>
-pf_status launch_items(pf_batch* B, const void* items) {
+pf_status launch_items(pf_batch* B, const void* items, const int* map, cudaStream_t st) {
   static_assert(pf::scratch_fits<Op>(), "reduction scratch must fit in the stage ring");
-  pf::k_stencil_batch<Op><<<B->nblocks, pf::NTHREADS, pf::smem_bytes<Op>(), B->stream>>>(
-      static_cast<const pf::BatchItem<Op>*>(items), B->dmap, WAIT_LIMIT);
+  pf::k_stencil_batch<Op><<<B->nblocks, pf::NTHREADS, pf::smem_bytes<Op>(), st>>>(
+      static_cast<const pf::BatchItem<Op>*>(items), map, WAIT_LIMIT);
   PF_CK(cudaGetLastError());
   return PF_OK;
 }
@@ -216,11 +268,15 @@ void set_attrs() {
   if constexpr (sizeof(T) == 8) set_smem_attr<pf::OpResSkip<UNI>>();
 }
 
-std::string key_of(const char* kind, int op, int f64, int par, const void* x, const void* b) {
-  char buf[128];
-  snprintf(buf, sizeof buf, "%s|%d|%d|%d|%p|%p", kind, op, f64, par, x, b);
+std::string key_of(const char* kind, int op, int f64, int par) {
+  char buf[64];
+  snprintf(buf, sizeof buf, "%s|%d|%d|%d", kind, op, f64, par);
   return buf;
 }
+
+// The unknown and right-hand side of each operator's linear solve inside the nonlinear iteration.
+double* x_of(pf_grid* g, int op) { return op == PF_OP_POISSON ? g->phi0 : op == PF_OP_PF1 ? g->psi : g->phi; }
+const double* b_of(const pf_grid* g, int op) { return op == PF_OP_PF1 ? g->b1 : g->b2; }
 
 // ---- item fillers (the same arrays, in the same slots, as the single-grid launches)
 template <typename T, bool UNI>
@@ -281,221 +337,386 @@ pf_status fill_res(pf_grid* g, int op, int init, const double* x, const double* 
   return PF_OK;
 }
 
-// One unknown of a batched linear solve.
-struct Job {
-  int inst;          // index in the batch
-  double* x;         // unknown (in: start, out: solution)
-  const double* b;   // right-hand side
-  double eta = 0.0;  // forcing: also stop at eta ||r0||
-  int iters = 0, refs = 0;
-  int status = PF_OK;
-  bool running = true;
-};
 
-pf_status gather(pf_batch* B, bool fp32, std::vector<BicgState>& out) {
-  const int n = (int)B->set.size();
-  pf::k_gather_states<<<(n + 127) / 128, 128, 0, B->stream>>>(fp32 ? B->dst_fp32 : B->dst_fp64, n, B->dgather);
-  PF_CK(cudaGetLastError());
-  PF_CK(cudaMemcpyAsync(B->hgather, B->dgather, n * sizeof(BicgState), cudaMemcpyDeviceToHost, B->stream));
-  PF_CK(cudaStreamSynchronize(B->stream));
-  out.assign(B->hgather, B->hgather + n);
-  return PF_OK;
+// ---- batched launches over the members flagged in a map slot -----------------------------------------
+template <bool UNI>
+pf_status launch_res(pf_batch* B, int op, int init, const int* map, cudaStream_t st) {
+  using OR = pf::OpResSkip<UNI>;
+  const void* items = nullptr;
+  PF_TRY((items_for<OR>(B, key_of(init ? "RES1" : "RES0", op, 1, 0),
+                        [&](int, pf_grid* g, pf::BatchItem<OR>& it) {
+                          return fill_res<UNI>(g, op, init, x_of(g, op), b_of(g, op), it);
+                        },
+                        &items)));
+  return launch_items<OR>(B, items, map, st);
 }
 
-// BiCGSTAB iterations of the current set (prime, then chunks of [B, C+A] pairs replayed as one graph)
-// until every grid's state is done.  x is the FP64 unknown of each job (FP64) or the FP32 correction.
 template <typename T, bool UNI>
-pf_status batch_iterate(pf_batch* B, int op, const std::vector<Job>& jobs, int max_iter, std::vector<BicgState>& fin) {
+pf_status ca_items(pf_batch* B, int op, int par, int prime, const void** out) {
+  using OC = pf::OpCA<T, UNI>;
   constexpr int f64 = sizeof(T) == 8;
+  return items_for<OC>(B, key_of(prime ? "CAP" : "CA", op, f64, par),
+                       [&](int, pf_grid* g, pf::BatchItem<OC>& it) {
+                         T* x;
+                         if constexpr (f64) x = x_of(g, op); else x = g->d32;
+                         return fill_ca<T, UNI>(g, op, par, prime, x, it);
+                       },
+                       out);
+}
+
+template <typename T, bool UNI>
+pf_status launch_prime(pf_batch* B, int op, const int* map, cudaStream_t st) {
+  const void* items = nullptr;
+  PF_TRY((ca_items<T, UNI>(B, op, 0, 1, &items)));
+  return launch_items<pf::OpCA<T, UNI>>(B, items, map, st);
+}
+
+// CHUNK BiCGSTAB iterations (from parity 1, where every chunk starts since CHUNK is even) of the members in
+// the map slot: one captured graph per operator and precision, replayed while the membership stands.
+template <typename T, bool UNI>
+pf_status launch_chunk(pf_batch* B, int op, const int* map, cudaStream_t st) {
   using OB = pf::OpB<T, UNI>;
   using OC = pf::OpCA<T, UNI>;
-  // the unknowns of the set, in set order (FP32: the corrections)
-  auto xof = [&](pf_grid* g, size_t j) -> T* {
-    if constexpr (f64) return jobs[j].x; else return g->d32;
-  };
-  const void* x0key = f64 ? (const void*)jobs[0].x : (const void*)B->grids[jobs[0].inst]->d32;
-  const void *ib[2], *ica[2], *iprime;
-  size_t jj = 0;
-  for (int par = 0; par < 2; ++par) {
-    PF_TRY((items_for<OB>(B, key_of("B", op, f64, par, x0key, nullptr),
-                          [&](pf_grid* g, pf::BatchItem<OB>& it) { return fill_b<T, UNI>(g, op, par, it); },
-                          &ib[par])));
-    jj = 0;
-    PF_TRY((items_for<OC>(B, key_of("CA", op, f64, par, x0key, nullptr),
-                          [&](pf_grid* g, pf::BatchItem<OC>& it) { return fill_ca<T, UNI>(g, op, par, 0, xof(g, jj++), it); },
-                          &ica[par])));
-  }
-  jj = 0;
-  PF_TRY((items_for<OC>(B, key_of("CAprime", op, f64, 0, x0key, nullptr),
-                        [&](pf_grid* g, pf::BatchItem<OC>& it) { return fill_ca<T, UNI>(g, op, 0, 1, xof(g, jj++), it); },
-                        &iprime)));
-  PF_TRY(launch_items<OC>(B, iprime));
-  // the chunk graph: CHUNK iterations starting at parity 1 (CHUNK is even, so every chunk starts there)
-  const std::string gk = key_of("graph", op, f64, 0, x0key, nullptr);
+  constexpr int f64 = sizeof(T) == 8;
+  const std::string gk = key_of("graph", op, f64, 0);
   auto git = B->graphs.find(gk);
-  cudaGraphExec_t exec = nullptr;
-  if (git != B->graphs.end()) {
-    exec = git->second;
-  } else {
+  if (git == B->graphs.end()) {
+    const void *ib[2], *ica[2];
+    for (int par = 0; par < 2; ++par) {
+      PF_TRY((items_for<OB>(B, key_of("B", op, f64, par),
+                            [&](int, pf_grid* g, pf::BatchItem<OB>& it) { return fill_b<T, UNI>(g, op, par, it); },
+                            &ib[par])));
+      PF_TRY((ca_items<T, UNI>(B, op, par, 0, &ica[par])));
+    }
     cudaGraph_t graph = nullptr;
-    PF_CK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+    PF_CK(cudaStreamBeginCapture(B->cstream, cudaStreamCaptureModeThreadLocal));
     int cur = 1;
     pf_status ls = PF_OK;
     for (int i = 0; i < CHUNK && ls == PF_OK; ++i) {
-      ls = launch_items<OB>(B, ib[cur]);
-      if (ls == PF_OK) ls = launch_items<OC>(B, ica[cur]);
+      ls = launch_items<OB>(B, ib[cur], map, B->cstream);
+      if (ls == PF_OK) ls = launch_items<OC>(B, ica[cur], map, B->cstream);
       cur = 1 - cur;
     }
-    const cudaError_t ce = cudaStreamEndCapture(B->stream, &graph);
+    const cudaError_t ce = cudaStreamEndCapture(B->cstream, &graph);
     if (ls != PF_OK) {
       if (graph) cudaGraphDestroy(graph);
       return ls;
     }
     PF_CK(ce);
+    cudaGraphExec_t exec = nullptr;
     const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     PF_CK(ie);
-    B->graphs[gk] = exec;
+    git = B->graphs.emplace(gk, exec).first;
   }
-  // every state ends within max_iter iterations (its own limit); the host bound only guards the loop
-  for (long chunk = 0; chunk <= max_iter / CHUNK + 2; ++chunk) {
-    PF_CK(cudaGraphLaunch(exec, B->stream));
-    PF_TRY(gather(B, !f64, fin));
-    bool all = true;
-    for (size_t j = 0; j < fin.size(); ++j) all = all && fin[j].done;
-    if (all) return PF_OK;
-  }
-  return fail(PF_E_NOCONV, "batched BiCGSTAB did not finish within its iteration limit");
-}
-
-// The FP64 residual b - A x of every running job (init: also start BiCGSTAB in the FP64 Krylov vectors).
-// Each running job's state must have been reset; the others are marked done and skipped.
-template <bool UNI>
-pf_status batch_residual(pf_batch* B, int op, std::vector<Job>& jobs, int init) {
-  using OR = pf::OpResSkip<UNI>;
-  const void* items = nullptr;
-  size_t jj = 0;
-  PF_TRY((items_for<OR>(B, key_of(init ? "RES1" : "RES0", op, 1, 0, jobs[0].x, jobs[0].b),
-                        [&](pf_grid* g, pf::BatchItem<OR>& it) {
-                          const Job& J = jobs[jj++];
-                          return fill_res<UNI>(g, op, init, J.x, J.b, it);
-                        },
-                        &items)));
-  return launch_items<OR>(B, items);
-}
-
-template <bool UNI>
-pf_status batch_solve_fp64(pf_batch* B, int op, std::vector<Job>& jobs, const pf_solve_opts& o) {
-  for (Job& J : jobs) {
-    pf_grid* g = B->grids[J.inst];
-    const OpArrays<double> A = ops64(g, op);
-    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_impose(J.x, J.b, A.dinv, g->geom.np, B->stream));
-    PF_TRY(set_state(g, g->st, o.tol, o.norm, o.max_iter, J.eta));
-    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(J.b, g->geom, g->st, B->stream));
-  }
-  PF_TRY(batch_residual<UNI>(B, op, jobs, 1));
-  std::vector<BicgState> fin;
-  PF_TRY((batch_iterate<double, UNI>(B, op, jobs, o.max_iter, fin)));
-  for (size_t j = 0; j < jobs.size(); ++j) {
-    jobs[j].iters = fin[j].iter;
-    jobs[j].status = fin[j].status;
-  }
+  PF_CK(cudaGraphLaunch(git->second, st));
   return PF_OK;
 }
 
 template <bool UNI>
-pf_status batch_solve_mixed(pf_batch* B, int op, std::vector<Job>& jobs, const pf_solve_opts& o) {
-  for (Job& J : jobs) {
-    pf_grid* g = B->grids[J.inst];
-    const OpArrays<double> A = ops64(g, op);
-    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_impose(J.x, J.b, A.dinv, g->geom.np, B->stream));
-    J.running = true;
-    J.iters = J.refs = 0;
-    J.status = PF_E_NOCONV;
+pf_status launch_kind(pf_batch* B, int op, int kind, const int* map, cudaStream_t st) {
+  switch (kind) {
+    case K_RES0: return launch_res<UNI>(B, op, 0, map, st);
+    case K_RES1: return launch_res<UNI>(B, op, 1, map, st);
+    case K_PRIME32: return launch_prime<float, UNI>(B, op, map, st);
+    case K_PRIME64: return launch_prime<double, UNI>(B, op, map, st);
+    case K_CHUNK32: return launch_chunk<float, UNI>(B, op, map, st);
+    default: return launch_chunk<double, UNI>(B, op, map, st);
   }
-  std::vector<BicgState> st;
-  for (;;) {
-    // FP64 true residual of the jobs still refining -> b32 (the others are skipped)
-    for (Job& J : jobs) {
-      pf_grid* g = B->grids[J.inst];
-      if (J.running) {
-        PF_TRY(set_state(g, g->st, o.tol, o.norm, 0, J.eta, J.refs > 0));
-        PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(J.b, g->geom, g->st, B->stream));
-      } else {
-        PF_CK(pf::launch_mark_done(g->st, B->stream));
-      }
+}
+
+// ---- the per-problem state machine ---------------------------------------------------------------
+enum Stage { S_NEW = 0, S_FERMI, S_PF2RHS, S_LIN, S_UPDATE, S_FINISH, S_DONE };
+enum Sub { L_RES = 0, L_INNER_START, L_INNER, L_START64, L_ITER64 };
+
+// Starts the linear solve of operator op (unknown and right-hand side of x_of / b_of) in this tick.
+pf_status lin_start(pf_batch* B, BatchMember& M, int op, int next_stage, double eta) {
+  pf_grid* g = M.g;
+  M.stage = S_LIN;
+  M.after = next_stage;
+  M.op = op;
+  M.eta = eta;
+  M.iters = M.refs = 0;
+  M.add_pending = false;
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_impose(x_of(g, op), b_of(g, op), ops64(g, op).dinv, g->geom.np, B->stream));
+  M.sub = M.o.lin.precision == PF_MIXED ? L_RES : L_START64;
+  return PF_OK;
+}
+
+// The per-member work of a tick before the batched launches; sets the launch kinds the member takes part in.
+pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
+  pf_grid* g = M.g;
+  cudaStream_t s = B->stream;
+  const long NP = g->geom.np;
+  const pf_solve_opts& lo = M.o.lin;
+  switch (M.stage) {
+    case S_NEW: {
+      pf_result& r = *M.res;
+      r.status = PF_OK;
+      r.outer_iters = r.lin_iters_total = r.lin_iters_first = 0;
+      r.delta = 0.0;
+      M.U = OuterUpdate{};
+      M.dprev = 1.0;
+      M.st = PF_OK;
+      if (M.o.accel_depth > 0) PF_TRY(ensure_aa(g, M.o.accel_depth));
+      PF_TRY(build_operators(g));
+      // initial potential (Table 4): PF2 with rho' = Psi = 0
+      PF_CK(cudaMemsetAsync(g->phi0, 0, NP * sizeof(double), s));
+      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, g->geom, s));
+      PF_CK(cudaMemsetAsync(g->psi, 0, NP * sizeof(double), s));
+      PF_LAUNCH(g, PF_PROF_OTHER,
+                pf::launch_pf2_rhs(g->psi, g->solvent, g->ffix, g->eps_s, g->lo_hat, g->hi_hat, g->geom, g->b2, s));
+      PF_TRY(lin_start(B, M, PF_OP_POISSON, S_FERMI, 0.0));
+      break;
     }
-    PF_TRY(batch_residual<UNI>(B, op, jobs, 0));
-    PF_TRY(gather(B, false, st));
-    bool any = false;
-    for (size_t j = 0; j < jobs.size(); ++j) {
-      Job& J = jobs[j];
-      if (!J.running) continue;
-      if (st[j].done) {
-        J.status = PF_OK;
-        J.running = false;
-      } else if (!isfinite(st[j].rnorm2)) {
-        J.status = PF_E_BREAKDOWN;
-        J.running = false;
-      } else if (J.refs >= o.max_refine || J.iters >= o.max_iter) {
-        J.status = PF_E_NOCONV;
-        J.running = false;
-      }
-      any = any || J.running;
+    case S_FERMI: {
+      // Eq. (1) at Phi_0 -> b_PF1, kappa, PF2 right-hand-side part; then PF1 (Eq. 12)
+      const int outer = M.res->outer_iters + 1;
+      const double eta = M.o.lin_forcing > 0 ? (outer == 1 ? 1e-2 : fmin(1e-2, M.o.lin_forcing * M.dprev)) : 0.0;
+      PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+      PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, g->geom, g->b1, g->sig,
+                                                   g->c2, nullptr, nullptr, nullptr, g->ulast, outer > 1, g->err, s));
+      PF_TRY(update_pf2(g));
+      PF_TRY(lin_start(B, M, PF_OP_PF1, S_PF2RHS, eta));
+      break;
     }
-    if (!any) break;
-    // FP32 inner solves A d = r of the running jobs from d = 0 to inner_tol (the others skip)
-    for (Job& J : jobs) {
-      pf_grid* g = B->grids[J.inst];
-      if (!J.running) {
-        PF_CK(pf::launch_mark_done(g->st2, B->stream));
-        continue;
+    case S_PF2RHS: {
+      // PF2 right-hand side from Psi, then PF2 (Eq. 13) from Phi_0
+      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat,
+                                                     g->geom, g->b2, s));
+      PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      PF_TRY(lin_start(B, M, PF_OP_PF2, S_UPDATE, M.eta));
+      break;
+    }
+    case S_FINISH: {
+      pf_result& r = *M.res;
+      PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+      PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, g->geom, nullptr, nullptr,
+                                                   nullptr, g->Cbuf, g->Sbuf, g->Gbuf, g->ulast, r.outer_iters > 0,
+                                                   g->err, s));
+      if (r.phi_V) {
+        PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, NP, s));
+        PF_TRY(unpack_out(g, g->phi, 1, r.phi_V, r.mem));
       }
+      if (r.C_M) {
+        PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->Cbuf, 1.0 / g->molar, g->Cbuf, NP * g->sp.ns, s));
+        PF_TRY(unpack_out(g, g->Cbuf, g->sp.ns, r.C_M, r.mem));
+      }
+      if (r.S) PF_TRY(unpack_out(g, g->Sbuf, 1, r.S, r.mem));
+      if (r.Gamma) PF_TRY(unpack_out(g, g->Gbuf, 1, r.Gamma, r.mem));
+      if (r.Psi) PF_TRY(unpack_out(g, g->psi, 1, r.Psi, r.mem));
+      PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      return PF_OK;
+    }
+    case S_UPDATE:
+      return outer_stage1(g, M.U, M.o.accel_depth, M.o.omega);
+    default:
+      break;
+  }
+  if (M.stage != S_LIN) return PF_OK;
+  const int base = M.op * K_PER_OP;
+  switch (M.sub) {
+    case L_RES:  // FP64 true residual b - A x -> b32 (mixed precision)
+      if (M.add_pending) {
+        PF_LAUNCH(g, PF_PROF_RESIDUAL, pf::launch_add_f32(x_of(g, M.op), g->d32, NP, s));  // x += d
+        M.add_pending = false;
+      }
+      PF_TRY(set_state(g, g->st, lo.tol, lo.norm, 0, M.eta, M.refs > 0));
+      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b_of(g, M.op), g->geom, g->st, s));
+      kinds.push_back(base + K_RES0);
+      break;
+    case L_INNER_START: {  // FP32 inner solve A d = r from d = 0 to inner_tol, prime and first chunk
       const Krylov<float> K = kry32(g);
-      PF_CK(cudaMemsetAsync(g->d32, 0, g->geom.np * sizeof(float), B->stream));
-      const int cap = o.max_iter - J.iters < INNER_CAP ? o.max_iter - J.iters : INNER_CAP;
-      PF_TRY(set_state(g, g->st2, o.inner_tol, PF_NORM_REL2, cap));
+      PF_CK(cudaMemsetAsync(g->d32, 0, NP * sizeof(float), s));
+      const int cap = lo.max_iter - M.iters < INNER_CAP ? lo.max_iter - M.iters : INNER_CAP;
+      PF_TRY(set_state(g, g->st2, lo.inner_tol, PF_NORM_REL2, cap));
       PF_LAUNCH(g, PF_PROF_INIT, pf::launch_init_zero<float>(g->b32, g->geom, K.r[0], K.rt, K.p[0], K.v[0], K.t,
-                                                              g->part, g->st2, B->stream));
+                                                              g->part, g->st2, s));
+      kinds.push_back(base + K_PRIME32);
+      kinds.push_back(base + K_CHUNK32);
+      M.sub = L_INNER;
+      break;
     }
-    std::vector<BicgState> fin;
-    PF_TRY((batch_iterate<float, UNI>(B, op, jobs, INNER_CAP, fin)));
-    for (size_t j = 0; j < jobs.size(); ++j) {
-      Job& J = jobs[j];
-      if (!J.running) continue;
-      pf_grid* g = B->grids[J.inst];
-      J.iters += fin[j].iter;
-      ++J.refs;
-      if (fin[j].status == PF_E_BREAKDOWN && fin[j].iter == 0) {
-        J.status = PF_E_BREAKDOWN;
-        J.running = false;
-        continue;
-      }
-      PF_LAUNCH(g, PF_PROF_RESIDUAL, pf::launch_add_f32(J.x, g->d32, g->geom.np, B->stream));  // x += d
-    }
+    case L_INNER:
+      kinds.push_back(base + K_CHUNK32);
+      break;
+    case L_START64:  // FP64 BiCGSTAB: r0 = b - A x, prime and first chunk
+      PF_TRY(set_state(g, g->st, lo.tol, lo.norm, lo.max_iter, M.eta));
+      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b_of(g, M.op), g->geom, g->st, s));
+      kinds.push_back(base + K_RES1);
+      kinds.push_back(base + K_PRIME64);
+      kinds.push_back(base + K_CHUNK64);
+      M.sub = L_ITER64;
+      break;
+    case L_ITER64:
+      kinds.push_back(base + K_CHUNK64);
+      break;
   }
   return PF_OK;
 }
 
-// A batched linear solve of the given jobs (one operator for all).
-pf_status batch_solve(pf_batch* B, int op, std::vector<Job>& jobs, const pf_solve_opts& o) {
-  if (jobs.empty()) return PF_OK;
-  std::vector<int> set;
-  for (const Job& J : jobs) set.push_back(J.inst);
-  PF_TRY(use_set(B, set));
-  const bool uni = op == PF_OP_PF1;
-  if (o.precision == PF_MIXED)
-    return uni ? batch_solve_mixed<true>(B, op, jobs, o) : batch_solve_mixed<false>(B, op, jobs, o);
-  return uni ? batch_solve_fp64<true>(B, op, jobs, o) : batch_solve_fp64<false>(B, op, jobs, o);
+// Ends the member's linear solve with status ls and moves it on.
+void lin_end(BatchMember& M, int ls) {
+  if (trace_level() > 0)
+    fprintf(stderr, "[pf batch] member %lld op %d linear solve: status %d iters %d refinements %d\n", M.tag, M.op, ls,
+            M.iters, M.refs);
+  M.res->lin_iters_total += M.iters;
+  if (M.op == PF_OP_POISSON) M.res->lin_iters_first = M.iters;
+  if (ls != PF_OK) {
+    M.st = (pf_status)ls;
+    M.stage = S_FINISH;
+  } else {
+    M.stage = M.after;
+  }
+}
+
+// The member's transition after the tick's launches landed (states gathered: s64 = st, s32 = st2).
+void post(BatchMember& M, const BicgState& s64, const BicgState& s32) {
+  const pf_solve_opts& lo = M.o.lin;
+  if (M.stage != S_LIN) return;
+  switch (M.sub) {
+    case L_RES:
+      if (s64.done) {
+        lin_end(M, PF_OK);
+      } else if (!isfinite(s64.rnorm2)) {
+        lin_end(M, PF_E_BREAKDOWN);
+      } else if (M.refs >= lo.max_refine || M.iters >= lo.max_iter) {
+        lin_end(M, PF_E_NOCONV);
+      } else {
+        M.sub = L_INNER_START;
+      }
+      break;
+    case L_INNER:
+      if (s32.done) {
+        M.iters += s32.iter;
+        ++M.refs;
+        if (s32.status == PF_E_BREAKDOWN && s32.iter == 0) {
+          lin_end(M, PF_E_BREAKDOWN);
+        } else {
+          M.add_pending = true;
+          M.sub = L_RES;
+        }
+      }
+      break;
+    case L_ITER64:
+      if (s64.done) {
+        M.iters = s64.iter;
+        lin_end(M, s64.status);
+      }
+      break;
+    default:
+      break;
+  }
+}
+
+// One tick of the engine over all members.
+pf_status tick(pf_batch* B) {
+  PF_TRY(build(B));
+  cudaStream_t s = B->stream;
+  const int n = (int)B->members.size();
+  std::vector<std::vector<int>> kinds(n);
+  std::vector<char> use(N_SLOTS, 0);
+  // the stage each member was in at the start of the tick (the one whose work this tick runs)
+  std::vector<int> was(n);
+  for (int i = 0; i < n; ++i) {
+    BatchMember& M = B->members[i];
+    was[i] = M.stage;
+    if (M.stage == S_DONE) continue;
+    PF_TRY(pre(B, M, kinds[i]));
+    for (int k : kinds[i]) use[k] = 1;
+  }
+  // block maps of the launch kinds in use: a member's blocks in the kinds it takes part in, -1 elsewhere
+  const int nb = B->nblocks;
+  for (int k = 0; k < SLOT_FULL; ++k)
+    if (use[k]) std::fill(B->hmaps.begin() + (size_t)k * nb, B->hmaps.begin() + (size_t)(k + 1) * nb, -1);
+  for (int i = 0; i < n; ++i)
+    for (int k : kinds[i])
+      for (int b = 0; b < B->nblk[i]; ++b) B->hmaps[(size_t)k * nb + B->block0[i] + b] = i;
+  // (the previous tick ended with a synchronisation, so the staging area is free)
+  int lo = SLOT_FULL, hi = -1;
+  for (int k = 0; k < SLOT_FULL; ++k)
+    if (use[k]) {
+      lo = std::min(lo, k);
+      hi = std::max(hi, k);
+    }
+  if (hi >= lo) {
+    const size_t off = (size_t)lo * nb * sizeof(int), bytes = (size_t)(hi - lo + 1) * nb * sizeof(int);
+    unsigned char* stage = B->harena + ((unsigned char*)B->dmaps - B->darena) + off;
+    memcpy(stage, (const unsigned char*)B->hmaps.data() + off, bytes);
+    PF_CK(cudaMemcpyAsync((unsigned char*)B->dmaps + off, stage, bytes, cudaMemcpyHostToDevice, s));
+  }
+  // the batched launches of each operator (residuals, then primes, then the chunk graphs) on the
+  // operator's own stream, so that the launches of different operators overlap on the device
+  const int order[] = {K_RES0, K_RES1, K_PRIME32, K_PRIME64, K_CHUNK32, K_CHUNK64};
+  PF_CK(cudaEventRecord(B->fork, s));
+  for (int op = 0; op < N_OPS; ++op) {
+    bool any = false;
+    for (int kind : order) any = any || use[op * K_PER_OP + kind];
+    if (!any) continue;
+    cudaStream_t st = B->ops[op];
+    PF_CK(cudaStreamWaitEvent(st, B->fork, 0));
+    for (int kind : order) {
+      const int slot = op * K_PER_OP + kind;
+      if (!use[slot]) continue;
+      const int* map = map_of(B, slot);
+      PF_TRY(op == PF_OP_PF1 ? launch_kind<true>(B, op, kind, map, st) : launch_kind<false>(B, op, kind, map, st));
+    }
+    PF_CK(cudaEventRecord(B->join[op], st));
+    PF_CK(cudaStreamWaitEvent(s, B->join[op], 0));
+  }
+  // every member's states
+  pf::k_gather_states<<<(n + 127) / 128, 128, 0, s>>>(B->dst64, B->dst32, n, B->dgather);
+  PF_CK(cudaGetLastError());
+  PF_CK(cudaMemcpyAsync(B->hgather, B->dgather, 2 * n * sizeof(BicgState), cudaMemcpyDeviceToHost, s));
+  PF_CK(cudaStreamSynchronize(s));
+  // transitions; the outer update's later stages (Anderson inner products, least squares)
+  bool dots = false;
+  std::vector<char> stop(n, 0);
+  for (int i = 0; i < n; ++i) {
+    BatchMember& M = B->members[i];
+    if (was[i] == S_UPDATE) {
+      const double d = outer_delta(M.g, M.o.accel_depth, M.o.omega);
+      stop[i] = d <= M.o.tol_outer;
+      M.res->delta = d;
+      PF_TRY(outer_stage2(M.g, M.U, M.o.accel_depth, stop[i]));
+      dots = dots || M.U.dots;
+    } else if (was[i] == S_FINISH) {
+      if (*M.g->host_err && M.st == PF_OK) M.st = PF_E_GAMMA;
+      M.res->status = M.st;
+      M.stage = S_DONE;
+      prof_resolve(M.g);
+    } else {
+      post(M, B->hgather[i], B->hgather[n + i]);
+    }
+  }
+  if (dots) PF_CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) {
+    BatchMember& M = B->members[i];
+    if (was[i] != S_UPDATE) continue;
+    PF_TRY(outer_stage3(M.g, M.U, M.o.accel_depth, M.o.omega, stop[i]));
+    const int outer = ++M.res->outer_iters;
+    M.dprev = M.res->delta;
+    if (trace_level() > 0)
+      fprintf(stderr, "[pf batch] member %lld outer %d delta %.6e\n", M.tag, outer, M.res->delta);
+    if (*M.g->host_err) {
+      M.st = PF_E_GAMMA;
+      M.stage = S_FINISH;
+    } else if (stop[i]) {
+      M.stage = S_FINISH;
+    } else if (outer >= M.o.max_outer) {
+      M.st = PF_E_NOCONV;
+      M.stage = S_FINISH;
+    } else {
+      M.stage = S_FERMI;
+    }
+  }
+  return PF_OK;
 }
 
 // Times the FP32 phase kernels of the batch's Poisson operators (right-hand side: the operator's diagonal
 // sums; the FP32 Krylov vectors, the correction and the inner state are scratch until a solve resets them)
 // for every tiles-per-block candidate, and keeps the fastest.
 pf_status autotune(pf_batch* B) {
-  const int n = (int)B->grids.size();
-  std::vector<int> all(n);
-  for (int i = 0; i < n; ++i) all[i] = i;
   for (pf_grid* g : B->grids) {
     PF_TRY(build_operators(g));
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->dsum, g->b32, g->geom.np, B->stream));
@@ -505,7 +726,9 @@ pf_status autotune(pf_batch* B) {
   int best_tpb = 4;
   for (int c : TPB_CANDIDATES) {
     B->tpb = c;
-    PF_TRY(use_set(B, all));
+    B->built = false;
+    PF_TRY(build(B));
+    const int* full = map_of(B, SLOT_FULL);
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {  // the first pass builds the tables and warms up
       for (pf_grid* g : B->grids) {
@@ -519,26 +742,20 @@ pf_status autotune(pf_batch* B) {
       using OC = pf::OpCA<float, false>;
       const void *ib[2], *ica[2], *ip;
       for (int par = 0; par < 2; ++par) {
-        PF_TRY((items_for<OB>(B, key_of("B", PF_OP_POISSON, 0, par, nullptr, nullptr),
-                              [&](pf_grid* g, pf::BatchItem<OB>& it) { return fill_b<float, false>(g, PF_OP_POISSON, par, it); },
-                              &ib[par])));
-        PF_TRY((items_for<OC>(B, key_of("CA", PF_OP_POISSON, 0, par, nullptr, nullptr),
-                              [&](pf_grid* g, pf::BatchItem<OC>& it) {
-                                return fill_ca<float, false>(g, PF_OP_POISSON, par, 0, g->d32, it);
+        PF_TRY((items_for<OB>(B, key_of("B", PF_OP_POISSON, 0, par),
+                              [&](int, pf_grid* g, pf::BatchItem<OB>& it) {
+                                return fill_b<float, false>(g, PF_OP_POISSON, par, it);
                               },
-                              &ica[par])));
+                              &ib[par])));
+        PF_TRY((ca_items<float, false>(B, PF_OP_POISSON, par, 0, &ica[par])));
       }
-      PF_TRY((items_for<OC>(B, key_of("CAprime", PF_OP_POISSON, 0, 0, nullptr, nullptr),
-                            [&](pf_grid* g, pf::BatchItem<OC>& it) {
-                              return fill_ca<float, false>(g, PF_OP_POISSON, 0, 1, g->d32, it);
-                            },
-                            &ip)));
+      PF_TRY((ca_items<float, false>(B, PF_OP_POISSON, 0, 1, &ip)));
       PF_CK(cudaEventRecord(B->e0, B->stream));
-      PF_TRY(launch_items<OC>(B, ip));
+      PF_TRY(launch_items<OC>(B, ip, full, B->stream));
       int cur = 1;
       for (int i = 0; i < 4; ++i) {
-        PF_TRY(launch_items<OB>(B, ib[cur]));
-        PF_TRY(launch_items<OC>(B, ica[cur]));
+        PF_TRY(launch_items<OB>(B, ib[cur], full, B->stream));
+        PF_TRY(launch_items<OC>(B, ica[cur], full, B->stream));
         cur = 1 - cur;
       }
       PF_CK(cudaEventRecord(B->e1, B->stream));
@@ -558,11 +775,47 @@ pf_status autotune(pf_batch* B) {
   B->tpb = best_tpb;
   t.chosen = best_tpb;
   B->tune = t;
-  drop_launches(B);
+  B->built = false;
   return PF_OK;
 }
 
-// Runs f on every grid of the batch with the batch's stream as the grid's stream.
+pf_status check_nl(const pf_nl_opts& o) {
+  PF_TRY(check_opts(o.lin));
+  if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1 || o.accel_depth < 0 ||
+      o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0))
+    return fail(PF_E_INVAL, "invalid pf_nl_opts");
+  return PF_OK;
+}
+
+pf_status batch_alloc(cudaStream_t user, int count_hint, pf_batch** out) {
+  pf_batch* B = new pf_batch();
+  B->user = user;
+  B->cap = ARENA_BYTES + (size_t)(count_hint > 0 ? count_hint : 1) * 64 * 1024;
+  cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cstream, cudaStreamNonBlocking);
+  for (int o = 0; o < N_OPS && e == cudaSuccess; ++o) {
+    e = cudaStreamCreateWithFlags(&B->ops[o], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->join[o], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&B->darena, B->cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&B->harena, B->cap);
+  if (e == cudaSuccess) e = cudaEventCreate(&B->e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&B->e1);
+  if (e != cudaSuccess) {
+    pf_batch_destroy(B);
+    cudaGetLastError();
+    return fail(PF_E_OOM, std::string("batch allocation failed: ") + cudaGetErrorString(e));
+  }
+  set_attrs<float, false>();
+  set_attrs<float, true>();
+  set_attrs<double, false>();
+  set_attrs<double, true>();
+  *out = B;
+  return PF_OK;
+}
+
+// Gives every grid of the batch the batch's stream while a call runs.
 struct StreamSwap {
   pf_batch* B;
   std::vector<cudaStream_t> saved;
@@ -581,6 +834,17 @@ struct StreamSwap {
   }
 };
 
+// The batch's stream waits for the work queued on the caller's and the grids' streams.
+pf_status enter(pf_batch* B) {
+  PF_CK(cudaEventRecord(B->e1, B->user));
+  PF_CK(cudaStreamWaitEvent(B->stream, B->e1, 0));
+  for (pf_grid* g : B->grids) {
+    PF_CK(cudaEventRecord(g->ev1, g->stream));
+    PF_CK(cudaStreamWaitEvent(B->stream, g->ev1, 0));
+  }
+  return PF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -594,33 +858,16 @@ pf_status pf_batch_create(pf_grid* const* grids, int count, void* cuda_stream, p
     for (int j = 0; j < i; ++j)
       if (grids[j] == grids[i]) return fail(PF_E_INVAL, "a grid appears twice in the batch");
   }
-  pf_batch* B = new pf_batch();
+  pf_batch* B = nullptr;
+  PF_TRY(batch_alloc(static_cast<cudaStream_t>(cuda_stream), count, &B));
   B->grids.assign(grids, grids + count);
-  B->user = static_cast<cudaStream_t>(cuda_stream);
-  B->cap = ARENA_BYTES + (size_t)count * 64 * 1024;
-  cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&B->darena, B->cap);
-  if (e == cudaSuccess) e = cudaMallocHost(&B->harena, B->cap);
-  if (e == cudaSuccess) e = cudaMalloc(&B->dgather, count * sizeof(BicgState));
-  if (e == cudaSuccess) e = cudaMallocHost(&B->hgather, count * sizeof(BicgState));
-  if (e == cudaSuccess) e = cudaEventCreate(&B->e0);
-  if (e == cudaSuccess) e = cudaEventCreate(&B->e1);
-  if (e != cudaSuccess) {
-    pf_batch_destroy(B);
-    cudaGetLastError();
-    return fail(PF_E_OOM, std::string("batch allocation failed: ") + cudaGetErrorString(e));
-  }
-  set_attrs<float, false>();
-  set_attrs<float, true>();
-  set_attrs<double, false>();
-  set_attrs<double, true>();
   *out = B;
   return PF_OK;
 }
 
 pf_status pf_batch_set_tiles_per_block(pf_batch* B, int tiles_per_block) {
   if (!B || tiles_per_block < 0) return fail(PF_E_INVAL, "bad batch or tiles_per_block");
-  if (tiles_per_block != B->tpb) drop_launches(B);
+  if (tiles_per_block != B->tpb) invalidate(B);
   B->tpb = tiles_per_block;
   return PF_OK;
 }
@@ -629,12 +876,7 @@ pf_status pf_batch_autotune(pf_batch* B, pf_batch_tune* out) {
   if (!B) return fail(PF_E_INVAL, "batch is NULL");
   for (pf_grid* g : B->grids)
     if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first on every grid");
-  PF_CK(cudaEventRecord(B->e1, B->user));
-  PF_CK(cudaStreamWaitEvent(B->stream, B->e1, 0));
-  for (pf_grid* g : B->grids) {
-    PF_CK(cudaEventRecord(g->ev1, g->stream));
-    PF_CK(cudaStreamWaitEvent(B->stream, g->ev1, 0));
-  }
+  PF_TRY(enter(B));
   StreamSwap sw(B);
   PF_TRY(autotune(B));
   PF_CK(cudaStreamSynchronize(B->stream));
@@ -653,185 +895,49 @@ pf_status pf_batch_nonlinear_solve(pf_batch* B, const pf_nl_opts* opts, pf_resul
   if (!B || !results) return fail(PF_E_INVAL, "batch and results are required");
   pf_nl_opts o;
   if (opts) o = *opts; else pf_default_nl_opts(&o);
-  PF_TRY(check_opts(o.lin));
-  if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1 || o.accel_depth < 0 ||
-      o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0))
-    return fail(PF_E_INVAL, "invalid pf_nl_opts");
+  PF_TRY(check_nl(o));
   const int n = (int)B->grids.size();
-  const int m = o.accel_depth;
   for (int i = 0; i < n; ++i) {
     if (!B->grids[i]->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first on every grid");
     if (results[i].mem != PF_MEM_HOST && results[i].mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "bad result mem");
   }
-  // the batch's stream waits for what is queued on the caller's and the grids' streams, and they wait for
-  // the batch at the end
-  PF_CK(cudaEventRecord(B->e1, B->user));
-  PF_CK(cudaStreamWaitEvent(B->stream, B->e1, 0));
-  for (pf_grid* g : B->grids) {
-    PF_CK(cudaEventRecord(g->ev1, g->stream));
-    PF_CK(cudaStreamWaitEvent(B->stream, g->ev1, 0));
-  }
+  PF_TRY(enter(B));
   StreamSwap sw(B);
   cudaStream_t s = B->stream;
   PF_CK(cudaEventRecord(B->e0, s));
   if (B->tpb == 0) PF_TRY(autotune(B));
-  std::vector<OuterUpdate> U(n);
-  std::vector<double> dprev(n, 1.0);
-  std::vector<pf_status> stat(n, PF_OK);
-  std::vector<bool> live(n, true);
+  B->members.assign(n, BatchMember{});
   for (int i = 0; i < n; ++i) {
-    pf_grid* g = B->grids[i];
-    pf_result& r = results[i];
-    r.status = PF_OK;
-    r.outer_iters = r.lin_iters_total = r.lin_iters_first = 0;
-    r.delta = 0.0;
-    if (m > 0) PF_TRY(ensure_aa(g, m));
-    const long NP = g->geom.np;
-    PF_TRY(build_operators(g));
-    PF_CK(cudaMemsetAsync(g->phi0, 0, NP * sizeof(double), s));
-    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, g->geom, s));
-    PF_CK(cudaMemsetAsync(g->psi, 0, NP * sizeof(double), s));
-    PF_LAUNCH(g, PF_PROF_OTHER,
-              pf::launch_pf2_rhs(g->psi, g->solvent, g->ffix, g->eps_s, g->lo_hat, g->hi_hat, g->geom, g->b2, s));
+    B->members[i].g = B->grids[i];
+    B->members[i].res = &results[i];
+    B->members[i].o = o;
+    B->members[i].tag = i;
   }
-  // initial potential (Table 4): PF2 with rho' = Psi = 0, all grids in one batched solve
-  {
-    std::vector<Job> jobs;
-    for (int i = 0; i < n; ++i) {
-      Job J;
-      J.inst = i;
-      J.x = B->grids[i]->phi0;
-      J.b = B->grids[i]->b2;
-      jobs.push_back(J);
+  // every problem ends within its limits (outer iterations, BiCGSTAB iterations, refinements); the host
+  // bound only guards the loop
+  const long long limit = 16LL * o.max_outer * (o.lin.max_iter / CHUNK + 4 * o.lin.max_refine + 8) + 64;
+  pf_status ts = PF_OK;
+  for (long long t = 0;; ++t) {
+    bool open = false;
+    for (const BatchMember& M : B->members) open = open || M.stage != S_DONE;
+    if (!open) break;
+    if (t > limit) {
+      ts = fail(PF_E_NOCONV, "batched solve exceeded its step bound");
+      break;
     }
-    PF_TRY(batch_solve(B, PF_OP_POISSON, jobs, o.lin));
-    for (const Job& J : jobs) {
-      results[J.inst].lin_iters_first = J.iters;
-      results[J.inst].lin_iters_total += J.iters;
-      if (J.status != PF_OK) {
-        stat[J.inst] = (pf_status)J.status;
-        live[J.inst] = false;
-      }
-    }
+    ts = tick(B);
+    if (ts != PF_OK) break;
   }
-  for (int outer = 1; outer <= o.max_outer; ++outer) {
-    std::vector<int> act;
-    for (int i = 0; i < n; ++i)
-      if (live[i]) act.push_back(i);
-    if (act.empty()) break;
-    std::vector<double> eta(n, 0.0);
-    for (int i : act) {
-      pf_grid* g = B->grids[i];
-      if (o.lin_forcing > 0) eta[i] = outer == 1 ? 1e-2 : fmin(1e-2, o.lin_forcing * dprev[i]);
-      // Eq. (1) at Phi_0 -> b_PF1, kappa, PF2 right-hand-side part
-      PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
-      PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, g->geom, g->b1, g->sig,
-                                                   g->c2, nullptr, nullptr, nullptr, g->ulast, outer > 1, g->err, s));
-      PF_TRY(update_pf2(g));
-    }
-    // PF1 (Eq. 12) on every live grid
-    std::vector<Job> jobs;
-    for (int i : act) {
-      Job J;
-      J.inst = i;
-      J.x = B->grids[i]->psi;
-      J.b = B->grids[i]->b1;
-      J.eta = eta[i];
-      jobs.push_back(J);
-    }
-    PF_TRY(batch_solve(B, PF_OP_PF1, jobs, o.lin));
-    std::vector<Job> jobs2;
-    for (const Job& J : jobs) {
-      results[J.inst].lin_iters_total += J.iters;
-      if (J.status != PF_OK) {
-        stat[J.inst] = (pf_status)J.status;
-        live[J.inst] = false;
-        continue;
-      }
-      pf_grid* g = B->grids[J.inst];
-      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat,
-                                                     g->geom, g->b2, s));
-      PF_CK(cudaMemcpyAsync(g->phi, g->phi0, g->geom.np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      Job K;
-      K.inst = J.inst;
-      K.x = g->phi;
-      K.b = g->b2;
-      K.eta = J.eta;
-      jobs2.push_back(K);
-    }
-    // PF2 (Eq. 13)
-    PF_TRY(batch_solve(B, PF_OP_PF2, jobs2, o.lin));
-    std::vector<int> upd;
-    for (const Job& J : jobs2) {
-      results[J.inst].lin_iters_total += J.iters;
-      if (J.status != PF_OK) {
-        stat[J.inst] = (pf_status)J.status;
-        live[J.inst] = false;
-        continue;
-      }
-      upd.push_back(J.inst);
-    }
-    // the outer update of every grid, stage by stage between two synchronisations
-    for (int i : upd) PF_TRY(outer_stage1(B->grids[i], U[i], m, o.omega));
-    PF_CK(cudaStreamSynchronize(s));
-    std::vector<char> stop(n, 0);
-    for (int i : upd) {
-      const double d = outer_delta(B->grids[i], m, o.omega);
-      stop[i] = d <= o.tol_outer;
-      results[i].delta = d;
-      PF_TRY(outer_stage2(B->grids[i], U[i], m, stop[i]));
-    }
-    if (m > 0) PF_CK(cudaStreamSynchronize(s));
-    for (int i : upd) {
-      pf_grid* g = B->grids[i];
-      PF_TRY(outer_stage3(g, U[i], m, o.omega, stop[i]));
-      results[i].outer_iters = outer;
-      dprev[i] = results[i].delta;
-      if (*g->host_err) {
-        stat[i] = PF_E_GAMMA;
-        live[i] = false;
-      } else if (stop[i]) {
-        live[i] = false;
-      } else if (outer == o.max_outer) {
-        stat[i] = PF_E_NOCONV;
-        live[i] = false;
-      }
-    }
-  }
-  // outputs at the final potentials
-  for (int i = 0; i < n; ++i) {
-    pf_grid* g = B->grids[i];
-    pf_result& r = results[i];
-    const long NP = g->geom.np;
-    PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
-    PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, g->geom, nullptr, nullptr,
-                                                 nullptr, g->Cbuf, g->Sbuf, g->Gbuf, g->ulast, r.outer_iters > 0,
-                                                 g->err, s));
-    if (r.phi_V) {
-      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, NP, s));
-      PF_TRY(unpack_out(g, g->phi, 1, r.phi_V, r.mem));
-    }
-    if (r.C_M) {
-      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->Cbuf, 1.0 / g->molar, g->Cbuf, NP * g->sp.ns, s));
-      PF_TRY(unpack_out(g, g->Cbuf, g->sp.ns, r.C_M, r.mem));
-    }
-    if (r.S) PF_TRY(unpack_out(g, g->Sbuf, 1, r.S, r.mem));
-    if (r.Gamma) PF_TRY(unpack_out(g, g->Gbuf, 1, r.Gamma, r.mem));
-    if (r.Psi) PF_TRY(unpack_out(g, g->psi, 1, r.Psi, r.mem));
-    PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  }
+  B->members.clear();
+  if (ts != PF_OK) return ts;
   PF_CK(cudaEventRecord(B->e1, s));
   PF_CK(cudaEventSynchronize(B->e1));
   float ms = 0.f;
   PF_CK(cudaEventElapsedTime(&ms, B->e0, B->e1));
   pf_status worst = PF_OK;
   for (int i = 0; i < n; ++i) {
-    pf_grid* g = B->grids[i];
-    if (*g->host_err && stat[i] == PF_OK) stat[i] = PF_E_GAMMA;
-    results[i].status = stat[i];
     results[i].time_ms = ms;
-    prof_resolve(g);
-    if (stat[i] != PF_OK && worst == PF_OK) worst = stat[i];
+    if (results[i].status != PF_OK && worst == PF_OK) worst = (pf_status)results[i].status;
   }
   for (size_t i = 0; i < B->grids.size(); ++i) {
     PF_CK(cudaEventRecord(B->grids[i]->ev1, s));
@@ -844,7 +950,7 @@ pf_status pf_batch_nonlinear_solve(pf_batch* B, const pf_nl_opts* opts, pf_resul
 
 pf_status pf_batch_destroy(pf_batch* B) {
   if (!B) return PF_OK;
-  if (B->stream || B->darena) cudaStreamSynchronize(B->stream);
+  drain(B);
   for (auto& kv : B->graphs) cudaGraphExecDestroy(kv.second);
   if (B->darena) cudaFree(B->darena);
   if (B->harena) cudaFreeHost(B->harena);
@@ -852,9 +958,65 @@ pf_status pf_batch_destroy(pf_batch* B) {
   if (B->hgather) cudaFreeHost(B->hgather);
   if (B->e0) cudaEventDestroy(B->e0);
   if (B->e1) cudaEventDestroy(B->e1);
+  if (B->fork) cudaEventDestroy(B->fork);
+  for (int o = 0; o < N_OPS; ++o) {
+    if (B->join[o]) cudaEventDestroy(B->join[o]);
+    if (B->ops[o]) cudaStreamDestroy(B->ops[o]);
+  }
+  if (B->cstream) cudaStreamDestroy(B->cstream);
   if (B->stream) cudaStreamDestroy(B->stream);
   delete B;
   return PF_OK;
 }
 
 }  // extern "C"
+
+// ---- the engine behind the server: members join and leave between ticks -----------------------------
+namespace pfi {
+
+pf_status engine_create(int max_members, pf_batch** out) {
+  PF_TRY(batch_alloc(nullptr, max_members, out));
+  (*out)->tpb = ENGINE_TILES_PER_BLOCK;
+  return PF_OK;
+}
+
+cudaStream_t engine_stream(pf_batch* B) { return B->stream; }
+
+int engine_size(pf_batch* B) { return (int)B->members.size(); }
+
+pf_status engine_add(pf_batch* B, pf_grid* g, pf_result* res, const pf_nl_opts& o, long long tag) {
+  if (!g || !res || !g->have_coeffs) return fail(PF_E_INVAL, "engine member needs a grid with coefficients");
+  PF_TRY(check_nl(o));
+  if (g->stream != B->stream) return fail(PF_E_INVAL, "engine member must use the engine's stream");
+  BatchMember M;
+  M.g = g;
+  M.res = res;
+  M.o = o;
+  M.tag = tag;
+  B->members.push_back(M);
+  B->grids.push_back(g);
+  B->built = false;
+  return PF_OK;
+}
+
+pf_status engine_step(pf_batch* B, std::vector<long long>* finished) {
+  PF_TRY(tick(B));
+  std::vector<BatchMember> keep;
+  std::vector<pf_grid*> kg;
+  for (const BatchMember& M : B->members) {
+    if (M.stage == S_DONE) {
+      finished->push_back(M.tag);
+    } else {
+      keep.push_back(M);
+      kg.push_back(M.g);
+    }
+  }
+  if (keep.size() != B->members.size()) {
+    B->members.swap(keep);
+    B->grids.swap(kg);
+    B->built = false;
+  }
+  return PF_OK;
+}
+
+}  // namespace pfi

@@ -204,6 +204,34 @@ struct OuterUpdate {
   pf::AAPtrs cols{};
   bool dots = false;
 };
+// One problem of a batch (pf_batch.cu): its grid, where its outputs go, its options and its place in the
+// per-problem state machine of the engine.
+struct BatchMember {
+  pf_grid* g = nullptr;
+  pf_result* res = nullptr;
+  pf_nl_opts o{};
+  OuterUpdate U;
+  double dprev = 1.0;   // delta of the previous outer iteration (forcing term)
+  int stage = 0;        // step of the nonlinear iteration (pf_batch.cu: Stage)
+  int after = 0;        // stage to enter when the running linear solve ends
+  // the linear solve in progress
+  int op = 0, sub = 0, iters = 0, refs = 0;
+  double eta = 0.0;     // forcing: also stop at eta ||r0||
+  bool add_pending = false;
+  pf_status st = PF_OK;
+  long long tag = 0;    // the owner's handle
+};
+
+// The batched engine behind the server: problems join (engine_add, grid created on engine_stream) and
+// leave (engine_step reports the tags of those that finished, their outputs written, and drops them)
+// between steps; every step runs one outer iteration of all members in shared batched launches.
+constexpr int ENGINE_TILES_PER_BLOCK = 4;
+pf_status engine_create(int max_members, pf_batch** out);
+cudaStream_t engine_stream(pf_batch* B);
+int engine_size(pf_batch* B);
+pf_status engine_add(pf_batch* B, pf_grid* g, pf_result* res, const pf_nl_opts& o, long long tag);
+pf_status engine_step(pf_batch* B, std::vector<long long>* finished);
+
 pf_status outer_stage1(pf_grid* g, OuterUpdate& u, int m, double omega);
 double outer_delta(const pf_grid* g, int m, double omega);
 pf_status outer_stage2(pf_grid* g, OuterUpdate& u, int m, bool stop);

@@ -1,17 +1,18 @@
 // pf_server.cu -- continuous batching of PF solves behind pf_submit / pf_poll.
 //
-// A fixed pool of worker threads (one per slot) takes requests from a FIFO queue as soon as a
-// slot is free and the request's device state fits the remaining HBM budget (first request in
-// arrival order that fits).  Each worker owns a non-blocking CUDA stream; it builds the grid,
-// runs the same nonlinear solve as pf_nonlinear_solve on that stream, copies the outputs to
-// host memory and frees the device state at once, so admitted problems overlap on the GPU and
-// memory returns to the budget when a solve ends.  Results are bitwise those of a standalone
-// solve on the same problem: the kernels, launch shapes and reduction orders depend only on the
-// problem.
+// One scheduler thread owns a batched engine (pf_batch.cu).  Between two engine steps it admits queued
+// requests, first fit in arrival order, while a slot is free and the request's device state fits the
+// remaining HBM budget: it creates the request's grid on the engine's stream and adds it as a member.
+// Every engine step runs one outer iteration of all members in shared batched launches (members that
+// just joined get their operators and initial potential first), so requests that arrive while others are
+// on the GPU join the running launches at the next step.  A member that finishes has its outputs written
+// to host memory, its grid freed at once (its bytes return to the budget), and its ticket completed.  The
+// state of every request in flight (potential, concentrations, Krylov vectors) stays on the device.
+// A request's arithmetic depends only on the request (the engine splits every grid into blocks the same
+// way), so its result is bitwise that of a batch of this problem alone with the engine's tiles per block.
 #include <cuda_runtime.h>
 #include <string.h>
 
-#include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -20,7 +21,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/pf_gb300.h"
+#include "pf_grid.cuh"
 
 size_t pf_internal_grid_bytes(int nx, int ny, int nz, int accel_depth);  // pf_api.cu
 
@@ -37,6 +38,7 @@ struct Request {
   pf_nl_opts opts{};
   size_t bytes = 0;
   long N = 0;
+  pf_grid* g = nullptr;  // while in flight
   // results
   std::vector<double> phi, C, S, G;
   pf_result res{};
@@ -49,74 +51,114 @@ struct Request {
 
 struct pf_server {
   size_t budget = 0, used = 0;
-  int device = 0;
+  int device = 0, max_slots = 1;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Request*> queue;
   std::unordered_map<uint64_t, Request*> all;
-  std::vector<std::thread> workers;
+  std::thread scheduler;
   bool stop = false;
   uint64_t next = 1;
 };
 
 namespace {
 
-void run_request(Request* r, cudaStream_t stream) {
-  pf_grid* g = nullptr;
-  pf_status s = pf_create_grid(r->nx, r->ny, r->nz, r->h, r->origin, stream, &g);
-  if (s == PF_OK) s = pf_set_coeffs(g, &r->coeffs);
+void complete(pf_server* sv, Request* r, pf_status s, const std::string& err) {
+  if (r->g) pf_destroy_grid(r->g);
+  r->g = nullptr;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->used -= r->bytes;
+  r->status = s;
+  r->res.status = s;
+  r->error = err;
+  r->done = true;
+  sv->cv.notify_all();
+}
+
+// Creates the request's grid on the engine's stream and makes it a member; false (request completed
+// with the failure) when that fails.
+bool join(pf_server* sv, pf_batch* E, Request* r) {
+  pf_status s = pf_create_grid(r->nx, r->ny, r->nz, r->h, r->origin, pfi::engine_stream(E), &r->g);
+  if (s == PF_OK) s = pf_set_coeffs(r->g, &r->coeffs);
   if (s == PF_OK) {
     r->phi.assign(r->N, 0.0);
     r->C.assign((size_t)r->N * r->species.size(), 0.0);
     r->S.assign(r->N, 0.0);
     r->G.assign(r->N, 0.0);
-    pf_result res{};
-    res.phi_V = r->phi.data();
-    res.C_M = r->C.data();
-    res.S = r->S.data();
-    res.Gamma = r->G.data();
-    res.mem = PF_MEM_HOST;
-    s = pf_nonlinear_solve(g, &r->opts, &res);
-    r->res = res;
+    r->res = pf_result{};
+    r->res.phi_V = r->phi.data();
+    r->res.C_M = r->C.data();
+    r->res.S = r->S.data();
+    r->res.Gamma = r->G.data();
+    r->res.mem = PF_MEM_HOST;
+    s = pfi::engine_add(E, r->g, &r->res, r->opts, (long long)r->ticket);
   }
-  if (s != PF_OK) r->error = pf_last_error();
-  pf_destroy_grid(g);
-  r->status = s;
-  r->res.status = s;
+  if (s != PF_OK) {
+    complete(sv, r, s, pf_last_error());
+    return false;
+  }
+  return true;
 }
 
-void worker_main(pf_server* sv) {
+void scheduler_main(pf_server* sv) {
   cudaSetDevice(sv->device);
-  cudaStream_t stream = nullptr;
-  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
-  std::unique_lock<std::mutex> lk(sv->mu);
+  pf_batch* E = nullptr;
+  const pf_status es = pfi::engine_create(sv->max_slots, &E);
+  std::unordered_map<long long, Request*> inflight;
   for (;;) {
-    Request* pick = nullptr;
-    sv->cv.wait(lk, [&] {
-      if (sv->stop) return true;
-      for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it)
-        if (sv->used + (*it)->bytes <= sv->budget) return true;
-      return false;
-    });
-    if (sv->stop) break;
-    for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
-      if (sv->used + (*it)->bytes <= sv->budget) {
-        pick = *it;
-        sv->queue.erase(it);
-        break;
+    std::vector<Request*> admit;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      auto admissible = [&] {
+        if ((int)inflight.size() >= sv->max_slots) return false;
+        for (Request* r : sv->queue)
+          if (sv->used + r->bytes <= sv->budget) return true;
+        return false;
+      };
+      sv->cv.wait(lk, [&] { return sv->stop || !inflight.empty() || admissible(); });
+      if (sv->stop) break;
+      for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+        if ((int)(inflight.size() + admit.size()) >= sv->max_slots) break;
+        if (sv->used + (*it)->bytes <= sv->budget) {
+          sv->used += (*it)->bytes;
+          admit.push_back(*it);
+          it = sv->queue.erase(it);
+        } else {
+          ++it;
+        }
       }
     }
-    if (!pick) continue;
-    sv->used += pick->bytes;
-    lk.unlock();
-    run_request(pick, stream);
-    lk.lock();
-    sv->used -= pick->bytes;
-    pick->done = true;
-    sv->cv.notify_all();
+    for (Request* r : admit) {
+      if (es != PF_OK) {
+        complete(sv, r, es, "the serving engine could not be created");
+        continue;
+      }
+      if (join(sv, E, r)) inflight[(long long)r->ticket] = r;
+    }
+    if (inflight.empty()) continue;
+    std::vector<long long> fin;
+    const pf_status s = pfi::engine_step(E, &fin);
+    if (s != PF_OK) {
+      // a failure of the engine itself (not of a problem): fail every request in flight and start afresh
+      const std::string err = pf_last_error();
+      pf_batch_destroy(E);
+      for (auto& kv : inflight) complete(sv, kv.second, s, err);
+      inflight.clear();
+      if (pfi::engine_create(sv->max_slots, &E) != PF_OK) E = nullptr;
+      if (!E) break;
+      continue;
+    }
+    for (long long t : fin) {
+      Request* r = inflight[t];
+      inflight.erase(t);
+      complete(sv, r, (pf_status)r->res.status, r->res.status == PF_OK ? "" : "solve failed");
+    }
   }
-  lk.unlock();
-  if (stream) cudaStreamDestroy(stream);
+  for (auto& kv : inflight) {
+    if (kv.second->g) pf_destroy_grid(kv.second->g);
+    kv.second->g = nullptr;
+  }
+  if (E) pf_batch_destroy(E);
 }
 
 }  // namespace
@@ -127,8 +169,9 @@ pf_status pf_server_create(size_t hbm_budget_bytes, int max_slots, pf_server** o
   if (!out || max_slots < 1 || hbm_budget_bytes == 0) return PF_E_INVAL;
   pf_server* sv = new pf_server();
   sv->budget = hbm_budget_bytes;
+  sv->max_slots = max_slots;
   cudaGetDevice(&sv->device);
-  for (int i = 0; i < max_slots; ++i) sv->workers.emplace_back(worker_main, sv);
+  sv->scheduler = std::thread(scheduler_main, sv);
   *out = sv;
   return PF_OK;
 }
@@ -213,7 +256,7 @@ pf_status pf_server_destroy(pf_server* sv) {
     sv->queue.clear();
   }
   sv->cv.notify_all();
-  for (auto& t : sv->workers) t.join();
+  if (sv->scheduler.joinable()) sv->scheduler.join();
   for (auto& kv : sv->all) delete kv.second;
   delete sv;
   return PF_OK;

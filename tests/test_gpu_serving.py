@@ -1,5 +1,7 @@
-"""Serving through pf_submit / pf_poll (GPU): admitted problems run concurrently, each result equals the
-same problem solved alone, the HBM budget gates admission, and requests that can never fit are refused."""
+"""Serving through pf_submit / pf_poll (GPU): admitted problems share the batched launches, each result is
+bitwise that of the same problem in a batch of its own (the engine's 4 tiles per block) and agrees with
+pf_nonlinear_solve to the solver tolerance, the HBM budget gates admission, and requests that can never fit
+are refused."""
 import time
 
 import numpy as np
@@ -42,6 +44,16 @@ def _wait(api, srv, ticket, prob, timeout=300.0):
 
 
 def _alone(api, prob, opts):
+    """The problem in a batch of its own with the serving engine's block split."""
+    grid = api.Grid.for_problem(prob)
+    batch = api.Batch([grid], tiles_per_block=4)
+    (out, rep), = batch.nonlinear_solve(opts)
+    batch.close()
+    grid.close()
+    return out, rep
+
+
+def _single(api, prob, opts):
     grid = api.Grid.for_problem(prob)
     out, rep = grid.nonlinear_solve(opts)
     grid.close()
@@ -63,10 +75,14 @@ def test_mixed_stream_equals_alone(api, precision):
     for p, (out, rep) in zip(probs, results):
         assert rep["status"] == 0
         ref, rref = _alone(api, p, opts)
-        # same kernels, launch shapes and reduction orders: identical to the standalone solve
+        # same kernels, block split and reduction orders: identical to the problem's own batch
         np.testing.assert_array_equal(out["phi_V"], ref["phi_V"])
         np.testing.assert_array_equal(out["C_M"], ref["C_M"])
         assert rep["outer_iters"] == rref["outer_iters"]
+        # and the single-grid solver (another block split) to the solver tolerance
+        sref, _ = _single(api, p, opts)
+        tol = 1e-8 if precision == "fp64" else 1e-6
+        assert np.abs(out["phi_V"] - sref["phi_V"]).max() <= tol * max(np.abs(sref["phi_V"]).max(), 0.0257)
 
 
 def test_budget_refuses_what_can_never_fit(api):
