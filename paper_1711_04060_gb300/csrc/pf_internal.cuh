@@ -9,7 +9,7 @@ namespace pf {
 constexpr int TX = 32;           // tile width in x (one warp per row)
 constexpr int TY = 8;            // tile height in y
 constexpr int NTHREADS = TX * TY;
-constexpr int ZC = 16;           // interior planes per z-chunk of a tile
+constexpr int ZC = 32;           // interior planes per z-chunk of a tile
 constexpr int MAXSP = 8;
 constexpr int NPART = 16;        // per-block partial values reduced by the last block
 constexpr int HBX = TX + 8;      // TMA halo box: x from x0-4 (16-byte aligned start) to x0+TX+3

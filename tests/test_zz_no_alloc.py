@@ -45,9 +45,12 @@ def test_fermi_noalloc_matches_nonlinear_solve(torch_api):
         G = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
         assert api.pf_fermi_noalloc(dev["phi_V"], solvent, prob.species, C, S, G, T_K=prob.T_K) == 0
         torch.cuda.synchronize()
+        # the pointwise Newton iteration stops once its step is below 1e-6 max(1, |ln Gamma|); it converges
+        # quadratically, so calls from different starting points (here: the bath value against the solve's
+        # previous iterate) agree to about 1e-12 max(1, ln^2 Gamma)
         for got, ref in ((C, dev["C_M"]), (S, dev["S"]), (G, dev["Gamma"])):
             g, r = got.cpu().numpy(), ref.cpu().numpy()
-            assert np.abs(g - r).max() <= 1e-12 * np.abs(r).max(), call
+            assert np.abs(g - r).max() <= 1e-10 * max(np.abs(r).max(), 1.0), call
 
 
 def test_fermi_noalloc_rejects_sizes_beyond_its_scratch(torch_api):
