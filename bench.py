@@ -87,6 +87,22 @@ def workload(n):
     return W.config2(n=n)
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest value of x over the ranks (x itself on one rank); the job's time is its slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks (each rank solves its own replica) per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -396,12 +412,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     prof = grid.profile_get()
     grid.profile(False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(args.steps, world, ms / 1e3)
     clocks = clk.summary()
     phi_mixed = out["phi_V"].cpu().numpy()
     C_mixed = out["C_M"].cpu().numpy()
@@ -498,14 +510,10 @@ def run_ours(args):
             solve(opts, hout)
         torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, world, dev)
         h2d = prob.eps.nbytes + prob.solvent.nbytes + prob.charges.nbytes
         d2h = sum(v.nbytes for v in hout.values())
-        line["e2e"] = {"value": world * max(1, args.steps) / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        line["e2e"] = {"value": whole_job_rate(max(1, args.steps), world, el), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)}
     grid.close()
 
