@@ -185,6 +185,15 @@ def iteration_gbps(prof, prec, n_int):
     return round(by / (ms / 1e3) / 1e9, 1) if ms > 0 else None
 
 
+def kernel_source_hash():
+    """sha256 prefix of the sources that decide a stencil kernel's memory traffic (its body and operators,
+    the tile constants, the launcher)."""
+    h = hashlib.sha256()
+    for name in ("pf_stencil.cuh", "pf_internal.cuh", "pf_kernels.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1711_04060_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(kind):
     """DRAM bytes per interior node of one launch from the committed ncu summary, if it was
     captured from the current kernel source; otherwise None."""
@@ -194,8 +203,7 @@ def kernel_traffic(kind):
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_1711_04060_gb300", "csrc", "pf_kernels.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash()
     e = d.get(kind)
     if not e or e.get("kernel_source_sha256_16") != h:
         return None
