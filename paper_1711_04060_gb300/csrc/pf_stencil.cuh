@@ -94,28 +94,36 @@ struct Acc<float> {
 template <typename T>
 __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
 
-// Inner-product partials of a thread: the products of one tile column (at most ZC + 1 terms) are
-// summed in the working precision, then added to an FP64 total once per tile, so the global inner
-// products are FP64 sums of short working-precision partial sums.
+// Inner-product partials: a thread sums the products of one tile column (at most ZC + 1 terms) in the
+// working precision; at the end of each tile the warp adds its threads' sums in FP64 (fixed shuffle tree)
+// to its FP64 totals in shared memory (wsum[warp * NV + j]), so the global inner products are FP64 sums of
+// short working-precision partial sums and no thread holds FP64 accumulators across tiles.
 template <typename T, int NV>
 struct Partials {
   T t[NV];
-  double d[NV];
   __device__ __forceinline__ Partials() {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      t[j] = T(0);
-      d[j] = 0.0;
-    }
+    for (int j = 0; j < NV; ++j) t[j] = T(0);
   }
-  __device__ __forceinline__ void flush() {
+  // all 32 lanes of the warp take part
+  __device__ __forceinline__ void flush(double* wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-      d[j] += (double)t[j];
+      double v = (double)t[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) wsum[warp * NV + j] += v;
       t[j] = T(0);
     }
   }
+  // the warp's total j (lane 0; 0 on the other lanes), once every tile is flushed
+  __device__ __forceinline__ static double total(const double* wsum, int j) {
+    return (threadIdx.x & 31) == 0 ? wsum[(threadIdx.x >> 5) * NV + j] : 0.0;
+  }
 };
+
+constexpr int WSUM_MAX = 8;  // FP64 warp totals per warp (at least the largest NV of a Partials)
 
 // Block reduction of NV values (bit j of maxmask: value j is a maximum, else a sum) into
 // part[bid * NPART + j] (bid: the block's index among the blocks of its reduction, blockIdx.x by
@@ -285,8 +293,9 @@ __host__ __device__ constexpr int stage_bytes() {
 
 template <class Op>
 __host__ __device__ constexpr int smem_bytes() {
-  // stages | three stencil planes | D mbarriers | 128 bytes of alignment slack
-  return Op::D * stage_bytes<Op>() + 3 * PLANE * (int)sizeof(typename Op::T) + Op::D * 8 + 128;
+  // stages | three stencil planes | D mbarriers | FP64 warp totals | 128 bytes of alignment slack
+  return Op::D * stage_bytes<Op>() + 3 * PLANE * (int)sizeof(typename Op::T) + Op::D * 8 +
+         NTHREADS / 32 * WSUM_MAX * 8 + 128;
 }
 
 // The reduction scratch at the end of a kernel reuses the stage ring (all copies consumed by then).
@@ -312,6 +321,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   T* qring = reinterpret_cast<T*>(smem + D * STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + D * STAGE + 3 * PLANE * sizeof(T));
+  double* wsum = reinterpret_cast<double*>(bars + D);
 
   if (Op::CHECK_DONE && *(volatile int*)&a.st->done) return;
   const typename Op::Sc sc = Op::scalars(a);
@@ -319,6 +329,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
     for (int d = 0; d < D; ++d) mbar_init(&bars[d], 1);
     fence_mbar_init();
   }
+  if (threadIdx.x < NTHREADS / 32 * WSUM_MAX) wsum[threadIdx.x] = 0.0;
   __syncthreads();
 
   // producer (thread 0): the next (tile, plane) of this block's stream of planes
@@ -400,7 +411,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
       Qprev = Qnow;
       Qnow = freed;
     }
-    acc.flush();
+    acc.flush(wsum);
     if (!failed) __syncthreads();
   }
   if (failed) {
@@ -413,7 +424,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
     return;
   }
   __syncthreads();
-  Op::finish(a, acc, reinterpret_cast<double*>(smem), bid, nblk);
+  Op::finish(a, acc, wsum, reinterpret_cast<double*>(smem), bid, nblk);
 }
 
 // ------------------------------------------------------------------ phase B: s = r - alpha v, t = A M^-1 s
@@ -440,7 +451,7 @@ struct OpB {
   struct Accs {
     Partials<T, 5> p;  // r~.s, r~.t, t.s, t.t, s.s
     T smax = T(0);
-    __device__ void flush() { p.flush(); }
+    __device__ void flush(double* wsum) { p.flush(wsum); }
   };
   __device__ static Sc scalars(const Args& a) { return Sc{(T)a.st->alpha}; }
   __device__ static T q_of(const Sc& sc, const T* const* H, int o, Ctr* c) {
@@ -494,8 +505,11 @@ struct OpB {
     acc.p.t[4] = fma(c.s, c.s, acc.p.t[4]);
     acc.smax = fmax(acc.smax, tabs(c.s));
   }
-  __device__ static void finish(const Args& a, const Accs& acc, double* scratch, int bid, int nblk) {
-    double vals[6] = {acc.p.d[0], acc.p.d[1], acc.p.d[2], acc.p.d[3], acc.p.d[4], (double)acc.smax};
+  __device__ static void finish(const Args& a, const Accs& acc, const double* wsum, double* scratch, int bid,
+                                int nblk) {
+    using P = Partials<T, 5>;
+    double vals[6] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), P::total(wsum, 3), P::total(wsum, 4),
+                      (double)acc.smax};
     block_partials<6>(vals, 32u, a.part, scratch, bid);
     if (!arrive_last(&a.st->ticket, nblk)) return;
     double tot[6];
@@ -556,7 +570,7 @@ struct OpCA {
   struct Accs {
     Partials<T, 3> p;  // r~.v', r~.r', r'.r'
     T rmax = T(0);
-    __device__ void flush() { p.flush(); }
+    __device__ void flush(double* wsum) { p.flush(wsum); }
   };
   __device__ static Sc scalars(const Args& a) { return Sc{(T)a.st->alpha, (T)a.st->omega, (T)a.st->beta}; }
   __device__ static T q_of(const Sc& sc, const T* const* H, int o, Ctr* c) {
@@ -622,8 +636,10 @@ struct OpCA {
     acc.p.t[2] = fma(c.rn, c.rn, acc.p.t[2]);
     acc.rmax = fmax(acc.rmax, tabs(c.rn));
   }
-  __device__ static void finish(const Args& a, const Accs& acc, double* scratch, int bid, int nblk) {
-    double vals[4] = {acc.p.d[0], acc.p.d[1], acc.p.d[2], (double)acc.rmax};
+  __device__ static void finish(const Args& a, const Accs& acc, const double* wsum, double* scratch, int bid,
+                                int nblk) {
+    using P = Partials<T, 3>;
+    double vals[4] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), (double)acc.rmax};
     block_partials<4>(vals, 8u, a.part, scratch, bid);
     if (!arrive_last(&a.st->ticket, nblk)) return;
     double tot[4];
@@ -695,7 +711,7 @@ struct OpRes {
   };
   struct Accs {
     double rr = 0.0, bb = 0.0, rmax = 0.0;
-    __device__ void flush() {}
+    __device__ void flush(double*) {}
   };
   __device__ static Sc scalars(const Args&) { return Sc{0}; }
   __device__ static double q_of(const Sc&, const double* const* H, int o, Ctr* c) {
@@ -755,7 +771,8 @@ struct OpRes {
     acc.bb = fma(c.b, c.b, acc.bb);
     acc.rmax = fmax(acc.rmax, fabs(rc));
   }
-  __device__ static void finish(const Args& a, const Accs& acc, double* scratch, int bid, int nblk) {
+  __device__ static void finish(const Args& a, const Accs& acc, const double* wsum, double* scratch, int bid,
+                                int nblk) {
     double vals[3] = {acc.rr, acc.bb, acc.rmax};
     block_partials<3>(vals, 4u, a.part, scratch, bid);
     if (!arrive_last(&a.st->ticket, nblk)) return;
