@@ -46,16 +46,17 @@ KERNEL_BYTES = {
     "ca_fp64_pf1": WORDS["ca_pf1"] * 8, "residual_fp64": 7 * 8 + 4,
 }
 KERNEL_NAMES = {
-    "b_fp32": "k_phase_b<float, false>", "ca_fp32": "k_phase_ca<float, false>", "b_fp64": "k_phase_b<double, false>",
-    "ca_fp64": "k_phase_ca<double, false>", "b_fp32_pf1": "k_phase_b<float, true>",
-    "ca_fp32_pf1": "k_phase_ca<float, true>", "b_fp64_pf1": "k_phase_b<double, true>",
-    "ca_fp64_pf1": "k_phase_ca<double, true>", "residual_fp64": "k_residual<false>",
+    "b_fp32": "k_stencil<OpB<float, false>>", "ca_fp32": "k_stencil<OpCA<float, false>>",
+    "b_fp64": "k_stencil<OpB<double, false>>", "ca_fp64": "k_stencil<OpCA<double, false>>",
+    "b_fp32_pf1": "k_stencil<OpB<float, true>>", "ca_fp32_pf1": "k_stencil<OpCA<float, true>>",
+    "b_fp64_pf1": "k_stencil<OpB<double, true>>", "ca_fp64_pf1": "k_stencil<OpCA<double, true>>",
+    "residual_fp64": "k_stencil<OpRes<false>>",
 }
-# Work of one FP64 solve of this workload (outer iterations, BiCGSTAB iterations), used by the
+# Work of one FP64 solve of the 257^3 workload (outer iterations, BiCGSTAB iterations), used by the
 # reference arm to turn the oracle's per-iteration cost into solves/s; the oracle runs the same
 # algorithm, whose BiCGSTAB counts agree with these up to the rounding sensitivity of BiCGSTAB.
 # The ours-arm cpu_baseline uses the counts of its own FP64 solve instead.
-REF_WORK = {"outer": 226, "lin_iters": 30000}
+REF_WORK = {"outer": 188, "lin_iters": 15600}
 
 
 def parse():

@@ -244,7 +244,7 @@ pf_status residual(pf_grid* g, const OpArrays<double>& A, const double* x, const
     PF_TRY((fill_maps<S::NH, S::NC, double>(g, &m, h,
                                             c)));
   }
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b, g->geom, st, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b, g->geom, g->part, st, g->stream));
   const int slot = prof_begin(g, 1);
   PF_CK((pf::launch_residual<UNI>(m, g->geom, A.wc, A.diagc, init, K ? K->r[0] : nullptr, K ? K->rt : nullptr,
                                   K ? K->p[0] : nullptr, K ? K->v[0] : nullptr, K ? K->t : nullptr, g->b32, g->part,
@@ -381,7 +381,7 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
       status = PF_E_BREAKDOWN;
       break;
     }
-    PF_LAUNCH(g, PF_PROF_RESIDUAL, pf::launch_add_f32(x, g->d32, g->geom.np, g->stream));  // x += d
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_add_f32(x, g->d32, g->geom.np, g->stream));  // x += d
   }
   rep->status = status;
   rep->iterations = iters;

@@ -518,11 +518,11 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
   switch (M.sub) {
     case L_RES:  // FP64 true residual b - A x -> b32 (mixed precision)
       if (M.add_pending) {
-        PF_LAUNCH(g, PF_PROF_RESIDUAL, pf::launch_add_f32(x_of(g, M.op), g->d32, NP, s));  // x += d
+        PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_add_f32(x_of(g, M.op), g->d32, NP, s));  // x += d
         M.add_pending = false;
       }
       PF_TRY(set_state(g, g->st, lo.tol, lo.norm, 0, M.eta, M.refs > 0));
-      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b_of(g, M.op), g->geom, g->st, s));
+      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b_of(g, M.op), g->geom, g->part, g->st, s));
       kinds.push_back(base + K_RES0);
       break;
     case L_INNER_START: {  // FP32 inner solve A d = r from d = 0 to inner_tol, prime and first chunk
@@ -542,7 +542,7 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
       break;
     case L_START64:  // FP64 BiCGSTAB: r0 = b - A x, prime and first chunk
       PF_TRY(set_state(g, g->st, lo.tol, lo.norm, lo.max_iter, M.eta));
-      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b_of(g, M.op), g->geom, g->st, s));
+      PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b_of(g, M.op), g->geom, g->part, g->st, s));
       kinds.push_back(base + K_RES1);
       kinds.push_back(base + K_PRIME64);
       kinds.push_back(base + K_CHUNK64);

@@ -116,7 +116,8 @@ cudaError_t launch_unpack(const double* src, double* dst, const Geom& g, int cou
 // keep_r0 != 0 keeps r0norm2 of the previous state (later refinement steps of one solve)
 cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, double tol_r0, int keep_r0,
                              cudaStream_t s);
-cudaError_t launch_plane_bb(const double* b, const Geom& g, BicgState* st, cudaStream_t s);
+// b.b over the two Dirichlet planes -> st->bnorm2 (uses the partials buffer and the state's ticket)
+cudaError_t launch_plane_bb(const double* b, const Geom& g, double* part, BicgState* st, cudaStream_t s);
 // st->done = 1 (the stencil kernels then skip the state's grid)
 cudaError_t launch_mark_done(BicgState* st, cudaStream_t s);
 // r = r~ = b, p = v = t = 0 on interior nodes (x0 = 0); partials b.b, r.r, max|r|

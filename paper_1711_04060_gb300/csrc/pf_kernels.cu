@@ -195,24 +195,29 @@ __global__ void k_unpack(const double* __restrict__ src, double* __restrict__ ds
   }
 }
 
-// b.b over the two Dirichlet planes (which the stencil kernels do not visit) -> st->bnorm2
-__global__ void k_plane_bb(const double* __restrict__ b, Geom g, BicgState* st) {
+// b.b over the two Dirichlet planes (which the stencil kernels do not visit) -> st->bnorm2: blocks take
+// rows of the two planes in turn, the last-arriving block sums the block partials in fixed order.
+__global__ void __launch_bounds__(NTHREADS) k_plane_bb(const double* __restrict__ b, Geom g, double* part,
+                                                       BicgState* st) {
+  __shared__ double scratch[NTHREADS];
   double a = 0.0;
   const long last = g.plane * (g.nz - 1);
-  for (long r = 0; r < g.ny; ++r)
+  for (long row = blockIdx.x; row < 2L * g.ny; row += gridDim.x) {
+    const long base = (row < g.ny ? 0 : last) + g.px * (row % g.ny);
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
-      const double u = b[i + g.px * r], w = b[last + i + g.px * r];
+      const double u = b[base + i];
       a = fma(u, u, a);
-      a = fma(w, w, a);
     }
-  __shared__ double red[NTHREADS];
-  red[threadIdx.x] = a;
-  __syncthreads();
-  for (int s = NTHREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
   }
-  if (threadIdx.x == 0) st->bnorm2 = red[0];
+  double vals[1] = {a};
+  block_partials<1>(vals, 0u, part, scratch);
+  if (!arrive_last(&st->ticket)) return;
+  double tot[1];
+  total_partials<1>(part, 0u, tot, scratch);
+  if (threadIdx.x == 0) {
+    st->bnorm2 = tot[0];
+    st->ticket = 0;
+  }
 }
 
 __global__ void k_set_state(BicgState* st, double tol, int norm, int max_iter, double tol_r0, int keep_r0) {
@@ -515,8 +520,9 @@ cudaError_t launch_mark_done(BicgState* st, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_plane_bb(const double* b, const Geom& g, BicgState* st, cudaStream_t s) {
-  k_plane_bb<<<1, NTHREADS, 0, s>>>(b, g, st);
+cudaError_t launch_plane_bb(const double* b, const Geom& g, double* part, BicgState* st, cudaStream_t s) {
+  const int rows = 2 * g.ny;
+  k_plane_bb<<<rows < 128 ? rows : 128, NTHREADS, 0, s>>>(b, g, part, st);
   return cudaGetLastError();
 }
 
