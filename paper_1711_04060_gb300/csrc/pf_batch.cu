@@ -42,13 +42,15 @@ __device__ __forceinline__ void tensormap_acquire(const void* p) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(p) : "memory");
 }
 
+// Block b works for problem block_item[b].x as its block block_item[b].y (of the problem's nblk); a map lists
+// only the blocks of the problems that take part in the launch.
 template <class Op>
 __global__ void __launch_bounds__(NTHREADS, Op::MINB)
-    k_stencil_batch(const BatchItem<Op>* __restrict__ items, const int* __restrict__ block_item,
+    k_stencil_batch(const BatchItem<Op>* __restrict__ items, const int2* __restrict__ block_item,
                     unsigned long long wait_limit) {
-  const int i = block_item[blockIdx.x];
-  if (i < 0) return;
-  const BatchItem<Op>* it = items + i;
+  const int2 e = block_item[blockIdx.x];
+  if (e.x < 0) return;
+  const BatchItem<Op>* it = items + e.x;
   __shared__ typename Op::Args sa;
   __shared__ Geom sg;
   __shared__ int sn[3];
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(NTHREADS, Op::MINB)
     sa = it->a;
     sg = it->g;
     sn[0] = it->ntiles;
-    sn[1] = (int)blockIdx.x - it->block0;
+    sn[1] = e.y;
     sn[2] = it->nblk;
 #pragma unroll
     for (int h = 0; h < Op::NH; ++h) tensormap_acquire(&it->maps.h[h]);
@@ -111,14 +113,22 @@ struct pf_batch {
   size_t cap = 0, top = 0;
   // tables built for the current membership (invalidated when it changes)
   bool built = false;
-  int nblocks = 0;                      // blocks of a batched launch (all members)
+  int nblocks = 0;                      // blocks of all members together
   std::vector<int> block0, nblk;        // block range of each member
-  int* dmaps = nullptr;                 // N_SLOTS block maps of nblocks entries
-  std::vector<int> hmaps;
+  int2* dmaps = nullptr;                // N_SLOTS block maps of up to nblocks entries
+  std::vector<int2> hmaps;
+  int mapn[N_SLOTS] = {};               // entries of each map in this tick (the launch's grid size)
   BicgState** dst64 = nullptr;          // members' state pointers (device)
   BicgState** dst32 = nullptr;
   std::map<std::string, const void*> items;
-  std::map<std::string, cudaGraphExec_t> graphs;
+  // chunk graphs: the instantiated graph, its kernel nodes, and the grid size they were last given
+  struct Chunk {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> nodes;
+    int grid = 0;
+  };
+  std::map<std::string, Chunk> graphs;
   BicgState* dgather = nullptr;         // gathered states (device) and their pinned copy
   BicgState* hgather = nullptr;
   int gather_cap = 0;
@@ -160,7 +170,10 @@ void drain(pf_batch* B) {
 // Forgets every table and graph (after every stream drained).
 void invalidate(pf_batch* B) {
   drain(B);
-  for (auto& kv : B->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : B->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphDestroy(kv.second.graph);
+  }
   B->graphs.clear();
   B->items.clear();
   B->top = 0;
@@ -195,10 +208,11 @@ pf_status build(pf_batch* B) {
     nb += B->nblk[i];
   }
   B->nblocks = nb;
-  B->hmaps.assign((size_t)N_SLOTS * nb, -1);
+  B->hmaps.assign((size_t)N_SLOTS * nb, make_int2(-1, 0));
   for (int i = 0; i < n; ++i)
-    for (int b = 0; b < B->nblk[i]; ++b) B->hmaps[(size_t)SLOT_FULL * nb + B->block0[i] + b] = i;
-  B->dmaps = (int*)upload(B, B->hmaps.data(), B->hmaps.size() * sizeof(int));
+    for (int b = 0; b < B->nblk[i]; ++b) B->hmaps[(size_t)SLOT_FULL * nb + B->block0[i] + b] = make_int2(i, b);
+  B->mapn[SLOT_FULL] = nb;
+  B->dmaps = (int2*)upload(B, B->hmaps.data(), B->hmaps.size() * sizeof(int2));
   std::vector<BicgState*> s64, s32;
   for (pf_grid* g : B->grids) {
     s64.push_back(g->st);
@@ -221,7 +235,7 @@ pf_status build(pf_batch* B) {
   return PF_OK;
 }
 
-const int* map_of(pf_batch* B, int slot) { return B->dmaps + (size_t)slot * B->nblocks; }
+const int2* map_of(pf_batch* B, int slot) { return B->dmaps + (size_t)slot * B->nblocks; }
 
 // The item table of one launch kind over all members, built on first use.
 template <class Op, class Fill>
@@ -248,9 +262,10 @@ pf_status items_for(pf_batch* B, const std::string& key, Fill fill, const void**
 }
 
 template <class Op>
-pf_status launch_items(pf_batch* B, const void* items, const int* map, cudaStream_t st) {
+pf_status launch_items(pf_batch* B, const void* items, const int2* map, int grid, cudaStream_t st) {
   static_assert(pf::scratch_fits<Op>(), "reduction scratch must fit in the stage ring");
-  pf::k_stencil_batch<Op><<<B->nblocks, pf::NTHREADS, pf::smem_bytes<Op>(), st>>>(
+  if (grid < 1) return PF_OK;
+  pf::k_stencil_batch<Op><<<grid, pf::NTHREADS, pf::smem_bytes<Op>(), st>>>(
       static_cast<const pf::BatchItem<Op>*>(items), map, WAIT_LIMIT);
   PF_CK(cudaGetLastError());
   return PF_OK;
@@ -340,7 +355,7 @@ pf_status fill_res(pf_grid* g, int op, int init, const double* x, const double* 
 
 // ---- batched launches over the members flagged in a map slot -----------------------------------------
 template <bool UNI>
-pf_status launch_res(pf_batch* B, int op, int init, const int* map, cudaStream_t st) {
+pf_status launch_res(pf_batch* B, int op, int init, const int2* map, int grid, cudaStream_t st) {
   using OR = pf::OpResSkip<UNI>;
   const void* items = nullptr;
   PF_TRY((items_for<OR>(B, key_of(init ? "RES1" : "RES0", op, 1, 0),
@@ -348,7 +363,7 @@ pf_status launch_res(pf_batch* B, int op, int init, const int* map, cudaStream_t
                           return fill_res<UNI>(g, op, init, x_of(g, op), b_of(g, op), it);
                         },
                         &items)));
-  return launch_items<OR>(B, items, map, st);
+  return launch_items<OR>(B, items, map, grid, st);
 }
 
 template <typename T, bool UNI>
@@ -365,16 +380,17 @@ pf_status ca_items(pf_batch* B, int op, int par, int prime, const void** out) {
 }
 
 template <typename T, bool UNI>
-pf_status launch_prime(pf_batch* B, int op, const int* map, cudaStream_t st) {
+pf_status launch_prime(pf_batch* B, int op, const int2* map, int grid, cudaStream_t st) {
   const void* items = nullptr;
   PF_TRY((ca_items<T, UNI>(B, op, 0, 1, &items)));
-  return launch_items<pf::OpCA<T, UNI>>(B, items, map, st);
+  return launch_items<pf::OpCA<T, UNI>>(B, items, map, grid, st);
 }
 
 // CHUNK BiCGSTAB iterations (from parity 1, where every chunk starts since CHUNK is even) of the members in
-// the map slot: one captured graph per operator and precision, replayed while the membership stands.
+// the map slot: one captured graph per operator and precision, replayed while the membership stands; its
+// kernel nodes get the tick's grid size (the map's length) when it changes.
 template <typename T, bool UNI>
-pf_status launch_chunk(pf_batch* B, int op, const int* map, cudaStream_t st) {
+pf_status launch_chunk(pf_batch* B, int op, const int2* map, int grid, cudaStream_t st) {
   using OB = pf::OpB<T, UNI>;
   using OC = pf::OpCA<T, UNI>;
   constexpr int f64 = sizeof(T) == 8;
@@ -393,8 +409,8 @@ pf_status launch_chunk(pf_batch* B, int op, const int* map, cudaStream_t st) {
     int cur = 1;
     pf_status ls = PF_OK;
     for (int i = 0; i < CHUNK && ls == PF_OK; ++i) {
-      ls = launch_items<OB>(B, ib[cur], map, B->cstream);
-      if (ls == PF_OK) ls = launch_items<OC>(B, ica[cur], map, B->cstream);
+      ls = launch_items<OB>(B, ib[cur], map, B->nblocks, B->cstream);
+      if (ls == PF_OK) ls = launch_items<OC>(B, ica[cur], map, B->nblocks, B->cstream);
       cur = 1 - cur;
     }
     const cudaError_t ce = cudaStreamEndCapture(B->cstream, &graph);
@@ -403,25 +419,43 @@ pf_status launch_chunk(pf_batch* B, int op, const int* map, cudaStream_t st) {
       return ls;
     }
     PF_CK(ce);
-    cudaGraphExec_t exec = nullptr;
-    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    PF_CK(ie);
-    git = B->graphs.emplace(gk, exec).first;
+    pf_batch::Chunk c;
+    c.graph = graph;
+    const cudaError_t ie = cudaGraphInstantiate(&c.exec, graph, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      PF_CK(ie);
+    }
+    size_t nn = 0;
+    PF_CK(cudaGraphGetNodes(graph, nullptr, &nn));
+    c.nodes.resize(nn);
+    PF_CK(cudaGraphGetNodes(graph, c.nodes.data(), &nn));
+    c.grid = B->nblocks;
+    git = B->graphs.emplace(gk, c).first;
   }
-  PF_CK(cudaGraphLaunch(git->second, st));
+  pf_batch::Chunk& c = git->second;
+  if (grid != c.grid) {
+    for (cudaGraphNode_t nd : c.nodes) {
+      cudaKernelNodeParams kp;
+      PF_CK(cudaGraphKernelNodeGetParams(nd, &kp));
+      kp.gridDim = dim3(grid, 1, 1);
+      PF_CK(cudaGraphExecKernelNodeSetParams(c.exec, nd, &kp));
+    }
+    c.grid = grid;
+  }
+  PF_CK(cudaGraphLaunch(c.exec, st));
   return PF_OK;
 }
 
 template <bool UNI>
-pf_status launch_kind(pf_batch* B, int op, int kind, const int* map, cudaStream_t st) {
+pf_status launch_kind(pf_batch* B, int op, int kind, const int2* map, int grid, cudaStream_t st) {
   switch (kind) {
-    case K_RES0: return launch_res<UNI>(B, op, 0, map, st);
-    case K_RES1: return launch_res<UNI>(B, op, 1, map, st);
-    case K_PRIME32: return launch_prime<float, UNI>(B, op, map, st);
-    case K_PRIME64: return launch_prime<double, UNI>(B, op, map, st);
-    case K_CHUNK32: return launch_chunk<float, UNI>(B, op, map, st);
-    default: return launch_chunk<double, UNI>(B, op, map, st);
+    case K_RES0: return launch_res<UNI>(B, op, 0, map, grid, st);
+    case K_RES1: return launch_res<UNI>(B, op, 1, map, grid, st);
+    case K_PRIME32: return launch_prime<float, UNI>(B, op, map, grid, st);
+    case K_PRIME64: return launch_prime<double, UNI>(B, op, map, grid, st);
+    case K_CHUNK32: return launch_chunk<float, UNI>(B, op, map, grid, st);
+    default: return launch_chunk<double, UNI>(B, op, map, grid, st);
   }
 }
 
@@ -625,22 +659,16 @@ pf_status tick(pf_batch* B) {
     PF_TRY(pre(B, M, kinds[i]));
     for (int k : kinds[i]) use[k] = 1;
   }
-  // block maps of the launch kinds in use: a member's blocks in the kinds it takes part in, -1 elsewhere
+  // block maps of the launch kinds in use: the blocks of the members that take part, nothing else (the
+  // previous tick ended with a synchronisation, so the staging area is free)
   const int nb = B->nblocks;
-  for (int k = 0; k < SLOT_FULL; ++k)
-    if (use[k]) std::fill(B->hmaps.begin() + (size_t)k * nb, B->hmaps.begin() + (size_t)(k + 1) * nb, -1);
+  for (int k = 0; k < SLOT_FULL; ++k) B->mapn[k] = 0;
   for (int i = 0; i < n; ++i)
     for (int k : kinds[i])
-      for (int b = 0; b < B->nblk[i]; ++b) B->hmaps[(size_t)k * nb + B->block0[i] + b] = i;
-  // (the previous tick ended with a synchronisation, so the staging area is free)
-  int lo = SLOT_FULL, hi = -1;
-  for (int k = 0; k < SLOT_FULL; ++k)
-    if (use[k]) {
-      lo = std::min(lo, k);
-      hi = std::max(hi, k);
-    }
-  if (hi >= lo) {
-    const size_t off = (size_t)lo * nb * sizeof(int), bytes = (size_t)(hi - lo + 1) * nb * sizeof(int);
+      for (int b = 0; b < B->nblk[i]; ++b) B->hmaps[(size_t)k * nb + B->mapn[k]++] = make_int2(i, b);
+  for (int k = 0; k < SLOT_FULL; ++k) {
+    if (!use[k]) continue;
+    const size_t off = (size_t)k * nb * sizeof(int2), bytes = (size_t)B->mapn[k] * sizeof(int2);
     unsigned char* stage = B->harena + ((unsigned char*)B->dmaps - B->darena) + off;
     memcpy(stage, (const unsigned char*)B->hmaps.data() + off, bytes);
     PF_CK(cudaMemcpyAsync((unsigned char*)B->dmaps + off, stage, bytes, cudaMemcpyHostToDevice, s));
@@ -658,8 +686,10 @@ pf_status tick(pf_batch* B) {
     for (int kind : order) {
       const int slot = op * K_PER_OP + kind;
       if (!use[slot]) continue;
-      const int* map = map_of(B, slot);
-      PF_TRY(op == PF_OP_PF1 ? launch_kind<true>(B, op, kind, map, st) : launch_kind<false>(B, op, kind, map, st));
+      const int2* map = map_of(B, slot);
+      const int grid = B->mapn[slot];
+      PF_TRY(op == PF_OP_PF1 ? launch_kind<true>(B, op, kind, map, grid, st)
+                             : launch_kind<false>(B, op, kind, map, grid, st));
     }
     PF_CK(cudaEventRecord(B->join[op], st));
     PF_CK(cudaStreamWaitEvent(s, B->join[op], 0));
@@ -728,7 +758,7 @@ pf_status autotune(pf_batch* B) {
     B->tpb = c;
     B->built = false;
     PF_TRY(build(B));
-    const int* full = map_of(B, SLOT_FULL);
+    const int2* full = map_of(B, SLOT_FULL);
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {  // the first pass builds the tables and warms up
       for (pf_grid* g : B->grids) {
@@ -751,11 +781,11 @@ pf_status autotune(pf_batch* B) {
       }
       PF_TRY((ca_items<float, false>(B, PF_OP_POISSON, 0, 1, &ip)));
       PF_CK(cudaEventRecord(B->e0, B->stream));
-      PF_TRY(launch_items<OC>(B, ip, full, B->stream));
+      PF_TRY(launch_items<OC>(B, ip, full, B->nblocks, B->stream));
       int cur = 1;
       for (int i = 0; i < 4; ++i) {
-        PF_TRY(launch_items<OB>(B, ib[cur], full, B->stream));
-        PF_TRY(launch_items<OC>(B, ica[cur], full, B->stream));
+        PF_TRY(launch_items<OB>(B, ib[cur], full, B->nblocks, B->stream));
+        PF_TRY(launch_items<OC>(B, ica[cur], full, B->nblocks, B->stream));
         cur = 1 - cur;
       }
       PF_CK(cudaEventRecord(B->e1, B->stream));
@@ -951,7 +981,10 @@ pf_status pf_batch_nonlinear_solve(pf_batch* B, const pf_nl_opts* opts, pf_resul
 pf_status pf_batch_destroy(pf_batch* B) {
   if (!B) return PF_OK;
   drain(B);
-  for (auto& kv : B->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : B->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphDestroy(kv.second.graph);
+  }
   if (B->darena) cudaFree(B->darena);
   if (B->harena) cudaFreeHost(B->harena);
   if (B->dgather) cudaFree(B->dgather);
