@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--tol-outer", type=float, default=1e-3, help="||Phi - Phi_0||_inf stop (phi_hat units)")
     ap.add_argument("--lin-tol", type=float, default=1e-6, help="relative 2-norm tolerance of each linear solve")
+    ap.add_argument("--inner-tol", type=float, default=0.1, help="relative tolerance of the FP32 inner solves")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -277,7 +278,7 @@ def config_of(args):
     return {"workload": f"pf_{args.n}_four_pores_NaCaCl", "grid": f"{args.n}^3", "h_A": 64.0 / (args.n - 1),
             "species": "Na+ 0.1 M, Ca2+ 1 mM, Cl- 0.102 M, water 55.5 M", "charges": 48,
             "precision": args.precision, "tol_outer": args.tol_outer, "lin_tol": args.lin_tol,
-            "omega": 0.3, "accel_depth": args.accel_depth, "l2": "inputs larger than L2 (working set > 1 GB)",
+            "omega": 0.3, "accel_depth": args.accel_depth, "inner_tol": args.inner_tol, "l2": "inputs larger than L2 (working set > 1 GB)",
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -384,7 +385,8 @@ def run_ours(args):
     out = {k: torch.zeros(m, dtype=torch.float64, device=dev)
            for k, m in (("phi_V", N), ("C_M", ns * N), ("S", N), ("Gamma", N))}
     prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
-    opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, accel_depth=args.accel_depth)
+    opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, accel_depth=args.accel_depth,
+                       inner_tol=args.inner_tol)
 
     def barrier():
         torch.cuda.synchronize(dev)
