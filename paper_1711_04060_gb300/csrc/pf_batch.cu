@@ -1015,8 +1015,6 @@ pf_status engine_create(int max_members, pf_batch** out) {
 
 cudaStream_t engine_stream(pf_batch* B) { return B->stream; }
 
-int engine_size(pf_batch* B) { return (int)B->members.size(); }
-
 pf_status engine_add(pf_batch* B, pf_grid* g, pf_result* res, const pf_nl_opts& o, long long tag) {
   if (!g || !res || !g->have_coeffs) return fail(PF_E_INVAL, "engine member needs a grid with coefficients");
   PF_TRY(check_nl(o));

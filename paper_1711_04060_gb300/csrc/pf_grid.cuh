@@ -228,7 +228,6 @@ struct BatchMember {
 constexpr int ENGINE_TILES_PER_BLOCK = 4;
 pf_status engine_create(int max_members, pf_batch** out);
 cudaStream_t engine_stream(pf_batch* B);
-int engine_size(pf_batch* B);
 pf_status engine_add(pf_batch* B, pf_grid* g, pf_result* res, const pf_nl_opts& o, long long tag);
 pf_status engine_step(pf_batch* B, std::vector<long long>* finished);
 

@@ -117,3 +117,30 @@ def test_budget_gates_admission(api):
         ref, _ = _alone(api, p, opts)
         np.testing.assert_array_equal(out["phi_V"], ref["phi_V"])
     assert B.PF_PENDING == 8
+
+
+def test_mixed_precisions_and_a_failing_request(api):
+    """Requests of both precisions share the engine; one that hits its outer-iteration limit ends with
+    PF_E_NOCONV while the others finish normally and still equal their own batches."""
+    probs = _problems()[:4]
+    o64 = api.nl_opts(tol_outer=1e-9, tol=1e-11, precision=api.PF_FP64)
+    omx = api.nl_opts(tol_outer=1e-9, tol=1e-11, precision=api.PF_MIXED)
+    ofail = api.nl_opts(tol_outer=1e-12, tol=1e-11, max_outer=3)
+    opts = [o64, omx, ofail, omx]
+    srv = api.pf_server_create(8 << 30, 4)
+    try:
+        tickets = [api.pf_submit(srv, api.make_request(p, o)) for p, o in zip(probs, opts)]
+        results = []
+        for t, p in zip(tickets, probs):
+            t0 = time.time()
+            while not api.pf_done(srv, t):
+                assert time.time() - t0 < 300
+                time.sleep(0.005)
+            results.append(api.pf_poll(srv, t, p.grid.n, len(p.species), allow=(3,)))
+    finally:
+        api.pf_server_destroy(srv)
+    assert [r[2]["status"] for r in results] == [0, 0, 3, 0]
+    assert results[2][2]["outer_iters"] == 3
+    for k in (0, 1, 3):
+        ref, _ = _alone(api, probs[k], opts[k])
+        np.testing.assert_array_equal(results[k][1]["phi_V"], ref["phi_V"])
