@@ -80,3 +80,10 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_binding, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         _binding.load()
+
+
+def test_size_limit_is_refused_before_allocation(lib):
+    h = ctypes.c_void_p()
+    org = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    assert lib.pf_create_grid(2000, 2000, 1000, 1.0, org, None, ctypes.byref(h)) == 1  # PF_E_INVAL
+    assert b"too large" in lib.pf_last_error()

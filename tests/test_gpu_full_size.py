@@ -67,3 +67,40 @@ def test_full_size_linear_solve_against_the_oracle_operator(api, orc, prob):
     assert rep["status"] == 0
     r = b - orc.dia_apply(g.nx, g.ny, g.nz, A, x)
     assert np.linalg.norm(r) <= 2e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_config_129_linear_solver(api, orc, precision, tol):
+    """The 129^3 lognormal-dielectric linear system with sphere inclusions (2 / 78.5): the GPU solve in each
+    precision leaves the residual the oracle's operator measures within the stated tolerance, and (FP64) agrees
+    with the oracle's own BiCGSTAB solution as far as the conditioning lets a 1e-10 residual fix the solution."""
+    p = W.linear_problem(n=129, seed=1, n_spheres=32)
+    g = p.grid
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, p.eps)
+    grid = api.Grid(g.nx, g.ny, g.nz, g.h, g.origin)
+    grid.set_coeffs(p.eps, np.ones(g.n, np.uint8), np.zeros((0, 4)), 0.0, 0.0, [W.NA, W.CL, W.WATER], 78.5, 1.2)
+    x = np.zeros(g.n)
+    prec = api.PF_FP64 if precision == "fp64" else api.PF_MIXED
+    rep = grid.linear_solve(api.PF_OP_POISSON, p.b, x, api.solve_opts(tol=tol, precision=prec))
+    grid.close()
+    assert rep["status"] == 0
+    r = p.b - orc.dia_apply(g.nx, g.ny, g.nz, A, x)
+    assert np.linalg.norm(r) <= 1.5 * tol * np.linalg.norm(p.b)
+    if precision == "fp64":
+        ref = orc.bicgstab(g.nx, g.ny, g.nz, A, p.b, tol=1e-10, max_it=20000)
+        assert ref["status"] == 0
+        assert np.abs(x - ref["x"]).max() <= 1e-4 * np.abs(ref["x"]).max()
+
+
+def test_zero_right_hand_side(api):
+    """b = 0 gives x = 0 at once (the degenerate start), in both precisions."""
+    p = W.linear_problem(n=17, seed=4, n_spheres=2)
+    g = p.grid
+    grid = api.Grid(g.nx, g.ny, g.nz, g.h, g.origin)
+    grid.set_coeffs(p.eps, np.ones(g.n, np.uint8), np.zeros((0, 4)), 0.0, 0.0, [W.NA, W.CL, W.WATER], 78.5, 1.2)
+    for prec in (api.PF_FP64, api.PF_MIXED):
+        x = np.full(g.n, 0.0)
+        rep = grid.linear_solve(api.PF_OP_POISSON, np.zeros(g.n), x, api.solve_opts(tol=1e-10, precision=prec))
+        assert rep["status"] == 0 and rep["iterations"] == 0
+        assert not x.any()
+    grid.close()
