@@ -129,6 +129,11 @@ typedef struct {
                          start and eta_k = min(1e-2, c * delta_{k-1}) (an inexact-Newton forcing term, not in the
                          paper; 2-norm stop only).  The outer update is then exact to a fraction eta_k of itself,
                          so the stop test on delta keeps its meaning. */
+  int warm_start;     /* 0: Phi_0 from the initial PF2 solve with rho' = Psi = 0 (Table 4).  1: the iteration
+                         starts from the grid's current potential: the final Phi_0 of the previous
+                         pf_nonlinear_solve on this grid (so a solve stopped by max_outer resumes where it
+                         stopped) or the one given to pf_set_potential; PF_E_INVAL if the grid holds none.  The
+                         fixed point does not depend on the start. */
 } pf_nl_opts;
 
 /* Output and report of pf_nonlinear_solve.  Output pointers may be NULL; `mem` says whether
@@ -173,6 +178,11 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c);
 
 /* Sets kappa_c (Angstrom^-2) of PF_OP_PF2 from N values in host or device memory. */
 pf_status pf_set_kappa(pf_grid* g, const double* kappa, int mem);
+
+/* Sets the grid's potential Phi_0 (phi_V: N values in volts, node-major, host or device per `mem`) as the
+ * start of the next pf_nonlinear_solve with warm_start = 1: a checkpoint written from pf_result.phi_V, or a
+ * caller's guess.  Psi restarts from 0.  Needs pf_set_coeffs first (which forgets any potential). */
+pf_status pf_set_potential(pf_grid* g, const double* phi_V, int mem);
 
 /* Solves A x = b for the operator `op` (Table 3, Jacobi-preconditioned BiCGSTAB, preconditioner
  * applied from the right).  b and x have N entries in host or device memory (`mem`); x holds the
@@ -248,6 +258,12 @@ pf_status pf_fermi_noalloc(long n, const double* phi_V, const uint8_t* solvent, 
 /* Frees the grid and all its device memory.  NULL is accepted. */
 pf_status pf_destroy_grid(pf_grid* g);
 
+/* Self-test of failure detection without a fault: a one-block kernel waits, with the bounded wait that
+ * guards every TMA stage of the stencil kernels, on an mbarrier on which nothing ever arrives.  Returns
+ * PF_E_TIMEOUT once the wait gave up after limit_cycles clock cycles (the expected outcome; the context
+ * stays usable), PF_OK if the wait completed, PF_E_CUDA on a CUDA error.  Not in the paper. */
+pf_status pf_selftest_wait_timeout(unsigned long long limit_cycles, void* cuda_stream);
+
 /* Message of the calling thread's last failing call ("" if none). */
 const char* pf_last_error(void);
 
@@ -316,6 +332,8 @@ typedef struct {
   double origin_A[3];
   pf_coeffs coeffs;   /* host arrays; copied by pf_submit, the caller may free them afterwards */
   pf_nl_opts opts;
+  const double* phi0_V; /* optional host array (N values, volts; copied): the solve starts from this potential
+                           (warm start, as pf_set_potential + warm_start = 1); NULL: the paper's start */
 } pf_request;
 
 /* hbm_budget_bytes: device memory the server may hold for problem state; max_slots: problems

@@ -45,7 +45,7 @@ class pf_report(ctypes.Structure):
 
 class pf_nl_opts(ctypes.Structure):
     _fields_ = [("omega", _D), ("tol_outer", _D), ("max_outer", _I), ("lin", pf_solve_opts), ("accel_depth", _I),
-                ("lin_forcing", _D)]
+                ("lin_forcing", _D), ("warm_start", _I)]
 
 
 class pf_result(ctypes.Structure):
@@ -66,7 +66,7 @@ class pf_profile(ctypes.Structure):
 
 class pf_request(ctypes.Structure):
     _fields_ = [("nx", _I), ("ny", _I), ("nz", _I), ("h_A", _D), ("origin_A", _D * 3), ("coeffs", pf_coeffs),
-                ("opts", pf_nl_opts)]
+                ("opts", pf_nl_opts), ("phi0_V", _VP)]
 
 
 PF_BATCH_TUNE_MAX = 8
@@ -84,12 +84,14 @@ SIGNATURES = {
     "pf_create_grid": (_I, [_I, _I, _I, _D, ctypes.POINTER(_D), _VP, ctypes.POINTER(_VP)]),
     "pf_set_coeffs": (_I, [_VP, ctypes.POINTER(pf_coeffs)]),
     "pf_set_kappa": (_I, [_VP, _VP, _I]),
+    "pf_set_potential": (_I, [_VP, _VP, _I]),
     "pf_linear_solve": (_I, [_VP, _I, _VP, _VP, _I, ctypes.POINTER(pf_solve_opts), ctypes.POINTER(pf_report)]),
     "pf_nonlinear_solve": (_I, [_VP, ctypes.POINTER(pf_nl_opts), ctypes.POINTER(pf_result)]),
     "pf_destroy_grid": (_I, [_VP]),
     "pf_profile_enable": (_I, [_VP, _I]),
     "pf_profile_get": (_I, [_VP, ctypes.POINTER(pf_profile)]),
     "pf_last_error": (ctypes.c_char_p, []),
+    "pf_selftest_wait_timeout": (_I, [ctypes.c_ulonglong, _VP]),
     "pf_fermi_noalloc": (_I, [ctypes.c_long, _VP, _VP, _I, ctypes.POINTER(pf_species), _D, _VP, _VP, _VP, _VP]),
     "pf_batch_create": (_I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
     "pf_batch_set_tiles_per_block": (_I, [_VP, _I]),

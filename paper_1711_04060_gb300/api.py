@@ -63,11 +63,11 @@ def solve_opts(max_iter=20000, tol=1e-10, norm=PF_NORM_REL2, precision=PF_FP64, 
     return o
 
 
-def nl_opts(omega=0.3, tol_outer=1e-9, max_outer=500, accel_depth=0, lin_forcing=0.0, **lin):
+def nl_opts(omega=0.3, tol_outer=1e-9, max_outer=500, accel_depth=0, lin_forcing=0.0, warm_start=0, **lin):
     o = B.pf_nl_opts()
     B.load().pf_default_nl_opts(ctypes.byref(o))
     o.omega, o.tol_outer, o.max_outer = omega, tol_outer, max_outer
-    o.accel_depth, o.lin_forcing = accel_depth, lin_forcing
+    o.accel_depth, o.lin_forcing, o.warm_start = accel_depth, lin_forcing, warm_start
     o.lin = solve_opts(**lin)
     return o
 
@@ -251,8 +251,15 @@ def pf_server_create(hbm_budget_bytes, max_slots):
     return h
 
 
-def make_request(prob, opts=None):
-    """A pf_request for a problem of the workloads module (keeps its arrays alive on the object)."""
+def pf_set_potential(grid, phi_V):
+    """Sets the grid's potential (volts; numpy host array or CUDA tensor) as the start of a warm-started solve."""
+    p, m = _ptr(phi_V, np.float64)
+    _check(B.load().pf_set_potential(grid, p, m))
+
+
+def make_request(prob, opts=None, phi0_V=None):
+    """A pf_request for a problem of the workloads module (keeps its arrays alive on the object); phi0_V: an
+    optional starting potential (host array, volts)."""
     q = B.pf_request()
     g = prob.grid
     q.nx, q.ny, q.nz, q.h_A = g.nx, g.ny, g.nz, g.h
@@ -262,6 +269,9 @@ def make_request(prob, opts=None):
     q.coeffs = co.c
     q.opts = opts if opts is not None else nl_opts()
     q._keep = co
+    if phi0_V is not None:
+        q._phi0 = np.ascontiguousarray(phi0_V, dtype=np.float64)
+        q.phi0_V = q._phi0.ctypes.data
     return q
 
 
@@ -371,6 +381,9 @@ class Grid:
 
     def nonlinear_solve(self, opts=None, out=None, allow=()):
         return pf_nonlinear_solve(self.handle, self.n, self.n_species, opts, out, allow)
+
+    def set_potential(self, phi_V):
+        pf_set_potential(self.handle, phi_V)
 
     def profile(self, on=True):
         pf_profile_enable(self.handle, on)

@@ -616,6 +616,7 @@ void pf_default_nl_opts(pf_nl_opts* o) {
   pf_default_solve_opts(&o->lin);
   o->accel_depth = 0;
   o->lin_forcing = 0.0;
+  o->warm_start = 0;
 }
 
 const char* pf_last_error(void) { return g_err.c_str(); }
@@ -755,6 +756,37 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
   PF_CK(cudaStreamSynchronize(g->stream));
   if (*g->host_err) return fail(PF_E_INVAL, "a fixed charge lies outside the grid");
   g->have_coeffs = true;
+  g->have_phi0 = false;
+  g->ulast_valid = false;
+  return PF_OK;
+}
+
+pf_status pf_selftest_wait_timeout(unsigned long long limit_cycles, void* cuda_stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int* d = nullptr;
+  int h = -1;
+  PF_CK(cudaMallocAsync(&d, sizeof(int), s));
+  cudaError_t e = pf::launch_wait_probe(limit_cycles, d, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+  if (h == 7) return fail(PF_E_TIMEOUT, "the bounded wait gave up as intended");
+  return PF_OK;
+}
+
+pf_status pf_set_potential(pf_grid* g, const double* phi_V, int mem) {
+  if (!g || !phi_V) return fail(PF_E_INVAL, "grid and phi_V are required");
+  if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first");
+  if (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "mem must be PF_MEM_HOST or PF_MEM_DEVICE");
+  const long NP = g->geom.np;
+  PF_TRY(pack_in(g, phi_V, mem, g->phi0, 0));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, 1.0 / g->Tv, g->phi0, NP, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, g->geom, g->stream));
+  PF_CK(cudaMemsetAsync(g->psi, 0, NP * sizeof(double), g->stream));
+  PF_CK(cudaStreamSynchronize(g->stream));
+  g->have_phi0 = true;
+  g->ulast_valid = false;
   return PF_OK;
 }
 
@@ -805,6 +837,9 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1 || o.accel_depth < 0 ||
       o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0))
     return fail(PF_E_INVAL, "invalid pf_nl_opts");
+  if (o.warm_start != 0 && o.warm_start != 1) return fail(PF_E_INVAL, "invalid pf_nl_opts");
+  if (o.warm_start && !g->have_phi0)
+    return fail(PF_E_INVAL, "warm_start needs a potential on the grid (a previous solve or pf_set_potential)");
   const int m = o.accel_depth;
   if (m > 0) PF_TRY(ensure_aa(g, m));
   if (res->mem != PF_MEM_HOST && res->mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "bad result mem");
@@ -821,15 +856,20 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   pf_report rep{};
   // step a1: operators and fixed-charge source from the device-resident coefficients
   PF_TRY(build_operators(g));
-  // initial potential (Table 4): PF2 with rho' = Psi = 0 -> Phi_0
-  PF_CK(cudaMemsetAsync(g->phi0, 0, NP * sizeof(double), s));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, G, s));
-  PF_CK(cudaMemsetAsync(g->psi, 0, NP * sizeof(double), s));
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf2_rhs(g->psi, g->solvent, g->ffix, g->eps_s, g->lo_hat, g->hi_hat, G, g->b2, s));
-  PF_TRY(solve_dev(g, PF_OP_POISSON, g->b2, g->phi0, o.lin, &rep));
-  res->lin_iters_first = rep.iterations;
-  res->lin_iters_total += rep.iterations;
-  if (rep.status != PF_OK) st = (pf_status)rep.status;
+  const bool warm = o.warm_start != 0;
+  const bool fermi_warm = warm && g->ulast_valid;
+  if (!warm) {
+    // initial potential (Table 4): PF2 with rho' = Psi = 0 -> Phi_0
+    PF_CK(cudaMemsetAsync(g->phi0, 0, NP * sizeof(double), s));
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, G, s));
+    PF_CK(cudaMemsetAsync(g->psi, 0, NP * sizeof(double), s));
+    PF_LAUNCH(g, PF_PROF_OTHER,
+              pf::launch_pf2_rhs(g->psi, g->solvent, g->ffix, g->eps_s, g->lo_hat, g->hi_hat, G, g->b2, s));
+    PF_TRY(solve_dev(g, PF_OP_POISSON, g->b2, g->phi0, o.lin, &rep));
+    res->lin_iters_first = rep.iterations;
+    res->lin_iters_total += rep.iterations;
+    if (rep.status != PF_OK) st = (pf_status)rep.status;
+  }
   OuterUpdate U;
   double delta_prev = 1.0;
   for (int outer = 1; st == PF_OK && outer <= o.max_outer; ++outer) {
@@ -841,7 +881,8 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
     // Eq. (1) at Phi_0 -> b_PF1 = -lambda rho, kappa, PF2 right-hand-side part (Table 4)
     PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
     PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, g->b1, g->sig, g->c2,
-                                                 nullptr, nullptr, nullptr, g->ulast, outer > 1, g->err, s));
+                                                 nullptr, nullptr, nullptr, g->ulast, outer > 1 || fermi_warm,
+                                                 g->err, s));
     PF_TRY(update_pf2(g));
     PF_TRY(solve_dev(g, PF_OP_PF1, g->b1, g->psi, lo, &rep, eta));  // Eq. (12)
     res->lin_iters_total += rep.iterations;
@@ -872,7 +913,8 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   // outputs at the final potential
   PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
   PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, nullptr, nullptr, nullptr,
-                                               g->Cbuf, g->Sbuf, g->Gbuf, g->ulast, res->outer_iters > 0, g->err, s));
+                                               g->Cbuf, g->Sbuf, g->Gbuf, g->ulast, res->outer_iters > 0 || fermi_warm,
+                                               g->err, s));
   if (res->phi_V) {
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, NP, s));
     PF_TRY(unpack_out(g, g->phi, 1, res->phi_V, res->mem));
@@ -894,6 +936,8 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   prof_resolve(g);
   res->time_ms = ms;
   res->status = st;
+  g->have_phi0 = true;
+  g->ulast_valid = true;
   if (st != PF_OK) return fail(st, "nonlinear solve ended with status " + std::to_string((int)st));
   return PF_OK;
 }

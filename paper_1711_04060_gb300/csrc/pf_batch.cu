@@ -494,6 +494,11 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
       M.st = PF_OK;
       if (M.o.accel_depth > 0) PF_TRY(ensure_aa(g, M.o.accel_depth));
       PF_TRY(build_operators(g));
+      M.fermi_warm = M.o.warm_start && g->ulast_valid;
+      if (M.o.warm_start) {  // start from the grid's potential: straight to the first outer iteration
+        M.stage = S_FERMI;
+        return PF_OK;
+      }
       // initial potential (Table 4): PF2 with rho' = Psi = 0
       PF_CK(cudaMemsetAsync(g->phi0, 0, NP * sizeof(double), s));
       PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_set_dirichlet(g->phi0, g->lo_hat, g->hi_hat, g->geom, s));
@@ -509,7 +514,8 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
       const double eta = M.o.lin_forcing > 0 ? (outer == 1 ? 1e-2 : fmin(1e-2, M.o.lin_forcing * M.dprev)) : 0.0;
       PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
       PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, g->geom, g->b1, g->sig,
-                                                   g->c2, nullptr, nullptr, nullptr, g->ulast, outer > 1, g->err, s));
+                                                   g->c2, nullptr, nullptr, nullptr, g->ulast,
+                                                   outer > 1 || M.fermi_warm, g->err, s));
       PF_TRY(update_pf2(g));
       PF_TRY(lin_start(B, M, PF_OP_PF1, S_PF2RHS, eta));
       break;
@@ -526,8 +532,8 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
       pf_result& r = *M.res;
       PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
       PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, g->geom, nullptr, nullptr,
-                                                   nullptr, g->Cbuf, g->Sbuf, g->Gbuf, g->ulast, r.outer_iters > 0,
-                                                   g->err, s));
+                                                   nullptr, g->Cbuf, g->Sbuf, g->Gbuf, g->ulast,
+                                                   r.outer_iters > 0 || M.fermi_warm, g->err, s));
       if (r.phi_V) {
         PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, NP, s));
         PF_TRY(unpack_out(g, g->phi, 1, r.phi_V, r.mem));
@@ -714,6 +720,8 @@ pf_status tick(pf_batch* B) {
       if (*M.g->host_err && M.st == PF_OK) M.st = PF_E_GAMMA;
       M.res->status = M.st;
       M.stage = S_DONE;
+      M.g->have_phi0 = true;
+      M.g->ulast_valid = true;
       prof_resolve(M.g);
     } else {
       post(M, B->hgather[i], B->hgather[n + i]);
@@ -812,7 +820,7 @@ pf_status autotune(pf_batch* B) {
 pf_status check_nl(const pf_nl_opts& o) {
   PF_TRY(check_opts(o.lin));
   if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1 || o.accel_depth < 0 ||
-      o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0))
+      o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0) || (o.warm_start != 0 && o.warm_start != 1))
     return fail(PF_E_INVAL, "invalid pf_nl_opts");
   return PF_OK;
 }
@@ -929,6 +937,8 @@ pf_status pf_batch_nonlinear_solve(pf_batch* B, const pf_nl_opts* opts, pf_resul
   const int n = (int)B->grids.size();
   for (int i = 0; i < n; ++i) {
     if (!B->grids[i]->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first on every grid");
+    if (o.warm_start && !B->grids[i]->have_phi0)
+      return fail(PF_E_INVAL, "warm_start needs a potential on every grid (a previous solve or pf_set_potential)");
     if (results[i].mem != PF_MEM_HOST && results[i].mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "bad result mem");
   }
   PF_TRY(enter(B));
@@ -1019,6 +1029,7 @@ pf_status engine_add(pf_batch* B, pf_grid* g, pf_result* res, const pf_nl_opts& 
   if (!g || !res || !g->have_coeffs) return fail(PF_E_INVAL, "engine member needs a grid with coefficients");
   PF_TRY(check_nl(o));
   if (g->stream != B->stream) return fail(PF_E_INVAL, "engine member must use the engine's stream");
+  if (o.warm_start && !g->have_phi0) return fail(PF_E_INVAL, "warm_start needs a potential on the grid");
   BatchMember M;
   M.g = g;
   M.res = res;

@@ -51,6 +51,8 @@ struct pf_grid {
   cudaStream_t stream = nullptr;
   pf::Launch L{};
   bool have_coeffs = false;
+  bool have_phi0 = false;    // phi0 holds a potential to warm-start from (last solve or pf_set_potential)
+  bool ulast_valid = false;  // ulast holds the per-node ln Gamma of the last Fermi step on this problem
   // problem constants
   double eps_s = 78.5, lc = 0.0, T = 298.15, Tv = 0.0, lam = 0.0, lo_hat = 0.0, hi_hat = 0.0, molar = 0.0;
   pf::SpeciesParams sp{};
@@ -218,6 +220,7 @@ struct BatchMember {
   int op = 0, sub = 0, iters = 0, refs = 0;
   double eta = 0.0;     // forcing: also stop at eta ||r0||
   bool add_pending = false;
+  bool fermi_warm = false;  // the first Fermi step may start Newton from the grid's last ln Gamma (warm start)
   pf_status st = PF_OK;
   long long tag = 0;    // the owner's handle
 };

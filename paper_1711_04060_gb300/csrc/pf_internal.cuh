@@ -120,6 +120,8 @@ cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, 
 cudaError_t launch_plane_bb(const double* b, const Geom& g, double* part, BicgState* st, cudaStream_t s);
 // st->done = 1 (the stencil kernels then skip the state's grid)
 cudaError_t launch_mark_done(BicgState* st, cudaStream_t s);
+// *status = 7 when a bounded wait on a barrier that never completes gives up after `limit` cycles, else 0
+cudaError_t launch_wait_probe(unsigned long long limit, int* status, cudaStream_t s);
 // r = r~ = b, p = v = t = 0 on interior nodes (x0 = 0); partials b.b, r.r, max|r|
 template <typename T>
 cudaError_t launch_init_zero(const T* b, const Geom& g, T* r, T* rt, T* p, T* v, T* t, double* part, BicgState* st,

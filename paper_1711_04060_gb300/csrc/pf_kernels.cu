@@ -515,6 +515,23 @@ cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, 
 
 __global__ void k_mark_done(BicgState* st) { st->done = 1; }
 
+// Self-test of the bounded wait that guards every TMA stage: one thread waits on an mbarrier on which
+// nothing ever arrives; the wait must give up after `limit` cycles and report PF_E_TIMEOUT (7).
+__global__ void k_wait_probe(unsigned long long limit, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *status = mbar_wait(&bar, 0u, limit) ? 0 : 7;
+}
+
+cudaError_t launch_wait_probe(unsigned long long limit, int* status, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(limit, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mark_done(BicgState* st, cudaStream_t s) {
   k_mark_done<<<1, 1, 0, s>>>(st);
   return cudaGetLastError();

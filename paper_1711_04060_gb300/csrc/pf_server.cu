@@ -31,7 +31,7 @@ struct Request {
   uint64_t ticket = 0;
   int nx = 0, ny = 0, nz = 0;
   double h = 1.0, origin[3] = {0, 0, 0};
-  std::vector<double> eps, charges;
+  std::vector<double> eps, charges, phi0;
   std::vector<uint8_t> solvent;
   std::vector<pf_species> species;
   pf_coeffs coeffs{};
@@ -80,6 +80,10 @@ void complete(pf_server* sv, Request* r, pf_status s, const std::string& err) {
 bool join(pf_server* sv, pf_batch* E, Request* r) {
   pf_status s = pf_create_grid(r->nx, r->ny, r->nz, r->h, r->origin, pfi::engine_stream(E), &r->g);
   if (s == PF_OK) s = pf_set_coeffs(r->g, &r->coeffs);
+  if (s == PF_OK && !r->phi0.empty()) {
+    s = pf_set_potential(r->g, r->phi0.data(), PF_MEM_HOST);
+    r->opts.warm_start = 1;
+  }
   if (s == PF_OK) {
     r->phi.assign(r->N, 0.0);
     r->C.assign((size_t)r->N * r->species.size(), 0.0);
@@ -204,6 +208,11 @@ pf_status pf_submit(pf_server* sv, const pf_request* q, uint64_t* ticket) {
   r->coeffs.charges = r->charges.empty() ? nullptr : r->charges.data();
   r->coeffs.species = r->species.data();
   r->opts = q->opts;
+  if (q->phi0_V) r->phi0.assign(q->phi0_V, q->phi0_V + r->N);
+  else if (r->opts.warm_start) {
+    delete r;
+    return PF_E_INVAL;  // a fresh grid has no potential to start from
+  }
   std::lock_guard<std::mutex> lk(sv->mu);
   r->ticket = sv->next++;
   sv->all[r->ticket] = r;
