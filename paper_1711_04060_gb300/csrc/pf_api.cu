@@ -394,6 +394,7 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
 // term of an inexact outer iteration
 pf_status solve_dev(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, pf_report* rep,
                     double tol_r0 = 0.0) {
+  NvtxRange range(op == PF_OP_PF1 ? "PF1 solve" : op == PF_OP_PF2 ? "PF2 solve" : "Poisson solve");
   const bool uni = op == PF_OP_PF1;
   if (o.precision == PF_MIXED)
     return uni ? solve_mixed<true>(g, op, b, x, o, tol_r0, rep) : solve_mixed<false>(g, op, b, x, o, tol_r0, rep);
@@ -801,6 +802,7 @@ pf_status pf_set_kappa(pf_grid* g, const double* kappa, int mem) {
 
 pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int mem, const pf_solve_opts* opts,
                           pf_report* report) {
+  NvtxRange range("pf_linear_solve");
   if (!g || !b || !x) return fail(PF_E_INVAL, "grid, b and x are required");
   if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first");
   if (op != PF_OP_POISSON && op != PF_OP_PF1 && op != PF_OP_PF2) return fail(PF_E_INVAL, "unknown operator");
@@ -829,6 +831,7 @@ pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int me
 }
 
 pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res) {
+  NvtxRange range("pf_nonlinear_solve");
   if (!g || !res) return fail(PF_E_INVAL, "grid and result are required");
   if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first");
   pf_nl_opts o;

@@ -651,6 +651,7 @@ void post(BatchMember& M, const BicgState& s64, const BicgState& s32) {
 
 // One tick of the engine over all members.
 pf_status tick(pf_batch* B) {
+  NvtxRange range("batch tick");
   PF_TRY(build(B));
   cudaStream_t s = B->stream;
   const int n = (int)B->members.size();

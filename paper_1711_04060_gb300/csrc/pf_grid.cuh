@@ -14,6 +14,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pf_gb300.h"
 #include "pf_internal.cuh"
 
@@ -102,6 +104,12 @@ struct pf_grid {
 namespace pfi {
 
 int trace_level();
+
+// NVTX range for profilers (a no-op unless a tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 void prof_resolve(pf_grid* g);
 int prof_begin(pf_grid* g, int n_launches);
 void prof_end(pf_grid* g, int slot, int kind);
