@@ -274,31 +274,36 @@ const char* pf_last_error(void);
  * of all grids still iterating is ONE launch of a batched stencil kernel in which every grid
  * owns nblk = ceil(tiles / tiles_per_block) blocks; the chunks of BiCGSTAB iterations between
  * host checks are replayed as a captured CUDA graph.  A grid's arithmetic and reduction order
- * depend only on its own size and tiles_per_block, so a problem's result is bitwise the same
- * in any batch with the same tiles_per_block; against pf_nonlinear_solve (another block count)
- * it agrees to the solver tolerance.  Not in the paper.
+ * depend only on its own size and the tiling (tiles_per_block, tile depth), so a problem's result
+ * is bitwise the same in any batch with the same tiling; against pf_nonlinear_solve (another block
+ * count) it agrees to the solver tolerance.  Not in the paper.
  *
  * The batch borrows the grids (they must outlive it and must not be used by another call while
  * a batch call runs); its work is queued on cuda_stream, ordered after the work queued on each
  * grid's stream before the call, and the grids' streams wait for it afterwards. */
 typedef struct pf_batch pf_batch;
 
-#define PF_BATCH_TUNE_MAX 8
-/* Autotuner record: candidate tiles-per-block values and the device time (ms) of one timed
- * prime + 4 BiCGSTAB iterations of the batch's FP32 Poisson operators for each; chosen = the value in use. */
+#define PF_BATCH_TUNE_MAX 16
+/* Autotuner record: the candidate tilings (tiles per block, z-planes per 32 x 8 tile) and the device time
+ * (ms) of one timed prime + 4 BiCGSTAB iterations of the batch's FP32 Poisson operators for each;
+ * chosen / chosen_z = the tiling in use. */
 typedef struct {
   int n;
   int tiles_per_block[PF_BATCH_TUNE_MAX];
+  int z_planes[PF_BATCH_TUNE_MAX];
   float ms[PF_BATCH_TUNE_MAX];
-  int chosen;
+  int chosen, chosen_z;
 } pf_batch_tune;
 
 /* PF_E_INVAL for count < 1, a NULL or repeated grid; PF_E_OOM if the launch tables cannot be allocated. */
 pf_status pf_batch_create(pf_grid* const* grids, int count, void* cuda_stream, pf_batch** out);
 
-/* tiles_per_block >= 1 pins the block split (reproducible results across runs); 0 makes the next
- * solve run the autotuner first (the default). */
+/* tiles_per_block >= 1 pins the block split (reproducible results across runs) with the current tile depth
+ * (32 z-planes unless tuned or set); 0 makes the next solve run the autotuner first (the default). */
 pf_status pf_batch_set_tiles_per_block(pf_batch* b, int tiles_per_block);
+
+/* Pins both: tiles per block (>= 1) and the tile depth in z (4..256 interior planes per 32 x 8 tile). */
+pf_status pf_batch_set_tiling(pf_batch* b, int tiles_per_block, int z_planes);
 
 /* Runs the autotuner now (needs the coefficients on every grid); *out (may be NULL) gets its record.
  * It uses the grids' FP32 scratch vectors, which every solve re-initialises. */

@@ -69,12 +69,12 @@ class pf_request(ctypes.Structure):
                 ("opts", pf_nl_opts), ("phi0_V", _VP)]
 
 
-PF_BATCH_TUNE_MAX = 8
+PF_BATCH_TUNE_MAX = 16
 
 
 class pf_batch_tune(ctypes.Structure):
-    _fields_ = [("n", _I), ("tiles_per_block", _I * PF_BATCH_TUNE_MAX), ("ms", ctypes.c_float * PF_BATCH_TUNE_MAX),
-                ("chosen", _I)]
+    _fields_ = [("n", _I), ("tiles_per_block", _I * PF_BATCH_TUNE_MAX), ("z_planes", _I * PF_BATCH_TUNE_MAX),
+                ("ms", ctypes.c_float * PF_BATCH_TUNE_MAX), ("chosen", _I), ("chosen_z", _I)]
 
 
 # names declared in include/pf_gb300.h, with their ctypes signatures
@@ -95,6 +95,7 @@ SIGNATURES = {
     "pf_fermi_noalloc": (_I, [ctypes.c_long, _VP, _VP, _I, ctypes.POINTER(pf_species), _D, _VP, _VP, _VP, _VP]),
     "pf_batch_create": (_I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
     "pf_batch_set_tiles_per_block": (_I, [_VP, _I]),
+    "pf_batch_set_tiling": (_I, [_VP, _I, _I]),
     "pf_batch_autotune": (_I, [_VP, ctypes.POINTER(pf_batch_tune)]),
     "pf_batch_get_tune": (_I, [_VP, ctypes.POINTER(pf_batch_tune)]),
     "pf_batch_nonlinear_solve": (_I, [_VP, ctypes.POINTER(pf_nl_opts), ctypes.POINTER(pf_result)]),

@@ -175,9 +175,14 @@ def pf_batch_set_tiles_per_block(batch, tiles_per_block):
     _check(B.load().pf_batch_set_tiles_per_block(batch, int(tiles_per_block)))
 
 
+def pf_batch_set_tiling(batch, tiles_per_block, z_planes):
+    _check(B.load().pf_batch_set_tiling(batch, int(tiles_per_block), int(z_planes)))
+
+
 def _tune_dict(t):
-    return {"tiles_per_block": [t.tiles_per_block[i] for i in range(t.n)], "ms": [t.ms[i] for i in range(t.n)],
-            "chosen": t.chosen}
+    return {"tiles_per_block": [t.tiles_per_block[i] for i in range(t.n)],
+            "z_planes": [t.z_planes[i] for i in range(t.n)], "ms": [t.ms[i] for i in range(t.n)],
+            "chosen": t.chosen, "chosen_z": t.chosen_z}
 
 
 def pf_batch_autotune(batch):
@@ -331,6 +336,9 @@ class Batch:
 
     def set_tiles_per_block(self, tiles_per_block):
         pf_batch_set_tiles_per_block(self.handle, tiles_per_block)
+
+    def set_tiling(self, tiles_per_block, z_planes):
+        pf_batch_set_tiling(self.handle, tiles_per_block, z_planes)
 
     def nonlinear_solve(self, opts=None, outs=None, allow=()):
         return pf_batch_nonlinear_solve(self.handle, [(g.n, g.n_species) for g in self.grids], opts, outs, allow)

@@ -106,6 +106,7 @@ struct pf_batch {
   cudaStream_t cstream = nullptr; // chunk graphs are captured here
   cudaEvent_t fork = nullptr, join[N_OPS] = {};
   int tpb = 0;                    // tiles per block; 0: tune at the next solve
+  int zc = pf::ZC;                // interior z-planes per tile
   pf_batch_tune tune{};
   // device arena for launch tables, filled from a pinned staging copy
   unsigned char* darena = nullptr;
@@ -114,7 +115,7 @@ struct pf_batch {
   // tables built for the current membership (invalidated when it changes)
   bool built = false;
   int nblocks = 0;                      // blocks of all members together
-  std::vector<int> block0, nblk;        // block range of each member
+  std::vector<int> block0, nblk, ntl;   // block range and tile count of each member
   int2* dmaps = nullptr;                // N_SLOTS block maps of up to nblocks entries
   std::vector<int2> hmaps;
   int mapn[N_SLOTS] = {};               // entries of each map in this tick (the launch's grid size)
@@ -138,7 +139,8 @@ struct pf_batch {
 namespace {
 
 constexpr size_t ARENA_BYTES = 16u << 20;
-const int TPB_CANDIDATES[] = {1, 2, 4, 8, 16, 32};
+const int TPB_CANDIDATES[] = {1, 2, 4, 8, 16};
+const int ZC_CANDIDATES[] = {16, 32, 64};
 
 template <typename T>
 OpArrays<T> opsT(const pf_grid* g, int op);
@@ -201,10 +203,13 @@ pf_status build(pf_batch* B) {
   const int n = (int)B->grids.size();
   B->block0.assign(n, 0);
   B->nblk.assign(n, 0);
+  B->ntl.assign(n, 0);
   int nb = 0;
   for (int i = 0; i < n; ++i) {
+    const pf_grid* g = B->grids[i];
+    B->ntl[i] = pf::tiles_for(g->nx, g->ny, g->nz, B->zc);
     B->block0[i] = nb;
-    B->nblk[i] = blocks_for(B->grids[i]->L.ntiles, B->tpb);
+    B->nblk[i] = blocks_for(B->ntl[i], B->tpb);
     nb += B->nblk[i];
   }
   B->nblocks = nb;
@@ -250,7 +255,8 @@ pf_status items_for(pf_batch* B, const std::string& key, Fill fill, const void**
     pf_grid* g = B->grids[j];
     PF_TRY(fill((int)j, g, v[j]));
     v[j].g = g->geom;
-    v[j].ntiles = g->L.ntiles;
+    v[j].g.zc = B->zc;
+    v[j].ntiles = B->ntl[j];
     v[j].nblk = B->nblk[j];
     v[j].block0 = B->block0[j];
   }
@@ -762,9 +768,11 @@ pf_status autotune(pf_batch* B) {
   }
   pf_batch_tune t{};
   float best = 1e30f;
-  int best_tpb = 4;
+  int best_tpb = 4, best_zc = pf::ZC;
+  for (int zc : ZC_CANDIDATES)
   for (int c : TPB_CANDIDATES) {
     B->tpb = c;
+    B->zc = zc;
     B->built = false;
     PF_TRY(build(B));
     const int2* full = map_of(B, SLOT_FULL);
@@ -803,16 +811,20 @@ pf_status autotune(pf_batch* B) {
     }
     if (t.n < PF_BATCH_TUNE_MAX) {
       t.tiles_per_block[t.n] = c;
+      t.z_planes[t.n] = zc;
       t.ms[t.n] = ms;
       ++t.n;
     }
     if (ms < best) {
       best = ms;
       best_tpb = c;
+      best_zc = zc;
     }
   }
   B->tpb = best_tpb;
+  B->zc = best_zc;
   t.chosen = best_tpb;
+  t.chosen_z = best_zc;
   B->tune = t;
   B->built = false;
   return PF_OK;
@@ -911,6 +923,14 @@ pf_status pf_batch_set_tiles_per_block(pf_batch* B, int tiles_per_block) {
   return PF_OK;
 }
 
+pf_status pf_batch_set_tiling(pf_batch* B, int tiles_per_block, int z_planes) {
+  if (!B || tiles_per_block < 1 || z_planes < 4 || z_planes > 256) return fail(PF_E_INVAL, "bad batch tiling");
+  invalidate(B);
+  B->tpb = tiles_per_block;
+  B->zc = z_planes;
+  return PF_OK;
+}
+
 pf_status pf_batch_autotune(pf_batch* B, pf_batch_tune* out) {
   if (!B) return fail(PF_E_INVAL, "batch is NULL");
   for (pf_grid* g : B->grids)
@@ -927,6 +947,7 @@ pf_status pf_batch_get_tune(pf_batch* B, pf_batch_tune* out) {
   if (!B || !out) return fail(PF_E_INVAL, "batch and out are required");
   *out = B->tune;
   out->chosen = B->tpb;
+  out->chosen_z = B->zc;
   return PF_OK;
 }
 

@@ -9,7 +9,7 @@ namespace pf {
 constexpr int TX = 32;           // tile width in x (one warp per row)
 constexpr int TY = 8;            // tile height in y
 constexpr int NTHREADS = TX * TY;
-constexpr int ZC = 32;           // interior planes per z-chunk of a tile
+constexpr int ZC = 32;           // interior planes per z-chunk of a tile (default; Geom::zc may choose another)
 constexpr int MAXSP = 8;
 constexpr int NPART = 16;        // per-block partial values reduced by the last block
 constexpr int HBX = TX + 8;      // TMA halo box: x from x0-4 (16-byte aligned start) to x0+TX+3
@@ -22,6 +22,7 @@ struct Geom {
   long plane;  // px * ny
   long np;     // plane * nz (allocated elements)
   long n;      // nx * ny * nz (nodes)
+  int zc;      // interior z-planes per tile of the stencil kernels
 };
 
 inline Geom make_geom(int nx, int ny, int nz) {
@@ -33,6 +34,7 @@ inline Geom make_geom(int nx, int ny, int nz) {
   g.plane = (long)g.px * ny;
   g.np = g.plane * nz;
   g.n = (long)nx * ny * nz;
+  g.zc = ZC;
   return g;
 }
 
@@ -90,7 +92,7 @@ struct SpeciesParams {
   double lam;           // lambda
 };
 
-int tiles_for(int nx, int ny, int nz);
+int tiles_for(int nx, int ny, int nz, int zc = ZC);
 int max_partial_blocks();
 
 // host: encode a 3D tensor map over a padded device array (halo box when halo, else centre box)

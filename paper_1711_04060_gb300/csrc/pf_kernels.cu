@@ -9,8 +9,8 @@
 
 namespace pf {
 
-int tiles_for(int nx, int ny, int nz) {
-  const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, nzc = (nz - 2 + ZC - 1) / ZC;
+int tiles_for(int nx, int ny, int nz, int zc) {
+  const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, nzc = (nz - 2 + zc - 1) / zc;
   return ntx * nty * nzc;
 }
 

@@ -94,7 +94,7 @@ struct Acc<float> {
 template <typename T>
 __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
 
-// Inner-product partials: a thread sums the products of one tile column (at most ZC + 1 terms) in the
+// Inner-product partials: a thread sums the products of one tile column (at most zc + 1 terms) in the
 // working precision; at the end of each tile the warp adds its threads' sums in FP64 (fixed shuffle tree)
 // to its FP64 totals in shared memory (wsum[warp * NV + j]), so the global inner products are FP64 sums of
 // short working-precision partial sums and no thread holds FP64 accumulators across tiles.
@@ -204,14 +204,14 @@ struct Tile {
   int x0, y0, kb, ke;
 };
 
-__device__ __forceinline__ Tile tile_of(int t, int nx, int nz) {
-  const int nzc = (nz - 2 + ZC - 1) / ZC, ntx = (nx + TX - 1) / TX;
+__device__ __forceinline__ Tile tile_of(int t, int nx, int nz, int zcs) {
+  const int nzc = (nz - 2 + zcs - 1) / zcs, ntx = (nx + TX - 1) / TX;
   const int zc = t % nzc, xy = t / nzc;
   Tile r;
   r.x0 = (xy % ntx) * TX;
   r.y0 = (xy / ntx) * TY;
-  r.kb = 1 + zc * ZC;
-  r.ke = min(r.kb + ZC, nz - 1);
+  r.kb = 1 + zc * zcs;
+  r.ke = min(r.kb + zcs, nz - 1);
   return r;
 }
 
@@ -336,7 +336,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
   static_assert((D & (D - 1)) == 0, "the stage ring has a power-of-two size");
   int pt = bid, pj = 0;
   unsigned pseq = 0;
-  Tile ptl = tile_of(pt, g.nx, g.nz);
+  Tile ptl = tile_of(pt, g.nx, g.nz, g.zc);
   auto issue = [&]() {
     const int stage = pseq & (D - 1);
     unsigned char* sb = smem + stage * STAGE;
@@ -351,7 +351,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
     if (++pj == ptl.ke - ptl.kb + 2) {
       pj = 0;
       pt += nblk;
-      if (pt < ntiles) ptl = tile_of(pt, g.nx, g.nz);
+      if (pt < ntiles) ptl = tile_of(pt, g.nx, g.nz, g.zc);
     }
   };
   if (threadIdx.x == 0)
@@ -362,7 +362,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
   unsigned seq = 0;
   bool failed = false;
   for (int t = bid; t < ntiles && !failed; t += nblk) {
-    const Tile tl = tile_of(t, g.nx, g.nz);
+    const Tile tl = tile_of(t, g.nx, g.nz, g.zc);
     const TileGeo geo = tile_geo(tl, g.nx, g.ny);
     const int planes = tl.ke - tl.kb + 2;
     typename Op::Ctr cprev{}, cnow{};

@@ -77,6 +77,23 @@ def test_batch_matches_oracle(api, orc, precision):
             assert _rel(C[i], ref["C_M"][i]) < TOL_CONC, (p.name, i)
 
 
+def test_other_tile_depths_match_the_oracle(api, orc):
+    probs = _problems()[:2]
+    grids = [api.Grid.for_problem(p) for p in probs]
+    batch = api.Batch(grids)
+    try:
+        for z in (16, 64):
+            batch.set_tiling(2, z)
+            res = batch.nonlinear_solve(api.nl_opts(tol_outer=1e-11, tol=1e-12))
+            for p, (out, rep) in zip(probs, res):
+                ref = orc.pf_solve_problem(p, tol_outer=1e-11, lin_tol=1e-12)
+                assert _rel(out["phi_V"], ref["phi_V"], floor=0.0257) < TOL_FP64
+    finally:
+        batch.close()
+        for g in grids:
+            g.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_alone_equals_in_mix_bitwise(api, precision):
     probs = _problems()
@@ -118,12 +135,14 @@ def test_autotuner_record(api):
     batch = api.Batch(grids)
     try:
         t = batch.autotune()
-        assert t["tiles_per_block"] == [1, 2, 4, 8, 16, 32]
+        assert t["tiles_per_block"] == [1, 2, 4, 8, 16] * 3
+        assert t["z_planes"] == [16] * 5 + [32] * 5 + [64] * 5
         assert all(ms > 0 for ms in t["ms"])
-        assert t["chosen"] == t["tiles_per_block"][int(np.argmin(t["ms"]))]
+        k = int(np.argmin(t["ms"]))
+        assert (t["chosen"], t["chosen_z"]) == (t["tiles_per_block"][k], t["z_planes"][k])
         res = batch.nonlinear_solve(api.nl_opts(tol_outer=1e-6, tol=1e-9, precision=api.PF_MIXED))
         assert all(r["status"] == 0 for _, r in res)
-        assert batch.tune()["chosen"] == t["chosen"]
+        assert (batch.tune()["chosen"], batch.tune()["chosen_z"]) == (t["chosen"], t["chosen_z"])
     finally:
         batch.close()
         for g in grids:
