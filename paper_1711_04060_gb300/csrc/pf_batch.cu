@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(NTHREADS, Op::MINB)
     for (int c = 0; c < Op::NC; ++c) tensormap_acquire(&it->maps.c[c]);
   }
   __syncthreads();
-  stencil_run<Op>(&it->maps, sa, sg, sn[0], sn[1], sn[2], wait_limit);
+  stencil_run<Op, false>(&it->maps, sa, sg, sn[0], sn[1], sn[2], wait_limit);
 }
 
 // dst[i] = *st64[i] (FP64 / refinement state) and dst[n + i] = *st32[i] (FP32 inner state) of every member

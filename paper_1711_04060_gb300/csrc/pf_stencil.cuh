@@ -309,10 +309,12 @@ constexpr bool scratch_fits() {
 // up_face(), output(), finish().  The calling block is block bid of the nblk blocks that share the
 // ntiles tiles of one grid (tiles bid, bid + nblk, ...) and its reductions; maps points to the grid's
 // tensor maps (kernel parameter or global memory).
-template <class Op>
+// FIXED_ZC: tiles of the compile-time depth ZC (single-grid kernels); else g.zc (batched kernels).
+template <class Op, bool FIXED_ZC = true>
 __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restrict__ maps,
                                             const typename Op::Args& a, const Geom& g, int ntiles, int bid,
                                             int nblk, unsigned long long wait_limit) {
+  const int zcs = FIXED_ZC ? ZC : g.zc;
   using T = typename Op::T;
   constexpr int D = Op::D, NH = Op::NH, NC = Op::NC;
   constexpr int HB = halo_slot_bytes<T>(), CB = centre_slot_bytes<T>(), STAGE = stage_bytes<Op>();
@@ -336,7 +338,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
   static_assert((D & (D - 1)) == 0, "the stage ring has a power-of-two size");
   int pt = bid, pj = 0;
   unsigned pseq = 0;
-  Tile ptl = tile_of(pt, g.nx, g.nz, g.zc);
+  Tile ptl = tile_of(pt, g.nx, g.nz, zcs);
   auto issue = [&]() {
     const int stage = pseq & (D - 1);
     unsigned char* sb = smem + stage * STAGE;
@@ -351,7 +353,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
     if (++pj == ptl.ke - ptl.kb + 2) {
       pj = 0;
       pt += nblk;
-      if (pt < ntiles) ptl = tile_of(pt, g.nx, g.nz, g.zc);
+      if (pt < ntiles) ptl = tile_of(pt, g.nx, g.nz, zcs);
     }
   };
   if (threadIdx.x == 0)
@@ -362,7 +364,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
   unsigned seq = 0;
   bool failed = false;
   for (int t = bid; t < ntiles && !failed; t += nblk) {
-    const Tile tl = tile_of(t, g.nx, g.nz, g.zc);
+    const Tile tl = tile_of(t, g.nx, g.nz, zcs);
     const TileGeo geo = tile_geo(tl, g.nx, g.ny);
     const int planes = tl.ke - tl.kb + 2;
     typename Op::Ctr cprev{}, cnow{};
