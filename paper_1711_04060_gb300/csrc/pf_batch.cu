@@ -139,6 +139,9 @@ struct pf_batch {
 namespace {
 
 constexpr size_t ARENA_BYTES = 16u << 20;
+// BiCGSTAB iterations per engine tick (even: every chunk starts at ping-pong parity 1); a problem whose
+// solve ends inside a chunk skips the rest of it (its state is done)
+constexpr int TICK_ITERS = 4;
 const int TPB_CANDIDATES[] = {1, 2, 4, 8, 16};
 const int ZC_CANDIDATES[] = {16, 32, 64};
 
@@ -392,7 +395,7 @@ pf_status launch_prime(pf_batch* B, int op, const int2* map, int grid, cudaStrea
   return launch_items<pf::OpCA<T, UNI>>(B, items, map, grid, st);
 }
 
-// CHUNK BiCGSTAB iterations (from parity 1, where every chunk starts since CHUNK is even) of the members in
+// TICK_ITERS BiCGSTAB iterations (from parity 1, where every chunk starts) of the members in
 // the map slot: one captured graph per operator and precision, replayed while the membership stands; its
 // kernel nodes get the tick's grid size (the map's length) when it changes.
 template <typename T, bool UNI>
@@ -414,7 +417,8 @@ pf_status launch_chunk(pf_batch* B, int op, const int2* map, int grid, cudaStrea
     PF_CK(cudaStreamBeginCapture(B->cstream, cudaStreamCaptureModeThreadLocal));
     int cur = 1;
     pf_status ls = PF_OK;
-    for (int i = 0; i < CHUNK && ls == PF_OK; ++i) {
+    static_assert(TICK_ITERS % 2 == 0, "chunks start at ping-pong parity 1");
+    for (int i = 0; i < TICK_ITERS && ls == PF_OK; ++i) {
       ls = launch_items<OB>(B, ib[cur], map, B->nblocks, B->cstream);
       if (ls == PF_OK) ls = launch_items<OC>(B, ica[cur], map, B->nblocks, B->cstream);
       cur = 1 - cur;
