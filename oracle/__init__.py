@@ -6,6 +6,7 @@ its package; callers pass plain arrays.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -49,26 +50,43 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
-        L.pfo_thermal_voltage.restype = _D
-        L.pfo_thermal_voltage.argtypes = [_D]
-        L.pfo_lambda.restype = _D
-        L.pfo_lambda.argtypes = [_D]
-        L.pfo_molar_to_per_A3.restype = _D
-        L.pfo_molar_to_per_A3.argtypes = []
-        L.pfo_species_setup.argtypes = [_I, _PD, _PD, _PD, _PD, _PD, _PD, _PD]
-        L.pfo_fermi_point.argtypes = [_I, _PD, _PD, _PD, _PD, _D, _D, _PD, _PD, _PD, _PI]
-        L.pfo_assemble_eps.argtypes = [_I, _I, _I, _D, _PD, _PD, _PD]
-        L.pfo_assemble_pf1.argtypes = [_I, _I, _I, _D, _PU8, _D, _D, _PD]
-        L.pfo_dia_apply.argtypes = [_I, _I, _I, _PD, _PD, _PD]
-        L.pfo_dia_apply.restype = None
-        L.pfo_bicgstab.argtypes = [_I, _I, _I, _PD, _PD, _PD, _I, _D, _I, _PI, _PD]
-        L.pfo_spread_charges.argtypes = [_I, _I, _I, _D, _PD, _I, _PD, _D, _PD]
-        L.pfo_pf_solve.argtypes = [_I, _I, _I, _D, _PD, _PD, _PU8, _I, _PD, _D, _D, _I, _PD, _PD, _PD,
-                                   _D, _D, _D, ctypes.POINTER(NlOpts), _PD, _PD, _PD, _PD, _PD, _PD,
-                                   ctypes.POINTER(NlReport)]
-        _lib = L
+        _lib = load(build())
     return _lib
+
+
+def load(path):
+    """The oracle library at `path` with its ctypes signatures (the tests also load mutated copies)."""
+    L = ctypes.CDLL(path)
+    L.pfo_thermal_voltage.restype = _D
+    L.pfo_thermal_voltage.argtypes = [_D]
+    L.pfo_lambda.restype = _D
+    L.pfo_lambda.argtypes = [_D]
+    L.pfo_molar_to_per_A3.restype = _D
+    L.pfo_molar_to_per_A3.argtypes = []
+    L.pfo_species_setup.argtypes = [_I, _PD, _PD, _PD, _PD, _PD, _PD, _PD]
+    L.pfo_fermi_point.argtypes = [_I, _PD, _PD, _PD, _PD, _D, _D, _PD, _PD, _PD, _PI]
+    L.pfo_assemble_eps.argtypes = [_I, _I, _I, _D, _PD, _PD, _PD]
+    L.pfo_assemble_pf1.argtypes = [_I, _I, _I, _D, _PU8, _D, _D, _PD]
+    L.pfo_dia_apply.argtypes = [_I, _I, _I, _PD, _PD, _PD]
+    L.pfo_dia_apply.restype = None
+    L.pfo_bicgstab.argtypes = [_I, _I, _I, _PD, _PD, _PD, _I, _D, _I, _PI, _PD]
+    L.pfo_spread_charges.argtypes = [_I, _I, _I, _D, _PD, _I, _PD, _D, _PD]
+    L.pfo_pf_solve.argtypes = [_I, _I, _I, _D, _PD, _PD, _PU8, _I, _PD, _D, _D, _I, _PD, _PD, _PD,
+                               _D, _D, _D, ctypes.POINTER(NlOpts), _PD, _PD, _PD, _PD, _PD, _PD,
+                               ctypes.POINTER(NlReport)]
+    return L
+
+
+@contextlib.contextmanager
+def using(L):
+    """Routes every oracle call inside the block to the library L."""
+    global _lib
+    saved = _lib
+    _lib = L
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 def _pd(a):

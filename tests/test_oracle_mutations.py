@@ -1,0 +1,75 @@
+"""The oracle's pins catch plausible mistakes: each test compiles a copy of the oracle with one mistake planted
+(on the CPU, in a temporary directory; the oracle source is untouched) and checks that at least one pin of
+tests/test_oracle_pins.py fails against it."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "pf_oracle.c")
+
+# (name, exact text in pf_oracle.c, planted replacement)
+MUTATIONS = [
+    ("arithmetic-mean faces instead of the SMIB/harmonic ones (Eqs. 15-18)",
+     "return 2.0 * a * b / (a + b);", "return 0.5 * (a + b);"),
+    ("p_i dropped from the steric exponent of Eq. (1)",
+     "double term = exp(la[i] + p[i] * u);", "double term = exp(la[i] + u);"),
+    ("kappa = lambda sum z_i C_i (z_i^2 lost, Eq. 13)",
+     "kap[c] += lam * z[i] * z[i] * Ci[i];", "kap[c] += lam * z[i] * Ci[i];"),
+    ("east and west neighbours transposed in the operator product",
+     "if (i < nx - 1) s += A[1 * N + c] * x[c + 1];\n        if (i > 0) s += A[2 * N + c] * x[c - 1];",
+     "if (i < nx - 1) s += A[1 * N + c] * x[c - 1 + 2 * (i == 0)];\n"
+     "        if (i > 0) s += A[2 * N + c] * x[c + 1 - 2 * (i == nx - 1)];"),
+    ("sign of the -eps_s Psi term of the PF2 right-hand side (Eq. 13)",
+     "(-eps_s * psi[c] + kap[c] * phi0[c])", "(eps_s * psi[c] + kap[c] * phi0[c])"),
+]
+
+# the pins, fastest first, with the arguments of one parametrisation each
+PINS = [
+    (P.test_fermi_bath_state, {"spec": P.SPEC2}),
+    (P.test_fermi_equal_radii_closed_form, {"phi": 0.7}),
+    (P.test_fermi_boltzmann_limit, {}),
+    (P.test_interface_1d_exact, {}),
+    (P.test_mirror_eigenfunction_3d, {}),
+    (P.test_operator_row_sums_and_symmetry, {}),
+    (P.test_debye_huckel_slab, {}),
+    (P.test_bicgstab_matches_dense_lu, {"seed": 0}),
+    (P.test_pf_fixed_point_satisfies_equations, {}),
+    (P.test_kappa_makes_pf2_a_newton_step, {}),
+    (P.test_pf_reduces_to_pb, {}),
+]
+
+
+def _build_mutant(tmp_path, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, old
+    path = tmp_path / "pf_oracle.c"
+    path.write_text(src.replace(old, new))
+    for h in ("pf_oracle.h",):
+        (tmp_path / h).write_text(open(os.path.join(os.path.dirname(SRC), h)).read())
+    so = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+                           "-shared", "-fPIC", "-o", str(so), str(path), "-lm"])
+    return oracle.load(str(so))
+
+
+def test_pins_pass_on_the_oracle():
+    for pin, kw in PINS:
+        pin(oracle, **kw)
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0][:40] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(tmp_path, name, old, new):
+    mutant = _build_mutant(tmp_path, old, new)
+    failed = []
+    with oracle.using(mutant):
+        for pin, kw in PINS:
+            try:
+                pin(oracle, **kw)
+            except AssertionError:
+                failed.append(pin.__name__)
+                break
+    assert failed, f"no pin catches: {name}"

@@ -446,3 +446,13 @@ def test_pf_antisymmetry(orc):
     ob = orc.pf_solve_problem(b, tol_outer=1e-12, lin_tol=1e-14)
     np.testing.assert_allclose(ob["phi_hat"], -oa["phi_hat"], atol=1e-9 * np.abs(oa["phi_hat"]).max())
     np.testing.assert_allclose(ob["C_M"][0], oa["C_M"][1], rtol=1e-8, atol=1e-12)
+
+
+def test_kappa_makes_pf2_a_newton_step(orc):
+    """Without relaxation (omega = 0), with lc = 0 and vanishing volumes, the kappa term of Eq. (13) is the
+    derivative of -lambda rho(phi), so each outer iteration is a Newton step of the PB equation: it converges
+    quadratically (5 steps to 1e-12 here), where a wrong linearisation only converges linearly."""
+    prob = _small_channel(9, lc=0.0, tiny=True)
+    out = orc.pf_solve_problem(prob, omega=0.0, tol_outer=1e-12, lin_tol=1e-14)
+    assert out["status"] == 0
+    assert out["report"]["outer_iters"] <= 6
