@@ -170,6 +170,11 @@ void pf_default_nl_opts(pf_nl_opts* o);
 pf_status pf_create_grid(int nx, int ny, int nz, double h_A, const double origin_A[3],
                          void* cuda_stream, pf_grid** out);
 
+/* Device bytes that pf_create_grid allocates for an nx x ny x nz grid, plus the 2m + 3 FP64 vectors that
+ * Anderson acceleration of depth m = accel_depth adds at its first use (0: none) — the figure the server's
+ * HBM budget admits requests by.  Needs no device. */
+size_t pf_grid_bytes(int nx, int ny, int nz, int accel_depth);
+
 /* Copies the problem data (host arrays) to the device and builds the operators: harmonic
  * face coefficients (Eqs. 15-18 with zero jump), diagonals and Jacobi scalings, the
  * trilinear fixed-charge source (Eq. 3) and the species constants of Eq. (1).  Validates

@@ -82,6 +82,7 @@ SIGNATURES = {
     "pf_default_solve_opts": (None, [ctypes.POINTER(pf_solve_opts)]),
     "pf_default_nl_opts": (None, [ctypes.POINTER(pf_nl_opts)]),
     "pf_create_grid": (_I, [_I, _I, _I, _D, ctypes.POINTER(_D), _VP, ctypes.POINTER(_VP)]),
+    "pf_grid_bytes": (ctypes.c_size_t, [_I, _I, _I, _I]),
     "pf_set_coeffs": (_I, [_VP, ctypes.POINTER(pf_coeffs)]),
     "pf_set_kappa": (_I, [_VP, _VP, _I]),
     "pf_set_potential": (_I, [_VP, _VP, _I]),

@@ -108,6 +108,11 @@ def pf_create_grid(nx, ny, nz, h_A, origin_A, cuda_stream=None):
     return h
 
 
+def pf_grid_bytes(nx, ny, nz, accel_depth=0):
+    """Device bytes of a grid of this size (the serving budget's figure); needs no device."""
+    return int(B.load().pf_grid_bytes(nx, ny, nz, accel_depth))
+
+
 def pf_set_coeffs(grid, coeffs: _Coeffs):
     _check(B.load().pf_set_coeffs(grid, ctypes.byref(coeffs.c)))
 

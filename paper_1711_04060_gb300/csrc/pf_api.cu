@@ -599,6 +599,11 @@ size_t pf_internal_grid_bytes(int nx, int ny, int nz, int accel_depth) {
 
 extern "C" {
 
+size_t pf_grid_bytes(int nx, int ny, int nz, int accel_depth) {
+  if (nx < 1 || ny < 1 || nz < 1) return 0;
+  return pf_internal_grid_bytes(nx, ny, nz, accel_depth < 0 ? 0 : accel_depth);
+}
+
 void pf_default_solve_opts(pf_solve_opts* o) {
   if (!o) return;
   o->max_iter = 20000;

@@ -14,7 +14,8 @@ HEADER = os.path.join(ROOT, "include", "pf_gb300.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:pf_status|void|const\s+char\s*\*)\s*\**\s*(pf_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:pf_status|void|size_t|const\s+char\s*\*)\s*\**\s*(pf_\w+)\s*\(", text,
+                                 flags=re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -87,3 +88,15 @@ def test_size_limit_is_refused_before_allocation(lib):
     org = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
     assert lib.pf_create_grid(2000, 2000, 1000, 1.0, org, None, ctypes.byref(h)) == 1  # PF_E_INVAL
     assert b"too large" in lib.pf_last_error()
+
+
+def test_grid_bytes_without_device(lib):
+    """The device footprint the server budgets by: about 385 bytes per padded node plus fixed buffers, and two
+    FP64 vectors per Anderson history column plus three."""
+    from paper_1711_04060_gb300 import api
+    n = 257
+    np_ = (n + 7) // 8 * 8 * n * n
+    b0 = api.pf_grid_bytes(n, n, n)
+    assert 385 * np_ < b0 < 385 * np_ + (1 << 20)
+    assert api.pf_grid_bytes(n, n, n, 5) - b0 == (2 * 5 + 3) * 8 * np_
+    assert api.pf_grid_bytes(0, 4, 4) == 0

@@ -101,10 +101,8 @@ def test_budget_gates_admission(api):
     probs = _problems()[:3]
     from paper_1711_04060_gb300 import _binding as B
     opts = api.nl_opts(tol_outer=1e-8, tol=1e-10)
-    # just above the device bytes of the largest grid (about 385 B per padded node plus reduction buffers
-    # of 16 doubles for each of 16 blocks per SM)
-    np_max = max(((p.grid.nx + 7) // 8 * 8) * p.grid.ny * p.grid.nz for p in probs)
-    one = int(1.05 * (385 * np_max + 152 * 16 * 128 + 8192))
+    # just above the device bytes of the largest grid
+    one = int(1.05 * max(api.pf_grid_bytes(p.grid.nx, p.grid.ny, p.grid.nz) for p in probs))
     srv = api.pf_server_create(one, 3)
     try:
         tickets = [api.pf_submit(srv, api.make_request(p, opts)) for p in probs]
