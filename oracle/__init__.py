@@ -27,7 +27,7 @@ _PI = ctypes.POINTER(ctypes.c_int)
 
 class NlOpts(ctypes.Structure):
     _fields_ = [("omega", _D), ("tol_outer", _D), ("lin_tol", _D), ("lin_norm", _I),
-                ("max_outer", _I), ("max_lin", _I)]
+                ("max_outer", _I), ("max_lin", _I), ("solver", _I)]
 
 
 class NlReport(ctypes.Structure):
@@ -70,6 +70,9 @@ def load(path):
     L.pfo_dia_apply.argtypes = [_I, _I, _I, _PD, _PD, _PD]
     L.pfo_dia_apply.restype = None
     L.pfo_bicgstab.argtypes = [_I, _I, _I, _PD, _PD, _PD, _I, _D, _I, _PI, _PD]
+    L.pfo_pcg.argtypes = [_I, _I, _I, _PD, _PD, _PD, _I, _D, _I, _PI, _PD]
+    L.pfo_weighted_asymmetry.restype = _D
+    L.pfo_weighted_asymmetry.argtypes = [_I, _I, _I, _PD]
     L.pfo_spread_charges.argtypes = [_I, _I, _I, _D, _PD, _I, _PD, _D, _PD]
     L.pfo_pf_solve.argtypes = [_I, _I, _I, _D, _PD, _PD, _PU8, _I, _PD, _D, _D, _I, _PD, _PD, _PD,
                                _D, _D, _D, ctypes.POINTER(NlOpts), _PD, _PD, _PD, _PD, _PD, _PD,
@@ -178,6 +181,23 @@ def bicgstab(nx, ny, nz, A, b, x0=None, max_it=1000, tol=1e-12, norm_mode=0):
     return {"status": st, "x": x, "iters": it.value, "res": res.value}
 
 
+def pcg(nx, ny, nz, A, b, x0=None, max_it=1000, tol=1e-12, norm_mode=0):
+    """Jacobi-preconditioned conjugate gradients (pfo_pcg); same results dict as bicgstab."""
+    A = _f64(A).ravel()
+    b = _f64(b)
+    x = np.zeros_like(b) if x0 is None else _f64(x0).copy()
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    st = lib().pfo_pcg(nx, ny, nz, _pd(A), _pd(b), _pd(x), max_it, tol, norm_mode, ctypes.byref(it),
+                       ctypes.byref(res))
+    return {"status": st, "x": x, "iters": it.value, "res": res.value}
+
+
+def weighted_asymmetry(nx, ny, nz, A):
+    A = _f64(A).ravel()
+    return lib().pfo_weighted_asymmetry(nx, ny, nz, _pd(A))
+
+
 def spread_charges(nx, ny, nz, h, origin, charges, lam_value):
     ch = _f64(charges).ravel()
     org = _f64(origin)
@@ -188,7 +208,7 @@ def spread_charges(nx, ny, nz, h, origin, charges, lam_value):
 
 def pf_solve(nx, ny, nz, h, origin, eps, solvent, charges, phi_lo_V, phi_hi_V, z, radius, bulk,
              eps_s, lc, T=298.15, omega=0.3, tol_outer=1e-10, lin_tol=1e-12, lin_norm=0, max_outer=500,
-             max_lin=20000):
+             max_lin=20000, solver=0):
     """Table 2 nonlinear PF solve; returns a dict of fields and the report."""
     N = nx * ny * nz
     ns = len(z)
@@ -199,7 +219,7 @@ def pf_solve(nx, ny, nz, h, origin, eps, solvent, charges, phi_lo_V, phi_hi_V, z
     z, radius, bulk = _f64(z), _f64(radius), _f64(bulk)
     out = {k: np.zeros(N) for k in ("phi_V", "S", "Gamma", "Psi", "phi_hat")}
     out["C_M"] = np.zeros(ns * N)
-    opts = NlOpts(omega, tol_outer, lin_tol, lin_norm, max_outer, max_lin)
+    opts = NlOpts(omega, tol_outer, lin_tol, lin_norm, max_outer, max_lin, solver)
     rep = NlReport()
     st = lib().pfo_pf_solve(nx, ny, nz, h, _pd(org), _pd(eps), sol.ctypes.data_as(_PU8), len(ch) // 4, _pd(ch),
                             phi_lo_V, phi_hi_V, ns, _pd(z), _pd(radius), _pd(bulk), eps_s, lc, T,

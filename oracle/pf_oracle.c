@@ -288,6 +288,101 @@ done:
   return status;
 }
 
+/* Conjugate gradients for the systems the paper calls symmetric (Section 3: the Laplace
+ * equation (9) and PF1 (12)).  The 7-diagonal operators here keep identity rows for fixed
+ * nodes and mirror ghosts on the x/y sides, so A itself is not symmetric: a mirror doubles a side
+ * row's coupling to its inner neighbour.  Weighting each row by w = (1/2 per mirrored direction)
+ * gives W A symmetric on the rows that are not identity rows, and with x = b on the identity rows
+ * the residual and every search direction vanish there.  Conjugate gradients in the inner product
+ * <u, v>_W = sum_c w_c u_c v_c with the Jacobi preconditioner M = diag(A) (a diagonal, hence
+ * self-adjoint in that inner product) is then ordinary preconditioned CG on W A x = W b. */
+static double side_weight(int nx, int ny, long c) {
+  const long i = c % nx, j = (c / nx) % ny;
+  return (i == 0 || i == nx - 1 ? 0.5 : 1.0) * (j == 0 || j == ny - 1 ? 0.5 : 1.0);
+}
+
+/* Largest |w_c A_cn - w_n A_nc| over couplings between rows that are not identity rows, relative
+ * to the largest |w_c A_cn|.  Zero (to rounding) for the operators of pfo_assemble_eps and
+ * pfo_assemble_pf1. */
+double pfo_weighted_asymmetry(int nx, int ny, int nz, const double* A) {
+  const long N = (long)nx * ny * nz, sy = nx, sz = (long)nx * ny;
+  double worst = 0.0, scale = 0.0;
+  for (long c = 0; c < N; ++c) {
+    if (is_identity_row(N, A, c)) continue;
+    const long i = c % nx, j = (c / nx) % ny, k = c / sz;
+    /* (diagonal slot of the neighbour, its slot pointing back, offset) */
+    const int fwd[6] = {1, 2, 3, 4, 5, 6}, back[6] = {2, 1, 4, 3, 6, 5};
+    const long off[6] = {1, -1, -sy, sy, -sz, sz};
+    const int ok[6] = {i < nx - 1, i > 0, j > 0, j < ny - 1, k > 0, k < nz - 1};
+    for (int d = 0; d < 6; ++d) {
+      if (!ok[d]) continue;
+      const long n = c + off[d];
+      if (is_identity_row(N, A, n)) continue;
+      const double a = side_weight(nx, ny, c) * A[fwd[d] * N + c];
+      const double b = side_weight(nx, ny, n) * A[back[d] * N + n];
+      if (fabs(a) > scale) scale = fabs(a);
+      if (fabs(a - b) > worst) worst = fabs(a - b);
+    }
+  }
+  return scale > 0.0 ? worst / scale : 0.0;
+}
+
+static double wdot(int nx, int ny, long n, const double* a, const double* b) {
+  double s = 0.0;
+  for (long c = 0; c < n; ++c) s += side_weight(nx, ny, c) * a[c] * b[c];
+  return s;
+}
+
+int pfo_pcg(int nx, int ny, int nz, const double* A, const double* b, double* x,
+            int max_it, double tol, int norm_mode, int* iters, double* res) {
+  const long N = (long)nx * ny * nz;
+  double* r = malloc(sizeof(double) * N);
+  double* z = malloc(sizeof(double) * N);
+  double* p = malloc(sizeof(double) * N);
+  double* q = malloc(sizeof(double) * N);
+  int status = PFO_E_NOCONV, it = 0;
+  double measure = 0.0;
+  if (!r || !z || !p || !q) { status = PFO_E_INVAL; goto done; }
+  for (long c = 0; c < N; ++c)
+    if (!(A[c] > 0.0)) { status = PFO_E_INVAL; goto done; } /* M = diag(A) must be positive */
+  if (pfo_weighted_asymmetry(nx, ny, nz, A) > 1e-13) { status = PFO_E_INVAL; goto done; }
+
+  for (long c = 0; c < N; ++c) if (is_identity_row(N, A, c)) x[c] = b[c];
+  double bnorm = sqrt(dot(N, b, b));
+  if (bnorm == 0.0) bnorm = 1.0;
+#define PFO_MEASURE(vec) (norm_mode == 0 ? sqrt(dot(N, vec, vec)) / bnorm : norm_inf(N, vec))
+#define PFO_CONVERGED(m) (norm_mode == 0 ? (m) <= tol : (m) < tol)
+
+  pfo_dia_apply(nx, ny, nz, A, x, r); /* r = b - A x */
+  for (long c = 0; c < N; ++c) r[c] = b[c] - r[c];
+  measure = PFO_MEASURE(r);
+  if (PFO_CONVERGED(measure)) { status = PFO_OK; goto done; }
+  for (long c = 0; c < N; ++c) { z[c] = r[c] / A[c]; p[c] = z[c]; } /* z = M^-1 r, p = z */
+  double rz = wdot(nx, ny, N, r, z);
+  for (it = 1; it <= max_it; ++it) {
+    pfo_dia_apply(nx, ny, nz, A, p, q); /* q = A p */
+    const double pq = wdot(nx, ny, N, p, q);
+    if (!(pq > 0.0)) { status = PFO_E_BREAKDOWN; break; } /* not positive definite */
+    const double alpha = rz / pq;
+    for (long c = 0; c < N; ++c) { x[c] += alpha * p[c]; r[c] -= alpha * q[c]; }
+    measure = PFO_MEASURE(r);
+    if (PFO_CONVERGED(measure)) { status = PFO_OK; break; }
+    for (long c = 0; c < N; ++c) z[c] = r[c] / A[c];
+    const double rz_next = wdot(nx, ny, N, r, z);
+    const double beta = rz_next / rz;
+    for (long c = 0; c < N; ++c) p[c] = z[c] + beta * p[c];
+    rz = rz_next;
+  }
+  if (it > max_it) it = max_it;
+#undef PFO_MEASURE
+#undef PFO_CONVERGED
+done:
+  if (iters) *iters = it;
+  if (res) *res = measure;
+  free(r); free(z); free(p); free(q);
+  return status;
+}
+
 /* Eq. (3) with the point charges spread onto the grid by trilinear weights: the source
  * lambda * q_j * delta(r - r_j) becomes lambda q_j w_c / h^3 at the 8 corners c. */
 int pfo_spread_charges(int nx, int ny, int nz, double h, const double* origin, int nq,
@@ -328,6 +423,11 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
   const long N = (long)nx * ny * nz;
   const double Tv = pfo_thermal_voltage(T), lam = pfo_lambda(T);
   pfo_nl_report R = {PFO_OK, 0, 0, 0, 0.0};
+  typedef int (*lin_fn)(int, int, int, const double*, const double*, double*, int, double, int, int*,
+                        double*);
+  if (opts->solver < 0 || opts->solver > 2) return PFO_E_INVAL;
+  const lin_fn solve_pf1 = opts->solver >= 1 ? pfo_pcg : pfo_bicgstab;
+  const lin_fn solve_pf2 = opts->solver == 2 ? pfo_pcg : pfo_bicgstab;
   double v[64], pr[64], cB[64], gB;
   if (ns > 64 || nx < 2 || ny < 2 || nz < 3) return PFO_E_INVAL;
   int st = pfo_species_setup(ns, z, radius_A, bulk_M, v, pr, cB, &gB);
@@ -362,7 +462,7 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
   PFO_SET_DIRICHLET(b);
   int its = 0;
   double res = 0.0;
-  st = pfo_bicgstab(nx, ny, nz, A, b, phi0, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
+  st = solve_pf2(nx, ny, nz, A, b, phi0, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
   R.lin_iters_first = its;
   R.lin_iters_total += its;
   if (st) goto out;
@@ -385,7 +485,7 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
     pfo_assemble_pf1(nx, ny, nz, h, solvent, eps_s, lc, A);
     for (long c = 0; c < N; ++c) b[c] = solvent[c] ? -lam * rho[c] : 0.0;
     for (long c = 0; c < plane; ++c) { b[c] = 0.0; b[N - plane + c] = 0.0; }
-    st = pfo_bicgstab(nx, ny, nz, A, b, psi, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
+    st = solve_pf1(nx, ny, nz, A, b, psi, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
     R.lin_iters_total += its;
     if (st) goto out;
     /* PF2, Eq. (13): -eps_s Lap phi - rho' phi = -eps_s Psi - rho' phi0 in the solvent,
@@ -396,7 +496,7 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
       b[c] = (solvent[c] ? (-eps_s * psi[c] + kap[c] * phi0[c]) : 0.0) + ffix[c];
     PFO_SET_DIRICHLET(b);
     for (long c = 0; c < N; ++c) phi[c] = phi0[c]; /* warm start */
-    st = pfo_bicgstab(nx, ny, nz, A, b, phi, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
+    st = solve_pf2(nx, ny, nz, A, b, phi, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
     R.lin_iters_total += its;
     if (st) goto out;
     /* relaxation and stop test */

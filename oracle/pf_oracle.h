@@ -76,6 +76,19 @@ void pfo_dia_apply(int nx, int ny, int nz, const double* A, const double* x, dou
 int pfo_bicgstab(int nx, int ny, int nz, const double* A, const double* b, double* x,
                  int max_it, double tol, int norm_mode, int* iters, double* res);
 
+/* Jacobi-preconditioned conjugate gradients for the symmetric systems of Section 3 (the Laplace
+ * equation (9) and PF1 (12)), in the inner product weighted by 1/2 per mirrored side direction
+ * under which the operators of pfo_assemble_eps / pfo_assemble_pf1 are self-adjoint (see
+ * pfo_weighted_asymmetry).  Same arguments, stop tests and results as pfo_bicgstab; returns
+ * PFO_E_INVAL when diag(A) is not positive or A is not symmetric in that inner product, and
+ * PFO_E_BREAKDOWN when a search direction has p.Ap <= 0 (A not positive definite). */
+int pfo_pcg(int nx, int ny, int nz, const double* A, const double* b, double* x,
+            int max_it, double tol, int norm_mode, int* iters, double* res);
+
+/* max |w_c A_cn - w_n A_nc| / max |w_c A_cn| over neighbouring rows that are not identity rows,
+ * with w = 1/2 per x or y side the node lies on. */
+double pfo_weighted_asymmetry(int nx, int ny, int nz, const double* A);
+
 /* Trilinear spreading of point charges q_j (units of e) at (x,y,z) in A onto the grid
  * nodes: adds lambda*q_j*w/h^3 to f at the 8 corners of the cell holding the charge. */
 int pfo_spread_charges(int nx, int ny, int nz, double h, const double* origin, int nq,
@@ -89,6 +102,9 @@ typedef struct {
   int lin_norm;      /* 0: relative 2-norm, 1: absolute inf-norm */
   int max_outer;
   int max_lin;
+  int solver;        /* 0: BiCGSTAB (Table 3) for every linear system; 1: conjugate gradients
+                        (pfo_pcg) for PF1; 2: conjugate gradients for PF1 and PF2 (symmetric in the
+                        zero-jump reading of Eqs. 15-18) */
 } pfo_nl_opts;
 
 typedef struct {

@@ -25,6 +25,10 @@ MUTATIONS = [
      "        if (i > 0) s += A[2 * N + c] * x[c + 1 - 2 * (i == nx - 1)];"),
     ("sign of the -eps_s Psi term of the PF2 right-hand side (Eq. 13)",
      "(-eps_s * psi[c] + kap[c] * phi0[c])", "(eps_s * psi[c] + kap[c] * phi0[c])"),
+    ("conjugate gradients with the unweighted inner product (mirror sides not symmetrised)",
+     "s += side_weight(nx, ny, c) * a[c] * b[c];", "s += a[c] * b[c];"),
+    ("conjugate gradients with the preconditioner left out of the search direction",
+     "p[c] = z[c] + beta * p[c];", "p[c] = r[c] + beta * p[c];"),
 ]
 
 # the pins, fastest first, with the arguments of one parametrisation each
@@ -40,6 +44,7 @@ PINS = [
     (P.test_pf_fixed_point_satisfies_equations, {}),
     (P.test_kappa_makes_pf2_a_newton_step, {}),
     (P.test_pf_reduces_to_pb, {}),
+    (P.test_pcg_iterates_minimise_the_energy_norm, {}),
 ]
 
 

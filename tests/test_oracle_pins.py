@@ -456,3 +456,133 @@ def test_kappa_makes_pf2_a_newton_step(orc):
     out = orc.pf_solve_problem(prob, omega=0.0, tol_outer=1e-12, lin_tol=1e-14)
     assert out["status"] == 0
     assert out["report"]["outer_iters"] <= 6
+
+
+# ---------------------------------------------------------------- conjugate gradients for the symmetric systems
+def _side_weights(nx, ny, nz):
+    """1/2 for every x or y side a node lies on: the mirror ghost doubles a side row's inward coupling."""
+    wx = np.where((np.arange(nx) == 0) | (np.arange(nx) == nx - 1), 0.5, 1.0)
+    wy = np.where((np.arange(ny) == 0) | (np.arange(ny) == ny - 1), 0.5, 1.0)
+    return np.broadcast_to(wy[:, None] * wx[None, :], (nz, ny, nx)).ravel()
+
+
+def _free_rows(M):
+    """Rows of a dense operator that are not identity rows (fixed nodes)."""
+    eye = np.eye(M.shape[0])
+    return np.array([not np.array_equal(M[c], eye[c]) for c in range(M.shape[0])])
+
+
+def _eps_system(seed, nx=5, ny=4, nz=6, h=0.9):
+    eps = W.to_f32_exact(2.0 + 76.5 * W.uniform(W.substream(seed, 1), nx * ny * nz))
+    sig = W.uniform(W.substream(seed, 2), nx * ny * nz, 0.0, 3.0)
+    b = W.uniform(W.substream(seed, 3), nx * ny * nz, -1.0, 1.0)
+    x0 = W.uniform(W.substream(seed, 4), nx * ny * nz, -0.5, 0.5)
+    return (nx, ny, nz), eps, sig, b, x0, h
+
+
+def test_operators_symmetric_in_the_side_weighted_inner_product(orc):
+    """Section 3 calls the Laplace and PF1 systems symmetric; with mirror sides and kept identity rows that holds
+    for diag(w) A on the free rows, w = 1/2 per side direction (dense check on small grids, both operators)."""
+    (nx, ny, nz), eps, sig, _, _, h = _eps_system(0)
+    p = W.channel_problem(9, box_half=4.0, slab_half=2.0, pores=((0.5, 0.0, 2.0),), n_charges=0)
+    g = p.grid
+    for dims, A in (((nx, ny, nz), orc.assemble_eps(nx, ny, nz, h, eps, sig)),
+                    ((g.nx, g.ny, g.nz), orc.assemble_pf1(g.nx, g.ny, g.nz, g.h, p.solvent, 78.5, 1.2))):
+        M = orc.dense_from_dia(*dims, A)
+        f = _free_rows(M)
+        S = (_side_weights(*dims)[:, None] * M)[np.ix_(f, f)]
+        np.testing.assert_allclose(S, S.T, rtol=0, atol=1e-14 * np.abs(S).max())
+        assert np.all(np.linalg.eigvalsh(0.5 * (S + S.T)) > 0)  # positive definite on the free rows
+        assert orc.weighted_asymmetry(*dims, A) < 1e-15
+    # one coupling changed: the check sees it and conjugate gradients refuses the matrix
+    A = orc.assemble_eps(nx, ny, nz, h, eps, sig).copy()
+    A[1, nx + 1 + nx * ny * 2] *= 1.01
+    assert orc.weighted_asymmetry(nx, ny, nz, A) > 1e-4
+    assert orc.pcg(nx, ny, nz, A, b=np.ones(nx * ny * nz))["status"] == 1
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_pcg_matches_dense_lu(orc, seed):
+    (nx, ny, nz), eps, sig, b, x0, h = _eps_system(seed)
+    A = orc.assemble_eps(nx, ny, nz, h, eps, sig)
+    xe = np.linalg.solve(orc.dense_from_dia(nx, ny, nz, A), b)
+    r = orc.pcg(nx, ny, nz, A, b, x0=x0, tol=1e-15, max_it=2000)
+    assert r["status"] == 0
+    np.testing.assert_allclose(r["x"], xe, rtol=0, atol=1e-11 * np.abs(xe).max())
+    r2 = orc.pcg(nx, ny, nz, A, b, tol=1e-13, norm_mode=1, max_it=2000)
+    assert r2["status"] == 0 and r2["res"] < 1e-13
+    np.testing.assert_allclose(r2["x"], xe, atol=1e-10 * np.abs(xe).max())
+
+
+def test_pcg_pf1_matches_dense_lu_and_diagonal_case(orc):
+    p = W.channel_problem(9, box_half=4.0, slab_half=2.0, pores=((0.5, 0.0, 2.0),), n_charges=0)
+    g = p.grid
+    A = orc.assemble_pf1(g.nx, g.ny, g.nz, g.h, p.solvent, 78.5, 1.2)
+    b = np.where(p.solvent == 1, W.uniform(11, g.n, -1, 1), 0.0)
+    xe = np.linalg.solve(orc.dense_from_dia(g.nx, g.ny, g.nz, A), b)
+    r = orc.pcg(g.nx, g.ny, g.nz, A, b, tol=1e-15, max_it=2000)
+    assert r["status"] == 0
+    np.testing.assert_allclose(r["x"], xe, atol=1e-12 * np.abs(xe).max())
+    # lc = 0: M^-1 A = I on the free rows, one step
+    A0 = orc.assemble_pf1(g.nx, g.ny, g.nz, g.h, p.solvent, 78.5, 0.0)
+    r0 = orc.pcg(g.nx, g.ny, g.nz, A0, b, tol=1e-14)
+    assert r0["status"] == 0 and r0["iters"] == 1
+
+
+def test_pcg_iterates_minimise_the_energy_norm(orc):
+    """The k-th CG iterate is the minimiser of the W A-energy norm of the error over x0 plus the k-dimensional
+    Krylov space of M^-1 A at M^-1 r0 (M = diag A); checked against a brute-force projection for k = 1..6."""
+    (nx, ny, nz), eps, sig, b, x0, h = _eps_system(1)
+    A = orc.assemble_eps(nx, ny, nz, h, eps, sig)
+    M = orc.dense_from_dia(nx, ny, nz, A)
+    w = _side_weights(nx, ny, nz)
+    f = _free_rows(M)
+    x0 = np.where(f, x0, b)  # the solver fixes the identity rows first
+    xe = np.linalg.solve(M, b)
+    WA = w[:, None] * M
+    d = np.diag(M)
+    r0 = b - M @ x0
+    basis = []
+    v = r0 / d
+    prev = np.inf
+    for k in range(1, 7):
+        for q in basis:  # two Gram-Schmidt passes keep the Krylov basis orthonormal
+            v = v - (q @ v) * q
+        for q in basis:
+            v = v - (q @ v) * q
+        basis.append(v / np.linalg.norm(v))
+        V = np.array(basis).T
+        y = np.linalg.solve(V.T @ WA @ V, V.T @ (w * r0))
+        x_best = x0 + V @ y
+        got = orc.pcg(nx, ny, nz, A, b, x0=x0, tol=1e-30, max_it=k)
+        assert got["status"] == 3 and got["iters"] == k
+        np.testing.assert_allclose(got["x"], x_best, rtol=0, atol=1e-9 * np.abs(xe).max())
+        e = got["x"] - xe
+        energy = e @ WA @ e
+        assert energy < prev
+        prev = energy
+        v = (M @ basis[-1]) / d
+
+
+def test_pcg_reports_noconv_and_rejects_nonpositive_diagonal(orc):
+    p = W.linear_problem(n=9, seed=3, n_spheres=4)
+    g = p.grid
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, p.eps)
+    r = orc.pcg(g.nx, g.ny, g.nz, A, p.b, tol=1e-14, max_it=3)
+    assert r["status"] == 3 and r["iters"] == 3
+    A2 = A.copy()
+    A2[0, g.n // 2] = -1.0
+    assert orc.pcg(g.nx, g.ny, g.nz, A2, p.b)["status"] == 1
+
+
+@pytest.mark.parametrize("solver", [1, 2])
+def test_pf_solve_with_cg_same_fixed_point(orc, solver):
+    """Conjugate gradients for PF1 (and PF2) reaches the fixed point the BiCGSTAB path reaches."""
+    prob = _small_channel(9)
+    ref = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-14)
+    out = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-14, solver=solver)
+    assert ref["status"] == 0 and out["status"] == 0
+    np.testing.assert_allclose(out["phi_hat"], ref["phi_hat"], rtol=0, atol=1e-10 * np.abs(ref["phi_hat"]).max())
+    for i in range(len(prob.species)):
+        np.testing.assert_allclose(out["C_M"][i], ref["C_M"][i], rtol=1e-9, atol=0)
+    assert abs(out["report"]["outer_iters"] - ref["report"]["outer_iters"]) <= 1
