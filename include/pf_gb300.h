@@ -196,6 +196,18 @@ pf_status pf_set_potential(pf_grid* g, const double* phi_V, int mem);
 pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int mem,
                           const pf_solve_opts* opts, pf_report* report);
 
+/* The same solve by Jacobi-preconditioned conjugate gradients, for the systems Section 3 calls
+ * symmetric (PF_OP_POISSON, the Laplace-type operator of Eq. 9, and PF_OP_PF1, Eq. 12) and for
+ * PF_OP_PF2 (Eq. 13), symmetric as well with the zero-jump faces of Eqs. (15)-(18) when kappa >= 0.
+ * The stored operators are symmetric in the inner product that weights a node by 1/2 for each x or
+ * y side it lies on (the mirror ghosts of Eq. 4 double a side row's inward coupling); CG runs in that
+ * inner product, one operator product per iteration.  Same arguments, layouts, stop tests and report
+ * as pf_linear_solve (iterations = CG iterations); FP64 only (PF_E_INVAL for PF_MIXED).  Returns
+ * PF_E_BREAKDOWN when a search direction has p.Ap <= 0 (an operator that is not positive definite,
+ * e.g. a negative kappa), PF_E_NOCONV at max_iter; x then holds the last iterate. */
+pf_status pf_linear_solve_cg(pf_grid* g, int op, const double* b, double* x, int mem,
+                             const pf_solve_opts* opts, pf_report* report);
+
 /* Runs the PF nonlinear iteration of Table 4 with the data of pf_set_coeffs: the initial PF2
  * solve with rho' = Psi = 0, then {Fermi/steric update (Eq. 1) -> PF1 solve (Eq. 12) -> PF2
  * solve (Eq. 13) -> Phi = omega Phi_0 + (1-omega) Phi, delta = ||Phi - Phi_0||_inf} until
@@ -219,7 +231,9 @@ enum {
   PF_PROF_RESIDUAL = 9,    /* FP64 true residual b - A x of iterative refinement */
   PF_PROF_FERMI = 10,      /* pointwise Fermi/steric step of Eq. (1) */
   PF_PROF_OTHER = 11,      /* setup, right-hand sides, relaxation, output conversion */
-  PF_PROF_KINDS = 12
+  PF_PROF_CG_DIRECTION = 12, /* conjugate gradients: direction u = r + beta u and q = A M^-1 u with <M^-1 u, q> */
+  PF_PROF_CG_UPDATE = 13,  /* conjugate gradients: x and r updates with the next inner products */
+  PF_PROF_KINDS = 14
 };
 
 typedef struct {

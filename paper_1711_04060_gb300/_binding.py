@@ -54,9 +54,9 @@ class pf_result(ctypes.Structure):
                 ("time_ms", _D)]
 
 
-PF_PROF_KINDS = 12
+PF_PROF_KINDS = 14
 PROF_NAMES = ["init", "b_fp64", "ca_fp64", "b_fp32", "ca_fp32", "b_fp64_pf1", "ca_fp64_pf1", "b_fp32_pf1",
-              "ca_fp32_pf1", "residual_fp64", "fermi", "other"]
+              "ca_fp32_pf1", "residual_fp64", "fermi", "other", "cg_direction", "cg_update"]
 
 
 class pf_profile(ctypes.Structure):
@@ -87,6 +87,7 @@ SIGNATURES = {
     "pf_set_kappa": (_I, [_VP, _VP, _I]),
     "pf_set_potential": (_I, [_VP, _VP, _I]),
     "pf_linear_solve": (_I, [_VP, _I, _VP, _VP, _I, ctypes.POINTER(pf_solve_opts), ctypes.POINTER(pf_report)]),
+    "pf_linear_solve_cg": (_I, [_VP, _I, _VP, _VP, _I, ctypes.POINTER(pf_solve_opts), ctypes.POINTER(pf_report)]),
     "pf_nonlinear_solve": (_I, [_VP, ctypes.POINTER(pf_nl_opts), ctypes.POINTER(pf_result)]),
     "pf_destroy_grid": (_I, [_VP]),
     "pf_profile_enable": (_I, [_VP, _I]),

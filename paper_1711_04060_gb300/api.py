@@ -122,15 +122,18 @@ def pf_set_kappa(grid, kappa):
     _check(B.load().pf_set_kappa(grid, p, mem))
 
 
-def pf_linear_solve(grid, op, b, x, opts=None, allow=()):
-    """Solves A x = b in place of x; returns the report as a dict.  Statuses in `allow` do not raise."""
+def pf_linear_solve(grid, op, b, x, opts=None, allow=(), method="bicgstab"):
+    """Solves A x = b in place of x (method "bicgstab": pf_linear_solve, "cg": pf_linear_solve_cg); returns
+    the report as a dict.  Statuses in `allow` do not raise."""
     pb, mb = _ptr(b, np.float64)
     px, mx = _ptr(x, np.float64)
     if mb != mx:
         raise TypeError("b and x must both be host or both be device arrays")
+    if method not in ("bicgstab", "cg"):
+        raise ValueError("method is 'bicgstab' or 'cg'")
+    fn = B.load().pf_linear_solve if method == "bicgstab" else B.load().pf_linear_solve_cg
     rep = B.pf_report()
-    st = B.load().pf_linear_solve(grid, op, pb, px, mb, ctypes.byref(opts) if opts is not None else None,
-                                  ctypes.byref(rep))
+    st = fn(grid, op, pb, px, mb, ctypes.byref(opts) if opts is not None else None, ctypes.byref(rep))
     _check(st, allow)
     return {"status": rep.status, "iterations": rep.iterations, "refinements": rep.refinements,
             "residual": rep.residual, "time_ms": rep.time_ms}
@@ -389,8 +392,8 @@ class Grid:
     def set_kappa(self, kappa):
         pf_set_kappa(self.handle, kappa)
 
-    def linear_solve(self, op, b, x, opts=None, allow=()):
-        return pf_linear_solve(self.handle, op, b, x, opts, allow)
+    def linear_solve(self, op, b, x, opts=None, allow=(), method="bicgstab"):
+        return pf_linear_solve(self.handle, op, b, x, opts, allow, method)
 
     def nonlinear_solve(self, opts=None, out=None, allow=()):
         return pf_nonlinear_solve(self.handle, self.n, self.n_species, opts, out, allow)

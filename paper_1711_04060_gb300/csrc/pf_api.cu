@@ -390,6 +390,48 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
   return PF_OK;
 }
 
+// Jacobi-preconditioned conjugate gradients in FP64 (the symmetric systems of Section 3): a start kernel,
+// then [direction, update] pairs in chunks of CHUNK iterations between reads of the device state, and the
+// true residual of the final iterate.
+pf_status solve_cg(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, pf_report* rep) {
+  const OpArrays<double> A = ops64(g, op);
+  const Krylov<double> K = kry64(g);
+  const pf::CgOperator C{A.dinv, A.diag, A.wE, A.wN, A.wU, A.wc, A.diagc};
+  cudaStream_t s = g->stream;
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_impose(x, b, A.dinv, g->geom.np, s));
+  PF_TRY(set_state(g, g->st, o.tol, o.norm, o.max_iter));
+  PF_LAUNCH(g, PF_PROF_INIT, pf::launch_cg_start(C, g->geom, b, x, K.r[0], K.p[0], g->part, g->st, s));
+  BicgState st{};
+  int cur = 0;
+  // the device state ends the solve by max_iter at the latest; the host bound only guards that
+  for (long launched = 0;; launched += CHUNK) {
+    PF_TRY(read_state(g, g->st, &st));
+    if (st.done) break;
+    if (launched > (long)o.max_iter + 2 * CHUNK) {
+      st.status = PF_E_NOCONV;
+      break;
+    }
+    for (int i = 0; i < CHUNK; ++i) {
+      PF_LAUNCH(g, PF_PROF_CG_DIRECTION,
+                pf::launch_cg_direction(C, g->geom, K.r[0], K.p[cur], K.p[1 - cur], K.v[0], g->part, g->st, s));
+      PF_LAUNCH(g, PF_PROF_CG_UPDATE, pf::launch_cg_update(C, g->geom, K.p[1 - cur], K.v[0], x, K.r[0], g->part, g->st, s));
+      cur = 1 - cur;
+    }
+  }
+  BicgState tr{};
+  PF_TRY(set_state(g, g->st2, o.tol, o.norm, 0));
+  PF_LAUNCH(g, PF_PROF_RESIDUAL, pf::launch_cg_start(C, g->geom, b, x, K.t, nullptr, g->part, g->st2, s));
+  PF_TRY(read_state(g, g->st2, &tr));
+  rep->status = st.status;
+  rep->iterations = st.iter;
+  rep->refinements = 0;
+  rep->residual = measure_of(tr, o.norm);
+  if (trace_level() > 0)
+    fprintf(stderr, "[pf] cg solve op %d: status %d iters %d residual %.3e\n", op, rep->status, rep->iterations,
+            rep->residual);
+  return PF_OK;
+}
+
 // tol_r0 > 0 also accepts ||r||_2 <= tol_r0 ||r0||_2 (r0: the residual of the starting x), the forcing
 // term of an inexact outer iteration
 pf_status solve_dev(pf_grid* g, int op, const double* b, double* x, const pf_solve_opts& o, pf_report* rep,
@@ -805,9 +847,8 @@ pf_status pf_set_kappa(pf_grid* g, const double* kappa, int mem) {
   return PF_OK;
 }
 
-pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int mem, const pf_solve_opts* opts,
-                          pf_report* report) {
-  NvtxRange range("pf_linear_solve");
+static pf_status linear_solve_entry(pf_grid* g, int op, const double* b, double* x, int mem,
+                                    const pf_solve_opts* opts, pf_report* report, bool cg) {
   if (!g || !b || !x) return fail(PF_E_INVAL, "grid, b and x are required");
   if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first");
   if (op != PF_OP_POISSON && op != PF_OP_PF1 && op != PF_OP_PF2) return fail(PF_E_INVAL, "unknown operator");
@@ -815,11 +856,17 @@ pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int me
   pf_solve_opts o;
   if (opts) o = *opts; else pf_default_solve_opts(&o);
   PF_TRY(check_opts(o));
+  if (cg && o.precision != PF_FP64) return fail(PF_E_INVAL, "conjugate gradients runs in FP64 only");
   pf_report rep{};
   PF_CK(cudaEventRecord(g->ev0, g->stream));
   PF_TRY(pack_in(g, b, mem, g->bb, 0));
   PF_TRY(pack_in(g, x, mem, g->xb, 0));
-  PF_TRY(solve_dev(g, op, g->bb, g->xb, o, &rep));
+  if (cg) {
+    NvtxRange r2("CG solve");
+    PF_TRY(solve_cg(g, op, g->bb, g->xb, o, &rep));
+  } else {
+    PF_TRY(solve_dev(g, op, g->bb, g->xb, o, &rep));
+  }
   PF_TRY(unpack_out(g, g->xb, 1, x, mem));
   PF_CK(cudaEventRecord(g->ev1, g->stream));
   PF_CK(cudaEventSynchronize(g->ev1));
@@ -831,8 +878,21 @@ pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int me
   if (rep.status != PF_OK)
     return fail((pf_status)rep.status, rep.status == PF_E_NOCONV ? "linear solve did not converge"
                                        : rep.status == PF_E_TIMEOUT ? "a device wait timed out"
-                                                                    : "BiCGSTAB breakdown");
+                                       : cg ? "conjugate gradients breakdown (operator not positive definite)"
+                                            : "BiCGSTAB breakdown");
   return PF_OK;
+}
+
+pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int mem, const pf_solve_opts* opts,
+                          pf_report* report) {
+  NvtxRange range("pf_linear_solve");
+  return linear_solve_entry(g, op, b, x, mem, opts, report, false);
+}
+
+pf_status pf_linear_solve_cg(pf_grid* g, int op, const double* b, double* x, int mem, const pf_solve_opts* opts,
+                             pf_report* report) {
+  NvtxRange range("pf_linear_solve_cg");
+  return linear_solve_entry(g, op, b, x, mem, opts, report, true);
 }
 
 pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res) {
