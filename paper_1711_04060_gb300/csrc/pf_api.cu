@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/pf_gb300.h"
+#include "pf_cg.cuh"
 #include "pf_grid.cuh"
 
 using pf::BicgState;

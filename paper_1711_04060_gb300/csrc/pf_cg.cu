@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include "pf_gb300.h"
+#include "pf_cg.cuh"
 #include "pf_stencil.cuh"
 
 namespace pf {

@@ -142,25 +142,6 @@ cudaError_t launch_phase_ca(const Maps<SlotsCA<UNI>::NH, SlotsCA<UNI>::NC>& m, c
                             T* p_out, T* v_out, double* part, BicgState* st, int prime, const Launch& L);
 cudaError_t launch_add_f32(double* x, const float* d, long n, cudaStream_t s);
 
-// ---- conjugate gradients for the symmetric systems (Section 3), FP64 ----
-// The operator as the BiCGSTAB kernels see it: Jacobi scalings (0 on identity rows), the diagonal
-// (diag, or the constant diagc when diag is null) and the east/north/up faces (or the constant wc).
-struct CgOperator {
-  const double* dinv;
-  const double* diag;
-  const double *wE, *wN, *wU;
-  double wc, diagc;
-};
-// r = b - A x, u = 0 (u may be null), and the state's norms, rho = <r, M^-1 r>_w and stop test
-cudaError_t launch_cg_start(const CgOperator& a, const Geom& g, const double* b, const double* x, double* r,
-                            double* u, double* part, BicgState* st, cudaStream_t s);
-// un = r + beta uo, q = A M^-1 un, alpha
-cudaError_t launch_cg_direction(const CgOperator& a, const Geom& g, const double* r, const double* uo, double* un,
-                                double* q, double* part, BicgState* st, cudaStream_t s);
-// x += alpha M^-1 un, r -= alpha q, stop test, beta
-cudaError_t launch_cg_update(const CgOperator& a, const Geom& g, const double* un, const double* q, double* x,
-                             double* r, double* part, BicgState* st, cudaStream_t s);
-
 // ---- nonlinear step (Eq. 1, Eq. 11-13, Table 4) ----
 // ulast: per-node ln Gamma of the previous call, read when warm != 0 (Newton start) and rewritten
 cudaError_t launch_fermi(const double* phi0, const uint8_t* solvent, const double* ffix, const SpeciesParams& sp,
