@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accel", action="store_true", help="skip the Anderson-accelerated comparison solve")
+    ap.add_argument("--no-cg", action="store_true", help="skip the conjugate-gradient comparison solves")
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--accel-depth", type=int, default=0, help="Anderson depth of the timed solves (0: relaxation)")
     ap.add_argument("--serve-requests", type=int, default=16, help="requests of the serving sample (0: skip)")
@@ -367,6 +368,44 @@ def batch_sample(api, args, torch, dev):
 
 
 # ------------------------------------------------------------------ GPU arm
+def cg_sample(api, grid, prob, torch, dev, lin_tol):
+    """Conjugate gradients (pf_linear_solve_cg) against BiCGSTAB, both FP64, on the bench grid's PF1 and
+    variable-dielectric Poisson systems with seeded right-hand sides, from x = 0 to the bench's linear
+    tolerance.  GBps: algorithmic bytes of the CG iterations (PF1 12, Poisson 15 FP64 words per node)
+    over the device time of the two CG kernels."""
+    from paper_1711_04060_gb300 import workloads as W
+    g = prob.grid
+    out = {}
+    for name, op, words in (("pf1", api.PF_OP_PF1, 12), ("poisson", api.PF_OP_POISSON, 15)):
+        b = W.uniform(W.substream(2024, 1 + op), g.n, -1.0, 1.0).reshape(g.shape_zyx)
+        b[0] = b[-1] = 0.0
+        b = b.ravel()
+        if op == api.PF_OP_PF1:
+            b = np.where(prob.solvent == 1, b, 0.0)
+        bd = torch.from_numpy(b).to(dev)
+        res, xs = {}, {}
+        for method in ("cg", "bicgstab"):
+            x = torch.zeros(g.n, dtype=torch.float64, device=dev)
+            grid.profile(True)
+            rep = grid.linear_solve(op, bd, x, api.solve_opts(tol=lin_tol, max_iter=100000), allow=(3, 4),
+                                    method=method)
+            prof = grid.profile_get()
+            grid.profile(False)
+            r = {"iterations": rep["iterations"], "ms": round(rep["time_ms"], 3), "status": rep["status"],
+                 "residual": rep["residual"]}
+            if method == "cg":
+                kms = prof.get("cg_direction", (0, 0.0))[1] + prof.get("cg_update", (0, 0.0))[1]
+                if kms > 0:
+                    r["GBps"] = round(rep["iterations"] * words * 8 * g.n / (kms / 1e3) / 1e9, 1)
+                    r["kernel_ms"] = round(kms, 3)
+            res[method] = r
+            xs[method] = x
+        res["x_rel_diff"] = float((xs["cg"] - xs["bicgstab"]).abs().max() / xs["bicgstab"].abs().max())
+        res["matvecs_cg_over_bicgstab"] = round(res["cg"]["iterations"] / max(1, 2 * res["bicgstab"]["iterations"]), 3)
+        out[name] = res
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -526,6 +565,13 @@ def run_ours(args):
         d2h = sum(v.nbytes for v in hout.values())
         line["e2e"] = {"value": whole_job_rate(max(1, args.steps), world, el), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)}
+
+    # conjugate gradients for the symmetric systems against BiCGSTAB (FP64 linear solves on this grid)
+    if not args.no_cg and world == 1:
+        try:
+            line["cg_vs_bicgstab_fp64"] = cg_sample(api, grid, prob, torch, dev, args.lin_tol)
+        except Exception as e:  # reported in the line; the other legs stand
+            line["cg_vs_bicgstab_fp64"] = {"error": f"{type(e).__name__}: {e}"}
     grid.close()
 
     # batched: many uneven problems in shared launches, against the FP64 single-grid path
