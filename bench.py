@@ -275,11 +275,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+L2_BYTES = 129e6  # GB300 L2
+
+
 def config_of(args):
+    # the solve streams its operator and Krylov arrays (about 100 B per node in the mixed path) every iteration
+    ws = 100.0 * ((args.n + 7) // 8 * 8) * args.n * args.n
+    l2 = (f"inputs larger than L2 (working set {ws / 1e9:.1f} GB > 129 MB)" if ws > L2_BYTES
+          else f"working set {ws / 1e6:.0f} MB fits in L2: not an HBM measurement")
     return {"workload": f"pf_{args.n}_four_pores_NaCaCl", "grid": f"{args.n}^3", "h_A": 64.0 / (args.n - 1),
             "species": "Na+ 0.1 M, Ca2+ 1 mM, Cl- 0.102 M, water 55.5 M", "charges": 48,
             "precision": args.precision, "tol_outer": args.tol_outer, "lin_tol": args.lin_tol,
-            "omega": 0.3, "accel_depth": args.accel_depth, "inner_tol": args.inner_tol, "l2": "inputs larger than L2 (working set > 1 GB)",
+            "omega": 0.3, "accel_depth": args.accel_depth, "inner_tol": args.inner_tol, "l2": l2,
             "parallelism": f"replicas x{args.gpus}"}
 
 
