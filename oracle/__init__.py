@@ -73,6 +73,7 @@ def load(path):
     L.pfo_pcg.argtypes = [_I, _I, _I, _PD, _PD, _PD, _I, _D, _I, _PI, _PD]
     L.pfo_weighted_asymmetry.restype = _D
     L.pfo_weighted_asymmetry.argtypes = [_I, _I, _I, _PD]
+    L.pfo_decompose.argtypes = [_I, _I, _I, _D, _PD, _PU8, _I, _PD, _D, _D, _D, _PD, _PD, _PI]
     L.pfo_spread_charges.argtypes = [_I, _I, _I, _D, _PD, _I, _PD, _D, _PD]
     L.pfo_pf_solve.argtypes = [_I, _I, _I, _D, _PD, _PD, _PU8, _I, _PD, _D, _D, _I, _PD, _PD, _PD,
                                _D, _D, _D, ctypes.POINTER(NlOpts), _PD, _PD, _PD, _PD, _PD, _PD,
@@ -204,6 +205,19 @@ def spread_charges(nx, ny, nz, h, origin, charges, lam_value):
     f = np.zeros(nx * ny * nz)
     st = lib().pfo_spread_charges(nx, ny, nz, h, _pd(org), len(ch) // 4, _pd(ch), lam_value, _pd(f))
     return st, f
+
+
+def decompose(nx, ny, nz, h, origin, solvent, charges, eps_m, eps_s, lam_value):
+    """G = phi* + phi^L at membrane nodes and the interface right-hand side (pfo_decompose)."""
+    sol = np.ascontiguousarray(solvent, dtype=np.uint8)
+    ch = _f64(charges).ravel()
+    org = _f64(origin)
+    N = nx * ny * nz
+    G, bif = np.zeros(N), np.zeros(N)
+    it = ctypes.c_int(0)
+    st = lib().pfo_decompose(nx, ny, nz, h, _pd(org), sol.ctypes.data_as(_PU8), len(ch) // 4, _pd(ch), eps_m,
+                             eps_s, lam_value, _pd(G), _pd(bif), ctypes.byref(it))
+    return {"status": st, "G": G, "bif": bif, "iters": it.value}
 
 
 def pf_solve(nx, ny, nz, h, origin, eps, solvent, charges, phi_lo_V, phi_hi_V, z, radius, bulk,

@@ -413,6 +413,169 @@ int pfo_spread_charges(int nx, int ny, int nz, double h, const double* origin, i
 /* ---- Table 2: the sequential PF nonlinear solver (initial PF2 solve, then PF1, PF2 and the
  * relaxation until the update is small; the charges are spread onto the grid, so no singular part
  * is split off) ----------------------------------------------------------------- */
+/* ---- potential decomposition (Eqs. 5-10) and the interface right-hand side (Eqs. 8, 16-18) ----
+ *
+ * In the biomolecular region Omega_m (the non-solvent nodes) the potential is split as
+ * phi = phi~ + G with G = phi* + phi^L:  phi* is the Coulomb potential of the point charges in a
+ * uniform dielectric eps_m (in scaled units lambda q / (4 pi eps_m |r - r_j|)), and phi^L is harmonic
+ * in Omega_m (Eq. 9) with G = 0 on the interface with the solvent, i.e. phi^L = -phi* there (Eq. 10
+ * read with the sign that keeps phi continuous), and with zero normal derivative of G on the x/y box
+ * sides (the zero-flux sides of Eq. 4).  phi~ then has no singular source, is continuous, and its flux
+ * jumps by eps_m dG/dn across the interface (Eq. 8, n from Omega_m to Omega_s).  With the interface at
+ * the midpoint of each face between a membrane and a solvent node, the SMIB rows (17)-(18) are the
+ * harmonic-face rows plus c0/h^2 on the membrane row and d0/h^2 on the solvent row, with
+ * c0 = -eps_m h J / (eps_m + eps_s), d0 = -eps_s h J / (eps_m + eps_s), J = eps_m dG/dn at the midpoint. */
+static void coulomb(int nq, const double* ch, double coef, const double r[3], double* phi, double grad[3]) {
+  double p = 0.0, g[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < nq; ++j) {
+    const double d[3] = {r[0] - ch[4 * j], r[1] - ch[4 * j + 1], r[2] - ch[4 * j + 2]};
+    const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double inv = 1.0 / sqrt(d2);
+    const double qj = ch[4 * j + 3];
+    p += qj * inv;
+    for (int a = 0; a < 3; ++a) g[a] -= qj * d[a] * inv * inv * inv;
+  }
+  if (phi) *phi = coef * p;
+  if (grad)
+    for (int a = 0; a < 3; ++a) grad[a] = coef * g[a];
+}
+
+int pfo_decompose(int nx, int ny, int nz, double h, const double* origin, const unsigned char* solvent,
+                  int nq, const double* charges, double eps_m, double eps_s, double lambda, double* G,
+                  double* bif, int* lin_iters) {
+  if (nx < 3 || ny < 3 || nz < 3 || h <= 0.0 || eps_m <= 0.0 || eps_s <= 0.0 || nq < 0) return PFO_E_INVAL;
+  const long N = (long)nx * ny * nz;
+  const int n3[3] = {nx, ny, nz};
+  const long st3[3] = {1, nx, (long)nx * ny};
+  const double coef = lambda / (4.0 * M_PI * eps_m);
+  /* charges strictly inside the box and off the nodes (G is evaluated at nodes) */
+  for (int j = 0; j < nq; ++j)
+    for (int a = 0; a < 3; ++a) {
+      const double g = (charges[4 * j + a] - origin[a]) / h;
+      if (!(g > 0.0 && g < n3[a] - 1)) return PFO_E_INVAL;
+    }
+  for (long c = 0; c < N; ++c) {
+    const int i = (int)(c % nx), jj = (int)((c / nx) % ny);
+    const double r[3] = {origin[0] + h * i, origin[1] + h * jj, origin[2] + h * (double)(c / ((long)nx * ny))};
+    for (int j = 0; j < nq; ++j) {
+      const double d2 = (r[0] - charges[4 * j]) * (r[0] - charges[4 * j]) +
+                        (r[1] - charges[4 * j + 1]) * (r[1] - charges[4 * j + 1]) +
+                        (r[2] - charges[4 * j + 2]) * (r[2] - charges[4 * j + 2]);
+      if (d2 < 1e-12 * h * h) return PFO_E_INVAL;
+    }
+    /* a side node and its mirror partner must be of the same kind (no interface across a mirror) */
+    if ((i == 0 && solvent[c] != solvent[c + 1]) || (i == nx - 1 && solvent[c] != solvent[c - 1]) ||
+        (jj == 0 && solvent[c] != solvent[c + nx]) || (jj == ny - 1 && solvent[c] != solvent[c - nx]))
+      return PFO_E_INVAL;
+  }
+  double* A = calloc((size_t)7 * N, sizeof(double));
+  double* b = calloc(N, sizeof(double));
+  double* phiL = calloc(N, sizeof(double));
+  int status = PFO_OK;
+  if (!A || !b || !phiL) { status = PFO_E_INVAL; goto out; }
+
+  /* phi^L: -Lap_h phi^L = 0 at membrane nodes off the Dirichlet planes, Shortley-Weller differences to
+   * the interface midpoints (distance h/2, value -phi*), zero normal derivative of G on the x/y sides */
+  for (long c = 0; c < N; ++c) {
+    const long k = c / ((long)nx * ny);
+    const int idx[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)k};
+    const double r[3] = {origin[0] + h * idx[0], origin[1] + h * idx[1], origin[2] + h * idx[2]};
+    if (solvent[c] || k == 0 || k == nz - 1) {
+      A[c] = 1.0;
+      if (!solvent[c]) { double p; coulomb(nq, charges, coef, r, &p, NULL); b[c] = -p; } /* G = 0 on the planes */
+      continue;
+    }
+    for (int a = 0; a < 3; ++a) {
+      /* diagonal slots of the neighbour below / above along axis a: west, south, down / east, north, up */
+      const int slot_of[2] = {a == 0 ? 2 : a == 1 ? 3 : 5, a == 0 ? 1 : a == 1 ? 4 : 6};
+      if (a < 2 && (idx[a] == 0 || idx[a] == n3[a] - 1)) {
+        /* box side: dG/dn = 0, so the ghost value is partner + 2h dphi^L/dn = partner - 2h dphi_star/dn */
+        const int low = idx[a] == 0;
+        double gr[3];
+        coulomb(nq, charges, coef, r, NULL, gr);
+        const double nout = low ? -1.0 : 1.0;
+        A[c] += 2.0 / (h * h);
+        A[slot_of[low ? 1 : 0] * N + c] -= 2.0 / (h * h);
+        b[c] += -2.0 * nout * gr[a] / h;
+        continue;
+      }
+      double hs[2], val[2];
+      int bnd[2];
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        const long nb = c + (sgn ? st3[a] : -st3[a]);
+        if (solvent[nb]) {
+          double rx[3] = {r[0], r[1], r[2]};
+          rx[a] += (sgn ? 0.5 : -0.5) * h;
+          double p;
+          coulomb(nq, charges, coef, rx, &p, NULL);
+          hs[sgn] = 0.5 * h;
+          val[sgn] = -p;
+          bnd[sgn] = 1;
+        } else {
+          hs[sgn] = h;
+          val[sgn] = 0.0;
+          bnd[sgn] = 0;
+        }
+      }
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        const double cf = 2.0 / ((hs[0] + hs[1]) * hs[sgn]);
+        A[c] += cf;
+        if (bnd[sgn]) b[c] += cf * val[sgn];
+        else A[slot_of[sgn] * N + c] -= cf;
+      }
+    }
+  }
+  {
+    int its = 0;
+    double res = 0.0;
+    status = pfo_bicgstab(nx, ny, nz, A, b, phiL, 20000, 1e-14, 0, &its, &res);
+    if (lin_iters) *lin_iters = its;
+    if (status) goto out;
+  }
+  for (long c = 0; c < N; ++c) {
+    if (solvent[c]) { G[c] = 0.0; continue; }
+    const long k = c / ((long)nx * ny);
+    const double r[3] = {origin[0] + h * (double)(c % nx), origin[1] + h * (double)((c / nx) % ny),
+                         origin[2] + h * (double)k};
+    double p;
+    coulomb(nq, charges, coef, r, &p, NULL);
+    G[c] = p + phiL[c];
+  }
+
+  /* the interface right-hand side: every face between a membrane and a solvent node */
+  memset(bif, 0, sizeof(double) * N);
+  for (long c = 0; c < N; ++c) {
+    const int idx[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long)nx * ny))};
+    for (int a = 0; a < 3; ++a) {
+      if (idx[a] == n3[a] - 1) continue;
+      const long nb = c + st3[a];
+      if (solvent[c] == solvent[nb]) continue;
+      const long cm = solvent[c] ? nb : c, cs = solvent[c] ? c : nb;
+      const double nsgn = solvent[c] ? -1.0 : 1.0; /* n from the membrane node to the solvent node */
+      double xi[3] = {origin[0] + h * idx[0], origin[1] + h * idx[1], origin[2] + h * idx[2]};
+      xi[a] += 0.5 * h;
+      double p, gr[3];
+      coulomb(nq, charges, coef, xi, &p, gr);
+      const double dstar = nsgn * gr[a];
+      /* d phi^L / dn at the midpoint from -phi* there and phi^L at the membrane node (h/2 inside) and at
+       * the next node inside (3h/2), when that one is a membrane node too */
+      const long cm2 = cm - (long)nsgn * st3[a];
+      const int im2 = (int)((a == 0 ? cm2 % nx : a == 1 ? (cm2 / nx) % ny : cm2 / ((long)nx * ny)));
+      const int im = (int)((a == 0 ? cm % nx : a == 1 ? (cm / nx) % ny : cm / ((long)nx * ny)));
+      const int inside = (nsgn > 0 ? im > 0 : im < n3[a] - 1) && (im2 >= 0) && !solvent[cm2];
+      const double f0 = -p, f1 = phiL[cm];
+      const double dL = inside ? (8.0 * f0 - 9.0 * f1 + phiL[cm2]) / (3.0 * h) : (f0 - f1) / (0.5 * h);
+      const double J = eps_m * (dstar + dL);
+      const long km = cm / ((long)nx * ny), ks = cs / ((long)nx * ny);
+      if (km > 0 && km < nz - 1) bif[cm] += -eps_m * J / ((eps_m + eps_s) * h);
+      if (ks > 0 && ks < nz - 1) bif[cs] += -eps_s * J / ((eps_m + eps_s) * h);
+    }
+  }
+out:
+  free(A); free(b); free(phiL);
+  return status;
+}
+
 int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
                  const double* eps, const unsigned char* solvent,
                  int nq, const double* charges, double phi_lo_V, double phi_hi_V,

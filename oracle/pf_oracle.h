@@ -94,6 +94,20 @@ double pfo_weighted_asymmetry(int nx, int ny, int nz, const double* A);
 int pfo_spread_charges(int nx, int ny, int nz, double h, const double* origin, int nq,
                        const double* charges, double lambda, double* f);
 
+/* ---- potential decomposition (Eqs. 5-10) and interface right-hand side (Eqs. 8, 16-18) ----
+ * For point charges (x, y, z in A, q in e) strictly inside Omega_m (the non-solvent nodes, dielectric
+ * eps_m; solvent eps_s), writes G = phi* + phi^L at the membrane nodes (0 at solvent nodes; phi* the
+ * Coulomb potential lambda q / (4 pi eps_m r), phi^L harmonic in Omega_m with G = 0 on the interface and
+ * zero normal derivative of G on the x/y sides) and bif, the SMIB jump terms c0/h^2, d0/h^2 on the
+ * membrane and solvent rows next to each interface face (midpoint interface).  The potential is then
+ * phi~ + G in Omega_m and phi~ in Omega_s, where phi~ solves the harmonic-face operator with bif added
+ * to its right-hand side and no spread charges.  PFO_E_INVAL when a charge lies outside the box or on a
+ * node, or when a side node and its mirror partner differ in kind.  lin_iters (may be NULL) receives
+ * the BiCGSTAB iterations of the phi^L solve. */
+int pfo_decompose(int nx, int ny, int nz, double h, const double* origin, const unsigned char* solvent,
+                  int nq, const double* charges, double eps_m, double eps_s, double lambda, double* G,
+                  double* bif, int* lin_iters);
+
 /* ---- nonlinear PF solve (Table 2; the GPU variant of Table 4 computes the same) ---- */
 typedef struct {
   double omega;      /* relaxation weight omega_PF of Table 2 */

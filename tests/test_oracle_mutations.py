@@ -29,6 +29,12 @@ MUTATIONS = [
      "s += side_weight(nx, ny, c) * a[c] * b[c];", "s += a[c] * b[c];"),
     ("conjugate gradients with the preconditioner left out of the search direction",
      "p[c] = z[c] + beta * p[c];", "p[c] = r[c] + beta * p[c];"),
+    ("phi^L = +phi* on the interface (Eq. 10 as printed, phi discontinuous)",
+     "val[sgn] = -p;", "val[sgn] = p;"),
+    ("jump of Eq. 8 with the opposite sign (the sign printed in Eq. 16)",
+     "const double J = eps_m * (dstar + dL);", "const double J = -eps_m * (dstar + dL);"),
+    ("phi^L left out of the interface jump (Eq. 16 without it)",
+     "const double J = eps_m * (dstar + dL);", "const double J = eps_m * dstar;"),
 ]
 
 # the pins, fastest first, with the arguments of one parametrisation each
@@ -45,6 +51,7 @@ PINS = [
     (P.test_kappa_makes_pf2_a_newton_step, {}),
     (P.test_pf_reduces_to_pb, {}),
     (P.test_pcg_iterates_minimise_the_energy_norm, {}),
+    (P.test_decomposition_converges_to_the_slab_solution, {}),
 ]
 
 

@@ -586,3 +586,135 @@ def test_pf_solve_with_cg_same_fixed_point(orc, solver):
     for i in range(len(prob.species)):
         np.testing.assert_allclose(out["C_M"][i], ref["C_M"][i], rtol=1e-9, atol=0)
     assert abs(out["report"]["outer_iters"] - ref["report"]["outer_iters"]) <= 1
+
+
+# ---------------------------------------------------------------- a point charge in a dielectric slab (closed form)
+# Box [-8, 8]^3 A with mirror sides and phi = 0 on the z planes, membrane |z| < 2.5 A (eps 2) in water (eps 80),
+# one charge off the nodes.  The interface z = +-2.5 lies at face midpoints for h = 1 and h = 1/3.
+SLAB = dict(L=8.0, Z=8.0, a=2.5, eps_m=2.0, eps_s=80.0)
+SLAB_Q, SLAB_R0 = 1.0, (0.37, -0.21, 0.29)
+SLAB_SOLVENT_PROBES = [(0, 0, 5), (2, -1, 4), (-3, 2, -5), (1, 1, -4)]
+SLAB_MEMBRANE_PROBES = [(3, 2, 2), (-4, 0, -2), (0, 3, 1)]
+_SLAB_REF = {}
+
+
+def _slab_reference(lam):
+    from tests.slab_reference import slab_potential
+    if lam not in _SLAB_REF:
+        _SLAB_REF[lam] = slab_potential(SLAB_SOLVENT_PROBES + SLAB_MEMBRANE_PROBES, SLAB_Q, SLAB_R0, SLAB["L"],
+                                        SLAB["Z"], SLAB["a"], SLAB["eps_m"], SLAB["eps_s"], lam, 0.7)
+    return _SLAB_REF[lam]
+
+
+def _slab_grid(h):
+    n = int(round(2 * SLAB["L"] / h)) + 1
+    z = -SLAB["Z"] + h * np.arange(n)
+    memb = np.broadcast_to((np.abs(z) < SLAB["a"])[:, None, None], (n, n, n)).ravel()
+    eps = np.where(memb, SLAB["eps_m"], SLAB["eps_s"])
+    return n, (~memb).astype(np.uint8), eps
+
+
+def _at_probes(phi, n, h):
+    L = SLAB["L"]
+    out = []
+    for (x, y, z) in SLAB_SOLVENT_PROBES + SLAB_MEMBRANE_PROBES:
+        i, j, k = (int(round((c + L) / h)) for c in (x, y, z))
+        out.append(phi[i + n * (j + n * k)])
+    return np.array(out)
+
+
+def _slab_solve(orc, h, decomposed):
+    """phi at the probes: charges spread trilinearly (Eq. 3 on the grid), or the decomposition of Eqs. 5-10 with
+    the interface right-hand side of Eq. 8 through the SMIB rows (17)-(18)."""
+    n, sol, eps = _slab_grid(h)
+    org = (-SLAB["L"], -SLAB["L"], -SLAB["Z"])
+    ch = np.array([[*SLAB_R0, SLAB_Q]])
+    A = orc.assemble_eps(n, n, n, h, eps)
+    if decomposed:
+        d = orc.decompose(n, n, n, h, org, sol, ch, SLAB["eps_m"], SLAB["eps_s"], orc.lam())
+        assert d["status"] == 0
+        b, G = d["bif"], d["G"]
+    else:
+        st, b = orc.spread_charges(n, n, n, h, org, ch, orc.lam())
+        assert st == 0
+        G = 0.0
+    b = b.reshape(n, n, n).copy()
+    b[0] = b[-1] = 0.0
+    r = orc.bicgstab(n, n, n, A, b.ravel(), tol=1e-12, max_it=20000)
+    assert r["status"] == 0
+    return _at_probes(r["x"] + G, n, h)
+
+
+def test_slab_reference_carries_the_point_charge(orc):
+    """The series solution has the charge's singularity: phi(r0 + d e_z) - phi(r0 + 2d e_z) tends to
+    lam q / (4 pi eps_m) (1/d - 1/(2d)), the free-space Coulomb difference, as d shrinks."""
+    from tests.slab_reference import slab_potential
+    lam = orc.lam()
+    x0, y0, z0 = SLAB_R0
+    devs = []
+    for d in (0.4, 0.2):
+        v = slab_potential([(x0, y0, z0 + d), (x0, y0, z0 + 2 * d)], SLAB_Q, SLAB_R0, SLAB["L"], SLAB["Z"],
+                           SLAB["a"], SLAB["eps_m"], SLAB["eps_s"], lam, d)
+        coulomb = lam * SLAB_Q / (4 * math.pi * SLAB["eps_m"]) * (1 / d - 1 / (2 * d))
+        devs.append(abs((v[0] - v[1]) / coulomb - 1))
+    assert devs[1] < 0.005 and devs[1] < devs[0] / 3
+
+
+def test_slab_reference_satisfies_its_equations(orc):
+    """Away from the charge: Laplace in each layer, eps dphi/dz continuous at the interface, zero normal
+    derivative on a side, zero on a Dirichlet plane."""
+    from tests.slab_reference import slab_potential
+    lam, g = orc.lam(), SLAB
+    f = lambda pts: slab_potential(pts, SLAB_Q, SLAB_R0, g["L"], g["Z"], g["a"], g["eps_m"], g["eps_s"], lam, 0.5)
+    d = 0.02
+    for c in ((1.0, 2.0, 4.5), (-2.0, 1.0, -1.5)):
+        pts = [c] + [tuple(c[i] + s * d * (i == ax) for i in range(3)) for ax in range(3) for s in (1, -1)]
+        v = f(pts)
+        second = [(v[1 + 2 * ax] + v[2 + 2 * ax] - 2 * v[0]) / d ** 2 for ax in range(3)]
+        assert abs(sum(second)) < 1e-3 * sum(abs(s) for s in second)
+    za = g["a"]
+    v = f([(1.0, 2.0, za - 2 * d), (1.0, 2.0, za - d), (1.0, 2.0, za + d), (1.0, 2.0, za + 2 * d),
+           (g["L"], 1.0, 4.0), (g["L"] - d, 1.0, 4.0), (0.5, 0.5, g["Z"])])
+    flux_in = g["eps_m"] * ((v[1] - v[0]) / d)  # one-sided differences: first order is enough here
+    flux_out = g["eps_s"] * ((v[3] - v[2]) / d)
+    assert abs(flux_in - flux_out) < 0.02 * abs(flux_in)
+    assert abs(v[4] - v[5]) < 1e-3 * abs(v[4])       # dphi/dx = 0 at x = L
+    assert abs(v[6]) < 1e-10
+
+
+def test_spread_charge_converges_to_the_slab_solution(orc):
+    """The 3D operator with trilinear charge spreading converges to the closed form at second order in the
+    solvent (h = 1 -> 1/3), the assembly, the spreading and the Dirichlet/mirror treatment together."""
+    ref = _slab_reference(orc.lam())
+    ns = len(SLAB_SOLVENT_PROBES)
+    e1 = np.abs(_slab_solve(orc, 1.0, False) - ref) / np.abs(ref)
+    e3 = np.abs(_slab_solve(orc, 1.0 / 3.0, False) - ref) / np.abs(ref)
+    assert e3[:ns].max() < 2.5e-3
+    assert e1[:ns].mean() > 5 * e3[:ns].mean()
+
+
+def test_decomposition_converges_to_the_slab_solution(orc):
+    """The potential decomposition (Eqs. 5-10) with the interface right-hand side (Eqs. 8, 16-18) converges to the
+    closed form at second order, and near the charge it is far more accurate than spreading the charge onto
+    the grid, which is what the decomposition is for."""
+    ref = _slab_reference(orc.lam())
+    ns = len(SLAB_SOLVENT_PROBES)
+    e1 = np.abs(_slab_solve(orc, 1.0, True) - ref) / np.abs(ref)
+    e3 = np.abs(_slab_solve(orc, 1.0 / 3.0, True) - ref) / np.abs(ref)
+    assert e3.max() < 2.5e-3
+    assert e1.mean() > 5 * e3.mean()
+    direct = np.abs(_slab_solve(orc, 1.0 / 3.0, False) - ref) / np.abs(ref)
+    # the two membrane probes nearest the charge
+    assert np.all(e3[ns + 1:] < direct[ns + 1:] / 10)
+
+
+def test_decomposition_rejects_bad_input(orc):
+    n, sol, _ = _slab_grid(1.0)
+    org = (-8.0, -8.0, -8.0)
+    for ch in ([[0.0, 0.0, 0.0, 1.0]],          # on a node
+               [[0.3, 0.2, 9.5, 1.0]]):         # outside the box
+        assert orc.decompose(n, n, n, 1.0, org, sol, np.array(ch), 2.0, 80.0, orc.lam())["status"] == 1
+    s = sol.reshape(n, n, n).copy()
+    s[3:6, 4, 0] = 0                           # membrane on a side whose mirror partner is solvent
+    assert orc.decompose(n, n, n, 1.0, org, s.ravel(), np.array([[0.3, 0.2, 0.1, 1.0]]), 2.0, 80.0,
+                         orc.lam())["status"] == 1
