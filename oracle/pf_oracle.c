@@ -608,12 +608,32 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
   double* C = calloc((size_t)ns * N, sizeof(double));
   double* Sv = calloc(N, sizeof(double));
   double* Gv = calloc(N, sizeof(double));
+  double* Gdec = NULL; /* G = phi* + phi^L of the decomposition (charge_mode 1) */
   if (!A || !ffix || !b || !phi0 || !phi || !psi || !rho || !kap || !sig || !C || !Sv || !Gv) {
     st = PFO_E_INVAL;
     goto out;
   }
-  st = pfo_spread_charges(nx, ny, nz, h, origin, nq, charges, lam, ffix);
-  if (st) goto out;
+  if (opts->charge_mode == 1) {
+    /* Eqs. 5-10: G = phi* + phi^L in Omega_m, the jump terms of Eq. 8 in place of the spread charges */
+    double eps_m = -1.0;
+    for (long c = 0; c < N; ++c)
+      if (!solvent[c]) {
+        if (eps_m < 0.0) eps_m = eps[c];
+        else if (eps[c] != eps_m) { st = PFO_E_INVAL; goto out; }
+      }
+    Gdec = calloc(N, sizeof(double));
+    if (!Gdec) { st = PFO_E_INVAL; goto out; }
+    if (eps_m > 0.0) {
+      st = pfo_decompose(nx, ny, nz, h, origin, solvent, nq, charges, eps_m, eps_s, lam, Gdec, ffix, NULL);
+      if (st) goto out;
+    }
+  } else if (opts->charge_mode == 0) {
+    st = pfo_spread_charges(nx, ny, nz, h, origin, nq, charges, lam, ffix);
+    if (st) goto out;
+  } else {
+    st = PFO_E_INVAL;
+    goto out;
+  }
   const double lo_hat = phi_lo_V / Tv, hi_hat = phi_hi_V / Tv;
   const long plane = (long)nx * ny;
 #define PFO_SET_DIRICHLET(vec)                                        \
@@ -689,8 +709,9 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
   {
     const double m = pfo_molar_to_per_A3();
     for (long c = 0; c < N; ++c) {
-      if (phi_V) phi_V[c] = phi0[c] * Tv;
-      if (phi_hat_out) phi_hat_out[c] = phi0[c];
+      const double full = phi0[c] + (Gdec ? Gdec[c] : 0.0); /* phi = phi~ + G in Omega_m (Eq. 5) */
+      if (phi_V) phi_V[c] = full * Tv;
+      if (phi_hat_out) phi_hat_out[c] = full;
       if (S) S[c] = Sv[c];
       if (Gamma) Gamma[c] = Gv[c];
       if (Psi_out) Psi_out[c] = psi[c];
@@ -701,6 +722,6 @@ out:
   R.status = st;
   if (rep) *rep = R;
   free(A); free(ffix); free(b); free(phi0); free(phi); free(psi); free(rho); free(kap);
-  free(sig); free(C); free(Sv); free(Gv);
+  free(sig); free(C); free(Sv); free(Gv); free(Gdec);
   return st;
 }

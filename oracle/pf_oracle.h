@@ -119,6 +119,10 @@ typedef struct {
   int solver;        /* 0: BiCGSTAB (Table 3) for every linear system; 1: conjugate gradients
                         (pfo_pcg) for PF1; 2: conjugate gradients for PF1 and PF2 (symmetric in the
                         zero-jump reading of Eqs. 15-18) */
+  int charge_mode;   /* 0: fixed charges spread trilinearly onto the grid (Eq. 3 on the grid); 1: the
+                        potential decomposition of Eqs. 5-10 (pfo_decompose): the interface right-hand
+                        side replaces the spread charges and phi = phi~ + G is returned in Omega_m.  Mode 1
+                        needs one dielectric value on all non-solvent nodes and charges inside Omega_m. */
 } pfo_nl_opts;
 
 typedef struct {

@@ -718,3 +718,61 @@ def test_decomposition_rejects_bad_input(orc):
     s[3:6, 4, 0] = 0                           # membrane on a side whose mirror partner is solvent
     assert orc.decompose(n, n, n, 1.0, org, s.ravel(), np.array([[0.3, 0.2, 0.1, 1.0]]), 2.0, 80.0,
                          orc.lam())["status"] == 1
+
+
+# ---------------------------------------------------------------- the decomposition inside the nonlinear iteration
+_DEC_CHARGES = np.array([[0.37, -0.21, 0.29, 1.0], [-2.13, 1.41, -1.07, -0.5]])
+_DEC_PROBES = [(0, 0, 5), (2, -1, 4), (-3, 2, -5), (1, 1, -4), (4, -4, 3)]
+
+
+def _slab_channel(h):
+    """The slab of the closed-form pins (membrane |z| < 2.5 A, eps 2) in 0.1 M NaCl at 50 mV."""
+    n = int(round(16.0 / h)) + 1
+    g = W.Grid(n, n, n, h, (-8.0, -8.0, -8.0))
+    memb = np.abs(g.coords()[2]) < 2.5
+    return g, (~memb).astype(np.uint8).ravel(), np.where(memb, 2.0, 78.5).ravel()
+
+
+def _pf_slab(orc, h, mode, charges=_DEC_CHARGES, **kw):
+    g, sol, eps = _slab_channel(h)
+    out = orc.pf_solve(g.nx, g.ny, g.nz, g.h, g.origin, eps, sol, charges, 0.0, 0.05, [1, -1, 0],
+                       [0.95, 1.81, 1.4], [0.1, 0.1, 55.5], 78.5, 1.2, charge_mode=mode, **kw)
+    assert out["status"] == 0
+    return g, sol, eps, out
+
+
+def test_pf_decomposition_without_charges_is_the_plain_solve(orc):
+    _, _, _, a = _pf_slab(orc, 1.0, 0, charges=np.zeros((0, 4)), tol_outer=1e-10, lin_tol=1e-12)
+    _, _, _, b = _pf_slab(orc, 1.0, 1, charges=np.zeros((0, 4)), tol_outer=1e-10, lin_tol=1e-12)
+    np.testing.assert_array_equal(a["phi_hat"], b["phi_hat"])
+
+
+def test_pf_decomposition_fixed_point_satisfies_equations(orc):
+    """With the decomposition, phi~ = phi - G solves PF2 of Eq. (13) with the jump terms of Eq. (8) as its only
+    fixed-charge source: -div(eps grad phi~) = -s eps_s Psi + b_IF."""
+    g, sol, eps, out = _pf_slab(orc, 1.0, 1, tol_outer=1e-13, lin_tol=1e-14)
+    d = orc.decompose(g.nx, g.ny, g.nz, g.h, g.origin, sol, _DEC_CHARGES, 2.0, 78.5, orc.lam())
+    phit = out["phi_hat"] - d["G"]
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, eps)
+    res = orc.dia_apply(g.nx, g.ny, g.nz, A, phit) + sol * 78.5 * out["Psi"] - d["bif"]
+    res = res.reshape(g.shape_zyx)[1:-1]
+    assert np.abs(res).max() < 1e-8 * np.abs(d["bif"]).max()
+    # in the solvent the returned potential is phi~ itself
+    assert np.all(d["G"][sol == 1] == 0.0)
+
+
+def test_pf_decomposition_agrees_with_spread_charges_as_h_shrinks(orc):
+    """The two treatments of the fixed charges discretise the same PF problem: their potentials in the solvent
+    approach each other under refinement (h = 1 -> 1/3)."""
+    diffs = []
+    for h in (1.0, 1.0 / 3.0):
+        vals = []
+        for mode in (0, 1):
+            g, _, _, out = _pf_slab(orc, h, mode, tol_outer=1e-9, lin_tol=1e-11)
+            ph = out["phi_hat"]
+            vals.append(np.array([ph[int(round((x + 8) / h)) + g.nx * (int(round((y + 8) / h)) +
+                                                                      g.ny * int(round((z + 8) / h)))]
+                                  for x, y, z in _DEC_PROBES]))
+        diffs.append(np.abs(vals[0] - vals[1]))
+    assert diffs[1].max() < 2e-3
+    assert diffs[0].mean() > 5 * diffs[1].mean()
