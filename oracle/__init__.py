@@ -78,6 +78,11 @@ def load(path):
     L.pfo_pf_solve.argtypes = [_I, _I, _I, _D, _PD, _PD, _PU8, _I, _PD, _D, _D, _I, _PD, _PD, _PD,
                                _D, _D, _D, ctypes.POINTER(NlOpts), _PD, _PD, _PD, _PD, _PD, _PD,
                                ctypes.POINTER(NlReport)]
+    L.pfo_pf_solve_fixed.argtypes = [_I, _I, _I, _D, _PD, _PD, _PU8, _I, _PD, _D, _D, _I, _PD, _PD, _PD,
+                                     _D, _D, _D, ctypes.POINTER(NlOpts), _PU8, _PD, _PD, _PD, _PD, _PD, _PD, _PD,
+                                     ctypes.POINTER(NlReport)]
+    L.pfo_site_potentials.argtypes = [_I, _PD, _PD, _PD, _PI, _D, _I, _PD, _D, _D, _PD]
+    L.pfo_site_steric.argtypes = [_I, _PD, _PI, _D, _D, _PD]
     return L
 
 
@@ -222,7 +227,7 @@ def decompose(nx, ny, nz, h, origin, solvent, charges, eps_m, eps_s, lam_value):
 
 def pf_solve(nx, ny, nz, h, origin, eps, solvent, charges, phi_lo_V, phi_hi_V, z, radius, bulk,
              eps_s, lc, T=298.15, omega=0.3, tol_outer=1e-10, lin_tol=1e-12, lin_norm=0, max_outer=500,
-             max_lin=20000, solver=0, charge_mode=0):
+             max_lin=20000, solver=0, charge_mode=0, fixed=None, fixed_phi_V=None):
     """Table 2 nonlinear PF solve; returns a dict of fields and the report."""
     N = nx * ny * nz
     ns = len(z)
@@ -235,10 +240,16 @@ def pf_solve(nx, ny, nz, h, origin, eps, solvent, charges, phi_lo_V, phi_hi_V, z
     out["C_M"] = np.zeros(ns * N)
     opts = NlOpts(omega, tol_outer, lin_tol, lin_norm, max_outer, max_lin, solver, charge_mode)
     rep = NlReport()
-    st = lib().pfo_pf_solve(nx, ny, nz, h, _pd(org), _pd(eps), sol.ctypes.data_as(_PU8), len(ch) // 4, _pd(ch),
-                            phi_lo_V, phi_hi_V, ns, _pd(z), _pd(radius), _pd(bulk), eps_s, lc, T,
-                            ctypes.byref(opts), _pd(out["phi_V"]), _pd(out["C_M"]), _pd(out["S"]),
-                            _pd(out["Gamma"]), _pd(out["Psi"]), _pd(out["phi_hat"]), ctypes.byref(rep))
+    outs = (_pd(out["phi_V"]), _pd(out["C_M"]), _pd(out["S"]), _pd(out["Gamma"]), _pd(out["Psi"]),
+            _pd(out["phi_hat"]), ctypes.byref(rep))
+    head = (nx, ny, nz, h, _pd(org), _pd(eps), sol.ctypes.data_as(_PU8), len(ch) // 4, _pd(ch), phi_lo_V, phi_hi_V,
+            ns, _pd(z), _pd(radius), _pd(bulk), eps_s, lc, T, ctypes.byref(opts))
+    if fixed is None:
+        st = lib().pfo_pf_solve(*head, *outs)
+    else:
+        fx = np.ascontiguousarray(fixed, dtype=np.uint8)
+        fv = _f64(fixed_phi_V)
+        st = lib().pfo_pf_solve_fixed(*head, fx.ctypes.data_as(_PU8), _pd(fv), *outs)
     out["C_M"] = out["C_M"].reshape(ns, N)
     out["status"] = st
     out["report"] = {f: getattr(rep, f) for f, _ in NlReport._fields_}
@@ -253,3 +264,24 @@ def pf_solve_problem(prob, **kw):
     c = [s.bulk_M for s in prob.species]
     return pf_solve(g.nx, g.ny, g.nz, g.h, g.origin, prob.eps, prob.solvent, prob.charges, prob.phi_lo_V,
                     prob.phi_hi_V, z, r, c, prob.eps_s, prob.lc_A, prob.T_K, **kw)
+
+
+def site_potentials(centers, radii, q_ion, occupied, eps_b, charges, eps_p, lam_value):
+    """Eq. (19) for every site; returns (status, phi_hat per site)."""
+    c = _f64(centers).ravel()
+    r, q = _f64(radii), _f64(q_ion)
+    occ = np.ascontiguousarray(occupied, dtype=np.int32)
+    ch = _f64(charges).ravel()
+    out = np.zeros(len(r))
+    st = lib().pfo_site_potentials(len(r), _pd(c), _pd(r), _pd(q), occ.ctypes.data_as(_PI), eps_b, len(ch) // 4,
+                                   _pd(ch), eps_p, lam_value, _pd(out))
+    return st, out
+
+
+def site_steric(ion_radii, occupied, v_sites, gammaB):
+    """Eq. (20); returns (status, S)."""
+    r = _f64(ion_radii)
+    occ = np.ascontiguousarray(occupied, dtype=np.int32)
+    S = ctypes.c_double(0.0)
+    st = lib().pfo_site_steric(len(r), _pd(r), occ.ctypes.data_as(_PI), v_sites, gammaB, ctypes.byref(S))
+    return st, S.value

@@ -576,13 +576,24 @@ out:
   return status;
 }
 
-int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
-                 const double* eps, const unsigned char* solvent,
-                 int nq, const double* charges, double phi_lo_V, double phi_hi_V,
-                 int ns, const double* z, const double* radius_A, const double* bulk_M,
-                 double eps_s, double lc, double T, const pfo_nl_opts* opts,
-                 double* phi_V, double* C_M, double* S, double* Gamma, double* Psi_out,
-                 double* phi_hat_out, pfo_nl_report* rep) {
+/* Rows of the fixed nodes (the filter region) become identity rows. */
+static void fix_rows(long N, const unsigned char* fixed, double* A) {
+  if (!fixed) return;
+  for (long c = 0; c < N; ++c)
+    if (fixed[c]) {
+      A[c] = 1.0;
+      for (int d = 1; d < 7; ++d) A[d * N + c] = 0.0;
+    }
+}
+
+static int pf_solve_impl(int nx, int ny, int nz, double h, const double* origin,
+                         const double* eps, const unsigned char* solvent,
+                         int nq, const double* charges, double phi_lo_V, double phi_hi_V,
+                         int ns, const double* z, const double* radius_A, const double* bulk_M,
+                         double eps_s, double lc, double T, const pfo_nl_opts* opts,
+                         double* phi_V, double* C_M, double* S, double* Gamma, double* Psi_out,
+                         double* phi_hat_out, pfo_nl_report* rep, const unsigned char* fixed,
+                         const double* fixed_phi_V) {
   const long N = (long)nx * ny * nz;
   const double Tv = pfo_thermal_voltage(T), lam = pfo_lambda(T);
   pfo_nl_report R = {PFO_OK, 0, 0, 0, 0.0};
@@ -637,10 +648,14 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
   const double lo_hat = phi_lo_V / Tv, hi_hat = phi_hi_V / Tv;
   const long plane = (long)nx * ny;
 #define PFO_SET_DIRICHLET(vec)                                        \
-  for (long c = 0; c < plane; ++c) { vec[c] = lo_hat; vec[N - plane + c] = hi_hat; }
+  for (long c = 0; c < plane; ++c) { vec[c] = lo_hat; vec[N - plane + c] = hi_hat; } \
+  if (fixed)                                                          \
+    for (long c = 0; c < N; ++c)                                      \
+      if (fixed[c]) vec[c] = fixed_phi_V[c] / Tv;
 
   /* initial potential: PF2 with rho' = Psi = 0, i.e. -div(eps grad phi0) = lambda rho_fix. */
   pfo_assemble_eps(nx, ny, nz, h, eps, NULL, A);
+  fix_rows(N, fixed, A);
   for (long c = 0; c < N; ++c) b[c] = ffix[c];
   PFO_SET_DIRICHLET(b);
   int its = 0;
@@ -655,7 +670,7 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
     for (long c = 0; c < N; ++c) {
       rho[c] = 0.0;
       kap[c] = 0.0;
-      if (!solvent[c]) continue;
+      if (!solvent[c] || (fixed && fixed[c])) continue;
       double Ci[64], s, g;
       st = pfo_fermi_point(ns, z, v, pr, cB, gB, phi0[c], Ci, &s, &g, NULL);
       if (st) goto out;
@@ -666,6 +681,7 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
     }
     /* PF1, Eq. (12) */
     pfo_assemble_pf1(nx, ny, nz, h, solvent, eps_s, lc, A);
+    fix_rows(N, fixed, A); /* Psi = 0 on the filter region, the boundary of the continuum solvent (Eq. 14) */
     for (long c = 0; c < N; ++c) b[c] = solvent[c] ? -lam * rho[c] : 0.0;
     for (long c = 0; c < plane; ++c) { b[c] = 0.0; b[N - plane + c] = 0.0; }
     st = solve_pf1(nx, ny, nz, A, b, psi, opts->max_lin, opts->lin_tol, opts->lin_norm, &its, &res);
@@ -675,6 +691,7 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
      * -div(eps_m grad phi) = lambda rho_fix in the membrane */
     for (long c = 0; c < N; ++c) sig[c] = solvent[c] ? kap[c] : 0.0;
     pfo_assemble_eps(nx, ny, nz, h, eps, sig, A);
+    fix_rows(N, fixed, A);
     for (long c = 0; c < N; ++c)
       b[c] = (solvent[c] ? (-eps_s * psi[c] + kap[c] * phi0[c]) : 0.0) + ffix[c];
     PFO_SET_DIRICHLET(b);
@@ -698,7 +715,12 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
 #undef PFO_SET_DIRICHLET
   /* concentrations, steric potential and void fraction at the final potential */
   for (long c = 0; c < N; ++c) {
-    if (!solvent[c]) { for (int i = 0; i < ns; ++i) C[(long)i * N + c] = 0.0; Sv[c] = 0.0; Gv[c] = 0.0; continue; }
+    if (!solvent[c] || (fixed && fixed[c])) {
+      for (int i = 0; i < ns; ++i) C[(long)i * N + c] = 0.0;
+      Sv[c] = 0.0;
+      Gv[c] = 0.0;
+      continue;
+    }
     double Ci[64], s, g;
     int st2 = pfo_fermi_point(ns, z, v, pr, cB, gB, phi0[c], Ci, &s, &g, NULL);
     if (st2) { st = st2; goto out; }
@@ -724,4 +746,76 @@ out:
   free(A); free(ffix); free(b); free(phi0); free(phi); free(psi); free(rho); free(kap);
   free(sig); free(C); free(Sv); free(Gv); free(Gdec);
   return st;
+}
+
+int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
+                 const double* eps, const unsigned char* solvent,
+                 int nq, const double* charges, double phi_lo_V, double phi_hi_V,
+                 int ns, const double* z, const double* radius_A, const double* bulk_M,
+                 double eps_s, double lc, double T, const pfo_nl_opts* opts,
+                 double* phi_V, double* C_M, double* S, double* Gamma, double* Psi_out,
+                 double* phi_hat_out, pfo_nl_report* rep) {
+  return pf_solve_impl(nx, ny, nz, h, origin, eps, solvent, nq, charges, phi_lo_V, phi_hi_V, ns, z, radius_A,
+                       bulk_M, eps_s, lc, T, opts, phi_V, C_M, S, Gamma, Psi_out, phi_hat_out, rep, NULL, NULL);
+}
+
+int pfo_pf_solve_fixed(int nx, int ny, int nz, double h, const double* origin,
+                       const double* eps, const unsigned char* solvent,
+                       int nq, const double* charges, double phi_lo_V, double phi_hi_V,
+                       int ns, const double* z, const double* radius_A, const double* bulk_M,
+                       double eps_s, double lc, double T, const pfo_nl_opts* opts,
+                       const unsigned char* fixed, const double* fixed_phi_V,
+                       double* phi_V, double* C_M, double* S, double* Gamma, double* Psi_out,
+                       double* phi_hat_out, pfo_nl_report* rep) {
+  if (!fixed || !fixed_phi_V) return PFO_E_INVAL;
+  return pf_solve_impl(nx, ny, nz, h, origin, eps, solvent, nq, charges, phi_lo_V, phi_hi_V, ns, z, radius_A,
+                       bulk_M, eps_s, lc, T, opts, phi_V, C_M, S, Gamma, Psi_out, phi_hat_out, rep, fixed,
+                       fixed_phi_V);
+}
+
+/* ---- the atomic site model of the filter region (Eqs. 19-20) ---------------------------------- */
+int pfo_site_potentials(int nsite, const double* center, const double* radius, const double* q_ion,
+                        const int* occupied, double eps_b, int nq, const double* charges, double eps_p,
+                        double lambda, double* phi_hat) {
+  if (nsite < 1 || nq < 0 || eps_b <= 0.0 || eps_p <= 0.0) return PFO_E_INVAL;
+  for (int b = 0; b < nsite; ++b) {
+    if (!(radius[b] > 0.0)) return PFO_E_INVAL;
+    /* the six symmetric points on the sphere of site b: +-radius along x, y and z */
+    double mean = 0.0;
+    for (int k = 0; k < 6; ++k) {
+      double A[3] = {center[3 * b], center[3 * b + 1], center[3 * b + 2]};
+      A[k / 2] += (k % 2 ? -1.0 : 1.0) * radius[b];
+      double sum = 0.0;
+      for (int j = 0; j < nq; ++j) {
+        const double d = sqrt((charges[4 * j] - A[0]) * (charges[4 * j] - A[0]) +
+                              (charges[4 * j + 1] - A[1]) * (charges[4 * j + 1] - A[1]) +
+                              (charges[4 * j + 2] - A[2]) * (charges[4 * j + 2] - A[2]));
+        if (!(d > 0.0)) return PFO_E_INVAL;
+        sum += charges[4 * j + 3] / (eps_p * d);
+      }
+      for (int m = 0; m < nsite; ++m) {
+        if (m == b || !occupied[m]) continue;
+        const double d = sqrt((center[3 * m] - A[0]) * (center[3 * m] - A[0]) +
+                              (center[3 * m + 1] - A[1]) * (center[3 * m + 1] - A[1]) +
+                              (center[3 * m + 2] - A[2]) * (center[3 * m + 2] - A[2]));
+        if (!(d > 0.0)) return PFO_E_INVAL;
+        sum += q_ion[m] / (eps_b * d);
+      }
+      mean += sum / 6.0;
+    }
+    const double own = occupied[b] ? q_ion[b] / (eps_b * radius[b]) : 0.0;
+    phi_hat[b] = lambda / (4.0 * M_PI) * (mean + own);
+  }
+  return PFO_OK;
+}
+
+int pfo_site_steric(int nsite, const double* ion_radius, const int* occupied, double v_sites, double gammaB,
+                    double* S) {
+  if (nsite < 1 || !(v_sites > 0.0) || !(gammaB > 0.0)) return PFO_E_INVAL;
+  double vol = 0.0;
+  for (int m = 0; m < nsite; ++m)
+    if (occupied[m]) vol += 4.0 * M_PI * ion_radius[m] * ion_radius[m] * ion_radius[m] / 3.0;
+  if (!(vol < v_sites)) return PFO_E_INVAL;
+  *S = log((1.0 - vol / v_sites) / gammaB);
+  return PFO_OK;
 }

@@ -146,6 +146,33 @@ int pfo_pf_solve(int nx, int ny, int nz, double h, const double* origin,
                  double* phi_V, double* C_M, double* S, double* Gamma, double* Psi,
                  double* phi_hat_out, pfo_nl_report* rep);
 
+/* The same solve with a filter region (Section 3, Eqs. 19-20 coupling): nodes with fixed[c] != 0 hold the
+ * potential fixed_phi_V[c] (volts) as a Dirichlet value of PF2 and of the initial solve, PF1 takes Psi = 0
+ * there (they bound the continuum solvent, Eq. 14), and they carry no continuum concentrations (C, S,
+ * Gamma written as 0). */
+int pfo_pf_solve_fixed(int nx, int ny, int nz, double h, const double* origin,
+                       const double* eps, const unsigned char* solvent,
+                       int nq, const double* charges, double phi_lo_V, double phi_hi_V,
+                       int ns, const double* z, const double* radius_A, const double* bulk_M,
+                       double eps_s, double lc, double T, const pfo_nl_opts* opts,
+                       const unsigned char* fixed, const double* fixed_phi_V,
+                       double* phi_V, double* C_M, double* S, double* Gamma, double* Psi_out,
+                       double* phi_hat_out, pfo_nl_report* rep);
+
+/* Eq. (19): the scaled potential phi_hat_b = e phi_b / k_B T of each of nsite spherical sites (centres x, y, z
+ * in A, radii in A), the mean over the six points +-radius along x, y, z of the protein charges (x, y, z, q)
+ * screened by eps_p and of the ions q_ion[m] at the other occupied sites screened by eps_b, plus the site's
+ * own ion q_ion[b] / (eps_b radius[b]) when occupied; lambda/(4 pi) converts to scaled units. */
+int pfo_site_potentials(int nsite, const double* center, const double* radius, const double* q_ion,
+                        const int* occupied, double eps_b, int nq, const double* charges, double eps_p,
+                        double lambda, double* phi_hat);
+
+/* Eq. (20): S = ln((1 - sum_m v_m / V_sites) / Gamma^B), v_m = 4 pi a_m^3 / 3 of the ion at each occupied
+ * site; V_sites (A^3) is the volume of the site region, a parameter (the paper does not give it).
+ * PFO_E_INVAL when the ions fill V_sites. */
+int pfo_site_steric(int nsite, const double* ion_radius, const int* occupied, double v_sites, double gammaB,
+                    double* S);
+
 #ifdef __cplusplus
 }
 #endif

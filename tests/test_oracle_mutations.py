@@ -35,6 +35,12 @@ MUTATIONS = [
      "const double J = eps_m * (dstar + dL);", "const double J = -eps_m * (dstar + dL);"),
     ("phi^L left out of the interface jump (Eq. 16 without it)",
      "const double J = eps_m * (dstar + dL);", "const double J = eps_m * dstar;"),
+    ("site points only on the positive half-axes (Eq. 19 not symmetric)",
+     "A[k / 2] += (k % 2 ? -1.0 : 1.0) * radius[b];", "A[k / 2] += radius[b];"),
+    ("the site's own ion left out of Eq. 19",
+     "const double own = occupied[b] ? q_ion[b] / (eps_b * radius[b]) : 0.0;", "const double own = 0.0;"),
+    ("Psi left free on the filter region (Eq. 14 not applied there)",
+     "fix_rows(N, fixed, A); /* Psi = 0", "/* Psi = 0"),
 ]
 
 # the pins, fastest first, with the arguments of one parametrisation each
@@ -52,6 +58,9 @@ PINS = [
     (P.test_pf_reduces_to_pb, {}),
     (P.test_pcg_iterates_minimise_the_energy_norm, {}),
     (P.test_decomposition_converges_to_the_slab_solution, {}),
+    (P.test_site_potential_of_a_charge_at_the_centre, {}),
+    (P.test_site_potential_six_point_mean_of_a_far_charge, {}),
+    (P.test_filter_region_with_site_potentials, {}),
 ]
 
 

@@ -776,3 +776,109 @@ def test_pf_decomposition_agrees_with_spread_charges_as_h_shrinks(orc):
         diffs.append(np.abs(vals[0] - vals[1]))
     assert diffs[1].max() < 2e-3
     assert diffs[0].mean() > 5 * diffs[1].mean()
+
+
+# ---------------------------------------------------------------- filter-region site model (Eqs. 19-20) and coupling
+def test_site_potential_of_a_charge_at_the_centre(orc):
+    """All six surface points are a_b from the centre: phi_b = lam q / (4 pi eps_p a_b), plus the site's own ion
+    q_b / (eps_b a_b) when occupied."""
+    lam = orc.lam()
+    c = np.array([[0.3, -0.2, 0.7]])
+    st, phi = orc.site_potentials(c, [0.95], [1.0], [0], 10.0, [[0.3, -0.2, 0.7, -0.5]], 4.0, lam)
+    assert st == 0
+    assert phi[0] == pytest.approx(lam * -0.5 / (4 * math.pi * 4.0 * 0.95), rel=1e-14)
+    st, phi = orc.site_potentials(c, [0.99], [2.0], [1], 10.0, [[0.3, -0.2, 0.7, -0.5]], 4.0, lam)
+    assert phi[0] == pytest.approx(lam / (4 * math.pi) * (-0.5 / (4.0 * 0.99) + 2.0 / (10.0 * 0.99)), rel=1e-14)
+
+
+def test_site_potential_of_another_occupied_site(orc):
+    """An ion at distance D along x from site b: the six distances are D - a, D + a and four times sqrt(D^2 + a^2)."""
+    lam, a, D = orc.lam(), 0.95, 3.1
+    centers = np.array([[0.0, 0.0, 0.0], [D, 0.0, 0.0]])
+    st, phi = orc.site_potentials(centers, [a, 0.99], [1.0, 2.0], [0, 1], 8.0, np.zeros((0, 4)), 4.0, lam)
+    assert st == 0
+    mean = (1 / (D - a) + 1 / (D + a) + 4 / math.sqrt(D * D + a * a)) / 6
+    assert phi[0] == pytest.approx(lam / (4 * math.pi) * 2.0 / 8.0 * mean, rel=1e-14)
+    # site 1 sees the empty site 0 not at all, and its own ion
+    assert phi[1] == pytest.approx(lam / (4 * math.pi) * 2.0 / (8.0 * 0.99), rel=1e-14)
+
+
+def test_site_potential_six_point_mean_of_a_far_charge(orc):
+    """The six-point mean of 1/|c - A_k| is exact for the harmonic terms up to degree 3, so for a far charge it
+    matches the sphere mean 1/d with an error falling as (a/d)^4 / d."""
+    lam, a = orc.lam(), 0.95
+    u = np.array([0.48, -0.6, 0.64])
+    u /= np.linalg.norm(u)
+    errs = []
+    for d in (4.0, 8.0):
+        ch = np.array([[*(d * u), 1.0]])
+        st, phi = orc.site_potentials(np.zeros((1, 3)), [a], [1.0], [0], 8.0, ch, 4.0, lam)
+        errs.append(abs(phi[0] * 4 * math.pi * 4.0 / lam - 1 / d))
+    assert errs[0] < (a / 4.0) ** 4 / 4.0
+    assert 20 < errs[0] / errs[1] < 45
+
+
+def test_site_steric(orc):
+    gB = 0.61412
+    st, S = orc.site_steric([0.95, 0.99], [0, 0], 20.0, gB)
+    assert st == 0 and S == pytest.approx(-math.log(gB), rel=1e-15)
+    st, S = orc.site_steric([0.95, 0.99], [1, 0], 20.0, gB)
+    assert S == pytest.approx(math.log((1 - 4 * math.pi * 0.95 ** 3 / 3 / 20.0) / gB), rel=1e-14)
+    assert orc.site_steric([0.95, 0.99], [1, 1], 4.0, gB)[0] == 1  # the ions fill the site volume
+
+
+def _filter_channel(lc):
+    return _small_channel(17, lc=lc)
+
+
+def _pore_ball(g, centre, radius):
+    X, Y, Z = g.coords()
+    return ((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2 <= radius ** 2).ravel()
+
+
+def test_filter_region_holding_the_solution_changes_nothing(orc):
+    """With lc = 0 each node's Psi depends only on its own density, so fixing a pore region at the potential the
+    unconstrained solve found there leaves the fixed point everywhere else unchanged."""
+    prob = _filter_channel(0.0)
+    g = prob.grid
+    free = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-13)
+    assert free["status"] == 0
+    fixed = _pore_ball(g, (0.0, 0.0, 0.5), 1.6) & (prob.solvent == 1)
+    assert 5 < fixed.sum() < 40
+    out = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-13, fixed=fixed.astype(np.uint8),
+                               fixed_phi_V=np.where(fixed, free["phi_V"], 0.0))
+    assert out["status"] == 0
+    np.testing.assert_allclose(out["phi_V"], free["phi_V"], rtol=0, atol=1e-9 * np.abs(free["phi_V"]).max())
+    assert np.all(out["C_M"][:, fixed] == 0.0)
+
+
+def test_filter_region_with_site_potentials(orc):
+    """Synthetic binding sites in the pore: Eq. (19) gives each site's potential from the wall charges and the
+    occupied sites; the nodes in each site's sphere hold it as a Dirichlet value of the continuum model, and PF2
+    holds at every other node."""
+    prob = _filter_channel(1.2)
+    g = prob.grid
+    lam, Tv = orc.lam(), orc.thermal_voltage(prob.T_K)
+    centres = np.array([[0.3, -0.2, -1.5], [-0.4, 0.3, 0.6], [0.2, 0.1, 2.4]])
+    radii, q_ion, occ = [0.95, 0.99, 0.95], [1.0, 2.0, 1.0], [1, 0, 1]
+    st, phib = orc.site_potentials(centres, radii, q_ion, occ, 20.0, prob.charges, 4.0, lam)
+    assert st == 0
+    fixed = np.zeros(g.n, bool)
+    fval = np.zeros(g.n)
+    for c, r, p in zip(centres, radii, phib):
+        ball = _pore_ball(g, c, max(r, 0.87 * g.h))
+        fixed |= ball
+        fval[ball] = p * Tv
+    assert fixed.sum() >= 3 and np.all(prob.solvent[fixed] == 1)
+    out = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-14, fixed=fixed.astype(np.uint8), fixed_phi_V=fval)
+    assert out["status"] == 0
+    np.testing.assert_allclose(out["phi_V"][fixed], fval[fixed], rtol=4e-16)  # volts -> k_BT/e -> volts
+    _, ffix = orc.spread_charges(g.nx, g.ny, g.nz, g.h, g.origin, prob.charges, lam)
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, prob.eps)
+    s = prob.solvent.astype(float)
+    res = orc.dia_apply(g.nx, g.ny, g.nz, A, out["phi_hat"]) + s * prob.eps_s * out["Psi"] - ffix
+    interior = np.zeros(g.shape_zyx, bool)
+    interior[1:-1] = True
+    check = interior.ravel() & ~fixed
+    assert np.abs(res[check]).max() < 1e-8 * np.abs(ffix).max()
+    assert np.all(out["Psi"][fixed] == 0.0) and np.all(out["C_M"][:, fixed] == 0.0)
