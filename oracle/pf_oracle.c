@@ -6,9 +6,15 @@
  * leg of the benchmark; never by the product path.  Every function follows one
  * passage of the paper, cited beside it, in the paper's order and notation, with no
  * blocking, fusion or reordering.  Readings of passages the paper leaves open:
- *   - charges are spread trilinearly onto the grid instead of the Green's-function
- *     decomposition of Eqs. (5)-(10), so the SMIB interface rows of Eqs. (17)-(18)
- *     carry no jump term and reduce to harmonic-mean face coefficients;
+ *   - by default charges are spread trilinearly onto the grid instead of the Green's-
+ *     function decomposition of Eqs. (5)-(10), so the SMIB interface rows of Eqs. (17)-(18)
+ *     carry no jump term and reduce to harmonic-mean face coefficients; the decomposition
+ *     itself (pfo_decompose, charge_mode 1) takes phi^L = -phi* on the interface and the
+ *     jump of Eq. (8), the signs that keep phi continuous (Eqs. 10 and 16 print others);
+ *   - conjugate gradients (pfo_pcg) run in the inner product that weights a node by 1/2
+ *     per mirrored side, in which the stored operators are symmetric;
+ *   - the filter region of Eqs. (19)-(20) is a node mask of Dirichlet values for the
+ *     continuum solves (pfo_pf_solve_fixed), with the six site points at +-a along the axes;
  *   - Gamma in Eq. (1) is taken from its own definition (an implicit pointwise
  *     equation) rather than lagged from the previous iterate;
  *   - Psi = 0 (Eq. 14) at membrane nodes and on the Dirichlet planes; the x/y sides
