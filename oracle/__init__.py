@@ -27,7 +27,7 @@ _PI = ctypes.POINTER(ctypes.c_int)
 
 class NlOpts(ctypes.Structure):
     _fields_ = [("omega", _D), ("tol_outer", _D), ("lin_tol", _D), ("lin_norm", _I),
-                ("max_outer", _I), ("max_lin", _I), ("solver", _I), ("charge_mode", _I)]
+                ("max_outer", _I), ("max_lin", _I), ("solver", _I), ("charge_mode", _I), ("gamma_mode", _I)]
 
 
 class NlReport(ctypes.Structure):
@@ -227,7 +227,7 @@ def decompose(nx, ny, nz, h, origin, solvent, charges, eps_m, eps_s, lam_value):
 
 def pf_solve(nx, ny, nz, h, origin, eps, solvent, charges, phi_lo_V, phi_hi_V, z, radius, bulk,
              eps_s, lc, T=298.15, omega=0.3, tol_outer=1e-10, lin_tol=1e-12, lin_norm=0, max_outer=500,
-             max_lin=20000, solver=0, charge_mode=0, fixed=None, fixed_phi_V=None):
+             max_lin=20000, solver=0, charge_mode=0, fixed=None, fixed_phi_V=None, gamma_mode=0):
     """Table 2 nonlinear PF solve; returns a dict of fields and the report."""
     N = nx * ny * nz
     ns = len(z)
@@ -238,7 +238,7 @@ def pf_solve(nx, ny, nz, h, origin, eps, solvent, charges, phi_lo_V, phi_hi_V, z
     z, radius, bulk = _f64(z), _f64(radius), _f64(bulk)
     out = {k: np.zeros(N) for k in ("phi_V", "S", "Gamma", "Psi", "phi_hat")}
     out["C_M"] = np.zeros(ns * N)
-    opts = NlOpts(omega, tol_outer, lin_tol, lin_norm, max_outer, max_lin, solver, charge_mode)
+    opts = NlOpts(omega, tol_outer, lin_tol, lin_norm, max_outer, max_lin, solver, charge_mode, gamma_mode)
     rep = NlReport()
     outs = (_pd(out["phi_V"]), _pd(out["C_M"]), _pd(out["S"]), _pd(out["Gamma"]), _pd(out["Psi"]),
             _pd(out["phi_hat"]), ctypes.byref(rep))

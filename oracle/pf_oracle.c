@@ -582,6 +582,22 @@ out:
   return status;
 }
 
+/* The lagged reading of Eq. (11): the concentrations from phi and the steric potential S_prev of the
+ * previous iterate, then Gamma = 1 - sum v_i C_i and the new S = ln(Gamma / Gamma^B). */
+static int lagged_fermi(int ns, const double* z, const double* v, const double* p, const double* cB, double gammaB,
+                        double phi, double S_prev, double* C, double* S, double* Gamma) {
+  double occ = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    C[i] = cB[i] * exp(-z[i] * phi + p[i] * S_prev);
+    occ += v[i] * C[i];
+  }
+  const double g = 1.0 - occ;
+  if (!(g > 0.0)) return PFO_E_GAMMA;
+  *Gamma = g;
+  *S = log(g / gammaB);
+  return PFO_OK;
+}
+
 /* Rows of the fixed nodes (the filter region) become identity rows. */
 static void fix_rows(long N, const unsigned char* fixed, double* A) {
   if (!fixed) return;
@@ -605,7 +621,7 @@ static int pf_solve_impl(int nx, int ny, int nz, double h, const double* origin,
   pfo_nl_report R = {PFO_OK, 0, 0, 0, 0.0};
   typedef int (*lin_fn)(int, int, int, const double*, const double*, double*, int, double, int, int*,
                         double*);
-  if (opts->solver < 0 || opts->solver > 2) return PFO_E_INVAL;
+  if (opts->solver < 0 || opts->solver > 2 || opts->gamma_mode < 0 || opts->gamma_mode > 1) return PFO_E_INVAL;
   const lin_fn solve_pf1 = opts->solver >= 1 ? pfo_pcg : pfo_bicgstab;
   const lin_fn solve_pf2 = opts->solver == 2 ? pfo_pcg : pfo_bicgstab;
   double v[64], pr[64], cB[64], gB;
@@ -626,7 +642,9 @@ static int pf_solve_impl(int nx, int ny, int nz, double h, const double* origin,
   double* Sv = calloc(N, sizeof(double));
   double* Gv = calloc(N, sizeof(double));
   double* Gdec = NULL; /* G = phi* + phi^L of the decomposition (charge_mode 1) */
-  if (!A || !ffix || !b || !phi0 || !phi || !psi || !rho || !kap || !sig || !C || !Sv || !Gv) {
+  double* Slag = opts->gamma_mode == 1 ? calloc(N, sizeof(double)) : NULL; /* lagged S (gamma_mode 1) */
+  if (!A || !ffix || !b || !phi0 || !phi || !psi || !rho || !kap || !sig || !C || !Sv || !Gv ||
+      (opts->gamma_mode == 1 && !Slag)) {
     st = PFO_E_INVAL;
     goto out;
   }
@@ -678,7 +696,12 @@ static int pf_solve_impl(int nx, int ny, int nz, double h, const double* origin,
       kap[c] = 0.0;
       if (!solvent[c] || (fixed && fixed[c])) continue;
       double Ci[64], s, g;
-      st = pfo_fermi_point(ns, z, v, pr, cB, gB, phi0[c], Ci, &s, &g, NULL);
+      if (Slag) {
+        st = lagged_fermi(ns, z, v, pr, cB, gB, phi0[c], Slag[c], Ci, &s, &g);
+        Slag[c] = s;
+      } else {
+        st = pfo_fermi_point(ns, z, v, pr, cB, gB, phi0[c], Ci, &s, &g, NULL);
+      }
       if (st) goto out;
       for (int i = 0; i < ns; ++i) {
         rho[c] += z[i] * Ci[i];
@@ -728,7 +751,8 @@ static int pf_solve_impl(int nx, int ny, int nz, double h, const double* origin,
       continue;
     }
     double Ci[64], s, g;
-    int st2 = pfo_fermi_point(ns, z, v, pr, cB, gB, phi0[c], Ci, &s, &g, NULL);
+    int st2 = Slag ? lagged_fermi(ns, z, v, pr, cB, gB, phi0[c], Slag[c], Ci, &s, &g)
+                   : pfo_fermi_point(ns, z, v, pr, cB, gB, phi0[c], Ci, &s, &g, NULL);
     if (st2) { st = st2; goto out; }
     for (int i = 0; i < ns; ++i) C[(long)i * N + c] = Ci[i];
     Sv[c] = s;
@@ -750,7 +774,7 @@ out:
   R.status = st;
   if (rep) *rep = R;
   free(A); free(ffix); free(b); free(phi0); free(phi); free(psi); free(rho); free(kap);
-  free(sig); free(C); free(Sv); free(Gv); free(Gdec);
+  free(sig); free(C); free(Sv); free(Gv); free(Gdec); free(Slag);
   return st;
 }
 

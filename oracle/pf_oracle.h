@@ -123,6 +123,10 @@ typedef struct {
                         potential decomposition of Eqs. 5-10 (pfo_decompose): the interface right-hand
                         side replaces the spread charges and phi = phi~ + G is returned in Omega_m.  Mode 1
                         needs one dielectric value on all non-solvent nodes and charges inside Omega_m. */
+  int gamma_mode;    /* 0: Gamma of Eq. (1) as the root of its own definition at every node (default);
+                        1: the lagged reading of Eq. (11): C_i = cB_i exp(-z_i phi + p_i S) with S from the
+                        previous outer iterate (0 at the start), then Gamma = 1 - sum v_i C_i and
+                        S = ln(Gamma / Gamma^B); PFO_E_GAMMA when Gamma <= 0.  Same fixed point. */
 } pfo_nl_opts;
 
 typedef struct {

@@ -395,6 +395,19 @@ def test_fixed_point_independent_of_omega(orc, omega):
     np.testing.assert_allclose(out["phi_hat"], ref["phi_hat"], atol=1e-9 * np.abs(ref["phi_hat"]).max())
 
 
+def test_fixed_point_independent_of_gamma_mode(orc):
+    """Gamma as the root of its definition and the lagged reading of Eq. (11) (S from the previous iterate) reach
+    the same fixed point: at convergence S = ln(Gamma(S)/Gamma^B) either way."""
+    prob = _small_channel(9)
+    ref = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-14)
+    lag = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-14, gamma_mode=1)
+    assert ref["status"] == 0 and lag["status"] == 0
+    np.testing.assert_allclose(lag["phi_hat"], ref["phi_hat"], atol=1e-9 * np.abs(ref["phi_hat"]).max())
+    for i in range(len(prob.species)):
+        np.testing.assert_allclose(lag["C_M"][i], ref["C_M"][i], rtol=1e-8, atol=0)
+    np.testing.assert_allclose(lag["S"], ref["S"], atol=1e-9)
+
+
 def test_pf_fixed_point_satisfies_equations(orc):
     """At convergence the PF1/PF2 pair of Eqs. (12)-(13) holds with phi0 = phi, i.e.
     -div(eps grad phi) = -s eps_s Psi + lambda rho_fix and eps_s(lc^2 Lap - 1) Psi = lambda rho(phi)."""
