@@ -35,6 +35,10 @@ MUTATIONS = [
      "const double J = eps_m * (dstar + dL);", "const double J = -eps_m * (dstar + dL);"),
     ("phi^L left out of the interface jump (Eq. 16 without it)",
      "const double J = eps_m * (dstar + dL);", "const double J = eps_m * dstar;"),
+    ("BiCGSTAB beta without the alpha/omega factor (Table 3)",
+     "const double beta = (rho / rho_prev) * (alpha / omega);", "const double beta = rho / rho_prev;"),
+    ("BiCGSTAB omega from s.s instead of t.t (Table 3)",
+     "omega = dot(N, t, s) / tt;", "omega = dot(N, t, s) / dot(N, s, s);"),
     ("site points only on the positive half-axes (Eq. 19 not symmetric)",
      "A[k / 2] += (k % 2 ? -1.0 : 1.0) * radius[b];", "A[k / 2] += radius[b];"),
     ("the site's own ion left out of Eq. 19",
@@ -53,6 +57,7 @@ PINS = [
     (P.test_operator_row_sums_and_symmetry, {}),
     (P.test_debye_huckel_slab, {}),
     (P.test_bicgstab_matches_dense_lu, {"seed": 0}),
+    (P.test_krylov_methods_terminate_within_the_distinct_eigenvalue_count, {"dims": (3, 3, 5)}),
     (P.test_pf_fixed_point_satisfies_equations, {}),
     (P.test_kappa_makes_pf2_a_newton_step, {}),
     (P.test_pf_reduces_to_pb, {}),

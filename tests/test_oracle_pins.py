@@ -277,6 +277,31 @@ def test_bicgstab_pf1_matches_dense_lu(orc):
     np.testing.assert_allclose(r["x"], xe, atol=1e-12 * np.abs(xe).max())
 
 
+def _distinct_eigenvalues_of_preconditioned(orc, dims, A):
+    M = orc.dense_from_dia(*dims, A)
+    n = M.shape[0]
+    free = np.array([not np.array_equal(M[c], np.eye(n)[c]) for c in range(n)])
+    ev = np.sort(np.linalg.eigvals(M[np.ix_(free, free)] / np.diag(M)[free][:, None]).real)
+    return 1 + int(np.sum(np.diff(ev) > 1e-8 * np.abs(ev).max()))
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 3), (3, 3, 5), (4, 3, 5)])
+def test_krylov_methods_terminate_within_the_distinct_eigenvalue_count(orc, dims):
+    """With m distinct eigenvalues of M^-1 A on the free rows (uniform eps and kappa), the Krylov space of r0 has
+    dimension at most m, so conjugate gradients and BiCGSTAB (whose BiCG part spans the same space) end
+    within m iterations: a property of the recurrences themselves (Table 3), which a wrong
+    beta or omega loses."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    A = orc.assemble_eps(nx, ny, nz, 0.8, np.full(n, 5.0), np.full(n, 0.7))
+    m = _distinct_eigenvalues_of_preconditioned(orc, dims, A)
+    b = W.uniform(7, n, -1.0, 1.0)
+    r = orc.bicgstab(nx, ny, nz, A, b, tol=1e-12, max_it=m)
+    c = orc.pcg(nx, ny, nz, A, b, tol=1e-12, max_it=m)
+    assert r["status"] == 0 and r["iters"] <= m
+    assert c["status"] == 0 and c["iters"] <= m
+
+
 def test_bicgstab_reports_noconv(orc):
     p = W.linear_problem(n=9, seed=3, n_spheres=4)
     g = p.grid
