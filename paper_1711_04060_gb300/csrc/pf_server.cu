@@ -107,7 +107,7 @@ bool join(pf_server* sv, pf_batch* E, Request* r) {
 void scheduler_main(pf_server* sv) {
   cudaSetDevice(sv->device);
   pf_batch* E = nullptr;
-  const pf_status es = pfi::engine_create(sv->max_slots, &E);
+  pf_status es = pfi::engine_create(sv->max_slots, &E);  // while not PF_OK, every admitted request fails with it
   std::unordered_map<long long, Request*> inflight;
   for (;;) {
     std::vector<Request*> admit;
@@ -146,10 +146,11 @@ void scheduler_main(pf_server* sv) {
       // a failure of the engine itself (not of a problem): fail every request in flight and start afresh
       const std::string err = pf_last_error();
       pf_batch_destroy(E);
+      E = nullptr;
       for (auto& kv : inflight) complete(sv, kv.second, s, err);
       inflight.clear();
-      if (pfi::engine_create(sv->max_slots, &E) != PF_OK) E = nullptr;
-      if (!E) break;
+      es = pfi::engine_create(sv->max_slots, &E);
+      if (es != PF_OK) E = nullptr;  // later requests are completed with the failure instead of waiting
       continue;
     }
     for (long long t : fin) {
