@@ -184,6 +184,17 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c);
 /* Sets kappa_c (Angstrom^-2) of PF_OP_PF2 from N values in host or device memory. */
 pf_status pf_set_kappa(pf_grid* g, const double* kappa, int mem);
 
+/* Sets a filter region (Section 3 with Eqs. 19-20): the nodes with fixed[c] = 1 (N bytes, 0/1) hold phi_V[c]
+ * (volts; N values) as Dirichlet values of the continuum model.  Their rows become identity rows of the
+ * Poisson, PF1 and PF2 operators, PF1 takes Psi = 0 there (they bound the continuum solvent, Eq. 14), and
+ * pf_nonlinear_solve writes C, S and Gamma as 0 there (the site model of Eqs. 19-20 describes them).  A
+ * caller computes the site potentials (Eq. 19) and maps the sites to nodes.  fixed = NULL clears the region.
+ * Replacing or clearing a region rebuilds the operators, which also resets kappa.  Host or device arrays per
+ * `mem`; copied.
+ * pf_set_coeffs clears the region; a grid with a region cannot be solved in a batch (PF_E_INVAL) and is
+ * not served. */
+pf_status pf_set_filter(pf_grid* g, const uint8_t* fixed, const double* phi_V, int mem);
+
 /* Sets the grid's potential Phi_0 (phi_V: N values in volts, node-major, host or device per `mem`) as the
  * start of the next pf_nonlinear_solve with warm_start = 1: a checkpoint written from pf_result.phi_V, or a
  * caller's guess.  Psi restarts from 0.  Needs pf_set_coeffs first (which forgets any potential). */

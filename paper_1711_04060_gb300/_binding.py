@@ -88,6 +88,7 @@ SIGNATURES = {
     "pf_set_potential": (_I, [_VP, _VP, _I]),
     "pf_linear_solve": (_I, [_VP, _I, _VP, _VP, _I, ctypes.POINTER(pf_solve_opts), ctypes.POINTER(pf_report)]),
     "pf_linear_solve_cg": (_I, [_VP, _I, _VP, _VP, _I, ctypes.POINTER(pf_solve_opts), ctypes.POINTER(pf_report)]),
+    "pf_set_filter": (_I, [_VP, _VP, _VP, _I]),
     "pf_nonlinear_solve": (_I, [_VP, ctypes.POINTER(pf_nl_opts), ctypes.POINTER(pf_result)]),
     "pf_destroy_grid": (_I, [_VP]),
     "pf_profile_enable": (_I, [_VP, _I]),

@@ -117,6 +117,18 @@ def pf_set_coeffs(grid, coeffs: _Coeffs):
     _check(B.load().pf_set_coeffs(grid, ctypes.byref(coeffs.c)))
 
 
+def pf_set_filter(grid, fixed=None, phi_V=None):
+    """Filter region: nodes with fixed = 1 hold phi_V (volts); fixed None clears it."""
+    if fixed is None:
+        _check(B.load().pf_set_filter(grid, None, None, PF_MEM_HOST))
+        return
+    pf_, mf = _ptr(fixed, np.uint8)
+    pv, mv = _ptr(phi_V, np.float64)
+    if mf != mv:
+        raise TypeError("fixed and phi_V must both be host or both be device arrays")
+    _check(B.load().pf_set_filter(grid, pf_, pv, mf))
+
+
 def pf_set_kappa(grid, kappa):
     p, mem = _ptr(kappa, np.float64)
     _check(B.load().pf_set_kappa(grid, p, mem))
@@ -391,6 +403,9 @@ class Grid:
 
     def set_kappa(self, kappa):
         pf_set_kappa(self.handle, kappa)
+
+    def set_filter(self, fixed=None, phi_V=None):
+        pf_set_filter(self.handle, fixed, phi_V)
 
     def linear_solve(self, op, b, x, opts=None, allow=(), method="bicgstab"):
         return pf_linear_solve(self.handle, op, b, x, opts, allow, method)

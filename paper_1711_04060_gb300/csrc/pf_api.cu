@@ -18,6 +18,7 @@
 
 #include "../../include/pf_gb300.h"
 #include "pf_cg.cuh"
+#include "pf_filter.cuh"
 #include "pf_grid.cuh"
 
 using pf::BicgState;
@@ -455,6 +456,16 @@ pf_status check_opts(const pf_solve_opts& o) {
 pf_status update_pf2(pf_grid* g) {
   PF_LAUNCH(g, PF_PROF_OTHER,
             pf::launch_eps_diag(g->dsum, g->sig, g->solvent, g->geom, g->diag2, g->dinv2, g->dinv2_32, g->stream));
+  if (g->filter_on)
+    PF_LAUNCH(g, PF_PROF_OTHER,
+              pf::launch_filter_rows(g->fmask, g->geom, g->dinv2, g->diag2, g->dinv2_32, g->stream));
+  return PF_OK;
+}
+
+// the filter region's identity rows in the Poisson and PF1 operators (PF2: update_pf2)
+pf_status filter_rows_p1(pf_grid* g) {
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_rows(g->fmask, g->geom, g->dinvP, g->diagP, g->dinvP32, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_rows(g->fmask, g->geom, g->dinv1, nullptr, g->dinv1_32, g->stream));
   return PF_OK;
 }
 
@@ -474,6 +485,7 @@ pf_status build_operators(pf_grid* g) {
   PF_TRY(update_pf2(g));
   PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf1_dinv(g->solvent, g->geom, 1.0 / (6.0 * pf1_face(g) + g->eps_s),
                                                   g->dinv1, g->dinv1_32, g->stream));
+  if (g->filter_on) PF_TRY(filter_rows_p1(g));
   PF_CK(cudaMemsetAsync(g->ffix, 0, NP * sizeof(double), g->stream));
   PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), g->stream));
   if (g->nq > 0)
@@ -800,6 +812,7 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
     PF_CK(cudaMallocAsync(&g->dch, sizeof(double) * 4 * g->nq, g->stream));
     PF_CK(cudaMemcpyAsync(g->dch, c->charges, sizeof(double) * 4 * g->nq, cudaMemcpyHostToDevice, g->stream));
   }
+  g->filter_on = false;  // new coefficients: the filter region must be set again
   PF_TRY(build_operators(g));
   PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
   PF_CK(cudaStreamSynchronize(g->stream));
@@ -884,6 +897,35 @@ static pf_status linear_solve_entry(pf_grid* g, int op, const double* b, double*
   return PF_OK;
 }
 
+pf_status pf_set_filter(pf_grid* g, const uint8_t* fixed, const double* phi_V, int mem) {
+  if (!g) return fail(PF_E_INVAL, "grid is required");
+  if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first");
+  if (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "mem must be PF_MEM_HOST or PF_MEM_DEVICE");
+  if (fixed && !phi_V) return fail(PF_E_INVAL, "phi_V is required with a filter mask");
+  if (fixed && mem == PF_MEM_HOST)
+    for (long i = 0; i < g->N; ++i)
+      if (fixed[i] > 1) return fail(PF_E_INVAL, "fixed must be 0 or 1");
+  if (g->filter_on) {  // drop the previous region: rebuild the operators without its identity rows
+    g->filter_on = false;
+    PF_TRY(build_operators(g));
+  }
+  if (!fixed) return PF_OK;
+  const long NP = g->geom.np;
+  if (!g->fmask) {
+    PF_TRY(dalloc(g, &g->fmask, NP));
+    PF_TRY(dalloc(g, &g->fval, NP));
+  }
+  PF_CK(cudaMemsetAsync(g->fmask, 0, NP, g->stream));
+  PF_TRY(pack_in(g, fixed, mem, g->fmask, 1));
+  PF_TRY(pack_in(g, phi_V, mem, g->fval, 0));
+  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->fval, 1.0 / g->Tv, g->fval, NP, g->stream));
+  g->filter_on = true;
+  PF_TRY(filter_rows_p1(g));
+  PF_LAUNCH(g, PF_PROF_OTHER,
+            pf::launch_filter_rows(g->fmask, g->geom, g->dinv2, g->diag2, g->dinv2_32, g->stream));
+  return PF_OK;
+}
+
 pf_status pf_linear_solve(pf_grid* g, int op, const double* b, double* x, int mem, const pf_solve_opts* opts,
                           pf_report* report) {
   NvtxRange range("pf_linear_solve");
@@ -934,6 +976,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
     PF_CK(cudaMemsetAsync(g->psi, 0, NP * sizeof(double), s));
     PF_LAUNCH(g, PF_PROF_OTHER,
               pf::launch_pf2_rhs(g->psi, g->solvent, g->ffix, g->eps_s, g->lo_hat, g->hi_hat, G, g->b2, s));
+    if (g->filter_on) PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_values(g->fmask, g->fval, G, g->b2, s));
     PF_TRY(solve_dev(g, PF_OP_POISSON, g->b2, g->phi0, o.lin, &rep));
     res->lin_iters_first = rep.iterations;
     res->lin_iters_total += rep.iterations;
@@ -952,12 +995,14 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
     PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, g->b1, g->sig, g->c2,
                                                  nullptr, nullptr, nullptr, g->ulast, outer > 1 || fermi_warm,
                                                  g->err, s));
+    if (g->filter_on) PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->b1, 1, s));  // Psi = 0
     PF_TRY(update_pf2(g));
     PF_TRY(solve_dev(g, PF_OP_PF1, g->b1, g->psi, lo, &rep, eta));  // Eq. (12)
     res->lin_iters_total += rep.iterations;
     if (rep.status != PF_OK) { st = (pf_status)rep.status; break; }
     PF_LAUNCH(g, PF_PROF_OTHER,
               pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat, G, g->b2, s));
+    if (g->filter_on) PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_values(g->fmask, g->fval, G, g->b2, s));
     PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
     PF_TRY(solve_dev(g, PF_OP_PF2, g->b2, g->phi, lo, &rep, eta));  // Eq. (13)
     res->lin_iters_total += rep.iterations;
@@ -984,6 +1029,11 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, nullptr, nullptr, nullptr,
                                                g->Cbuf, g->Sbuf, g->Gbuf, g->ulast, res->outer_iters > 0 || fermi_warm,
                                                g->err, s));
+  if (g->filter_on) {  // no continuum concentrations on the filter region
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->Cbuf, g->sp.ns, s));
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->Sbuf, 1, s));
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->Gbuf, 1, s));
+  }
   if (res->phi_V) {
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, NP, s));
     PF_TRY(unpack_out(g, g->phi, 1, res->phi_V, res->mem));

@@ -963,6 +963,7 @@ pf_status pf_batch_nonlinear_solve(pf_batch* B, const pf_nl_opts* opts, pf_resul
   const int n = (int)B->grids.size();
   for (int i = 0; i < n; ++i) {
     if (!B->grids[i]->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first on every grid");
+    if (B->grids[i]->filter_on) return fail(PF_E_INVAL, "a grid with a filter region cannot be solved in a batch");
     if (o.warm_start && !B->grids[i]->have_phi0)
       return fail(PF_E_INVAL, "warm_start needs a potential on every grid (a previous solve or pf_set_potential)");
     if (results[i].mem != PF_MEM_HOST && results[i].mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "bad result mem");
@@ -1053,6 +1054,7 @@ cudaStream_t engine_stream(pf_batch* B) { return B->stream; }
 
 pf_status engine_add(pf_batch* B, pf_grid* g, pf_result* res, const pf_nl_opts& o, long long tag) {
   if (!g || !res || !g->have_coeffs) return fail(PF_E_INVAL, "engine member needs a grid with coefficients");
+  if (g->filter_on) return fail(PF_E_INVAL, "a grid with a filter region cannot join a batch");
   PF_TRY(check_nl(o));
   if (g->stream != B->stream) return fail(PF_E_INVAL, "engine member must use the engine's stream");
   if (o.warm_start && !g->have_phi0) return fail(PF_E_INVAL, "warm_start needs a potential on the grid");

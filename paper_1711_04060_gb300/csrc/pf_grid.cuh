@@ -55,6 +55,9 @@ struct pf_grid {
   bool have_coeffs = false;
   bool have_phi0 = false;    // phi0 holds a potential to warm-start from (last solve or pf_set_potential)
   bool ulast_valid = false;  // ulast holds the per-node ln Gamma of the last Fermi step on this problem
+  bool filter_on = false;    // a filter region (pf_set_filter) holds fixed potentials
+  uint8_t* fmask = nullptr;  // its nodes (padded layout), allocated on first use
+  double* fval = nullptr;    // their potentials in units of k_BT/e (padded layout)
   // problem constants
   double eps_s = 78.5, lc = 0.0, T = 298.15, Tv = 0.0, lam = 0.0, lo_hat = 0.0, hi_hat = 0.0, molar = 0.0;
   pf::SpeciesParams sp{};

@@ -73,6 +73,7 @@ def test_errors_without_device_are_reported(lib):
     assert lib.pf_batch_create(None, 0, None, ctypes.byref(b)) == 1
     assert b"grid" in lib.pf_last_error()
     assert lib.pf_batch_destroy(None) == 0
+    assert lib.pf_set_filter(None, None, None, 0) == 1
     for fn in (lib.pf_linear_solve, lib.pf_linear_solve_cg):
         assert fn(None, 0, None, None, 0, None, None) == 1
         assert b"required" in lib.pf_last_error()
