@@ -39,6 +39,14 @@ MUTATIONS = [
      "const double beta = (rho / rho_prev) * (alpha / omega);", "const double beta = rho / rho_prev;"),
     ("BiCGSTAB omega from s.s instead of t.t (Table 3)",
      "omega = dot(N, t, s) / tt;", "omega = dot(N, t, s) / dot(N, s, s);"),
+    ("phi^L boundary at the solvent node instead of the face midpoint",
+     "hs[sgn] = 0.5 * h;", "hs[sgn] = h;"),
+    ("first-order one-sided derivative of phi^L in the jump",
+     "(8.0 * f0 - 9.0 * f1 + phiL[cm2]) / (3.0 * h)", "(f0 - f1) / (0.5 * h)"),
+    ("zero normal derivative of G on the sides not imposed",
+     "b[c] += -2.0 * nout * gr[a] / h;", "(void)nout;"),
+    ("c0 and d0 of Eqs. 17-18 swapped",
+     "bif[cm] += -eps_m * J / ((eps_m + eps_s) * h);", "bif[cm] += -eps_s * J / ((eps_m + eps_s) * h);"),
     ("site points only on the positive half-axes (Eq. 19 not symmetric)",
      "A[k / 2] += (k % 2 ? -1.0 : 1.0) * radius[b];", "A[k / 2] += radius[b];"),
     ("the site's own ion left out of Eq. 19",
