@@ -404,6 +404,9 @@ def cg_sample(api, grid, prob, torch, dev, lin_tol):
                 kms = prof.get("cg_direction", (0, 0.0))[1] + prof.get("cg_update", (0, 0.0))[1]
                 if kms > 0:
                     r["GBps"] = round(rep["iterations"] * words * 8 * g.n / (kms / 1e3) / 1e9, 1)
+                    peak, src = measured_peaks()
+                    r["frac_of_hbm"] = round(r["GBps"] / peak, 3)
+                    r["hbm_peak_source"] = src
                     r["kernel_ms"] = round(kms, 3)
             res[method] = r
             xs[method] = x
