@@ -45,7 +45,7 @@ def _sites(orc, prob):
     g = prob.grid
     centres = np.array([[0.3, -0.2, -1.5], [-0.4, 0.3, 0.6], [0.2, 0.1, 2.4]])
     radii, q_ion, occ = [0.95, 0.99, 0.95], [1.0, 2.0, 1.0], [1, 0, 1]
-    st, phib = orc.site_potentials(centres, radii, q_ion, occ, 20.0, prob.charges, 4.0, orc.lam())
+    st, phib = orc.site_potentials(centres, radii, q_ion, occ, 80.0, prob.charges, 20.0, orc.lam())
     assert st == 0
     Tv = orc.thermal_voltage(prob.T_K)
     fixed = np.zeros(g.n, bool)
@@ -68,7 +68,7 @@ def test_filter_region_matches_oracle(api, orc, precision):
     grid = api.Grid.for_problem(prob)
     grid.set_filter(fixed, val)
     prec = api.PF_FP64 if precision == "fp64" else api.PF_MIXED
-    out, rep = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=prec))
+    out, rep = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=prec, max_outer=2000))
     grid.close()
     assert rep["status"] == 0
     assert _rel(out["phi_V"], ref["phi_V"], floor=0.0257) < (TOL_FP64 if precision == "fp64" else TOL_MIXED)
