@@ -276,6 +276,7 @@ def run_reference(args):
 
 
 L2_BYTES = 129e6  # GB300 L2
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
 def config_of(args):
@@ -489,6 +490,7 @@ def run_ours(args):
     traffic = kernel_traffic(dom)
     roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                 "traffic": (traffic * n_int) if traffic is not None else None,
                 "algorithmic_bytes_per_launch": KERNEL_BYTES[dom] * n_int, "avg_launch_ms": avg_s * 1e3,
                 "launches": cnt}
