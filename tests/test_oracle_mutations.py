@@ -53,6 +53,15 @@ MUTATIONS = [
      "const double own = occupied[b] ? q_ion[b] / (eps_b * radius[b]) : 0.0;", "const double own = 0.0;"),
     ("Psi left free on the filter region (Eq. 14 not applied there)",
      "fix_rows(N, fixed, A); /* Psi = 0", "/* Psi = 0"),
+    ("PF1 couplings eps_s lc / h^2 instead of eps_s lc^2 / h^2 (Eq. 12)",
+     "const double w = eps_s * lc * lc / (h * h);", "const double w = eps_s * lc / (h * h);"),
+    ("PF1 mirror doubling dropped on the x sides (Eq. 4 for Psi)",
+     "if (i < nx - 1) A[1 * N + c] -= w; else A[2 * N + c] -= w;\n        if (i > 0) A[2 * N + c] -= w; "
+     "else A[1 * N + c] -= w;",
+     "if (i < nx - 1) A[1 * N + c] -= w;\n        if (i > 0) A[2 * N + c] -= w;"),
+    ("PF1 z couplings halved (a stray factor 1/2 on both off-diagonals)",
+     "A[6 * N + c] -= w;\n        A[5 * N + c] -= w;\n        A[c] = 6.0 * w + eps_s;",
+     "A[6 * N + c] -= 0.5 * w;\n        A[5 * N + c] -= 0.5 * w;\n        A[c] = 6.0 * w + eps_s;"),
 ]
 
 # the pins, fastest first, with the arguments of one parametrisation each
@@ -67,6 +76,8 @@ PINS = [
     (P.test_bicgstab_matches_dense_lu, {"seed": 0}),
     (P.test_krylov_methods_terminate_within_the_distinct_eigenvalue_count, {"dims": (3, 3, 5)}),
     (P.test_pf_fixed_point_satisfies_equations, {}),
+    (P.test_linearised_pf_slab_closed_form, {"lc": 1.2}),
+    (P.test_linearised_pf_transverse_mode, {}),
     (P.test_kappa_makes_pf2_a_newton_step, {}),
     (P.test_pf_reduces_to_pb, {}),
     (P.test_pcg_iterates_minimise_the_energy_norm, {}),

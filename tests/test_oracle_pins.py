@@ -496,6 +496,117 @@ def test_kappa_makes_pf2_a_newton_step(orc):
     assert out["report"]["outer_iters"] <= 6
 
 
+# ---------------------------------------------------------------- the correlation operator (lc > 0, Eqs. 2, 12-14)
+def _linear_pf_slab_exact(K, h, lc, kd2, V, lam_t=0.0):
+    """Exact discrete solution of the linearised PF pair on nodes k = 0..K of a slab, for a field
+    phi = X(i) Y(j) f(k) whose transverse factor is an eigenvector of the 7-point Laplacian with
+    eigenvalue -lam_t (lam_t = 0: uniform in x and y).  At the fixed point of Eqs. (11)-(13) with
+    uniform eps = eps_s, no fixed charge and the Debye-Hueckel density lambda rho = -eps_s kd2 phi:
+        PF2:  Psi = Lap_h phi,        PF1:  -lc^2 Lap_h Psi + Psi = kd2 phi,
+    with phi = 0 / V and Psi = 0 (Eq. 14) on the planes k = 0 and k = K.  A mode f(k) = r^k has
+    Lap_h = M = (r - 2 + 1/r)/h^2 - lam_t, so lc^2 M^2 - M + kd2 = 0 (the discrete form of
+    Eq. 2's lc^2 phi'''' - phi'' + kd2 phi = 0): two values of M, two roots r, 1/r for each."""
+    disc = np.sqrt(complex(1.0 - 4.0 * lc * lc * kd2))
+    Ms = [(1.0 + disc) / (2.0 * lc * lc), (1.0 - disc) / (2.0 * lc * lc)]
+    roots = []
+    for M in Ms:
+        q = 2.0 + (M + lam_t) * h * h
+        r = (q - np.sqrt(q * q - 4.0)) / 2.0
+        if abs(r) > 1.0:
+            r = 1.0 / r
+        roots.append(r)
+    # f(k) = sum_m A_m r_m^k + B_m r_m^(K-k) (decaying from each plane); Psi-factor = sum_m M_m (...)
+    rows, rhs = [], []
+    for kk, fv in ((0, 0.0), (K, V)):
+        rows.append([x for r in roots for x in (r ** kk, r ** (K - kk))])
+        rhs.append(fv)
+        rows.append([x for r, M in zip(roots, Ms) for x in (M * r ** kk, M * r ** (K - kk))])
+        rhs.append(0.0)
+    coef = np.linalg.solve(np.array(rows, complex), np.array(rhs, complex))
+    k = np.arange(K + 1)
+    f = sum(coef[2 * m] * roots[m] ** k + coef[2 * m + 1] * roots[m] ** (K - k) for m in range(2))
+    psi = sum(Ms[m] * (coef[2 * m] * roots[m] ** k + coef[2 * m + 1] * roots[m] ** (K - k)) for m in range(2))
+    assert np.abs(f.imag).max() < 1e-12 * abs(V) and np.abs(psi.imag).max() < 1e-12 * abs(V)
+    return f.real, psi.real, [complex(M) for M in Ms]
+
+
+_LC_SALT = 0.5   # mol/L 1:1 salt: 4 lc^2 kD^2 = 0.31 at lc = 1.2 A, so the two decay rates differ by 10x
+_LC_V = 1e-5     # phi_hat on the upper plane: the sinh of Eq. (1) is linear to (1e-5)^2 / 6
+
+
+def _lc_slab_solve(orc, nx, ny, nz, h, lc, fixed=None, fixed_phi_V=None):
+    n = nx * ny * nz
+    Tv = orc.thermal_voltage()
+    out = orc.pf_solve(nx, ny, nz, h, (0.0, 0.0, 0.0), np.full(n, 78.5), np.ones(n, np.uint8), np.zeros((0, 4)),
+                       0.0, _LC_V * Tv, [1, -1, 0], [1e-3, 1e-3, 1e-3], [_LC_SALT, _LC_SALT, 55.5], 78.5, lc,
+                       tol_outer=1e-16, lin_tol=1e-14, max_outer=200, fixed=fixed, fixed_phi_V=fixed_phi_V)
+    assert out["status"] == 0
+    kd2 = orc.lam() * 2 * _LC_SALT * orc.molar_to_per_A3() / 78.5
+    return out, kd2
+
+
+@pytest.mark.parametrize("lc", [1.2, 2.0])
+def test_linearised_pf_slab_closed_form(orc, lc):
+    """Eq. (2) in the Debye-Hueckel limit on a slab with mirror sides: the nonlinear iteration's phi and Psi
+    equal the exact discrete solution of the linearised PF pair built from the roots of its characteristic
+    polynomial (two decay rates; lc = 2 A makes them complex).  This pins the off-diagonal couplings
+    eps_s lc^2/h^2 of the PF1 rows (Eq. 12), the mirror doubling on their sides and Psi = 0 on the planes (Eq. 14)."""
+    nx, ny, nz, h = 3, 2, 41, 0.5
+    out, kd2 = _lc_slab_solve(orc, nx, ny, nz, h, lc)
+    f, psi, Ms = _linear_pf_slab_exact(nz - 1, h, lc, kd2, _LC_V)
+    got = out["phi_hat"].reshape(nz, ny, nx)
+    gpsi = out["Psi"].reshape(nz, ny, nx)
+    np.testing.assert_allclose(got, np.broadcast_to(f[:, None, None], got.shape), rtol=0, atol=2e-10 * _LC_V)
+    np.testing.assert_allclose(gpsi, np.broadcast_to(psi[:, None, None], gpsi.shape), rtol=0,
+                               atol=1e-9 * np.abs(psi).max())
+    # the correlation term matters here: the Debye-Hueckel profile (lc = 0) is far from this one
+    f0, _, _ = _linear_pf_slab_exact(nz - 1, h, 1e-6, kd2, _LC_V)
+    assert np.abs(f - f0).max() > 1e-2 * _LC_V
+
+
+def test_linearised_pf_transverse_mode(orc):
+    """The same pair for phi = V cos(pi i/(nx-1)) cos(2 pi j/(ny-1)) held on the upper plane (fixed nodes): the
+    solution keeps that transverse factor, an eigenvector of the mirrored x/y couplings with eigenvalue lam_t,
+    and its z profile follows from lc^2 M^2 - M + kD^2 = 0 with M = (r - 2 + 1/r)/h^2 - lam_t.  Pins the x/y
+    couplings of the PF1 rows and their mirror ghosts."""
+    nx, ny, nz, h, lc = 5, 5, 33, 0.5, 1.2
+    Tv = orc.thermal_voltage()
+    i = np.arange(nx)
+    j = np.arange(ny)
+    X = np.cos(np.pi * i / (nx - 1))
+    Y = np.cos(2 * np.pi * j / (ny - 1))
+    lam_t = (2 - 2 * np.cos(np.pi / (nx - 1))) / h ** 2 + (2 - 2 * np.cos(2 * np.pi / (ny - 1))) / h ** 2
+    fixed = np.zeros((nz, ny, nx), np.uint8)
+    fixed[-1] = 1
+    fval = np.zeros((nz, ny, nx))
+    fval[-1] = _LC_V * Tv * Y[:, None] * X[None, :]
+    out, kd2 = _lc_slab_solve(orc, nx, ny, nz, h, lc, fixed.ravel(), fval.ravel())
+    f, psi, _ = _linear_pf_slab_exact(nz - 1, h, lc, kd2, _LC_V, lam_t)
+    exact = f[:, None, None] * Y[None, :, None] * X[None, None, :]
+    epsi = psi[:, None, None] * Y[None, :, None] * X[None, None, :]
+    np.testing.assert_allclose(out["phi_hat"].reshape(nz, ny, nx), exact, rtol=0, atol=2e-10 * _LC_V)
+    np.testing.assert_allclose(out["Psi"].reshape(nz, ny, nx), epsi, rtol=0, atol=1e-9 * np.abs(psi).max())
+
+
+def test_linearised_pf_continuum_decay_rates(orc):
+    """The discrete decay rates of the slab solution converge at second order to the continuum ones of
+    lc^2 k^4 - k^2 + kD^2 = 0, k^2 = (1 +- sqrt(1 - 4 lc^2 kD^2)) / (2 lc^2) (Eq. 2 linearised)."""
+    lc = 1.2
+    kd2 = orc.lam() * 2 * _LC_SALT * orc.molar_to_per_A3() / 78.5
+    cont = [math.sqrt((1 + s * math.sqrt(1 - 4 * lc * lc * kd2)) / (2 * lc * lc)) for s in (1, -1)]
+    errs = []
+    for h in (0.5, 0.25):
+        _, _, Ms = _linear_pf_slab_exact(int(round(20 / h)), h, lc, kd2, _LC_V)
+        disc = []
+        for M in Ms:
+            q = 2.0 + M.real * h * h
+            r = (q - math.sqrt(q * q - 4.0)) / 2.0
+            disc.append(-math.log(r) / h)
+        errs.append(max(abs(a - b) / b for a, b in zip(disc, cont)))
+    assert errs[0] < 2e-2
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
 # ---------------------------------------------------------------- conjugate gradients for the symmetric systems
 def _side_weights(nx, ny, nz):
     """1/2 for every x or y side a node lies on: the mirror ghost doubles a side row's inward coupling."""
