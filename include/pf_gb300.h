@@ -263,27 +263,32 @@ pf_status pf_profile_get(pf_grid* g, pf_profile* out);
  * allocate device memory when they need the step -- an application that owns all device memory
  * through its own arena or pool, or code running where a cudaMalloc is not allowed or would stall.
  *
- * pf_fermi_noalloc evaluates Eq. (1) at n nodes from a given potential, like the final step of
- * pf_nonlinear_solve: for solvent nodes it finds the void fraction Gamma of the Fermi-like
- * distributions and writes C_M (mol/L, species-major, n entries per species), S = ln(Gamma/Gamma^B)
- * and Gamma; non-solvent nodes get zeros.  phi_V (volts, n entries), solvent (n bytes, 1 = solvent),
- * C_M, S and Gamma are DEVICE pointers of the current device; S or Gamma may be NULL; species and
- * T_K are as in pf_coeffs.  The work is issued on cuda_stream (NULL = legacy default stream) and the
- * call returns after it has finished.
+ * pf_fermi_noalloc computes, at n nodes and from a given potential, the same quantities as the final
+ * step of pf_nonlinear_solve: at each solvent node it finds the void fraction Gamma of the Fermi-like
+ * ion and water distributions and writes the concentrations C_M (mol/L, species-major, n entries per
+ * species), the steric potential S = ln(Gamma/Gamma^B) and Gamma; non-solvent nodes get zeros.
+ * phi_V (volts, n entries), solvent (n bytes, 1 = solvent), C_M, S and Gamma are DEVICE pointers of
+ * the current device; S or Gamma may be NULL, C_M may not; species and T_K are as in pf_coeffs.
+ * warm_start = 1 starts each solvent node's root search from the ln Gamma that the previous call left
+ * in the scratch array at that node (useful when a caller iterates on the same n nodes, as the
+ * library's own nonlinear loop does); 0 starts from the bath value.  Both give the same root to the
+ * search's tolerance, and any scratch contents are safe as a start.
  *
- * It allocates nothing: its scratch (one double per node and a failure flag) is a fixed array of
- * PF_FERMI_NOALLOC_MAX_NODES + 1 doubles (8 MiB) that every GPU loading the library holds until the
- * process exits.  n above PF_FERMI_NOALLOC_MAX_NODES is rejected with PF_E_INVAL.  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the one array: each call clears
- * the failure flag it needs, but calls whose GPU work overlaps (different streams, or threads without
- * ordering) race on the scratch and must be serialised by the caller.
+ * It allocates nothing: its scratch (one double of ln Gamma per node and a failure flag) is a fixed
+ * array of PF_FERMI_NOALLOC_MAX_NODES + 1 doubles (8 MiB) that every GPU loading the library holds
+ * until the process exits.  n above PF_FERMI_NOALLOC_MAX_NODES is rejected with PF_E_INVAL.  The
+ * first call on each device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current.  The work is issued on cuda_stream (NULL = legacy default stream); every call
+ * then copies the failure flag to the host and synchronises that stream, so the call returns after
+ * its work has finished and cannot be made while the stream is being captured.  All calls share the
+ * one array: each call clears the failure flag it needs, but calls whose GPU work overlaps (different
+ * streams, or threads without ordering) race on the scratch and must be serialised by the caller.
  * Returns PF_OK, PF_E_INVAL, PF_E_GAMMA (a root was not found) or PF_E_CUDA; pf_last_error() has
  * the message. */
 #define PF_FERMI_NOALLOC_MAX_NODES (1L << 20)
 pf_status pf_fermi_noalloc(long n, const double* phi_V, const uint8_t* solvent, int n_species,
-                           const pf_species* species, double T_K, double* C_M, double* S, double* Gamma,
-                           void* cuda_stream);
+                           const pf_species* species, double T_K, int warm_start, double* C_M, double* S,
+                           double* Gamma, void* cuda_stream);
 
 /* Frees the grid and all its device memory.  NULL is accepted. */
 pf_status pf_destroy_grid(pf_grid* g);

@@ -95,7 +95,7 @@ SIGNATURES = {
     "pf_profile_get": (_I, [_VP, ctypes.POINTER(pf_profile)]),
     "pf_last_error": (ctypes.c_char_p, []),
     "pf_selftest_wait_timeout": (_I, [ctypes.c_ulonglong, _VP]),
-    "pf_fermi_noalloc": (_I, [ctypes.c_long, _VP, _VP, _I, ctypes.POINTER(pf_species), _D, _VP, _VP, _VP, _VP]),
+    "pf_fermi_noalloc": (_I, [ctypes.c_long, _VP, _VP, _I, ctypes.POINTER(pf_species), _D, _I, _VP, _VP, _VP, _VP]),
     "pf_batch_create": (_I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
     "pf_batch_set_tiles_per_block": (_I, [_VP, _I]),
     "pf_batch_set_tiling": (_I, [_VP, _I, _I]),

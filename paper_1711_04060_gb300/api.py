@@ -252,17 +252,19 @@ def pf_profile_get(grid):
     return out
 
 
-def pf_fermi_noalloc(phi_V, solvent, species, C_M, S=None, Gamma=None, T_K=298.15, cuda_stream=None, allow=()):
-    """Eq. (1) on caller-owned CUDA tensors without any device allocation (see include/pf_gb300.h):
-    phi_V (float64, volts), solvent (uint8) -> C_M (float64, species-major), S, Gamma."""
+def pf_fermi_noalloc(phi_V, solvent, species, C_M, S=None, Gamma=None, T_K=298.15, warm_start=False,
+                     cuda_stream=None, allow=()):
+    """The pointwise Fermi/steric step on caller-owned CUDA tensors without any device allocation (see
+    include/pf_gb300.h): phi_V (float64, volts), solvent (uint8) -> C_M (float64, species-major), S, Gamma;
+    warm_start starts each node's root search from the previous call's ln Gamma there."""
     n = phi_V.numel()
     sp = (B.pf_species * len(species))()
     for i, s_ in enumerate(species):
         sp[i].z, sp[i].radius_A, sp[i].bulk_M = int(s_.z), float(s_.radius_A), float(s_.bulk_M)
     ptr = lambda a: ctypes.c_void_p(a.data_ptr()) if a is not None else None  # noqa: E731
     stream = _torch_stream() if cuda_stream is None else ctypes.c_void_p(cuda_stream)
-    st = B.load().pf_fermi_noalloc(n, ptr(phi_V), ptr(solvent), len(species), sp, float(T_K), ptr(C_M), ptr(S),
-                                   ptr(Gamma), stream)
+    st = B.load().pf_fermi_noalloc(n, ptr(phi_V), ptr(solvent), len(species), sp, float(T_K), int(bool(warm_start)),
+                                   ptr(C_M), ptr(S), ptr(Gamma), stream)
     return _check(st, allow)
 
 

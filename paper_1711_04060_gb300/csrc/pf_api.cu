@@ -640,6 +640,52 @@ pf_status outer_stage3(pf_grid* g, OuterUpdate& u, int m, double omega, bool sto
 
 }  // namespace pfi
 
+// Species constants of Eq. (1) from the caller's species list (Table 1 constants): v_i = 4 pi a_i^3 / 3,
+// v0 = the mean volume over all species, p_i = v_i / v0, Gamma^B = 1 - sum_i v_i cB_i, lambda, the thermal
+// voltage k_B T / e and the mol/L -> A^-3 factor.  Returns nullptr, or a message when the list is invalid
+// (radius <= 0, bulk < 0, Gamma^B <= 0 or a charged bath).
+namespace pf {
+const char* species_params(int ns, const pf_species* species, double T_K, SpeciesParams* out, double* tv,
+                           double* molar_out) {
+  if (ns < 1 || ns > PF_MAX_SPECIES || !species) return "need 1..PF_MAX_SPECIES species";
+  if (!(T_K > 0)) return "need T > 0";
+  const double molar = NAVO * 1e-27;
+  double v[PF_MAX_SPECIES], v0 = 0.0, gB = 1.0, q = 0.0, qs = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    const pf_species& s = species[i];
+    if (!(s.radius_A > 0) || !(s.bulk_M >= 0)) return "species need radius > 0 and bulk >= 0";
+    v[i] = 4.0 * M_PI * s.radius_A * s.radius_A * s.radius_A / 3.0;
+    v0 += v[i];
+  }
+  v0 /= ns;
+  SpeciesParams sp{};
+  sp.ns = ns;
+  for (int i = 0; i < ns; ++i) {
+    const pf_species& s = species[i];
+    const double cB = s.bulk_M * molar;
+    sp.z[i] = s.z;
+    sp.p[i] = v[i] / v0;
+    sp.lvc[i] = cB > 0 ? log(v[i] * cB) : -INFINITY;
+    sp.lcB[i] = cB > 0 ? log(cB) : -INFINITY;
+    sp.inv_v[i] = 1.0 / v[i];
+    sp.inv_p[i] = 1.0 / sp.p[i];
+    if (cB > 0) sp.lnn += 1.0;
+    gB -= v[i] * cB;
+    q += s.z * cB;
+    qs += fabs((double)s.z) * cB;
+  }
+  if (!(gB > 0)) return "bulk void fraction Gamma^B <= 0";
+  if (fabs(q) > 1e-12 * (qs > 0 ? qs : 1.0)) return "bath is not electroneutral";
+  sp.lgB = log(gB);
+  sp.lnn = log(1.0 + sp.lnn);  // ln(n + 1) over the species present
+  sp.lam = QE * QE / (EPS0 * KB * T_K * 1e-10);
+  *out = sp;
+  *tv = KB * T_K / QE;
+  *molar_out = molar;
+  return nullptr;
+}
+}  // namespace pf
+
 // Sets the message that pf_last_error returns on this thread (used by entry points in other files).
 void pf_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
 
@@ -759,41 +805,13 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
   if (!(c->eps_s > 0) || !(c->lc_A >= 0) || !(c->T_K > 0)) return fail(PF_E_INVAL, "need eps_s > 0, lc >= 0, T > 0");
   for (long i = 0; i < g->N; ++i)
     if (!(c->eps[i] > 0) || c->solvent[i] > 1) return fail(PF_E_INVAL, "eps must be > 0 and solvent 0/1");
-  // species constants of Eq. (1): v_i = 4 pi a^3/3, v0 = mean volume, p_i = v_i/v0, Gamma^B = 1 - sum v cB
-  const double molar = NAVO * 1e-27;
-  double v[PF_MAX_SPECIES], v0 = 0.0, gB = 1.0, q = 0.0, qs = 0.0;
-  const int ns = c->n_species;
-  for (int i = 0; i < ns; ++i) {
-    const pf_species& s = c->species[i];
-    if (!(s.radius_A > 0) || !(s.bulk_M >= 0)) return fail(PF_E_INVAL, "species need radius > 0 and bulk >= 0");
-    v[i] = 4.0 * M_PI * s.radius_A * s.radius_A * s.radius_A / 3.0;
-    v0 += v[i];
-  }
-  v0 /= ns;
   pf::SpeciesParams sp{};
-  sp.ns = ns;
-  for (int i = 0; i < ns; ++i) {
-    const pf_species& s = c->species[i];
-    const double cB = s.bulk_M * molar;
-    sp.z[i] = s.z;
-    sp.p[i] = v[i] / v0;
-    sp.lvc[i] = cB > 0 ? log(v[i] * cB) : -INFINITY;
-    sp.lcB[i] = cB > 0 ? log(cB) : -INFINITY;
-    sp.inv_v[i] = 1.0 / v[i];
-    sp.inv_p[i] = 1.0 / sp.p[i];
-    if (cB > 0) sp.lnn += 1.0;
-    gB -= v[i] * cB;
-    q += s.z * cB;
-    qs += fabs((double)s.z) * cB;
-  }
-  if (!(gB > 0)) return fail(PF_E_INVAL, "bulk void fraction Gamma^B <= 0");
-  if (fabs(q) > 1e-12 * (qs > 0 ? qs : 1.0)) return fail(PF_E_INVAL, "bath is not electroneutral");
-  sp.lgB = log(gB);
-  sp.lnn = log(1.0 + sp.lnn);  // ln(n + 1) over the species present
+  double tv = 0.0, molar = 0.0;
+  if (const char* why = pf::species_params(c->n_species, c->species, c->T_K, &sp, &tv, &molar))
+    return fail(PF_E_INVAL, why);
   g->T = c->T_K;
-  g->Tv = KB * g->T / QE;
-  g->lam = QE * QE / (EPS0 * KB * g->T * 1e-10);
-  sp.lam = g->lam;
+  g->Tv = tv;
+  g->lam = sp.lam;
   g->sp = sp;
   g->molar = molar;
   g->eps_s = c->eps_s;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/pf_gb300.h"
+
 namespace pf {
 
 constexpr int TX = 32;           // tile width in x (one warp per row)
@@ -91,6 +93,11 @@ struct SpeciesParams {
   double lnn;           // ln(1 + number of species with cB_i > 0)
   double lam;           // lambda
 };
+
+// host: species constants of Eq. (1) from a caller's species list (nullptr, or why the list is invalid);
+// tv = k_B T / e in volts, molar = the mol/L -> A^-3 factor
+const char* species_params(int ns, const pf_species* species, double T_K, SpeciesParams* out, double* tv,
+                           double* molar);
 
 int tiles_for(int nx, int ny, int nz, int zc = ZC);
 int max_partial_blocks();

@@ -644,18 +644,17 @@ template cudaError_t launch_init_zero<double>(const double*, const Geom&, double
 }  // namespace pf
 
 // ====================================================================================================
-// Entry point that allocates nothing: the pointwise Fermi/steric step of Eq. (1) on caller arrays.
+// Entry point that allocates nothing: the pointwise Fermi/steric step on caller arrays.
 //
 // Some callers cannot allocate device memory at the moment they need this step: a host application
 // that hands the library a fixed device arena, or code that runs where cudaMalloc is not allowed or
 // would stall (a memory pool owned by another runtime, a latency-critical loop).  This variant of
-// k_fermi keeps its scratch -- each node's ln Gamma and the root-failure flag -- in a file-scope device
-// array of fixed size instead of in a pf_grid, so a call needs only the caller's input and output
-// arrays.  The paper has no counterpart: it is a property of this library's interface only.
+// k_fermi keeps its scratch -- each node's ln Gamma, the warm start of the next call, and the
+// root-failure flag -- in a file-scope device array of fixed size instead of in a pf_grid, so a call
+// needs only the caller's input and output arrays.  The paper has no counterpart: it is a property of
+// this library's interface only.
 // ====================================================================================================
 #include <mutex>
-
-#include "../../include/pf_gb300.h"
 
 void pf_internal_set_error(const char* msg);  // pf_api.cu: the message pf_last_error returns
 
@@ -665,10 +664,12 @@ namespace pf {
 static __device__ __align__(256) double g_fermi_scratch[PF_FERMI_NOALLOC_MAX_NODES + 1];
 
 // Same arithmetic as k_fermi: phi arrives in volts (phi_hat = phi * inv_tv), C leaves in mol/L; arrays are
-// compact (x fastest, N = n entries per field).
+// compact (x fastest, n entries per field).  Like k_fermi's ulast, the scratch holds each solvent node's
+// ln Gamma: read as the Newton start when warm != 0 (fermi_point clamps any start into its bracket, so
+// stale or foreign contents only cost iterations), rewritten with the new root.
 __global__ void k_fermi_noalloc(const double* __restrict__ phi_V, const uint8_t* __restrict__ solvent, long n,
-                                SpeciesParams sp, double inv_tv, double inv_molar, double* C, double* S, double* G,
-                                double* scratch) {
+                                SpeciesParams sp, double inv_tv, double inv_molar, int warm, double* C, double* S,
+                                double* G, double* scratch) {
   double* ulast = scratch;
   unsigned long long* flag = reinterpret_cast<unsigned long long*>(scratch + PF_FERMI_NOALLOC_MAX_NODES);
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < n; c += (long)gridDim.x * blockDim.x) {
@@ -677,12 +678,11 @@ __global__ void k_fermi_noalloc(const double* __restrict__ phi_V, const uint8_t*
     FermiOut fo;
     bool ok = false;
     if (sol) {
-      ok = fermi_point(sp, ph, sp.lgB, fo);
+      ok = fermi_point(sp, ph, warm ? ulast[c] : sp.lgB, fo);
       if (!ok) atomicExch(flag, 1ull);
       else ulast[c] = fo.u;
     }
-    for (int s = 0; s < sp.ns; ++s)
-      if (C) C[s * n + c] = (sol && ok) ? fo.C[s] * inv_molar : 0.0;
+    for (int s = 0; s < sp.ns; ++s) C[s * n + c] = (sol && ok) ? fo.C[s] * inv_molar : 0.0;
     if (S) S[c] = (sol && ok) ? fo.S : 0.0;
     if (G) G[c] = (sol && ok) ? fo.G : 0.0;
   }
@@ -704,44 +704,20 @@ pf_status noalloc_fail(pf_status s, const char* msg) {
 extern "C" {
 
 pf_status pf_fermi_noalloc(long n, const double* phi_V, const uint8_t* solvent, int n_species,
-                           const pf_species* species, double T_K, double* C_M, double* S, double* Gamma,
-                           void* cuda_stream) {
+                           const pf_species* species, double T_K, int warm_start, double* C_M, double* S,
+                           double* Gamma, void* cuda_stream) {
   using namespace pf;
   if (n < 1 || n > PF_FERMI_NOALLOC_MAX_NODES)
     return noalloc_fail(PF_E_INVAL, "pf_fermi_noalloc: n must be between 1 and PF_FERMI_NOALLOC_MAX_NODES");
-  if (!phi_V || !solvent || !species || n_species < 1 || n_species > PF_MAX_SPECIES || !(T_K > 0))
-    return noalloc_fail(PF_E_INVAL, "pf_fermi_noalloc: bad arguments");
-  // species constants of Eq. (1), as pf_set_coeffs computes them (Table 1 constants)
-  const double kb = 1.38e-23, qe = 1.602e-19, eps0 = 8.85e-12, molar = 6.02214076e23 * 1e-27;
+  if (!phi_V || !solvent || !C_M || (warm_start != 0 && warm_start != 1))
+    return noalloc_fail(PF_E_INVAL, "pf_fermi_noalloc: phi_V, solvent and C_M are required, warm_start is 0 or 1");
   SpeciesParams sp{};
-  double v[PF_MAX_SPECIES], v0 = 0.0, gB = 1.0, q = 0.0, qs = 0.0;
-  for (int i = 0; i < n_species; ++i) {
-    if (!(species[i].radius_A > 0) || !(species[i].bulk_M >= 0))
-      return noalloc_fail(PF_E_INVAL, "pf_fermi_noalloc: species need radius > 0 and bulk >= 0");
-    v[i] = 4.0 * M_PI * species[i].radius_A * species[i].radius_A * species[i].radius_A / 3.0;
-    v0 += v[i];
+  double tv = 0.0, molar = 0.0;
+  if (const char* why = species_params(n_species, species, T_K, &sp, &tv, &molar)) {
+    static thread_local char msg[160];
+    snprintf(msg, sizeof msg, "pf_fermi_noalloc: %s", why);
+    return noalloc_fail(PF_E_INVAL, msg);
   }
-  v0 /= n_species;
-  sp.ns = n_species;
-  for (int i = 0; i < n_species; ++i) {
-    const double cB = species[i].bulk_M * molar;
-    sp.z[i] = species[i].z;
-    sp.p[i] = v[i] / v0;
-    sp.lvc[i] = cB > 0 ? log(v[i] * cB) : -INFINITY;
-    sp.lcB[i] = cB > 0 ? log(cB) : -INFINITY;
-    sp.inv_v[i] = 1.0 / v[i];
-    sp.inv_p[i] = 1.0 / sp.p[i];
-    if (cB > 0) sp.lnn += 1.0;
-    gB -= v[i] * cB;
-    q += species[i].z * cB;
-    qs += fabs((double)species[i].z) * cB;
-  }
-  if (!(gB > 0)) return noalloc_fail(PF_E_INVAL, "pf_fermi_noalloc: bulk void fraction Gamma^B <= 0");
-  if (fabs(q) > 1e-12 * (qs > 0 ? qs : 1.0)) return noalloc_fail(PF_E_INVAL, "pf_fermi_noalloc: bath not neutral");
-  sp.lgB = log(gB);
-  sp.lnn = log(1.0 + sp.lnn);
-  sp.lam = qe * qe / (eps0 * kb * T_K * 1e-10);
-  const double tv = kb * T_K / qe;
 
   // set-up, once per device and with that device current: the device address of the scratch array
   int dev = 0;
@@ -759,12 +735,13 @@ pf_status pf_fermi_noalloc(long n, const double* phi_V, const uint8_t* solvent, 
     scratch = g_noalloc_ptr[dev];
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  // the failure flag must start at zero; the ln Gamma part is written before it is read
+  // the failure flag must start at zero; the ln Gamma part is only a starting point (read when warm_start)
   if (cudaMemsetAsync(scratch + PF_FERMI_NOALLOC_MAX_NODES, 0, sizeof(double), s) != cudaSuccess)
     return noalloc_fail(PF_E_CUDA, "pf_fermi_noalloc: clearing the flag failed");
   long blocks = (n + 255) / 256;
   if (blocks > 8192) blocks = 8192;
-  k_fermi_noalloc<<<(int)blocks, 256, 0, s>>>(phi_V, solvent, n, sp, 1.0 / tv, 1.0 / molar, C_M, S, Gamma, scratch);
+  k_fermi_noalloc<<<(int)blocks, 256, 0, s>>>(phi_V, solvent, n, sp, 1.0 / tv, 1.0 / molar, warm_start, C_M, S,
+                                              Gamma, scratch);
   if (cudaGetLastError() != cudaSuccess) return noalloc_fail(PF_E_CUDA, "pf_fermi_noalloc: launch failed");
   unsigned long long flag = 0;
   if (cudaMemcpyAsync(&flag, scratch + PF_FERMI_NOALLOC_MAX_NODES, sizeof(flag), cudaMemcpyDeviceToHost, s) !=

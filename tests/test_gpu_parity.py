@@ -202,6 +202,46 @@ def test_nonlinear_33_single_pore(api, orc, precision):
         assert abs(rep["outer_iters"] - ref["report"]["outer_iters"]) <= 1
 
 
+_MULTI = {}
+
+
+def _multichunk_problem():
+    """65^3 channel at h = 1 A on [-32, 32]^3: 63 interior z-planes, i.e. two z-chunks of the stencil tiles,
+    three x-tiles (the last one ragged: one column) and nine y-tiles per plane."""
+    return W.channel_problem(65, box_half=32.0, name="pf_65_single_pore_h1")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nonlinear_65_crosses_z_chunks(api, orc, precision):
+    """The whole nonlinear iteration on a grid whose tiles span two z-chunks (plane ring restarted mid-column,
+    partial sums across chunks) against the oracle element by element: phi to 1e-8 (FP64) / 1e-6 (mixed),
+    every concentration, S and Gamma to 1e-6.  The oracle's solve (about a minute) is shared by both
+    precisions."""
+    prob = _multichunk_problem()
+    if "ref" not in _MULTI:
+        _MULTI["ref"] = orc.pf_solve_problem(prob, tol_outer=1e-11, lin_tol=1e-12)
+    ref = _MULTI["ref"]
+    assert ref["status"] == 0
+    g = prob.grid
+    grid = api.Grid.for_problem(prob)
+    prec = api.PF_FP64 if precision == "fp64" else api.PF_MIXED
+    out, rep = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=prec))
+    grid.close()
+    assert rep["status"] == 0
+    tol = TOL_FP64 if precision == "fp64" else TOL_MIXED
+    assert _rel(out["phi_V"], ref["phi_V"]) < tol
+    ns = len(prob.species)
+    C = out["C_M"].reshape(ns, g.n)
+    for i in range(ns):
+        assert _rel(C[i], ref["C_M"][i]) < TOL_CONC, (i, _rel(C[i], ref["C_M"][i]))
+    sol = prob.solvent == 1
+    assert _rel(out["S"][sol], ref["S"][sol], floor=1.0) < TOL_CONC
+    assert _rel(out["Gamma"][sol], ref["Gamma"][sol]) < TOL_CONC
+    assert _rel(out["Psi"], ref["Psi"]) < (TOL_FP64 if precision == "fp64" else TOL_MIXED) * 10
+    if precision == "fp64":
+        assert abs(rep["outer_iters"] - ref["report"]["outer_iters"]) <= 1
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("depth,forcing", [(5, 0.0), (5, 0.1), (1, 0.0), (0, 0.1)])
 def test_nonlinear_accelerated_same_fixed_point(api, orc, precision, depth, forcing):
