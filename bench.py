@@ -76,6 +76,12 @@ def parse():
     ap.add_argument("--no-accel", action="store_true", help="skip the Anderson-accelerated comparison solve")
     ap.add_argument("--no-cg", action="store_true", help="skip the conjugate-gradient comparison solves")
     ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--cpu-nodes", type=int, default=100000, help="nodes of the oracle's timed pointwise-step sample")
+    ap.add_argument("--no-tight", action="store_true", help="skip the tight-tolerance legs and their reference solve")
+    ap.add_argument("--tight-tol-outer", type=float, default=1e-8)
+    ap.add_argument("--tight-lin-tol", type=float, default=1e-10)
+    ap.add_argument("--e2e-steps", type=int, default=3, help="solves of the end-to-end leg (at most --steps)")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle checks of the returned solution")
     ap.add_argument("--accel-depth", type=int, default=0, help="Anderson depth of the timed solves (0: relaxation)")
     ap.add_argument("--serve-requests", type=int, default=16, help="requests of the serving sample (0: skip)")
     ap.add_argument("--serve-gap", type=float, default=0.25, help="mean inter-arrival time of the serving sample (s)")
@@ -214,32 +220,63 @@ def kernel_traffic(kind):
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(prob, phi_hat_sample, iters):
-    """Times the FP64 CPU oracle on a bounded sample of the workload: BiCGSTAB iterations on the
-    full-size PF2 operator and the pointwise Fermi step on sampled solvent nodes."""
+def cpu_info():
+    """Host threads available to this process and the CPU model (lscpu, else /proc/cpuinfo)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": cores, "model": model or "unknown", "machine": os.uname().machine}
+
+
+def oracle_sample(prob, phi_hat_sample, iters, all_cores=False):
+    """Times the FP64 CPU oracle on a bounded sample of the workload: one operator assembly, BiCGSTAB
+    iterations on the full-size operator and the pointwise Fermi step (a C loop) on sampled solvent nodes.
+    all_cores: the same source compiled with OpenMP (operator product, inner products, vector updates and
+    the node loop on every host thread); otherwise the single-threaded checker build."""
     import oracle
     oracle.build()
+    L = oracle.load(oracle.build_all_cores()) if all_cores else oracle.lib()
     g = prob.grid
     z = [s.z for s in prob.species]
-    sp = oracle.species_setup(z, [s.radius_A for s in prob.species], [s.bulk_M for s in prob.species])
-    t0 = time.perf_counter()
-    A = oracle.assemble_eps(g.nx, g.ny, g.nz, g.h, prob.eps)
-    t_asm = time.perf_counter() - t0
-    b = np.zeros(g.n)
-    b[g.nx * g.ny: -g.nx * g.ny] = 1.0
-    t0 = time.perf_counter()
-    oracle.bicgstab(g.nx, g.ny, g.nz, A, b, tol=1e-300, max_it=1)
-    t1 = time.perf_counter()
-    oracle.bicgstab(g.nx, g.ny, g.nz, A, b, tol=1e-300, max_it=1 + iters)
-    t2 = time.perf_counter()
-    t_iter = max((t2 - t1) - (t1 - t0), 1e-9) / iters
-    del A
-    t0 = time.perf_counter()
-    for ph in phi_hat_sample:
-        oracle.fermi_point(sp, z, float(ph))
-    t_node = (time.perf_counter() - t0) / len(phi_hat_sample)
-    return {"t_iter": t_iter, "t_node": t_node, "t_asm": t_asm, "iters": iters, "nodes": len(phi_hat_sample),
-            "n_solvent": int(prob.solvent.sum())}
+    with oracle.using(L):
+        sp = oracle.species_setup(z, [s.radius_A for s in prob.species], [s.bulk_M for s in prob.species])
+        t0 = time.perf_counter()
+        A = oracle.assemble_eps(g.nx, g.ny, g.nz, g.h, prob.eps)
+        t_asm = time.perf_counter() - t0
+        b = np.zeros(g.n)
+        b[g.nx * g.ny: -g.nx * g.ny] = 1.0
+        t0 = time.perf_counter()
+        oracle.bicgstab(g.nx, g.ny, g.nz, A, b, tol=1e-300, max_it=1)
+        t1 = time.perf_counter()
+        oracle.bicgstab(g.nx, g.ny, g.nz, A, b, tol=1e-300, max_it=1 + iters)
+        t2 = time.perf_counter()
+        t_iter = max((t2 - t1) - (t1 - t0), 1e-9) / iters
+        del A
+        ph = np.ascontiguousarray(phi_hat_sample, dtype=np.float64)
+        t0 = time.perf_counter()
+        oracle.fermi_nodes(sp, z, ph)
+        t_node = (time.perf_counter() - t0) / len(ph)
+    threads = int(os.environ.get("OMP_NUM_THREADS", cpu_info()["nproc"])) if all_cores else 1
+    return {"t_iter": t_iter, "t_node": t_node, "t_asm": t_asm, "iters": iters, "nodes": len(ph),
+            "n_solvent": int(prob.solvent.sum()), "threads": threads}
 
 
 def oracle_solve_time(samp, outer, lin_iters):
@@ -247,30 +284,41 @@ def oracle_solve_time(samp, outer, lin_iters):
     return outer * (samp["n_solvent"] * samp["t_node"] + 2 * samp["t_asm"]) + lin_iters * samp["t_iter"]
 
 
+def sample_text(samp, n, outer, lin, scaled_by):
+    return (f"{samp['iters']} FP64 BiCGSTAB iterations on the full {n}^3 operator ({samp['t_iter']:.4f} s each), "
+            f"the pointwise step on {samp['nodes']} solvent nodes ({samp['t_node'] * 1e6:.3f} us each), one operator "
+            f"assembly ({samp['t_asm']:.3f} s), on {samp['threads']} thread(s); extrapolated to {scaled_by} of "
+            f"{outer} outer and {lin} BiCGSTAB iterations")
+
+
+def phi_sample(prob, n_nodes, seed=11):
+    """Potentials for the oracle's timed pointwise step: seeded, uniform over [-8, 8] k_BT/e."""
+    from paper_1711_04060_gb300 import workloads as W
+    return W.uniform(W.substream(seed, 1), n_nodes, -8.0, 8.0)
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if world > 1 and rank != 0:
         return
     prob = workload(args.n)
-    rng_phi = np.linspace(-8.0, 8.0, 4000)
+    ph = phi_sample(prob, args.cpu_nodes)
+    info = cpu_info()
     t_steps = []
     samp = None
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        samp = oracle_sample(prob, rng_phi, args.cpu_iters)
-        el = time.perf_counter() - t0
+        samp = oracle_sample(prob, ph, args.cpu_iters, all_cores=True)
         if i >= args.warmup:
             t_steps.append(oracle_solve_time(samp, REF_WORK["outer"], REF_WORK["lin_iters"]))
     T = float(np.mean(t_steps))
     value = 1.0 / T
-    sample = (f"{args.cpu_iters} FP64 BiCGSTAB iterations of the oracle on the full {args.n}^3 operator plus the "
-              f"pointwise Fermi step on {len(rng_phi)} nodes per step, scaled to one solve of "
-              f"{REF_WORK['outer']} outer and {REF_WORK['lin_iters']} BiCGSTAB iterations")
+    sample = sample_text(samp, args.n, REF_WORK["outer"], REF_WORK["lin_iters"], "one FP64 solve")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": T * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(args),
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1, "sample": sample},
+            "config": config_of(args), "precision": "fp64 (CPU oracle)",
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": samp["threads"],
+                             "cpu": info, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -286,8 +334,8 @@ def config_of(args):
           else f"working set {ws / 1e6:.0f} MB fits in L2: not an HBM measurement")
     return {"workload": f"pf_{args.n}_four_pores_NaCaCl", "grid": f"{args.n}^3", "h_A": 64.0 / (args.n - 1),
             "species": "Na+ 0.1 M, Ca2+ 1 mM, Cl- 0.102 M, water 55.5 M", "charges": 48,
-            "precision": args.precision, "tol_outer": args.tol_outer, "lin_tol": args.lin_tol,
-            "omega": 0.3, "accel_depth": args.accel_depth, "inner_tol": args.inner_tol, "l2": l2,
+            "tol_outer": args.tol_outer, "lin_tol": args.lin_tol,
+            "omega": 0.3, "accel_depth": args.accel_depth, "l2": l2,
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -375,6 +423,58 @@ def batch_sample(api, args, torch, dev):
             "speedup_vs_fp64_single": t_seq / t_batch, "phi_rel_vs_fp64_single": worst_phi}
 
 
+# ------------------------------------------------------------------ accuracy of a returned solution
+def rel_errors(phi, C, ref_phi, ref_C, ns):
+    """Max |phi - ref| over max |ref|, and per species max |C_i - ref_i| over max ref_i."""
+    C = C.reshape(ns, -1)
+    ref_C = ref_C.reshape(ns, -1)
+    return {"phi_rel": float(np.abs(phi - ref_phi).max() / np.abs(ref_phi).max()),
+            "conc_rel": [float(np.abs(C[i] - ref_C[i]).max() / np.abs(ref_C[i]).max()) for i in range(ns)]}
+
+
+def oracle_accuracy(prob, out, n_sample=4000):
+    """The returned solution against the CPU oracle: the oracle's pointwise step (Eq. 1) at sampled solvent
+    nodes of the returned potential against the returned C, S and Gamma; the PF2 equation at the fixed point
+    (Eq. 13 with phi_0 = phi: L_eps phi + s eps_s Psi = lambda rho_fix) with the oracle's operator at every
+    interior node, relative to the norm of its right-hand side with the Dirichlet lift; and PF1 (Eq. 12)
+    with the oracle's operator and the oracle's density of the returned potential at the sampled nodes."""
+    import oracle
+    g = prob.grid
+    N, ns = g.n, len(prob.species)
+    z = [s.z for s in prob.species]
+    sp = oracle.species_setup(z, [s.radius_A for s in prob.species], [s.bulk_M for s in prob.species])
+    Tv, lam, m = oracle.thermal_voltage(prob.T_K), oracle.lam(prob.T_K), oracle.molar_to_per_A3()
+    phat = out["phi_V"] / Tv
+    psi = out["Psi"]
+    interior = np.zeros(g.shape_zyx, bool)
+    interior[1:-1] = True
+    interior = interior.ravel()
+    sol = np.flatnonzero((prob.solvent == 1) & interior)
+    pick = sol[np.linspace(0, len(sol) - 1, n_sample).astype(np.int64)]
+    r = oracle.fermi_nodes(sp, z, phat[pick])
+    assert r["status"] == 0
+    C = out["C_M"].reshape(ns, N)
+    oc = r["C"] / m
+    acc = {"sampled_nodes": int(len(pick)),
+           "eq1_conc_rel": [float(np.abs(C[i, pick] - oc[i]).max() / np.abs(oc[i]).max()) for i in range(ns)],
+           "eq1_S_abs": float(np.abs(out["S"][pick] - r["S"]).max()),
+           "eq1_Gamma_rel": float(np.abs(out["Gamma"][pick] - r["Gamma"]).max() / np.abs(r["Gamma"]).max())}
+    A = oracle.assemble_eps(g.nx, g.ny, g.nz, g.h, prob.eps)
+    _, ffix = oracle.spread_charges(g.nx, g.ny, g.nz, g.h, g.origin, prob.charges, lam)
+    s = prob.solvent.astype(float)
+    res = oracle.dia_apply(g.nx, g.ny, g.nz, A, phat) + s * prob.eps_s * psi - ffix
+    phiD = np.where(interior, 0.0, phat)
+    lift = -oracle.dia_apply(g.nx, g.ny, g.nz, A, phiD)
+    del A
+    acc["pf2_residual_rel2"] = float(np.linalg.norm(res[interior]) / np.linalg.norm((ffix + lift)[interior]))
+    A1 = oracle.assemble_pf1(g.nx, g.ny, g.nz, g.h, prob.solvent, prob.eps_s, prob.lc_A)
+    r1 = oracle.dia_apply(g.nx, g.ny, g.nz, A1, psi)[pick]
+    del A1
+    rho = (np.asarray(z, float)[:, None] * r["C"]).sum(0)
+    acc["pf1_residual_rel_inf_sampled"] = float(np.abs(r1 + lam * rho).max() / np.abs(lam * rho).max())
+    return acc
+
+
 # ------------------------------------------------------------------ GPU arm
 def cg_sample(api, grid, prob, torch, dev, lin_tol):
     """Conjugate gradients (pf_linear_solve_cg) against BiCGSTAB, both FP64, on the bench grid's PF1 and
@@ -433,7 +533,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     grid = api.Grid.for_problem(prob, cuda_stream=stream.cuda_stream)
     out = {k: torch.zeros(m, dtype=torch.float64, device=dev)
-           for k, m in (("phi_V", N), ("C_M", ns * N), ("S", N), ("Gamma", N))}
+           for k, m in (("phi_V", N), ("C_M", ns * N), ("S", N), ("Gamma", N), ("Psi", N))}
     prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
     opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, accel_depth=args.accel_depth,
                        inner_tol=args.inner_tol)
@@ -476,8 +576,9 @@ def run_ours(args):
     ms = max_over_ranks(ms, world, dev)
     value = whole_job_rate(args.steps, world, ms / 1e3)
     clocks = clk.summary()
-    phi_mixed = out["phi_V"].cpu().numpy()
-    C_mixed = out["C_M"].cpu().numpy()
+    host = {k: v.cpu().numpy() for k, v in out.items()}
+    phi_mixed = host["phi_V"]
+    C_mixed = host["C_M"]
 
     # roofline of the dominant stencil kernel (by device time in the timed region)
     n_int = g.nx * g.ny * (g.nz - 2)
@@ -504,14 +605,20 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic (seeded channel geometry, wall charges and bath; no dataset)",
-            "config": config_of(args), "clocks": clocks, "gpu_launches": int(prof["launches"]),
+            "config": config_of(args), "precision": args.precision, "inner_tol": args.inner_tol,
+            "clocks": clocks, "gpu_launches": int(prof["launches"]),
             "roofline": roofline,
             "solve": {"outer_iters": reps[-1]["outer_iters"], "lin_iters": reps[-1]["lin_iters_total"],
                       "status": reps[-1]["status"], "delta": reps[-1]["delta"]},
             "kernels": kernels}
 
+    # the headline solution against the oracle (pointwise step at sampled nodes, PF2 / PF1 residuals)
+    if not args.no_accuracy and rank == 0:
+        line["accuracy_vs_oracle"] = oracle_accuracy(prob, host)
+
     # FP64 path on the same workload (solves/s and the mixed path's deviation from it)
     fp64_rep = None
+    host64 = None
     if not args.no_fp64 and args.precision == "mixed":
         o64 = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_FP64)
         out64 = {k: torch.zeros_like(v) for k, v in out.items()}
@@ -528,11 +635,14 @@ def run_ours(args):
         ms64 = e0.elapsed_time(e1)
         prof64 = grid.profile_get()
         grid.profile(False)
-        phi64 = out64["phi_V"].cpu().numpy()
-        C64 = out64["C_M"].cpu().numpy().reshape(ns, N)
+        host64 = {k: v.cpu().numpy() for k, v in out64.items()}
+        phi64 = host64["phi_V"]
+        C64 = host64["C_M"].reshape(ns, N)
         Cm = C_mixed.reshape(ns, N)
         line["fp64"] = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "outer_iters": fp64_rep["outer_iters"],
                         "lin_iters": fp64_rep["lin_iters_total"], "status": fp64_rep["status"]}
+        if not args.no_accuracy and rank == 0:
+            line["fp64"]["accuracy_vs_oracle"] = oracle_accuracy(prob, host64)
         line["accuracy_vs_fp64"] = {
             "phi_rel": float(np.abs(phi_mixed - phi64).max() / np.abs(phi64).max()),
             "conc_rel": float(max(np.abs(Cm[i] - C64[i]).max() / C64[i].max() for i in range(ns)))}
@@ -540,6 +650,44 @@ def run_ours(args):
         line["bicgstab_iteration_GBps"] = {"fp32_inner": iteration_gbps(prof, "fp32", n_int),
                                            "fp64": iteration_gbps(prof64, "fp64", n_int),
                                            "peak": peak, "unit": "GB/s"}
+
+    # tight tolerances: mixed and FP64 to tol_outer / lin_tol that meet the accuracy bars, timed, and every
+    # solution against a tighter FP64 reference (Anderson-accelerated: same fixed point, fewer outer steps)
+    if not args.no_tight and args.precision == "mixed":
+        def timed(o):
+            outs = {k: torch.zeros_like(v) for k, v in out.items()}
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rp = solve(o, outs)
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1), rp, {k: v.cpu().numpy() for k, v in outs.items()}
+
+        tt, tl = args.tight_tol_outer, args.tight_lin_tol
+        ms_m, rep_m, out_m = timed(api.nl_opts(tol_outer=tt, tol=tl, precision=api.PF_MIXED, inner_tol=args.inner_tol))
+        ms_d, rep_d, out_d = timed(api.nl_opts(tol_outer=tt, tol=tl, precision=api.PF_FP64))
+        ms_r, rep_r, out_r = timed(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=api.PF_FP64, accel_depth=5))
+        ref_phi, ref_C = out_r["phi_V"], out_r["C_M"]
+
+        def leg(ms, rp, o):
+            d = {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "outer_iters": rp["outer_iters"],
+                 "lin_iters": rp["lin_iters_total"], "status": rp["status"]}
+            d.update(rel_errors(o["phi_V"], o["C_M"], ref_phi, ref_C, ns))
+            return d
+
+        line["tight"] = {
+            "tol_outer": tt, "lin_tol": tl,
+            "reference": {"what": "FP64, Anderson depth 5 (same fixed point), tol_outer 1e-11, lin_tol 1e-12",
+                          "ms": ms_r, "outer_iters": rep_r["outer_iters"], "status": rep_r["status"]},
+            "mixed": leg(ms_m, rep_m, out_m), "fp64": leg(ms_d, rep_d, out_d),
+            "mixed_speedup_vs_fp64": ms_d / ms_m}
+        if not args.no_accuracy and rank == 0:
+            line["tight"]["mixed"]["accuracy_vs_oracle"] = oracle_accuracy(prob, out_m)
+        line["headline_vs_reference"] = {"mixed": rel_errors(phi_mixed, C_mixed, ref_phi, ref_C, ns)}
+        if host64 is not None:
+            line["headline_vs_reference"]["fp64"] = rel_errors(host64["phi_V"], host64["C_M"], ref_phi, ref_C, ns)
 
     # Anderson-accelerated solve of the same workload (same fixed point and stop test)
     if args.accel_depth == 0 and not args.no_accel:
@@ -565,9 +713,10 @@ def run_ours(args):
     # end to end through the public API with host buffers
     if not args.no_e2e:
         hout = {k: np.zeros(m) for k, m in (("phi_V", N), ("C_M", ns * N), ("S", N), ("Gamma", N))}
+        k_e2e = max(1, min(args.steps, args.e2e_steps))
         barrier()
         t0 = time.perf_counter()
-        for _ in range(max(1, args.steps)):
+        for _ in range(k_e2e):
             grid.set_problem(prob)
             solve(opts, hout)
         torch.cuda.synchronize(dev)
@@ -575,8 +724,8 @@ def run_ours(args):
         el = max_over_ranks(el, world, dev)
         h2d = prob.eps.nbytes + prob.solvent.nbytes + prob.charges.nbytes
         d2h = sum(v.nbytes for v in hout.values())
-        line["e2e"] = {"value": whole_job_rate(max(1, args.steps), world, el), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                       "d2h_bytes_per_step": int(d2h)}
+        line["e2e"] = {"value": whole_job_rate(k_e2e, world, el), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h), "steps": k_e2e}
 
     # conjugate gradients for the symmetric systems against BiCGSTAB (FP64 linear solves on this grid)
     if not args.no_cg and world == 1:
@@ -596,24 +745,22 @@ def run_ours(args):
         if not args.no_fp64:
             line["serving"]["fp64"] = serve_sample(api, args, api.PF_FP64)
 
-    # CPU oracle on a bounded sample (rank 0, one GPU only)
+    # CPU oracle on a bounded sample (rank 0, one GPU only): all host threads (OpenMP copy) and one thread
     if rank == 0 and world == 1 and not args.no_cpu:
-        phat = phi_mixed / 0.025683333333333336
-        sol = np.flatnonzero(prob.solvent)
-        pick = sol[np.linspace(0, len(sol) - 1, 4000).astype(np.int64)]
-        samp = oracle_sample(prob, phat[pick], args.cpu_iters)
+        ph = phi_sample(prob, args.cpu_nodes)
         if fp64_rep is not None:
             work_outer, work_lin = fp64_rep["outer_iters"], fp64_rep["lin_iters_total"]
         else:
             work_outer, work_lin = reps[-1]["outer_iters"], reps[-1]["lin_iters_total"]
-        T = oracle_solve_time(samp, work_outer, work_lin)
+        what = "this workload's FP64 solve"
+        sa = oracle_sample(prob, ph, args.cpu_iters, all_cores=True)
+        s1 = oracle_sample(prob, ph, args.cpu_iters, all_cores=False)
+        Ta, T1 = oracle_solve_time(sa, work_outer, work_lin), oracle_solve_time(s1, work_outer, work_lin)
         line["cpu_baseline"] = {
-            "value": 1.0 / T, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{samp['iters']} FP64 BiCGSTAB iterations on the full {args.n}^3 operator "
-                       f"({samp['t_iter']:.3f} s each), the Fermi step on {samp['nodes']} solvent nodes of this "
-                       f"solution ({samp['t_node'] * 1e6:.2f} us each), one operator assembly ({samp['t_asm']:.2f} s); "
-                       f"scaled to this workload's FP64 solve of {work_outer} outer and {work_lin} BiCGSTAB "
-                       f"iterations")}
+            "value": 1.0 / Ta, "unit": UNIT, "cores": sa["threads"], "kind": "oracle", "cpu": cpu_info(),
+            "sample": sample_text(sa, args.n, work_outer, work_lin, what),
+            "single_thread": {"value": 1.0 / T1, "unit": UNIT, "cores": 1,
+                              "sample": sample_text(s1, args.n, work_outer, work_lin, what)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -47,6 +47,23 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+_SO_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
+
+
+def build_all_cores(force: bool = False) -> str:
+    """The benchmark's all-cores timing copy: the same source compiled with -fopenmp, which turns on its
+    OpenMP pragmas (operator product, inner products, vector updates, the pointwise node loop).  Its
+    reductions run in another order, so it is never the checker: tests use build()."""
+    os.makedirs(os.path.dirname(_SO_OMP), exist_ok=True)
+    if force or not os.path.exists(_SO_OMP) or os.path.getmtime(_SO_OMP) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "pf_oracle.h"))):
+        tmp = _SO_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off",
+                               "-fno-fast-math", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO_OMP)
+    return _SO_OMP
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -65,6 +82,7 @@ def load(path):
     L.pfo_molar_to_per_A3.argtypes = []
     L.pfo_species_setup.argtypes = [_I, _PD, _PD, _PD, _PD, _PD, _PD, _PD]
     L.pfo_fermi_point.argtypes = [_I, _PD, _PD, _PD, _PD, _D, _D, _PD, _PD, _PD, _PI]
+    L.pfo_fermi_nodes.argtypes = [_I, _PD, _PD, _PD, _PD, _D, ctypes.c_long, _PD, _PD, _PD, _PD]
     L.pfo_assemble_eps.argtypes = [_I, _I, _I, _D, _PD, _PD, _PD]
     L.pfo_assemble_pf1.argtypes = [_I, _I, _I, _D, _PU8, _D, _D, _PD]
     L.pfo_dia_apply.argtypes = [_I, _I, _I, _PD, _PD, _PD]
@@ -137,6 +155,17 @@ def fermi_point(sp: dict, z, phi_hat: float):
     st = lib().pfo_fermi_point(n, _pd(z), _pd(sp["v"]), _pd(sp["p"]), _pd(sp["cB"]), sp["gammaB"],
                                float(phi_hat), _pd(C), ctypes.byref(S), ctypes.byref(G), ctypes.byref(it))
     return {"status": st, "C": C, "S": S.value, "Gamma": G.value, "iters": it.value}
+
+
+def fermi_nodes(sp: dict, z, phi_hat):
+    """Eq. (1) at every node of the array phi_hat: C (species-major, A^-3), S, Gamma and the status."""
+    z = _f64(z)
+    ph = _f64(phi_hat)
+    n, ns = len(ph), len(z)
+    C, S, G = np.zeros(ns * n), np.zeros(n), np.zeros(n)
+    st = lib().pfo_fermi_nodes(ns, _pd(z), _pd(sp["v"]), _pd(sp["p"]), _pd(sp["cB"]), sp["gammaB"], n, _pd(ph),
+                               _pd(C), _pd(S), _pd(G))
+    return {"status": st, "C": C.reshape(ns, n), "S": S, "Gamma": G}
 
 
 def assemble_eps(nx, ny, nz, h, eps, sigma=None):

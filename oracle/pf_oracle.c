@@ -21,6 +21,8 @@
  *     keep the zero-flux mirror of Eq. (4);
  *   - the fixed charges enter the PF2 right-hand side at whatever node type holds them;
  *   - Jacobi preconditioning is the right-preconditioned form of BiCGSTAB.
+ * The OpenMP pragmas are inert in the checker build (compiled without -fopenmp); only the
+ * benchmark's all-cores timing copy of this file is compiled with them.
  */
 #include "pf_oracle.h"
 
@@ -126,6 +128,24 @@ int pfo_fermi_point(int ns, const double* z, const double* v, const double* p, c
 }
 
 /* ---- 7-point FD operators in the diagonal storage of Section 4 --------------- */
+/* Eq. (1) at n nodes, one after another (the pointwise step of the Table 2 loop over a node list):
+ * C (species-major, n per species) in A^-3, S and Gamma; PFO_OK, or the largest status of a node that failed. */
+int pfo_fermi_nodes(int ns, const double* z, const double* v, const double* p, const double* cB, double gammaB,
+                    long n, const double* phi_hat, double* C, double* S, double* Gamma) {
+  int status = PFO_OK;
+  if (ns < 1 || ns > 64) return PFO_E_INVAL;
+#pragma omp parallel for schedule(static) reduction(max : status)
+  for (long c = 0; c < n; ++c) {
+    double Ci[64], s, g;
+    const int st = pfo_fermi_point(ns, z, v, p, cB, gammaB, phi_hat[c], Ci, &s, &g, NULL);
+    if (st > status) status = st;
+    for (int i = 0; i < ns; ++i) C[(long)i * n + c] = Ci[i];
+    S[c] = s;
+    Gamma[c] = g;
+  }
+  return status;
+}
+
 static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
 
 /* Eqs. (7), (13), (15)-(18): with a zero jump the SMIB rows at x_l, x_{l+1} are
@@ -188,6 +208,7 @@ int pfo_assemble_pf1(int nx, int ny, int nz, double h, const unsigned char* solv
 
 void pfo_dia_apply(int nx, int ny, int nz, const double* A, const double* x, double* y) {
   const long N = (long)nx * ny * nz, sy = nx, sz = (long)nx * ny;
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -205,12 +226,14 @@ void pfo_dia_apply(int nx, int ny, int nz, const double* A, const double* x, dou
 
 static double dot(long n, const double* a, const double* b) {
   double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
   for (long i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
 }
 
 static double norm_inf(long n, const double* a) {
   double m = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : m)
   for (long i = 0; i < n; ++i) if (fabs(a[i]) > m) m = fabs(a[i]);
   return m;
 }
@@ -255,16 +278,20 @@ int pfo_bicgstab(int nx, int ny, int nz, const double* A, const double* b, doubl
     const double rho = dot(N, rt, r); /* rho = rtilde . r */
     if (rho == 0.0) { status = PFO_E_BREAKDOWN; break; }
     if (it == 1) {
+#pragma omp parallel for schedule(static)
       for (long c = 0; c < N; ++c) p[c] = r[c]; /* first direction p = r */
     } else {
       const double beta = (rho / rho_prev) * (alpha / omega);
+#pragma omp parallel for schedule(static)
       for (long c = 0; c < N; ++c) p[c] = r[c] + beta * (p[c] - omega * v[c]);
     }
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < N; ++c) ph[c] = p[c] / A[c]; /* Jacobi: phat = M^-1 p */
     pfo_dia_apply(nx, ny, nz, A, ph, v); /* v = A phat */
     const double rtv = dot(N, rt, v);
     if (rtv == 0.0) { status = PFO_E_BREAKDOWN; break; }
     alpha = rho / rtv;
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < N; ++c) s[c] = r[c] - alpha * v[c];
     measure = PFO_MEASURE(s);
     if (PFO_CONVERGED(measure)) { /* early exit on s: x = x + alpha phat */
@@ -272,12 +299,15 @@ int pfo_bicgstab(int nx, int ny, int nz, const double* A, const double* b, doubl
       status = PFO_OK;
       break;
     }
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < N; ++c) sh[c] = s[c] / A[c];
     pfo_dia_apply(nx, ny, nz, A, sh, t); /* t = A shat */
     const double tt = dot(N, t, t);
     if (tt == 0.0) { status = PFO_E_BREAKDOWN; break; }
     omega = dot(N, t, s) / tt; /* minimises ||s - omega t||_2 */
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < N; ++c) x[c] += alpha * ph[c] + omega * sh[c];
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < N; ++c) r[c] = s[c] - omega * t[c];
     measure = PFO_MEASURE(r);
     if (PFO_CONVERGED(measure)) { status = PFO_OK; break; }

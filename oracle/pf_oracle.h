@@ -48,6 +48,11 @@ int pfo_species_setup(int ns, const double* z, const double* radius_A, const dou
 int pfo_fermi_point(int ns, const double* z, const double* v, const double* p, const double* cB,
                     double gammaB, double phi_hat, double* C, double* S, double* Gamma, int* iters);
 
+/* Eq. (1) at n nodes (phi_hat[n]): C[ns * n] (species-major, A^-3), S[n], Gamma[n]; PFO_OK, or the largest
+ * status of a node that failed. */
+int pfo_fermi_nodes(int ns, const double* z, const double* v, const double* p, const double* cB, double gammaB,
+                    long n, const double* phi_hat, double* C, double* S, double* Gamma);
+
 /* ---- matrices in the 7-diagonal format of Section 4 ----------------------
  * A is 7*N doubles: A[0*N+i] diagonal, A[1*N+i] east (i+1), A[2*N+i] west (i-1),
  * A[3*N+i] south (i-nx), A[4*N+i] north (i+nx), A[5*N+i] down (i-nx*ny), A[6*N+i] up. */

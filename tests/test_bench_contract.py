@@ -5,6 +5,8 @@ import os
 import subprocess
 import sys
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -25,6 +27,9 @@ def test_reference_arm_json_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "pf_33_four_pores_NaCaCl"
     assert "fits in L2" in d["config"]["l2"]
+    # the config names the workload only; the arm's arithmetic is stated beside it
+    assert "precision" not in d["config"] and d["precision"].startswith("fp64")
+    assert d["cpu_baseline"]["cpu"]["nproc"] >= 1 and d["cpu_baseline"]["cpu"]["model"]
 
 
 def test_l2_statement_at_the_bench_size():
@@ -33,3 +38,47 @@ def test_l2_statement_at_the_bench_size():
     args = type("A", (), dict(n=257, precision="mixed", tol_outer=1e-3, lin_tol=1e-6, accel_depth=0, inner_tol=0.1,
                               gpus=1))
     assert bench.config_of(args)["l2"].startswith("inputs larger than L2")
+
+
+def test_accuracy_check_on_an_oracle_solution(orc):
+    """The bench's after-the-fact accuracy check, fed the oracle's own converged solution of a small channel:
+    the pointwise step agrees to rounding and both residuals are at the solve's tolerance."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1711_04060_gb300 import workloads as W
+    prob = W.config2(n=17)
+    ref = orc.pf_solve_problem(prob, tol_outer=1e-12, lin_tol=1e-13)
+    assert ref["status"] == 0
+    out = {"phi_V": ref["phi_V"], "C_M": ref["C_M"].ravel(), "S": ref["S"], "Gamma": ref["Gamma"], "Psi": ref["Psi"]}
+    acc = bench.oracle_accuracy(prob, out, n_sample=500)
+    assert max(acc["eq1_conc_rel"]) < 1e-13 and acc["eq1_S_abs"] < 1e-13 and acc["eq1_Gamma_rel"] < 1e-13
+    assert acc["pf2_residual_rel2"] < 1e-9 and acc["pf1_residual_rel_inf_sampled"] < 1e-9
+    # a perturbed potential shows up in both
+    out2 = dict(out, phi_V=out["phi_V"] * (1 + 1e-4))
+    acc2 = bench.oracle_accuracy(prob, out2, n_sample=500)
+    assert max(acc2["eq1_conc_rel"]) > 1e-7 and acc2["pf2_residual_rel2"] > 1e-6
+
+
+def test_all_cores_oracle_copy_agrees(orc):
+    """The benchmark's OpenMP copy of the oracle runs the same arithmetic: the pointwise node loop bitwise,
+    BiCGSTAB to rounding (its reductions run in another order)."""
+    from paper_1711_04060_gb300 import workloads as W
+    L = orc.load(orc.build_all_cores())
+    z, r, b = [1, 2, -1, 0], [0.95, 0.99, 1.81, 1.4], [0.1, 0.001, 0.102, 55.5]
+    sp = orc.species_setup(z, r, b)
+    ph = W.uniform(W.substream(3, 1), 2000, -12.0, 12.0)
+    one = orc.fermi_nodes(sp, z, ph)
+    with orc.using(L):
+        many = orc.fermi_nodes(sp, z, ph)
+    assert one["status"] == 0 and many["status"] == 0
+    assert np.array_equal(one["C"], many["C"]) and np.array_equal(one["Gamma"], many["Gamma"])
+    for k in (0, 777, 1999):
+        pt = orc.fermi_point(sp, z, float(ph[k]))
+        assert np.array_equal(pt["C"], one["C"][:, k]) and pt["Gamma"] == one["Gamma"][k]
+    p = W.linear_problem(n=17, seed=2, n_spheres=3)
+    g = p.grid
+    A = orc.assemble_eps(g.nx, g.ny, g.nz, g.h, p.eps)
+    x1 = orc.bicgstab(g.nx, g.ny, g.nz, A, p.b, tol=1e-12, max_it=2000)["x"]
+    with orc.using(L):
+        xa = orc.bicgstab(g.nx, g.ny, g.nz, A, p.b, tol=1e-12, max_it=2000)["x"]
+    assert np.abs(xa - x1).max() <= 1e-9 * np.abs(x1).max()
