@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--tight-lin-tol", type=float, default=1e-10)
     ap.add_argument("--e2e-steps", type=int, default=3, help="solves of the end-to-end leg (at most --steps)")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle checks of the returned solution")
+    ap.add_argument("--ablation-outer", type=int, default=3,
+                    help="outer iterations of the host-nonlinear + GPU-linear ablation (0: skip)")
     ap.add_argument("--accel-depth", type=int, default=0, help="Anderson depth of the timed solves (0: relaxation)")
     ap.add_argument("--serve-requests", type=int, default=16, help="requests of the serving sample (0: skip)")
     ap.add_argument("--serve-gap", type=float, default=0.25, help="mean inter-arrival time of the serving sample (s)")
@@ -475,6 +477,142 @@ def oracle_accuracy(prob, out, n_sample=4000):
     return acc
 
 
+# ------------------------------------------------------------------ ablation: host nonlinear step + GPU linear
+# Table 1 constants (k_B, e, eps0) and Avogadro's number, for the host-side step of the ablation below
+KB, QE, EPS0, NAVO = 1.38e-23, 1.602e-19, 8.85e-12, 6.02214076e23
+
+
+def host_species(prob):
+    """Species constants of Eq. (1) on the host: v_i = 4 pi a_i^3 / 3, p_i = v_i / mean(v), bulk in A^-3,
+    Gamma^B = 1 - sum v_i cB_i, lambda = e^2 / (eps0 k_B T 1 A)."""
+    a = np.array([s.radius_A for s in prob.species])
+    v = 4.0 * np.pi * a ** 3 / 3.0
+    cB = np.array([s.bulk_M for s in prob.species]) * NAVO * 1e-27
+    return {"z": np.array([s.z for s in prob.species], float), "v": v, "p": v / v.mean(), "cB": cB,
+            "gB": 1.0 - float((v * cB).sum()), "lam": QE * QE / (EPS0 * KB * prob.T_K * 1e-10),
+            "Tv": KB * prob.T_K / QE}
+
+
+def host_fermi_chunk(sp, phi, u):
+    """The pointwise step of Eq. (1) on a node array, numpy: Newton on u = ln Gamma for
+    f(u) = e^u + sum_i exp(la_i + p_i u) - 1, la_i = ln(v_i cB_i) - z_i phi - p_i ln Gamma^B, kept inside the
+    bracket where every term is at most one; u holds the start and receives the root.  Returns rho = sum z_i C_i
+    and kappa = lambda sum z_i^2 C_i."""
+    pres = sp["cB"] > 0
+    z, p, v = sp["z"][pres], sp["p"][pres], sp["v"][pres]
+    la = (np.log(v * sp["cB"][pres]) - p * np.log(sp["gB"]))[:, None] - z[:, None] * phi[None, :]
+    lnn = np.log(1.0 + pres.sum())
+    hi = np.minimum(0.0, (-la / p[:, None]).min(0))
+    lo = np.minimum(-lnn, ((-la - lnn) / p[:, None]).min(0))
+    u[:] = np.where((u > lo) & (u < hi), u, 0.5 * (lo + hi))
+    for _ in range(60):
+        t = np.exp(la + p[:, None] * u[None, :])
+        eu = np.exp(u)
+        f = eu + t.sum(0) - 1.0
+        d = eu + (p[:, None] * t).sum(0)
+        pos = f > 0
+        hi = np.where(pos, u, hi)
+        lo = np.where(pos, lo, u)
+        un = u - f / d
+        un = np.where((un > lo) & (un < hi), un, 0.5 * (lo + hi))
+        step = np.abs(un - u).max()
+        u[:] = un
+        if step <= 1e-13:
+            break
+    C = np.exp(la + p[:, None] * u[None, :]) / v[:, None]
+    return (z[:, None] * C).sum(0), sp["lam"] * (z[:, None] ** 2 * C).sum(0)
+
+
+def host_fermi(sp, phi, u, pool, chunk=1 << 18):
+    """host_fermi_chunk over chunks of nodes on a thread pool (numpy releases the GIL in its array loops)."""
+    n = len(phi)
+    rho, kap = np.empty(n), np.empty(n)
+
+    def run(a):
+        b = min(n, a + chunk)
+        rho[a:b], kap[a:b] = host_fermi_chunk(sp, phi[a:b], u[a:b])
+
+    list(pool.map(run, range(0, n, chunk)))
+    return rho, kap
+
+
+def host_spread(prob, lam):
+    """The fixed-charge source of Eq. (3) on the grid: lambda q w / h^3 at the 8 corners of each charge's cell
+    (trilinear weights w)."""
+    g = prob.grid
+    f = np.zeros(g.n)
+    for x, y, zz, q in prob.charges:
+        t = [(c - o) / g.h for c, o in zip((x, y, zz), g.origin)]
+        i0 = [min(int(np.floor(tt)), nn - 2) for tt, nn in zip(t, (g.nx, g.ny, g.nz))]
+        w = [tt - ii for tt, ii in zip(t, i0)]
+        for c in range(8):
+            d = (c & 1, (c >> 1) & 1, (c >> 2) & 1)
+            wt = np.prod([w[a] if d[a] else 1.0 - w[a] for a in range(3)])
+            f[(i0[0] + d[0]) + g.nx * ((i0[1] + d[1]) + g.ny * (i0[2] + d[2]))] += lam * q * wt / g.h ** 3
+    return f
+
+
+def ablation_sample(api, grid, prob, args, fused_ms, fused_outer):
+    """The paper's "CPU nonlinear + GPU linear" mode: the outer iteration of Table 4 with the pointwise step
+    and the right-hand sides on the host (numpy over all host threads) and only the two linear solves on the
+    GPU (pf_linear_solve with host arrays, mixed precision as the headline).  Times the initial solve and
+    `ablation_outer` outer iterations and projects a solve of the fused path's outer-iteration count."""
+    from concurrent.futures import ThreadPoolExecutor
+    g = prob.grid
+    N = g.n
+    sp = host_species(prob)
+    lam, Tv = sp["lam"], sp["Tv"]
+    ffix = host_spread(prob, lam)
+    sol = prob.solvent == 1
+    interior = np.zeros(g.shape_zyx, bool)
+    interior[1:-1] = True
+    interior = interior.ravel()
+    plane = g.nx * g.ny
+    lo, hi = prob.phi_lo_V / Tv, prob.phi_hi_V / Tv
+    lin = api.solve_opts(tol=args.lin_tol, precision=api.PF_MIXED, inner_tol=args.inner_tol)
+    grid.set_problem(prob)
+    pool = ThreadPoolExecutor(max_workers=cpu_info()["nproc"])
+    t0 = time.perf_counter()
+    b = ffix.copy()
+    b[:plane], b[-plane:] = lo, hi
+    phi0 = np.zeros(N)
+    grid.linear_solve(api.PF_OP_POISSON, b, phi0, lin, allow=(3,))
+    t_first = time.perf_counter() - t0
+    psi, u = np.zeros(N), np.full(N, np.log(sp["gB"]))
+    t_host = t_gpu = 0.0
+    t_loop = time.perf_counter()
+    delta = None
+    for _ in range(args.ablation_outer):
+        t0 = time.perf_counter()
+        rho, kap = np.zeros(N), np.zeros(N)
+        rho[sol], kap[sol] = host_fermi(sp, phi0[sol], u[sol], pool)
+        b1 = np.where(sol & interior, -lam * rho, 0.0)
+        t1 = time.perf_counter()
+        grid.set_kappa(kap)
+        grid.linear_solve(api.PF_OP_PF1, b1, psi, lin, allow=(3,))
+        t2 = time.perf_counter()
+        b2 = np.where(sol, -prob.eps_s * psi + kap * phi0, 0.0) + ffix
+        b2[:plane], b2[-plane:] = lo, hi
+        phi = phi0.copy()
+        t3 = time.perf_counter()
+        grid.linear_solve(api.PF_OP_PF2, b2, phi, lin, allow=(3,))
+        t4 = time.perf_counter()
+        phi = 0.3 * phi0 + 0.7 * phi
+        delta = float(np.abs(phi - phi0).max())
+        phi0 = phi
+        t_host += (t1 - t0) + (t3 - t2) + (time.perf_counter() - t4)
+        t_gpu += (t2 - t1) + (t4 - t3)
+    per_outer = (time.perf_counter() - t_loop) / args.ablation_outer
+    pool.shutdown()
+    proj = t_first + fused_outer * per_outer
+    return {"what": "host pointwise step and right-hand sides (numpy, all host threads) + GPU linear solves "
+                    "(pf_linear_solve, host arrays, mixed precision)",
+            "outer_iters_timed": args.ablation_outer, "first_solve_s": t_first, "per_outer_s": per_outer,
+            "per_outer_host_s": t_host / args.ablation_outer, "per_outer_gpu_linear_s": t_gpu / args.ablation_outer,
+            "fused_per_outer_s": fused_ms / 1e3 / max(1, fused_outer), "projected_solve_s": proj,
+            "fused_solve_s": fused_ms / 1e3, "fused_speedup": proj / (fused_ms / 1e3), "last_delta": delta}
+
+
 # ------------------------------------------------------------------ GPU arm
 def cg_sample(api, grid, prob, torch, dev, lin_tol):
     """Conjugate gradients (pf_linear_solve_cg) against BiCGSTAB, both FP64, on the bench grid's PF1 and
@@ -726,6 +864,11 @@ def run_ours(args):
         d2h = sum(v.nbytes for v in hout.values())
         line["e2e"] = {"value": whole_job_rate(k_e2e, world, el), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "steps": k_e2e}
+
+    # ablation: the paper's CPU-nonlinear + GPU-linear mode on the same workload
+    if args.ablation_outer > 0 and world == 1:
+        line["host_nonlinear_ablation"] = ablation_sample(api, grid, prob, args, ms / args.steps,
+                                                          reps[-1]["outer_iters"])
 
     # conjugate gradients for the symmetric systems against BiCGSTAB (FP64 linear solves on this grid)
     if not args.no_cg and world == 1:

@@ -195,6 +195,56 @@ pf_status pf_set_kappa(pf_grid* g, const double* kappa, int mem);
  * not served. */
 pf_status pf_set_filter(pf_grid* g, const uint8_t* fixed, const double* phi_V, int mem);
 
+/* Treatment of the fixed charges.  PF_CHARGES_SPREAD (the default after pf_set_coeffs): each charge is spread
+ * onto the 8 corners of its cell (Eq. 3 on the grid).  PF_CHARGES_DECOMPOSED: the potential decomposition of
+ * Eqs. (5)-(10).  In the biomolecular domain phi = phi~ + G with G = phi* + phi^L, phi* the Coulomb potential of
+ * the charges in the uniform membrane dielectric eps_m (Eq. 6) and phi^L the harmonic function with
+ * phi^L = -phi* on the interface (the sign that keeps phi continuous; Eq. 10 prints the other) and dG/dn = 0 on
+ * the x/y sides; phi~ then solves the charge-free problem whose interface rows (Eqs. 16-18) carry the jump
+ * [eps dphi~/dn] = eps_m d(phi* + phi^L)/dn of Eq. (8) (again the sign of Eq. 8, not Eq. 16's) through the
+ * c0 / d0 terms.  The interface sits at the midpoint of each face between a membrane and a solvent node;
+ * phi^L is solved on the device with Shortley-Weller rows (Jacobi-BiCGSTAB, relative residual 1e-13).
+ * pf_set_charge_mode(PF_CHARGES_DECOMPOSED) builds G and the interface right-hand side once for the current
+ * coefficients; every later pf_nonlinear_solve (and batch) uses them and returns phi = phi~ + G.  Needs
+ * pf_set_coeffs first, nx, ny >= 3, one dielectric value over all non-solvent nodes, every charge off the nodes
+ * and every side node of the same kind as its mirror partner (PF_E_INVAL otherwise).  report (may be NULL) gets
+ * the phi^L solve's iterations, residual and device time.  pf_set_coeffs returns the grid to
+ * PF_CHARGES_SPREAD. */
+typedef enum { PF_CHARGES_SPREAD = 0, PF_CHARGES_DECOMPOSED = 1 } pf_charge_mode;
+pf_status pf_set_charge_mode(pf_grid* g, int mode, pf_report* report);
+
+/* The decomposition's G (volts, N values; 0 in the solvent) and interface right-hand side (the scaled
+ * source term that replaces the spread charges in the PF2 rows, N values) into host or device arrays per mem;
+ * either may be NULL.  PF_E_INVAL unless the grid is in PF_CHARGES_DECOMPOSED mode. */
+pf_status pf_get_decomposition(pf_grid* g, double* G_V, double* b_if, int mem);
+
+/* A filter region built from the site model of Eqs. (19)-(20) on the device.  Site b is a sphere of radius
+ * a_b at center_A[3b..3b+2] that may hold an ion of charge number q_ion[b] and hard-sphere radius
+ * ion_radius_A[b].  Eq. (19): its scaled potential is the mean over the six points center +- a_b along x, y and z
+ * of the grid's fixed charges (those of pf_set_coeffs) screened by eps_p and of the ions at the other occupied
+ * sites screened by eps_b, plus its own ion q_b / (eps_b a_b) when occupied (lambda / 4 pi converts to k_BT/e).
+ * The solvent nodes within max(a_b, map_radius_A) of a centre then hold that site's potential as a filter
+ * region (exactly as pf_set_filter with those nodes; where spheres overlap the lowest b wins).  Eq. (20): the
+ * site region's steric potential S = ln((1 - sum of the occupied ions' volumes / v_sites_A3) / Gamma^B).
+ * Outputs (host, may be NULL): site_phi_V[n_sites] (volts), *site_S.  PF_E_INVAL for bad sizes or radii, a six-
+ * point position on a charge or site centre, or ions that fill v_sites_A3 (nothing is changed then).
+ * The choices the paper leaves open (the six points on the axes, the node mapping, V_sites as a parameter)
+ * are stated here; a caller with its own mapping can use pf_set_filter with the returned potentials. */
+typedef struct {
+  int n_sites;
+  const double* center_A;      /* n_sites x 3 (x, y, z) */
+  const double* radius_A;      /* a_b > 0 */
+  const double* q_ion;         /* charge number of each site's ion */
+  const int* occupied;         /* 1: an ion occupies the site */
+  const double* ion_radius_A;  /* hard-sphere radius of each site's ion (Eq. 20) */
+  double eps_b;                /* dielectric of the site region */
+  double eps_p;                /* dielectric screening the protein's fixed charges */
+  double map_radius_A;         /* >= 0: nodes within max(a_b, map_radius_A) of a centre are that site's */
+  double v_sites_A3;           /* volume of the site region (Eq. 20), > 0 */
+} pf_sites;
+
+pf_status pf_set_filter_sites(pf_grid* g, const pf_sites* sites, double* site_phi_V, double* site_S);
+
 /* Sets the grid's potential Phi_0 (phi_V: N values in volts, node-major, host or device per `mem`) as the
  * start of the next pf_nonlinear_solve with warm_start = 1: a checkpoint written from pf_result.phi_V, or a
  * caller's guess.  Psi restarts from 0.  Needs pf_set_coeffs first (which forgets any potential). */

@@ -22,6 +22,7 @@ PF_MEM_HOST, PF_MEM_DEVICE = 0, 1
 PF_NORM_REL2, PF_NORM_ABSINF = 0, 1
 PF_MAX_SPECIES = 8
 PF_FERMI_NOALLOC_MAX_NODES = 1 << 20
+PF_CHARGES_SPREAD, PF_CHARGES_DECOMPOSED = 0, 1
 
 
 class pf_species(ctypes.Structure):
@@ -69,6 +70,11 @@ class pf_request(ctypes.Structure):
                 ("opts", pf_nl_opts), ("phi0_V", _VP)]
 
 
+class pf_sites(ctypes.Structure):
+    _fields_ = [("n_sites", _I), ("center_A", _VP), ("radius_A", _VP), ("q_ion", _VP), ("occupied", _VP),
+                ("ion_radius_A", _VP), ("eps_b", _D), ("eps_p", _D), ("map_radius_A", _D), ("v_sites_A3", _D)]
+
+
 PF_BATCH_TUNE_MAX = 16
 
 
@@ -89,6 +95,9 @@ SIGNATURES = {
     "pf_linear_solve": (_I, [_VP, _I, _VP, _VP, _I, ctypes.POINTER(pf_solve_opts), ctypes.POINTER(pf_report)]),
     "pf_linear_solve_cg": (_I, [_VP, _I, _VP, _VP, _I, ctypes.POINTER(pf_solve_opts), ctypes.POINTER(pf_report)]),
     "pf_set_filter": (_I, [_VP, _VP, _VP, _I]),
+    "pf_set_filter_sites": (_I, [_VP, ctypes.POINTER(pf_sites), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "pf_set_charge_mode": (_I, [_VP, _I, ctypes.POINTER(pf_report)]),
+    "pf_get_decomposition": (_I, [_VP, _VP, _VP, _I]),
     "pf_nonlinear_solve": (_I, [_VP, ctypes.POINTER(pf_nl_opts), ctypes.POINTER(pf_result)]),
     "pf_destroy_grid": (_I, [_VP]),
     "pf_profile_enable": (_I, [_VP, _I]),

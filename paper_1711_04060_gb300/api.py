@@ -13,7 +13,8 @@ import numpy as np
 
 from . import _binding as B
 from ._binding import (PF_FP64, PF_MIXED, PF_OP_POISSON, PF_OP_PF1, PF_OP_PF2, PF_MEM_HOST, PF_MEM_DEVICE,  # noqa
-                       PF_NORM_REL2, PF_NORM_ABSINF, PF_OK, PF_PENDING, STATUS_NAMES)
+                       PF_NORM_REL2, PF_NORM_ABSINF, PF_OK, PF_PENDING, STATUS_NAMES, PF_CHARGES_SPREAD,
+                       PF_CHARGES_DECOMPOSED)
 
 
 class PFError(RuntimeError):
@@ -127,6 +128,48 @@ def pf_set_filter(grid, fixed=None, phi_V=None):
     if mf != mv:
         raise TypeError("fixed and phi_V must both be host or both be device arrays")
     _check(B.load().pf_set_filter(grid, pf_, pv, mf))
+
+
+def pf_set_filter_sites(grid, centers, radii, q_ion, occupied, ion_radii, eps_b, eps_p, map_radius_A=0.0,
+                        v_sites_A3=1.0):
+    """Filter region from the site model (Eqs. 19-20) on the device: returns the site potentials (volts) and
+    the site region's steric potential S."""
+    c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1)
+    n = len(c) // 3
+    r = np.ascontiguousarray(radii, dtype=np.float64)
+    q = np.ascontiguousarray(q_ion, dtype=np.float64)
+    o = np.ascontiguousarray(occupied, dtype=np.int32)
+    ir = np.ascontiguousarray(ion_radii, dtype=np.float64)
+    if not (len(r) == len(q) == len(o) == len(ir) == n):
+        raise ValueError("one radius, ion charge, occupancy and ion radius per site")
+    vp = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    st = B.pf_sites(n, vp(c), vp(r), vp(q), vp(o), vp(ir), float(eps_b), float(eps_p), float(map_radius_A),
+                    float(v_sites_A3))
+    phi = np.zeros(n)
+    S = ctypes.c_double(0.0)
+    _check(B.load().pf_set_filter_sites(grid, ctypes.byref(st), phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.byref(S)))
+    return phi, S.value
+
+
+def pf_set_charge_mode(grid, mode):
+    """PF_CHARGES_SPREAD (Eq. 3) or PF_CHARGES_DECOMPOSED (Eqs. 5-10, built on the device now); returns the
+    report of the phi^L solve."""
+    rep = B.pf_report()
+    _check(B.load().pf_set_charge_mode(grid, int(mode), ctypes.byref(rep)))
+    return {"status": rep.status, "iterations": rep.iterations, "residual": rep.residual, "time_ms": rep.time_ms}
+
+
+def pf_get_decomposition(grid, G_V, b_if):
+    """Copies G (volts) and the interface right-hand side into the given arrays (numpy or CUDA; either None)."""
+    arrs = [a for a in (G_V, b_if) if a is not None]
+    mems = {_ptr(a, np.float64)[1] for a in arrs}
+    if len(mems) > 1:
+        raise TypeError("G_V and b_if must both be host or both be device arrays")
+    mem = mems.pop() if mems else PF_MEM_HOST
+    pg = _ptr(G_V, np.float64)[0] if G_V is not None else None
+    pb = _ptr(b_if, np.float64)[0] if b_if is not None else None
+    _check(B.load().pf_get_decomposition(grid, pg, pb, mem))
 
 
 def pf_set_kappa(grid, kappa):
@@ -408,6 +451,15 @@ class Grid:
 
     def set_filter(self, fixed=None, phi_V=None):
         pf_set_filter(self.handle, fixed, phi_V)
+
+    def set_filter_sites(self, *args, **kw):
+        return pf_set_filter_sites(self.handle, *args, **kw)
+
+    def set_charge_mode(self, mode):
+        return pf_set_charge_mode(self.handle, mode)
+
+    def get_decomposition(self, G_V=None, b_if=None):
+        pf_get_decomposition(self.handle, G_V, b_if)
 
     def linear_solve(self, op, b, x, opts=None, allow=(), method="bicgstab"):
         return pf_linear_solve(self.handle, op, b, x, opts, allow, method)

@@ -18,6 +18,7 @@
 
 #include "../../include/pf_gb300.h"
 #include "pf_cg.cuh"
+#include "pf_decomp.cuh"
 #include "pf_filter.cuh"
 #include "pf_grid.cuh"
 
@@ -106,7 +107,8 @@ pf_status allocate(pf_grid* g) {
                     &g->v64[1], &g->rt64, &g->t64, &g->xb, &g->bb, &g->stage, &g->phi0, &g->phi, &g->psi, &g->b1,
                     &g->c2, &g->b2, &g->Sbuf, &g->Gbuf, &g->ulast};
   float** d32[] = {&g->wE32, &g->wN32, &g->wU32, &g->dinvP32, &g->dinv2_32, &g->dinv1_32, &g->r32[0], &g->r32[1],
-                   &g->p32[0], &g->p32[1], &g->v32[0], &g->v32[1], &g->rt32, &g->t32, &g->d32, &g->b32};
+                   &g->p32[0], &g->p32[1], &g->v32[0], &g->v32[1], &g->rt32, &g->t32, &g->d32, &g->b32,
+                   &g->ulast32};
   std::vector<std::pair<void**, size_t>> parts;
   for (double** p : d64) parts.push_back({reinterpret_cast<void**>(p), NP * sizeof(double)});
   parts.push_back({reinterpret_cast<void**>(&g->Cbuf), (size_t)NP * pf::MAXSP * sizeof(double)});
@@ -486,8 +488,12 @@ pf_status build_operators(pf_grid* g) {
   PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf1_dinv(g->solvent, g->geom, 1.0 / (6.0 * pf1_face(g) + g->eps_s),
                                                   g->dinv1, g->dinv1_32, g->stream));
   if (g->filter_on) PF_TRY(filter_rows_p1(g));
-  PF_CK(cudaMemsetAsync(g->ffix, 0, NP * sizeof(double), g->stream));
   PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), g->stream));
+  if (g->charge_mode == 1) {  // the decomposition's interface right-hand side replaces the spread charges
+    PF_CK(cudaMemcpyAsync(g->ffix, g->bif, NP * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    return PF_OK;
+  }
+  PF_CK(cudaMemsetAsync(g->ffix, 0, NP * sizeof(double), g->stream));
   if (g->nq > 0)
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_spread(g->dch, g->nq, g->origin[0], g->origin[1], g->origin[2], g->h,
                                                   g->lam, g->geom, g->ffix, g->err, g->stream));
@@ -694,7 +700,7 @@ size_t pf_internal_grid_bytes(int nx, int ny, int nz, int accel_depth) {
   const pf::Geom g = pf::make_geom(nx, ny, nz);
   // Anderson acceleration adds f, f_prev, x_prev and two history columns per depth
   const int aa = accel_depth > 0 ? 3 + 2 * accel_depth : 0;
-  const size_t per_node = (32 + aa) * sizeof(double) + pf::MAXSP * sizeof(double) + 16 * sizeof(float) + 1;
+  const size_t per_node = (32 + aa) * sizeof(double) + pf::MAXSP * sizeof(double) + 17 * sizeof(float) + 1;
   return (size_t)g.np * per_node + (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double) + 8192;
 }
 
@@ -803,8 +809,14 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
     return fail(PF_E_INVAL, "need 1..PF_MAX_SPECIES species");
   if (c->n_charges < 0 || (c->n_charges > 0 && !c->charges)) return fail(PF_E_INVAL, "bad charges");
   if (!(c->eps_s > 0) || !(c->lc_A >= 0) || !(c->T_K > 0)) return fail(PF_E_INVAL, "need eps_s > 0, lc >= 0, T > 0");
-  for (long i = 0; i < g->N; ++i)
+  double eps_m = 0.0;
+  for (long i = 0; i < g->N; ++i) {
     if (!(c->eps[i] > 0) || c->solvent[i] > 1) return fail(PF_E_INVAL, "eps must be > 0 and solvent 0/1");
+    if (!c->solvent[i] && eps_m == eps_m) {  // the membrane dielectric, NaN once two values differ
+      if (eps_m == 0.0) eps_m = c->eps[i];
+      else if (c->eps[i] != eps_m) eps_m = NAN;
+    }
+  }
   pf::SpeciesParams sp{};
   double tv = 0.0, molar = 0.0;
   if (const char* why = pf::species_params(c->n_species, c->species, c->T_K, &sp, &tv, &molar))
@@ -813,6 +825,7 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
   g->Tv = tv;
   g->lam = sp.lam;
   g->sp = sp;
+  g->spd = pf::species_df(sp);
   g->molar = molar;
   g->eps_s = c->eps_s;
   g->lc = c->lc_A;
@@ -830,7 +843,9 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
     PF_CK(cudaMallocAsync(&g->dch, sizeof(double) * 4 * g->nq, g->stream));
     PF_CK(cudaMemcpyAsync(g->dch, c->charges, sizeof(double) * 4 * g->nq, cudaMemcpyHostToDevice, g->stream));
   }
-  g->filter_on = false;  // new coefficients: the filter region must be set again
+  g->filter_on = false;  // new coefficients: the filter region and the charge treatment must be set again
+  g->charge_mode = 0;
+  g->eps_m = eps_m;
   PF_TRY(build_operators(g));
   PF_CK(cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
   PF_CK(cudaStreamSynchronize(g->stream));
@@ -838,6 +853,7 @@ pf_status pf_set_coeffs(pf_grid* g, const pf_coeffs* c) {
   g->have_coeffs = true;
   g->have_phi0 = false;
   g->ulast_valid = false;
+  g->u32_valid = false;
   return PF_OK;
 }
 
@@ -915,6 +931,187 @@ static pf_status linear_solve_entry(pf_grid* g, int op, const double* b, double*
   return PF_OK;
 }
 
+pf_status pf_set_charge_mode(pf_grid* g, int mode, pf_report* rep) {
+  if (!g) return fail(PF_E_INVAL, "grid is required");
+  if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first");
+  if (mode != PF_CHARGES_SPREAD && mode != PF_CHARGES_DECOMPOSED) return fail(PF_E_INVAL, "bad charge mode");
+  if (rep) *rep = pf_report{};
+  if (mode == PF_CHARGES_SPREAD) {
+    g->charge_mode = 0;
+    return PF_OK;
+  }
+  if (g->nx < 3 || g->ny < 3) return fail(PF_E_INVAL, "the decomposition needs nx, ny >= 3");
+  if (!(g->eps_m == g->eps_m)) return fail(PF_E_INVAL, "the decomposition needs a uniform membrane dielectric");
+  const long NP = g->geom.np;
+  cudaStream_t s = g->stream;
+  if (!g->Gdec) {
+    PF_TRY(dalloc(g, &g->Gdec, NP));
+    PF_TRY(dalloc(g, &g->bif, NP));
+    PF_CK(cudaMemsetAsync(g->Gdec, 0, NP * sizeof(double), s));
+    PF_CK(cudaMemsetAsync(g->bif, 0, NP * sizeof(double), s));
+  }
+  PF_CK(cudaEventRecord(g->ev0, s));
+  // the phi^L matrix (7 diagonals) and its state live in one stream-ordered block for the call
+  unsigned char* blk = nullptr;
+  const size_t arr = ((size_t)NP * sizeof(double) + 255) / 256 * 256;
+  PF_CK(cudaMallocAsync(reinterpret_cast<void**>(&blk), 7 * arr + 256, s));
+  double* A[7];
+  for (int d = 0; d < 7; ++d) A[d] = reinterpret_cast<double*>(blk + d * arr);
+  pf::DiaState* dst = reinterpret_cast<pf::DiaState*>(blk + 7 * arr);
+  const double eps_m = g->eps_m > 0 ? g->eps_m : 1.0;  // no membrane node: G = 0 everywhere
+  const pf::DecompArgs a{g->dch, g->nq, g->lam / (4.0 * M_PI * eps_m), g->origin[0], g->origin[1], g->origin[2],
+                         g->h, eps_m, g->eps_s, g->solvent, g->geom, g->err};
+  const pf::DiaVecs w{g->xb, g->bb, g->r64[0], g->rt64, {g->p64[0], g->p64[1]}, {g->v64[0], g->v64[1]}, g->t64};
+  pf_status out = PF_OK;
+  pf::DiaState hs{};
+  do {
+    if (cudaMemsetAsync(g->err, 0, sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(g->xb, 0, NP * sizeof(double), s) != cudaSuccess) { out = cuda_fail(cudaGetLastError(), "memset"); break; }
+    if (pf::launch_phiL_rows(a, A, g->bb, s) != cudaSuccess) { out = cuda_fail(cudaGetLastError(), "phiL rows"); break; }
+    if (pf::launch_dia_start(A, w, g->geom, 1e-13, 20000, g->part, dst, s) != cudaSuccess) {
+      out = cuda_fail(cudaGetLastError(), "phiL start");
+      break;
+    }
+    int cur = 0;
+    static_assert(sizeof(pf::DiaState) <= 512, "the state fits the pinned block");
+    pf::DiaState* hp = reinterpret_cast<pf::DiaState*>(g->host_st);
+    for (long launched = 0;; launched += CHUNK) {
+      if (cudaMemcpyAsync(hp, dst, sizeof(pf::DiaState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { out = cuda_fail(cudaGetLastError(), "phiL state"); break; }
+      hs = *hp;
+      if (hs.done || launched > 20000 + 2 * CHUNK) break;
+      for (int i = 0; i < CHUNK && out == PF_OK; ++i) {
+        if (pf::launch_dia_iteration(A, w, cur, g->geom, g->part, dst, s) != cudaSuccess)
+          out = cuda_fail(cudaGetLastError(), "phiL iteration");
+        cur = 1 - cur;
+      }
+      if (out != PF_OK) break;
+      g->launches += 3 * CHUNK;
+    }
+    if (out != PF_OK) break;
+    if (!hs.done || hs.status != 0) {
+      out = fail(hs.status == 4 ? PF_E_BREAKDOWN : PF_E_NOCONV, "the phi^L solve of the decomposition failed");
+      break;
+    }
+    if (pf::launch_decomp_G(a, g->xb, g->Gdec, s) != cudaSuccess ||
+        pf::launch_decomp_bif(a, g->xb, g->bif, s) != cudaSuccess) { out = cuda_fail(cudaGetLastError(), "G / bif"); break; }
+    if (cudaMemcpyAsync(g->host_err, g->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaEventRecord(g->ev1, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+      out = cuda_fail(cudaGetLastError(), "decomposition");
+      break;
+    }
+    if (*g->host_err)
+      out = fail(PF_E_INVAL, *g->host_err == 1 ? "the decomposition needs every charge off the nodes"
+                                               : "the decomposition needs each side node to match its mirror partner");
+  } while (0);
+  cudaFreeAsync(blk, s);
+  if (out != PF_OK) return out;
+  g->charge_mode = 1;
+  if (rep) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+    rep->status = PF_OK;
+    rep->iterations = hs.iter;
+    rep->residual = sqrt(hs.rnorm2 / hs.bnorm2);
+    rep->time_ms = ms;
+  }
+  return PF_OK;
+}
+
+pf_status pf_get_decomposition(pf_grid* g, double* G_V, double* b_if, int mem) {
+  if (!g) return fail(PF_E_INVAL, "grid is required");
+  if (g->charge_mode != 1) return fail(PF_E_INVAL, "pf_set_charge_mode(PF_CHARGES_DECOMPOSED) must come first");
+  if (mem != PF_MEM_HOST && mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "bad mem");
+  if (G_V) {
+    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->Gdec, g->Tv, g->phi, g->geom.np, g->stream));
+    PF_TRY(unpack_out(g, g->phi, 1, G_V, mem));
+  }
+  if (b_if) PF_TRY(unpack_out(g, g->bif, 1, b_if, mem));
+  PF_CK(cudaStreamSynchronize(g->stream));
+  return PF_OK;
+}
+
+pf_status pf_set_filter_sites(pf_grid* g, const pf_sites* st, double* site_phi_V, double* site_S) {
+  if (!g || !st) return fail(PF_E_INVAL, "grid and sites are required");
+  if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first");
+  const int n = st->n_sites;
+  if (n < 1 || n > 65535 || !st->center_A || !st->radius_A || !st->q_ion || !st->occupied || !st->ion_radius_A ||
+      !(st->eps_b > 0) || !(st->eps_p > 0) || !(st->map_radius_A >= 0) || !(st->v_sites_A3 > 0))
+    return fail(PF_E_INVAL, "pf_set_filter_sites: bad site description");
+  std::vector<double> packed(8 * (size_t)n);
+  for (int b = 0; b < n; ++b) {
+    if (!(st->radius_A[b] > 0) || !(st->ion_radius_A[b] > 0) || (st->occupied[b] != 0 && st->occupied[b] != 1))
+      return fail(PF_E_INVAL, "pf_set_filter_sites: radii must be > 0 and occupied 0 or 1");
+    double* q = &packed[8 * (size_t)b];
+    q[0] = st->center_A[3 * b];
+    q[1] = st->center_A[3 * b + 1];
+    q[2] = st->center_A[3 * b + 2];
+    q[3] = st->radius_A[b];
+    q[4] = st->q_ion[b];
+    q[5] = st->occupied[b];
+    q[6] = st->ion_radius_A[b];
+    q[7] = 0.0;
+  }
+  cudaStream_t s = g->stream;
+  // site table, potentials, S and the error flag in one small stream-ordered block
+  unsigned char* blk = nullptr;
+  const size_t tb = packed.size() * sizeof(double), pb = (size_t)n * sizeof(double);
+  PF_CK(cudaMallocAsync(reinterpret_cast<void**>(&blk), tb + pb + 2 * sizeof(double), s));
+  double* dsite = reinterpret_cast<double*>(blk);
+  double* dphi = reinterpret_cast<double*>(blk + tb);
+  double* dS = reinterpret_cast<double*>(blk + tb + pb);
+  int* derr = reinterpret_cast<int*>(blk + tb + pb + sizeof(double));
+  pf_status out = PF_OK;
+  std::vector<double> hphi(n);
+  double hS = 0.0;
+  int herr = 0;
+  do {
+    if (cudaMemcpyAsync(dsite, packed.data(), tb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(derr, 0, sizeof(int), s) != cudaSuccess) { out = cuda_fail(cudaGetLastError(), "site copy"); break; }
+    if (pf::launch_site_potentials(dsite, n, g->dch, g->nq, st->eps_b, st->eps_p, g->lam, st->v_sites_A3,
+                                   g->sp.lgB, dphi, dS, derr, s) != cudaSuccess) {
+      out = cuda_fail(cudaGetLastError(), "launch_site_potentials");
+      break;
+    }
+    if (cudaMemcpyAsync(hphi.data(), dphi, pb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hS, dS, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { out = cuda_fail(cudaGetLastError(), "site results"); break; }
+    if (herr) {
+      out = fail(PF_E_INVAL, herr == 1 ? "pf_set_filter_sites: a site point coincides with a charge or a site centre"
+                                       : "pf_set_filter_sites: the ions fill v_sites_A3");
+      break;
+    }
+    // the region: drop a previous one, then map the sites to the solvent nodes of their spheres
+    if (g->filter_on) {
+      g->filter_on = false;
+      out = build_operators(g);
+      if (out != PF_OK) break;
+    }
+    const long NP = g->geom.np;
+    if (!g->fmask) {
+      if ((out = dalloc(g, &g->fmask, NP)) != PF_OK) break;
+      if ((out = dalloc(g, &g->fval, NP)) != PF_OK) break;
+    }
+    if (cudaMemsetAsync(g->fmask, 0, NP, s) != cudaSuccess) { out = cuda_fail(cudaGetLastError(), "fmask"); break; }
+    if (pf::launch_site_map(dsite, n, dphi, g->solvent, g->geom, g->origin[0], g->origin[1], g->origin[2], g->h,
+                            st->map_radius_A, g->fmask, g->fval, s) != cudaSuccess) {
+      out = cuda_fail(cudaGetLastError(), "launch_site_map");
+      break;
+    }
+    g->filter_on = true;
+    if ((out = filter_rows_p1(g)) != PF_OK) break;
+    if (pf::launch_filter_rows(g->fmask, g->geom, g->dinv2, g->diag2, g->dinv2_32, s) != cudaSuccess)
+      out = cuda_fail(cudaGetLastError(), "launch_filter_rows");
+  } while (0);
+  cudaFreeAsync(blk, s);
+  if (out != PF_OK) return out;
+  if (site_phi_V)
+    for (int b = 0; b < n; ++b) site_phi_V[b] = hphi[b] * g->Tv;
+  if (site_S) *site_S = hS;
+  return PF_OK;
+}
+
 pf_status pf_set_filter(pf_grid* g, const uint8_t* fixed, const double* phi_V, int mem) {
   if (!g) return fail(PF_E_INVAL, "grid is required");
   if (!g->have_coeffs) return fail(PF_E_INVAL, "pf_set_coeffs must come first");
@@ -987,6 +1184,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   PF_TRY(build_operators(g));
   const bool warm = o.warm_start != 0;
   const bool fermi_warm = warm && g->ulast_valid;
+  const bool mixed = o.lin.precision == PF_MIXED;
   if (!warm) {
     // initial potential (Table 4): PF2 with rho' = Psi = 0 -> Phi_0
     PF_CK(cudaMemsetAsync(g->phi0, 0, NP * sizeof(double), s));
@@ -1010,9 +1208,13 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
     const pf_solve_opts& lo = o.lin;
     // Eq. (1) at Phi_0 -> b_PF1 = -lambda rho, kappa, PF2 right-hand-side part (Table 4)
     PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
-    PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, g->b1, g->sig, g->c2,
-                                                 nullptr, nullptr, nullptr, g->ulast, outer > 1 || fermi_warm,
-                                                 g->err, s));
+    if (mixed)  // the in-loop step of the mixed path in double-float on the FP32 pipes
+      PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi_df(g->phi0, g->solvent, g->ffix, g->spd, G, g->b1, g->sig, g->c2,
+                                                      g->ulast32, outer > 1 || (warm && g->u32_valid), g->err, s));
+    else
+      PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, g->b1, g->sig, g->c2,
+                                                   nullptr, nullptr, nullptr, g->ulast, outer > 1 || fermi_warm,
+                                                   g->err, s));
     if (g->filter_on) PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->b1, 1, s));  // Psi = 0
     PF_TRY(update_pf2(g));
     PF_TRY(solve_dev(g, PF_OP_PF1, g->b1, g->psi, lo, &rep, eta));  // Eq. (12)
@@ -1044,16 +1246,19 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   }
   // outputs at the final potential
   PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+  // (FP64 in both precisions; after double-float steps it starts from their FP32 roots)
+  const bool df_ran = mixed && res->outer_iters > 0;
   PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, G, nullptr, nullptr, nullptr,
                                                g->Cbuf, g->Sbuf, g->Gbuf, g->ulast, res->outer_iters > 0 || fermi_warm,
-                                               g->err, s));
+                                               g->err, s, df_ran ? g->ulast32 : nullptr));
   if (g->filter_on) {  // no continuum concentrations on the filter region
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->Cbuf, g->sp.ns, s));
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->Sbuf, 1, s));
     PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->Gbuf, 1, s));
   }
-  if (res->phi_V) {
-    PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, NP, s));
+  if (res->phi_V) {  // phi = phi~ + G in the membrane when the charges are decomposed (Eq. 5)
+    PF_LAUNCH(g, PF_PROF_OTHER,
+              pf::launch_add_scale(g->phi0, g->charge_mode == 1 ? g->Gdec : nullptr, g->Tv, g->phi, NP, s));
     PF_TRY(unpack_out(g, g->phi, 1, res->phi_V, res->mem));
   }
   if (res->C_M) {
@@ -1075,6 +1280,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   res->status = st;
   g->have_phi0 = true;
   g->ulast_valid = true;
+  if (df_ran) g->u32_valid = true;
   if (st != PF_OK) return fail(st, "nonlinear solve ended with status " + std::to_string((int)st));
   return PF_OK;
 }

@@ -17,6 +17,7 @@
 // tiles_per_block is chosen by timing the FP32 phase kernels of the batch's own operators for each
 // candidate (pf_batch_autotune), or set by the caller.  The tensor maps and arguments of all problems live
 // in device tables that each block reads at start.
+#include "pf_decomp.cuh"
 #include "pf_grid.cuh"
 #include "pf_stencil.cuh"
 
@@ -523,9 +524,14 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
       const int outer = M.res->outer_iters + 1;
       const double eta = M.o.lin_forcing > 0 ? (outer == 1 ? 1e-2 : fmin(1e-2, M.o.lin_forcing * M.dprev)) : 0.0;
       PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
-      PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, g->geom, g->b1, g->sig,
-                                                   g->c2, nullptr, nullptr, nullptr, g->ulast,
-                                                   outer > 1 || M.fermi_warm, g->err, s));
+      if (M.o.lin.precision == PF_MIXED)  // double-float on the FP32 pipes, as pf_nonlinear_solve
+        PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi_df(g->phi0, g->solvent, g->ffix, g->spd, g->geom, g->b1, g->sig,
+                                                        g->c2, g->ulast32, outer > 1 || (M.o.warm_start && g->u32_valid),
+                                                        g->err, s));
+      else
+        PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, g->geom, g->b1, g->sig,
+                                                     g->c2, nullptr, nullptr, nullptr, g->ulast,
+                                                     outer > 1 || M.fermi_warm, g->err, s));
       PF_TRY(update_pf2(g));
       PF_TRY(lin_start(B, M, PF_OP_PF1, S_PF2RHS, eta));
       break;
@@ -541,11 +547,15 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
     case S_FINISH: {
       pf_result& r = *M.res;
       PF_CK(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+      const bool df_ran = M.o.lin.precision == PF_MIXED && r.outer_iters > 0;
       PF_LAUNCH(g, PF_PROF_FERMI, pf::launch_fermi(g->phi0, g->solvent, g->ffix, g->sp, g->geom, nullptr, nullptr,
                                                    nullptr, g->Cbuf, g->Sbuf, g->Gbuf, g->ulast,
-                                                   r.outer_iters > 0 || M.fermi_warm, g->err, s));
-      if (r.phi_V) {
-        PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_scale(g->phi0, g->Tv, g->phi, NP, s));
+                                                   r.outer_iters > 0 || M.fermi_warm, g->err, s,
+                                                   df_ran ? g->ulast32 : nullptr));
+      if (df_ran) g->u32_valid = true;
+      if (r.phi_V) {  // phi = phi~ + G in the membrane when the charges are decomposed (Eq. 5)
+        PF_LAUNCH(g, PF_PROF_OTHER,
+                  pf::launch_add_scale(g->phi0, g->charge_mode == 1 ? g->Gdec : nullptr, g->Tv, g->phi, NP, s));
         PF_TRY(unpack_out(g, g->phi, 1, r.phi_V, r.mem));
       }
       if (r.C_M) {

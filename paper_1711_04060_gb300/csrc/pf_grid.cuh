@@ -55,12 +55,17 @@ struct pf_grid {
   bool have_coeffs = false;
   bool have_phi0 = false;    // phi0 holds a potential to warm-start from (last solve or pf_set_potential)
   bool ulast_valid = false;  // ulast holds the per-node ln Gamma of the last Fermi step on this problem
+  bool u32_valid = false;    // ulast32 holds the FP32 ln Gamma of the last double-float Fermi step
   bool filter_on = false;    // a filter region (pf_set_filter) holds fixed potentials
+  int charge_mode = 0;       // 0: charges spread (Eq. 3); 1: decomposition (Eqs. 5-10, pf_set_charge_mode)
+  double eps_m = 0.0;        // the membrane dielectric when it is uniform (pf_set_coeffs), else NaN
+  double *Gdec = nullptr, *bif = nullptr;  // G = phi* + phi^L and the interface right-hand side (mode 1)
   uint8_t* fmask = nullptr;  // its nodes (padded layout), allocated on first use
   double* fval = nullptr;    // their potentials in units of k_BT/e (padded layout)
   // problem constants
   double eps_s = 78.5, lc = 0.0, T = 298.15, Tv = 0.0, lam = 0.0, lo_hat = 0.0, hi_hat = 0.0, molar = 0.0;
   pf::SpeciesParams sp{};
+  pf::SpeciesDF spd{};       // the same constants as double-float pairs
   // device arrays (padded layout)
   std::vector<void*> allocs;
   double *eps = nullptr, *wE = nullptr, *wN = nullptr, *wU = nullptr, *dsum = nullptr, *ffix = nullptr;
@@ -71,7 +76,7 @@ struct pf_grid {
   double *r64[2] = {nullptr, nullptr}, *p64[2] = {nullptr, nullptr}, *v64[2] = {nullptr, nullptr};
   double *rt64 = nullptr, *t64 = nullptr;
   float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr}, *v32[2] = {nullptr, nullptr};
-  float *rt32 = nullptr, *t32 = nullptr, *d32 = nullptr, *b32 = nullptr;
+  float *rt32 = nullptr, *t32 = nullptr, *d32 = nullptr, *b32 = nullptr, *ulast32 = nullptr;
   double *xb = nullptr, *bb = nullptr, *stage = nullptr;
   double *phi0 = nullptr, *phi = nullptr, *psi = nullptr, *b1 = nullptr, *c2 = nullptr, *b2 = nullptr;
   double *Cbuf = nullptr, *Sbuf = nullptr, *Gbuf = nullptr, *ulast = nullptr;

@@ -94,6 +94,21 @@ struct SpeciesParams {
   double lam;           // lambda
 };
 
+// The same constants as double-float pairs (value = hi + lo) for the FP32-pipe form of the pointwise step.
+struct SpeciesDF {
+  int ns;
+  int present[MAXSP];                   // cB_i > 0
+  float z[MAXSP];
+  float phi[MAXSP], plo[MAXSP];         // p_i
+  float inv_p[MAXSP];                   // 1 / p_i (bracket only)
+  float chi[MAXSP], clo[MAXSP];         // ln(v_i cB_i) - p_i ln Gamma^B
+  float ivhi[MAXSP], ivlo[MAXSP];       // 1 / v_i
+  float lnn;                            // ln(1 + number of species present)
+  float lgB;                            // ln Gamma^B (the cold start)
+  float lamhi, lamlo;                   // lambda
+};
+SpeciesDF species_df(const SpeciesParams& sp);
+
 // host: species constants of Eq. (1) from a caller's species list (nullptr, or why the list is invalid);
 // tv = k_B T / e in volts, molar = the mol/L -> A^-3 factor
 const char* species_params(int ns, const pf_species* species, double T_K, SpeciesParams* out, double* tv,
@@ -150,10 +165,17 @@ cudaError_t launch_phase_ca(const Maps<SlotsCA<UNI>::NH, SlotsCA<UNI>::NC>& m, c
 cudaError_t launch_add_f32(double* x, const float* d, long n, cudaStream_t s);
 
 // ---- nonlinear step (Eq. 1, Eq. 11-13, Table 4) ----
-// ulast: per-node ln Gamma of the previous call, read when warm != 0 (Newton start) and rewritten
+// ulast: per-node ln Gamma of the previous call, read when warm != 0 (Newton start) and rewritten; with
+// u32start != nullptr a warm start reads that FP32 copy instead (the one the double-float step keeps)
 cudaError_t launch_fermi(const double* phi0, const uint8_t* solvent, const double* ffix, const SpeciesParams& sp,
                          const Geom& g, double* b1, double* sig, double* c2, double* C, double* S, double* G,
-                         double* ulast, int warm, int* err, cudaStream_t s);
+                         double* ulast, int warm, int* err, cudaStream_t s, const float* u32start = nullptr);
+// The in-loop pointwise step of the mixed-precision solve in double-float arithmetic on the FP32 pipes:
+// b1 = -lambda rho, kappa and kappa phi0 + ffix as the FP64 step writes them (rho to about 1e-14 relative,
+// kappa, which only steers the iteration, to FP32); u32 holds each node's ln Gamma (warm start, rewritten).
+cudaError_t launch_fermi_df(const double* phi0, const uint8_t* solvent, const double* ffix, const SpeciesDF& sp,
+                            const Geom& g, double* b1, double* sig, double* c2, float* u32, int warm, int* err,
+                            cudaStream_t s);
 cudaError_t launch_pf2_rhs(const double* psi, const uint8_t* solvent, const double* c2, double eps_s, double lo,
                            double hi, const Geom& g, double* b2, cudaStream_t s);
 cudaError_t launch_relax(double* phi0, const double* phi, double omega, long n, double* part, unsigned int* ticket,

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include "pf_df.cuh"
 #include "pf_stencil.cuh"
 
 namespace pf {
@@ -314,10 +315,12 @@ __device__ __forceinline__ bool fermi_point(const SpeciesParams& sp, double phi,
   return false;
 }
 
-// ulast holds each node's ln Gamma from the previous call (warm != 0) and receives the new one.
+// ulast holds each node's ln Gamma from the previous call (warm != 0; from u32start when that is given) and
+// receives the new one.
 __global__ void k_fermi(const double* __restrict__ phi0, const uint8_t* __restrict__ solvent,
                         const double* __restrict__ ffix, SpeciesParams sp, Geom g, double* b1, double* sig, double* c2,
-                        double* C, double* S, double* G, double* ulast, int warm, int* err) {
+                        double* C, double* S, double* G, double* ulast, int warm, int* err,
+                        const float* __restrict__ u32start) {
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < g.np; c += (long)gridDim.x * blockDim.x) {
     const long row = c / g.px;
     const int i = (int)(c - row * g.px);
@@ -328,7 +331,7 @@ __global__ void k_fermi(const double* __restrict__ phi0, const uint8_t* __restri
     FermiOut fo;
     bool ok = false;
     if (sol) {
-      ok = fermi_point(sp, ph, warm ? ulast[c] : sp.lgB, fo);
+      ok = fermi_point(sp, ph, warm ? (u32start ? (double)u32start[c] : ulast[c]) : sp.lgB, fo);
       if (!ok) atomicExch(err, 5);
       else ulast[c] = fo.u;
     }
@@ -345,6 +348,167 @@ __global__ void k_fermi(const double* __restrict__ phi0, const uint8_t* __restri
     if (S) S[c] = (sol && ok) ? fo.S : 0.0;
     if (G) G[c] = (sol && ok) ? fo.G : 0.0;
   }
+}
+
+// ------------------------------------------------------------------ Eq. (1) in double-float arithmetic
+// The same root and Newton finish as fermi_point, with every operation on the FP32 pipes: the bracket and
+// the FP32 Newton phase as there, then Newton steps in double-float (hi + lo pairs, about 48 bits) until the
+// step is below 1e-6 max(1, |u|); the terms term_i = v_i C_i come from df_exp to about 1e-14 relative and
+// are moved to the finished root by exp(p_i du) = 1 + p_i du + (p_i du)^2 / 2 like the FP64 form.
+struct FermiDF {
+  dfl u;
+  dfl C[MAXSP];  // A^-3
+};
+
+__device__ __forceinline__ bool fermi_point_df(const SpeciesDF& sp, dfl phi, float u0, const float* thi,
+                                               const float* tlo, FermiDF& o) {
+  dfl la[MAXSP];
+  float hi = 0.0f, lo = -sp.lnn;
+#pragma unroll
+  for (int i = 0; i < MAXSP; ++i) {
+    if (i >= sp.ns) break;
+    la[i] = df_add({sp.chi[i], sp.clo[i]}, df_mul_f(phi, -sp.z[i]));
+    if (!sp.present[i]) continue;
+    hi = fminf(hi, -la[i].hi * sp.inv_p[i]);
+    lo = fminf(lo, (-la[i].hi - sp.lnn) * sp.inv_p[i]);
+  }
+  float uc = u0;
+  if (!(uc < hi && uc > lo)) uc = 0.5f * (lo + hi);
+  // FP32 phase on du = u - uc: the exponents la_i + p_i uc are formed in double-float and rounded once
+  float A[MAXSP];
+#pragma unroll
+  for (int i = 0; i < MAXSP; ++i) {
+    if (i >= sp.ns) break;
+    const dfl x = df_add(la[i], df_mul_f({sp.phi[i], sp.plo[i]}, uc));
+    A[i] = sp.present[i] ? x.hi + x.lo : -INFINITY;
+  }
+  float du = 0.f, dlo = lo - uc, dhi = hi - uc;
+  for (int it = 0; it < 60; ++it) {
+    const float eu = __expf(uc + du);
+    float f = eu - 1.f, dfd = eu;
+#pragma unroll
+    for (int i = 0; i < MAXSP; ++i) {
+      if (i >= sp.ns) break;
+      const float term = __expf(A[i] + sp.phi[i] * du);
+      f += term;
+      dfd = fmaf(sp.phi[i], term, dfd);
+    }
+    if (f > 0.f) dhi = du; else dlo = du;
+    float dn = du - __fdividef(f, dfd);
+    if (!(dn > dlo && dn < dhi)) dn = 0.5f * (dlo + dhi);
+    const float step = dn - du;
+    du = dn;
+    if (fabsf(step) <= 2e-6f * fmaxf(1.f, fabsf(uc + du))) break;
+  }
+  dfl u = two_sum(uc, du);
+  float blo = lo, bhi = hi;
+  // double-float Newton phase
+  for (int it = 0; it < 8; ++it) {
+    const dfl eu = df_exp(u, thi, tlo);
+    dfl f = df_add_f(eu, -1.0f);
+    float dfd = eu.hi;
+    dfl t[MAXSP];
+#pragma unroll
+    for (int i = 0; i < MAXSP; ++i) {
+      if (i >= sp.ns) break;
+      t[i] = {0.f, 0.f};
+      if (!sp.present[i]) continue;
+      t[i] = df_exp(df_add(la[i], df_mul({sp.phi[i], sp.plo[i]}, u)), thi, tlo);
+      f = df_add(f, t[i]);
+      dfd = fmaf(sp.phi[i], t[i].hi, dfd);
+    }
+    const float d = -(f.hi + f.lo) / dfd;
+    if (fabsf(d) <= 1e-6f * fmaxf(1.f, fabsf(u.hi))) {  // converged: finish with this Newton step
+      o.u = df_add_f(u, d);
+#pragma unroll
+      for (int i = 0; i < MAXSP; ++i) {
+        if (i >= sp.ns) break;
+        const float x = sp.phi[i] * d;
+        const dfl corr = fast_two_sum(1.0f, fmaf(0.5f * x, x, x));
+        o.C[i] = df_mul(df_mul(t[i], {sp.ivhi[i], sp.ivlo[i]}), corr);
+      }
+      return isfinite(o.u.hi);
+    }
+    if (f.hi > 0.f) bhi = u.hi; else blo = u.hi;
+    dfl un = df_add_f(u, d);
+    if (!(un.hi > blo && un.hi < bhi)) un = {0.5f * (blo + bhi), 0.f};  // safeguard: bisect
+    u = un;
+  }
+  return false;
+}
+
+// Splits a finite double into a double-float pair (hi: nearest float, lo: nearest float to the rest).
+__device__ __forceinline__ dfl split_double(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+
+__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+__global__ void __launch_bounds__(256, 3) k_fermi_df(const double* __restrict__ phi0, const uint8_t* __restrict__ solvent,
+                                                  const double* __restrict__ ffix, SpeciesDF sp, Exp2Table tab, Geom g,
+                                                  double* b1, double* sig, double* c2, float* u32, int warm, int* err) {
+  __shared__ float thi[64], tlo[64];
+  if (threadIdx.x < 64) {
+    thi[threadIdx.x] = tab.hi[threadIdx.x];
+    tlo[threadIdx.x] = tab.lo[threadIdx.x];
+  }
+  __syncthreads();
+  const dfl lam = {sp.lamhi, sp.lamlo};
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < g.np; c += (long)gridDim.x * blockDim.x) {
+    const long row = c / g.px;
+    const int i = (int)(c - row * g.px);
+    if (i >= g.nx) continue;  // pad column
+    const long k = row / g.ny;
+    const double ph = phi0[c];
+    if (!solvent[c]) {
+      b1[c] = 0.0;
+      sig[c] = 0.0;
+      c2[c] = ffix[c];
+      continue;
+    }
+    FermiDF fo;
+    const bool ok = fermi_point_df(sp, split_double(ph), warm ? u32[c] : sp.lgB, thi, tlo, fo);
+    dfl rho = {0.f, 0.f};
+    float kap = 0.f;
+    if (ok) {
+      u32[c] = fo.u.hi;
+#pragma unroll
+      for (int s = 0; s < MAXSP; ++s) {
+        if (s >= sp.ns) break;
+        rho = df_add(rho, df_mul_f(fo.C[s], sp.z[s]));
+        kap = fmaf(sp.z[s] * sp.z[s], fo.C[s].hi, kap);
+      }
+      kap *= sp.lamhi;
+    } else {
+      atomicExch(err, 5);
+    }
+    const double kd = (double)kap;
+    b1[c] = (k > 0 && k < g.nz - 1) ? -df_to_double(df_mul(lam, rho)) : 0.0;
+    sig[c] = kd;
+    c2[c] = fma(kd, ph, ffix[c]);
+  }
+}
+
+SpeciesDF species_df(const SpeciesParams& sp) {
+  SpeciesDF d{};
+  d.ns = sp.ns;
+  auto split = [](double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+  };
+  for (int i = 0; i < sp.ns; ++i) {
+    d.present[i] = sp.lvc[i] > -INFINITY ? 1 : 0;
+    d.z[i] = (float)sp.z[i];
+    split(sp.p[i], d.phi[i], d.plo[i]);
+    d.inv_p[i] = (float)sp.inv_p[i];
+    split(d.present[i] ? sp.lvc[i] - sp.p[i] * sp.lgB : -200.0, d.chi[i], d.clo[i]);
+    split(sp.inv_v[i], d.ivhi[i], d.ivlo[i]);
+  }
+  d.lnn = (float)sp.lnn;
+  d.lgB = (float)sp.lgB;
+  split(sp.lam, d.lamhi, d.lamlo);
+  return d;
 }
 
 __global__ void k_pf2_rhs(const double* __restrict__ psi, const uint8_t* __restrict__ solvent,
@@ -593,8 +757,17 @@ cudaError_t launch_unpack(const double* src, double* dst, const Geom& g, int cou
 
 cudaError_t launch_fermi(const double* phi0, const uint8_t* solvent, const double* ffix, const SpeciesParams& sp,
                          const Geom& g, double* b1, double* sig, double* c2, double* C, double* S, double* G,
-                         double* ulast, int warm, int* err, cudaStream_t s) {
-  k_fermi<<<ew_blocks(g.np), 256, 0, s>>>(phi0, solvent, ffix, sp, g, b1, sig, c2, C, S, G, ulast, warm, err);
+                         double* ulast, int warm, int* err, cudaStream_t s, const float* u32start) {
+  k_fermi<<<ew_blocks(g.np), 256, 0, s>>>(phi0, solvent, ffix, sp, g, b1, sig, c2, C, S, G, ulast, warm, err,
+                                          u32start);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fermi_df(const double* phi0, const uint8_t* solvent, const double* ffix, const SpeciesDF& sp,
+                            const Geom& g, double* b1, double* sig, double* c2, float* u32, int warm, int* err,
+                            cudaStream_t s) {
+  static const Exp2Table tab = make_exp2_table();
+  k_fermi_df<<<ew_blocks(g.np), 256, 0, s>>>(phi0, solvent, ffix, sp, tab, g, b1, sig, c2, u32, warm, err);
   return cudaGetLastError();
 }
 

@@ -44,7 +44,8 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_1711_04060_gb300 import _binding as B
     structs = {"pf_species": B.pf_species, "pf_coeffs": B.pf_coeffs, "pf_solve_opts": B.pf_solve_opts,
                "pf_report": B.pf_report, "pf_nl_opts": B.pf_nl_opts, "pf_result": B.pf_result,
-               "pf_request": B.pf_request, "pf_profile": B.pf_profile, "pf_batch_tune": B.pf_batch_tune}
+               "pf_request": B.pf_request, "pf_profile": B.pf_profile, "pf_batch_tune": B.pf_batch_tune,
+               "pf_sites": B.pf_sites}
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
@@ -95,12 +96,12 @@ def test_size_limit_is_refused_before_allocation(lib):
 
 
 def test_grid_bytes_without_device(lib):
-    """The device footprint the server budgets by: about 385 bytes per padded node plus fixed buffers, and two
+    """The device footprint the server budgets by: about 389 bytes per padded node plus fixed buffers, and two
     FP64 vectors per Anderson history column plus three."""
     from paper_1711_04060_gb300 import api
     n = 257
     np_ = (n + 7) // 8 * 8 * n * n
     b0 = api.pf_grid_bytes(n, n, n)
-    assert 385 * np_ < b0 < 385 * np_ + (1 << 20)
+    assert 389 * np_ < b0 < 389 * np_ + (1 << 20)
     assert api.pf_grid_bytes(n, n, n, 5) - b0 == (2 * 5 + 3) * 8 * np_
     assert api.pf_grid_bytes(0, 4, 4) == 0

@@ -82,3 +82,27 @@ def test_all_cores_oracle_copy_agrees(orc):
     with orc.using(L):
         xa = orc.bicgstab(g.nx, g.ny, g.nz, A, p.b, tol=1e-12, max_it=2000)["x"]
     assert np.abs(xa - x1).max() <= 1e-9 * np.abs(x1).max()
+
+
+def test_ablation_host_step_against_the_oracle(orc):
+    """The ablation's host-side pointwise step (numpy, bench.py) and charge spreading agree with the oracle's."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1711_04060_gb300 import workloads as W
+    prob = W.config2(n=17)
+    sp = bench.host_species(prob)
+    assert sp["lam"] == orc.lam(prob.T_K) and abs(sp["Tv"] - orc.thermal_voltage(prob.T_K)) < 1e-18
+    phi = W.uniform(W.substream(21, 1), 3000, -15.0, 15.0)
+    u = np.full(len(phi), np.log(sp["gB"]))
+    rho, kap = bench.host_fermi_chunk(sp, phi, u)
+    z = [s.z for s in prob.species]
+    osp = orc.species_setup(z, [s.radius_A for s in prob.species], [s.bulk_M for s in prob.species])
+    r = orc.fermi_nodes(osp, z, phi)
+    orho = (np.asarray(z, float)[:, None] * r["C"]).sum(0)
+    okap = orc.lam(prob.T_K) * (np.asarray(z, float)[:, None] ** 2 * r["C"]).sum(0)
+    assert np.abs(rho - orho).max() <= 1e-12 * np.abs(orho).max()
+    assert np.abs(kap - okap).max() <= 1e-12 * np.abs(okap).max()
+    assert np.abs(u - np.log(r["Gamma"])).max() <= 1e-12
+    g = prob.grid
+    _, ffix = orc.spread_charges(g.nx, g.ny, g.nz, g.h, g.origin, prob.charges, orc.lam(prob.T_K))
+    assert np.abs(bench.host_spread(prob, orc.lam(prob.T_K)) - ffix).max() <= 1e-12 * np.abs(ffix).max()

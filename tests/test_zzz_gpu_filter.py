@@ -117,3 +117,43 @@ def test_filter_region_cleared_by_new_coefficients_and_refused_in_batches(api, o
     plain.close()
     grid.close()
     assert _rel(out["phi_V"], ref["phi_V"]) < 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_site_model_on_the_device_matches_oracle(api, orc, precision):
+    """pf_set_filter_sites: the site potentials of Eq. (19) and the site steric potential of Eq. (20) computed
+    on the device against the oracle's pfo_site_potentials / pfo_site_steric, and the nonlinear solve with the
+    region they define against the oracle's fixed-region solve."""
+    prob = _channel(1.2)
+    g = prob.grid
+    centres = np.array([[0.3, -0.2, -1.5], [-0.4, 0.3, 0.6], [0.2, 0.1, 2.4]])
+    radii, q_ion, occ, ion_r = [0.95, 0.99, 0.95], [1.0, 2.0, 1.0], [1, 0, 1], [0.95, 0.99, 0.95]
+    st, phib = orc.site_potentials(centres, radii, q_ion, occ, 80.0, prob.charges, 20.0, orc.lam())
+    assert st == 0
+    Tv = orc.thermal_voltage(prob.T_K)
+    grid = api.Grid.for_problem(prob)
+    phi_sites, S = grid.set_filter_sites(centres, radii, q_ion, occ, ion_r, 80.0, 20.0, map_radius_A=0.87 * g.h,
+                                         v_sites_A3=20.0)
+    np.testing.assert_allclose(phi_sites, phib * Tv, rtol=1e-12)
+    gB = orc.species_setup([1, -1, 0], [0.95, 1.81, 1.4], [0.1, 0.1, 55.5])["gammaB"]
+    assert S == pytest.approx(orc.site_steric(ion_r, occ, 20.0, gB)[1], rel=1e-13)
+    fixed, val = _sites(orc, prob)
+    ref = orc.pf_solve_problem(prob, tol_outer=1e-11, lin_tol=1e-12, fixed=fixed, fixed_phi_V=val)
+    assert ref["status"] == 0
+    prec = api.PF_FP64 if precision == "fp64" else api.PF_MIXED
+    out, rep = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=prec, max_outer=2000))
+    assert rep["status"] == 0
+    assert _rel(out["phi_V"], ref["phi_V"], floor=0.0257) < (TOL_FP64 if precision == "fp64" else TOL_MIXED)
+    f = fixed == 1
+    np.testing.assert_allclose(out["phi_V"][f], val[f], rtol=1e-12)
+    assert np.all(out["Psi"][f] == 0.0)
+    # a six-point position on another occupied site's centre, or ions that fill the site volume, are refused and
+    # leave the region as it was
+    with pytest.raises(api.PFError):
+        grid.set_filter_sites([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]], [0.5, 0.5], [1.0, 1.0], [1, 1], [0.5, 0.5], 80.0,
+                              20.0, v_sites_A3=20.0)
+    with pytest.raises(api.PFError):
+        grid.set_filter_sites(centres, radii, q_ion, [1, 1, 1], ion_r, 80.0, 20.0, v_sites_A3=5.0)
+    again, _ = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=prec, max_outer=2000))
+    grid.close()
+    assert _rel(again["phi_V"], out["phi_V"], floor=0.0257) < (TOL_FP64 if precision == "fp64" else TOL_MIXED)
