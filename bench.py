@@ -78,15 +78,22 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--cpu-nodes", type=int, default=100000, help="nodes of the oracle's timed pointwise-step sample")
     ap.add_argument("--no-tight", action="store_true", help="skip the tight-tolerance legs and their reference solve")
-    ap.add_argument("--tight-tol-outer", type=float, default=1e-8)
-    ap.add_argument("--tight-lin-tol", type=float, default=1e-10)
+    ap.add_argument("--tight-tol-outer", type=float, default=1e-9)
+    ap.add_argument("--tight-lin-tol", type=float, default=1e-11)
+    ap.add_argument("--tight-accel", type=int, default=5,
+                    help="Anderson depth of the tight legs (the relaxed iteration needs thousands of outer steps there)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="solves of the end-to-end leg (at most --steps)")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle checks of the returned solution")
     ap.add_argument("--ablation-outer", type=int, default=3,
                     help="outer iterations of the host-nonlinear + GPU-linear ablation (0: skip)")
     ap.add_argument("--accel-depth", type=int, default=0, help="Anderson depth of the timed solves (0: relaxation)")
-    ap.add_argument("--serve-requests", type=int, default=16, help="requests of the serving sample (0: skip)")
-    ap.add_argument("--serve-gap", type=float, default=0.25, help="mean inter-arrival time of the serving sample (s)")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests of the serving sample (0: skip)")
+    ap.add_argument("--serve-gap", type=float, default=0.005,
+                    help="mean inter-arrival time of the serving sample (s); 0.005 is the 200/s of the request stream")
+    ap.add_argument("--serve-sub-gap", type=float, default=0.0,
+                    help="also replay the mixed-precision sample at this mean gap (s), below capacity (0: skip)")
+    ap.add_argument("--serve-sub-requests", type=int, default=0, help="requests of the sub-capacity sample")
+    ap.add_argument("--no-serve-fp64", action="store_true", help="serve in mixed precision only")
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--batch", type=int, default=64, help="instances of the batched leg (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -342,11 +349,13 @@ def config_of(args):
 
 
 # ------------------------------------------------------------------ serving sample
-def serve_sample(api, args, precision):
+def serve_sample(api, args, precision, count=None, gap=None):
     """Replays the first requests of the Poisson request stream (edges 49..193, voltage and salt drawn per
     request) against pf_submit / pf_poll at their arrival times; latency = completion - arrival."""
     from paper_1711_04060_gb300 import workloads as W
-    reqs = W.request_stream(count=args.serve_requests, seed=4, mean_gap_s=args.serve_gap)
+    count = args.serve_requests if count is None else count
+    gap = args.serve_gap if gap is None else gap
+    reqs = W.request_stream(count=count, seed=4, mean_gap_s=gap)
     probs = [(t, make()) for t, _, make in reqs]
     opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=precision,
                        accel_depth=args.accel_depth)
@@ -379,8 +388,10 @@ def serve_sample(api, args, precision):
     return {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
             "solves_per_s": len(lat) / span, "mean_nodes": nodes / max(1, len(lat)),
-            "all_ok": bool(all(st == 0 for st in status)), "offered_per_s": 1.0 / args.serve_gap,
-            "slots": args.serve_slots, "budget_GB": args.serve_budget_gb}
+            "all_ok": bool(all(st == 0 for st in status)), "offered_per_s": 1.0 / gap,
+            "slots": args.serve_slots, "budget_GB": args.serve_budget_gb,
+            "stream": f"first {count} requests of the Poisson stream (edges log-uniform in [49, 193], seed 4), mean gap "
+                      f"{gap * 1e3:g} ms"}
 
 
 # ------------------------------------------------------------------ batched leg
@@ -790,7 +801,9 @@ def run_ours(args):
                                            "peak": peak, "unit": "GB/s"}
 
     # tight tolerances: mixed and FP64 to tol_outer / lin_tol that meet the accuracy bars, timed, and every
-    # solution against a tighter FP64 reference (Anderson-accelerated: same fixed point, fewer outer steps)
+    # solution against a tighter FP64 reference.  All three use Anderson acceleration (same fixed point and
+    # stop test): the paper's relaxation contracts by about 0.98 per outer step on this workload, so it
+    # reaches tol_outer 1e-8 only after more than 500 outer iterations.
     if not args.no_tight and args.precision == "mixed":
         def timed(o):
             outs = {k: torch.zeros_like(v) for k, v in out.items()}
@@ -803,10 +816,13 @@ def run_ours(args):
             e1.synchronize()
             return e0.elapsed_time(e1), rp, {k: v.cpu().numpy() for k, v in outs.items()}
 
-        tt, tl = args.tight_tol_outer, args.tight_lin_tol
-        ms_m, rep_m, out_m = timed(api.nl_opts(tol_outer=tt, tol=tl, precision=api.PF_MIXED, inner_tol=args.inner_tol))
-        ms_d, rep_d, out_d = timed(api.nl_opts(tol_outer=tt, tol=tl, precision=api.PF_FP64))
-        ms_r, rep_r, out_r = timed(api.nl_opts(tol_outer=1e-11, tol=1e-12, precision=api.PF_FP64, accel_depth=5))
+        tt, tl, ta = args.tight_tol_outer, args.tight_lin_tol, args.tight_accel
+        ms_m, rep_m, out_m = timed(api.nl_opts(tol_outer=tt, tol=tl, precision=api.PF_MIXED, inner_tol=args.inner_tol,
+                                               accel_depth=ta, max_outer=3000))
+        ms_d, rep_d, out_d = timed(api.nl_opts(tol_outer=tt, tol=tl, precision=api.PF_FP64, accel_depth=ta,
+                                               max_outer=3000))
+        ms_r, rep_r, out_r = timed(api.nl_opts(tol_outer=tt / 10, tol=tl / 10, precision=api.PF_FP64, accel_depth=5,
+                                               max_outer=3000))
         ref_phi, ref_C = out_r["phi_V"], out_r["C_M"]
 
         def leg(ms, rp, o):
@@ -816,10 +832,11 @@ def run_ours(args):
             return d
 
         line["tight"] = {
-            "tol_outer": tt, "lin_tol": tl,
-            "reference": {"what": "FP64, Anderson depth 5 (same fixed point), tol_outer 1e-11, lin_tol 1e-12",
+            "tol_outer": tt, "lin_tol": tl, "accel_depth": ta,
+            "reference": {"what": f"FP64, Anderson depth 5, tol_outer {tt / 10:g}, lin_tol {tl / 10:g}",
                           "ms": ms_r, "outer_iters": rep_r["outer_iters"], "status": rep_r["status"]},
             "mixed": leg(ms_m, rep_m, out_m), "fp64": leg(ms_d, rep_d, out_d),
+            "mixed_vs_fp64": rel_errors(out_m["phi_V"], out_m["C_M"], out_d["phi_V"], out_d["C_M"], ns),
             "mixed_speedup_vs_fp64": ms_d / ms_m}
         if not args.no_accuracy and rank == 0:
             line["tight"]["mixed"]["accuracy_vs_oracle"] = oracle_accuracy(prob, out_m)
@@ -885,8 +902,11 @@ def run_ours(args):
     # serving: Poisson arrivals of mixed-size requests through pf_submit / pf_poll
     if args.serve_requests > 0 and world == 1:
         line["serving"] = {"mixed": serve_sample(api, args, api.PF_MIXED)}
-        if not args.no_fp64:
+        if not args.no_serve_fp64:
             line["serving"]["fp64"] = serve_sample(api, args, api.PF_FP64)
+        if args.serve_sub_gap > 0 and args.serve_sub_requests > 0:
+            line["serving"]["mixed_sub_capacity"] = serve_sample(api, args, api.PF_MIXED, args.serve_sub_requests,
+                                                                 args.serve_sub_gap)
 
     # CPU oracle on a bounded sample (rank 0, one GPU only): all host threads (OpenMP copy) and one thread
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -234,7 +234,7 @@ Krylov<float> kry32(pf_grid* g) { return {{g->r32[0], g->r32[1]}, {g->p32[0], g-
 // init = 0 writes (float) r to b32 for iterative refinement.  The state must have been reset.
 template <bool UNI>
 pf_status residual(pf_grid* g, const OpArrays<double>& A, const double* x, const double* b, int init,
-                   const Krylov<double>* K, BicgState* st) {
+                   const Krylov<double>* K, BicgState* st, const pf::ResidualExtras& ex = pf::ResidualExtras()) {
   using S = pf::SlotsRes<UNI>;
   pf::Maps<S::NH, S::NC> m;
   if constexpr (UNI) {
@@ -248,11 +248,11 @@ pf_status residual(pf_grid* g, const OpArrays<double>& A, const double* x, const
     PF_TRY((fill_maps<S::NH, S::NC, double>(g, &m, h,
                                             c)));
   }
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b, g->geom, g->part, st, g->stream));
+  if (ex.need_bb) PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_plane_bb(b, g->geom, g->part, st, g->stream));
   const int slot = prof_begin(g, 1);
   PF_CK((pf::launch_residual<UNI>(m, g->geom, A.wc, A.diagc, init, K ? K->r[0] : nullptr, K ? K->rt : nullptr,
                                   K ? K->p[0] : nullptr, K ? K->v[0] : nullptr, K ? K->t : nullptr, g->b32, g->part,
-                                  st, g->L)));
+                                  st, g->L, ex)));
   prof_end(g, slot, init ? PF_PROF_INIT : PF_PROF_RESIDUAL);
   return PF_OK;
 }
@@ -327,10 +327,13 @@ pf_status solve_fp64(pf_grid* g, int op, const double* b, double* x, const pf_so
   PF_TRY(residual<UNI>(g, A, x, b, 1, &K, g->st));  // r0 = b - A x0 (Table 3)
   BicgState s;
   PF_TRY((iterate<double, UNI>(g, A, x, K, g->st, &s)));
-  // true residual of the final iterate
+  // true residual of the final iterate (b.b kept from the start)
   BicgState tr;
   PF_TRY(set_state(g, g->st, o.tol, o.norm, 0, tol_r0, 1));
-  PF_TRY(residual<UNI>(g, A, x, b, 0, nullptr, g->st));
+  pf::ResidualExtras ex;
+  ex.need_bb = 0;
+  ex.need_max = o.norm == PF_NORM_ABSINF;
+  PF_TRY(residual<UNI>(g, A, x, b, 0, nullptr, g->st, ex));
   PF_TRY(read_state(g, g->st, &tr));
   rep->status = s.status;
   rep->iterations = s.iter;
@@ -352,9 +355,23 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
   int iters = 0, ref = 0, status = PF_E_NOCONV;
   BicgState tr{};
   for (;;) {
-    // FP64 true residual b - A x -> b32 (and its norms)
+    // FP64 true residual b - A x and its norms; the same pass starts the FP32 inner solve A d = r from d = 0
+    // (r = r~ = (float) r, p = v = t = 0) to relative tolerance inner_tol; an inner solve that stagnates is cut
+    // off after INNER_CAP iterations and its correction kept
+    const int cap = o.max_iter - iters < INNER_CAP ? o.max_iter - iters : INNER_CAP;
     PF_TRY(set_state(g, g->st, o.tol, o.norm, 0, tol_r0, ref > 0));
-    PF_TRY(residual<UNI>(g, A, x, b, 0, nullptr, g->st));
+    PF_TRY(set_state(g, g->st2, o.inner_tol, PF_NORM_REL2, cap > 0 ? cap : 1));
+    pf::ResidualExtras ex;
+    ex.need_bb = ref == 0;
+    ex.need_max = o.norm == PF_NORM_ABSINF;
+    ex.r = K.r[0];
+    ex.rt = K.rt;
+    ex.p = K.p[0];
+    ex.v = K.v[0];
+    ex.t = K.t;
+    ex.d = g->d32;
+    ex.st2 = g->st2;
+    PF_TRY(residual<UNI>(g, A, x, b, 0, nullptr, g->st, ex));
     PF_TRY(read_state(g, g->st, &tr));
     if (trace_level() > 0)
       fprintf(stderr, "[pf] mixed op %d refinement %d: true residual %.3e\n", op, ref, measure_of(tr, o.norm));
@@ -370,13 +387,6 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
       status = PF_E_NOCONV;
       break;
     }
-    // FP32 inner solve A d = r from d = 0 to relative tolerance inner_tol; an inner solve that stagnates is cut
-    // off after INNER_CAP iterations and its correction kept
-    PF_CK(cudaMemsetAsync(g->d32, 0, g->geom.np * sizeof(float), g->stream));
-    const int cap = o.max_iter - iters < INNER_CAP ? o.max_iter - iters : INNER_CAP;
-    PF_TRY(set_state(g, g->st2, o.inner_tol, PF_NORM_REL2, cap));
-    PF_LAUNCH(g, PF_PROF_INIT, pf::launch_init_zero<float>(g->b32, g->geom, K.r[0], K.rt, K.p[0], K.v[0], K.t,
-                                                            g->part, g->st2, g->stream));
     BicgState s;
     PF_TRY((iterate<float, UNI>(g, W, g->d32, K, g->st2, &s)));
     iters += s.iter;

@@ -137,7 +137,7 @@ cudaError_t launch_pack(const void* src, void* dst, const Geom& g, int type, cud
 cudaError_t launch_unpack(const double* src, double* dst, const Geom& g, int count, cudaStream_t s);
 
 // ---- BiCGSTAB (Table 3) ----
-// keep_r0 != 0 keeps r0norm2 of the previous state (later refinement steps of one solve)
+// keep_r0 != 0 keeps r0norm2 and bnorm2 of the previous state (later refinement steps of one solve)
 cudaError_t launch_set_state(BicgState* st, double tol, int norm, int max_iter, double tol_r0, int keep_r0,
                              cudaStream_t s);
 // b.b over the two Dirichlet planes -> st->bnorm2 (uses the partials buffer and the state's ticket)
@@ -150,12 +150,21 @@ cudaError_t launch_wait_probe(unsigned long long limit, int* status, cudaStream_
 template <typename T>
 cudaError_t launch_init_zero(const T* b, const Geom& g, T* r, T* rt, T* p, T* v, T* t, double* part, BicgState* st,
                              cudaStream_t s);
+// Options of the FP64 residual: need_bb = 0 reuses b.b kept in the state (a later refinement step of the same
+// right-hand side); need_max = 0 skips max |r| (2-norm stop test); st2 != nullptr starts the FP32 inner solve
+// of refinement in the same pass: r = r~ = (float) r, p = v = t = d = 0 and st2 from ||r||^2.
+struct ResidualExtras {
+  int need_bb = 1, need_max = 1;
+  float *r = nullptr, *rt = nullptr, *p = nullptr, *v = nullptr, *t = nullptr, *d = nullptr;
+  BicgState* st2 = nullptr;
+};
 // r = b - A x (x holds b on identity rows) in FP64; init = 1 also writes r~ = r, p = v = t = 0 and starts
-// the BiCGSTAB state; init = 0 writes r32 = (float) r and the refinement state
+// the BiCGSTAB state; init = 0 writes r32 = (float) r (or starts the inner solve, see ResidualExtras) and the
+// refinement state
 template <bool UNI>
 cudaError_t launch_residual(const Maps<SlotsRes<UNI>::NH, SlotsRes<UNI>::NC>& m, const Geom& g, double wc,
                             double diagc, int init, double* r, double* rt, double* p, double* v, double* t, float* r32,
-                            double* part, BicgState* st, const Launch& L);
+                            double* part, BicgState* st, const Launch& L, const ResidualExtras& ex = ResidualExtras());
 template <typename T, bool UNI>
 cudaError_t launch_phase_b(const Maps<SlotsB<UNI>::NH, SlotsB<UNI>::NC>& m, const Geom& g, T wc, T* t, double* part,
                            BicgState* st, const Launch& L);

@@ -221,14 +221,17 @@ __global__ void __launch_bounds__(NTHREADS) k_plane_bb(const double* __restrict_
   }
 }
 
+// keep_r0 != 0 keeps r0norm2 and bnorm2 of the previous state (the same right-hand side)
 __global__ void k_set_state(BicgState* st, double tol, int norm, int max_iter, double tol_r0, int keep_r0) {
   const double r0 = keep_r0 ? st->r0norm2 : -1.0;
+  const double b0 = keep_r0 ? st->bnorm2 : 0.0;
   BicgState s = {};
   s.tol = tol;
   s.norm = norm;
   s.max_iter = max_iter;
   s.tol_r0 = tol_r0;
   s.r0norm2 = r0;
+  s.bnorm2 = b0;
   *st = s;
 }
 
@@ -654,8 +657,19 @@ cudaError_t launch_phase_ca(const Maps<SlotsCA<UNI>::NH, SlotsCA<UNI>::NC>& m, c
 template <bool UNI>
 cudaError_t launch_residual(const Maps<SlotsRes<UNI>::NH, SlotsRes<UNI>::NC>& m, const Geom& g, double wc,
                             double diagc, int init, double* r, double* rt, double* p, double* v, double* t, float* r32,
-                            double* part, BicgState* st, const Launch& L) {
+                            double* part, BicgState* st, const Launch& L, const ResidualExtras& ex) {
   typename OpRes<UNI>::Args a{part, st, wc, diagc, init, r, rt, p, v, t, r32};
+  a.need_bb = ex.need_bb;
+  a.need_max = ex.need_max;
+  if (ex.st2) {
+    a.in_r = ex.r;
+    a.in_rt = ex.rt;
+    a.in_p = ex.p;
+    a.in_v = ex.v;
+    a.in_t = ex.t;
+    a.in_d = ex.d;
+    a.st2 = ex.st2;
+  }
   return launch_stencil<OpRes<UNI>>(m, a, g, L);
 }
 
@@ -805,10 +819,10 @@ PF_INST(float, false)
 PF_INST(float, true)
 template cudaError_t launch_residual<false>(const Maps<SlotsRes<false>::NH, SlotsRes<false>::NC>&, const Geom&, double,
                                             double, int, double*, double*, double*, double*, double*, float*, double*,
-                                            BicgState*, const Launch&);
+                                            BicgState*, const Launch&, const ResidualExtras&);
 template cudaError_t launch_residual<true>(const Maps<SlotsRes<true>::NH, SlotsRes<true>::NC>&, const Geom&, double,
                                            double, int, double*, double*, double*, double*, double*, float*, double*,
-                                           BicgState*, const Launch&);
+                                           BicgState*, const Launch&, const ResidualExtras&);
 template cudaError_t launch_init_zero<float>(const float*, const Geom&, float*, float*, float*, float*, float*, double*,
                                              BicgState*, cudaStream_t);
 template cudaError_t launch_init_zero<double>(const double*, const Geom&, double*, double*, double*, double*, double*,

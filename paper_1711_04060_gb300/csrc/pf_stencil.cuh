@@ -318,9 +318,10 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
   using T = typename Op::T;
   constexpr int D = Op::D, NH = Op::NH, NC = Op::NC;
   constexpr int HB = halo_slot_bytes<T>(), CB = centre_slot_bytes<T>(), STAGE = stage_bytes<Op>();
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // 128-byte aligned start, formed by an offset on the shared array so that the compiler keeps every stage and
+  // plane access in the shared address space
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   T* qring = reinterpret_cast<T*>(smem + D * STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + D * STAGE + 3 * PLANE * sizeof(T));
   double* wsum = reinterpret_cast<double*>(bars + D);
@@ -704,6 +705,12 @@ struct OpRes {
     int init;
     double *r, *rt, *p, *v, *t;
     float* r32;
+    int need_bb = 1;   // 0: b.b of this right-hand side is already in st->bnorm2 (later refinement steps)
+    int need_max = 1;  // 0: the stop test is the 2-norm, max |r| is not needed
+    // init = 0 with in_r set: start the FP32 inner solve of refinement here (in place of writing r32 and a
+    // separate start kernel): r = r~ = (float) r, p = v = t = d = 0, and its state st2 from ||r||^2
+    float *in_r = nullptr, *in_rt = nullptr, *in_p = nullptr, *in_v = nullptr, *in_t = nullptr, *in_d = nullptr;
+    BicgState* st2 = nullptr;
   };
   struct Sc {
     int unused;
@@ -766,12 +773,20 @@ struct OpRes {
       a.p[cidx] = 0.0;
       a.v[cidx] = 0.0;
       a.t[cidx] = 0.0;
+    } else if (a.in_r) {
+      const float rf = (float)rc;
+      a.in_r[cidx] = rf;
+      a.in_rt[cidx] = rf;
+      a.in_p[cidx] = 0.f;
+      a.in_v[cidx] = 0.f;
+      a.in_t[cidx] = 0.f;
+      a.in_d[cidx] = 0.f;
     } else {
       a.r32[cidx] = (float)rc;
     }
     acc.rr = fma(rc, rc, acc.rr);
-    acc.bb = fma(c.b, c.b, acc.bb);
-    acc.rmax = fmax(acc.rmax, fabs(rc));
+    if (a.need_bb) acc.bb = fma(c.b, c.b, acc.bb);
+    if (a.need_max) acc.rmax = fmax(acc.rmax, fabs(rc));
   }
   __device__ static void finish(const Args& a, const Accs& acc, const double* wsum, double* scratch, int bid,
                                 int nblk) {
@@ -782,7 +797,8 @@ struct OpRes {
     total_partials<3>(a.part, 4u, tot, scratch, nblk);
     if (threadIdx.x != 0) return;
     BicgState* st = a.st;
-    double bb = tot[1] + st->bnorm2;  // bnorm2 was preset to b.b over the Dirichlet planes
+    // bnorm2 was preset to b.b over the Dirichlet planes, or kept from the first residual of this solve
+    double bb = a.need_bb ? tot[1] + st->bnorm2 : st->bnorm2;
     if (bb == 0.0) bb = 1.0;
     st->bnorm2 = bb;
     st->rnorm2 = tot[0];
@@ -798,6 +814,21 @@ struct OpRes {
     }
     st->done = conv ? 1 : 0;
     st->ticket = 0;
+    if (a.st2) {  // the FP32 inner solve on r starts here (its tolerance, norm and limit were set before)
+      BicgState* s2 = a.st2;
+      const double b2 = tot[0] > 0.0 ? tot[0] : 1.0;
+      s2->bnorm2 = b2;
+      s2->rho = tot[0];
+      s2->rnorm2 = tot[0];
+      s2->rinf = tot[2];
+      set_tol2(s2, tot[0], b2);
+      s2->alpha = s2->omega = s2->beta = 0.0;
+      s2->sexit = 0;
+      s2->iter = 0;
+      s2->status = 0;
+      s2->done = (s2->norm == 0 ? tot[0] <= s2->tol2 : tot[2] < s2->tol) ? 1 : 0;
+      s2->ticket = 0;
+    }
   }
 };
 
