@@ -414,6 +414,7 @@ def batch_sample(api, args, torch, dev):
         torch.cuda.synchronize(dev)
         t_batch = time.perf_counter() - t0
         tune = batch.tune()
+        bstats = batch.stats()
         t0 = time.perf_counter()
         worst_phi, seq_ok = 0.0, True
         for g, (out, _) in zip(grids, res):
@@ -428,7 +429,17 @@ def batch_sample(api, args, torch, dev):
         for g in grids:
             g.close()
     sizes = sorted({p.grid.nx for p in probs})
+    # FP32 BiCGSTAB iterations move at least 64 B per interior node (PF1's uniform faces) and at most 88 B (the
+    # variable-dielectric operators); the refinement residuals and pointwise steps come on top
+    it_nodes = sum(r["lin_iters_total"] * p.grid.nx * p.grid.ny * (p.grid.nz - 2) for p, (_, r) in zip(probs, res))
+    dev_s = bstats["device_ms"] / 1e3
+    engine = {"ticks": bstats["ticks"], "wall_s": bstats["wall_ms"] / 1e3, "device_busy_s": dev_s,
+              "device_busy_fraction": dev_s / t_batch if t_batch > 0 else None,
+              "host_ms_per_tick": (bstats["wall_ms"] - bstats["device_ms"]) / max(1, bstats["ticks"]),
+              "bicgstab_iteration_GBps_range": [round(64 * it_nodes / dev_s / 1e9, 1),
+                                                round(88 * it_nodes / dev_s / 1e9, 1)] if dev_s > 0 else None}
     return {"workload": f"{args.batch} channel problems, n in {sizes}, mixed precision, one pf_batch",
+            "engine": engine,
             "value": args.batch / t_batch, "unit": UNIT, "s": t_batch,
             "all_ok": bool(all(r["status"] == 0 for _, r in res)), "outer_iters_sum": int(sum(r["outer_iters"] for _, r in res)),
             "tiles_per_block": tune["chosen"], "tile_z_planes": tune["chosen_z"],

@@ -401,6 +401,18 @@ pf_status pf_batch_get_tune(pf_batch* b, pf_batch_tune* out);
  * its own).  accel_depth and lin_forcing work per grid as in pf_nonlinear_solve. */
 pf_status pf_batch_nonlinear_solve(pf_batch* b, const pf_nl_opts* opts, pf_result* results);
 
+/* Where the time of the last pf_batch_nonlinear_solve went: the engine's ticks (one step of every problem's
+ * state machine, its shared launches and the read-back of all problems' solver states), their summed host wall
+ * time, and the summed device span of each tick's work (from its first launch to the state read-back, CUDA
+ * events on the batch stream).  wall_ms - device_ms is the host's share between ticks; device_ms / wall_ms
+ * the fraction of the ticks' time the device had work queued.  Not in the paper. */
+typedef struct {
+  long long ticks;
+  double wall_ms;
+  double device_ms;
+} pf_batch_stats;
+pf_status pf_batch_get_stats(pf_batch* b, pf_batch_stats* out);
+
 /* Frees the batch (not its grids). */
 pf_status pf_batch_destroy(pf_batch* b);
 

@@ -75,6 +75,10 @@ class pf_sites(ctypes.Structure):
                 ("ion_radius_A", _VP), ("eps_b", _D), ("eps_p", _D), ("map_radius_A", _D), ("v_sites_A3", _D)]
 
 
+class pf_batch_stats(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_longlong), ("wall_ms", _D), ("device_ms", _D)]
+
+
 PF_BATCH_TUNE_MAX = 16
 
 
@@ -106,6 +110,7 @@ SIGNATURES = {
     "pf_selftest_wait_timeout": (_I, [ctypes.c_ulonglong, _VP]),
     "pf_fermi_noalloc": (_I, [ctypes.c_long, _VP, _VP, _I, ctypes.POINTER(pf_species), _D, _I, _VP, _VP, _VP, _VP]),
     "pf_batch_create": (_I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
+    "pf_batch_get_stats": (_I, [_VP, ctypes.POINTER(pf_batch_stats)]),
     "pf_batch_set_tiles_per_block": (_I, [_VP, _I]),
     "pf_batch_set_tiling": (_I, [_VP, _I, _I]),
     "pf_batch_autotune": (_I, [_VP, ctypes.POINTER(pf_batch_tune)]),

@@ -408,6 +408,11 @@ class Batch:
     def nonlinear_solve(self, opts=None, outs=None, allow=()):
         return pf_batch_nonlinear_solve(self.handle, [(g.n, g.n_species) for g in self.grids], opts, outs, allow)
 
+    def stats(self):
+        st = B.pf_batch_stats()
+        _check(B.load().pf_batch_get_stats(self.handle, ctypes.byref(st)))
+        return {"ticks": st.ticks, "wall_ms": st.wall_ms, "device_ms": st.device_ms}
+
     def close(self):
         pf_batch_destroy(self.handle)
         self.handle = None

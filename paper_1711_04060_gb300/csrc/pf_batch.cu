@@ -17,6 +17,8 @@
 // tiles_per_block is chosen by timing the FP32 phase kernels of the batch's own operators for each
 // candidate (pf_batch_autotune), or set by the caller.  The tensor maps and arguments of all problems live
 // in device tables that each block reads at start.
+#include <chrono>
+
 #include "pf_decomp.cuh"
 #include "pf_grid.cuh"
 #include "pf_stencil.cuh"
@@ -106,6 +108,8 @@ struct pf_batch {
   cudaStream_t ops[N_OPS] = {};   // the batched launches of each operator run concurrently on these
   cudaStream_t cstream = nullptr; // chunk graphs are captured here
   cudaEvent_t fork = nullptr, join[N_OPS] = {};
+  cudaEvent_t tick0 = nullptr, tick1 = nullptr;  // device span of a tick's work (launches to state read-back)
+  pf_batch_stats stats{};                        // of the last pf_batch_nonlinear_solve
   int tpb = 0;                    // tiles per block; 0: tune at the next solve
   int zc = pf::ZC;                // interior z-planes per tile
   pf_batch_tune tune{};
@@ -672,8 +676,10 @@ void post(BatchMember& M, const BicgState& s64, const BicgState& s32) {
 // One tick of the engine over all members.
 pf_status tick(pf_batch* B) {
   NvtxRange range("batch tick");
+  const auto wall0 = std::chrono::steady_clock::now();
   PF_TRY(build(B));
   cudaStream_t s = B->stream;
+  PF_CK(cudaEventRecord(B->tick0, s));
   const int n = (int)B->members.size();
   std::vector<std::vector<int>> kinds(n);
   std::vector<char> use(N_SLOTS, 0);
@@ -725,7 +731,13 @@ pf_status tick(pf_batch* B) {
   pf::k_gather_states<<<(n + 127) / 128, 128, 0, s>>>(B->dst64, B->dst32, n, B->dgather);
   PF_CK(cudaGetLastError());
   PF_CK(cudaMemcpyAsync(B->hgather, B->dgather, 2 * n * sizeof(BicgState), cudaMemcpyDeviceToHost, s));
+  PF_CK(cudaEventRecord(B->tick1, s));
   PF_CK(cudaStreamSynchronize(s));
+  {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, B->tick0, B->tick1) == cudaSuccess) B->stats.device_ms += ms;
+    ++B->stats.ticks;
+  }
   // transitions; the outer update's later stages (Anderson inner products, least squares)
   bool dots = false;
   std::vector<char> stop(n, 0);
@@ -769,6 +781,7 @@ pf_status tick(pf_batch* B) {
       M.stage = S_FERMI;
     }
   }
+  B->stats.wall_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
   return PF_OK;
 }
 
@@ -867,6 +880,8 @@ pf_status batch_alloc(cudaStream_t user, int count_hint, pf_batch** out) {
   if (e == cudaSuccess) e = cudaMallocHost(&B->harena, B->cap);
   if (e == cudaSuccess) e = cudaEventCreate(&B->e0);
   if (e == cudaSuccess) e = cudaEventCreate(&B->e1);
+  if (e == cudaSuccess) e = cudaEventCreate(&B->tick0);
+  if (e == cudaSuccess) e = cudaEventCreate(&B->tick1);
   if (e != cudaSuccess) {
     pf_batch_destroy(B);
     cudaGetLastError();
@@ -965,6 +980,12 @@ pf_status pf_batch_get_tune(pf_batch* B, pf_batch_tune* out) {
   return PF_OK;
 }
 
+pf_status pf_batch_get_stats(pf_batch* B, pf_batch_stats* out) {
+  if (!B || !out) return fail(PF_E_INVAL, "batch and out are required");
+  *out = B->stats;
+  return PF_OK;
+}
+
 pf_status pf_batch_nonlinear_solve(pf_batch* B, const pf_nl_opts* opts, pf_result* results) {
   if (!B || !results) return fail(PF_E_INVAL, "batch and results are required");
   pf_nl_opts o;
@@ -983,6 +1004,7 @@ pf_status pf_batch_nonlinear_solve(pf_batch* B, const pf_nl_opts* opts, pf_resul
   cudaStream_t s = B->stream;
   PF_CK(cudaEventRecord(B->e0, s));
   if (B->tpb == 0) PF_TRY(autotune(B));
+  B->stats = pf_batch_stats{};
   B->members.assign(n, BatchMember{});
   for (int i = 0; i < n; ++i) {
     B->members[i].g = B->grids[i];
@@ -1038,6 +1060,8 @@ pf_status pf_batch_destroy(pf_batch* B) {
   if (B->hgather) cudaFreeHost(B->hgather);
   if (B->e0) cudaEventDestroy(B->e0);
   if (B->e1) cudaEventDestroy(B->e1);
+  if (B->tick0) cudaEventDestroy(B->tick0);
+  if (B->tick1) cudaEventDestroy(B->tick1);
   if (B->fork) cudaEventDestroy(B->fork);
   for (int o = 0; o < N_OPS; ++o) {
     if (B->join[o]) cudaEventDestroy(B->join[o]);

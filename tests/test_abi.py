@@ -45,7 +45,7 @@ def test_struct_layouts_match_c(tmp_path):
     structs = {"pf_species": B.pf_species, "pf_coeffs": B.pf_coeffs, "pf_solve_opts": B.pf_solve_opts,
                "pf_report": B.pf_report, "pf_nl_opts": B.pf_nl_opts, "pf_result": B.pf_result,
                "pf_request": B.pf_request, "pf_profile": B.pf_profile, "pf_batch_tune": B.pf_batch_tune,
-               "pf_sites": B.pf_sites}
+               "pf_sites": B.pf_sites, "pf_batch_stats": B.pf_batch_stats}
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
