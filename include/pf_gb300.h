@@ -164,7 +164,7 @@ void pf_default_nl_opts(pf_nl_opts* o);
 
 /* Creates a grid: nx, ny >= 2, nz >= 3, h_A > 0; origin_A[3] is the coordinate of node (0,0,0).
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream) that every later call on
- * this grid uses.  Allocates the device state of the grid (about 370 bytes per node: operators,
+ * this grid uses.  Allocates the device state of the grid (about 390 bytes per node: operators,
  * FP64 and FP32 Krylov vectors, nonlinear state and outputs); returns PF_E_OOM when that fails.
  * *out receives the handle. */
 pf_status pf_create_grid(int nx, int ny, int nz, double h_A, const double origin_A[3],
