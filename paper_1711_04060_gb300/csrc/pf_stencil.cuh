@@ -123,7 +123,45 @@ struct Partials {
   }
 };
 
-constexpr int WSUM_MAX = 8;  // FP64 warp totals per warp (at least the largest NV of a Partials)
+// FP32 kernels: GB300's FP64 pipe issues 1/64 of the FP32 rate, so the per-tile flush stays on the FP32 pipes: the
+// 32 lane sums are added by an FP32 shuffle tree (5 roundings on top of the lanes' own FP32 sums) and lane 0 adds
+// the warp's tile sum to a compensated (TwoSum, Knuth) hi + lo pair in the same shared slot; the pair becomes an
+// FP64 value once, in the block reduction at the end of the kernel.
+template <int NV>
+struct Partials<float, NV> {
+  float t[NV];
+  __device__ __forceinline__ Partials() {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) t[j] = 0.f;
+  }
+  __device__ __forceinline__ void flush(double* wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2* w2 = reinterpret_cast<float2*>(wsum);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      float v = t[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        float2 acc = w2[warp * NV + j];
+        const float s = __fadd_rn(acc.x, v);
+        const float bb = __fsub_rn(s, acc.x);
+        const float e = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+        acc.x = s;
+        acc.y = __fadd_rn(acc.y, e);
+        w2[warp * NV + j] = acc;
+      }
+      t[j] = 0.f;
+    }
+  }
+  __device__ __forceinline__ static double total(const double* wsum, int j) {
+    if ((threadIdx.x & 31) != 0) return 0.0;
+    const float2 acc = reinterpret_cast<const float2*>(wsum)[(threadIdx.x >> 5) * NV + j];
+    return (double)acc.x + (double)acc.y;
+  }
+};
+
+constexpr int WSUM_MAX = 8;  // warp totals per warp (at least the largest NV of a Partials)
 
 // Block reduction of NV values (bit j of maxmask: value j is a maximum, else a sum) into
 // part[bid * NPART + j] (bid: the block's index among the blocks of its reduction, blockIdx.x by
@@ -151,6 +189,33 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], unsigned maxmask
       a = ((maxmask >> j) & 1u) ? fmax(a, scratch[w * NV + j]) : a + scratch[w * NV + j];
     part[bid * NPART + j] = a;
   }
+}
+
+// The same block reduction for values that lane 0 of each warp already holds as the warp's total (the other lanes'
+// values are ignored): no shuffle stage, so the FP32 kernels spend only NV short sums of FP64 work here.
+template <int NV>
+__device__ __forceinline__ void block_partials_warp_totals(const double (&v)[NV], unsigned maxmask, double* part,
+                                                           double* scratch, int bid) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) scratch[warp * NV + j] = v[j];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int j = threadIdx.x;
+    double a = scratch[j];
+    for (int w = 1; w < NTHREADS / 32; ++w)
+      a = ((maxmask >> j) & 1u) ? fmax(a, scratch[w * NV + j]) : a + scratch[w * NV + j];
+    part[bid * NPART + j] = a;
+  }
+}
+
+// Warp maximum of a non-negative FP32 value, at every lane.
+__device__ __forceinline__ float warp_max(float m) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
 }
 
 // True in the block that arrives last of the nblk blocks (gridDim.x by default) counted on ticket;
@@ -511,9 +576,15 @@ struct OpB {
   __device__ static void finish(const Args& a, const Accs& acc, const double* wsum, double* scratch, int bid,
                                 int nblk) {
     using P = Partials<T, 5>;
-    double vals[6] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), P::total(wsum, 3), P::total(wsum, 4),
-                      (double)acc.smax};
-    block_partials<6>(vals, 32u, a.part, scratch, bid);
+    if constexpr (sizeof(T) == 4) {
+      const double vals[6] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), P::total(wsum, 3),
+                              P::total(wsum, 4), (double)warp_max(acc.smax)};
+      block_partials_warp_totals<6>(vals, 32u, a.part, scratch, bid);
+    } else {
+      double vals[6] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), P::total(wsum, 3),
+                        P::total(wsum, 4), (double)acc.smax};
+      block_partials<6>(vals, 32u, a.part, scratch, bid);
+    }
     if (!arrive_last(&a.st->ticket, nblk)) return;
     double tot[6];
     total_partials<6>(a.part, 32u, tot, scratch, nblk);
@@ -642,8 +713,13 @@ struct OpCA {
   __device__ static void finish(const Args& a, const Accs& acc, const double* wsum, double* scratch, int bid,
                                 int nblk) {
     using P = Partials<T, 3>;
-    double vals[4] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), (double)acc.rmax};
-    block_partials<4>(vals, 8u, a.part, scratch, bid);
+    if constexpr (sizeof(T) == 4) {
+      const double vals[4] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), (double)warp_max(acc.rmax)};
+      block_partials_warp_totals<4>(vals, 8u, a.part, scratch, bid);
+    } else {
+      double vals[4] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), (double)acc.rmax};
+      block_partials<4>(vals, 8u, a.part, scratch, bid);
+    }
     if (!arrive_last(&a.st->ticket, nblk)) return;
     double tot[4];
     total_partials<4>(a.part, 8u, tot, scratch, nblk);
