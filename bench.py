@@ -36,12 +36,13 @@ METRIC = "PF solves/s"
 UNIT = "solves/s"
 # algorithmic DRAM bytes per interior node per launch of each stencil kernel (operator data read
 # once, each vector read or written once): phase B reads r, v, M^-1, r~ and three faces and
-# writes t; phase C+A reads r, v, t, p, M^-1, x, r~ and three faces and writes x, r, p, v; the
-# PF1 operator has uniform faces (no face arrays); the FP64 residual of refinement reads x, b,
-# M^-1, the diagonal and three faces and writes the FP32 residual.
-WORDS = {"b": 8, "ca": 14, "b_pf1": 5, "ca_pf1": 11}
+# writes t; phase C+A reads r, v, t, p, M^-1, x, r~ and three faces (FP32: the one gh array from
+# which it forms the faces) and writes x, r, p, v; the PF1 operator has uniform faces (no face
+# arrays); the FP64 residual of refinement reads x, b, M^-1, the diagonal and three faces and
+# writes the FP32 residual.
+WORDS = {"b": 8, "ca": 14, "ca_gh": 12, "b_pf1": 5, "ca_pf1": 11}
 KERNEL_BYTES = {
-    "b_fp32": WORDS["b"] * 4, "ca_fp32": WORDS["ca"] * 4, "b_fp64": WORDS["b"] * 8, "ca_fp64": WORDS["ca"] * 8,
+    "b_fp32": WORDS["b"] * 4, "ca_fp32": WORDS["ca_gh"] * 4, "b_fp64": WORDS["b"] * 8, "ca_fp64": WORDS["ca"] * 8,
     "b_fp32_pf1": WORDS["b_pf1"] * 4, "ca_fp32_pf1": WORDS["ca_pf1"] * 4, "b_fp64_pf1": WORDS["b_pf1"] * 8,
     "ca_fp64_pf1": WORDS["ca_pf1"] * 8, "residual_fp64": 7 * 8 + 4,
 }

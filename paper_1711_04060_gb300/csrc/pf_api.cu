@@ -106,7 +106,7 @@ pf_status allocate(pf_grid* g) {
                     &g->dinv2, &g->sig, &g->dinv1, &g->r64[0], &g->r64[1], &g->p64[0], &g->p64[1], &g->v64[0],
                     &g->v64[1], &g->rt64, &g->t64, &g->xb, &g->bb, &g->stage, &g->phi0, &g->phi, &g->psi, &g->b1,
                     &g->c2, &g->b2, &g->Sbuf, &g->Gbuf, &g->ulast};
-  float** d32[] = {&g->wE32, &g->wN32, &g->wU32, &g->dinvP32, &g->dinv2_32, &g->dinv1_32, &g->r32[0], &g->r32[1],
+  float** d32[] = {&g->wE32, &g->wN32, &g->wU32, &g->gh32, &g->dinvP32, &g->dinv2_32, &g->dinv1_32, &g->r32[0], &g->r32[1],
                    &g->p32[0], &g->p32[1], &g->v32[0], &g->v32[1], &g->rt32, &g->t32, &g->d32, &g->b32,
                    &g->ulast32};
   std::vector<std::pair<void**, size_t>> parts;
@@ -199,17 +199,18 @@ double pf1_face(const pf_grid* g) { return g->eps_s * g->lc * g->lc / (g->h * g-
 OpArrays<double> ops64(const pf_grid* g, int op) {
   if (op == PF_OP_PF1) {
     const double wc = pf1_face(g);
-    return {g->dinv1, nullptr, nullptr, nullptr, nullptr, wc, 6.0 * wc + g->eps_s};
+    return {g->dinv1, nullptr, nullptr, nullptr, nullptr, wc, 6.0 * wc + g->eps_s, nullptr};
   }
-  return {op == PF_OP_PF2 ? g->dinv2 : g->dinvP, op == PF_OP_PF2 ? g->diag2 : g->diagP, g->wE, g->wN, g->wU, 0.0, 0.0};
+  return {op == PF_OP_PF2 ? g->dinv2 : g->dinvP, op == PF_OP_PF2 ? g->diag2 : g->diagP, g->wE, g->wN, g->wU, 0.0, 0.0,
+          nullptr};
 }
 
 OpArrays<float> ops32(const pf_grid* g, int op) {
   if (op == PF_OP_PF1) {
     const double wc = pf1_face(g);
-    return {g->dinv1_32, nullptr, nullptr, nullptr, nullptr, wc, 6.0 * wc + g->eps_s};
+    return {g->dinv1_32, nullptr, nullptr, nullptr, nullptr, wc, 6.0 * wc + g->eps_s, nullptr};
   }
-  return {op == PF_OP_PF2 ? g->dinv2_32 : g->dinvP32, nullptr, g->wE32, g->wN32, g->wU32, 0.0, 0.0};
+  return {op == PF_OP_PF2 ? g->dinv2_32 : g->dinvP32, nullptr, g->wE32, g->wN32, g->wU32, 0.0, 0.0, g->gh32};
 }
 
 pf_status set_state(pf_grid* g, BicgState* dst, double tol, int norm, int max_iter, double tol_r0,
@@ -261,8 +262,8 @@ pf_status residual(pf_grid* g, const OpArrays<double>& A, const double* x, const
 // r~, p[0] = v[0] = t = 0 and started the state.  Returns the final device state in *out.
 template <typename T, bool UNI>
 pf_status iterate(pf_grid* g, const OpArrays<T>& A, T* x, const Krylov<T>& K, BicgState* st, BicgState* out) {
-  using SB = pf::SlotsB<UNI>;
-  using SC = pf::SlotsCA<UNI>;
+  using SB = pf::SlotsB<T, UNI>;
+  using SC = pf::SlotsCA<T, UNI>;
   const bool f64 = sizeof(T) == 8;
   const int kb = UNI ? (f64 ? PF_PROF_B_FP64_PF1 : PF_PROF_B_FP32_PF1) : (f64 ? PF_PROF_B_FP64 : PF_PROF_B_FP32);
   const int kca = UNI ? (f64 ? PF_PROF_CA_FP64_PF1 : PF_PROF_CA_FP32_PF1) : (f64 ? PF_PROF_CA_FP64 : PF_PROF_CA_FP32);
@@ -279,6 +280,13 @@ pf_status iterate(pf_grid* g, const OpArrays<T>& A, T* x, const Krylov<T>& K, Bi
       const T* cc[SC::NC] = {x, K.rt};
       PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &mca[cur], hc,
                                            cc)));
+    } else if constexpr (pf::ca_face_from_gh<T>()) {
+      const T* hb[SB::NH] = {K.r[cur], K.v[cur], A.dinv, A.wE, A.wN};
+      const T* cb[SB::NC] = {K.rt, A.wU};
+      PF_TRY((fill_maps<SB::NH, SB::NC, T>(g, &mb[cur], hb, cb)));
+      const T* hc[SC::NH] = {K.r[cur], K.v[cur], K.t, K.p[cur], A.dinv, A.gh};
+      const T* cc[SC::NC] = {x, K.rt};
+      PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &mca[cur], hc, cc)));
     } else {
       const T* hb[SB::NH] = {K.r[cur], K.v[cur], A.dinv, A.wE, A.wN};
       const T* cb[SB::NC] = {K.rt, A.wU};
@@ -487,7 +495,8 @@ pf_status filter_rows_p1(pf_grid* g) {
 // lies outside the grid.
 pf_status build_operators(pf_grid* g) {
   const long NP = g->geom.np;
-  PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_faces(g->eps, g->geom, g->h, g->wE, g->wN, g->wU, g->dsum, g->stream));
+  PF_LAUNCH(g, PF_PROF_OTHER,
+            pf::launch_faces(g->eps, g->geom, g->h, g->wE, g->wN, g->wU, g->dsum, g->gh32, g->stream));
   PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wE, g->wE32, NP, g->stream));
   PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wN, g->wN32, NP, g->stream));
   PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_to_f32(g->wU, g->wU32, NP, g->stream));
@@ -710,7 +719,7 @@ size_t pf_internal_grid_bytes(int nx, int ny, int nz, int accel_depth) {
   const pf::Geom g = pf::make_geom(nx, ny, nz);
   // Anderson acceleration adds f, f_prev, x_prev and two history columns per depth
   const int aa = accel_depth > 0 ? 3 + 2 * accel_depth : 0;
-  const size_t per_node = (32 + aa) * sizeof(double) + pf::MAXSP * sizeof(double) + 17 * sizeof(float) + 1;
+  const size_t per_node = (32 + aa) * sizeof(double) + pf::MAXSP * sizeof(double) + 18 * sizeof(float) + 1;
   return (size_t)g.np * per_node + (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double) + 8192;
 }
 

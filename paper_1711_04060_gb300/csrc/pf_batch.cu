@@ -310,7 +310,7 @@ const double* b_of(const pf_grid* g, int op) { return op == PF_OP_PF1 ? g->b1 : 
 // ---- item fillers (the same arrays, in the same slots, as the single-grid launches)
 template <typename T, bool UNI>
 pf_status fill_b(pf_grid* g, int op, int cur, pf::BatchItem<pf::OpB<T, UNI>>& it) {
-  using SB = pf::SlotsB<UNI>;
+  using SB = pf::SlotsB<T, UNI>;
   const OpArrays<T> A = opsT<T>(g, op);
   const Krylov<T> K = kryT<T>(g);
   if constexpr (UNI) {
@@ -328,11 +328,15 @@ pf_status fill_b(pf_grid* g, int op, int cur, pf::BatchItem<pf::OpB<T, UNI>>& it
 
 template <typename T, bool UNI>
 pf_status fill_ca(pf_grid* g, int op, int cur, int prime, T* x, pf::BatchItem<pf::OpCA<T, UNI>>& it) {
-  using SC = pf::SlotsCA<UNI>;
+  using SC = pf::SlotsCA<T, UNI>;
   const OpArrays<T> A = opsT<T>(g, op);
   const Krylov<T> K = kryT<T>(g);
   if constexpr (UNI) {
     const T* h[SC::NH] = {K.r[cur], K.v[cur], K.t, K.p[cur], A.dinv};
+    const T* c[SC::NC] = {x, K.rt};
+    PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &it.maps, h, c)));
+  } else if constexpr (pf::ca_face_from_gh<T>()) {
+    const T* h[SC::NH] = {K.r[cur], K.v[cur], K.t, K.p[cur], A.dinv, A.gh};
     const T* c[SC::NC] = {x, K.rt};
     PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &it.maps, h, c)));
   } else {

@@ -71,8 +71,9 @@ struct pf_grid {
   double *eps = nullptr, *wE = nullptr, *wN = nullptr, *wU = nullptr, *dsum = nullptr, *ffix = nullptr;
   uint8_t* solvent = nullptr;
   double *diagP = nullptr, *dinvP = nullptr, *diag2 = nullptr, *dinv2 = nullptr, *sig = nullptr, *dinv1 = nullptr;
-  float *wE32 = nullptr, *wN32 = nullptr, *wU32 = nullptr, *dinvP32 = nullptr, *dinv2_32 = nullptr,
-        *dinv1_32 = nullptr;
+  float *wE32 = nullptr, *wN32 = nullptr, *wU32 = nullptr;  // FP32 faces (phase B)
+  float *gh32 = nullptr;  // h^2 / (2 eps): phase C+A's FP32 faces are 1 / (gh_a + gh_b)
+  float *dinvP32 = nullptr, *dinv2_32 = nullptr, *dinv1_32 = nullptr;
   double *r64[2] = {nullptr, nullptr}, *p64[2] = {nullptr, nullptr}, *v64[2] = {nullptr, nullptr};
   double *rt64 = nullptr, *t64 = nullptr;
   float *r32[2] = {nullptr, nullptr}, *p32[2] = {nullptr, nullptr}, *v32[2] = {nullptr, nullptr};
@@ -173,13 +174,15 @@ pf_status fill_maps(pf_grid* g, pf::Maps<NH, NC>* m, const T* const (&h)[NH], co
 }
 
 // The arrays of one operator in one precision: Jacobi scaling (0 on identity rows), FP64 diagonal,
-// face arrays (null for the uniform PF1 operator), uniform face and diagonal.
+// face arrays (null for the uniform PF1 operator), uniform face and diagonal, and for the FP32
+// variable-face operators gh = h^2 / (2 eps) per node (phase C+A's faces).
 template <typename T>
 struct OpArrays {
   const T* dinv;
   const double* diag;
   const T *wE, *wN, *wU;
   double wc, diagc;
+  const T* gh;
 };
 
 // Krylov vectors of one precision

@@ -67,11 +67,20 @@ struct Maps {
 };
 
 // Slots of the stencil kernels (the API fills the maps in this order):
-//   phase B:   halo {r, v, dinv, wE, wN} (PF1: {r, v, dinv}),      centre {r~, wU} (PF1: {r~})
-//   phase C+A: halo {r, v, t, p, dinv, wE, wN} (PF1: first five), centre {x, r~, wU} (PF1: {x, r~})
+//   phase B:   halo {r, v, dinv, wE, wN},       centre {r~, wU}     (variable-face operators)
+//              halo {r, v, dinv},               centre {r~}         (PF1)
+//   phase C+A: halo {r, v, t, p, dinv, wE, wN}, centre {x, r~, wU}  (FP64 variable-face operators)
+//              halo {r, v, t, p, dinv, gh},     centre {x, r~}      (FP32 variable-face operators)
+//              halo {r, v, t, p, dinv},         centre {x, r~}      (PF1)
 //   residual:  halo {x, dinv, wE, wN} (PF1: {x, dinv}),             centre {b, diag, wU} (PF1: {b})
-template <bool UNI> struct SlotsB { static constexpr int NH = UNI ? 3 : 5, NC = UNI ? 1 : 2; };
-template <bool UNI> struct SlotsCA { static constexpr int NH = UNI ? 5 : 7, NC = UNI ? 2 : 3; };
+// gh = h^2 / (2 eps) per node: the FP32 phase C+A kernel, bound by DRAM traffic, forms each harmonic face
+// (Eqs. 15-18 with zero jump) as 1 / (gh_a + gh_b) = 2 eps_a eps_b / ((eps_a + eps_b) h^2) instead of reading
+// three face arrays; the FP32 phase B kernel, bound by instruction issue, reads the stored FP32 faces.
+template <typename T> constexpr bool ca_face_from_gh() { return sizeof(T) == 4; }
+template <typename T, bool UNI> struct SlotsB { static constexpr int NH = UNI ? 3 : 5, NC = UNI ? 1 : 2; };
+template <typename T, bool UNI> struct SlotsCA {
+  static constexpr int NH = UNI ? 5 : (ca_face_from_gh<T>() ? 6 : 7), NC = UNI ? 2 : (ca_face_from_gh<T>() ? 2 : 3);
+};
 template <bool UNI> struct SlotsRes { static constexpr int NH = UNI ? 2 : 4, NC = UNI ? 1 : 3; };
 
 struct Launch {
@@ -121,8 +130,9 @@ int max_partial_blocks();
 bool encode_map(CUtensorMap* m, const void* base, const Geom& g, int elem_bytes, bool halo);
 
 // ---- setup (a1) ----
+// FP64 faces and their sum per node, and gh = h^2 / (2 eps) in FP32 for the FP32 phase C+A kernel
 cudaError_t launch_faces(const double* eps, const Geom& g, double h, double* wE, double* wN, double* wU,
-                         double* dsum, cudaStream_t s);
+                         double* dsum, float* gh32, cudaStream_t s);
 cudaError_t launch_spread(const double* charges, int nq, double ox, double oy, double oz, double h, double lam,
                           const Geom& g, double* f, int* err, cudaStream_t s);
 cudaError_t launch_eps_diag(const double* dsum, const double* sig, const uint8_t* smask, const Geom& g, double* diag,
@@ -166,10 +176,10 @@ cudaError_t launch_residual(const Maps<SlotsRes<UNI>::NH, SlotsRes<UNI>::NC>& m,
                             double diagc, int init, double* r, double* rt, double* p, double* v, double* t, float* r32,
                             double* part, BicgState* st, const Launch& L, const ResidualExtras& ex = ResidualExtras());
 template <typename T, bool UNI>
-cudaError_t launch_phase_b(const Maps<SlotsB<UNI>::NH, SlotsB<UNI>::NC>& m, const Geom& g, T wc, T* t, double* part,
+cudaError_t launch_phase_b(const Maps<SlotsB<T, UNI>::NH, SlotsB<T, UNI>::NC>& m, const Geom& g, T wc, T* t, double* part,
                            BicgState* st, const Launch& L);
 template <typename T, bool UNI>
-cudaError_t launch_phase_ca(const Maps<SlotsCA<UNI>::NH, SlotsCA<UNI>::NC>& m, const Geom& g, T wc, T* x, T* r_out,
+cudaError_t launch_phase_ca(const Maps<SlotsCA<T, UNI>::NH, SlotsCA<T, UNI>::NC>& m, const Geom& g, T wc, T* x, T* r_out,
                             T* p_out, T* v_out, double* part, BicgState* st, int prime, const Launch& L);
 cudaError_t launch_add_f32(double* x, const float* d, long n, cudaStream_t s);
 

@@ -79,7 +79,7 @@ __device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b 
 // every node; at i = nx-1 (j = ny-1) the east (north) face is the mirror face to the ghost node.
 // dsum = sum of the six faces (the diagonal of -div(eps grad)), 1 on the Dirichlet planes.
 __global__ void k_faces(const double* __restrict__ eps, Geom g, double ih2, double* wE, double* wN, double* wU,
-                        double* dsum) {
+                        double* dsum, float* gh32) {
   const long sy = g.px, sz = g.plane;
   PF_ROWS(g) {
     const long c = i + g.px * row;
@@ -101,6 +101,7 @@ __global__ void k_faces(const double* __restrict__ eps, Geom g, double ih2, doub
     d = __dadd_rn(d, fu);
     d = __dadd_rn(d, fd);
     dsum[c] = (k == 0 || k == g.nz - 1) ? 1.0 : d;
+    gh32[c] = (float)(0.5 / (e * ih2));
   }
 }
 
@@ -641,14 +642,14 @@ static cudaError_t launch_stencil(const Maps<Op::NH, Op::NC>& m, const typename 
 }
 
 template <typename T, bool UNI>
-cudaError_t launch_phase_b(const Maps<SlotsB<UNI>::NH, SlotsB<UNI>::NC>& m, const Geom& g, T wc, T* t, double* part,
+cudaError_t launch_phase_b(const Maps<SlotsB<T, UNI>::NH, SlotsB<T, UNI>::NC>& m, const Geom& g, T wc, T* t, double* part,
                            BicgState* st, const Launch& L) {
   typename OpB<T, UNI>::Args a{part, st, t, wc};
   return launch_stencil<OpB<T, UNI>>(m, a, g, L);
 }
 
 template <typename T, bool UNI>
-cudaError_t launch_phase_ca(const Maps<SlotsCA<UNI>::NH, SlotsCA<UNI>::NC>& m, const Geom& g, T wc, T* x, T* r_out,
+cudaError_t launch_phase_ca(const Maps<SlotsCA<T, UNI>::NH, SlotsCA<T, UNI>::NC>& m, const Geom& g, T wc, T* x, T* r_out,
                             T* p_out, T* v_out, double* part, BicgState* st, int prime, const Launch& L) {
   typename OpCA<T, UNI>::Args a{part, st, x, r_out, p_out, v_out, wc, prime};
   return launch_stencil<OpCA<T, UNI>>(m, a, g, L);
@@ -722,8 +723,8 @@ cudaError_t launch_plane_bb(const double* b, const Geom& g, double* part, BicgSt
 }
 
 cudaError_t launch_faces(const double* eps, const Geom& g, double h, double* wE, double* wN, double* wU, double* dsum,
-                         cudaStream_t s) {
-  k_faces<<<row_blocks(g), 128, 0, s>>>(eps, g, 1.0 / (h * h), wE, wN, wU, dsum);
+                         float* gh32, cudaStream_t s) {
+  k_faces<<<row_blocks(g), 128, 0, s>>>(eps, g, 1.0 / (h * h), wE, wN, wU, dsum, gh32);
   return cudaGetLastError();
 }
 
@@ -809,10 +810,10 @@ cudaError_t launch_set_dirichlet(double* x, double lo, double hi, const Geom& g,
 
 // explicit instantiations
 #define PF_INST(T, U)                                                                                               \
-  template cudaError_t launch_phase_b<T, U>(const Maps<SlotsB<U>::NH, SlotsB<U>::NC>&, const Geom&, T, T*, double*, \
-                                            BicgState*, const Launch&);                                            \
-  template cudaError_t launch_phase_ca<T, U>(const Maps<SlotsCA<U>::NH, SlotsCA<U>::NC>&, const Geom&, T, T*, T*,   \
-                                             T*, T*, double*, BicgState*, int, const Launch&);
+  template cudaError_t launch_phase_b<T, U>(const Maps<SlotsB<T, U>::NH, SlotsB<T, U>::NC>&, const Geom&, T, T*,   \
+                                            double*, BicgState*, const Launch&);                                   \
+  template cudaError_t launch_phase_ca<T, U>(const Maps<SlotsCA<T, U>::NH, SlotsCA<T, U>::NC>&, const Geom&, T, T*, \
+                                             T*, T*, T*, double*, BicgState*, int, const Launch&);
 PF_INST(double, false)
 PF_INST(double, true)
 PF_INST(float, false)

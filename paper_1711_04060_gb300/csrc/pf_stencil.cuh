@@ -369,9 +369,67 @@ constexpr bool scratch_fits() {
   return Op::D * stage_bytes<Op>() >= NTHREADS * 8 * (int)sizeof(double);
 }
 
+// ------------------------------------------------------------------ face data of a node
+// The harmonic face between two nodes from their gh = h^2 / (2 eps): 1 / (gh_a + gh_b) (an approximate FP32
+// reciprocal; both nodes of a face form it from the same sum, so the FP32 operator stays symmetric).
+__device__ __forceinline__ float gh_face(float ga, float gb) { return __fdividef(1.0f, ga + gb); }
+
+// What centre() reads for a node's faces and output() uses: the stored faces (up from the centre box, east and
+// north from the halo box, west and south as the neighbours' east and north faces, or on the first x / y node the
+// node's own, which the mirror condition makes equal), or with GH the gh of the node (u) and of its four side
+// neighbours (mirror images on the x / y sides), from which output() forms the faces.  PF1's faces are uniform.
+template <typename T, bool UNI, bool GH>
+struct FaceData {
+  T u, e, w, n, s;
+  __device__ __forceinline__ void load(T wc, const T* const* H, const T* const* C, int o, int co, bool west,
+                                       bool south, bool east, bool north, int iwe, int iwn, int iwu, int igh) {
+    if constexpr (UNI) {
+      u = e = w = n = s = wc;
+    } else if constexpr (GH) {
+      const T* gh = H[igh];
+      u = gh[o];
+      e = gh[east ? o + 1 : o - 1];
+      w = gh[west ? o - 1 : o + 1];
+      n = gh[north ? o + HBX : o - HBX];
+      s = gh[south ? o - HBX : o + HBX];
+    } else {
+      u = C[iwu][co];
+      e = H[iwe][o];
+      w = west ? H[iwe][o - 1] : e;
+      n = H[iwn][o];
+      s = south ? H[iwn][o - HBX] : n;
+    }
+  }
+  // east, west, north and south faces
+  __device__ __forceinline__ void sides(T& fe, T& fw, T& fn, T& fs) const {
+    if constexpr (GH) {
+      fe = gh_face(u, e);
+      fw = gh_face(w, u);
+      fn = gh_face(u, n);
+      fs = gh_face(s, u);
+    } else {
+      fe = e;
+      fw = w;
+      fn = n;
+      fs = s;
+    }
+  }
+  // the face to the node above, whose face data is hi
+  __device__ __forceinline__ T up(T wc, const FaceData& hi) const {
+    if constexpr (UNI) {
+      return wc;
+    } else if constexpr (GH) {
+      return gh_face(u, hi.u);
+    } else {
+      return u;
+    }
+  }
+};
+
 // ------------------------------------------------------------------ the pipelined stencil body
 // Op supplies: T, NH, NC, D, CHECK_DONE, Args, Sc, Ctr, Accs and scalars(), q_of(), centre(),
-// up_face(), output(), finish().  The calling block is block bid of the nblk blocks that share the
+// up_face() (the face between two planes from their Ctr), output() (given the faces below and above),
+// finish().  The calling block is block bid of the nblk blocks that share the
 // ntiles tiles of one grid (tiles bid, bid + nblk, ...) and its reductions; maps points to the grid's
 // tensor maps (kernel parameter or global memory).
 // FIXED_ZC: tiles of the compile-time depth ZC (single-grid kernels); else g.zc (batched kernels).
@@ -452,7 +510,9 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
 #pragma unroll
         for (int c = 0; c < NC; ++c) C[c] = reinterpret_cast<const T*>(sb + NH * HB + c * CB);
         if (geo.cbo >= 0) qc = Op::q_of(sc, H, geo.cbo, &cnow);
-        if (geo.valid) Op::centre(a, H, C, geo.cbo, ly * TX + lx, geo.gi > 0, geo.gj > 0, cnow);
+        if (geo.valid)
+          Op::centre(a, H, C, geo.cbo, ly * TX + lx, geo.gi > 0, geo.gj > 0, geo.gi < g.nx - 1, geo.gj < g.ny - 1,
+                     cnow);
         Qnow[cs(lx, ly)] = qc;
         if (geo.hs >= 0) Qnow[geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
       }
@@ -465,10 +525,11 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
         fence_proxy_async();
         issue();
       }
-      if (j >= 2 && geo.valid) Op::output(sc, a, Qprev, lx, ly, cidx, cprev, q_dn, qc, wD, acc);
       if (j >= 1) {
+        const T wUp = Op::up_face(a, cprev, cnow);  // the face between planes j - 1 and j
+        if (j >= 2 && geo.valid) Op::output(sc, a, Qprev, lx, ly, cidx, cprev, q_dn, qc, wD, wUp, acc);
         q_dn = q_prev;
-        wD = Op::up_face(a, cprev);
+        wD = wUp;
         cidx += g.plane;
       }
       q_prev = qc;
@@ -499,10 +560,11 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
 template <typename T_, bool UNI>
 struct OpB {
   using T = T_;
-  static constexpr int NH = SlotsB<UNI>::NH, NC = SlotsB<UNI>::NC, D = sizeof(T_) == 4 ? 4 : 2;
+  static constexpr bool GH = false;
+  static constexpr int NH = SlotsB<T_, UNI>::NH, NC = SlotsB<T_, UNI>::NC, D = sizeof(T_) == 4 ? 4 : 2;
   static constexpr int MINB = sizeof(T_) == 4 ? 4 : 2;
   static constexpr bool CHECK_DONE = true;
-  enum { R = 0, V = 1, DI = 2, WE = 3, WN = 4 };
+  enum { R = 0, V = 1, DI = 2, WE = 3, WN = 4, GHS = 0 };
   enum { RT = 0, WU = 1 };
   struct Args {
     double* part;
@@ -514,7 +576,8 @@ struct OpB {
     T al;
   };
   struct Ctr {
-    T s, di, rt, wU, wEc, wEw, wNc, wNs;
+    T s, di, rt;
+    FaceData<T, UNI, GH> f;
   };
   struct Accs {
     Partials<T, 5> p;  // r~.s, r~.t, t.s, t.t, s.s
@@ -532,21 +595,13 @@ struct OpB {
     return di * s;
   }
   __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, int co, bool west,
-                                bool south, Ctr& c) {
+                                bool south, bool east, bool north, Ctr& c) {
     c.rt = C[RT][co];
-    if (UNI) {
-      c.wU = c.wEc = c.wEw = c.wNc = c.wNs = a.wc;
-    } else {
-      c.wU = C[WU][co];
-      c.wEc = H[WE][o];
-      c.wEw = west ? H[WE][o - 1] : c.wEc;
-      c.wNc = H[WN][o];
-      c.wNs = south ? H[WN][o - HBX] : c.wNc;
-    }
+    c.f.load(a.wc, H, C, o, co, west, south, east, north, WE, WN, WU, GHS);
   }
-  __device__ static T up_face(const Args& a, const Ctr& c) { return UNI ? a.wc : c.wU; }
+  __device__ static T up_face(const Args& a, const Ctr& lo, const Ctr& hi) { return lo.f.up(a.wc, hi.f); }
   __device__ static void output(const Sc&, const Args& a, const T* Q, int lx, int ly, long cidx, const Ctr& c, T q_dn,
-                                T q_up, T wD, Accs& acc) {
+                                T q_up, T wD, T wU, Accs& acc) {
     T tc;
     if (c.di == T(0)) {
       tc = c.s;
@@ -556,11 +611,13 @@ struct OpB {
       if (UNI) {
         nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
       } else {
-        nb = c.wEc * qE;
-        nb = fma(c.wEw, qW, nb);
-        nb = fma(c.wNc, qN, nb);
-        nb = fma(c.wNs, qS, nb);
-        nb = fma(c.wU, q_up, nb);
+        T fe, fw, fn, fs;
+        c.f.sides(fe, fw, fn, fs);
+        nb = fe * qE;
+        nb = fma(fw, qW, nb);
+        nb = fma(fn, qN, nb);
+        nb = fma(fs, qS, nb);
+        nb = fma(wU, q_up, nb);
         nb = fma(wD, q_dn, nb);
       }
       tc = c.s - nb;
@@ -620,10 +677,11 @@ struct OpB {
 template <typename T_, bool UNI>
 struct OpCA {
   using T = T_;
-  static constexpr int NH = SlotsCA<UNI>::NH, NC = SlotsCA<UNI>::NC, D = 2;
+  static constexpr bool GH = !UNI && ca_face_from_gh<T_>();
+  static constexpr int NH = SlotsCA<T_, UNI>::NH, NC = SlotsCA<T_, UNI>::NC, D = 2;
   static constexpr int MINB = sizeof(T_) == 4 ? 4 : 2;
   static constexpr bool CHECK_DONE = true;
-  enum { R = 0, V = 1, TT = 2, P = 3, DI = 4, WE = 5, WN = 6 };
+  enum { R = 0, V = 1, TT = 2, P = 3, DI = 4, WE = 5, WN = 6, GHS = 5 };
   enum { X = 0, RT = 1, WU = 2 };
   struct Args {
     double* part;
@@ -639,7 +697,8 @@ struct OpCA {
     T al, om, be;
   };
   struct Ctr {
-    T s, rn, pn, pold, di, x, rt, wU, wEc, wEw, wNc, wNs;
+    T s, rn, pn, pold, di, x, rt;
+    FaceData<T, UNI, GH> f;
   };
   struct Accs {
     Partials<T, 3> p;  // r~.v', r~.r', r'.r'
@@ -663,22 +722,14 @@ struct OpCA {
     return di * pn;
   }
   __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, int co, bool west,
-                                bool south, Ctr& c) {
+                                bool south, bool east, bool north, Ctr& c) {
     c.x = C[X][co];
     c.rt = C[RT][co];
-    if (UNI) {
-      c.wU = c.wEc = c.wEw = c.wNc = c.wNs = a.wc;
-    } else {
-      c.wU = C[WU][co];
-      c.wEc = H[WE][o];
-      c.wEw = west ? H[WE][o - 1] : c.wEc;
-      c.wNc = H[WN][o];
-      c.wNs = south ? H[WN][o - HBX] : c.wNc;
-    }
+    c.f.load(a.wc, H, C, o, co, west, south, east, north, WE, WN, WU, GHS);
   }
-  __device__ static T up_face(const Args& a, const Ctr& c) { return UNI ? a.wc : c.wU; }
+  __device__ static T up_face(const Args& a, const Ctr& lo, const Ctr& hi) { return lo.f.up(a.wc, hi.f); }
   __device__ static void output(const Sc& sc, const Args& a, const T* Q, int lx, int ly, long cidx, const Ctr& c,
-                                T q_dn, T q_up, T wD, Accs& acc) {
+                                T q_dn, T q_up, T wD, T wU, Accs& acc) {
     T vn;
     if (c.di == T(0)) {
       vn = c.pn;
@@ -688,11 +739,13 @@ struct OpCA {
       if (UNI) {
         nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
       } else {
-        nb = c.wEc * qE;
-        nb = fma(c.wEw, qW, nb);
-        nb = fma(c.wNc, qN, nb);
-        nb = fma(c.wNs, qS, nb);
-        nb = fma(c.wU, q_up, nb);
+        T fe, fw, fn, fs;
+        c.f.sides(fe, fw, fn, fs);
+        nb = fe * qE;
+        nb = fma(fw, qW, nb);
+        nb = fma(fn, qN, nb);
+        nb = fma(fs, qS, nb);
+        nb = fma(wU, q_up, nb);
         nb = fma(wD, q_dn, nb);
       }
       vn = c.pn - nb;
@@ -770,7 +823,7 @@ template <bool UNI>
 struct OpRes {
   using T = double;
   static constexpr int NH = SlotsRes<UNI>::NH, NC = SlotsRes<UNI>::NC, D = 2;
-  static constexpr int MINB = 2;
+  static constexpr int MINB = 3;  // 24 warps per SM hide the FP64 pipe's latency better than 16
   static constexpr bool CHECK_DONE = false;
   enum { X = 0, DI = 1, WE = 2, WN = 3 };
   enum { B = 0, DG = 1, WU = 2 };
@@ -792,7 +845,9 @@ struct OpRes {
     int unused;
   };
   struct Ctr {
-    double xc, di, b, diag, wU, wEc, wEw, wNc, wNs;
+    double b, diag;
+    bool ident;  // an identity row (Jacobi scaling +0); x at the node is the stencil plane's centre value
+    FaceData<double, UNI, false> f;
   };
   struct Accs {
     double rr = 0.0, bb = 0.0, rmax = 0.0;
@@ -801,47 +856,43 @@ struct OpRes {
   __device__ static Sc scalars(const Args&) { return Sc{0}; }
   __device__ static double q_of(const Sc&, const double* const* H, int o, Ctr* c) {
     const double xv = H[X][o];
-    if (c) {
-      c->xc = xv;
-      c->di = H[DI][o];
-    }
+    if (c) c->ident = __double_as_longlong(H[DI][o]) == 0;
     return xv;
   }
   __device__ static void centre(const Args& a, const double* const* H, const double* const* C, int o, int co,
-                                bool west, bool south, Ctr& c) {
+                                bool west, bool south, bool east, bool north, Ctr& c) {
     c.b = C[B][co];
-    if (UNI) {
+    if constexpr (UNI) {
       c.diag = a.diagc;
-      c.wU = c.wEc = c.wEw = c.wNc = c.wNs = a.wc;
     } else {
       c.diag = C[DG][co];
-      c.wU = C[WU][co];
-      c.wEc = H[WE][o];
-      c.wEw = west ? H[WE][o - 1] : c.wEc;
-      c.wNc = H[WN][o];
-      c.wNs = south ? H[WN][o - HBX] : c.wNc;
     }
+    c.f.load(a.wc, H, C, o, co, west, south, east, north, WE, WN, WU, 0);
   }
-  __device__ static double up_face(const Args& a, const Ctr& c) { return UNI ? a.wc : c.wU; }
+  __device__ static double up_face(const Args& a, const Ctr& lo, const Ctr& hi) { return lo.f.up(a.wc, hi.f); }
   __device__ static void output(const Sc&, const Args& a, const double* Q, int lx, int ly, long cidx, const Ctr& c,
-                                double q_dn, double q_up, double wD, Accs& acc) {
+                                double q_dn, double q_up, double wD, double wU, Accs& acc) {
     double rc;
-    if (c.di == 0.0) {
-      rc = c.b - c.xc;
+    const double xc = Q[cs(lx, ly)];
+    if (c.ident) {
+      rc = c.b - xc;
     } else {
       const double qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
-      double nb;
       if (UNI) {
-        nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
+        const double nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
+        rc = c.b - (c.diag * xc - nb);
       } else {
-        nb = c.wEc * qE;
-        nb = fma(c.wEw, qW, nb);
-        nb = fma(c.wNc, qN, nb);
-        nb = fma(c.wNs, qS, nb);
-        nb = fma(c.wU, q_up, nb);
-        nb = fma(wD, q_dn, nb);
+        // b + sum of face * neighbour, then - diag * x: seven FP64 operations
+        double fe, fw, fn, fs;
+        c.f.sides(fe, fw, fn, fs);
+        double acc_b = fma(fe, qE, c.b);
+        acc_b = fma(fw, qW, acc_b);
+        acc_b = fma(fn, qN, acc_b);
+        acc_b = fma(fs, qS, acc_b);
+        acc_b = fma(wU, q_up, acc_b);
+        acc_b = fma(wD, q_dn, acc_b);
+        rc = fma(-c.diag, xc, acc_b);
       }
-      rc = c.b - (c.diag * c.xc - nb);
     }
     if (a.init) {
       a.r[cidx] = rc;
