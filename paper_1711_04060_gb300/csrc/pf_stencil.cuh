@@ -493,10 +493,12 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
     const int planes = tl.ke - tl.kb + 2;
     typename Op::Ctr cprev{}, cnow{};
     T q_dn = T(0), q_prev = T(0), wD = T(0);
-    T* Qnow = qring;                 // plane j
-    T* Qprev = qring + 2 * PLANE;    // plane j-1
-    T* Qold = qring + PLANE;         // plane j-2 (free for plane j+1)
+    // offsets of the three stencil planes in the ring (integers, so that every access stays a shared-memory
+    // access of the ring): plane j, plane j - 1, plane j - 2 (free for plane j + 1)
+    int qnow = 0, qprev = 2 * PLANE, qold = PLANE;
     long cidx = geo.gi + (long)g.px * geo.gj + g.plane * (tl.kb - 1);
+    // Op::UNROLL = 2: the two Ctr values trade roles without copies (where registers allow)
+#pragma unroll(Op::UNROLL)
     for (int j = 0; j < planes; ++j, ++seq) {
       const int stage = seq & (D - 1);
       const bool ok = mbar_wait(&bars[stage], (seq / D) & 1u, wait_limit);
@@ -513,8 +515,8 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
         if (geo.valid)
           Op::centre(a, H, C, geo.cbo, ly * TX + lx, geo.gi > 0, geo.gj > 0, geo.gi < g.nx - 1, geo.gj < g.ny - 1,
                      cnow);
-        Qnow[cs(lx, ly)] = qc;
-        if (geo.hs >= 0) Qnow[geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
+        qring[qnow + cs(lx, ly)] = qc;
+        if (geo.hs >= 0) qring[qnow + geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
       }
       // one barrier per plane; the vote makes a timed-out wait a decision of the whole block
       if (__syncthreads_or(!ok)) {
@@ -527,7 +529,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
       }
       if (j >= 1) {
         const T wUp = Op::up_face(a, cprev, cnow);  // the face between planes j - 1 and j
-        if (j >= 2 && geo.valid) Op::output(sc, a, Qprev, lx, ly, cidx, cprev, q_dn, qc, wD, wUp, acc);
+        if (j >= 2 && geo.valid) Op::output(sc, a, qring + qprev, lx, ly, cidx, cprev, q_dn, qc, wD, wUp, acc);
         q_dn = q_prev;
         wD = wUp;
         cidx += g.plane;
@@ -535,10 +537,10 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
       q_prev = qc;
       cprev = cnow;
       // rotate the three stencil planes
-      T* const freed = Qold;
-      Qold = Qprev;
-      Qprev = Qnow;
-      Qnow = freed;
+      const int freed = qold;
+      qold = qprev;
+      qprev = qnow;
+      qnow = freed;
     }
     acc.flush(wsum);
     if (!failed) __syncthreads();
@@ -563,6 +565,7 @@ struct OpB {
   static constexpr bool GH = false;
   static constexpr int NH = SlotsB<T_, UNI>::NH, NC = SlotsB<T_, UNI>::NC, D = sizeof(T_) == 4 ? 4 : 2;
   static constexpr int MINB = sizeof(T_) == 4 ? 4 : 2;
+  static constexpr int UNROLL = 2;
   static constexpr bool CHECK_DONE = true;
   enum { R = 0, V = 1, DI = 2, WE = 3, WN = 4, GHS = 0 };
   enum { RT = 0, WU = 1 };
@@ -680,6 +683,7 @@ struct OpCA {
   static constexpr bool GH = !UNI && ca_face_from_gh<T_>();
   static constexpr int NH = SlotsCA<T_, UNI>::NH, NC = SlotsCA<T_, UNI>::NC, D = 2;
   static constexpr int MINB = sizeof(T_) == 4 ? 4 : 2;
+  static constexpr int UNROLL = UNI ? 2 : 1;
   static constexpr bool CHECK_DONE = true;
   enum { R = 0, V = 1, TT = 2, P = 3, DI = 4, WE = 5, WN = 6, GHS = 5 };
   enum { X = 0, RT = 1, WU = 2 };
@@ -824,6 +828,7 @@ struct OpRes {
   using T = double;
   static constexpr int NH = SlotsRes<UNI>::NH, NC = SlotsRes<UNI>::NC, D = 2;
   static constexpr int MINB = 3;  // 24 warps per SM hide the FP64 pipe's latency better than 16
+  static constexpr int UNROLL = UNI ? 2 : 1;
   static constexpr bool CHECK_DONE = false;
   enum { X = 0, DI = 1, WE = 2, WN = 3 };
   enum { B = 0, DG = 1, WU = 2 };
