@@ -766,6 +766,7 @@ pf_status pf_create_grid(int nx, int ny, int nz, double h_A, const double origin
   g->nz = nz;
   g->N = (long)nx * ny * nz;
   g->geom = pf::make_geom(nx, ny, nz);
+  g->geom.edges = pf::edges_for(nx, ny, nz);
   g->h = h_A;
   for (int a = 0; a < 3; ++a) g->origin[a] = origin_A[a];
   g->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -775,7 +776,7 @@ pf_status pf_create_grid(int nx, int ny, int nz, double h_A, const double origin
     delete g;
     return s;
   }
-  g->L.ntiles = pf::tiles_for(nx, ny, nz);
+  g->L.ntiles = pf::tiles_for(nx, ny, nz, pf::ZC, g->geom.edges);
   g->L.stream = g->stream;
   g->L.wait_limit = WAIT_LIMIT;
   cudaError_t e = cudaStreamSynchronize(g->stream);

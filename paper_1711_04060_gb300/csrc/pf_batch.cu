@@ -215,7 +215,7 @@ pf_status build(pf_batch* B) {
   int nb = 0;
   for (int i = 0; i < n; ++i) {
     const pf_grid* g = B->grids[i];
-    B->ntl[i] = pf::tiles_for(g->nx, g->ny, g->nz, B->zc);
+    B->ntl[i] = pf::tiles_for(g->nx, g->ny, g->nz, B->zc, 1);
     B->block0[i] = nb;
     B->nblk[i] = blocks_for(B->ntl[i], B->tpb);
     nb += B->nblk[i];
@@ -264,6 +264,7 @@ pf_status items_for(pf_batch* B, const std::string& key, Fill fill, const void**
     PF_TRY(fill((int)j, g, v[j]));
     v[j].g = g->geom;
     v[j].g.zc = B->zc;
+    v[j].g.edges = 1;  // a batch launch holds many tiles per block
     v[j].ntiles = B->ntl[j];
     v[j].nblk = B->nblk[j];
     v[j].block0 = B->block0[j];
@@ -288,6 +289,8 @@ pf_status launch_items(pf_batch* B, const void* items, const int2* map, int grid
 template <class Op>
 void set_smem_attr() {
   cudaFuncSetAttribute(pf::k_stencil_batch<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, pf::smem_bytes<Op>());
+  cudaFuncSetAttribute(pf::k_stencil_batch<Op>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
 }
 
 template <typename T, bool UNI>

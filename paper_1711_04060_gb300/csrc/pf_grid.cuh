@@ -166,7 +166,7 @@ pf_status fill_maps(pf_grid* g, pf::Maps<NH, NC>* m, const T* const (&h)[NH], co
     m->h[i] = *p;
   }
   for (int i = 0; i < NC; ++i) {
-    const CUtensorMap* p = tmap(g, c[i], false);
+    const CUtensorMap* p = tmap(g, c[i], true);
     if (!p) return fail(PF_E_CUDA, "cuTensorMapEncodeTiled failed");
     m->c[i] = *p;
   }

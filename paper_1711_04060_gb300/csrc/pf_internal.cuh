@@ -17,6 +17,16 @@ constexpr int NPART = 16;        // per-block partial values reduced by the last
 constexpr int HBX = TX + 8;      // TMA halo box: x from x0-4 (16-byte aligned start) to x0+TX+3
 constexpr int HBY = TY + 2;      // halo box rows y0-1 .. y0+TY
 
+// Tiles in x and y.  With edges on, a grid whose extent in x (y) is one more than a multiple of TX (TY) -- every
+// 2^k + 1 grid -- gets no tile for its last column (row): the tile next to it computes those nodes in its halo
+// slots (edge nodes), so no block spends a whole tile on a single column or row.  That pays when a launch has
+// several tiles per block; a grid with fewer tiles than the GPU holds at once keeps the narrow tiles, which run
+// beside the others.
+__host__ __device__ inline bool edge_x(int nx, int edges) { return edges && nx > TX && nx % TX == 1; }
+__host__ __device__ inline bool edge_y(int ny, int edges) { return edges && ny > TY && ny % TY == 1; }
+__host__ __device__ inline int tiles_x(int nx, int edges) { return edge_x(nx, edges) ? nx / TX : (nx + TX - 1) / TX; }
+__host__ __device__ inline int tiles_y(int ny, int edges) { return edge_y(ny, edges) ? ny / TY : (ny + TY - 1) / TY; }
+
 // Device arrays use a padded layout: node (i,j,k) at i + px*j + px*ny*k with px a multiple of 8,
 // so every row starts on a 32-byte boundary and rows are valid TMA strides.
 struct Geom {
@@ -25,6 +35,7 @@ struct Geom {
   long np;     // plane * nz (allocated elements)
   long n;      // nx * ny * nz (nodes)
   int zc;      // interior z-planes per tile of the stencil kernels
+  int edges;   // 1: the last column / row of a 2^k + 1 grid are edge nodes of the tiles next to them
 };
 
 inline Geom make_geom(int nx, int ny, int nz) {
@@ -37,6 +48,7 @@ inline Geom make_geom(int nx, int ny, int nz) {
   g.np = g.plane * nz;
   g.n = (long)nx * ny * nz;
   g.zc = ZC;
+  g.edges = 0;
   return g;
 }
 
@@ -58,8 +70,8 @@ struct BicgState {
   int pad;
 };
 
-// Tensor maps of one stencil kernel: NH arrays loaded as halo boxes (HBX x HBY at (x0-4, y0-1, k)),
-// NC arrays loaded as centre boxes (TX x TY at (x0, y0, k)).
+// Tensor maps of one stencil kernel: NH arrays read at neighbours and NC arrays read at the node only; both are
+// loaded as halo boxes (HBX x HBY at (x0-4, y0-1, k)), so that a tile's edge nodes find every array in its box.
 template <int NH, int NC>
 struct Maps {
   CUtensorMap h[NH];
@@ -123,7 +135,9 @@ SpeciesDF species_df(const SpeciesParams& sp);
 const char* species_params(int ns, const pf_species* species, double T_K, SpeciesParams* out, double* tv,
                            double* molar);
 
-int tiles_for(int nx, int ny, int nz, int zc = ZC);
+int tiles_for(int nx, int ny, int nz, int zc = ZC, int edges = 0);
+// edges for a single grid: on when its stencil launches hold several tiles per block
+int edges_for(int nx, int ny, int nz);
 int max_partial_blocks();
 
 // host: encode a 3D tensor map over a padded device array (halo box when halo, else centre box)

@@ -10,8 +10,8 @@
 
 namespace pf {
 
-int tiles_for(int nx, int ny, int nz, int zc) {
-  const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, nzc = (nz - 2 + zc - 1) / zc;
+int tiles_for(int nx, int ny, int nz, int zc, int edges) {
+  const int ntx = tiles_x(nx, edges), nty = tiles_y(ny, edges), nzc = (nz - 2 + zc - 1) / zc;
   return ntx * nty * nzc;
 }
 
@@ -586,6 +586,10 @@ static int ew_blocks(long n) {
   return (int)b;
 }
 
+// At least three waves of the FP32 phase kernels (four blocks per SM) with the narrow tiles: below that the
+// narrow tiles run beside the full ones and taking them into the edge tiles only lengthens those.
+int edges_for(int nx, int ny, int nz) { return tiles_for(nx, ny, nz, ZC, 0) >= 3 * 4 * nsm() ? 1 : 0; }
+
 static int row_blocks(const Geom& g) {
   long b = (long)g.ny * g.nz;
   const long cap = (long)nsm() * 16;
@@ -624,6 +628,7 @@ static int stencil_blocks(int ntiles) {
   if (!per_sm) {
     const int bytes = smem_bytes<Op>();
     cudaFuncSetAttribute(k_stencil<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_stencil<Op>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     int o = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_stencil<Op>, NTHREADS, bytes);
     per_sm = o > 0 ? o : 1;

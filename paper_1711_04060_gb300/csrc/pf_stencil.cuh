@@ -1,12 +1,14 @@
 // pf_stencil.cuh -- the TMA-pipelined 7-point stencil body and the BiCGSTAB / residual operators that
-// run on it, shared by the single-grid kernels (pf_kernels.cu) and the batched kernels (pf_batch_kernels.cu).
+// run on it, shared by the single-grid kernels (pf_kernels.cu) and the batched kernels (pf_batch.cu).
 //
 // A stencil body walks 2D tiles of TX x TY nodes (one warp per x row) up through a chunk of ZC interior
 // z-planes.  Every input plane of a tile arrives by TMA (cp.async.bulk.tensor.3d) into a ring of D
 // shared-memory stages, each guarded by an mbarrier that the copies complete; one thread keeps D planes
 // in flight ahead of the consumers, and the stream of planes continues across the tiles a block owns, so
-// the copy engine hides DRAM latency without registers.  Arrays read at neighbours arrive as halo boxes
-// (x0-4 .. x0+TX+3, y0-1 .. y0+TY: the x start stays 16-byte aligned), the others as centre boxes.  Each
+// the copy engine hides DRAM latency without registers.  Every array arrives as a halo box (x0-4 .. x0+TX+3,
+// y0-1 .. y0+TY: the x start stays 16-byte aligned).  On a grid whose x (y) extent is one more than a multiple
+// of TX (TY) the last column (row) has no tile of its own: the threads whose halo slots hold those nodes in the
+// tile next to them also compute them (edge nodes), keeping their per-plane state in shared memory.  Each
 // plane's stencil input (the BiCGSTAB direction p or s after the axpy and the Jacobi scaling) is computed
 // once per node into a ring of three shared planes; the planes below and above come from registers.  The
 // axpy updates of p, s, x and r (Table 3), the Jacobi scaling and the inner products that give rho, alpha
@@ -267,16 +269,19 @@ __device__ __forceinline__ void total_partials(const double* part, unsigned maxm
 
 struct Tile {
   int x0, y0, kb, ke;
+  bool ee, en;  // the tile also computes the grid's last column (ee) / last row (en), which have no tile
 };
 
-__device__ __forceinline__ Tile tile_of(int t, int nx, int nz, int zcs) {
-  const int nzc = (nz - 2 + zcs - 1) / zcs, ntx = (nx + TX - 1) / TX;
+__device__ __forceinline__ Tile tile_of(int t, int nx, int ny, int nz, int zcs, int edges) {
+  const int nzc = (nz - 2 + zcs - 1) / zcs, ntx = tiles_x(nx, edges);
   const int zc = t % nzc, xy = t / nzc;
   Tile r;
   r.x0 = (xy % ntx) * TX;
   r.y0 = (xy / ntx) * TY;
   r.kb = 1 + zc * zcs;
   r.ke = min(r.kb + zcs, nz - 1);
+  r.ee = edge_x(nx, edges) && r.x0 + TX == nx - 1;
+  r.en = edge_y(ny, edges) && r.y0 + TY == ny - 1;
   return r;
 }
 
@@ -292,6 +297,13 @@ __device__ __forceinline__ int mirror(int g, int n) {
 constexpr int PW = TX + 2;             // shared stencil-plane row pitch
 constexpr int PLANE = (TY + 2) * PW;   // shared stencil-plane size
 constexpr int NHALO = 2 * (TX + 2) + 2 * TY;
+constexpr int NEDGE = TY + TX + 1;     // edge nodes of a tile at most: last column, last row, corner
+
+// Offsets of a node's four side neighbours in a stencil plane, relative to the node's own slot.
+struct Nb {
+  int e, w, n, s;
+};
+__host__ __device__ constexpr Nb nb_tile() { return Nb{1, -1, PW, -PW}; }
 
 __device__ __forceinline__ int cs(int lx, int ly) { return (ly + 1) * PW + (lx + 1); }
 
@@ -346,21 +358,22 @@ template <typename T>
 __host__ __device__ constexpr int halo_slot_bytes() {
   return (HBX * HBY * (int)sizeof(T) + 127) / 128 * 128;
 }
-template <typename T>
-__host__ __device__ constexpr int centre_slot_bytes() {
-  return TX * TY * (int)sizeof(T);
-}
-
 template <class Op>
 __host__ __device__ constexpr int stage_bytes() {
-  return Op::NH * halo_slot_bytes<typename Op::T>() + Op::NC * centre_slot_bytes<typename Op::T>();
+  return (Op::NH + Op::NC) * halo_slot_bytes<typename Op::T>();
+}
+
+// bytes of the edge-node records: global index at the tile's first plane, the Ctr of two planes, the face below
+template <class Op>
+__host__ __device__ constexpr int edge_bytes() {
+  return NEDGE * 8 + 2 * NEDGE * (int)sizeof(typename Op::Ctr) + (NEDGE * (int)sizeof(typename Op::T) + 7) / 8 * 8;
 }
 
 template <class Op>
 __host__ __device__ constexpr int smem_bytes() {
-  // stages | three stencil planes | D mbarriers | FP64 warp totals | 128 bytes of alignment slack
+  // stages | three stencil planes | D mbarriers | FP64 warp totals | edge records | 128 bytes of alignment slack
   return Op::D * stage_bytes<Op>() + 3 * PLANE * (int)sizeof(typename Op::T) + Op::D * 8 +
-         NTHREADS / 32 * WSUM_MAX * 8 + 128;
+         NTHREADS / 32 * WSUM_MAX * 8 + edge_bytes<Op>() + 128;
 }
 
 // The reduction scratch at the end of a kernel reuses the stage ring (all copies consumed by then).
@@ -381,8 +394,8 @@ __device__ __forceinline__ float gh_face(float ga, float gb) { return __fdividef
 template <typename T, bool UNI, bool GH>
 struct FaceData {
   T u, e, w, n, s;
-  __device__ __forceinline__ void load(T wc, const T* const* H, const T* const* C, int o, int co, bool west,
-                                       bool south, bool east, bool north, int iwe, int iwn, int iwu, int igh) {
+  __device__ __forceinline__ void load(T wc, const T* const* H, const T* const* C, int o, bool west, bool south,
+                                       bool east, bool north, int iwe, int iwn, int iwu, int igh) {
     if constexpr (UNI) {
       u = e = w = n = s = wc;
     } else if constexpr (GH) {
@@ -393,7 +406,7 @@ struct FaceData {
       n = gh[north ? o + HBX : o - HBX];
       s = gh[south ? o - HBX : o + HBX];
     } else {
-      u = C[iwu][co];
+      u = C[iwu][o];
       e = H[iwe][o];
       w = west ? H[iwe][o - 1] : e;
       n = H[iwn][o];
@@ -440,7 +453,7 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
   const int zcs = FIXED_ZC ? ZC : g.zc;
   using T = typename Op::T;
   constexpr int D = Op::D, NH = Op::NH, NC = Op::NC;
-  constexpr int HB = halo_slot_bytes<T>(), CB = centre_slot_bytes<T>(), STAGE = stage_bytes<Op>();
+  constexpr int HB = halo_slot_bytes<T>(), STAGE = stage_bytes<Op>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // 128-byte aligned start, formed by an offset on the shared array so that the compiler keeps every stage and
   // plane access in the shared address space
@@ -448,6 +461,11 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
   T* qring = reinterpret_cast<T*>(smem + D * STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + D * STAGE + 3 * PLANE * sizeof(T));
   double* wsum = reinterpret_cast<double*>(bars + D);
+  // edge records, each owned by the thread whose halo slot holds the edge node: its global index at the tile's
+  // first plane, its Ctr of planes j and j - 1 (between centre() and output()), the face below it
+  long* eidx = reinterpret_cast<long*>(wsum + NTHREADS / 32 * WSUM_MAX);
+  typename Op::Ctr* ering = reinterpret_cast<typename Op::Ctr*>(eidx + NEDGE);
+  T* ewd = reinterpret_cast<T*>(ering + 2 * NEDGE);
 
   if (Op::CHECK_DONE && *(volatile int*)&a.st->done) return;
   const typename Op::Sc sc = Op::scalars(a);
@@ -462,22 +480,22 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
   static_assert((D & (D - 1)) == 0, "the stage ring has a power-of-two size");
   int pt = bid, pj = 0;
   unsigned pseq = 0;
-  Tile ptl = tile_of(pt, g.nx, g.nz, zcs);
+  Tile ptl = tile_of(pt, g.nx, g.ny, g.nz, zcs, g.edges);
   auto issue = [&]() {
     const int stage = pseq & (D - 1);
     unsigned char* sb = smem + stage * STAGE;
     uint64_t* bar = &bars[stage];
-    mbar_expect_tx(bar, NH * HBX * HBY * sizeof(T) + NC * TX * TY * sizeof(T));
+    mbar_expect_tx(bar, (NH + NC) * HBX * HBY * sizeof(T));
     const int k = ptl.kb - 1 + pj;
 #pragma unroll
     for (int h = 0; h < NH; ++h) tma_load_3d(sb + h * HB, &maps->h[h], ptl.x0 - 4, ptl.y0 - 1, k, bar);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) tma_load_3d(sb + NH * HB + c * CB, &maps->c[c], ptl.x0, ptl.y0, k, bar);
+    for (int c = 0; c < NC; ++c) tma_load_3d(sb + (NH + c) * HB, &maps->c[c], ptl.x0 - 4, ptl.y0 - 1, k, bar);
     ++pseq;
     if (++pj == ptl.ke - ptl.kb + 2) {
       pj = 0;
       pt += nblk;
-      if (pt < ntiles) ptl = tile_of(pt, g.nx, g.nz, zcs);
+      if (pt < ntiles) ptl = tile_of(pt, g.nx, g.ny, g.nz, zcs, g.edges);
     }
   };
   if (threadIdx.x == 0)
@@ -488,9 +506,25 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
   unsigned seq = 0;
   bool failed = false;
   for (int t = bid; t < ntiles && !failed; t += nblk) {
-    const Tile tl = tile_of(t, g.nx, g.nz, zcs);
+    const Tile tl = tile_of(t, g.nx, g.ny, g.nz, zcs, g.edges);
     const TileGeo geo = tile_geo(tl, g.nx, g.ny);
     const int planes = tl.ke - tl.kb + 2;
+    // edge role: the node in this thread's halo slot is one of the tile's edge nodes -- the last column (slot
+    // es = row), the last row (es = TY + column) or their corner (es = TY + TX).  edge = es | side flags << 6
+    // (1 west, 2 south, 4 east, 8 north: the neighbour on that side is a node, not a mirror image), else -1.
+    int edge = -1;
+    if (geo.hs >= 0 && (tl.ee || tl.en)) {
+      int hx, hy;
+      halo_pos((int)threadIdx.x - (NTHREADS - NHALO), hx, hy);
+      int es = -1;
+      if (tl.ee && hx == TX && hy >= 0 && hy < TY && tl.y0 + hy < g.ny) es = hy;
+      if (tl.en && hy == TY && hx >= 0 && (hx < TX || tl.ee) && tl.x0 + hx < g.nx) es = TY + hx;
+      if (es >= 0) {
+        const int gi = tl.x0 + hx, gj = tl.y0 + hy;
+        edge = es | ((gi > 0 ? 1 : 0) | (gj > 0 ? 2 : 0) | (gi < g.nx - 1 ? 4 : 0) | (gj < g.ny - 1 ? 8 : 0)) << 6;
+        eidx[es] = gi + (long)g.px * gj + g.plane * (tl.kb - 1);
+      }
+    }
     typename Op::Ctr cprev{}, cnow{};
     T q_dn = T(0), q_prev = T(0), wD = T(0);
     // offsets of the three stencil planes in the ring (integers, so that every access stays a shared-memory
@@ -510,13 +544,17 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
 #pragma unroll
         for (int h = 0; h < NH; ++h) H[h] = reinterpret_cast<const T*>(sb + h * HB);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) C[c] = reinterpret_cast<const T*>(sb + NH * HB + c * CB);
+        for (int c = 0; c < NC; ++c) C[c] = reinterpret_cast<const T*>(sb + (NH + c) * HB);
+        if (edge >= 0) {  // the edge node's stencil value and its Ctr of plane j, written straight to shared memory
+          typename Op::Ctr& ce = ering[(j & 1) * NEDGE + (edge & 63)];
+          qring[qnow + geo.hs] = Op::q_of(sc, H, geo.hbo, &ce);
+          Op::centre(a, H, C, geo.hbo, (edge >> 6) & 1, (edge >> 7) & 1, (edge >> 8) & 1, (edge >> 9) & 1, ce);
+        }
         if (geo.cbo >= 0) qc = Op::q_of(sc, H, geo.cbo, &cnow);
         if (geo.valid)
-          Op::centre(a, H, C, geo.cbo, ly * TX + lx, geo.gi > 0, geo.gj > 0, geo.gi < g.nx - 1, geo.gj < g.ny - 1,
-                     cnow);
+          Op::centre(a, H, C, geo.cbo, geo.gi > 0, geo.gj > 0, geo.gi < g.nx - 1, geo.gj < g.ny - 1, cnow);
         qring[qnow + cs(lx, ly)] = qc;
-        if (geo.hs >= 0) qring[qnow + geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
+        if (geo.hs >= 0 && edge < 0) qring[qnow + geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
       }
       // one barrier per plane; the vote makes a timed-out wait a decision of the whole block
       if (__syncthreads_or(!ok)) {
@@ -529,10 +567,23 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
       }
       if (j >= 1) {
         const T wUp = Op::up_face(a, cprev, cnow);  // the face between planes j - 1 and j
-        if (j >= 2 && geo.valid) Op::output(sc, a, qring + qprev, lx, ly, cidx, cprev, q_dn, qc, wD, wUp, acc);
+        if (j >= 2 && geo.valid)
+          Op::output(sc, a, qring + qprev, cs(lx, ly), nb_tile(), cidx, cprev, q_dn, qc, wD, wUp, acc);
         q_dn = q_prev;
         wD = wUp;
         cidx += g.plane;
+        if (edge >= 0) {  // the edge node of plane j - 1: its stencil values below and above are in the ring
+          const int es = edge & 63;
+          const typename Op::Ctr& ep = ering[((j - 1) & 1) * NEDGE + es];
+          const T wUe = Op::up_face(a, ep, ering[(j & 1) * NEDGE + es]);
+          if (j >= 2) {
+            // a side neighbour beyond the last column / row is the mirror image of the one before it
+            const Nb nbe{(edge >> 8) & 1 ? 1 : -1, -1, (edge >> 9) & 1 ? PW : -PW, -PW};
+            Op::output(sc, a, qring + qprev, geo.hs, nbe, eidx[es] + g.plane * (j - 1), ep, qring[qold + geo.hs],
+                       qring[qnow + geo.hs], ewd[es], wUe, acc);
+          }
+          ewd[es] = wUe;
+        }
       }
       q_prev = qc;
       cprev = cnow;
@@ -597,19 +648,19 @@ struct OpB {
     }
     return di * s;
   }
-  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, int co, bool west,
-                                bool south, bool east, bool north, Ctr& c) {
-    c.rt = C[RT][co];
-    c.f.load(a.wc, H, C, o, co, west, south, east, north, WE, WN, WU, GHS);
+  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, bool west, bool south,
+                                bool east, bool north, Ctr& c) {
+    c.rt = C[RT][o];
+    c.f.load(a.wc, H, C, o, west, south, east, north, WE, WN, WU, GHS);
   }
   __device__ static T up_face(const Args& a, const Ctr& lo, const Ctr& hi) { return lo.f.up(a.wc, hi.f); }
-  __device__ static void output(const Sc&, const Args& a, const T* Q, int lx, int ly, long cidx, const Ctr& c, T q_dn,
+  __device__ static void output(const Sc&, const Args& a, const T* Q, int pc, Nb nb, long cidx, const Ctr& c, T q_dn,
                                 T q_up, T wD, T wU, Accs& acc) {
     T tc;
     if (c.di == T(0)) {
       tc = c.s;
     } else {
-      const T qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
+      const T qE = Q[pc + nb.e], qW = Q[pc + nb.w], qN = Q[pc + nb.n], qS = Q[pc + nb.s];
       T nb;
       if (UNI) {
         nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
@@ -725,20 +776,20 @@ struct OpCA {
     }
     return di * pn;
   }
-  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, int co, bool west,
-                                bool south, bool east, bool north, Ctr& c) {
-    c.x = C[X][co];
-    c.rt = C[RT][co];
-    c.f.load(a.wc, H, C, o, co, west, south, east, north, WE, WN, WU, GHS);
+  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, bool west, bool south,
+                                bool east, bool north, Ctr& c) {
+    c.x = C[X][o];
+    c.rt = C[RT][o];
+    c.f.load(a.wc, H, C, o, west, south, east, north, WE, WN, WU, GHS);
   }
   __device__ static T up_face(const Args& a, const Ctr& lo, const Ctr& hi) { return lo.f.up(a.wc, hi.f); }
-  __device__ static void output(const Sc& sc, const Args& a, const T* Q, int lx, int ly, long cidx, const Ctr& c,
+  __device__ static void output(const Sc& sc, const Args& a, const T* Q, int pc, Nb nb, long cidx, const Ctr& c,
                                 T q_dn, T q_up, T wD, T wU, Accs& acc) {
     T vn;
     if (c.di == T(0)) {
       vn = c.pn;
     } else {
-      const T qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
+      const T qE = Q[pc + nb.e], qW = Q[pc + nb.w], qN = Q[pc + nb.n], qS = Q[pc + nb.s];
       T nb;
       if (UNI) {
         nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
@@ -864,25 +915,25 @@ struct OpRes {
     if (c) c->ident = __double_as_longlong(H[DI][o]) == 0;
     return xv;
   }
-  __device__ static void centre(const Args& a, const double* const* H, const double* const* C, int o, int co,
-                                bool west, bool south, bool east, bool north, Ctr& c) {
-    c.b = C[B][co];
+  __device__ static void centre(const Args& a, const double* const* H, const double* const* C, int o, bool west,
+                                bool south, bool east, bool north, Ctr& c) {
+    c.b = C[B][o];
     if constexpr (UNI) {
       c.diag = a.diagc;
     } else {
-      c.diag = C[DG][co];
+      c.diag = C[DG][o];
     }
-    c.f.load(a.wc, H, C, o, co, west, south, east, north, WE, WN, WU, 0);
+    c.f.load(a.wc, H, C, o, west, south, east, north, WE, WN, WU, 0);
   }
   __device__ static double up_face(const Args& a, const Ctr& lo, const Ctr& hi) { return lo.f.up(a.wc, hi.f); }
-  __device__ static void output(const Sc&, const Args& a, const double* Q, int lx, int ly, long cidx, const Ctr& c,
+  __device__ static void output(const Sc&, const Args& a, const double* Q, int pc, Nb nb, long cidx, const Ctr& c,
                                 double q_dn, double q_up, double wD, double wU, Accs& acc) {
     double rc;
-    const double xc = Q[cs(lx, ly)];
+    const double xc = Q[pc];
     if (c.ident) {
       rc = c.b - xc;
     } else {
-      const double qE = Q[cs(lx + 1, ly)], qW = Q[cs(lx - 1, ly)], qN = Q[cs(lx, ly + 1)], qS = Q[cs(lx, ly - 1)];
+      const double qE = Q[pc + nb.e], qW = Q[pc + nb.w], qN = Q[pc + nb.n], qS = Q[pc + nb.s];
       if (UNI) {
         const double nb = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
         rc = c.b - (c.diag * xc - nb);
