@@ -319,11 +319,11 @@ pf_status fill_b(pf_grid* g, int op, int cur, pf::BatchItem<pf::OpB<T, UNI>>& it
   if constexpr (UNI) {
     const T* h[SB::NH] = {K.r[cur], K.v[cur], A.dinv};
     const T* c[SB::NC] = {K.rt};
-    PF_TRY((fill_maps<SB::NH, SB::NC, T>(g, &it.maps, h, c)));
+    PF_TRY((fill_maps<SB::NH, SB::NC, T>(g, &it.maps, h, c, 1)));
   } else {
     const T* h[SB::NH] = {K.r[cur], K.v[cur], A.dinv, A.wE, A.wN};
     const T* c[SB::NC] = {K.rt, A.wU};
-    PF_TRY((fill_maps<SB::NH, SB::NC, T>(g, &it.maps, h, c)));
+    PF_TRY((fill_maps<SB::NH, SB::NC, T>(g, &it.maps, h, c, 1)));
   }
   it.a = typename pf::OpB<T, UNI>::Args{g->part, sizeof(T) == 8 ? g->st : g->st2, K.t, (T)A.wc};
   return PF_OK;
@@ -337,15 +337,15 @@ pf_status fill_ca(pf_grid* g, int op, int cur, int prime, T* x, pf::BatchItem<pf
   if constexpr (UNI) {
     const T* h[SC::NH] = {K.r[cur], K.v[cur], K.t, K.p[cur], A.dinv};
     const T* c[SC::NC] = {x, K.rt};
-    PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &it.maps, h, c)));
+    PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &it.maps, h, c, 1)));
   } else if constexpr (pf::ca_face_from_gh<T>()) {
     const T* h[SC::NH] = {K.r[cur], K.v[cur], K.t, K.p[cur], A.dinv, A.gh};
     const T* c[SC::NC] = {x, K.rt};
-    PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &it.maps, h, c)));
+    PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &it.maps, h, c, 1)));
   } else {
     const T* h[SC::NH] = {K.r[cur], K.v[cur], K.t, K.p[cur], A.dinv, A.wE, A.wN};
     const T* c[SC::NC] = {x, K.rt, A.wU};
-    PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &it.maps, h, c)));
+    PF_TRY((fill_maps<SC::NH, SC::NC, T>(g, &it.maps, h, c, 1)));
   }
   it.a = typename pf::OpCA<T, UNI>::Args{g->part, sizeof(T) == 8 ? g->st : g->st2, x, K.r[1 - cur], K.p[1 - cur],
                                          K.v[1 - cur], (T)A.wc, prime};
@@ -361,11 +361,11 @@ pf_status fill_res(pf_grid* g, int op, int init, const double* x, const double* 
   if constexpr (UNI) {
     const double* h[S::NH] = {x, A.dinv};
     const double* c[S::NC] = {b};
-    PF_TRY((fill_maps<S::NH, S::NC, double>(g, &it.maps, h, c)));
+    PF_TRY((fill_maps<S::NH, S::NC, double>(g, &it.maps, h, c, 1)));
   } else {
     const double* h[S::NH] = {x, A.dinv, A.wE, A.wN};
     const double* c[S::NC] = {b, A.diag, A.wU};
-    PF_TRY((fill_maps<S::NH, S::NC, double>(g, &it.maps, h, c)));
+    PF_TRY((fill_maps<S::NH, S::NC, double>(g, &it.maps, h, c, 1)));
   }
   it.a = typename pf::OpRes<UNI>::Args{g->part, g->st, A.wc, A.diagc, init,
                                        init ? K.r[0] : nullptr, init ? K.rt : nullptr, init ? K.p[0] : nullptr,

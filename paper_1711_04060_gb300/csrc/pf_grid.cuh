@@ -149,24 +149,27 @@ pf_status dalloc(pf_grid* g, T** p, size_t count) {
 
 // ---- TMA descriptors ---------------------------------------------------------------------
 template <typename T>
-const CUtensorMap* tmap(pf_grid* g, const T* base, bool halo) {
-  const auto key = std::make_pair(static_cast<const void*>(base), (int)sizeof(T) * 2 + (halo ? 1 : 0));
+const CUtensorMap* tmap(pf_grid* g, const T* base, int box) {
+  const auto key = std::make_pair(static_cast<const void*>(base), (int)sizeof(T) * 4 + box);
   auto it = g->maps.find(key);
   if (it != g->maps.end()) return &it->second;
   CUtensorMap m;
-  if (!pf::encode_map(&m, base, g->geom, (int)sizeof(T), halo)) return nullptr;
+  if (!pf::encode_map(&m, base, g->geom, (int)sizeof(T), box)) return nullptr;
   return &(g->maps[key] = m);
 }
 
 template <int NH, int NC, typename T>
-pf_status fill_maps(pf_grid* g, pf::Maps<NH, NC>* m, const T* const (&h)[NH], const T* const (&c)[NC]) {
+// centre_halo: the centre arrays as halo boxes, else as row boxes (-1: as the grid's own launches need them)
+pf_status fill_maps(pf_grid* g, pf::Maps<NH, NC>* m, const T* const (&h)[NH], const T* const (&c)[NC],
+                    int centre_halo = -1) {
+  if (centre_halo < 0) centre_halo = g->geom.edges;
   for (int i = 0; i < NH; ++i) {
-    const CUtensorMap* p = tmap(g, h[i], true);
+    const CUtensorMap* p = tmap(g, h[i], pf::BOX_HALO);
     if (!p) return fail(PF_E_CUDA, "cuTensorMapEncodeTiled failed");
     m->h[i] = *p;
   }
   for (int i = 0; i < NC; ++i) {
-    const CUtensorMap* p = tmap(g, c[i], true);
+    const CUtensorMap* p = tmap(g, c[i], centre_halo ? pf::BOX_HALO : pf::BOX_ROWS);
     if (!p) return fail(PF_E_CUDA, "cuTensorMapEncodeTiled failed");
     m->c[i] = *p;
   }

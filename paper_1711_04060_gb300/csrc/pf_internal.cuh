@@ -70,8 +70,9 @@ struct BicgState {
   int pad;
 };
 
-// Tensor maps of one stencil kernel: NH arrays read at neighbours and NC arrays read at the node only; both are
-// loaded as halo boxes (HBX x HBY at (x0-4, y0-1, k)), so that a tile's edge nodes find every array in its box.
+// Tensor maps of one stencil kernel: NH arrays read at neighbours, loaded as halo boxes (HBX x HBY at (x0-4, y0-1,
+// k)), and NC arrays read at the node only, loaded as row boxes (HBX x TY at (x0-4, y0, k): the halo box without
+// its first and last row) -- or as halo boxes when the grid has edge nodes (Geom::edges), which lie in those rows.
 template <int NH, int NC>
 struct Maps {
   CUtensorMap h[NH];
@@ -141,7 +142,9 @@ int edges_for(int nx, int ny, int nz);
 int max_partial_blocks();
 
 // host: encode a 3D tensor map over a padded device array (halo box when halo, else centre box)
-bool encode_map(CUtensorMap* m, const void* base, const Geom& g, int elem_bytes, bool halo);
+// box: BOX_HALO (HBX x HBY) or BOX_ROWS (HBX x TY)
+enum { BOX_HALO = 1, BOX_ROWS = 2 };
+bool encode_map(CUtensorMap* m, const void* base, const Geom& g, int elem_bytes, int box);
 
 // ---- setup (a1) ----
 // FP64 faces and their sum per node, and gh = h^2 / (2 eps) in FP32 for the FP32 phase C+A kernel

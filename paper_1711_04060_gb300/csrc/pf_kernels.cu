@@ -597,7 +597,7 @@ static int row_blocks(const Geom& g) {
   return (int)(b < 1 ? 1 : b);
 }
 
-bool encode_map(CUtensorMap* m, const void* base, const Geom& g, int elem_bytes, bool halo) {
+bool encode_map(CUtensorMap* m, const void* base, const Geom& g, int elem_bytes, int box_kind) {
   typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -612,7 +612,7 @@ bool encode_map(CUtensorMap* m, const void* base, const Geom& g, int elem_bytes,
   }
   const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
   const cuuint64_t strides[2] = {(cuuint64_t)g.px * elem_bytes, (cuuint64_t)g.plane * elem_bytes};
-  const cuuint32_t box[3] = {(cuuint32_t)(halo ? HBX : TX), (cuuint32_t)(halo ? HBY : TY), 1};
+  const cuuint32_t box[3] = {(cuuint32_t)HBX, (cuuint32_t)(box_kind == BOX_HALO ? HBY : TY), 1};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUtensorMapDataType dt = elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   return fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -5,11 +5,12 @@
 // z-planes.  Every input plane of a tile arrives by TMA (cp.async.bulk.tensor.3d) into a ring of D
 // shared-memory stages, each guarded by an mbarrier that the copies complete; one thread keeps D planes
 // in flight ahead of the consumers, and the stream of planes continues across the tiles a block owns, so
-// the copy engine hides DRAM latency without registers.  Every array arrives as a halo box (x0-4 .. x0+TX+3,
-// y0-1 .. y0+TY: the x start stays 16-byte aligned).  On a grid whose x (y) extent is one more than a multiple
-// of TX (TY) the last column (row) has no tile of its own: the threads whose halo slots hold those nodes in the
-// tile next to them also compute them (edge nodes), keeping their per-plane state in shared memory.  Each
-// plane's stencil input (the BiCGSTAB direction p or s after the axpy and the Jacobi scaling) is computed
+// the copy engine hides DRAM latency without registers.  Arrays read at neighbours arrive as halo boxes (x0-4 ..
+// x0+TX+3, y0-1 .. y0+TY: the x start stays 16-byte aligned), the others as the same box without its first and
+// last row.  On a grid whose x (y) extent is one more than a multiple of TX (TY) the last column (row) can go
+// without a tile of its own: the threads whose halo slots hold those nodes in the tile next to them also compute
+// them (edge nodes), keeping their per-plane state in shared memory; such a grid loads every array as a halo box.
+// Each plane's stencil input (the BiCGSTAB direction p or s after the axpy and the Jacobi scaling) is computed
 // once per node into a ring of three shared planes; the planes below and above come from registers.  The
 // axpy updates of p, s, x and r (Table 3), the Jacobi scaling and the inner products that give rho, alpha
 // and omega are fused into the two stencil kernels of an iteration.  Inner products are reduced by warp
@@ -485,12 +486,14 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
     const int stage = pseq & (D - 1);
     unsigned char* sb = smem + stage * STAGE;
     uint64_t* bar = &bars[stage];
-    mbar_expect_tx(bar, (NH + NC) * HBX * HBY * sizeof(T));
+    // the centre arrays come as halo boxes when the grid has edge nodes, else as row boxes (no first / last row)
+    mbar_expect_tx(bar, (NH * HBY + NC * (g.edges ? HBY : TY)) * HBX * sizeof(T));
     const int k = ptl.kb - 1 + pj;
 #pragma unroll
     for (int h = 0; h < NH; ++h) tma_load_3d(sb + h * HB, &maps->h[h], ptl.x0 - 4, ptl.y0 - 1, k, bar);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) tma_load_3d(sb + (NH + c) * HB, &maps->c[c], ptl.x0 - 4, ptl.y0 - 1, k, bar);
+    for (int c = 0; c < NC; ++c)
+      tma_load_3d(sb + (NH + c) * HB, &maps->c[c], ptl.x0 - 4, g.edges ? ptl.y0 - 1 : ptl.y0, k, bar);
     ++pseq;
     if (++pj == ptl.ke - ptl.kb + 2) {
       pj = 0;
@@ -543,8 +546,10 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
         const T* C[NC];
 #pragma unroll
         for (int h = 0; h < NH; ++h) H[h] = reinterpret_cast<const T*>(sb + h * HB);
+        // a row box lacks the halo box's first row: shift its base so that both are indexed by halo-box offsets
+        const int crow = g.edges ? 0 : HBX * (int)sizeof(T);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) C[c] = reinterpret_cast<const T*>(sb + (NH + c) * HB);
+        for (int c = 0; c < NC; ++c) C[c] = reinterpret_cast<const T*>(sb + (NH + c) * HB - crow);
         if (edge >= 0) {  // the edge node's stencil value and its Ctr of plane j, written straight to shared memory
           typename Op::Ctr& ce = ering[(j & 1) * NEDGE + (edge & 63)];
           qring[qnow + geo.hs] = Op::q_of(sc, H, geo.hbo, &ce);
