@@ -142,8 +142,8 @@ pf_status allocate(pf_grid* g) {
   PF_CK(cudaMemsetAsync(base, 0, total, g->stream));
   PF_CK(cudaEventCreate(&g->ev0));
   PF_CK(cudaEventCreate(&g->ev1));
-  g->pool.resize(2 * PROF_SLOTS, nullptr);
-  g->pkind.resize(PROF_SLOTS, 0);
+  g->pool.resize(4 * PROF_SLOTS, nullptr);
+  g->pkind.resize(2 * PROF_SLOTS, 0);
   for (auto& e : g->pool) PF_CK(cudaEventCreate(&e));
   return PF_OK;
 }
@@ -160,10 +160,12 @@ int trace_level() {
 }
 
 // ---- profiling ---------------------------------------------------------------------------
-void prof_resolve(pf_grid* g) {
-  if (g->np == 0) return;
-  if (cudaEventSynchronize(g->pool[2 * (g->np - 1) + 1]) == cudaSuccess) {
-    for (int i = 0; i < g->np; ++i) {
+// read back the first n pairs of half h
+static void prof_resolve_half(pf_grid* g, int h, int n) {
+  if (n <= 0) return;
+  const int b = h * PROF_SLOTS;
+  if (cudaEventSynchronize(g->pool[2 * (b + n - 1) + 1]) == cudaSuccess) {
+    for (int i = b; i < b + n; ++i) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, g->pool[2 * i], g->pool[2 * i + 1]) == cudaSuccess) {
         g->pms[g->pkind[i]] += ms;
@@ -172,21 +174,33 @@ void prof_resolve(pf_grid* g) {
     }
   }
   cudaGetLastError();
+}
+
+void prof_resolve(pf_grid* g) {
+  prof_resolve_half(g, g->half ^ 1, g->nold);
+  prof_resolve_half(g, g->half, g->np);
+  g->nold = 0;
   g->np = 0;
 }
 
 int prof_begin(pf_grid* g, int n_launches) {
   g->launches += n_launches;
   if (!g->prof_on) return -1;
-  if (g->np == PROF_SLOTS) prof_resolve(g);
-  cudaEventRecord(g->pool[2 * g->np], g->stream);
+  if (g->np == PROF_SLOTS) {  // the current half is full: read back the other one and reuse it
+    prof_resolve_half(g, g->half ^ 1, g->nold);
+    g->half ^= 1;
+    g->nold = PROF_SLOTS;
+    g->np = 0;
+  }
+  cudaEventRecord(g->pool[2 * (g->half * PROF_SLOTS + g->np)], g->stream);
   return g->np;
 }
 
 void prof_end(pf_grid* g, int slot, int kind) {
   if (slot < 0) return;
-  cudaEventRecord(g->pool[2 * slot + 1], g->stream);
-  g->pkind[slot] = kind;
+  const int i = g->half * PROF_SLOTS + slot;
+  cudaEventRecord(g->pool[2 * i + 1], g->stream);
+  g->pkind[i] = kind;
   g->np = slot + 1;
 }
 
@@ -223,7 +237,6 @@ pf_status read_state(pf_grid* g, const BicgState* src, BicgState* out) {
   PF_CK(cudaMemcpyAsync(g->host_st, src, sizeof(BicgState), cudaMemcpyDeviceToHost, g->stream));
   PF_CK(cudaStreamSynchronize(g->stream));
   *out = *g->host_st;
-  prof_resolve(g);
   return PF_OK;
 }
 

@@ -100,14 +100,17 @@ struct pf_grid {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // TMA descriptors, keyed by (array, halo box?)
   std::map<std::pair<const void*, int>, CUtensorMap> maps;
-  // profiling: event pairs around launches, resolved at the next host synchronisation
+  // profiling: event pairs around launches in two halves of PROF_SLOTS pairs; a half is read back when the other
+  // fills up (its events long complete by then) or at the end of a solve, never at the solve's own host checks
   int prof_on = 0;
   long long launches = 0;
   long long pcount[PF_PROF_KINDS] = {};
   double pms[PF_PROF_KINDS] = {};
   std::vector<cudaEvent_t> pool;
   std::vector<int> pkind;
-  int np = 0;
+  int np = 0;    // pairs recorded in the current half
+  int half = 0;  // the current half
+  int nold = 0;  // pairs of the other half not yet read back
 };
 
 namespace pfi {
