@@ -40,11 +40,14 @@ UNIT = "solves/s"
 # which it forms the faces) and writes x, r, p, v; the PF1 operator has uniform faces (no face
 # arrays); the FP64 residual of refinement reads x, b, M^-1, the diagonal and three faces and
 # writes the FP32 residual.
-WORDS = {"b": 8, "ca": 14, "ca_gh": 12, "b_pf1": 5, "ca_pf1": 11}
+WORDS = {"b": 8, "ca": 14, "ca_gh": 12, "b_pf1": 5, "ca_pf1": 11, "cg": 14, "cg_gh": 12, "cg_pf1": 11}
 KERNEL_BYTES = {
     "b_fp32": WORDS["b"] * 4, "ca_fp32": WORDS["ca_gh"] * 4, "b_fp64": WORDS["b"] * 8, "ca_fp64": WORDS["ca"] * 8,
     "b_fp32_pf1": WORDS["b_pf1"] * 4, "ca_fp32_pf1": WORDS["ca_pf1"] * 4, "b_fp64_pf1": WORDS["b_pf1"] * 8,
     "ca_fp64_pf1": WORDS["ca_pf1"] * 8, "residual_fp64": 7 * 8 + 4,
+    # one-pass CG: reads r, w, s, M^-1 (and the faces) at neighbours, p and x at the node; writes r, w, s, p, x
+    "cg_fp32": WORDS["cg_gh"] * 4, "cg_fp64": WORDS["cg"] * 8, "cg_fp32_pf1": WORDS["cg_pf1"] * 4,
+    "cg_fp64_pf1": WORDS["cg_pf1"] * 8,
 }
 KERNEL_NAMES = {
     "b_fp32": "k_stencil<OpB<float, false>>", "ca_fp32": "k_stencil<OpCA<float, false>>",
@@ -52,6 +55,8 @@ KERNEL_NAMES = {
     "b_fp32_pf1": "k_stencil<OpB<float, true>>", "ca_fp32_pf1": "k_stencil<OpCA<float, true>>",
     "b_fp64_pf1": "k_stencil<OpB<double, true>>", "ca_fp64_pf1": "k_stencil<OpCA<double, true>>",
     "residual_fp64": "k_stencil<OpRes<false>>",
+    "cg_fp32": "k_stencil<OpCG<float, false>>", "cg_fp64": "k_stencil<OpCG<double, false>>",
+    "cg_fp32_pf1": "k_stencil<OpCG<float, true>>", "cg_fp64_pf1": "k_stencil<OpCG<double, true>>",
 }
 # Work of one FP64 solve of the 257^3 workload (outer iterations, BiCGSTAB iterations), used by the
 # reference arm to turn the oracle's per-iteration cost into solves/s; the oracle runs the same
@@ -67,6 +72,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--method", default="bicgstab", choices=["bicgstab", "cg-symmetric"],
+                    help="Krylov method of the headline: BiCGSTAB (Table 3) or CG for the Poisson and PF1 systems")
+    ap.add_argument("--no-cg-leg", action="store_true", help="skip the solve with CG for the symmetric systems")
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--tol-outer", type=float, default=1e-3, help="||Phi - Phi_0||_inf stop (phi_hat units)")
     ap.add_argument("--lin-tol", type=float, default=1e-6, help="relative 2-norm tolerance of each linear solve")
@@ -191,6 +199,15 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def kernel_table(prof, n_int):
+    """Launches, device time and algorithmic GB/s per kernel kind of one profile."""
+    return {k: {"launches": prof[k][0], "ms": round(prof[k][1], 3),
+                "avg_us": round(prof[k][1] / prof[k][0] * 1e3, 2) if prof[k][0] else None,
+                "GB/s": round(KERNEL_BYTES[k] * n_int / (prof[k][1] / prof[k][0] / 1e3) / 1e9, 1)
+                if k in KERNEL_BYTES and prof[k][0] else None}
+            for k in prof if k != "launches" and prof[k][0] > 0}
 
 
 def iteration_gbps(prof, prec, n_int):
@@ -345,7 +362,7 @@ def config_of(args):
     return {"workload": f"pf_{args.n}_four_pores_NaCaCl", "grid": f"{args.n}^3", "h_A": 64.0 / (args.n - 1),
             "species": "Na+ 0.1 M, Ca2+ 1 mM, Cl- 0.102 M, water 55.5 M", "charges": 48,
             "tol_outer": args.tol_outer, "lin_tol": args.lin_tol,
-            "omega": 0.3, "accel_depth": args.accel_depth, "l2": l2,
+            "omega": 0.3, "accel_depth": args.accel_depth, "method": getattr(args, "method", "bicgstab"), "l2": l2,
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -696,8 +713,9 @@ def run_ours(args):
     out = {k: torch.zeros(m, dtype=torch.float64, device=dev)
            for k, m in (("phi_V", N), ("C_M", ns * N), ("S", N), ("Gamma", N), ("Psi", N))}
     prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
+    method = api.PF_CG_SYMMETRIC if args.method == "cg-symmetric" else api.PF_BICGSTAB
     opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, accel_depth=args.accel_depth,
-                       inner_tol=args.inner_tol)
+                       inner_tol=args.inner_tol, method=method)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -756,11 +774,7 @@ def run_ours(args):
                 "traffic": (traffic * n_int) if traffic is not None else None,
                 "algorithmic_bytes_per_launch": KERNEL_BYTES[dom] * n_int, "avg_launch_ms": avg_s * 1e3,
                 "launches": cnt}
-    kernels = {k: {"launches": prof[k][0], "ms": round(prof[k][1], 3),
-                   "avg_us": round(prof[k][1] / prof[k][0] * 1e3, 2) if prof[k][0] else None,
-                   "GB/s": round(KERNEL_BYTES[k] * n_int / (prof[k][1] / prof[k][0] / 1e3) / 1e9, 1)
-                   if k in KERNEL_BYTES and prof[k][0] else None}
-               for k in prof if k != "launches" and prof[k][0] > 0}
+    kernels = kernel_table(prof, n_int)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -855,6 +869,32 @@ def run_ours(args):
         line["headline_vs_reference"] = {"mixed": rel_errors(phi_mixed, C_mixed, ref_phi, ref_C, ns)}
         if host64 is not None:
             line["headline_vs_reference"]["fp64"] = rel_errors(host64["phi_V"], host64["C_M"], ref_phi, ref_C, ns)
+
+    # the same solve with CG (one pass per iteration) for the systems Section 3 names symmetric: Poisson and PF1
+    if not args.no_cg_leg and args.method == "bicgstab":
+        oc = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, inner_tol=args.inner_tol,
+                         method=api.PF_CG_SYMMETRIC)
+        outc = {k: torch.zeros_like(v) for k, v in out.items()}
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        grid.profile(True)
+        e0.record(stream)
+        crep = solve(oc, outc)
+        e1.record(stream)
+        e1.synchronize()
+        msc = e0.elapsed_time(e1)
+        profc = grid.profile_get()
+        grid.profile(False)
+        phic = outc["phi_V"].cpu().numpy()
+        Cc = outc["C_M"].cpu().numpy().reshape(ns, N)
+        Cm = C_mixed.reshape(ns, N)
+        line["cg_symmetric"] = {
+            "value": 1e3 / msc, "unit": UNIT, "ms_per_step": msc, "outer_iters": crep["outer_iters"],
+            "lin_iters": crep["lin_iters_total"], "status": crep["status"],
+            "phi_rel_vs_headline": float(np.abs(phic - phi_mixed).max() / np.abs(phi_mixed).max()),
+            "conc_rel_vs_headline": float(max(np.abs(Cc[i] - Cm[i]).max() / Cm[i].max() for i in range(ns))),
+            "kernels": kernel_table(profc, n_int)}
 
     # Anderson-accelerated solve of the same workload (same fixed point and stop test)
     if args.accel_depth == 0 and not args.no_accel:

@@ -52,6 +52,12 @@ typedef enum {
 } pf_status;
 
 typedef enum { PF_FP64 = 0, PF_MIXED = 1 } pf_precision;
+/* Krylov method of a linear solve.  Section 3 names the Laplace/Poisson system (Eq. 9) and PF1 (Eq. 12)
+ * symmetric, PF2 (Eq. 13) not in general; with the zero-jump faces this library assembles, PF2 is symmetric in
+ * the side-weighted inner product too.  PF_CG_SYMMETRIC: Jacobi-preconditioned conjugate gradients
+ * (Chronopoulos-Gear form, one pass per iteration) for the Poisson and PF1 systems, BiCGSTAB for PF2;
+ * PF_CG_ALL: conjugate gradients for all three. */
+typedef enum { PF_BICGSTAB = 0, PF_CG_SYMMETRIC = 1, PF_CG_ALL = 2 } pf_method;
 
 /* Linear operators that pf_linear_solve can invert (all 7-point, Section 3):
  *  PF_OP_POISSON: (A x)_c = (1/h^2) sum_nb eps_f (x_c - x_nb), eps_f = 2 eps_a eps_b/(eps_a+eps_b)
@@ -105,6 +111,8 @@ typedef struct {
                          iterative refinement (true residual b - A x in FP64) */
   double inner_tol;   /* PF_MIXED: relative residual reduction of each FP32 inner solve */
   int max_refine;     /* PF_MIXED: limit on FP64 refinement steps */
+  int method;         /* pf_method (PF_BICGSTAB, Table 3, by default); single-grid solves only: a batch or a
+                         served request with another method is refused with PF_E_INVAL */
 } pf_solve_opts;
 
 typedef struct {
@@ -294,7 +302,11 @@ enum {
   PF_PROF_OTHER = 11,      /* setup, right-hand sides, relaxation, output conversion */
   PF_PROF_CG_DIRECTION = 12, /* conjugate gradients: direction u = r + beta u and q = A M^-1 u with <M^-1 u, q> */
   PF_PROF_CG_UPDATE = 13,  /* conjugate gradients: x and r updates with the next inner products */
-  PF_PROF_KINDS = 14
+  PF_PROF_CG_PASS_FP64 = 14,      /* one-pass CG iteration (PF_CG_*) in FP64, variable-dielectric operators */
+  PF_PROF_CG_PASS_FP32 = 15,      /* the same in FP32 (mixed precision inner solves) */
+  PF_PROF_CG_PASS_FP64_PF1 = 16,  /* one-pass CG iteration on the PF1 operator, FP64 */
+  PF_PROF_CG_PASS_FP32_PF1 = 17,  /* and FP32 */
+  PF_PROF_KINDS = 18
 };
 
 typedef struct {

@@ -17,6 +17,7 @@ PF_OK, PF_E_INVAL, PF_E_OOM, PF_E_NOCONV, PF_E_BREAKDOWN, PF_E_GAMMA, PF_E_CUDA,
 STATUS_NAMES = ["PF_OK", "PF_E_INVAL", "PF_E_OOM", "PF_E_NOCONV", "PF_E_BREAKDOWN", "PF_E_GAMMA", "PF_E_CUDA",
                 "PF_E_TIMEOUT", "PF_PENDING"]
 PF_FP64, PF_MIXED = 0, 1
+PF_BICGSTAB, PF_CG_SYMMETRIC, PF_CG_ALL = 0, 1, 2
 PF_OP_POISSON, PF_OP_PF1, PF_OP_PF2 = 0, 1, 2
 PF_MEM_HOST, PF_MEM_DEVICE = 0, 1
 PF_NORM_REL2, PF_NORM_ABSINF = 0, 1
@@ -37,7 +38,7 @@ class pf_coeffs(ctypes.Structure):
 
 class pf_solve_opts(ctypes.Structure):
     _fields_ = [("max_iter", _I), ("tol", _D), ("norm", _I), ("precision", _I), ("inner_tol", _D),
-                ("max_refine", _I)]
+                ("max_refine", _I), ("method", _I)]
 
 
 class pf_report(ctypes.Structure):
@@ -55,9 +56,10 @@ class pf_result(ctypes.Structure):
                 ("time_ms", _D)]
 
 
-PF_PROF_KINDS = 14
+PF_PROF_KINDS = 18
 PROF_NAMES = ["init", "b_fp64", "ca_fp64", "b_fp32", "ca_fp32", "b_fp64_pf1", "ca_fp64_pf1", "b_fp32_pf1",
-              "ca_fp32_pf1", "residual_fp64", "fermi", "other", "cg_direction", "cg_update"]
+              "ca_fp32_pf1", "residual_fp64", "fermi", "other", "cg_direction", "cg_update", "cg_fp64", "cg_fp32",
+              "cg_fp64_pf1", "cg_fp32_pf1"]
 
 
 class pf_profile(ctypes.Structure):

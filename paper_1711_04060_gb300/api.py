@@ -13,8 +13,8 @@ import numpy as np
 
 from . import _binding as B
 from ._binding import (PF_FP64, PF_MIXED, PF_OP_POISSON, PF_OP_PF1, PF_OP_PF2, PF_MEM_HOST, PF_MEM_DEVICE,  # noqa
-                       PF_NORM_REL2, PF_NORM_ABSINF, PF_OK, PF_PENDING, STATUS_NAMES, PF_CHARGES_SPREAD,
-                       PF_CHARGES_DECOMPOSED)
+                       PF_BICGSTAB, PF_CG_SYMMETRIC, PF_CG_ALL, PF_NORM_REL2, PF_NORM_ABSINF, PF_OK, PF_PENDING,
+                       STATUS_NAMES, PF_CHARGES_SPREAD, PF_CHARGES_DECOMPOSED)
 
 
 class PFError(RuntimeError):
@@ -56,11 +56,13 @@ def _torch_stream():
     return ctypes.c_void_p(0)
 
 
-def solve_opts(max_iter=20000, tol=1e-10, norm=PF_NORM_REL2, precision=PF_FP64, inner_tol=0.1, max_refine=64):
+def solve_opts(max_iter=20000, tol=1e-10, norm=PF_NORM_REL2, precision=PF_FP64, inner_tol=0.1, max_refine=64,
+               method=0):
     o = B.pf_solve_opts()
     B.load().pf_default_solve_opts(ctypes.byref(o))
     o.max_iter, o.tol, o.norm, o.precision, o.inner_tol, o.max_refine = max_iter, tol, norm, precision, inner_tol, \
         max_refine
+    o.method = method
     return o
 
 

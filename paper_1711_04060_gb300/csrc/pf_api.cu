@@ -334,6 +334,55 @@ pf_status iterate(pf_grid* g, const OpArrays<T>& A, T* x, const Krylov<T>& K, Bi
   }
 }
 
+// Conjugate gradients (one pass per iteration, OpCG) after the start kernel has written r0 = r[0] and zeroed
+// w = v[0], s = p[0] and p = t and started the state: the prime pass, then chunks of CHUNK passes between reads of
+// the device state.  The Krylov vectors of BiCGSTAB serve: r <- r[], w <- v[], s <- p[], p <- t.
+template <typename T, bool UNI>
+pf_status iterate_cg(pf_grid* g, const OpArrays<T>& A, T* x, const Krylov<T>& K, BicgState* st, BicgState* out) {
+  using S = pf::SlotsCG<T, UNI>;
+  const bool f64 = sizeof(T) == 8;
+  const int kind = UNI ? (f64 ? PF_PROF_CG_PASS_FP64_PF1 : PF_PROF_CG_PASS_FP32_PF1)
+                       : (f64 ? PF_PROF_CG_PASS_FP64 : PF_PROF_CG_PASS_FP32);
+  pf::Maps<S::NH, S::NC> m[2];
+  for (int cur = 0; cur < 2; ++cur) {
+    if constexpr (UNI) {
+      const T* h[S::NH] = {K.r[cur], K.v[cur], K.p[cur], A.dinv};
+      const T* c[S::NC] = {K.t, x};
+      PF_TRY((fill_maps<S::NH, S::NC, T>(g, &m[cur], h, c)));
+    } else if constexpr (pf::ca_face_from_gh<T>()) {
+      const T* h[S::NH] = {K.r[cur], K.v[cur], K.p[cur], A.dinv, A.gh};
+      const T* c[S::NC] = {K.t, x};
+      PF_TRY((fill_maps<S::NH, S::NC, T>(g, &m[cur], h, c)));
+    } else {
+      const T* h[S::NH] = {K.r[cur], K.v[cur], K.p[cur], A.dinv, A.wE, A.wN};
+      const T* c[S::NC] = {K.t, x, A.wU};
+      PF_TRY((fill_maps<S::NH, S::NC, T>(g, &m[cur], h, c)));
+    }
+  }
+  const T wc = (T)A.wc;
+  PF_LAUNCH(g, kind, (pf::launch_cg_pass<T, UNI>(m[0], g->geom, wc, K.r[1], K.v[1], K.p[1], K.t, x, g->part, st, 1,
+                                                 g->L)));
+  int cur = 1;
+  for (;;) {
+    for (int i = 0; i < CHUNK; ++i) {
+      PF_LAUNCH(g, kind, (pf::launch_cg_pass<T, UNI>(m[cur], g->geom, wc, K.r[1 - cur], K.v[1 - cur], K.p[1 - cur],
+                                                     K.t, x, g->part, st, 0, g->L)));
+      cur = 1 - cur;
+    }
+    BicgState s;
+    PF_TRY(read_state(g, st, &s));
+    if (s.done) {
+      *out = s;
+      return PF_OK;
+    }
+  }
+}
+
+// Conjugate gradients in place of BiCGSTAB for this operator?
+bool use_cg(const pf_solve_opts& o, int op) {
+  return o.method == PF_CG_ALL || (o.method == PF_CG_SYMMETRIC && op != PF_OP_PF2);
+}
+
 double measure_of(const BicgState& s, int norm) {
   return norm == PF_NORM_REL2 ? sqrt(s.rnorm2 / s.bnorm2) : s.rinf;
 }
@@ -347,7 +396,10 @@ pf_status solve_fp64(pf_grid* g, int op, const double* b, double* x, const pf_so
   PF_TRY(set_state(g, g->st, o.tol, o.norm, o.max_iter, tol_r0));
   PF_TRY(residual<UNI>(g, A, x, b, 1, &K, g->st));  // r0 = b - A x0 (Table 3)
   BicgState s;
-  PF_TRY((iterate<double, UNI>(g, A, x, K, g->st, &s)));
+  if (use_cg(o, op))
+    PF_TRY((iterate_cg<double, UNI>(g, A, x, K, g->st, &s)));
+  else
+    PF_TRY((iterate<double, UNI>(g, A, x, K, g->st, &s)));
   // true residual of the final iterate (b.b kept from the start)
   BicgState tr;
   PF_TRY(set_state(g, g->st, o.tol, o.norm, 0, tol_r0, 1));
@@ -409,7 +461,10 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
       break;
     }
     BicgState s;
-    PF_TRY((iterate<float, UNI>(g, W, g->d32, K, g->st2, &s)));
+    if (use_cg(o, op))
+      PF_TRY((iterate_cg<float, UNI>(g, W, g->d32, K, g->st2, &s)));
+    else
+      PF_TRY((iterate<float, UNI>(g, W, g->d32, K, g->st2, &s)));
     iters += s.iter;
     ++ref;
     if (s.status == PF_E_BREAKDOWN && s.iter == 0) {
@@ -481,7 +536,7 @@ pf_status solve_dev(pf_grid* g, int op, const double* b, double* x, const pf_sol
 pf_status check_opts(const pf_solve_opts& o) {
   if (o.max_iter < 1 || !(o.tol > 0) || (o.norm != PF_NORM_REL2 && o.norm != PF_NORM_ABSINF) ||
       (o.precision != PF_FP64 && o.precision != PF_MIXED) || !(o.inner_tol > 0 && o.inner_tol < 1) ||
-      o.max_refine < 1)
+      o.max_refine < 1 || o.method < PF_BICGSTAB || o.method > PF_CG_ALL)
     return fail(PF_E_INVAL, "invalid pf_solve_opts");
   return PF_OK;
 }
@@ -751,6 +806,7 @@ void pf_default_solve_opts(pf_solve_opts* o) {
   o->precision = PF_FP64;
   o->inner_tol = 0.1;
   o->max_refine = 64;
+  o->method = PF_BICGSTAB;
 }
 
 void pf_default_nl_opts(pf_nl_opts* o) {

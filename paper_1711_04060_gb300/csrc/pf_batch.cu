@@ -866,6 +866,8 @@ pf_status autotune(pf_batch* B) {
 
 pf_status check_nl(const pf_nl_opts& o) {
   PF_TRY(check_opts(o.lin));
+  if (o.lin.method != PF_BICGSTAB)
+    return fail(PF_E_INVAL, "batches and served requests solve with BiCGSTAB (pf_solve_opts.method = PF_BICGSTAB)");
   if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1 || o.accel_depth < 0 ||
       o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0) || (o.warm_start != 0 && o.warm_start != 1))
     return fail(PF_E_INVAL, "invalid pf_nl_opts");

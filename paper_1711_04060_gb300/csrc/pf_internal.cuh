@@ -95,6 +95,12 @@ template <typename T, bool UNI> struct SlotsCA {
   static constexpr int NH = UNI ? 5 : (ca_face_from_gh<T>() ? 6 : 7), NC = UNI ? 2 : (ca_face_from_gh<T>() ? 2 : 3);
 };
 template <bool UNI> struct SlotsRes { static constexpr int NH = UNI ? 2 : 4, NC = UNI ? 1 : 3; };
+//   CG pass:   halo {r, w, s, dinv, wE, wN}, centre {p, x, wU}  (FP64 variable-face operators)
+//              halo {r, w, s, dinv, gh},     centre {p, x}      (FP32 variable-face operators)
+//              halo {r, w, s, dinv},         centre {p, x}      (PF1)
+template <typename T, bool UNI> struct SlotsCG {
+  static constexpr int NH = UNI ? 4 : (ca_face_from_gh<T>() ? 5 : 6), NC = UNI ? 2 : (ca_face_from_gh<T>() ? 2 : 3);
+};
 
 struct Launch {
   int ntiles;
@@ -198,6 +204,10 @@ cudaError_t launch_phase_b(const Maps<SlotsB<T, UNI>::NH, SlotsB<T, UNI>::NC>& m
 template <typename T, bool UNI>
 cudaError_t launch_phase_ca(const Maps<SlotsCA<T, UNI>::NH, SlotsCA<T, UNI>::NC>& m, const Geom& g, T wc, T* x, T* r_out,
                             T* p_out, T* v_out, double* part, BicgState* st, int prime, const Launch& L);
+// One pass of Jacobi-preconditioned CG (Chronopoulos-Gear form, OpCG): prime = 1 is the start pass.
+template <typename T, bool UNI>
+cudaError_t launch_cg_pass(const Maps<SlotsCG<T, UNI>::NH, SlotsCG<T, UNI>::NC>& m, const Geom& g, T wc, T* r_out,
+                           T* w_out, T* s_out, T* p, T* x, double* part, BicgState* st, int prime, const Launch& L);
 cudaError_t launch_add_f32(double* x, const float* d, long n, cudaStream_t s);
 
 // ---- nonlinear step (Eq. 1, Eq. 11-13, Table 4) ----

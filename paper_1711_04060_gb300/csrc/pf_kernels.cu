@@ -660,6 +660,13 @@ cudaError_t launch_phase_ca(const Maps<SlotsCA<T, UNI>::NH, SlotsCA<T, UNI>::NC>
   return launch_stencil<OpCA<T, UNI>>(m, a, g, L);
 }
 
+template <typename T, bool UNI>
+cudaError_t launch_cg_pass(const Maps<SlotsCG<T, UNI>::NH, SlotsCG<T, UNI>::NC>& m, const Geom& g, T wc, T* r_out,
+                           T* w_out, T* s_out, T* p, T* x, double* part, BicgState* st, int prime, const Launch& L) {
+  typename OpCG<T, UNI>::Args a{part, st, r_out, w_out, s_out, p, x, wc, prime};
+  return launch_stencil<OpCG<T, UNI>>(m, a, g, L);
+}
+
 template <bool UNI>
 cudaError_t launch_residual(const Maps<SlotsRes<UNI>::NH, SlotsRes<UNI>::NC>& m, const Geom& g, double wc,
                             double diagc, int init, double* r, double* rt, double* p, double* v, double* t, float* r32,
@@ -818,7 +825,9 @@ cudaError_t launch_set_dirichlet(double* x, double lo, double hi, const Geom& g,
   template cudaError_t launch_phase_b<T, U>(const Maps<SlotsB<T, U>::NH, SlotsB<T, U>::NC>&, const Geom&, T, T*,   \
                                             double*, BicgState*, const Launch&);                                   \
   template cudaError_t launch_phase_ca<T, U>(const Maps<SlotsCA<T, U>::NH, SlotsCA<T, U>::NC>&, const Geom&, T, T*, \
-                                             T*, T*, T*, double*, BicgState*, int, const Launch&);
+                                             T*, T*, T*, double*, BicgState*, int, const Launch&);                 \
+  template cudaError_t launch_cg_pass<T, U>(const Maps<SlotsCG<T, U>::NH, SlotsCG<T, U>::NC>&, const Geom&, T, T*,   \
+                                            T*, T*, T*, T*, double*, BicgState*, int, const Launch&);
 PF_INST(double, false)
 PF_INST(double, true)
 PF_INST(float, false)

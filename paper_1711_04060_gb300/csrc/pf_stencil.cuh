@@ -553,11 +553,11 @@ __device__ __forceinline__ void stencil_run(const Maps<Op::NH, Op::NC>* __restri
         if (edge >= 0) {  // the edge node's stencil value and its Ctr of plane j, written straight to shared memory
           typename Op::Ctr& ce = ering[(j & 1) * NEDGE + (edge & 63)];
           qring[qnow + geo.hs] = Op::q_of(sc, H, geo.hbo, &ce);
-          Op::centre(a, H, C, geo.hbo, (edge >> 6) & 1, (edge >> 7) & 1, (edge >> 8) & 1, (edge >> 9) & 1, ce);
+          Op::centre(sc, a, H, C, geo.hbo, (edge >> 6) & 1, (edge >> 7) & 1, (edge >> 8) & 1, (edge >> 9) & 1, ce);
         }
         if (geo.cbo >= 0) qc = Op::q_of(sc, H, geo.cbo, &cnow);
         if (geo.valid)
-          Op::centre(a, H, C, geo.cbo, geo.gi > 0, geo.gj > 0, geo.gi < g.nx - 1, geo.gj < g.ny - 1, cnow);
+          Op::centre(sc, a, H, C, geo.cbo, geo.gi > 0, geo.gj > 0, geo.gi < g.nx - 1, geo.gj < g.ny - 1, cnow);
         qring[qnow + cs(lx, ly)] = qc;
         if (geo.hs >= 0 && edge < 0) qring[qnow + geo.hs] = geo.hbo >= 0 ? Op::q_of(sc, H, geo.hbo, nullptr) : T(0);
       }
@@ -653,8 +653,8 @@ struct OpB {
     }
     return di * s;
   }
-  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, bool west, bool south,
-                                bool east, bool north, Ctr& c) {
+  __device__ static void centre(const Sc&, const Args& a, const T* const* H, const T* const* C, int o, bool west,
+                                bool south, bool east, bool north, Ctr& c) {
     c.rt = C[RT][o];
     c.f.load(a.wc, H, C, o, west, south, east, north, WE, WN, WU, GHS);
   }
@@ -781,8 +781,8 @@ struct OpCA {
     }
     return di * pn;
   }
-  __device__ static void centre(const Args& a, const T* const* H, const T* const* C, int o, bool west, bool south,
-                                bool east, bool north, Ctr& c) {
+  __device__ static void centre(const Sc&, const Args& a, const T* const* H, const T* const* C, int o, bool west,
+                                bool south, bool east, bool north, Ctr& c) {
     c.x = C[X][o];
     c.rt = C[RT][o];
     c.f.load(a.wc, H, C, o, west, south, east, north, WE, WN, WU, GHS);
@@ -871,6 +871,156 @@ struct OpCA {
   }
 };
 
+// ------------------------------------------------------------------ conjugate gradients, one pass per iteration
+// Jacobi-preconditioned CG for the symmetric systems (Section 3: Eq. 9 and PF1; with zero-jump faces PF2 too) in
+// the single-reduction form of Chronopoulos and Gear, in the inner product <u, v>_w = sum_c w_c u_c v_c that weights
+// a node by 1/2 for every x or y side it lies on (A is symmetric in it; see pf_cg.cu).  With z = M^-1 r, w = A z,
+// s = A p, gamma = <r, z>_w, delta = <w, z>_w, one pass of iteration i forms at every node
+//   s_i = w_i + beta_i s_{i-1},  r_{i+1} = r_i - alpha_i s_i,  z_{i+1} = M^-1 r_{i+1},
+//   p_i = z_i + beta_i p_{i-1},  x_{i+1} = x_i + alpha_i p_i,    w_{i+1} = A z_{i+1} (the stencil),
+// and gamma_{i+1}, delta_{i+1}; the last block sets beta_{i+1} = gamma_{i+1} / gamma_i and
+// alpha_{i+1} = gamma_{i+1} / (delta_{i+1} - beta_{i+1} gamma_{i+1} / alpha_i).  The prime pass (alpha = beta = 0
+// on zeroed w, s, p) gives w_0 = A z_0, alpha_0 = gamma_0 / delta_0.  On identity rows r, w, s and p vanish.
+template <typename T_, bool UNI>
+struct OpCG {
+  using T = T_;
+  static constexpr bool GH = !UNI && ca_face_from_gh<T_>();
+  static constexpr int NH = SlotsCG<T_, UNI>::NH, NC = SlotsCG<T_, UNI>::NC, D = 2;
+  static constexpr int MINB = sizeof(T_) == 4 ? 4 : 2;
+  static constexpr int UNROLL = 1;
+  static constexpr bool CHECK_DONE = true;
+  enum { R = 0, W = 1, S = 2, DI = 3, WE = 4, WN = 5, GHS = 4 };
+  enum { P = 0, X = 1, WU = 2 };
+  struct Args {
+    double* part;
+    BicgState* st;
+    T* r_out;
+    T* w_out;
+    T* s_out;
+    T* p;  // p_{i-1} in, p_i out (read at the node only)
+    T* x;
+    T wc;
+    int prime;
+  };
+  struct Sc {
+    T al, be;
+  };
+  struct Ctr {
+    T s, rn, zold, pn, xn, di, sw;
+    FaceData<T, UNI, GH> f;
+  };
+  struct Accs {
+    Partials<T, 3> p;  // gamma' = <r', z'>_w, delta' = <w', z'>_w, r'.r'
+    T rmax = T(0);
+    __device__ void flush(double* wsum) { p.flush(wsum); }
+  };
+  __device__ static Sc scalars(const Args& a) { return Sc{(T)a.st->alpha, (T)a.st->beta}; }
+  __device__ static T q_of(const Sc& sc, const T* const* H, int o, Ctr* c) {
+    const T s = fma(sc.be, H[S][o], H[W][o]);
+    const T r = H[R][o];
+    const T rn = fma(-sc.al, s, r);
+    const T di = H[DI][o];
+    if (c) {
+      c->s = s;
+      c->rn = rn;
+      c->zold = di * r;
+      c->di = di;
+    }
+    return di * rn;  // z_{i+1}, the stencil's input
+  }
+  __device__ static void centre(const Sc& sc, const Args& a, const T* const* H, const T* const* C, int o, bool west,
+                                bool south, bool east, bool north, Ctr& c) {
+    c.pn = fma(sc.be, C[P][o], c.zold);
+    c.xn = fma(sc.al, c.pn, C[X][o]);
+    c.sw = (west && east ? T(1) : T(0.5)) * (south && north ? T(1) : T(0.5));
+    c.f.load(a.wc, H, C, o, west, south, east, north, WE, WN, WU, GHS);
+  }
+  __device__ static T up_face(const Args& a, const Ctr& lo, const Ctr& hi) { return lo.f.up(a.wc, hi.f); }
+  __device__ static void output(const Sc&, const Args& a, const T* Q, int pc, Nb nb, long cidx, const Ctr& c, T q_dn,
+                                T q_up, T wD, T wU, Accs& acc) {
+    T wn;
+    if (c.di == T(0)) {
+      wn = c.rn;
+    } else {
+      const T qE = Q[pc + nb.e], qW = Q[pc + nb.w], qN = Q[pc + nb.n], qS = Q[pc + nb.s];
+      T nbs;
+      if (UNI) {
+        nbs = a.wc * (((qE + qW) + (qN + qS)) + (q_up + q_dn));
+      } else {
+        T fe, fw, fn, fs;
+        c.f.sides(fe, fw, fn, fs);
+        nbs = fe * qE;
+        nbs = fma(fw, qW, nbs);
+        nbs = fma(fn, qN, nbs);
+        nbs = fma(fs, qS, nbs);
+        nbs = fma(wU, q_up, nbs);
+        nbs = fma(wD, q_dn, nbs);
+      }
+      wn = c.rn - nbs;
+      if (!a.prime) a.x[cidx] = c.xn;
+    }
+    a.r_out[cidx] = c.rn;
+    a.w_out[cidx] = wn;
+    a.s_out[cidx] = c.s;
+    a.p[cidx] = c.pn;
+    const T z = c.di * c.rn, swz = c.sw * z;
+    acc.p.t[0] = fma(swz, c.rn, acc.p.t[0]);
+    acc.p.t[1] = fma(swz, wn, acc.p.t[1]);
+    acc.p.t[2] = fma(c.rn, c.rn, acc.p.t[2]);
+    acc.rmax = fmax(acc.rmax, tabs(c.rn));
+  }
+  __device__ static void finish(const Args& a, const Accs& acc, const double* wsum, double* scratch, int bid,
+                                int nblk) {
+    using P = Partials<T, 3>;
+    if constexpr (sizeof(T) == 4) {
+      const double vals[4] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), (double)warp_max(acc.rmax)};
+      block_partials_warp_totals<4>(vals, 8u, a.part, scratch, bid);
+    } else {
+      double vals[4] = {P::total(wsum, 0), P::total(wsum, 1), P::total(wsum, 2), (double)acc.rmax};
+      block_partials<4>(vals, 8u, a.part, scratch, bid);
+    }
+    if (!arrive_last(&a.st->ticket, nblk)) return;
+    double tot[4];
+    total_partials<4>(a.part, 8u, tot, scratch, nblk);
+    if (threadIdx.x != 0) return;
+    BicgState* st = a.st;
+    const double ga = tot[0], de = tot[1], r2 = tot[2], rmx = tot[3];
+    st->ticket = 0;
+    if (!a.prime) {
+      st->iter += 1;
+      st->rnorm2 = r2;
+      st->rinf = rmx;
+      const bool conv = st->norm == 0 ? (r2 <= st->tol2) : (rmx < st->tol);
+      if (conv) {
+        st->done = 1;
+        st->status = 0;
+        return;
+      }
+      if (st->iter >= st->max_iter) {
+        st->done = 1;
+        st->status = 3;  // PF_E_NOCONV
+        return;
+      }
+    }
+    // gamma and delta are positive for a positive definite operator on a non-zero residual
+    double al = 0.0, be = 0.0;
+    if (a.prime || st->alpha == 0.0) {
+      al = ga / de;
+    } else {
+      be = ga / st->rho;
+      al = ga / (de - be * ga / st->alpha);
+    }
+    if (!(ga > 0.0) || !(de > 0.0) || !(al > 0.0) || !isfinite(al) || !isfinite(be)) {
+      st->done = 1;
+      st->status = 4;  // PF_E_BREAKDOWN
+      return;
+    }
+    st->rho = ga;
+    st->alpha = al;
+    st->beta = be;
+  }
+};
+
 // Squared 2-norm stop of a state whose residual has squared norm rr and right-hand side bb: the first
 // residual of a solve fixes r0norm2; the threshold is the larger of the b-relative and r0-relative ones.
 __device__ __forceinline__ void set_tol2(BicgState* st, double rr, double bb) {
@@ -920,8 +1070,8 @@ struct OpRes {
     if (c) c->ident = __double_as_longlong(H[DI][o]) == 0;
     return xv;
   }
-  __device__ static void centre(const Args& a, const double* const* H, const double* const* C, int o, bool west,
-                                bool south, bool east, bool north, Ctr& c) {
+  __device__ static void centre(const Sc&, const Args& a, const double* const* H, const double* const* C, int o,
+                                bool west, bool south, bool east, bool north, Ctr& c) {
     c.b = C[B][o];
     if constexpr (UNI) {
       c.diag = a.diagc;
