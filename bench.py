@@ -362,7 +362,7 @@ def config_of(args):
     return {"workload": f"pf_{args.n}_four_pores_NaCaCl", "grid": f"{args.n}^3", "h_A": 64.0 / (args.n - 1),
             "species": "Na+ 0.1 M, Ca2+ 1 mM, Cl- 0.102 M, water 55.5 M", "charges": 48,
             "tol_outer": args.tol_outer, "lin_tol": args.lin_tol,
-            "omega": 0.3, "accel_depth": args.accel_depth, "method": getattr(args, "method", "bicgstab"), "l2": l2,
+            "omega": 0.3, "accel_depth": args.accel_depth, "l2": l2,
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -780,7 +780,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic (seeded channel geometry, wall charges and bath; no dataset)",
-            "config": config_of(args), "precision": args.precision, "inner_tol": args.inner_tol,
+            "config": config_of(args), "precision": args.precision, "method": args.method,
+            "inner_tol": args.inner_tol,
             "clocks": clocks, "gpu_launches": int(prof["launches"]),
             "roofline": roofline,
             "solve": {"outer_iters": reps[-1]["outer_iters"], "lin_iters": reps[-1]["lin_iters_total"],

@@ -106,3 +106,21 @@ def test_ablation_host_step_against_the_oracle(orc):
     g = prob.grid
     _, ffix = orc.spread_charges(g.nx, g.ny, g.nz, g.h, g.origin, prob.charges, orc.lam(prob.T_K))
     assert np.abs(bench.host_spread(prob, orc.lam(prob.T_K)) - ffix).max() <= 1e-12 * np.abs(ffix).max()
+
+
+def test_kernel_tables_cover_every_timed_kind():
+    """Every kernel kind with algorithmic bytes has a kernel name and a profiler slot, and the per-kind table turns a
+    profile into launches, average time and algorithmic GB/s."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1711_04060_gb300 import _binding as B
+    assert set(bench.KERNEL_BYTES) <= set(bench.KERNEL_NAMES)
+    assert set(bench.KERNEL_BYTES) <= set(B.PROF_NAMES)
+    assert len(B.PROF_NAMES) == B.PF_PROF_KINDS
+    # phase C+A in FP32 reads one gh array for its faces (12 words); the one-pass CG on PF1 moves 11 words
+    assert bench.KERNEL_BYTES["ca_fp32"] == 48 and bench.KERNEL_BYTES["cg_fp32_pf1"] == 44
+    prof = {"launches": 3, "ca_fp32": (2, 0.3), "cg_fp32_pf1": (1, 0.1), "fermi": (0, 0.0)}
+    t = bench.kernel_table(prof, 10 ** 6)
+    assert set(t) == {"ca_fp32", "cg_fp32_pf1"}
+    assert t["ca_fp32"]["avg_us"] == 150.0 and t["ca_fp32"]["GB/s"] == round(48e6 / 150e-6 / 1e9, 1)
+    assert t["cg_fp32_pf1"]["launches"] == 1
