@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--method", default="bicgstab", choices=["bicgstab", "cg-symmetric"],
                     help="Krylov method of the headline: BiCGSTAB (Table 3) or CG for the Poisson and PF1 systems")
     ap.add_argument("--no-cg-leg", action="store_true", help="skip the solve with CG for the symmetric systems")
+    ap.add_argument("--predict", type=int, default=1, choices=[0, 1],
+                    help="starting vectors of the linear solves: 1 extrapolated (default), 0 previous iterates")
+    ap.add_argument("--no-predict-leg", action="store_true", help="skip the solve with predict = 0")
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--tol-outer", type=float, default=1e-3, help="||Phi - Phi_0||_inf stop (phi_hat units)")
     ap.add_argument("--lin-tol", type=float, default=1e-6, help="relative 2-norm tolerance of each linear solve")
@@ -376,7 +379,7 @@ def serve_sample(api, args, precision, count=None, gap=None):
     reqs = W.request_stream(count=count, seed=4, mean_gap_s=gap)
     probs = [(t, make()) for t, _, make in reqs]
     opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=precision,
-                       accel_depth=args.accel_depth)
+                       accel_depth=args.accel_depth, predict=args.predict)
     qs = [api.make_request(p, opts) for _, p in probs]
     srv = api.pf_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
     lat, status, nodes = [], [], 0
@@ -422,8 +425,8 @@ def batch_sample(api, args, torch, dev):
     probs = W.batch_instances(args.batch)
     grids = [api.Grid.for_problem(p) for p in probs]
     batch = api.Batch(grids)
-    om = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_MIXED)
-    o64 = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_FP64)
+    om = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_MIXED, predict=args.predict)
+    o64 = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_FP64, predict=args.predict)
     try:
         batch.nonlinear_solve(om, allow=(3,))  # warm-up (runs the autotuner)
         torch.cuda.synchronize(dev)
@@ -715,7 +718,7 @@ def run_ours(args):
     prec = api.PF_MIXED if args.precision == "mixed" else api.PF_FP64
     method = api.PF_CG_SYMMETRIC if args.method == "cg-symmetric" else api.PF_BICGSTAB
     opts = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, accel_depth=args.accel_depth,
-                       inner_tol=args.inner_tol, method=method)
+                       inner_tol=args.inner_tol, method=method, predict=args.predict)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -796,7 +799,7 @@ def run_ours(args):
     fp64_rep = None
     host64 = None
     if not args.no_fp64 and args.precision == "mixed":
-        o64 = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_FP64)
+        o64 = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=api.PF_FP64, predict=args.predict)
         out64 = {k: torch.zeros_like(v) for k, v in out.items()}
         xw = np.zeros(N)
         grid.linear_solve(api.PF_OP_POISSON, np.zeros(N), xw, api.solve_opts(max_iter=2), allow=(3,))
@@ -845,9 +848,9 @@ def run_ours(args):
 
         tt, tl, ta = args.tight_tol_outer, args.tight_lin_tol, args.tight_accel
         ms_m, rep_m, out_m = timed(api.nl_opts(tol_outer=tt, tol=tl, precision=api.PF_MIXED, inner_tol=args.inner_tol,
-                                               accel_depth=ta, max_outer=3000))
+                                               accel_depth=ta, max_outer=3000, predict=args.predict))
         ms_d, rep_d, out_d = timed(api.nl_opts(tol_outer=tt, tol=tl, precision=api.PF_FP64, accel_depth=ta,
-                                               max_outer=3000))
+                                               max_outer=3000, predict=args.predict))
         ms_r, rep_r, out_r = timed(api.nl_opts(tol_outer=tt / 10, tol=tl / 10, precision=api.PF_FP64, accel_depth=5,
                                                max_outer=3000))
         ref_phi, ref_C = out_r["phi_V"], out_r["C_M"]
@@ -871,10 +874,32 @@ def run_ours(args):
         if host64 is not None:
             line["headline_vs_reference"]["fp64"] = rel_errors(host64["phi_V"], host64["C_M"], ref_phi, ref_C, ns)
 
+    # the same solve with the linear solves started from the previous iterates (predict = 0)
+    if not args.no_predict_leg and args.predict == 1:
+        op0 = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, inner_tol=args.inner_tol,
+                          method=method, predict=0)
+        outp = {k: torch.zeros_like(v) for k, v in out.items()}
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prep = solve(op0, outp)
+        e1.record(stream)
+        e1.synchronize()
+        msp = e0.elapsed_time(e1)
+        phip = outp["phi_V"].cpu().numpy()
+        Cp = outp["C_M"].cpu().numpy().reshape(ns, N)
+        Cm = C_mixed.reshape(ns, N)
+        line["predict_off"] = {
+            "value": 1e3 / msp, "unit": UNIT, "ms_per_step": msp, "outer_iters": prep["outer_iters"],
+            "lin_iters": prep["lin_iters_total"], "status": prep["status"],
+            "phi_rel_vs_headline": float(np.abs(phip - phi_mixed).max() / np.abs(phi_mixed).max()),
+            "conc_rel_vs_headline": float(max(np.abs(Cp[i] - Cm[i]).max() / Cm[i].max() for i in range(ns)))}
+
     # the same solve with CG (one pass per iteration) for the systems Section 3 names symmetric: Poisson and PF1
     if not args.no_cg_leg and args.method == "bicgstab":
         oc = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, inner_tol=args.inner_tol,
-                         method=api.PF_CG_SYMMETRIC)
+                         method=api.PF_CG_SYMMETRIC, predict=args.predict)
         outc = {k: torch.zeros_like(v) for k, v in out.items()}
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -899,7 +924,8 @@ def run_ours(args):
 
     # Anderson-accelerated solve of the same workload (same fixed point and stop test)
     if args.accel_depth == 0 and not args.no_accel:
-        oa = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, accel_depth=5)
+        oa = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, accel_depth=5,
+                         predict=args.predict)
         outa = {k: torch.zeros_like(v) for k, v in out.items()}
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -964,11 +990,17 @@ def run_ours(args):
     # CPU oracle on a bounded sample (rank 0, one GPU only): all host threads (OpenMP copy) and one thread
     if rank == 0 and world == 1 and not args.no_cpu:
         ph = phi_sample(prob, args.cpu_nodes)
-        if fp64_rep is not None:
+        # the oracle starts each linear solve from the previous iterates: on the default workload it is charged
+        # its own counts (REF_WORK), elsewhere those of this arm's FP64 solve with the same starting vectors
+        if args.n == 257 and args.tol_outer == 1e-3 and args.lin_tol == 1e-6:
+            work_outer, work_lin = REF_WORK["outer"], REF_WORK["lin_iters"]
+            what = "the oracle's FP64 solve of this workload (linear solves started from the previous iterates)"
+        elif fp64_rep is not None:
             work_outer, work_lin = fp64_rep["outer_iters"], fp64_rep["lin_iters_total"]
+            what = f"this workload's FP64 solve (predict = {args.predict})"
         else:
             work_outer, work_lin = reps[-1]["outer_iters"], reps[-1]["lin_iters_total"]
-        what = "this workload's FP64 solve"
+            what = f"this workload's solve (predict = {args.predict})"
         sa = oracle_sample(prob, ph, args.cpu_iters, all_cores=True)
         s1 = oracle_sample(prob, ph, args.cpu_iters, all_cores=False)
         Ta, T1 = oracle_solve_time(sa, work_outer, work_lin), oracle_solve_time(s1, work_outer, work_lin)

@@ -47,7 +47,7 @@ class pf_report(ctypes.Structure):
 
 class pf_nl_opts(ctypes.Structure):
     _fields_ = [("omega", _D), ("tol_outer", _D), ("max_outer", _I), ("lin", pf_solve_opts), ("accel_depth", _I),
-                ("lin_forcing", _D), ("warm_start", _I)]
+                ("lin_forcing", _D), ("warm_start", _I), ("predict", _I)]
 
 
 class pf_result(ctypes.Structure):

@@ -611,6 +611,34 @@ pf_status unpack_out(pf_grid* g, const double* src, int count, double* dst, int 
   return PF_OK;
 }
 
+// Starting vector of a linear solve in the outer iteration: x <- x + c (x - x_prev), x_prev <- the old x (the last
+// two solutions of the same system extrapolated along their last change; c = 0 keeps x and only saves it).
+__global__ void k_predict(double* __restrict__ x, double* __restrict__ xprev, double c, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double t = x[i];
+    x[i] = fma(c, t - xprev[i], t);
+    xprev[i] = t;
+  }
+}
+
+pf_status predict(pf_grid* g, double* x, double* xprev, double c) {
+  const long n = g->geom.np;
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  long blocks = (n + 255) / 256;
+  if (blocks > 8L * nsm) blocks = 8L * nsm;
+  PF_LAUNCH(g, PF_PROF_OTHER, (k_predict<<<(int)blocks, 256, 0, g->stream>>>(x, xprev, c, n), cudaGetLastError()));
+  return PF_OK;
+}
+
+pf_status ensure_predict(pf_grid* g) {
+  if (g->xp_psi) return PF_OK;
+  PF_TRY(dalloc(g, &g->xp_psi, g->geom.np));
+  PF_TRY(dalloc(g, &g->xp_phi, g->geom.np));
+  return PF_OK;
+}
+
 // Buffers of Anderson acceleration with depth m (kept for later solves on the grid).
 pf_status ensure_aa(pf_grid* g, int m) {
   const long NP = g->geom.np;
@@ -785,9 +813,10 @@ void pf_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
 // Device bytes that pf_create_grid allocates for a grid (used for the serving budget).
 size_t pf_internal_grid_bytes(int nx, int ny, int nz, int accel_depth) {
   const pf::Geom g = pf::make_geom(nx, ny, nz);
-  // Anderson acceleration adds f, f_prev, x_prev and two history columns per depth
+  // Anderson acceleration adds f, f_prev, x_prev and two history columns per depth; the count includes the two
+  // vectors of the predicted starting vectors (pf_nl_opts.predict = 1, the default)
   const int aa = accel_depth > 0 ? 3 + 2 * accel_depth : 0;
-  const size_t per_node = (32 + aa) * sizeof(double) + pf::MAXSP * sizeof(double) + 18 * sizeof(float) + 1;
+  const size_t per_node = (34 + aa) * sizeof(double) + pf::MAXSP * sizeof(double) + 18 * sizeof(float) + 1;
   return (size_t)g.np * per_node + (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double) + 8192;
 }
 
@@ -818,6 +847,7 @@ void pf_default_nl_opts(pf_nl_opts* o) {
   o->accel_depth = 0;
   o->lin_forcing = 0.0;
   o->warm_start = 0;
+  o->predict = 1;
 }
 
 const char* pf_last_error(void) { return g_err.c_str(); }
@@ -1253,10 +1283,12 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
       o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0))
     return fail(PF_E_INVAL, "invalid pf_nl_opts");
   if (o.warm_start != 0 && o.warm_start != 1) return fail(PF_E_INVAL, "invalid pf_nl_opts");
+  if (o.predict != 0 && o.predict != 1) return fail(PF_E_INVAL, "invalid pf_nl_opts.predict");
   if (o.warm_start && !g->have_phi0)
     return fail(PF_E_INVAL, "warm_start needs a potential on the grid (a previous solve or pf_set_potential)");
   const int m = o.accel_depth;
   if (m > 0) PF_TRY(ensure_aa(g, m));
+  if (o.predict) PF_TRY(ensure_predict(g));
   if (res->mem != PF_MEM_HOST && res->mem != PF_MEM_DEVICE) return fail(PF_E_INVAL, "bad result mem");
   const pf::Geom& G = g->geom;
   const long NP = G.np;
@@ -1288,8 +1320,13 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
     if (rep.status != PF_OK) st = (pf_status)rep.status;
   }
   OuterUpdate U;
-  double delta_prev = 1.0;
+  double delta_prev = 1.0, delta_prev2 = 0.0;
   for (int outer = 1; st == PF_OK && outer <= o.max_outer; ++outer) {
+    // starting vectors (pf_nl_opts.predict): from the third outer iteration on, the previous two solutions
+    // extrapolated with c = delta_{k-1} / delta_{k-2} while the outer updates shrink
+    const int have = outer - 1;  // PF1 / PF2 solutions of this solve so far
+    const double c_pred =
+        (o.predict && have >= 2 && delta_prev2 > 0.0 && delta_prev < delta_prev2) ? delta_prev / delta_prev2 : 0.0;
     // forcing term: the linear solves of this outer iteration stop at eta ||r0|| (r0: the residual of the warm
     // start, which shrinks with the outer update) or at lin.tol ||b||, whichever is reached first
     double eta = 0.0;
@@ -1306,13 +1343,17 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
                                                    g->err, s));
     if (g->filter_on) PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->b1, 1, s));  // Psi = 0
     PF_TRY(update_pf2(g));
+    if (o.predict && have >= 1) PF_TRY(predict(g, g->psi, g->xp_psi, c_pred));
     PF_TRY(solve_dev(g, PF_OP_PF1, g->b1, g->psi, lo, &rep, eta));  // Eq. (12)
     res->lin_iters_total += rep.iterations;
     if (rep.status != PF_OK) { st = (pf_status)rep.status; break; }
     PF_LAUNCH(g, PF_PROF_OTHER,
               pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat, G, g->b2, s));
     if (g->filter_on) PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_values(g->fmask, g->fval, G, g->b2, s));
-    PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (o.predict && have >= 1)
+      PF_TRY(predict(g, g->phi, g->xp_phi, c_pred));  // from the previous PF2 solution
+    else
+      PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
     PF_TRY(solve_dev(g, PF_OP_PF2, g->b2, g->phi, lo, &rep, eta));  // Eq. (13)
     res->lin_iters_total += rep.iterations;
     if (rep.status != PF_OK) { st = (pf_status)rep.status; break; }
@@ -1326,6 +1367,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
     if (*g->host_err) { st = PF_E_GAMMA; break; }
     res->outer_iters = outer;
     res->delta = delta;
+    delta_prev2 = delta_prev;
     delta_prev = delta;
     if (trace_level() > 0)
       fprintf(stderr, "[pf] outer %d delta %.6e lin_total %d eta %.1e\n", outer, res->delta, res->lin_iters_total,

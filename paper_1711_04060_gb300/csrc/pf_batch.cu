@@ -513,8 +513,10 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
       r.delta = 0.0;
       M.U = OuterUpdate{};
       M.dprev = 1.0;
+      M.dprev2 = 0.0;
       M.st = PF_OK;
       if (M.o.accel_depth > 0) PF_TRY(ensure_aa(g, M.o.accel_depth));
+      if (M.o.predict) PF_TRY(ensure_predict(g));
       PF_TRY(build_operators(g));
       M.fermi_warm = M.o.warm_start && g->ulast_valid;
       if (M.o.warm_start) {  // start from the grid's potential: straight to the first outer iteration
@@ -544,6 +546,10 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
                                                      g->c2, nullptr, nullptr, nullptr, g->ulast,
                                                      outer > 1 || M.fermi_warm, g->err, s));
       PF_TRY(update_pf2(g));
+      // starting vectors as pf_nonlinear_solve: the last two solutions extrapolated while the updates shrink
+      const bool pred = M.o.predict && outer >= 2;
+      M.cpred = (pred && outer >= 3 && M.dprev2 > 0.0 && M.dprev < M.dprev2) ? M.dprev / M.dprev2 : 0.0;
+      if (pred) PF_TRY(predict(g, g->psi, g->xp_psi, M.cpred));
       PF_TRY(lin_start(B, M, PF_OP_PF1, S_PF2RHS, eta));
       break;
     }
@@ -551,7 +557,10 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
       // PF2 right-hand side from Psi, then PF2 (Eq. 13) from Phi_0
       PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat,
                                                      g->geom, g->b2, s));
-      PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (M.o.predict && M.res->outer_iters >= 1)
+        PF_TRY(predict(g, g->phi, g->xp_phi, M.cpred));  // from the previous PF2 solution
+      else
+        PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
       PF_TRY(lin_start(B, M, PF_OP_PF2, S_UPDATE, M.eta));
       break;
     }
@@ -773,6 +782,7 @@ pf_status tick(pf_batch* B) {
     if (was[i] != S_UPDATE) continue;
     PF_TRY(outer_stage3(M.g, M.U, M.o.accel_depth, M.o.omega, stop[i]));
     const int outer = ++M.res->outer_iters;
+    M.dprev2 = M.dprev;
     M.dprev = M.res->delta;
     if (trace_level() > 0)
       fprintf(stderr, "[pf batch] member %lld outer %d delta %.6e\n", M.tag, outer, M.res->delta);
@@ -869,7 +879,8 @@ pf_status check_nl(const pf_nl_opts& o) {
   if (o.lin.method != PF_BICGSTAB)
     return fail(PF_E_INVAL, "batches and served requests solve with BiCGSTAB (pf_solve_opts.method = PF_BICGSTAB)");
   if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1 || o.accel_depth < 0 ||
-      o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0) || (o.warm_start != 0 && o.warm_start != 1))
+      o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0) || (o.warm_start != 0 && o.warm_start != 1) ||
+      (o.predict != 0 && o.predict != 1))
     return fail(PF_E_INVAL, "invalid pf_nl_opts");
   return PF_OK;
 }

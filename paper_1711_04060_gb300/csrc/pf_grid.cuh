@@ -85,6 +85,8 @@ struct pf_grid {
   // Anderson acceleration of the outer loop (allocated on first use)
   int aa_alloc = 0;
   double *aa_f = nullptr, *aa_fprev = nullptr, *aa_xprev = nullptr, *aa_out = nullptr, *aa_host = nullptr;
+  // the PF1 and PF2 solutions of the outer iteration before the last one (pf_nl_opts.predict; on first use)
+  double *xp_psi = nullptr, *xp_phi = nullptr;
   double *aa_dF[pf::AA_MAX] = {}, *aa_dX[pf::AA_MAX] = {};
   double* dch = nullptr;     // fixed charges (x, y, z, q) on the device
   int nq = 0;
@@ -216,6 +218,11 @@ pf_status build_operators(pf_grid* g);
 pf_status pack_in(pf_grid* g, const void* src, int mem, void* dst, int type);
 pf_status unpack_out(pf_grid* g, const double* src, int count, double* dst, int mem);
 pf_status ensure_aa(pf_grid* g, int m);
+// x <- x + c (x - xprev), xprev <- the old x: the starting vector of a linear solve of the outer iteration
+// (pf_nl_opts.predict); both vectors FP64 over the padded grid
+pf_status predict(pf_grid* g, double* x, double* xprev, double c);
+// the two FP64 vectors of pf_nl_opts.predict, allocated on first use
+pf_status ensure_predict(pf_grid* g);
 bool small_spd_solve(int k, const double (&A)[pf::AA_MAX][pf::AA_MAX], const double* b, double* x);
 
 // The update at the end of an outer iteration (Table 4's relaxation, or Anderson acceleration of the same
@@ -239,6 +246,8 @@ struct BatchMember {
   pf_nl_opts o{};
   OuterUpdate U;
   double dprev = 1.0;   // delta of the previous outer iteration (forcing term)
+  double dprev2 = 0.0;  // delta of the one before (pf_nl_opts.predict)
+  double cpred = 0.0;   // extrapolation factor of this outer iteration's starting vectors
   int stage = 0;        // step of the nonlinear iteration (pf_batch.cu: Stage)
   int after = 0;        // stage to enter when the running linear solve ends
   // the linear solve in progress
