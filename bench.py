@@ -463,6 +463,7 @@ def batch_sample(api, args, torch, dev):
             "engine": engine,
             "value": args.batch / t_batch, "unit": UNIT, "s": t_batch,
             "all_ok": bool(all(r["status"] == 0 for _, r in res)), "outer_iters_sum": int(sum(r["outer_iters"] for _, r in res)),
+            "lin_iters_sum": int(sum(r["lin_iters_total"] for _, r in res)),
             "tiles_per_block": tune["chosen"], "tile_z_planes": tune["chosen_z"],
             "fp64_single_solves": {"value": args.batch / t_seq, "unit": UNIT, "s": t_seq, "all_ok": seq_ok},
             "speedup_vs_fp64_single": t_seq / t_batch, "phi_rel_vs_fp64_single": worst_phi}

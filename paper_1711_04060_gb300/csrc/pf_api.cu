@@ -460,6 +460,9 @@ pf_status solve_mixed(pf_grid* g, int op, const double* b, double* x, const pf_s
       status = PF_E_NOCONV;
       break;
     }
+    // a step that can end the refinement stops its inner solve at FINAL_INNER_MARGIN of the target
+    const double t2 = final_inner_tol2(o, tr.rnorm2, tr.tol2);
+    if (t2 > 0.0) PF_TRY(raise_tol2(g, g->st2, t2, g->stream));
     BicgState s;
     if (use_cg(o, op))
       PF_TRY((iterate_cg<float, UNI>(g, W, g->d32, K, g->st2, &s)));
@@ -630,6 +633,21 @@ pf_status predict(pf_grid* g, double* x, double* xprev, double c) {
   if (blocks > 8L * nsm) blocks = 8L * nsm;
   PF_LAUNCH(g, PF_PROF_OTHER, (k_predict<<<(int)blocks, 256, 0, g->stream>>>(x, xprev, c, n), cudaGetLastError()));
   return PF_OK;
+}
+
+__global__ void k_raise_tol2(BicgState* st, double t2) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->tol2 = fmax(st->tol2, t2);
+}
+
+pf_status raise_tol2(pf_grid* g, BicgState* st, double t2, cudaStream_t s) {
+  PF_LAUNCH(g, PF_PROF_OTHER, (k_raise_tol2<<<1, 32, 0, s>>>(st, t2), cudaGetLastError()));
+  return PF_OK;
+}
+
+double final_inner_tol2(const pf_solve_opts& o, double rr, double t2) {
+  if (o.norm != PF_NORM_REL2) return 0.0;
+  const double f2 = FINAL_INNER_MARGIN * FINAL_INNER_MARGIN * t2;
+  return f2 > o.inner_tol * o.inner_tol * rr ? f2 : 0.0;
 }
 
 pf_status ensure_predict(pf_grid* g) {

@@ -612,6 +612,7 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
       PF_TRY(set_state(g, g->st2, lo.inner_tol, PF_NORM_REL2, cap));
       PF_LAUNCH(g, PF_PROF_INIT, pf::launch_init_zero<float>(g->b32, g->geom, K.r[0], K.rt, K.p[0], K.v[0], K.t,
                                                               g->part, g->st2, s));
+      if (M.inner_t2 > 0.0) PF_TRY(raise_tol2(g, g->st2, M.inner_t2, s));  // as pf_nonlinear_solve
       kinds.push_back(base + K_PRIME32);
       kinds.push_back(base + K_CHUNK32);
       M.sub = L_INNER;
@@ -663,6 +664,7 @@ void post(BatchMember& M, const BicgState& s64, const BicgState& s32) {
       } else if (M.refs >= lo.max_refine || M.iters >= lo.max_iter) {
         lin_end(M, PF_E_NOCONV);
       } else {
+        M.inner_t2 = final_inner_tol2(lo, s64.rnorm2, s64.tol2);
         M.sub = L_INNER_START;
       }
       break;

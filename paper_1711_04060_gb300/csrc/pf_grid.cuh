@@ -40,6 +40,9 @@ pf_status cuda_fail(cudaError_t e, const char* what);
 
 constexpr int CHUNK = 8;         // BiCGSTAB iterations launched between two host checks of the done flag
 constexpr int INNER_CAP = 1000;  // FP32 iterations per refinement step at most
+// An FP32 inner solve that can end the refinement (its start ||r|| within 1/inner_tol of the solve's target T)
+// stops at FINAL_INNER_MARGIN * T instead of inner_tol ||r||: the next FP64 true residual decides
+constexpr double FINAL_INNER_MARGIN = 0.5;
 constexpr int PROF_SLOTS = 64;   // timed launches between two resolutions of the profiling events
 constexpr unsigned long long WAIT_LIMIT = 4000000000ull;  // clock cycles (about 2 s) per TMA stage wait
 
@@ -223,6 +226,12 @@ pf_status ensure_aa(pf_grid* g, int m);
 pf_status predict(pf_grid* g, double* x, double* xprev, double c);
 // the two FP64 vectors of pf_nl_opts.predict, allocated on first use
 pf_status ensure_predict(pf_grid* g);
+// Squared 2-norm stop of the FP32 inner solve of a refinement step, given the step's FP64 residual norm^2 rr and
+// the solve's squared target t2 (REL2 only): FINAL_INNER_MARGIN^2 t2 when that is above inner_tol^2 rr, else 0
+// (keep inner_tol)
+double final_inner_tol2(const pf_solve_opts& o, double rr, double t2);
+// st->tol2 = max(st->tol2, t2) on the device, in stream order
+pf_status raise_tol2(pf_grid* g, BicgState* st, double t2, cudaStream_t s);
 bool small_spd_solve(int k, const double (&A)[pf::AA_MAX][pf::AA_MAX], const double* b, double* x);
 
 // The update at the end of an outer iteration (Table 4's relaxation, or Anderson acceleration of the same
@@ -248,6 +257,7 @@ struct BatchMember {
   double dprev = 1.0;   // delta of the previous outer iteration (forcing term)
   double dprev2 = 0.0;  // delta of the one before (pf_nl_opts.predict)
   double cpred = 0.0;   // extrapolation factor of this outer iteration's starting vectors
+  double inner_t2 = 0.0;  // squared stop of the next FP32 inner solve when it may end the refinement (else 0)
   int stage = 0;        // step of the nonlinear iteration (pf_batch.cu: Stage)
   int after = 0;        // stage to enter when the running linear solve ends
   // the linear solve in progress
