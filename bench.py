@@ -309,6 +309,19 @@ def oracle_sample(prob, phi_hat_sample, iters, all_cores=False):
             "n_solvent": int(prob.solvent.sum()), "threads": threads}
 
 
+def oracle_work(args, fp64_rep, rep):
+    """(outer iterations, BiCGSTAB iterations, description) the oracle's extrapolated solve is charged.  The oracle
+    starts each linear solve from the previous iterates: on the default workload it is charged its own counts
+    (REF_WORK); elsewhere the counts of this arm's FP64 solve (else its headline solve), with the arm's starting
+    vectors named."""
+    if args.n == 257 and args.tol_outer == 1e-3 and args.lin_tol == 1e-6:
+        return (REF_WORK["outer"], REF_WORK["lin_iters"],
+                "the oracle's FP64 solve of this workload (linear solves started from the previous iterates)")
+    if fp64_rep is not None:
+        return fp64_rep["outer_iters"], fp64_rep["lin_iters_total"], f"this workload's FP64 solve (predict = {args.predict})"
+    return rep["outer_iters"], rep["lin_iters_total"], f"this workload's solve (predict = {args.predict})"
+
+
 def oracle_solve_time(samp, outer, lin_iters):
     # per outer iteration: one Fermi step over the solvent nodes and two operator assemblies
     return outer * (samp["n_solvent"] * samp["t_node"] + 2 * samp["t_asm"]) + lin_iters * samp["t_iter"]
@@ -991,17 +1004,7 @@ def run_ours(args):
     # CPU oracle on a bounded sample (rank 0, one GPU only): all host threads (OpenMP copy) and one thread
     if rank == 0 and world == 1 and not args.no_cpu:
         ph = phi_sample(prob, args.cpu_nodes)
-        # the oracle starts each linear solve from the previous iterates: on the default workload it is charged
-        # its own counts (REF_WORK), elsewhere those of this arm's FP64 solve with the same starting vectors
-        if args.n == 257 and args.tol_outer == 1e-3 and args.lin_tol == 1e-6:
-            work_outer, work_lin = REF_WORK["outer"], REF_WORK["lin_iters"]
-            what = "the oracle's FP64 solve of this workload (linear solves started from the previous iterates)"
-        elif fp64_rep is not None:
-            work_outer, work_lin = fp64_rep["outer_iters"], fp64_rep["lin_iters_total"]
-            what = f"this workload's FP64 solve (predict = {args.predict})"
-        else:
-            work_outer, work_lin = reps[-1]["outer_iters"], reps[-1]["lin_iters_total"]
-            what = f"this workload's solve (predict = {args.predict})"
+        work_outer, work_lin, what = oracle_work(args, fp64_rep, reps[-1])
         sa = oracle_sample(prob, ph, args.cpu_iters, all_cores=True)
         s1 = oracle_sample(prob, ph, args.cpu_iters, all_cores=False)
         Ta, T1 = oracle_solve_time(sa, work_outer, work_lin), oracle_solve_time(s1, work_outer, work_lin)

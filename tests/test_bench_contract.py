@@ -124,3 +124,20 @@ def test_kernel_tables_cover_every_timed_kind():
     assert set(t) == {"ca_fp32", "cg_fp32_pf1"}
     assert t["ca_fp32"]["avg_us"] == 150.0 and t["ca_fp32"]["GB/s"] == round(48e6 / 150e-6 / 1e9, 1)
     assert t["cg_fp32_pf1"]["launches"] == 1
+
+
+def test_oracle_baseline_charged_its_own_iterations():
+    """The CPU baseline extrapolates the oracle's per-iteration cost to the oracle's own solve: on the default 257^3
+    workload the counts of its previous-iterate starts, never the fewer iterations of the GPU arm's predicted
+    starts; on other workloads the arm's FP64 counts, with the arm's starting vectors named."""
+    sys.path.insert(0, ROOT)
+    import bench
+    fp64 = {"outer_iters": 188, "lin_iters_total": 6152}
+    head = {"outer_iters": 188, "lin_iters_total": 6810}
+    A = lambda **kw: type("A", (), dict(dict(n=257, tol_outer=1e-3, lin_tol=1e-6, predict=1), **kw))
+    o, l, what = bench.oracle_work(A(), fp64, head)
+    assert (o, l) == (bench.REF_WORK["outer"], bench.REF_WORK["lin_iters"]) and "previous iterates" in what
+    o, l, what = bench.oracle_work(A(n=129), fp64, head)
+    assert (o, l) == (188, 6152) and "predict = 1" in what
+    o, l, what = bench.oracle_work(A(lin_tol=1e-8), None, head)
+    assert (o, l) == (188, 6810)
