@@ -18,6 +18,11 @@ def test_option_structs(api):
     n = api.nl_opts(omega=0.4, tol_outer=1e-5, max_outer=77, accel_depth=3, lin_forcing=0.5, tol=1e-8)
     assert (n.omega, n.tol_outer, n.max_outer, n.accel_depth, n.lin_forcing, n.lin.tol) == (0.4, 1e-5, 77, 3, 0.5, 1e-8)
     assert n.warm_start == 0
+    # the library's defaults: the paper's relaxation and tolerances, extrapolated starting vectors, BiCGSTAB
+    d = api.nl_opts()
+    assert (d.omega, d.tol_outer, d.accel_depth, d.lin_forcing, d.predict) == (0.3, 1e-9, 0, 0.0, 1)
+    assert (d.lin.method, d.lin.precision, d.lin.inner_tol) == (api.PF_BICGSTAB, api.PF_FP64, 0.1)
+    assert api.nl_opts(predict=0).predict == 0
 
 
 def test_arrays_are_checked_before_the_library_is_called(api):
