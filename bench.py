@@ -75,8 +75,9 @@ def parse():
     ap.add_argument("--method", default="bicgstab", choices=["bicgstab", "cg-symmetric"],
                     help="Krylov method of the headline: BiCGSTAB (Table 3) or CG for the Poisson and PF1 systems")
     ap.add_argument("--no-cg-leg", action="store_true", help="skip the solve with CG for the symmetric systems")
-    ap.add_argument("--predict", type=int, default=1, choices=[0, 1],
-                    help="starting vectors of the linear solves: 1 extrapolated (default), 0 previous iterates")
+    ap.add_argument("--predict", type=int, default=2, choices=[0, 1, 2],
+                    help="starting vectors of the linear solves: 2 extrapolated with each vector's own ratio (default), "
+                         "1 with the outer updates' ratio, 0 previous iterates")
     ap.add_argument("--no-predict-leg", action="store_true", help="skip the solve with predict = 0")
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--tol-outer", type=float, default=1e-3, help="||Phi - Phi_0||_inf stop (phi_hat units)")
@@ -889,7 +890,7 @@ def run_ours(args):
             line["headline_vs_reference"]["fp64"] = rel_errors(host64["phi_V"], host64["C_M"], ref_phi, ref_C, ns)
 
     # the same solve with the linear solves started from the previous iterates (predict = 0)
-    if not args.no_predict_leg and args.predict == 1:
+    if not args.no_predict_leg and args.predict != 0:
         op0 = api.nl_opts(tol_outer=args.tol_outer, tol=args.lin_tol, precision=prec, inner_tol=args.inner_tol,
                           method=method, predict=0)
         outp = {k: torch.zeros_like(v) for k, v in out.items()}

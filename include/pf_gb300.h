@@ -143,11 +143,13 @@ typedef struct {
                          stopped) or the one given to pf_set_potential; PF_E_INVAL if the grid holds none.  The
                          fixed point does not depend on the start. */
   int predict;        /* starting vector of the PF1 and PF2 solves of outer iteration k (the paper does not fix
-                         it).  1 (default): the previous two solutions of the same system extrapolated along
-                         their last change, x_{k-1} + c (x_{k-1} - x_{k-2}) with c = delta_{k-1} / delta_{k-2}
-                         while the outer updates shrink (else c = 0); 2 FP64 vectors on first use.  0: PF1 from
-                         the previous Psi, PF2 from Phi_0.  Either way each solve meets lin.tol; single-grid
-                         solves, batches and served requests alike. */
+                         it): the last solution of the same system extrapolated along its last change,
+                         x_{k-1} + c (x_{k-1} - x_{k-2}).  2 (default): c = d1.d0 / d0.d0 clamped to [0, 1]
+                         (d1 = x_{k-1} - x_{k-2}, d0 = x_{k-2} - x_{k-3}; in outer iteration 3, as 1).  1: c =
+                         delta_{k-1} / delta_{k-2} while the outer updates shrink, else 0.  0: PF1 from the
+                         previous Psi, PF2 from Phi_0.  1 and 2 hold 4 FP64 vectors, allocated on first use.
+                         Either way each solve meets lin.tol; single-grid solves, batches and served requests
+                         alike. */
 } pf_nl_opts;
 
 /* Output and report of pf_nonlinear_solve.  Output pointers may be NULL; `mem` says whether
@@ -184,8 +186,8 @@ void pf_default_nl_opts(pf_nl_opts* o);
 pf_status pf_create_grid(int nx, int ny, int nz, double h_A, const double origin_A[3],
                          void* cuda_stream, pf_grid** out);
 
-/* Device bytes that pf_create_grid allocates for an nx x ny x nz grid, plus the two FP64 vectors of the
- * predicted starting vectors (pf_nl_opts.predict = 1, allocated by the first nonlinear solve that uses them)
+/* Device bytes that pf_create_grid allocates for an nx x ny x nz grid, plus the four FP64 vectors of the
+ * predicted starting vectors (pf_nl_opts.predict, allocated by the first nonlinear solve that uses them)
  * and the 2m + 3 FP64 vectors that Anderson acceleration of depth m = accel_depth adds at its first use
  * (0: none) — the figure the server's HBM budget admits requests by.  Needs no device. */
 size_t pf_grid_bytes(int nx, int ny, int nz, int accel_depth);

@@ -66,7 +66,7 @@ def solve_opts(max_iter=20000, tol=1e-10, norm=PF_NORM_REL2, precision=PF_FP64, 
     return o
 
 
-def nl_opts(omega=0.3, tol_outer=1e-9, max_outer=500, accel_depth=0, lin_forcing=0.0, warm_start=0, predict=1,
+def nl_opts(omega=0.3, tol_outer=1e-9, max_outer=500, accel_depth=0, lin_forcing=0.0, warm_start=0, predict=2,
             **lin):
     o = B.pf_nl_opts()
     B.load().pf_default_nl_opts(ctypes.byref(o))

@@ -614,24 +614,110 @@ pf_status unpack_out(pf_grid* g, const double* src, int count, double* dst, int 
   return PF_OK;
 }
 
-// Starting vector of a linear solve in the outer iteration: x <- x + c (x - x_prev), x_prev <- the old x (the last
-// two solutions of the same system extrapolated along their last change; c = 0 keeps x and only saves it).
-__global__ void k_predict(double* __restrict__ x, double* __restrict__ xprev, double c, long n) {
+// Starting vectors of the linear solves of the outer iteration (pf_nl_opts.predict).  x holds the last solution
+// x_{k-1}; h0 and h1 the two before it (x_{k-2}, x_{k-3}).  The next start is x_{k-1} + c (x_{k-1} - x_{k-2}).
+constexpr int PREDICT_THREADS = 256;
+
+// Block partials of d1.d0 and d0.d0 (d1 = x - h0, d0 = h0 - h1) into part[2 b], part[2 b + 1].
+__global__ void __launch_bounds__(PREDICT_THREADS) k_predict_dots(const double* __restrict__ x,
+                                                                  const double* __restrict__ h0,
+                                                                  const double* __restrict__ h1, long n,
+                                                                  double* __restrict__ part) {
+  __shared__ double sh[2][PREDICT_THREADS / 32];
+  double a = 0.0, b = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const double t = x[i];
-    x[i] = fma(c, t - xprev[i], t);
-    xprev[i] = t;
+    const double p = h0[i];
+    const double d1 = x[i] - p, d0 = p - h1[i];
+    a = fma(d1, d0, a);
+    b = fma(d0, d0, b);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][w] = a;
+    sh[1][w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < PREDICT_THREADS / 32; ++k) {
+      sa += sh[0][k];
+      sb += sh[1][k];
+    }
+    part[2 * blockIdx.x] = sa;
+    part[2 * blockIdx.x + 1] = sb;
   }
 }
 
-pf_status predict(pf_grid* g, double* x, double* xprev, double c) {
+// x <- x + c (x - h0) and hnew <- the old x.  With nparts > 0 every block first sums the nparts block partials of
+// k_predict_dots in the same fixed order and takes c = d1.d0 / d0.d0 clamped to [0, 1] (0 when d0 = 0); else
+// c = c_fixed, and with c_fixed = 0 x is kept and h0 is not read.
+__global__ void __launch_bounds__(PREDICT_THREADS) k_predict(double* __restrict__ x, const double* __restrict__ h0,
+                                                             double* __restrict__ hnew, double c_fixed,
+                                                             const double* __restrict__ part, int nparts, long n) {
+  __shared__ double sh[2][PREDICT_THREADS];
+  double c = c_fixed;
+  if (nparts > 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += PREDICT_THREADS) {
+      a += part[2 * k];
+      b += part[2 * k + 1];
+    }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int st = PREDICT_THREADS / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+        sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+      }
+      __syncthreads();
+    }
+    const double num = sh[0][0], den = sh[1][0];
+    c = den > 0.0 ? num / den : 0.0;
+    c = c > 0.0 ? (c < 1.0 ? c : 1.0) : 0.0;  // also maps a NaN ratio to 0
+  }
+  const bool extrapolate = c != 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double t = x[i];
+    if (extrapolate) x[i] = fma(c, t - h0[i], t);
+    hnew[i] = t;
+  }
+}
+
+// have = solutions of this system so far in this solve (>= 1).  have = 1 only saves x; have = 2 extrapolates with
+// c_fallback (the outer updates' ratio); from have = 3 on, with c from the vector's own last two changes.  The
+// history pointers rotate, so the newest previous solution is always h0.
+pf_status predict(pf_grid* g, double* x, double*& h0, double*& h1, int have, double c_fallback) {
   const long n = g->geom.np;
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  long blocks = (n + 255) / 256;
-  if (blocks > 8L * nsm) blocks = 8L * nsm;
-  PF_LAUNCH(g, PF_PROF_OTHER, (k_predict<<<(int)blocks, 256, 0, g->stream>>>(x, xprev, c, n), cudaGetLastError()));
+  long blocks = (n + PREDICT_THREADS - 1) / PREDICT_THREADS;
+  if (blocks > 8L * nsm) blocks = 8L * nsm;  // partials: 2 per block, well inside the grid's partials buffer
+  cudaStream_t s = g->stream;
+  if (have <= 1) {
+    PF_LAUNCH(g, PF_PROF_OTHER,
+              (k_predict<<<(int)blocks, PREDICT_THREADS, 0, s>>>(x, nullptr, h0, 0.0, nullptr, 0, n),
+               cudaGetLastError()));
+    return PF_OK;
+  }
+  int nparts = 0;
+  if (have >= 3) {
+    PF_LAUNCH(g, PF_PROF_OTHER,
+              (k_predict_dots<<<(int)blocks, PREDICT_THREADS, 0, s>>>(x, h0, h1, n, g->part), cudaGetLastError()));
+    nparts = (int)blocks;
+  }
+  PF_LAUNCH(g, PF_PROF_OTHER,
+            (k_predict<<<(int)blocks, PREDICT_THREADS, 0, s>>>(x, h0, h1, have >= 3 ? 0.0 : c_fallback, g->part,
+                                                                 nparts, n),
+             cudaGetLastError()));
+  double* t = h0;  // h1 now holds x_{k-1}, h0 x_{k-2}
+  h0 = h1;
+  h1 = t;
   return PF_OK;
 }
 
@@ -653,7 +739,9 @@ double final_inner_tol2(const pf_solve_opts& o, double rr, double t2) {
 pf_status ensure_predict(pf_grid* g) {
   if (g->xp_psi) return PF_OK;
   PF_TRY(dalloc(g, &g->xp_psi, g->geom.np));
+  PF_TRY(dalloc(g, &g->xpp_psi, g->geom.np));
   PF_TRY(dalloc(g, &g->xp_phi, g->geom.np));
+  PF_TRY(dalloc(g, &g->xpp_phi, g->geom.np));
   return PF_OK;
 }
 
@@ -831,10 +919,10 @@ void pf_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
 // Device bytes that pf_create_grid allocates for a grid (used for the serving budget).
 size_t pf_internal_grid_bytes(int nx, int ny, int nz, int accel_depth) {
   const pf::Geom g = pf::make_geom(nx, ny, nz);
-  // Anderson acceleration adds f, f_prev, x_prev and two history columns per depth; the count includes the two
-  // vectors of the predicted starting vectors (pf_nl_opts.predict = 1, the default)
+  // Anderson acceleration adds f, f_prev, x_prev and two history columns per depth; the count includes the four
+  // history vectors of the predicted starting vectors (pf_nl_opts.predict, on by default)
   const int aa = accel_depth > 0 ? 3 + 2 * accel_depth : 0;
-  const size_t per_node = (34 + aa) * sizeof(double) + pf::MAXSP * sizeof(double) + 18 * sizeof(float) + 1;
+  const size_t per_node = (36 + aa) * sizeof(double) + pf::MAXSP * sizeof(double) + 18 * sizeof(float) + 1;
   return (size_t)g.np * per_node + (size_t)pf::max_partial_blocks() * pf::NPART * sizeof(double) + 8192;
 }
 
@@ -865,7 +953,7 @@ void pf_default_nl_opts(pf_nl_opts* o) {
   o->accel_depth = 0;
   o->lin_forcing = 0.0;
   o->warm_start = 0;
-  o->predict = 1;
+  o->predict = 2;
 }
 
 const char* pf_last_error(void) { return g_err.c_str(); }
@@ -1301,7 +1389,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
       o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0))
     return fail(PF_E_INVAL, "invalid pf_nl_opts");
   if (o.warm_start != 0 && o.warm_start != 1) return fail(PF_E_INVAL, "invalid pf_nl_opts");
-  if (o.predict != 0 && o.predict != 1) return fail(PF_E_INVAL, "invalid pf_nl_opts.predict");
+  if (o.predict < 0 || o.predict > 2) return fail(PF_E_INVAL, "invalid pf_nl_opts.predict");
   if (o.warm_start && !g->have_phi0)
     return fail(PF_E_INVAL, "warm_start needs a potential on the grid (a previous solve or pf_set_potential)");
   const int m = o.accel_depth;
@@ -1340,9 +1428,11 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
   OuterUpdate U;
   double delta_prev = 1.0, delta_prev2 = 0.0;
   for (int outer = 1; st == PF_OK && outer <= o.max_outer; ++outer) {
-    // starting vectors (pf_nl_opts.predict): from the third outer iteration on, the previous two solutions
-    // extrapolated with c = delta_{k-1} / delta_{k-2} while the outer updates shrink
+    // starting vectors (pf_nl_opts.predict): from the third outer iteration on, the last solution extrapolated
+    // along its last change, with c = delta_{k-1} / delta_{k-2} while the outer updates shrink (predict = 1, and
+    // predict = 2 in the third), and with c from the vector's own last two changes from the fourth on (predict = 2)
     const int have = outer - 1;  // PF1 / PF2 solutions of this solve so far
+    const int pred_have = o.predict == 1 && have > 2 ? 2 : have;
     const double c_pred =
         (o.predict && have >= 2 && delta_prev2 > 0.0 && delta_prev < delta_prev2) ? delta_prev / delta_prev2 : 0.0;
     // forcing term: the linear solves of this outer iteration stop at eta ||r0|| (r0: the residual of the warm
@@ -1361,7 +1451,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
                                                    g->err, s));
     if (g->filter_on) PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_zero(g->fmask, G, g->b1, 1, s));  // Psi = 0
     PF_TRY(update_pf2(g));
-    if (o.predict && have >= 1) PF_TRY(predict(g, g->psi, g->xp_psi, c_pred));
+    if (o.predict && have >= 1) PF_TRY(predict(g, g->psi, g->xp_psi, g->xpp_psi, pred_have, c_pred));
     PF_TRY(solve_dev(g, PF_OP_PF1, g->b1, g->psi, lo, &rep, eta));  // Eq. (12)
     res->lin_iters_total += rep.iterations;
     if (rep.status != PF_OK) { st = (pf_status)rep.status; break; }
@@ -1369,7 +1459,7 @@ pf_status pf_nonlinear_solve(pf_grid* g, const pf_nl_opts* opts, pf_result* res)
               pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat, G, g->b2, s));
     if (g->filter_on) PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_filter_values(g->fmask, g->fval, G, g->b2, s));
     if (o.predict && have >= 1)
-      PF_TRY(predict(g, g->phi, g->xp_phi, c_pred));  // from the previous PF2 solution
+      PF_TRY(predict(g, g->phi, g->xp_phi, g->xpp_phi, pred_have, c_pred));  // from the previous PF2 solutions
     else
       PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
     PF_TRY(solve_dev(g, PF_OP_PF2, g->b2, g->phi, lo, &rep, eta));  // Eq. (13)

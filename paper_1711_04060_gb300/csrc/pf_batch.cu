@@ -546,10 +546,11 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
                                                      g->c2, nullptr, nullptr, nullptr, g->ulast,
                                                      outer > 1 || M.fermi_warm, g->err, s));
       PF_TRY(update_pf2(g));
-      // starting vectors as pf_nonlinear_solve: the last two solutions extrapolated while the updates shrink
+      // starting vectors as pf_nonlinear_solve (pf_nl_opts.predict)
       const bool pred = M.o.predict && outer >= 2;
       M.cpred = (pred && outer >= 3 && M.dprev2 > 0.0 && M.dprev < M.dprev2) ? M.dprev / M.dprev2 : 0.0;
-      if (pred) PF_TRY(predict(g, g->psi, g->xp_psi, M.cpred));
+      M.pred_have = M.o.predict == 1 && outer - 1 > 2 ? 2 : outer - 1;
+      if (pred) PF_TRY(predict(g, g->psi, g->xp_psi, g->xpp_psi, M.pred_have, M.cpred));
       PF_TRY(lin_start(B, M, PF_OP_PF1, S_PF2RHS, eta));
       break;
     }
@@ -558,7 +559,7 @@ pf_status pre(pf_batch* B, BatchMember& M, std::vector<int>& kinds) {
       PF_LAUNCH(g, PF_PROF_OTHER, pf::launch_pf2_rhs(g->psi, g->solvent, g->c2, g->eps_s, g->lo_hat, g->hi_hat,
                                                      g->geom, g->b2, s));
       if (M.o.predict && M.res->outer_iters >= 1)
-        PF_TRY(predict(g, g->phi, g->xp_phi, M.cpred));  // from the previous PF2 solution
+        PF_TRY(predict(g, g->phi, g->xp_phi, g->xpp_phi, M.pred_have, M.cpred));  // from the previous PF2 solutions
       else
         PF_CK(cudaMemcpyAsync(g->phi, g->phi0, NP * sizeof(double), cudaMemcpyDeviceToDevice, s));
       PF_TRY(lin_start(B, M, PF_OP_PF2, S_UPDATE, M.eta));
@@ -882,7 +883,7 @@ pf_status check_nl(const pf_nl_opts& o) {
     return fail(PF_E_INVAL, "batches and served requests solve with BiCGSTAB (pf_solve_opts.method = PF_BICGSTAB)");
   if (!(o.omega >= 0 && o.omega < 1) || !(o.tol_outer > 0) || o.max_outer < 1 || o.accel_depth < 0 ||
       o.accel_depth > pf::AA_MAX || !(o.lin_forcing >= 0) || (o.warm_start != 0 && o.warm_start != 1) ||
-      (o.predict != 0 && o.predict != 1))
+      o.predict < 0 || o.predict > 2)
     return fail(PF_E_INVAL, "invalid pf_nl_opts");
   return PF_OK;
 }

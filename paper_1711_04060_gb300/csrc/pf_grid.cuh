@@ -88,8 +88,9 @@ struct pf_grid {
   // Anderson acceleration of the outer loop (allocated on first use)
   int aa_alloc = 0;
   double *aa_f = nullptr, *aa_fprev = nullptr, *aa_xprev = nullptr, *aa_out = nullptr, *aa_host = nullptr;
-  // the PF1 and PF2 solutions of the outer iteration before the last one (pf_nl_opts.predict; on first use)
-  double *xp_psi = nullptr, *xp_phi = nullptr;
+  // the PF1 and PF2 solutions of the two outer iterations before the last one, newest first (pf_nl_opts.predict;
+  // on first use; the pointers of a pair swap as the history moves on)
+  double *xp_psi = nullptr, *xpp_psi = nullptr, *xp_phi = nullptr, *xpp_phi = nullptr;
   double *aa_dF[pf::AA_MAX] = {}, *aa_dX[pf::AA_MAX] = {};
   double* dch = nullptr;     // fixed charges (x, y, z, q) on the device
   int nq = 0;
@@ -221,10 +222,11 @@ pf_status build_operators(pf_grid* g);
 pf_status pack_in(pf_grid* g, const void* src, int mem, void* dst, int type);
 pf_status unpack_out(pf_grid* g, const double* src, int count, double* dst, int mem);
 pf_status ensure_aa(pf_grid* g, int m);
-// x <- x + c (x - xprev), xprev <- the old x: the starting vector of a linear solve of the outer iteration
-// (pf_nl_opts.predict); both vectors FP64 over the padded grid
-pf_status predict(pf_grid* g, double* x, double* xprev, double c);
-// the two FP64 vectors of pf_nl_opts.predict, allocated on first use
+// The starting vector of a linear solve of the outer iteration (pf_nl_opts.predict) from the last solution x and
+// the two before it (h0 newest; the pointers rotate): have = solutions so far (1: x only saved; 2: extrapolated
+// with c_fallback; 3 and more: with c from the vector's own last two changes).  FP64 over the padded grid.
+pf_status predict(pf_grid* g, double* x, double*& h0, double*& h1, int have, double c_fallback);
+// the four FP64 vectors of pf_nl_opts.predict, allocated on first use
 pf_status ensure_predict(pf_grid* g);
 // Squared 2-norm stop of the FP32 inner solve of a refinement step, given the step's FP64 residual norm^2 rr and
 // the solve's squared target t2 (REL2 only): FINAL_INNER_MARGIN^2 t2 when that is above inner_tol^2 rr, else 0
@@ -257,6 +259,7 @@ struct BatchMember {
   double dprev = 1.0;   // delta of the previous outer iteration (forcing term)
   double dprev2 = 0.0;  // delta of the one before (pf_nl_opts.predict)
   double cpred = 0.0;   // extrapolation factor of this outer iteration's starting vectors
+  int pred_have = 0;    // history length predict() is given in this outer iteration
   double inner_t2 = 0.0;  // squared stop of the next FP32 inner solve when it may end the refinement (else 0)
   int stage = 0;        // step of the nonlinear iteration (pf_batch.cu: Stage)
   int after = 0;        // stage to enter when the running linear solve ends

@@ -20,7 +20,7 @@ def test_option_structs(api):
     assert n.warm_start == 0
     # the library's defaults: the paper's relaxation and tolerances, extrapolated starting vectors, BiCGSTAB
     d = api.nl_opts()
-    assert (d.omega, d.tol_outer, d.accel_depth, d.lin_forcing, d.predict) == (0.3, 1e-9, 0, 0.0, 1)
+    assert (d.omega, d.tol_outer, d.accel_depth, d.lin_forcing, d.predict) == (0.3, 1e-9, 0, 0.0, 2)
     assert (d.lin.method, d.lin.precision, d.lin.inner_tol) == (api.PF_BICGSTAB, api.PF_FP64, 0.1)
     assert api.nl_opts(predict=0).predict == 0
 

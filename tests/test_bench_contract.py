@@ -134,10 +134,10 @@ def test_oracle_baseline_charged_its_own_iterations():
     import bench
     fp64 = {"outer_iters": 188, "lin_iters_total": 6152}
     head = {"outer_iters": 188, "lin_iters_total": 6810}
-    A = lambda **kw: type("A", (), dict(dict(n=257, tol_outer=1e-3, lin_tol=1e-6, predict=1), **kw))
+    A = lambda **kw: type("A", (), dict(dict(n=257, tol_outer=1e-3, lin_tol=1e-6, predict=2), **kw))
     o, l, what = bench.oracle_work(A(), fp64, head)
     assert (o, l) == (bench.REF_WORK["outer"], bench.REF_WORK["lin_iters"]) and "previous iterates" in what
     o, l, what = bench.oracle_work(A(n=129), fp64, head)
-    assert (o, l) == (188, 6152) and "predict = 1" in what
+    assert (o, l) == (188, 6152) and "predict = 2" in what
     o, l, what = bench.oracle_work(A(lin_tol=1e-8), None, head)
     assert (o, l) == (188, 6810)

@@ -257,28 +257,32 @@ def test_nonlinear_accelerated_same_fixed_point(api, orc, precision, depth, forc
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_predicted_starts_same_fixed_point_fewer_iterations(api, orc, precision):
     """The linear solves' starting vectors change the path, not the fixed point: with the previous iterates
-    (predict = 0) the potential and concentrations agree with the oracle as with the extrapolated starts that
-    every other test uses (predict = 1, the default); at the paper's tolerances the extrapolated starts need
-    fewer BiCGSTAB iterations for the same number of outer iterations."""
+    (predict = 0) and with the outer updates' ratio (predict = 1) the potential and concentrations agree with the
+    oracle as with each vector's own ratio that every other test uses (predict = 2, the default); at the paper's
+    tolerances the extrapolated starts need fewer BiCGSTAB iterations for the same number of outer iterations."""
     tol = TOL_FP64 if precision == "fp64" else TOL_MIXED
     _nl_compare(api, orc, W.config0(), precision, tol, predict=0)
+    _nl_compare(api, orc, W.config0(), precision, tol, predict=1)
     prob = W.config0()
     grid = api.Grid.for_problem(prob)
     prec = api.PF_FP64 if precision == "fp64" else api.PF_MIXED
-    o1, r1 = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-3, tol=1e-6, precision=prec, predict=1))
-    o0, r0 = grid.nonlinear_solve(api.nl_opts(tol_outer=1e-3, tol=1e-6, precision=prec, predict=0))
+    runs = {k: grid.nonlinear_solve(api.nl_opts(tol_outer=1e-3, tol=1e-6, precision=prec, predict=k))
+            for k in (2, 1, 0)}
     grid.close()
-    assert r1["status"] == 0 and r0["status"] == 0
-    assert abs(r1["outer_iters"] - r0["outer_iters"]) <= 1
+    (o2, r2), (o1, r1), (o0, r0) = runs[2], runs[1], runs[0]
+    assert r2["status"] == 0 and r1["status"] == 0 and r0["status"] == 0
+    assert abs(r1["outer_iters"] - r0["outer_iters"]) <= 1 and abs(r2["outer_iters"] - r0["outer_iters"]) <= 1
     assert r1["lin_iters_total"] < r0["lin_iters_total"], (r1["lin_iters_total"], r0["lin_iters_total"])
-    assert _rel(o1["phi_V"], o0["phi_V"]) < 1e-4
+    assert r2["lin_iters_total"] < r0["lin_iters_total"], (r2["lin_iters_total"], r0["lin_iters_total"])
+    assert _rel(o1["phi_V"], o0["phi_V"]) < 1e-4 and _rel(o2["phi_V"], o0["phi_V"]) < 1e-4
 
 
 def test_nonlinear_options_rejected(api):
     prob = W.channel_problem(9, box_half=4.0, slab_half=1.0, pores=((0, 0, 2.0),), n_charges=0)
     grid = api.Grid.for_problem(prob)
     try:
-        for bad in (dict(accel_depth=9), dict(accel_depth=-1), dict(lin_forcing=-1.0), dict(predict=2)):
+        for bad in (dict(accel_depth=9), dict(accel_depth=-1), dict(lin_forcing=-1.0), dict(predict=3),
+                    dict(predict=-1)):
             with pytest.raises(api.PFError) as e:
                 grid.nonlinear_solve(api.nl_opts(**bad))
             assert e.value.status == 1  # PF_E_INVAL
