@@ -800,6 +800,8 @@ def run_ours(args):
             "data": "synthetic (seeded channel geometry, wall charges and bath; no dataset)",
             "config": config_of(args), "precision": args.precision, "method": args.method,
             "inner_tol": args.inner_tol,
+            "starting_vectors": {0: "previous iterates", 1: "extrapolated, outer updates' ratio",
+                                 2: "extrapolated, each vector's own ratio"}[args.predict],
             "clocks": clocks, "gpu_launches": int(prof["launches"]),
             "roofline": roofline,
             "solve": {"outer_iters": reps[-1]["outer_iters"], "lin_iters": reps[-1]["lin_iters_total"],
