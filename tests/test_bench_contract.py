@@ -141,3 +141,19 @@ def test_oracle_baseline_charged_its_own_iterations():
     assert (o, l) == (188, 6152) and "predict = 2" in what
     o, l, what = bench.oracle_work(A(lin_tol=1e-8), None, head)
     assert (o, l) == (188, 6810)
+
+
+def test_kernel_traffic_follows_the_source_hash(monkeypatch):
+    """roofline.traffic comes from the committed ncu figures only while the stencil sources hash as they did when
+    the figures were captured; any other source gives null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for kind in ("ca_fp32", "b_fp32"):
+        e = d[kind]
+        assert e["dram_bytes_per_node"] >= e["algorithmic_bytes_per_node"]
+        if e["kernel_source_sha256_16"] == bench.kernel_source_hash():
+            assert bench.kernel_traffic(kind) == e["dram_bytes_per_node"]
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.kernel_traffic("ca_fp32") is None and bench.kernel_traffic("b_fp32") is None
+    assert bench.kernel_traffic("no_such_kind") is None
