@@ -171,4 +171,56 @@ PF_HD dfl df_exp(dfl x, const float* thi, const float* tlo) {
   return {f_mul(y.hi, sc), f_mul(y.lo, sc)};
 }
 
+// The bit pattern of a double (no arithmetic).
+PF_HD uint64_t d_bits(double v) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(v);
+#else
+  uint64_t u;
+  memcpy(&u, &v, 8);
+  return u;
+#endif
+}
+
+// A double as a double-float pair without FP64 arithmetic (on GB300 a conversion from double issues on the slow
+// FP64 pipe; this split uses integer operations, one integer-to-float conversion and FP32 multiplications).  For
+// v = (1.m) 2^E: hi = v with its 52-bit mantissa cut to the first 23 bits, lo = the remaining 29 bits as an integer
+// rounded to FP32 and scaled by 2^(E-52); FastTwoSum then gives the usual |lo| <= ulp(hi) / 2.  Relative error at
+// most 2^-48 for 2^-97 <= |v| <= the largest float; for 2^-126 <= |v| < 2^-97 lo loses bits (absolute error below
+// 2^-149), below 2^-126 the pair is a signed zero; above the largest float hi is a signed infinity once |v|
+// reaches it plus half its unit, as a conversion to FP32 would round; NaN gives a NaN.
+PF_HD dfl df_from_double_bits(double v) {
+  const uint64_t u = d_bits(v);
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ffu);
+  const uint64_t m = u & 0xfffffffffffffull;
+  if (e == 0x7ff) return {f_from_bits(sign | 0x7f800000u | (m ? 0x400000u : 0u)), 0.0f};
+  const int E = e - 1023;
+  if (E < -126) return {f_from_bits(sign), 0.0f};
+  if (E > 127) return {f_from_bits(sign | 0x7f800000u), 0.0f};
+  const float hi = f_from_bits(sign | ((uint32_t)(E + 127) << 23) | (uint32_t)(m >> 29));
+  const uint32_t rest = (uint32_t)(m & 0x1fffffffu);
+  float lo = (float)rest;  // at most 29 bits: rounded to 24
+  // times 2^(E-52), E - 52 in [-178, 75]: one power-of-two factor when it is a normal float, else two
+  const int k = E - 52;
+  if (k >= -126) {
+    lo = f_mul(lo, f_from_bits((uint32_t)(k + 127) << 23));
+  } else {
+    lo = f_mul(f_mul(lo, f_from_bits((uint32_t)(-64 + 127) << 23)), f_from_bits((uint32_t)(k + 64 + 127) << 23));
+  }
+  if (sign) lo = -lo;
+  return fast_two_sum(hi, lo);
+}
+
+// The residual r = b + sum_k f_k q_k - d x of one row of a 7-point operator (nk couplings f_k to the neighbour
+// values q_k, diagonal d, the node's value x), from FP64 inputs in double-float on the FP32 pipes: each input
+// split by df_from_double_bits, the terms added in the order b, f_0 q_0, ..., f_{nk-1} q_{nk-1}, -d x.  The error
+// stays within about 2^-44 (|b| + sum_k |f_k q_k| + |d x|) for inputs in the range df_from_double_bits keeps to
+// 2^-48, and products within the float range.
+PF_HD dfl df_residual_row(double b, double d, double x, const double* f, const double* q, int nk) {
+  dfl r = df_from_double_bits(b);
+  for (int k = 0; k < nk; ++k) r = df_add(r, df_mul(df_from_double_bits(f[k]), df_from_double_bits(q[k])));
+  return df_add(r, df_neg(df_mul(df_from_double_bits(d), df_from_double_bits(x))));
+}
+
 }  // namespace pf
